@@ -1,0 +1,486 @@
+/*
+ * tmc_oracle.c -- plain, slow, FP64 CPU oracle for the Tensor Monte Carlo estimator
+ * (Aitchison, "Tensor Monte Carlo: Particle Methods for the GPU Era", ICML 2019).
+ *
+ * TEST INFRASTRUCTURE.  Only the test-suite, the smoke check and the benchmark's CPU
+ * baseline leg may load this library.  It shares no source with the CUDA path.
+ *
+ * What it computes (all in double precision, plain loops, no blocking or fusion):
+ *
+ *   Eq. (is):  P_TMC = 1/prod_i K_i * sum_{k_1..k_n} P(x, z_1^{k_1},..,z_n^{k_n}) / prod_i Q(z_i^{k_i})
+ *
+ *   tmc_oracle_brute_force    -- that sum enumerated literally over all prod_i K_i sample
+ *                                combinations (log-sum-exp over combinations).
+ *   tmc_oracle_log_marginal   -- the same quantity by summing out one index at a time
+ *                                (Section 2.2 "Efficient averaging": the importance ratio is a
+ *                                product of factors, Eq. (fac); sums over the indices of leaves
+ *                                are pushed inside, as in the latent-variable example of
+ *                                Fig. 2), using the factor choice of the Appendix ("Typical
+ *                                choice of factors for a directed graphical model").
+ *   tmc_oracle_grad           -- the adjoint of that recursion: gradient of log P_TMC with
+ *                                respect to the samples, the model parameters and the proposal
+ *                                parameters under the reparameterisation z = m + exp(logs)*eps.
+ *
+ * Model: z_0 ~ N(bias_0, prior_var I); z_i | z_p ~ N(W_i z_p + bias_i, prior_var I) for i >= 1
+ * with p = parent[i] < i; every leaf l carries x_l ~ N(C z_l, obs_var I).
+ * Proposal: Q_i(z) = N(z; m_i, diag(exp(2 logs_i))), samples z_i^k = m_i + exp(logs_i) eps_i^k.
+ *
+ * Factors (Appendix):  f_i^{(k_i, k_p)} = P(z_i^{k_i} | z_p^{k_p}) / Q_i(z_i^{k_i})   (i >= 1)
+ *                      f_0^{k_0}        = P(z_0^{k_0}) / Q_0(z_0^{k_0})
+ *                      g_l^{k_l}        = P(x_l | z_l^{k_l})                          (leaves)
+ *
+ * Log-sum-exp subtracts the maximum of the whole exponent being summed (one combined
+ * maximum), which is exact in real arithmetic and cannot underflow every term.
+ *
+ * Flat layouts: see tmc_oracle.h.
+ */
+#include "tmc_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define LOG_2PI 1.8378770664093454835606594728112
+
+/* ---------------------------------------------------------------------------------------
+ * Instance view: pointers into the flat arrays for one instance b.
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+  int n, K, d, obs;
+  const int* parent;
+  const double *eps, *m, *logs, *W, *bias, *C, *x;
+  double prior_var, obs_var;
+  int* leaf_slot; /* leaf_slot[i] = index of leaf i among the instance's leaves, or -1 */
+  int n_children_max;
+} inst_t;
+
+typedef struct {
+  long long eps, q, x, W, bias, C, parent;
+} offs_t;
+
+static int count_leaves(int n, const int* parent, int* leaf_slot) {
+  int i, nl = 0;
+  for (i = 0; i < n; ++i) leaf_slot[i] = 0;
+  for (i = 1; i < n; ++i) leaf_slot[parent[i]] = -1; /* has a child */
+  for (i = 0; i < n; ++i) {
+    if (leaf_slot[i] == 0) leaf_slot[i] = nl++;
+    else leaf_slot[i] = -1;
+  }
+  return nl;
+}
+
+static int validate(int B, const int* n, const int* parent, const int* K, const int* d,
+                    const int* obs) {
+  long long off = 0;
+  int b, i;
+  for (b = 0; b < B; ++b) {
+    if (n[b] < 1 || K[b] < 1 || d[b] < 1 || obs[b] < 1) return TMC_ORACLE_BAD_ARG;
+    if (parent[off] != -1) return TMC_ORACLE_BAD_ARG;
+    for (i = 1; i < n[b]; ++i)
+      if (parent[off + i] < 0 || parent[off + i] >= i) return TMC_ORACLE_BAD_ARG;
+    off += n[b];
+  }
+  return TMC_ORACLE_OK;
+}
+
+/* z_i^k = m_i + exp(logs_i) * eps_i^k (reparameterised sample). */
+static void sample(const inst_t* I, int i, int k, double* z) {
+  int j;
+  const double* e = I->eps + ((long long)i * I->K + k) * I->d;
+  for (j = 0; j < I->d; ++j) z[j] = I->m[i * I->d + j] + exp(I->logs[i * I->d + j]) * e[j];
+}
+
+/* log N(y; mean, var I) in dimension dim. */
+static double log_normal_iso(const double* y, const double* mean, int dim, double var) {
+  double s = 0.0;
+  int j;
+  for (j = 0; j < dim; ++j) {
+    double r = y[j] - mean[j];
+    s += r * r;
+  }
+  return -0.5 * s / var - 0.5 * dim * (LOG_2PI + log(var));
+}
+
+/* log Q_i(z) for the diagonal Gaussian proposal, evaluated as a density of z. */
+static double log_q(const inst_t* I, int i, const double* z) {
+  double s = 0.0;
+  int j;
+  for (j = 0; j < I->d; ++j) {
+    double ls = I->logs[i * I->d + j];
+    double r = (z[j] - I->m[i * I->d + j]) * exp(-ls);
+    s += -0.5 * r * r - ls - 0.5 * LOG_2PI;
+  }
+  return s;
+}
+
+/* mean of z_i given its parent sample: W_i zp + bias_i (i >= 1), or bias_0 for the root. */
+static void cond_mean(const inst_t* I, int i, const double* zp, double* mu) {
+  int r, c, d = I->d;
+  for (r = 0; r < d; ++r) {
+    double s = I->bias[i * d + r];
+    if (i > 0)
+      for (c = 0; c < d; ++c) s += I->W[((long long)i * d + r) * d + c] * zp[c];
+    mu[r] = s;
+  }
+}
+
+/* log P(x_l | z) at leaf l. */
+static double log_obs(const inst_t* I, int leaf_slot, const double* z, double* pred) {
+  int o, c;
+  const double* xl = I->x + (long long)leaf_slot * I->obs;
+  for (o = 0; o < I->obs; ++o) {
+    double s = 0.0;
+    for (c = 0; c < I->d; ++c) s += I->C[(long long)o * I->d + c] * z[c];
+    pred[o] = s;
+  }
+  return log_normal_iso(xl, pred, I->obs, I->obs_var);
+}
+
+static double logsumexp(const double* v, int len) {
+  double mx = -INFINITY, s = 0.0;
+  int k;
+  for (k = 0; k < len; ++k)
+    if (v[k] > mx) mx = v[k];
+  if (mx == -INFINITY) return -INFINITY;
+  for (k = 0; k < len; ++k) s += exp(v[k] - mx);
+  return mx + log(s);
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Per-instance workspace.
+ *   z[i][k][:]      samples
+ *   mu[i][kp][:]    conditional mean of z_i given parent sample kp (i >= 1)
+ *   node[i][k]      log of everything indexed by k_i alone: -log Q_i, plus log P(z_0) at the
+ *                   root, plus log P(x_i | z_i) at a leaf
+ *   logg[i][k]      node[i][k] + sum over children c of logmsg[c][k]
+ *   logmsg[i][kp]   message of node i to its parent: log(1/K sum_k f_i^{(k,kp)} * children)
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+  double *z, *mu, *node, *logg, *logmsg;
+  double* pred;
+} ws_t;
+
+static int ws_alloc(ws_t* w, const inst_t* I) {
+  long long nkd = (long long)I->n * I->K * I->d, nk = (long long)I->n * I->K;
+  w->z = (double*)calloc(nkd, sizeof(double));
+  w->mu = (double*)calloc(nkd, sizeof(double));
+  w->node = (double*)calloc(nk, sizeof(double));
+  w->logg = (double*)calloc(nk, sizeof(double));
+  w->logmsg = (double*)calloc(nk, sizeof(double));
+  w->pred = (double*)calloc(I->obs, sizeof(double));
+  return (w->z && w->mu && w->node && w->logg && w->logmsg && w->pred) ? 0 : -1;
+}
+
+static void ws_free(ws_t* w) {
+  free(w->z); free(w->mu); free(w->node); free(w->logg); free(w->logmsg); free(w->pred);
+}
+
+#define Z(w, I, i, k) ((w)->z + ((long long)(i) * (I)->K + (k)) * (I)->d)
+#define MU(w, I, i, k) ((w)->mu + ((long long)(i) * (I)->K + (k)) * (I)->d)
+
+/* log f_i^{(k, kp)} for i >= 1: log P(z_i^k | z_p^kp) (the -log Q_i part lives in node[]). */
+static double log_pair(const ws_t* w, const inst_t* I, int i, int k, int kp) {
+  return log_normal_iso(Z(w, I, i, k), MU(w, I, i, kp), I->d, I->prior_var);
+}
+
+/* Forward recursion; returns log P_TMC of the instance. */
+static double instance_forward(const inst_t* I, ws_t* w) {
+  int n = I->n, K = I->K, d = I->d, i, k, kp;
+  double root_mean_dummy = 0.0;
+  (void)root_mean_dummy;
+  for (i = 0; i < n; ++i)
+    for (k = 0; k < K; ++k) sample(I, i, k, Z(w, I, i, k));
+  for (i = 1; i < n; ++i) {
+    int p = I->parent[i];
+    for (kp = 0; kp < K; ++kp) cond_mean(I, i, Z(w, I, p, kp), MU(w, I, i, kp));
+  }
+  for (i = 0; i < n; ++i)
+    for (k = 0; k < K; ++k) {
+      const double* z = Z(w, I, i, k);
+      double v = -log_q(I, i, z);
+      if (i == 0) v += log_normal_iso(z, I->bias, d, I->prior_var);
+      if (I->leaf_slot[i] >= 0) v += log_obs(I, I->leaf_slot[i], z, w->pred);
+      w->node[(long long)i * K + k] = v;
+    }
+  /* logg starts as node; children (larger index) add their messages before the parent's
+     own message is formed because we sweep i from n-1 down to 0. */
+  memcpy(w->logg, w->node, sizeof(double) * (size_t)n * K);
+  for (i = n - 1; i >= 1; --i) {
+    int p = I->parent[i];
+#pragma omp parallel for if (K >= 64) schedule(static)
+    for (kp = 0; kp < K; ++kp) {
+      double* t = (double*)malloc(sizeof(double) * K);
+      int kk;
+      for (kk = 0; kk < K; ++kk)
+        t[kk] = log_pair(w, I, i, kk, kp) + w->logg[(long long)i * K + kk];
+      w->logmsg[(long long)i * K + kp] = logsumexp(t, K) - log((double)K);
+      free(t);
+    }
+    for (kp = 0; kp < K; ++kp) w->logg[(long long)p * K + kp] += w->logmsg[(long long)i * K + kp];
+  }
+  return logsumexp(w->logg, K) - log((double)K);
+}
+
+static void make_instance(inst_t* I, int b, const offs_t* o, const int* n, const int* parent,
+                          const int* K, const int* d, const int* obs, double prior_var,
+                          double obs_var, const double* eps, const double* q_mean,
+                          const double* q_logstd, const double* W, const double* bias,
+                          const double* C, const double* x, int* leaf_slot) {
+  (void)b;
+  I->n = n[b]; I->K = K[b]; I->d = d[b]; I->obs = obs[b];
+  I->parent = parent + o->parent;
+  I->eps = eps + o->eps;
+  I->m = q_mean + o->q;
+  I->logs = q_logstd + o->q;
+  I->W = W + o->W;
+  I->bias = bias + o->bias;
+  I->C = C + o->C;
+  I->x = x + o->x;
+  I->prior_var = prior_var;
+  I->obs_var = obs_var;
+  I->leaf_slot = leaf_slot;
+}
+
+static void advance(offs_t* o, int b, const int* n, const int* K, const int* d, const int* obs,
+                    int shared, int nleaves) {
+  o->eps += (long long)n[b] * K[b] * d[b];
+  o->q += (long long)n[b] * d[b];
+  o->x += (long long)nleaves * obs[b];
+  o->parent += n[b];
+  if (!shared) {
+    o->W += (long long)n[b] * d[b] * d[b];
+    o->bias += (long long)n[b] * d[b];
+    o->C += (long long)obs[b] * d[b];
+  }
+}
+
+int tmc_oracle_log_marginal(int B, const int* n, const int* parent, const int* K, const int* d,
+                            const int* obs, int shared, double prior_var, double obs_var,
+                            const double* eps, const double* q_mean, const double* q_logstd,
+                            const double* W, const double* bias, const double* C,
+                            const double* x, double* log_phat) {
+  offs_t o;
+  int b, rc = validate(B, n, parent, K, d, obs);
+  if (rc) return rc;
+  memset(&o, 0, sizeof(o));
+  for (b = 0; b < B; ++b) {
+    inst_t I;
+    ws_t w;
+    int* slot = (int*)malloc(sizeof(int) * n[b]);
+    int nl = count_leaves(n[b], parent + o.parent, slot);
+    make_instance(&I, b, &o, n, parent, K, d, obs, prior_var, obs_var, eps, q_mean, q_logstd,
+                  W, bias, C, x, slot);
+    if (ws_alloc(&w, &I)) { free(slot); return TMC_ORACLE_NOMEM; }
+    log_phat[b] = instance_forward(&I, &w);
+    ws_free(&w);
+    free(slot);
+    advance(&o, b, n, K, d, obs, shared, nl);
+  }
+  return TMC_ORACLE_OK;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Adjoint.  With L = log P_TMC:
+ *   weight of a root sample   w_0[k]   = exp(logg_0[k] - log K_0 - L)
+ *   weight of an edge entry   pi_i[kp][k] = w_p[kp] * exp(log f_i^{(k,kp)} + logg_i[k]
+ *                                              - log K_i - logmsg_i[kp])
+ *   weight of a sample        w_i[k]   = sum_kp pi_i[kp][k]
+ * dL/d(log f_i^{(k,kp)}) = pi_i[kp][k]; dL/d(node_i[k]) = w_i[k].
+ * Samples: dz = sum over factors touching z of weight * d(log factor)/dz, with -log Q taken
+ * as a density of z at fixed (m, logs).  Reparameterisation: z = m + exp(logs) eps, and
+ * -log Q(m + exp(logs) eps) = sum_j (eps_j^2/2 + logs_j + log(2 pi)/2), so with
+ * g = dz - w * (z - m)/exp(2 logs)  (dz without the proposal's own score):
+ *   dm = sum_k g,   dlogs = sum_k w + sum_k g * (z - m).
+ * ------------------------------------------------------------------------------------- */
+static void instance_backward(const inst_t* I, ws_t* w, double L, double go, double* dz,
+                              double* dm, double* dlogs, double* dW, double* dbias, double* dC) {
+  int n = I->n, K = I->K, d = I->d, i, k, kp, j, c;
+  double var = I->prior_var;
+  double* wt = (double*)calloc((size_t)n * K, sizeof(double));
+  double* dmu = (double*)calloc((size_t)K * d, sizeof(double));
+  double* dzl = (double*)calloc((size_t)n * K * d, sizeof(double));
+  double* pred = (double*)calloc(I->obs, sizeof(double));
+  for (k = 0; k < K; ++k) wt[k] = exp(w->logg[k] - log((double)K) - L);
+  for (i = 1; i < n; ++i) {
+    int p = I->parent[i];
+    memset(dmu, 0, sizeof(double) * (size_t)K * d);
+    /* rows kp: parent sample; columns k: child sample */
+#pragma omp parallel for if (K >= 64) schedule(static) private(k, j)
+    for (kp = 0; kp < K; ++kp) {
+      const double* mu = MU(w, I, i, kp);
+      for (k = 0; k < K; ++k) {
+        const double* z = Z(w, I, i, k);
+        double pi = wt[(long long)p * K + kp] *
+                    exp(log_pair(w, I, i, k, kp) + w->logg[(long long)i * K + k] -
+                        log((double)K) - w->logmsg[(long long)i * K + kp]);
+        for (j = 0; j < d; ++j) dmu[(long long)kp * d + j] += pi * (z[j] - mu[j]) / var;
+      }
+    }
+    /* column direction: weights and sample gradients of the child */
+#pragma omp parallel for if (K >= 64) schedule(static) private(kp, j)
+    for (k = 0; k < K; ++k) {
+      const double* z = Z(w, I, i, k);
+      double acc_w = 0.0;
+      for (kp = 0; kp < K; ++kp) {
+        const double* mu = MU(w, I, i, kp);
+        double pi = wt[(long long)p * K + kp] *
+                    exp(log_pair(w, I, i, k, kp) + w->logg[(long long)i * K + k] -
+                        log((double)K) - w->logmsg[(long long)i * K + kp]);
+        acc_w += pi;
+        for (j = 0; j < d; ++j) dzl[((long long)i * K + k) * d + j] += pi * (mu[j] - z[j]) / var;
+      }
+      wt[(long long)i * K + k] = acc_w;
+    }
+    /* mu_i^kp = W_i z_p^kp + bias_i */
+    for (kp = 0; kp < K; ++kp) {
+      const double* zp = Z(w, I, p, kp);
+      for (j = 0; j < d; ++j) {
+        double g = dmu[(long long)kp * d + j];
+        dbias[i * d + j] += go * g;
+        for (c = 0; c < d; ++c) {
+          dW[((long long)i * d + j) * d + c] += go * g * zp[c];
+          dzl[((long long)p * K + kp) * d + c] += I->W[((long long)i * d + j) * d + c] * g;
+        }
+      }
+    }
+  }
+  /* node terms */
+  for (i = 0; i < n; ++i)
+    for (k = 0; k < K; ++k) {
+      const double* z = Z(w, I, i, k);
+      double wk = wt[(long long)i * K + k];
+      double* g = dzl + ((long long)i * K + k) * d;
+      for (j = 0; j < d; ++j) {
+        double s2 = exp(2.0 * I->logs[i * d + j]);
+        g[j] += wk * (z[j] - I->m[i * d + j]) / s2; /* from -log Q_i(z) */
+      }
+      if (i == 0)
+        for (j = 0; j < d; ++j) {
+          double r = (z[j] - I->bias[j]) / var;
+          g[j] -= wk * r;
+          dbias[j] += go * wk * r;
+        }
+      if (I->leaf_slot[i] >= 0) {
+        const double* xl = I->x + (long long)I->leaf_slot[i] * I->obs;
+        int o;
+        for (o = 0; o < I->obs; ++o) {
+          double s = 0.0;
+          for (c = 0; c < d; ++c) s += I->C[(long long)o * d + c] * z[c];
+          pred[o] = (xl[o] - s) / I->obs_var; /* residual / obs_var */
+        }
+        for (o = 0; o < I->obs; ++o)
+          for (c = 0; c < d; ++c) {
+            g[c] += wk * I->C[(long long)o * d + c] * pred[o];
+            dC[(long long)o * d + c] += go * wk * pred[o] * z[c];
+          }
+      }
+    }
+  /* outputs */
+  for (i = 0; i < n; ++i) {
+    double wsum = 0.0;
+    for (k = 0; k < K; ++k) wsum += wt[(long long)i * K + k];
+    for (j = 0; j < d; ++j) {
+      double s2 = exp(2.0 * I->logs[i * d + j]), am = 0.0, al = 0.0;
+      for (k = 0; k < K; ++k) {
+        const double* z = Z(w, I, i, k);
+        double g = dzl[((long long)i * K + k) * d + j];
+        double zc = z[j] - I->m[i * d + j];
+        double gp = g - wt[(long long)i * K + k] * zc / s2;
+        am += gp;
+        al += gp * zc;
+        if (dz) dz[((long long)i * K + k) * d + j] += go * g;
+      }
+      dm[i * d + j] += go * am;
+      dlogs[i * d + j] += go * (wsum + al);
+    }
+  }
+  free(wt); free(dmu); free(dzl); free(pred);
+}
+
+int tmc_oracle_grad(int B, const int* n, const int* parent, const int* K, const int* d,
+                    const int* obs, int shared, double prior_var, double obs_var,
+                    const double* eps, const double* q_mean, const double* q_logstd,
+                    const double* W, const double* bias, const double* C, const double* x,
+                    const double* grad_out, double* log_phat, double* dz, double* dq_mean,
+                    double* dq_logstd, double* dW, double* dbias, double* dC) {
+  offs_t o;
+  int b, rc = validate(B, n, parent, K, d, obs);
+  if (rc) return rc;
+  memset(&o, 0, sizeof(o));
+  for (b = 0; b < B; ++b) {
+    inst_t I;
+    ws_t w;
+    double L;
+    int* slot = (int*)malloc(sizeof(int) * n[b]);
+    int nl = count_leaves(n[b], parent + o.parent, slot);
+    make_instance(&I, b, &o, n, parent, K, d, obs, prior_var, obs_var, eps, q_mean, q_logstd,
+                  W, bias, C, x, slot);
+    if (ws_alloc(&w, &I)) { free(slot); return TMC_ORACLE_NOMEM; }
+    L = instance_forward(&I, &w);
+    if (log_phat) log_phat[b] = L;
+    instance_backward(&I, &w, L, grad_out ? grad_out[b] : 1.0, dz ? dz + o.eps : NULL,
+                      dq_mean + o.q, dq_logstd + o.q, dW + o.W, dbias + o.bias, dC + o.C);
+    ws_free(&w);
+    free(slot);
+    advance(&o, b, n, K, d, obs, shared, nl);
+  }
+  return TMC_ORACLE_OK;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Brute force: enumerate every combination (k_0..k_{n-1}) and evaluate the importance
+ * ratio of Eq. (is) from the joint density directly.
+ * ------------------------------------------------------------------------------------- */
+int tmc_oracle_brute_force(int B, const int* n, const int* parent, const int* K, const int* d,
+                           const int* obs, int shared, double prior_var, double obs_var,
+                           const double* eps, const double* q_mean, const double* q_logstd,
+                           const double* W, const double* bias, const double* C,
+                           const double* x, long long max_combos, double* log_phat) {
+  offs_t o;
+  int b, rc = validate(B, n, parent, K, d, obs);
+  if (rc) return rc;
+  memset(&o, 0, sizeof(o));
+  for (b = 0; b < B; ++b) {
+    inst_t I;
+    int* slot = (int*)malloc(sizeof(int) * n[b]);
+    int nl = count_leaves(n[b], parent + o.parent, slot);
+    long long combos = 1, t;
+    int i, j;
+    make_instance(&I, b, &o, n, parent, K, d, obs, prior_var, obs_var, eps, q_mean, q_logstd,
+                  W, bias, C, x, slot);
+    for (i = 0; i < I.n; ++i) {
+      combos *= I.K;
+      if (combos > max_combos) { free(slot); return TMC_ORACLE_TOO_BIG; }
+    }
+    {
+      double* lw = (double*)malloc(sizeof(double) * combos);
+      double* zs = (double*)malloc(sizeof(double) * (size_t)I.n * I.d);
+      double* mu = (double*)malloc(sizeof(double) * I.d);
+      double* pred = (double*)malloc(sizeof(double) * I.obs);
+      int* kk = (int*)malloc(sizeof(int) * I.n);
+      for (t = 0; t < combos; ++t) {
+        long long r = t;
+        double v = 0.0;
+        for (i = 0; i < I.n; ++i) { kk[i] = (int)(r % I.K); r /= I.K; }
+        for (i = 0; i < I.n; ++i) sample(&I, i, kk[i], zs + (long long)i * I.d);
+        /* log P(x, z): root prior, conditionals, observations */
+        for (i = 0; i < I.n; ++i) {
+          if (i == 0) {
+            for (j = 0; j < I.d; ++j) mu[j] = I.bias[j];
+          } else {
+            cond_mean(&I, i, zs + (long long)I.parent[i] * I.d, mu);
+          }
+          v += log_normal_iso(zs + (long long)i * I.d, mu, I.d, I.prior_var);
+          if (slot[i] >= 0) v += log_obs(&I, slot[i], zs + (long long)i * I.d, pred);
+          v -= log_q(&I, i, zs + (long long)i * I.d);
+        }
+        lw[t] = v;
+      }
+      log_phat[b] = logsumexp(lw, (int)combos) - I.n * log((double)I.K);
+      free(lw); free(zs); free(mu); free(pred); free(kk);
+    }
+    free(slot);
+    advance(&o, b, n, K, d, obs, shared, nl);
+  }
+  return TMC_ORACLE_OK;
+}

@@ -1,0 +1,58 @@
+/*
+ * tmc_oracle.h -- FP64 CPU oracle for the Tensor Monte Carlo estimator.
+ *
+ * TEST INFRASTRUCTURE: only the tests, the smoke check and the benchmark's CPU baseline may
+ * call these functions.  Nothing here is shared with the CUDA path.
+ *
+ * Batch layout (instance b follows instance b-1 in every flat array; all arrays are host
+ * memory owned by the caller):
+ *   n[B], K[B], d[B], obs[B]          latents, samples per latent, latent dim, obs dim
+ *   parent[sum n]                     local indices; parent[0] = -1, 0 <= parent[i] < i
+ *   eps[sum n*K*d]       [i][k][j]    proposal noise
+ *   q_mean, q_logstd [sum n*d]        proposal mean / log std, [i][j]
+ *   W     [n*d*d]  (shared) or [sum n*d*d]   [i][r][c], W_0 unused
+ *   bias  [n*d]    (shared) or [sum n*d]     bias_0 is the root prior mean
+ *   C     [obs*d]  (shared) or [sum obs*d]   [o][c]
+ *   x     [sum leaves*obs]            one observation per leaf, leaves in node order
+ * With shared != 0 every instance uses the same W/bias/C (and must have the same n, parent,
+ * d, obs); their gradients are summed over instances.
+ *
+ * Gradient outputs have the layout of the matching input and are ACCUMULATED (+=), each
+ * instance's contribution multiplied by grad_out[b] (grad_out may be NULL: all ones).
+ * dz may be NULL.  Return value: TMC_ORACLE_* status.
+ */
+#ifndef TMC_ORACLE_H
+#define TMC_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { TMC_ORACLE_OK = 0, TMC_ORACLE_BAD_ARG = 1, TMC_ORACLE_NOMEM = 2, TMC_ORACLE_TOO_BIG = 3 };
+
+/* log P_TMC per instance by summing out one index at a time (Section 2.2, Appendix). */
+int tmc_oracle_log_marginal(int B, const int* n, const int* parent, const int* K, const int* d,
+                            const int* obs, int shared, double prior_var, double obs_var,
+                            const double* eps, const double* q_mean, const double* q_logstd,
+                            const double* W, const double* bias, const double* C,
+                            const double* x, double* log_phat);
+
+/* Analytic gradient of sum_b grad_out[b] * log P_TMC_b (reparameterisation gradients). */
+int tmc_oracle_grad(int B, const int* n, const int* parent, const int* K, const int* d,
+                    const int* obs, int shared, double prior_var, double obs_var,
+                    const double* eps, const double* q_mean, const double* q_logstd,
+                    const double* W, const double* bias, const double* C, const double* x,
+                    const double* grad_out, double* log_phat, double* dz, double* dq_mean,
+                    double* dq_logstd, double* dW, double* dbias, double* dC);
+
+/* Eq. (is) enumerated over all prod K_i combinations; TMC_ORACLE_TOO_BIG above max_combos. */
+int tmc_oracle_brute_force(int B, const int* n, const int* parent, const int* K, const int* d,
+                           const int* obs, int shared, double prior_var, double obs_var,
+                           const double* eps, const double* q_mean, const double* q_logstd,
+                           const double* W, const double* bias, const double* C,
+                           const double* x, long long max_combos, double* log_phat);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
