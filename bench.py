@@ -1,0 +1,364 @@
+"""TMC hot-path benchmark: forward + backward factor entries per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload chain_n16_K1024_d128_B64] [--precision fp32|bf16|fp16]
+
+A step is one full pass of the hot path over one batch of synthetic linear-Gaussian
+instances: samples and node terms, conditional means, the fused pairwise-factor +
+log-sum-exp messages from the leaves to the root, the FP64 root reduction, the fused
+adjoint, and the gradients w.r.t. eps, the proposal (m, logs) and the model (W, bias, C).
+Unit of work: B*n*K^2 factor entries per step (summed over instances).
+
+Prints ONE JSON line (rank 0).  Under torchrun each rank runs an independent replica of
+the workload on its own GPU (no data-path collective; the path has no exchange step
+because instances are independent), so scaling is weak and `value` sums all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "chain_n16_K1024_d128_B64"
+GRADS = ("deps", "dq_mean", "dq_logstd", "dW", "dbias", "dC")
+RESULT_GRADS = ("dq_mean", "dq_logstd", "dW", "dbias", "dC")  # read back in the e2e leg
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def make_workload(name):
+    from paper_1806_08593_gb300 import workload as wl
+    if name in wl.CHAIN_CONFIGS:
+        return wl.chain_config(name)
+    if name.startswith("trees"):
+        return wl.tree_batch()
+    raise SystemExit("unknown workload %s" % name)
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+# multi-rank helpers (replicas only)
+# ---------------------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of instances
+# ---------------------------------------------------------------------------------------
+def oracle_cores():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def time_oracle_sample(p, target_s=15.0, max_inst=None):
+    import oracle
+    oracle.build()
+    entries_per_inst = p.entries() / p.B
+    n_inst, elapsed, done = 1, 0.0, 0
+    t_all = 0.0
+    while True:
+        idx = list(range(done, min(p.B, done + n_inst)))
+        if not idx:
+            break
+        sub = oracle.subset(p, idx)
+        t0 = time.perf_counter()
+        oracle.grad(sub)
+        dt = time.perf_counter() - t0
+        t_all += dt
+        done += len(idx)
+        if t_all >= target_s or done >= p.B or (max_inst and done >= max_inst):
+            break
+        n_inst = max(1, int(len(idx) * min(4.0, (target_s - t_all) / max(dt, 1e-3))))
+    return entries_per_inst * done / t_all, done, t_all
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    p = make_workload(args.workload)
+    vals = []
+    # bounded steps: one instance per step keeps K+W steps within minutes
+    import oracle
+    oracle.build()
+    sub = oracle.subset(p, [0])
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.grad(sub)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            vals.append(dt)
+    t = float(np.mean(vals))
+    value = sub.entries() / t
+    line = {
+        "impl": "reference", "metric": "tmc_fwd_bwd_factor_entries_per_s", "value": value,
+        "unit": "entries/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": "1 instance of %d per step" % p.B},
+        "cpu_baseline": {"value": value, "unit": "entries/s", "cores": oracle_cores(),
+                         "kind": "oracle", "sample": "instance 0 of the workload, fwd+bwd, FP64"},
+        "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+def algorithmic_flops(p, precision):
+    """Algorithmic FLOPs of the dominant kernel class per step (pairwise contractions):
+    forward 2*K_p*K_i*d per edge; adjoint 4*K_p*K_i*d per edge (pi z~ and pi^T mu~)."""
+    e = (p.n.astype(np.int64) - 1) * p.K.astype(np.int64) ** 2 * p.d.astype(np.int64)
+    return {"edge_fwd": 2.0 * float(e.sum()), "edge_bwd": 4.0 * float(e.sum())}
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_1806_08593_gb300.build import build
+    if rank == 0 or ws == 1:
+        build()
+    barrier()
+    from paper_1806_08593_gb300.tmc import Plan
+
+    p = make_workload(args.workload)
+    plan = Plan.from_problem(p, args.precision)
+    t = plan.to_device(p, dev)
+    out_lp = torch.empty(p.B, dtype=torch.float64, device=dev)
+    grads = {k: torch.empty_like(t[{"deps": "eps", "dq_mean": "q_mean", "dq_logstd": "q_logstd",
+                                    "dW": "W", "dbias": "bias", "dC": "C"}[k]]) for k in GRADS}
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.forward(t, out=out_lp)
+        plan.backward(t, out=grads, want=GRADS)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    plan.sync_status()
+
+    # ---- device-resident timed region (CUDA events on the launch stream) ---------------
+    plan.profile_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local if ws > 1 else 0) as clk:
+        barrier()
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = plan.profile_read()
+    plan.profile_enable(False)
+    plan.sync_status()
+    ms_max = max_over_ranks(ms, dev)
+    ms_step = ms_max / args.steps
+    entries = p.entries()
+    value = entries * ws / (ms_step * 1e-3)
+
+    # ---- end to end through host buffers ---------------------------------------------
+    host_in = {k: v.cpu().pin_memory() for k, v in t.items()}
+    dev_in = {k: torch.empty_like(v) for k, v in t.items()}
+    host_out = {k: torch.empty(grads[k].shape, dtype=grads[k].dtype).pin_memory() for k in RESULT_GRADS}
+    host_lp = torch.empty(p.B, dtype=torch.float64).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host_in.values())
+    d2h = host_lp.numel() * 8 + sum(v.numel() * v.element_size() for v in host_out.values())
+
+    def e2e_step():
+        for k in dev_in:
+            dev_in[k].copy_(host_in[k], non_blocking=True)
+        plan.forward(dev_in, out=out_lp)
+        plan.backward(dev_in, out=grads, want=GRADS)
+        host_lp.copy_(out_lp, non_blocking=True)
+        for k in RESULT_GRADS:
+            host_out[k].copy_(grads[k], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e2e_steps = max(3, args.steps // 2)
+    barrier()
+    ev0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e2e_ms = max_over_ranks(ev0.elapsed_time(ev1), dev) / e2e_steps
+    plan.sync_status()
+
+    if rank != 0:
+        return
+    # ---- roofline of the dominant kernel class ---------------------------------------
+    peaks, src = load_peaks()
+    flops = algorithmic_flops(p, args.precision)
+    dom = max(("edge_fwd", "edge_bwd"), key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dom]
+    launches_per_step = dom_n / args.steps
+    per_launch_ms = dom_ms / dom_n
+    per_launch_flop = flops[dom] / launches_per_step
+    achieved = per_launch_flop / (per_launch_ms * 1e-3)
+    if args.precision == "fp32":
+        peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
+        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz"}
+    else:
+        peak = peaks["bf16_tflops"] * 1e12
+        roof = {"bound": "tensor", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "peak_source": "bf16_tflops (%s)" % src}
+    total_launches = int(sum(v[1] for v in prof.values()))
+
+    # ---- CPU baseline (oracle on a bounded sample) ------------------------------------
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        v, ninst, secs = time_oracle_sample(p, target_s=args.cpu_seconds)
+        cpu = {"value": v, "unit": "entries/s", "cores": oracle_cores(), "kind": "oracle",
+               "sample": "%d of %d instances, fwd+bwd FP64, %.1f s" % (ninst, p.B, secs)}
+
+    line = {
+        "metric": "tmc_fwd_bwd_factor_entries_per_s", "value": value, "unit": "entries/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "B": int(p.B), "n": int(p.n[0]), "K": int(p.K[0]),
+                   "d": int(p.d[0]), "obs": int(p.obs[0]), "precision": args.precision,
+                   "entries_per_step": entries, "grads": list(GRADS),
+                   "l2": "inputs larger than L2 (eps %.0f MB per step)" % (p.eps.nbytes / 1e6),
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": entries * ws / (e2e_ms * 1e-3), "unit": "entries/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": total_launches,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--precision", default=os.environ.get("TMC_BENCH_PRECISION", "fp32"),
+                    choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

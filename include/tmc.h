@@ -1,0 +1,159 @@
+/*
+ * tmc.h -- C ABI of the GB300 (sm_103a) Tensor Monte Carlo hot path.
+ *
+ * Tensor Monte Carlo (Aitchison, ICML 2019) estimates the marginal likelihood of a latent
+ * variable model by drawing K_i proposal samples for each latent z_i and averaging the
+ * importance ratio over all prod_i K_i combinations of samples (Eq. (is), Section 2.1).
+ * For a tree-structured directed model the ratio is a product of factors, one per latent,
+ * each indexed by the latent's own sample and its parent's (Eq. (fac), Section 2.2, and
+ * the Appendix "Typical choice of factors"), so the sum is evaluated exactly by summing
+ * out one index at a time from the leaves up: a chain of log-space K x K tensor
+ * contractions (Section 2.2, Fig. 2; the log-domain product of the Appendix
+ * "Numerically stable matrix (tensor) products").  This library evaluates log P_TMC and its
+ * reparameterisation gradient (Section 2.2: gradient ascent on log P_TMC) for batches of
+ * linear-Gaussian instances:
+ *
+ *   z_0 ~ N(bias_0, prior_var I)
+ *   z_i | z_p ~ N(W_i z_p + bias_i, prior_var I),   i >= 1, p = parent[i] < i
+ *   x_l | z_l ~ N(C z_l, obs_var I)                 for every leaf l of the tree
+ *   Q_i(z_i) = N(m_i, diag(exp(2 logs_i))),  z_i^k = m_i + exp(logs_i) * eps_i^k
+ *
+ * Conventions for every entry point
+ *   - Status codes are returned, never raised; no entry point aborts the process.
+ *   - Memory: pointers named "host" are host memory, every tensor in tmc_inputs / tmc_grads
+ *     and log_phat / grad_out are DEVICE memory owned by the caller; the plan owns its
+ *     workspace (allocated once by tmc_plan_create, freed by tmc_plan_destroy).
+ *   - Streams: `stream` is a cudaStream_t (0 = legacy default stream).  Calls enqueue work
+ *     and return without synchronising; inputs must stay valid until the work completes.
+ *   - A plan is not thread-safe; calls on one plan must be serialised by the caller.
+ *   - After tmc_plan_create no call allocates device or host memory.
+ */
+#ifndef TMC_H
+#define TMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TMC_OK = 0,
+  TMC_ERR_INVALID_ARG = 1, /* malformed description / NULL required pointer / bad sizes */
+  TMC_ERR_UNSUPPORTED = 2, /* valid problem outside what the kernels implement            */
+  TMC_ERR_NOMEM = 3,       /* workspace allocation failed                                  */
+  TMC_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed                  */
+  TMC_ERR_NUMERIC = 5,     /* the device saw a non-finite input or result                  */
+  TMC_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up                           */
+  TMC_ERR_STATE = 7        /* call order violated (e.g. backward before forward)           */
+} tmc_status;
+
+typedef enum {
+  TMC_PREC_FP32 = 0,    /* CUDA-core FP32 contractions                                     */
+  TMC_PREC_BF16_TC = 1, /* tcgen05 tensor cores, bf16 operands, FP32 accumulate            */
+  TMC_PREC_FP16_TC = 2  /* tcgen05 tensor cores, fp16 operands, FP32 accumulate            */
+} tmc_precision;
+
+typedef struct tmc_plan_s* tmc_plan;
+
+/* Problem description; all arrays are HOST memory and are copied into the plan.
+ * Section 2.1 fixes what a problem is: the graph (parents), K_i samples per latent, the
+ * generative model P and the proposal Q. */
+typedef struct {
+  int32_t num_instances;  /* B >= 1                                                        */
+  const int32_t* n;       /* [B]    latents per instance, n_b >= 1                          */
+  const int32_t* parent;  /* [sum n_b] local parent index, parent[0] = -1, 0<=parent[i]<i   */
+  const int32_t* K;       /* [B]    samples per latent (the same for every latent of b)     */
+  const int32_t* d;       /* [B]    latent dimension                                        */
+  const int32_t* obs_dim; /* [B]    observation dimension                                   */
+  int32_t shared_params;  /* 1: all instances share W, bias, C (then n, parent, d, obs_dim  */
+                          /*    must agree); 0: each instance has its own                   */
+  double prior_var;       /* sigma_z^2 > 0                                                  */
+  double obs_var;         /* sigma_x^2 > 0                                                  */
+  int32_t precision;      /* tmc_precision                                                  */
+} tmc_problem_desc;
+
+/* Device inputs: contiguous float32, instance b directly after instance b-1.
+ *   eps       [sum n_b*K_b*d_b]  [i][k][j]   proposal noise
+ *   q_mean    [sum n_b*d_b]      [i][j]      proposal means m_i
+ *   q_logstd  [sum n_b*d_b]      [i][j]      proposal log standard deviations
+ *   W         [n*d*d] shared, else [sum n_b*d_b*d_b]; [i][r][c]; W_0 is ignored
+ *   bias      [n*d]   shared, else [sum n_b*d_b];     bias_0 is the root prior mean
+ *   C         [obs*d] shared, else [sum obs_b*d_b];   [o][c]
+ *   x         [sum leaves_b*obs_b]  one observation per leaf, leaves in node order */
+typedef struct {
+  const float *eps, *q_mean, *q_logstd, *W, *bias, *C, *x;
+} tmc_inputs;
+
+/* Device gradient outputs (same layouts as the inputs).  Every non-NULL buffer is
+ * OVERWRITTEN with d(sum_b grad_out[b] * log P_TMC_b)/d(input); NULL skips that output.
+ *   dz         gradient w.r.t. the samples z_i^k (proposal density evaluated at z, its
+ *              parameters held fixed)
+ *   deps       gradient w.r.t. the noise eps (= exp(logs) * dz), same layout as eps
+ *   dq_mean, dq_logstd   reparameterisation gradients w.r.t. m_i and logs_i
+ *   dW, dbias, dC        model gradients (summed over instances when shared)            */
+typedef struct {
+  float *dz, *deps, *dq_mean, *dq_logstd, *dW, *dbias, *dC;
+} tmc_grads;
+
+/* Builds a plan: validates the description (tree shape, sizes), derives the
+ * leaves-to-root elimination schedule of Section 2.2 (one level of the tree at a time),
+ * allocates the device workspace.  On success *out owns the plan.  Errors:
+ * TMC_ERR_INVALID_ARG, TMC_ERR_UNSUPPORTED (e.g. a precision the kernels do not cover for these shapes,
+ * d or obs_dim > 1024, K > 16384), TMC_ERR_NOMEM, TMC_ERR_CUDA. */
+tmc_status tmc_plan_create(const tmc_problem_desc* desc, tmc_plan* out);
+
+/* log P_TMC of Eq. (is) for every instance, evaluated by the elimination of Section 2.2:
+ * for each edge (p -> i), lambda_i[k] = log (1/K_i) sum_k' exp(log f_i^{(k',k)} + beta_i[k'])
+ * with f_i = P(z_i | z_p) / Q_i(z_i) (Appendix) and beta_i the log of everything indexed by
+ * k_i alone (node terms and children's messages); the root closes the sum.
+ * log_phat: DEVICE double[B], written.  Saves what tmc_backward needs in the plan. */
+tmc_status tmc_log_marginal(tmc_plan plan, const tmc_inputs* in, double* log_phat,
+                            void* stream);
+
+/* Reparameterisation gradient of sum_b grad_out[b] * log P_TMC_b (Section 2.2, "gradient
+ * ascent on log P_TMC"; Section 1, reparameterisation trick), computed by the adjoint of
+ * the elimination: top-down marginal weights over samples, with the K x K factors
+ * recomputed rather than stored.  grad_out: DEVICE double[B] or NULL (all ones).
+ * Requires a preceding tmc_log_marginal on the same plan with the same inputs
+ * (TMC_ERR_STATE otherwise).  Outputs are overwritten (see tmc_grads). */
+tmc_status tmc_backward(tmc_plan plan, const tmc_inputs* in, const double* grad_out,
+                        const tmc_grads* grads, void* stream);
+
+/* Waits for the plan's outstanding work on `stream` and reports device-side errors recorded
+ * since the last call (TMC_ERR_NUMERIC for non-finite values, TMC_ERR_TIMEOUT), clearing
+ * them.  TMC_OK if none. */
+tmc_status tmc_plan_sync_status(tmc_plan plan, void* stream);
+
+/* Bytes of device workspace owned by the plan. */
+tmc_status tmc_plan_workspace_bytes(tmc_plan plan, size_t* bytes);
+
+/* Releases the plan and its workspace (synchronises the device first).  NULL is a no-op. */
+tmc_status tmc_plan_destroy(tmc_plan plan);
+
+/* Static, human-readable name of a status code. */
+const char* tmc_status_string(tmc_status s);
+
+/* ---- kernel timing (library-internal CUDA events on the launch stream) ----------------
+ * Kernel classes, in the order of the hot path: */
+enum {
+  TMC_KC_SAMPLE = 0,  /* samples, node terms, observation residuals                         */
+  TMC_KC_PROJECT = 1, /* conditional means mu_i = W_i z_p + bias_i                          */
+  TMC_KC_EDGE_FWD = 2,/* fused pairwise factor + log-sum-exp message                        */
+  TMC_KC_ROOT = 3,    /* root reduction to log P_TMC (FP64)                                 */
+  TMC_KC_EDGE_BWD = 4,/* fused adjoint of the messages (factors recomputed)                 */
+  TMC_KC_PARAM = 5,   /* parameter / proposal gradient assembly                             */
+  TMC_KC_COUNT = 6
+};
+/* Turns event timing of every launch on (1) or off (0); resets the accumulators. */
+tmc_status tmc_profile_enable(tmc_plan plan, int enable);
+/* Synchronises, then returns the summed device time (ms) and launch count of a kernel
+ * class since the last enable. */
+tmc_status tmc_profile_read(tmc_plan plan, int kernel_class, double* total_ms,
+                            long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TMC_H */

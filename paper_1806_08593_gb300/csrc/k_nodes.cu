@@ -1,0 +1,623 @@
+// k_nodes.cu -- per-node kernels of the TMC hot path (both precisions use them):
+// proposal samples and node terms, observation residuals, conditional means, the FP64 root
+// reduction, and the gradient assembly after the fused edge adjoint.
+//
+// Notation (Appendix, typical factors): for latent i with parent p,
+//   f_i^{(k', k)} = P(z_i^{k'} | z_p^k) / Q_i(z_i^{k'}),  f_root^{k} = P(z_0^k) / Q_0(z_0^k),
+//   and every leaf carries P(x_l | z_l^k).
+// Everything indexed by one sample k of latent i alone is collected in the node term
+//   u_i[k] = -log Q_i(z_i^k) [+ log P(z_0^k) at the root] [+ log P(x_i | z_i^k) at a leaf],
+// split into an FP64 constant (nodeconst) and an FP32 per-sample part (u).
+// Samples and means are kept centred on the proposal mean m_i: z~ = z - m_i, mu~ = mu - m_i,
+// which leaves every pairwise distance unchanged and keeps FP32 magnitudes small.
+#include "simt_tile.cuh"
+
+namespace tmc {
+
+namespace {
+constexpr double kLog2Pi = 1.8378770664093454835606594728112;
+
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; ++i) t += red[i];
+  return t;
+}
+__device__ __forceinline__ float block_max_f(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  float t = -INFINITY;
+  for (int i = 0; i < nw; ++i) t = fmaxf(t, red[i]);
+  return t;
+}
+__device__ __forceinline__ float block_sum_f(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  float t = 0.f;
+  for (int i = 0; i < nw; ++i) t += red[i];
+  return t;
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// FP64 node constants: sum_j logs_ij + (d/2) log 2pi  (from -log Q_i)
+//   + root: -(d/2) log(2 pi prior_var)   + leaf: -(obs/2) log(2 pi obs_var)
+// ---------------------------------------------------------------------------------------
+__global__ void k_node_const(Dev D) {
+  __shared__ double red[32];
+  const NodeInfo nd = D.nodes[blockIdx.x];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < nd.d; j += blockDim.x) s += (double)D.q_logstd[nd.off_q + j];
+  s = block_sum_d(s, red);
+  if (threadIdx.x == 0) {
+    double c = s + 0.5 * nd.d * kLog2Pi;
+    if (nd.parent < 0) c += -0.5 * nd.d * (kLog2Pi + log(D.prior_var));
+    if (nd.leaf_slot >= 0) c += -0.5 * nd.obs * (kLog2Pi + log(D.obs_var));
+    D.nodeconst[blockIdx.x] = c;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Samples (Section 2.1: z_i^k ~ Q_i, reparameterised) and the per-sample node term:
+//   z~ = exp(logs) * eps,  u = |eps|^2 / 2  [ - |z_0 - bias_0|^2 / (2 prior_var) at the root ]
+// One warp per sample row, lanes over the latent dimension.
+// ---------------------------------------------------------------------------------------
+__global__ void k_sample(Dev D, const Tile* __restrict__ tiles) {
+  extern __shared__ float sm[];
+  const Tile t = tiles[blockIdx.x];
+  const NodeInfo nd = D.nodes[t.node];
+  const int d = nd.d;
+  float* s_std = sm;         // exp(logs)
+  float* s_off = sm + d;     // m_0 - bias_0 (root only)
+  const bool root = nd.parent < 0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    s_std[j] = expf(D.q_logstd[nd.off_q + j]);
+    s_off[j] = root ? D.q_mean[nd.off_q + j] - D.bias[nd.off_bias + j] : 0.f;
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  bool bad = false;
+  for (int r = w; r < kTile; r += kThreads / 32) {
+    const int k = t.row0 + r;
+    if (k >= nd.K) break;
+    const long long base = nd.off_nkd + (long long)k * d;
+    float se = 0.f, sz = 0.f, sr = 0.f;
+    for (int j = lane; j < d; j += 32) {
+      const float e = D.eps[base + j];
+      const float z = s_std[j] * e;
+      bad |= !isfinite(z);
+      D.zt[base + j] = z;
+      se = fmaf(e, e, se);
+      sz = fmaf(z, z, sz);
+      const float rr = z + s_off[j];
+      sr = fmaf(rr, rr, sr);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      se += __shfl_xor_sync(0xffffffffu, se, o);
+      sz += __shfl_xor_sync(0xffffffffu, sz, o);
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    }
+    if (lane == 0) {
+      float u = 0.5f * se;
+      if (root) u -= 0.5f * sr * D.inv_var;
+      D.u[nd.off_nk + k] = u;
+      D.zn[nd.off_nk + k] = sz;
+    }
+  }
+  if (bad) flag_error(D.err, kErrNumeric);
+}
+
+// x~ = x_l - C m_l for the leaf of node nd (into shared memory, obs floats).
+__device__ __forceinline__ void centred_obs(const Dev& D, const NodeInfo& nd, float* xs) {
+  for (int o = threadIdx.x; o < nd.obs; o += blockDim.x) {
+    const float* c = D.C + nd.off_C + (long long)o * nd.d;
+    const float* m = D.q_mean + nd.off_q;
+    float s = 0.f;
+    for (int j = 0; j < nd.d; ++j) s = fmaf(c[j], m[j], s);
+    xs[o] = D.x[nd.off_x + o] - s;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Observation term at a leaf: u[k] -= |x - C z^k|^2 / (2 obs_var), residual r = x~ - C z~^k.
+// Grid: (leaf node, 64-sample tile); loops over 64-wide observation tiles.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_obs_fwd(Dev D, const Tile* __restrict__ tiles) {
+  extern __shared__ float xs[];
+  __shared__ TileSmem sm;
+  const Tile t = tiles[blockIdx.x];
+  const NodeInfo nd = D.nodes[t.node];
+  centred_obs(D, nd, xs);
+  __syncthreads();
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  const int rows = min(kTile, nd.K - t.row0);
+  const float* Z = D.zt + nd.off_nkd + (long long)t.row0 * nd.d;
+  float rs[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int o0 = 0; o0 < nd.obs; o0 += kTile) {
+    float acc[4][4];
+    zero_acc(acc);
+    tile_gemm<true, true>(acc, Z, nd.d, rows, D.C + nd.off_C + (long long)o0 * nd.d, nd.d,
+                          min(kTile, nd.obs - o0), nd.d, sm);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int o = o0 + tx * 4 + b;
+      if (o < nd.obs) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const float r = xs[o] - acc[a][b];
+          rs[a] = fmaf(r, r, rs[a]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const float s = row_group_sum(rs[a]);
+    const int k = t.row0 + ty * 4 + a;
+    if (tx == 0 && k < nd.K) D.u[nd.off_nk + k] -= 0.5f * s * D.inv_obs_var;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Conditional means (the linear cost of Section 2.4): mu~_i[k] = W_i z_p^k + bias_i - m_i
+//   = W_i z~_p^k + c_i,  c_i = W_i m_p + bias_i - m_i;  also |mu~_i[k]|^2.
+// Grid: (non-root node i, 64-sample tile of the parent's samples).
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_project(Dev D, const Tile* __restrict__ tiles) {
+  extern __shared__ float cs[];
+  __shared__ TileSmem sm;
+  const Tile t = tiles[blockIdx.x];
+  const NodeInfo nd = D.nodes[t.node];
+  const NodeInfo pn = D.nodes[nd.parent];
+  const int d = nd.d;
+  const float* Wi = D.W + nd.off_W;
+  for (int r = threadIdx.x; r < d; r += blockDim.x) {
+    const float* w = Wi + (long long)r * d;
+    const float* mp = D.q_mean + pn.off_q;
+    float s = 0.f;
+    for (int c = 0; c < d; ++c) s = fmaf(w[c], mp[c], s);
+    cs[r] = s + D.bias[nd.off_bias + r] - D.q_mean[nd.off_q + r];
+  }
+  __syncthreads();
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  const int rows = min(kTile, nd.K - t.row0);
+  const float* Zp = D.zt + pn.off_nkd + (long long)t.row0 * d;
+  float rs[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int r0 = 0; r0 < d; r0 += kTile) {
+    float acc[4][4];
+    zero_acc(acc);
+    tile_gemm<true, true>(acc, Zp, d, rows, Wi + (long long)r0 * d, d, min(kTile, d - r0), d, sm);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int k = t.row0 + ty * 4 + a;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int r = r0 + tx * 4 + b;
+        if (k < nd.K && r < d) {
+          const float v = acc[a][b] + cs[r];
+          D.mut[nd.off_nkd + (long long)k * d + r] = v;
+          rs[a] = fmaf(v, v, rs[a]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const float s = row_group_sum(rs[a]);
+    const int k = t.row0 + ty * 4 + a;
+    if (tx == 0 && k < nd.K) D.mun[nd.off_nk + k] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Root: closes the sum of Eq. (is) in FP64.
+//   beta'_0 = u_0 + sum_children lam_c,  M_0 = max beta'_0,  beta_0 = beta'_0 - M_0,
+//   log P = sum_nodes (nodeconst + M) + sum_{i>=1} (-(d/2) log(2 pi prior_var) - log K)
+//           + log sum_k exp(beta_0[k]) - log K_0,
+// and the root's sample weights q_0[k] = exp(beta_0[k] - logsumexp(beta_0)).
+// ---------------------------------------------------------------------------------------
+__global__ void k_root(Dev D) {
+  extern __shared__ float sb[];
+  __shared__ double redd[32];
+  __shared__ float redf[32];
+  const InstInfo in = D.insts[blockIdx.x];
+  const NodeInfo nd = D.nodes[in.node0];
+  const int K = nd.K;
+  float mx = -INFINITY;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    float v = D.u[nd.off_nk + k];
+    for (int c = nd.child_begin; c < nd.child_end; ++c) v += D.lam[D.nodes[D.children[c]].off_nk + k];
+    sb[k] = v;
+    mx = fmaxf(mx, v);
+  }
+  mx = block_max_f(mx, redf);
+  float s = 0.f;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const float b = sb[k] - mx;
+    sb[k] = b;
+    D.beta[nd.off_nk + k] = b;
+    s += expf(b);
+  }
+  s = block_sum_f(s, redf);
+  const float lse = logf(s);
+  for (int k = threadIdx.x; k < K; k += blockDim.x) D.q[nd.off_nk + k] = expf(sb[k] - lse);
+  double acc = 0.0;
+  for (int g = in.node0 + threadIdx.x; g < in.node0 + in.n; g += blockDim.x) {
+    const NodeInfo ng = D.nodes[g];
+    double m = (g == in.node0) ? (double)mx : (double)D.nodemax[g];
+    acc += D.nodeconst[g] + m;
+    if (ng.parent >= 0) acc += -0.5 * ng.d * (kLog2Pi + log(D.prior_var)) - log((double)ng.K);
+  }
+  acc = block_sum_d(acc, redd);
+  if (threadIdx.x == 0) {
+    D.nodemax[in.node0] = mx;
+    const double lp = acc + (double)lse - log((double)K);
+    D.log_phat[blockIdx.x] = lp;
+    if (!isfinite(lp)) flag_error(D.err, kErrNumeric);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Sample gradients without the proposal's own score (the "path" part):
+//   gz_i[k] = [edge part, written by the edge adjoint, if i is not the root]
+//           + sum_{children c} W_c^T dmu_c[k]                      (mu_c = W_c z_i + bias_c)
+//           - q_0[k] (z_0^k - bias_0) / prior_var                   (root prior)
+//           + q_i[k] C^T (x_i - C z_i^k) / obs_var                  (leaf observation)
+// and the requested sample gradients dz = grad_out * (gz + q z~ / exp(2 logs)),
+// deps = exp(logs) * dz.
+// Grid: (node, 64-sample tile); loops over 64-wide latent-dimension tiles.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_node_grad(Dev D, const Tile* __restrict__ tiles) {
+  extern __shared__ float xs[];  // centred observation (leaves)
+  __shared__ TileSmem sm;
+  __shared__ float rsm[kTile * kLd];  // residual tile, [o][k]
+  const Tile t = tiles[blockIdx.x];
+  const NodeInfo nd = D.nodes[t.node];
+  const int d = nd.d, K = nd.K;
+  const bool root = nd.parent < 0, leaf = nd.leaf_slot >= 0;
+  if (leaf) centred_obs(D, nd, xs);
+  __syncthreads();
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  const int rows = min(kTile, K - t.row0);
+  const float* Z = D.zt + nd.off_nkd + (long long)t.row0 * d;
+  const float go = D.grad_out ? (float)D.grad_out[nd.b] : 1.f;
+  float qk[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int k = t.row0 + ty * 4 + a;
+    qk[a] = (k < K) ? D.q[nd.off_nk + k] : 0.f;
+  }
+  for (int c0 = 0; c0 < d; c0 += kTile) {
+    const int ncol = min(kTile, d - c0);
+    float acc[4][4];
+    zero_acc(acc);
+    // children: out[k][c] += sum_r dmu_c[k][r] W_c[r][c]
+    for (int ci = nd.child_begin; ci < nd.child_end; ++ci) {
+      const NodeInfo ch = D.nodes[D.children[ci]];
+      tile_gemm<true, false>(acc, D.dmu + ch.off_nkd + (long long)t.row0 * d, d, rows,
+                             D.W + ch.off_W + c0, d, ncol, d, sm);
+    }
+    if (leaf) {
+      // out[k][c] += q[k] / obs_var * sum_o r[k][o] C[o][c],  r = x~ - C z~
+      float acc2[4][4];
+      zero_acc(acc2);
+      for (int o0 = 0; o0 < nd.obs; o0 += kTile) {
+        const int nob = min(kTile, nd.obs - o0);
+        float racc[4][4];
+        zero_acc(racc);
+        tile_gemm<true, true>(racc, Z, d, rows, D.C + nd.off_C + (long long)o0 * d, d, nob, d, sm);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int o = o0 + tx * 4 + b;
+            rsm[(tx * 4 + b) * kLd + ty * 4 + a] = (o < nd.obs) ? xs[o] - racc[a][b] : 0.f;
+          }
+        __syncthreads();
+        for (int l0 = 0; l0 < nob; l0 += kSlice) {
+          load_slice<false>(sm.b, D.C + nd.off_C + (long long)o0 * d + c0, d, ncol, l0, nob);
+          __syncthreads();
+          slice_fma(acc2, rsm + l0 * kLd, sm.b);
+          __syncthreads();
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(qk[a] * D.inv_obs_var, acc2[a][b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int k = t.row0 + ty * 4 + a;
+      if (k >= K) continue;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int c = c0 + tx * 4 + b;
+        if (c >= d) continue;
+        const long long idx = nd.off_nkd + (long long)k * d + c;
+        float g = acc[a][b];
+        const float zt = D.zt[idx];
+        if (root) {
+          const float off = D.q_mean[nd.off_q + c] - D.bias[nd.off_bias + c];
+          g -= qk[a] * (zt + off) * D.inv_var;
+        } else {
+          g += D.gz[idx];
+        }
+        D.gz[idx] = g;
+        if (D.dz || D.deps) {
+          const float ls = D.q_logstd[nd.off_q + c];
+          const float dzv = go * (g + qk[a] * zt * expf(-2.f * ls));
+          if (D.dz) D.dz[idx] = dzv;
+          if (D.deps) D.deps[idx] = dzv * expf(ls);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Per-latent reductions over samples (reparameterisation z = m + exp(logs) eps):
+//   dm_i    = grad_out * sum_k gz_i[k]
+//   dlogs_i = grad_out * (sum_k q_i[k] + sum_k gz_i[k] * z~_i[k])
+// Root also: dbias_0 = grad_out * sum_k q_0[k] (z_0^k - bias_0) / prior_var.
+// Non-shared parameters: writes the instance's dW_0 = 0 (the root has no W).
+// ---------------------------------------------------------------------------------------
+__global__ void k_node_reduce(Dev D) {
+  __shared__ float red[3][8][33];
+  const NodeInfo nd = D.nodes[blockIdx.x];
+  const int d = nd.d, K = nd.K;
+  const bool root = nd.parent < 0;
+  const float go = D.grad_out ? (float)D.grad_out[nd.b] : 1.f;
+  const int grp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float qs = 0.f;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) qs += D.q[nd.off_nk + k];
+  for (int o = 16; o > 0; o >>= 1) qs += __shfl_xor_sync(0xffffffffu, qs, o);
+  __shared__ float qred[8];
+  if (lane == 0) qred[grp] = qs;
+  __syncthreads();
+  float qtot = 0.f;
+  for (int i = 0; i < 8; ++i) qtot += qred[i];
+  for (int j0 = 0; j0 < d; j0 += 32) {
+    const int j = j0 + lane;
+    float sm_ = 0.f, sl = 0.f, sb = 0.f;
+    if (j < d) {
+      const float off = root ? D.q_mean[nd.off_q + j] - D.bias[nd.off_bias + j] : 0.f;
+      for (int k = grp; k < K; k += 8) {
+        const long long idx = nd.off_nkd + (long long)k * d + j;
+        const float g = D.gz[idx], zt = D.zt[idx];
+        sm_ += g;
+        sl = fmaf(g, zt, sl);
+        if (root) sb = fmaf(D.q[nd.off_nk + k], zt + off, sb);
+      }
+    }
+    red[0][grp][lane] = sm_;
+    red[1][grp][lane] = sl;
+    red[2][grp][lane] = sb;
+    __syncthreads();
+    if (grp == 0 && j < d) {
+      float a = 0.f, b = 0.f, c = 0.f;
+      for (int i = 0; i < 8; ++i) { a += red[0][i][lane]; b += red[1][i][lane]; c += red[2][i][lane]; }
+      if (D.dq_mean) D.dq_mean[nd.off_q + j] = go * a;
+      if (D.dq_logstd) D.dq_logstd[nd.off_q + j] = go * (qtot + b);
+      if (root) {
+        const float db = go * c * D.inv_var;
+        if (D.shared) { if (D.pbias) D.pbias[nd.off_q + j] = db; }
+        else if (D.dbias) D.dbias[nd.off_bias + j] = db;
+      }
+    }
+    __syncthreads();
+  }
+  if (root && !D.shared && D.dW)
+    for (long long e = threadIdx.x; e < (long long)d * d; e += blockDim.x) D.dW[nd.off_W + e] = 0.f;
+}
+
+// ---------------------------------------------------------------------------------------
+// dW_i = grad_out * sum_k dmu_i[k] z_p^k^T,  dbias_i = grad_out * sum_k dmu_i[k]
+// (z_p = m_p + z~_p).  Grid: (non-root node, 64-row tile of W, 64-col tile of W).
+// Shared parameters go to per-(instance, node) partials, summed later in a fixed order.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_param_dW(Dev D, const int* __restrict__ nonroot) {
+  __shared__ TileSmem sm;
+  __shared__ float colsum[kTile];
+  const int g = nonroot[blockIdx.x];
+  const NodeInfo nd = D.nodes[g];
+  const NodeInfo pn = D.nodes[nd.parent];
+  const int d = nd.d, K = nd.K;
+  const int r0 = blockIdx.y * kTile, c0 = blockIdx.z * kTile;
+  if (r0 >= d || c0 >= d) return;
+  const float go = D.grad_out ? (float)D.grad_out[nd.b] : 1.f;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  if (threadIdx.x < kTile) {
+    const int r = r0 + threadIdx.x;
+    float s = 0.f;
+    if (r < d)
+      for (int k = 0; k < K; ++k) s += D.dmu[nd.off_nkd + (long long)k * d + r];
+    colsum[threadIdx.x] = s;
+  }
+  float acc[4][4];
+  zero_acc(acc);
+  // opA(m = r, l = k) = dmu[k][r0 + m];  opB(n = c, l = k) = z~_p[k][c0 + n]
+  tile_gemm<false, false>(acc, D.dmu + nd.off_nkd + r0, d, min(kTile, d - r0),
+                          D.zt + pn.off_nkd + c0, d, min(kTile, d - c0), K, sm);
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int r = r0 + ty * 4 + a;
+    if (r >= d) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = c0 + tx * 4 + b;
+      if (c >= d) continue;
+      const float v = go * (acc[a][b] + colsum[ty * 4 + a] * D.q_mean[pn.off_q + c]);
+      if (D.shared) D.pW[nd.off_pW + (long long)r * d + c] = v;
+      else if (D.dW) D.dW[nd.off_W + (long long)r * d + c] = v;
+    }
+  }
+  if (c0 == 0 && threadIdx.x < kTile && r0 + threadIdx.x < d) {
+    const float v = go * colsum[threadIdx.x];
+    if (D.shared) D.pbias[nd.off_q + r0 + threadIdx.x] = v;
+    else if (D.dbias) D.dbias[nd.off_bias + r0 + threadIdx.x] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// dC = grad_out * sum_{leaves l} sum_k q_l[k] (x_l - C z_l^k) z_l^k^T / obs_var.
+// Grid: (instance, 64-row tile of C (observation), 64-col tile of C (latent)).
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_param_dC(Dev D) {
+  extern __shared__ float xs[];
+  __shared__ TileSmem sm;
+  __shared__ float rsm[kTile * kLd];  // q-weighted residuals, [k][o]
+  __shared__ float rsum[kTile];
+  const InstInfo in = D.insts[blockIdx.x];
+  const int d = in.d, obs = in.obs, K = in.K;
+  const int o0 = blockIdx.y * kTile, c0 = blockIdx.z * kTile;
+  if (o0 >= obs || c0 >= d) return;
+  const int nob = min(kTile, obs - o0), ncol = min(kTile, d - c0);
+  const float go = D.grad_out ? (float)D.grad_out[blockIdx.x] : 1.f;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  float acc[4][4];
+  zero_acc(acc);
+  float macc[4][4];                          // sum_k r[k][o] * m[c]: folded at the end per leaf
+  zero_acc(macc);
+  for (int g = in.node0; g < in.node0 + in.n; ++g) {
+    const NodeInfo nd = D.nodes[g];
+    if (nd.leaf_slot < 0) continue;
+    __syncthreads();
+    centred_obs(D, nd, xs);
+    __syncthreads();
+    float leaf_rsum[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k0 = 0; k0 < K; k0 += kTile) {
+      const int rows = min(kTile, K - k0);
+      float racc[4][4];
+      zero_acc(racc);
+      tile_gemm<true, true>(racc, D.zt + nd.off_nkd + (long long)k0 * d, d, rows,
+                            D.C + nd.off_C + (long long)o0 * d, d, nob, d, sm);
+      // racc[a][b]: k = k0 + ty*4 + a, o = o0 + tx*4 + b; store rsm[k][o] as [l = k][m = o]
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int k = k0 + ty * 4 + a;
+        const float qv = (k < K) ? D.q[nd.off_nk + k] * D.inv_obs_var : 0.f;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int o = o0 + tx * 4 + b;
+          rsm[(ty * 4 + a) * kLd + tx * 4 + b] = (o < obs && k < K) ? qv * (xs[o] - racc[a][b]) : 0.f;
+        }
+      }
+      __syncthreads();
+      // acc[o][c] += sum_k rsm[k][o] * z~[k][c]
+      for (int l0 = 0; l0 < rows; l0 += kSlice) {
+        load_slice<false>(sm.b, D.zt + nd.off_nkd + (long long)k0 * d + c0, d, ncol, l0, rows);
+        __syncthreads();
+        slice_fma(acc, rsm + l0 * kLd, sm.b);
+        __syncthreads();
+      }
+      // row sums of the weighted residual for the m_l term
+      if (threadIdx.x < kTile) {
+        float s = 0.f;
+        for (int k = 0; k < rows; ++k) s += rsm[k * kLd + threadIdx.x];
+        rsum[threadIdx.x] = s;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int a = 0; a < 4; ++a) leaf_rsum[a] += rsum[ty * 4 + a];
+      __syncthreads();
+    }
+    // + (sum_k r[k][o]) * m_l[c]
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int c = c0 + tx * 4 + b;
+        const float m = (c < d) ? D.q_mean[nd.off_q + c] : 0.f;
+        macc[a][b] = fmaf(leaf_rsum[a], m, macc[a][b]);
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int o = o0 + ty * 4 + a;
+    if (o >= obs) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = c0 + tx * 4 + b;
+      if (c >= d) continue;
+      const float v = go * (acc[a][b] + macc[a][b]);
+      if (D.shared) D.pC[in.off_pC + (long long)o * d + c] = v;
+      else D.dC[in.off_C + (long long)o * d + c] = v;
+    }
+  }
+}
+
+// Shared parameters: dW, dbias, dC = sum over instances of the partials (fixed order).
+__global__ void k_shared_reduce(Dev D, int n, int d, int obs) {
+  const long long nW = (long long)n * d * d, nb = (long long)n * d, nC = (long long)obs * d;
+  const long long total = nW + nb + nC;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    if (e < nW) {
+      if (e >= (long long)d * d)
+        for (int b = 0; b < D.num_inst; ++b) s += D.pW[(long long)b * nW + e];
+      if (D.dW) D.dW[e] = s;
+    } else if (e < nW + nb) {
+      const long long f = e - nW;
+      for (int b = 0; b < D.num_inst; ++b) s += D.pbias[(long long)b * nb + f];
+      if (D.dbias) D.dbias[f] = s;
+    } else {
+      const long long f = e - nW - nb;
+      for (int b = 0; b < D.num_inst; ++b) s += D.pC[(long long)b * nC + f];
+      if (D.dC) D.dC[f] = s;
+    }
+  }
+}
+
+// ---- launchers ----------------------------------------------------------------------------
+void launch_node_const(const Dev& D, cudaStream_t s) {
+  k_node_const<<<D.num_nodes, 128, 0, s>>>(D);
+}
+void launch_sample(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s) {
+  k_sample<<<ntiles, kThreads, 2 * kMaxD * sizeof(float), s>>>(D, tiles);
+}
+void launch_obs_fwd(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s) {
+  if (ntiles) k_obs_fwd<<<ntiles, kThreads, kMaxD * sizeof(float), s>>>(D, tiles);
+}
+void launch_project(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s) {
+  if (ntiles) k_project<<<ntiles, kThreads, kMaxD * sizeof(float), s>>>(D, tiles);
+}
+void launch_root(const Dev& D, int maxK, cudaStream_t s) {
+  static bool once = (cudaFuncSetAttribute(k_root, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           kMaxK * (int)sizeof(float)), true);
+  (void)once;
+  k_root<<<D.num_inst, 256, maxK * sizeof(float), s>>>(D);
+}
+void launch_node_grad(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s) {
+  k_node_grad<<<ntiles, kThreads, kMaxD * sizeof(float), s>>>(D, tiles);
+}
+void launch_node_reduce(const Dev& D, cudaStream_t s) { k_node_reduce<<<D.num_nodes, 256, 0, s>>>(D); }
+void launch_param_dW(const Dev& D, const int* nonroot, int n_nonroot, int maxd, cudaStream_t s) {
+  if (!n_nonroot) return;
+  const int t = (maxd + kTile - 1) / kTile;
+  k_param_dW<<<dim3(n_nonroot, t, t), kThreads, 0, s>>>(D, nonroot);
+}
+void launch_param_dC(const Dev& D, int maxd, int maxobs, cudaStream_t s) {
+  k_param_dC<<<dim3(D.num_inst, (maxobs + kTile - 1) / kTile, (maxd + kTile - 1) / kTile), kThreads,
+               kMaxD * sizeof(float), s>>>(D);
+}
+void launch_shared_reduce(const Dev& D, int n, int d, int obs, cudaStream_t s) {
+  const long long total = (long long)n * d * d + (long long)n * d + (long long)obs * d;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+  k_shared_reduce<<<blocks, 256, 0, s>>>(D, n, d, obs);
+}
+void launch_root_bias(const Dev&, cudaStream_t) {}
+
+}  // namespace tmc

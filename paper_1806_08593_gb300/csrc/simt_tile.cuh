@@ -1,0 +1,97 @@
+// simt_tile.cuh -- FP32 CUDA-core 64x64 tile products used by the FP32 path.
+//
+// A CTA of 256 threads owns a 64x64 output tile; thread (ty, tx) = (tid / 16, tid % 16)
+// holds rows ty*4 .. ty*4+3 and columns tx*4 .. tx*4+3 in acc[4][4].  Operands are staged
+// through shared memory in 16-deep slices laid out [l][m] (contraction index major), so the
+// inner loop reads one float4 of each operand per step.
+#pragma once
+#include "tmc_internal.cuh"
+
+namespace tmc {
+
+constexpr int kSlice = 16;
+constexpr int kLd = kTile + 4;  // padded shared-memory row (floats)
+
+struct TileSmem {
+  float a[kSlice * kLd];
+  float b[kSlice * kLd];
+};
+
+// Loads a 16 x 64 slice into s[l][m].
+//   TRANS = true : element (m, l) of a row-major matrix src[m * ld + l] ("row m, depth l")
+//   TRANS = false: element (l, m) of a row-major matrix src[l * ld + m]
+// Out-of-range entries (m >= mlim or l0 + l >= llim) are zero.
+template <bool TRANS>
+__device__ __forceinline__ void load_slice(float* s, const float* __restrict__ src, long long ld,
+                                           int mlim, int l0, int llim) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int e = tid; e < kSlice * kTile; e += kThreads) {
+    int l, m;
+    if (TRANS) { m = e >> 4; l = e & 15; }
+    else       { l = e >> 6; m = e & 63; }
+    const int gl = l0 + l;
+    float v = 0.f;
+    if (m < mlim && gl < llim) v = TRANS ? src[(long long)m * ld + gl] : src[(long long)gl * ld + m];
+    s[l * kLd + m] = v;
+  }
+}
+
+__device__ __forceinline__ void slice_fma(float acc[4][4], const float* sa, const float* sb) {
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+  for (int l = 0; l < kSlice; ++l) {
+    const float4 a = *reinterpret_cast<const float4*>(sa + l * kLd + ty * 4);
+    const float4 b = *reinterpret_cast<const float4*>(sb + l * kLd + tx * 4);
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+}
+
+// acc += opA * opB over contraction length L, where
+//   opA(m, l) = A_TRANS ? A[m*lda + l] : A[l*lda + m]     (m < ma)
+//   opB(n, l) = B_TRANS ? B[n*ldb + l] : B[l*ldb + n]     (n < nb)
+// and the product is sum_l opA(m, l) * opB(n, l).
+template <bool A_TRANS, bool B_TRANS>
+__device__ __forceinline__ void tile_gemm(float acc[4][4], const float* __restrict__ A,
+                                          long long lda, int ma, const float* __restrict__ B,
+                                          long long ldb, int nb, int L, TileSmem& sm) {
+  for (int l0 = 0; l0 < L; l0 += kSlice) {
+    load_slice<A_TRANS>(sm.a, A, lda, ma, l0, L);
+    load_slice<B_TRANS>(sm.b, B, ldb, nb, l0, L);
+    __syncthreads();
+    slice_fma(acc, sm.a, sm.b);
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ void zero_acc(float acc[4][4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+}
+
+// Sum over the 16 threads that share a row group (tx = 0..15 live in one half-warp).
+__device__ __forceinline__ float row_group_sum(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 8);
+  return v;
+}
+__device__ __forceinline__ float row_group_max(float v) {
+  v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 1));
+  v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 2));
+  v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 4));
+  v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 8));
+  return v;
+}
+
+__device__ __forceinline__ void flag_error(int* err, int bit) { atomicOr(err, bit); }
+
+}  // namespace tmc

@@ -1,0 +1,107 @@
+// tmc_internal.cuh -- data structures shared by the host runtime and the kernels.
+//
+// Every latent of every instance is a "node" with a global id g.  Per-sample scalars
+// (node term, messages, weights) live in [g][k] blocks, per-sample vectors (centred samples,
+// conditional means, gradients) in [g][k][j] blocks; NodeInfo carries the offsets.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tmc {
+
+constexpr int kTile = 64;       // rows / columns of one FP32 SIMT tile
+constexpr int kThreads = 256;   // threads of every FP32 SIMT tile kernel (16 x 16, 4x4 each)
+constexpr int kMaxK = 16384;    // samples per latent supported (edge prologue keeps K floats)
+constexpr int kMaxD = 1024;     // latent / observation dimension supported
+
+struct NodeInfo {
+  int b, i;            // instance, local node index
+  int parent;          // global id of the parent node, -1 for the root
+  int K, d, obs;       // samples, latent dim, observation dim of the instance
+  int leaf_slot;       // >= 0: index of this leaf among the instance's leaves; -1 otherwise
+  int child_begin;     // children[child_begin .. child_end) are global ids of the children
+  int child_end;
+  int level;           // depth below the root
+  int root;            // global id of the instance's root
+  long long off_nk;    // start of this node's [K] block in per-sample scalar arrays
+  long long off_nkd;   // start of this node's [K][d] block in per-sample vector arrays
+  long long off_q;     // start of m_i / logs_i ([d]) in q_mean / q_logstd
+  long long off_W;     // start of W_i ([d][d]) in W
+  long long off_bias;  // start of bias_i ([d]) in bias
+  long long off_C;     // start of the instance's C ([obs][d])
+  long long off_x;     // start of this leaf's observation ([obs]) in x (leaves only)
+  long long off_pW;    // start of this node's block in the per-(instance, node) dW partials
+};
+
+struct InstInfo {
+  int node0;           // global id of the root
+  int n, K, d, obs;
+  long long off_C, off_pC;  // instance C offset; per-instance dC partial offset
+};
+
+// One unit of work of a tiled kernel: a node and the first sample row of the tile.
+struct Tile {
+  int node;
+  int row0;
+};
+
+// Device-side error word bits.
+enum : int { kErrNumeric = 1, kErrTimeout = 2 };
+
+// Everything a kernel may touch, passed by value.
+struct Dev {
+  const NodeInfo* nodes;
+  const InstInfo* insts;
+  const int* children;
+  int num_nodes, num_inst;
+  float inv_var, inv_obs_var;   // 1/prior_var, 1/obs_var
+  double prior_var, obs_var;
+  int shared;
+
+  // inputs (caller's device memory)
+  const float *eps, *q_mean, *q_logstd, *W, *bias, *C, *x;
+
+  // workspace
+  float* zt;      // [nkd] centred samples  z~ = exp(logs) * eps
+  float* mut;     // [nkd] centred conditional means mu~_i[k] = W_i z_p^k + bias_i - m_i
+  float* zn;      // [nk]  ||z~||^2
+  float* mun;     // [nk]  ||mu~||^2
+  float* u;       // [nk]  per-sample node term (constants removed)
+  float* beta;    // [nk]  normalised node log-potential: node term + children messages - max
+  float* lam;     // [nk]  message to the parent (constants removed)
+  float* q;       // [nk]  marginal weight of each sample
+  float* nodemax; // [nodes] max over k of the unnormalised beta
+  double* nodeconst; // [nodes] FP64 constants of the node term
+  float* dmu;     // [nkd] d logP / d mu_i[k]
+  float* gz;      // [nkd] d logP / d z_i[k] without the proposal's own score term
+  float* pW;      // per-(instance, node) dW partials  (shared params only)
+  float* pbias;   // per-(instance, node) dbias partials (shared params only)
+  float* pC;      // per-instance dC partials (shared params only)
+  int* err;       // device error word
+
+  // outputs of the current call
+  double* log_phat;
+  const double* grad_out;
+  float *dz, *deps, *dq_mean, *dq_logstd, *dW, *dbias, *dC;
+};
+
+// ---- launchers (defined in the .cu files) -------------------------------------------------
+// FP32 SIMT path
+void launch_node_const(const Dev& D, cudaStream_t s);
+void launch_sample(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s);
+void launch_obs_fwd(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s);
+void launch_project(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s);
+void launch_edge_fwd_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK, cudaStream_t s);
+void launch_root(const Dev& D, int maxK, cudaStream_t s);
+void launch_edge_bwd_rows_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK,
+                              cudaStream_t s);
+void launch_edge_bwd_cols_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK,
+                              cudaStream_t s);
+void launch_node_grad(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s);
+void launch_node_reduce(const Dev& D, cudaStream_t s);
+void launch_param_dW(const Dev& D, const int* nonroot, int n_nonroot, int maxd, cudaStream_t s);
+void launch_param_dC(const Dev& D, int maxd, int maxobs, cudaStream_t s);
+void launch_shared_reduce(const Dev& D, int n, int d, int obs, cudaStream_t s);
+void launch_root_bias(const Dev& D, cudaStream_t s);
+
+}  // namespace tmc

@@ -1,0 +1,467 @@
+// tmc_plan.cu -- host runtime behind the C ABI of include/tmc.h.
+//
+// A plan turns the problem description into:
+//   * a node table (one entry per latent of every instance) with all buffer offsets,
+//   * the elimination schedule of Section 2.2: tree levels processed from the deepest up
+//     (forward: messages to parents) and from the root down (adjoint),
+//   * tile lists (node, first sample row) for every kernel, and
+//   * one device workspace holding samples, means, messages, weights and gradient partials.
+// Calls only enqueue kernels on the caller's stream; nothing allocates after creation.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/tmc.h"
+#include "tmc_internal.cuh"
+#include "tmc_tc.cuh"
+
+using namespace tmc;
+
+namespace {
+
+struct ProfileSlot {
+  cudaEvent_t start, stop;
+  int cls;
+};
+
+}  // namespace
+
+struct tmc_plan_s {
+  // description
+  int B = 0, shared = 0, precision = 0;
+  double prior_var = 1.0, obs_var = 1.0;
+  int maxK = 0, maxd = 0, maxobs = 0, maxlevel = 0, shared_n = 0, shared_d = 0, shared_obs = 0;
+  long long tot_nk = 0, tot_nkd = 0, tot_q = 0, tot_W = 0;
+
+  std::vector<NodeInfo> nodes;
+  std::vector<InstInfo> insts;
+  std::vector<int> children, nonroot;
+
+  // tile lists: [begin, end) ranges into one device array
+  std::vector<Tile> tiles;
+  int t_sample_b = 0, t_sample_e = 0, t_leaf_b = 0, t_leaf_e = 0, t_proj_b = 0, t_proj_e = 0;
+  std::vector<int> t_level_b, t_level_e;  // per level (index = level), edges whose child is there
+
+  // device
+  NodeInfo* d_nodes = nullptr;
+  InstInfo* d_insts = nullptr;
+  int* d_children = nullptr;
+  int* d_nonroot = nullptr;
+  Tile* d_tiles = nullptr;
+  int* d_err = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  Dev dev{};
+  tc::TcWork tcw{};
+
+  // state
+  bool fwd_done = false;
+  tmc_inputs last_in{};
+
+  // profiling
+  bool prof = false;
+  std::vector<ProfileSlot> slots;
+  size_t slot_next = 0;
+  double prof_ms[TMC_KC_COUNT] = {0};
+  long long prof_n[TMC_KC_COUNT] = {0};
+};
+
+namespace {
+
+tmc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TMC_OK : TMC_ERR_CUDA; }
+
+void drain_profile(tmc_plan p) {
+  for (size_t i = 0; i < p->slot_next; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->slots[i].start, p->slots[i].stop) == cudaSuccess) {
+      p->prof_ms[p->slots[i].cls] += ms;
+      p->prof_n[p->slots[i].cls] += 1;
+    }
+  }
+  p->slot_next = 0;
+}
+
+// Launch wrapper: optional event pair around the launch, then the launch error check.
+template <class F>
+tmc_status timed(tmc_plan p, int cls, cudaStream_t s, F&& launch) {
+  ProfileSlot* slot = nullptr;
+  if (p->prof) {
+    if (p->slot_next == p->slots.size()) {  // pool exhausted: settle and reuse
+      cudaStreamSynchronize(s);
+      drain_profile(p);
+    }
+    slot = &p->slots[p->slot_next++];
+    slot->cls = cls;
+    cudaEventRecord(slot->start, s);
+  }
+  launch();
+  cudaError_t e = cudaGetLastError();
+  if (slot) cudaEventRecord(slot->stop, s);
+  return cuda_status(e);
+}
+
+#define TRY(x)                        \
+  do {                                \
+    tmc_status _st = (x);             \
+    if (_st != TMC_OK) return _st;    \
+  } while (0)
+
+template <class T>
+tmc_status upload(T** dst, const std::vector<T>& v) {
+  if (v.empty()) { *dst = nullptr; return TMC_OK; }
+  if (cudaMalloc(dst, sizeof(T) * v.size()) != cudaSuccess) return TMC_ERR_NOMEM;
+  return cuda_status(cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+}
+
+tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
+  const int B = ds->num_instances;
+  if (B < 1 || !ds->n || !ds->parent || !ds->K || !ds->d || !ds->obs_dim) return TMC_ERR_INVALID_ARG;
+  if (!(ds->prior_var > 0.0) || !(ds->obs_var > 0.0) || !std::isfinite(ds->prior_var) ||
+      !std::isfinite(ds->obs_var))
+    return TMC_ERR_INVALID_ARG;
+  if (ds->precision < TMC_PREC_FP32 || ds->precision > TMC_PREC_FP16_TC) return TMC_ERR_INVALID_ARG;
+  p->B = B;
+  p->shared = ds->shared_params ? 1 : 0;
+  p->precision = ds->precision;
+  p->prior_var = ds->prior_var;
+  p->obs_var = ds->obs_var;
+
+  long long poff = 0, off_nk = 0, off_nkd = 0, off_q = 0, off_W = 0, off_bias = 0, off_C = 0,
+            off_x = 0, off_pW = 0, off_pC = 0;
+  for (int b = 0; b < B; ++b) {
+    const int n = ds->n[b], K = ds->K[b], d = ds->d[b], obs = ds->obs_dim[b];
+    if (n < 1 || K < 1 || d < 1 || obs < 1) return TMC_ERR_INVALID_ARG;
+    if (K > kMaxK || d > kMaxD || obs > kMaxD) return TMC_ERR_UNSUPPORTED;
+    const int* par = ds->parent + poff;
+    if (par[0] != -1) return TMC_ERR_INVALID_ARG;
+    for (int i = 1; i < n; ++i)
+      if (par[i] < 0 || par[i] >= i) return TMC_ERR_INVALID_ARG;
+    if (p->shared && b > 0) {
+      if (n != ds->n[0] || d != ds->d[0] || obs != ds->obs_dim[0]) return TMC_ERR_INVALID_ARG;
+      for (int i = 0; i < n; ++i)
+        if (par[i] != ds->parent[i]) return TMC_ERR_INVALID_ARG;
+    }
+    const int node0 = (int)p->nodes.size();
+    // children lists and levels
+    std::vector<std::vector<int>> ch(n);
+    std::vector<int> level(n, 0);
+    for (int i = 1; i < n; ++i) {
+      ch[par[i]].push_back(i);
+      level[i] = level[par[i]] + 1;
+    }
+    // instance-level offsets
+    const long long iW = p->shared ? 0 : off_W, ib = p->shared ? 0 : off_bias,
+                    iC = p->shared ? 0 : off_C;
+    int leaves = 0;
+    for (int i = 0; i < n; ++i) {
+      NodeInfo nd{};
+      nd.b = b;
+      nd.i = i;
+      nd.parent = i ? node0 + par[i] : -1;
+      nd.K = K;
+      nd.d = d;
+      nd.obs = obs;
+      nd.leaf_slot = ch[i].empty() ? leaves++ : -1;
+      nd.child_begin = (int)p->children.size();
+      for (int c : ch[i]) p->children.push_back(node0 + c);
+      nd.child_end = (int)p->children.size();
+      nd.level = level[i];
+      nd.root = node0;
+      nd.off_nk = off_nk + (long long)i * K;
+      nd.off_nkd = off_nkd + (long long)i * K * d;
+      nd.off_q = off_q + (long long)i * d;
+      nd.off_W = iW + (long long)i * d * d;
+      nd.off_bias = ib + (long long)i * d;
+      nd.off_C = iC;
+      nd.off_x = off_x + (long long)(nd.leaf_slot >= 0 ? nd.leaf_slot : 0) * obs;
+      nd.off_pW = off_pW + (long long)i * d * d;
+      p->nodes.push_back(nd);
+      p->maxlevel = std::max(p->maxlevel, level[i]);
+    }
+    InstInfo in{};
+    in.node0 = node0;
+    in.n = n;
+    in.K = K;
+    in.d = d;
+    in.obs = obs;
+    in.off_C = iC;
+    in.off_pC = off_pC;
+    p->insts.push_back(in);
+    p->maxK = std::max(p->maxK, K);
+    p->maxd = std::max(p->maxd, d);
+    p->maxobs = std::max(p->maxobs, obs);
+    poff += n;
+    off_nk += (long long)n * K;
+    off_nkd += (long long)n * K * d;
+    off_q += (long long)n * d;
+    off_x += (long long)leaves * obs;
+    off_pW += (long long)n * d * d;
+    off_pC += (long long)obs * d;
+    if (!p->shared) {
+      off_W += (long long)n * d * d;
+      off_bias += (long long)n * d;
+      off_C += (long long)obs * d;
+    }
+  }
+  p->tot_nk = off_nk;
+  p->tot_nkd = off_nkd;
+  p->tot_q = off_q;
+  p->shared_n = ds->n[0];
+  p->shared_d = ds->d[0];
+  p->shared_obs = ds->obs_dim[0];
+
+  // tile lists
+  auto add_tiles = [&](int g) {
+    for (int r = 0; r < p->nodes[g].K; r += kTile) p->tiles.push_back(Tile{g, r});
+  };
+  const int G = (int)p->nodes.size();
+  p->t_sample_b = (int)p->tiles.size();
+  for (int g = 0; g < G; ++g) add_tiles(g);
+  p->t_sample_e = (int)p->tiles.size();
+  p->t_leaf_b = (int)p->tiles.size();
+  for (int g = 0; g < G; ++g)
+    if (p->nodes[g].leaf_slot >= 0) add_tiles(g);
+  p->t_leaf_e = (int)p->tiles.size();
+  p->t_proj_b = (int)p->tiles.size();
+  for (int g = 0; g < G; ++g)
+    if (p->nodes[g].parent >= 0) {
+      add_tiles(g);
+      p->nonroot.push_back(g);
+    }
+  p->t_proj_e = (int)p->tiles.size();
+  p->t_level_b.assign(p->maxlevel + 1, 0);
+  p->t_level_e.assign(p->maxlevel + 1, 0);
+  for (int L = 1; L <= p->maxlevel; ++L) {
+    p->t_level_b[L] = (int)p->tiles.size();
+    for (int g = 0; g < G; ++g)
+      if (p->nodes[g].level == L) add_tiles(g);
+    p->t_level_e[L] = (int)p->tiles.size();
+  }
+  return TMC_OK;
+}
+
+tmc_status alloc_device(tmc_plan p) {
+  TRY(upload(&p->d_nodes, p->nodes));
+  TRY(upload(&p->d_insts, p->insts));
+  TRY(upload(&p->d_children, p->children));
+  TRY(upload(&p->d_nonroot, p->nonroot));
+  TRY(upload(&p->d_tiles, p->tiles));
+  if (cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess) return TMC_ERR_NOMEM;
+  if (cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) return TMC_ERR_CUDA;
+
+  const long long nk = p->tot_nk, nkd = p->tot_nkd, G = (long long)p->nodes.size();
+  const long long nW = p->shared ? (long long)p->B * p->shared_n * p->shared_d * p->shared_d : 0;
+  const long long nb = p->shared ? (long long)p->B * p->shared_n * p->shared_d : 0;
+  const long long nC = p->shared ? (long long)p->B * p->shared_obs * p->shared_d : 0;
+  // layout: 256-byte aligned sub-buffers
+  struct Sub { void** dst; size_t bytes; };
+  float *zt, *mut, *zn, *mun, *u, *beta, *lam, *q, *nodemax, *dmu, *gz, *pW, *pbias, *pC;
+  double* nodeconst;
+  std::vector<Sub> subs = {
+      {(void**)&zt, sizeof(float) * nkd},      {(void**)&mut, sizeof(float) * nkd},
+      {(void**)&dmu, sizeof(float) * nkd},     {(void**)&gz, sizeof(float) * nkd},
+      {(void**)&zn, sizeof(float) * nk},       {(void**)&mun, sizeof(float) * nk},
+      {(void**)&u, sizeof(float) * nk},        {(void**)&beta, sizeof(float) * nk},
+      {(void**)&lam, sizeof(float) * nk},      {(void**)&q, sizeof(float) * nk},
+      {(void**)&nodemax, sizeof(float) * G},   {(void**)&nodeconst, sizeof(double) * G},
+      {(void**)&pW, sizeof(float) * nW},       {(void**)&pbias, sizeof(float) * nb},
+      {(void**)&pC, sizeof(float) * nC},
+  };
+  std::vector<tc::TcSub> tsubs;
+  if (p->precision != TMC_PREC_FP32) tc::workspace_layout(p->tcw, p->nodes, nk, nkd, tsubs);
+  size_t total = 0;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  for (auto& s : subs) total += al(s.bytes);
+  for (auto& s : tsubs) total += al(s.bytes);
+  if (cudaMalloc(&p->ws, total) != cudaSuccess) { p->ws = nullptr; return TMC_ERR_NOMEM; }
+  p->ws_bytes = total;
+  char* base = (char*)p->ws;
+  for (auto& s : subs) { *s.dst = base; base += al(s.bytes); }
+  for (auto& s : tsubs) { *s.dst = base; base += al(s.bytes); }
+
+  Dev& D = p->dev;
+  D.nodes = p->d_nodes;
+  D.insts = p->d_insts;
+  D.children = p->d_children;
+  D.num_nodes = (int)G;
+  D.num_inst = p->B;
+  D.inv_var = (float)(1.0 / p->prior_var);
+  D.inv_obs_var = (float)(1.0 / p->obs_var);
+  D.prior_var = p->prior_var;
+  D.obs_var = p->obs_var;
+  D.shared = p->shared;
+  D.zt = zt; D.mut = mut; D.zn = zn; D.mun = mun; D.u = u; D.beta = beta; D.lam = lam; D.q = q;
+  D.nodemax = nodemax; D.nodeconst = nodeconst; D.dmu = dmu; D.gz = gz;
+  D.pW = nW ? pW : nullptr; D.pbias = nb ? pbias : nullptr; D.pC = nC ? pC : nullptr;
+  D.err = p->d_err;
+  if (p->precision != TMC_PREC_FP32) TRY(tc::prepare(p->tcw, p->nodes, p->tiles, p->maxK, p->maxd));
+  return TMC_OK;
+}
+
+void free_plan(tmc_plan p) {
+  cudaFree(p->d_nodes);
+  cudaFree(p->d_insts);
+  cudaFree(p->d_children);
+  cudaFree(p->d_nonroot);
+  cudaFree(p->d_tiles);
+  cudaFree(p->d_err);
+  cudaFree(p->ws);
+  tc::release(p->tcw);
+  for (auto& s : p->slots) {
+    cudaEventDestroy(s.start);
+    cudaEventDestroy(s.stop);
+  }
+  delete p;
+}
+
+bool inputs_ok(const tmc_inputs* in) {
+  return in && in->eps && in->q_mean && in->q_logstd && in->W && in->bias && in->C && in->x;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tmc_status_string(tmc_status s) {
+  switch (s) {
+    case TMC_OK: return "TMC_OK";
+    case TMC_ERR_INVALID_ARG: return "TMC_ERR_INVALID_ARG";
+    case TMC_ERR_UNSUPPORTED: return "TMC_ERR_UNSUPPORTED";
+    case TMC_ERR_NOMEM: return "TMC_ERR_NOMEM";
+    case TMC_ERR_CUDA: return "TMC_ERR_CUDA";
+    case TMC_ERR_NUMERIC: return "TMC_ERR_NUMERIC";
+    case TMC_ERR_TIMEOUT: return "TMC_ERR_TIMEOUT";
+    case TMC_ERR_STATE: return "TMC_ERR_STATE";
+  }
+  return "TMC_ERR_UNKNOWN";
+}
+
+tmc_status tmc_plan_create(const tmc_problem_desc* desc, tmc_plan* out) {
+  if (!desc || !out) return TMC_ERR_INVALID_ARG;
+  *out = nullptr;
+  tmc_plan p = new (std::nothrow) tmc_plan_s();
+  if (!p) return TMC_ERR_NOMEM;
+  tmc_status st = build_plan(desc, p);
+  if (st == TMC_OK && p->precision != TMC_PREC_FP32) st = tc::supported(p->nodes, p->precision);
+  if (st == TMC_OK) st = alloc_device(p);
+  if (st != TMC_OK) {
+    free_plan(p);
+    return st;
+  }
+  *out = p;
+  return TMC_OK;
+}
+
+tmc_status tmc_plan_destroy(tmc_plan p) {
+  if (!p) return TMC_OK;
+  cudaDeviceSynchronize();
+  free_plan(p);
+  return TMC_OK;
+}
+
+tmc_status tmc_plan_workspace_bytes(tmc_plan p, size_t* bytes) {
+  if (!p || !bytes) return TMC_ERR_INVALID_ARG;
+  *bytes = p->ws_bytes;
+  return TMC_OK;
+}
+
+tmc_status tmc_log_marginal(tmc_plan p, const tmc_inputs* in, double* log_phat, void* stream) {
+  if (!p || !inputs_ok(in) || !log_phat) return TMC_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Dev D = p->dev;
+  D.eps = in->eps; D.q_mean = in->q_mean; D.q_logstd = in->q_logstd;
+  D.W = in->W; D.bias = in->bias; D.C = in->C; D.x = in->x;
+  D.log_phat = log_phat;
+  const Tile* T = p->d_tiles;
+  const bool tc_path = p->precision != TMC_PREC_FP32;
+  TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_node_const(D, s); }));
+  TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_sample(D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
+  TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_obs_fwd(D, T + p->t_leaf_b, p->t_leaf_e - p->t_leaf_b, s); }));
+  TRY(timed(p, TMC_KC_PROJECT, s, [&] { launch_project(D, T + p->t_proj_b, p->t_proj_e - p->t_proj_b, s); }));
+  if (tc_path) TRY(timed(p, TMC_KC_PROJECT, s, [&] { tc::launch_pack(p->tcw, D, s); }));
+  for (int L = p->maxlevel; L >= 1; --L) {
+    const int b = p->t_level_b[L], e = p->t_level_e[L];
+    if (tc_path)
+      TRY(timed(p, TMC_KC_EDGE_FWD, s, [&] { tc::launch_edge_fwd(p->tcw, D, L, s); }));
+    else
+      TRY(timed(p, TMC_KC_EDGE_FWD, s, [&] { launch_edge_fwd_f32(D, T + b, e - b, p->maxK, s); }));
+  }
+  TRY(timed(p, TMC_KC_ROOT, s, [&] { launch_root(D, p->maxK, s); }));
+  p->fwd_done = true;
+  p->last_in = *in;
+  return TMC_OK;
+}
+
+tmc_status tmc_backward(tmc_plan p, const tmc_inputs* in, const double* grad_out,
+                        const tmc_grads* g, void* stream) {
+  if (!p || !inputs_ok(in) || !g) return TMC_ERR_INVALID_ARG;
+  if (!p->fwd_done || std::memcmp(&p->last_in, in, sizeof(tmc_inputs)) != 0) return TMC_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  Dev D = p->dev;
+  D.eps = in->eps; D.q_mean = in->q_mean; D.q_logstd = in->q_logstd;
+  D.W = in->W; D.bias = in->bias; D.C = in->C; D.x = in->x;
+  D.grad_out = grad_out;
+  D.dz = g->dz; D.deps = g->deps; D.dq_mean = g->dq_mean; D.dq_logstd = g->dq_logstd;
+  D.dW = g->dW; D.dbias = g->dbias; D.dC = g->dC;
+  const Tile* T = p->d_tiles;
+  const bool tc_path = p->precision != TMC_PREC_FP32;
+  for (int L = 1; L <= p->maxlevel; ++L) {
+    const int b = p->t_level_b[L], e = p->t_level_e[L];
+    if (tc_path) {
+      TRY(timed(p, TMC_KC_EDGE_BWD, s, [&] { tc::launch_edge_bwd(p->tcw, D, L, s); }));
+    } else {
+      TRY(timed(p, TMC_KC_EDGE_BWD, s, [&] { launch_edge_bwd_cols_f32(D, T + b, e - b, p->maxK, s); }));
+      TRY(timed(p, TMC_KC_EDGE_BWD, s, [&] { launch_edge_bwd_rows_f32(D, T + b, e - b, p->maxK, s); }));
+    }
+  }
+  if (tc_path) TRY(timed(p, TMC_KC_PARAM, s, [&] { tc::launch_unpack_grads(p->tcw, D, s); }));
+  TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_node_grad(D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
+  TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_node_reduce(D, s); }));
+  if (g->dW || g->dbias)
+    TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_param_dW(D, p->d_nonroot, (int)p->nonroot.size(), p->maxd, s); }));
+  if (g->dC) TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_param_dC(D, p->maxd, p->maxobs, s); }));
+  if (p->shared && (g->dW || g->dbias || g->dC))
+    TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_shared_reduce(D, p->shared_n, p->shared_d, p->shared_obs, s); }));
+  return TMC_OK;
+}
+
+tmc_status tmc_plan_sync_status(tmc_plan p, void* stream) {
+  if (!p) return TMC_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return TMC_ERR_CUDA;
+  int err = 0;
+  if (cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TMC_ERR_CUDA;
+  if (err && cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) return TMC_ERR_CUDA;
+  if (err & kErrTimeout) return TMC_ERR_TIMEOUT;
+  if (err & kErrNumeric) return TMC_ERR_NUMERIC;
+  return TMC_OK;
+}
+
+tmc_status tmc_profile_enable(tmc_plan p, int enable) {
+  if (!p) return TMC_ERR_INVALID_ARG;
+  if (enable && p->slots.empty()) {
+    p->slots.resize(8192);
+    for (auto& s : p->slots) {
+      if (cudaEventCreate(&s.start) != cudaSuccess || cudaEventCreate(&s.stop) != cudaSuccess)
+        return TMC_ERR_CUDA;
+    }
+  }
+  p->prof = enable != 0;
+  p->slot_next = 0;
+  for (int i = 0; i < TMC_KC_COUNT; ++i) { p->prof_ms[i] = 0.0; p->prof_n[i] = 0; }
+  return TMC_OK;
+}
+
+tmc_status tmc_profile_read(tmc_plan p, int cls, double* total_ms, long long* launches) {
+  if (!p || cls < 0 || cls >= TMC_KC_COUNT || !total_ms || !launches) return TMC_ERR_INVALID_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return TMC_ERR_CUDA;
+  drain_profile(p);
+  *total_ms = p->prof_ms[cls];
+  *launches = p->prof_n[cls];
+  return TMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,240 @@
+"""Python binding of the C ABI in include/tmc.h (argument marshalling only).
+
+Every step of the TMC hot path runs in the CUDA library ``_build/libtmc_gb300.so``; this
+module only passes device pointers and streams.  PyTorch provides device memory, streams
+and autograd plumbing.  There is no CPU fallback: if the library or a CUDA device is
+missing, the calls raise.
+
+    plan = Plan.from_problem(problem, precision="fp32")
+    t = plan.to_device(problem)                 # dict of CUDA tensors in the C-ABI layout
+    logp = tmc_log_marginal(plan, **t)          # differentiable w.r.t. eps, q_mean, q_logstd, W, bias, C
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtmc_gb300.so")
+
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
+STATUS = {0: "TMC_OK", 1: "TMC_ERR_INVALID_ARG", 2: "TMC_ERR_UNSUPPORTED", 3: "TMC_ERR_NOMEM",
+          4: "TMC_ERR_CUDA", 5: "TMC_ERR_NUMERIC", 6: "TMC_ERR_TIMEOUT", 7: "TMC_ERR_STATE"}
+KERNEL_CLASSES = ["sample", "project", "edge_fwd", "root", "edge_bwd", "param"]
+EXPORTS = ["tmc_plan_create", "tmc_log_marginal", "tmc_backward", "tmc_plan_sync_status",
+           "tmc_plan_workspace_bytes", "tmc_plan_destroy", "tmc_status_string",
+           "tmc_profile_enable", "tmc_profile_read"]
+
+
+class TMCError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s: %s" % (where, STATUS.get(status, str(status))))
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("num_instances", ctypes.c_int32), ("n", ctypes.c_void_p),
+                ("parent", ctypes.c_void_p), ("K", ctypes.c_void_p), ("d", ctypes.c_void_p),
+                ("obs_dim", ctypes.c_void_p), ("shared_params", ctypes.c_int32),
+                ("prior_var", ctypes.c_double), ("obs_var", ctypes.c_double),
+                ("precision", ctypes.c_int32)]
+
+
+class Inputs(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("eps", "q_mean", "q_logstd", "W", "bias", "C", "x")]
+
+
+class Grads(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("dz", "deps", "dq_mean", "dq_logstd", "dW", "dbias", "dC")]
+
+
+INPUT_NAMES = [f[0] for f in Inputs._fields_]
+GRAD_NAMES = [f[0] for f in Grads._fields_]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads the CUDA library (built by ``paper_1806_08593_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("TMC CUDA library not built (%s); run paper_1806_08593_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    P, V = ctypes.c_void_p, ctypes.c_void_p
+    lib.tmc_plan_create.argtypes = [ctypes.POINTER(ProblemDesc), ctypes.POINTER(P)]
+    lib.tmc_log_marginal.argtypes = [P, ctypes.POINTER(Inputs), P, V]
+    lib.tmc_backward.argtypes = [P, ctypes.POINTER(Inputs), P, ctypes.POINTER(Grads), V]
+    lib.tmc_plan_sync_status.argtypes = [P, V]
+    lib.tmc_plan_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.tmc_plan_destroy.argtypes = [P]
+    lib.tmc_status_string.argtypes = [ctypes.c_int]
+    lib.tmc_status_string.restype = ctypes.c_char_p
+    lib.tmc_profile_enable.argtypes = [P, ctypes.c_int]
+    lib.tmc_profile_read.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_longlong)]
+    for f in ("tmc_plan_create", "tmc_log_marginal", "tmc_backward", "tmc_plan_sync_status",
+              "tmc_plan_workspace_bytes", "tmc_plan_destroy", "tmc_profile_enable", "tmc_profile_read"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise TMCError(st, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """Owns a tmc_plan (topology, schedule, device workspace) for one batch shape."""
+
+    def __init__(self, n, parent, K, d, obs, shared: bool, prior_var: float, obs_var: float,
+                 precision: str = "fp32"):
+        lib = load_library()
+        self._keep = [np.ascontiguousarray(a, dtype=np.int32) for a in (n, parent, K, d, obs)]
+        n_, par_, K_, d_, o_ = self._keep
+        desc = ProblemDesc(len(n_), n_.ctypes.data, par_.ctypes.data, K_.ctypes.data, d_.ctypes.data,
+                           o_.ctypes.data, int(bool(shared)), float(prior_var), float(obs_var),
+                           PRECISIONS[precision])
+        h = ctypes.c_void_p()
+        _check(lib.tmc_plan_create(ctypes.byref(desc), ctypes.byref(h)), "tmc_plan_create")
+        self._h = h
+        self._lib = lib
+        self.B = len(n_)
+        self.precision = precision
+        self.shared = bool(shared)
+        self.forward_calls = 0  # identifies the forward whose state the plan holds
+
+    @classmethod
+    def from_problem(cls, p, precision: str = "fp32") -> "Plan":
+        return cls(p.n, p.parent, p.K, p.d, p.obs, p.shared, p.prior_var, p.obs_var, precision)
+
+    @staticmethod
+    def to_device(p, device="cuda") -> dict:
+        import torch
+        return {k: torch.from_numpy(np.ascontiguousarray(getattr(p, k), dtype=np.float32)).to(device)
+                for k in INPUT_NAMES}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.tmc_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- raw C-ABI calls ---------------------------------------------------------------
+    def _inputs(self, t: dict) -> Inputs:
+        return Inputs(*[_ptr(t[k]) for k in INPUT_NAMES])
+
+    def forward(self, t: dict, out=None, stream=None):
+        """log P_TMC per instance (float64 CUDA tensor [B])."""
+        import torch
+        if out is None:
+            out = torch.empty(self.B, dtype=torch.float64, device=t["eps"].device)
+        inp = self._inputs(t)
+        _check(self._lib.tmc_log_marginal(self._h, ctypes.byref(inp), _ptr(out), _stream(stream)),
+               "tmc_log_marginal")
+        self.forward_calls += 1
+        return out
+
+    def backward(self, t: dict, grad_out=None, want=("deps", "dq_mean", "dq_logstd", "dW", "dbias", "dC"),
+                 out: dict | None = None, stream=None) -> dict:
+        """Gradients of sum_b grad_out[b] log P_TMC_b; ``want`` selects the outputs."""
+        import torch
+        src = {"dz": "eps", "deps": "eps", "dq_mean": "q_mean", "dq_logstd": "q_logstd",
+               "dW": "W", "dbias": "bias", "dC": "C"}
+        if out is None:
+            out = {k: torch.empty_like(t[src[k]]) for k in want}
+        g = Grads(*[_ptr(out.get(k)) for k in GRAD_NAMES])
+        go = None if grad_out is None else grad_out.to(torch.float64).contiguous()
+        inp = self._inputs(t)
+        _check(self._lib.tmc_backward(self._h, ctypes.byref(inp), _ptr(go), ctypes.byref(g),
+                                      _stream(stream)), "tmc_backward")
+        return out
+
+    def sync_status(self, stream=None):
+        _check(self._lib.tmc_plan_sync_status(self._h, _stream(stream)), "tmc_plan_sync_status")
+
+    def workspace_bytes(self) -> int:
+        v = ctypes.c_size_t()
+        _check(self._lib.tmc_plan_workspace_bytes(self._h, ctypes.byref(v)), "tmc_plan_workspace_bytes")
+        return int(v.value)
+
+    def profile_enable(self, on: bool = True):
+        _check(self._lib.tmc_profile_enable(self._h, int(on)), "tmc_profile_enable")
+
+    def profile_read(self) -> dict:
+        res = {}
+        for i, name in enumerate(KERNEL_CLASSES):
+            ms, n = ctypes.c_double(), ctypes.c_longlong()
+            _check(self._lib.tmc_profile_read(self._h, i, ctypes.byref(ms), ctypes.byref(n)),
+                   "tmc_profile_read")
+            res[name] = (ms.value, n.value)
+        return res
+
+
+def _autograd():
+    import torch
+
+    class TMCLogMarginal(torch.autograd.Function):
+        """log P_TMC per instance; backward runs the library's fused adjoint."""
+
+        @staticmethod
+        def forward(ctx, plan, eps, q_mean, q_logstd, W, bias, C, x):
+            t = dict(eps=eps.contiguous(), q_mean=q_mean.contiguous(), q_logstd=q_logstd.contiguous(),
+                     W=W.contiguous(), bias=bias.contiguous(), C=C.contiguous(), x=x.contiguous())
+            out = plan.forward(t)
+            ctx.plan = plan
+            ctx.t = t
+            ctx.call = plan.forward_calls
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            plan, t = ctx.plan, ctx.t
+            names = ["deps", "dq_mean", "dq_logstd", "dW", "dbias", "dC"]
+            flags = ctx.needs_input_grad[1:7]
+            want = [n for n, f in zip(names, flags) if f]
+            if not want:
+                return (None,) * 8
+            # the adjoint reads the state saved by the matching forward; redo it if another
+            # forward ran on this plan in between
+            if plan.forward_calls != ctx.call:
+                plan.forward(t)
+            g = plan.backward(t, grad_out=grad_out.contiguous(), want=want)
+            return (None,) + tuple(g.get(n) for n in names) + (None,)
+
+    return TMCLogMarginal
+
+
+_TMC = None
+
+
+def tmc_log_marginal(plan: Plan, eps, q_mean, q_logstd, W, bias, C, x):
+    """Differentiable log P_TMC[b] (float64, [B]) through the CUDA library."""
+    global _TMC
+    if _TMC is None:
+        _TMC = _autograd()
+    return _TMC.apply(plan, eps, q_mean, q_logstd, W, bias, C, x)
