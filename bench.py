@@ -30,8 +30,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 DEFAULT_WORKLOAD = "chain_n16_K1024_d128_B64"
-GRADS = ("deps", "dq_mean", "dq_logstd", "dW", "dbias", "dC")
-RESULT_GRADS = ("dq_mean", "dq_logstd", "dW", "dbias", "dC")  # read back in the e2e leg
+# A training step needs the gradients of every parameter of the model and the proposal.
+GRADS = ("dq_mean", "dq_logstd", "dW", "dbias", "dC")
+RESULT_GRADS = GRADS  # read back in the e2e leg
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
 SM_MAX_MHZ = 2070.0
@@ -200,10 +201,41 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------------------
 def algorithmic_flops(p, precision):
-    """Algorithmic FLOPs of the dominant kernel class per step (pairwise contractions):
-    forward 2*K_p*K_i*d per edge; adjoint 4*K_p*K_i*d per edge (pi z~ and pi^T mu~)."""
+    """Algorithmic FLOPs of the edge kernels per step (pairwise contractions, per edge with
+    K_p = K_i = K): forward 2*K^2*d (S = mu~ z~^T); adjoint 4*K^2*d (S recomputed, V = P z~_p).
+    The split-fp16 tensor-core path executes each S product as 3 MMAs; those extra MMAs are
+    not counted."""
     e = (p.n.astype(np.int64) - 1) * p.K.astype(np.int64) ** 2 * p.d.astype(np.int64)
     return {"edge_fwd": 2.0 * float(e.sum()), "edge_bwd": 4.0 * float(e.sum())}
+
+
+def time_plan_steps(p, precision, dev, steps, warmup):
+    """Device time per fwd+bwd step of a plan at the given precision (for the comparison)."""
+    import torch
+    from paper_1806_08593_gb300.tmc import Plan
+    plan = Plan.from_problem(p, precision)
+    t = plan.to_device(p, dev)
+    out = torch.empty(p.B, dtype=torch.float64, device=dev)
+    g = {k: torch.empty_like(t[{"dq_mean": "q_mean", "dq_logstd": "q_logstd", "dW": "W",
+                                 "dbias": "bias", "dC": "C"}[k]]) for k in GRADS}
+    for _ in range(warmup):
+        plan.forward(t, out=out)
+        plan.backward(t, out=g, want=GRADS)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        plan.forward(t, out=out)
+        plan.backward(t, out=g, want=GRADS)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    plan.sync_status()
+    ms = e0.elapsed_time(e1) / steps
+    lp = out.cpu().numpy()
+    plan.close()
+    del t, g
+    torch.cuda.empty_cache()
+    return ms, lp
 
 
 def run_ours(args):
@@ -225,7 +257,7 @@ def run_ours(args):
     plan = Plan.from_problem(p, args.precision)
     t = plan.to_device(p, dev)
     out_lp = torch.empty(p.B, dtype=torch.float64, device=dev)
-    grads = {k: torch.empty_like(t[{"deps": "eps", "dq_mean": "q_mean", "dq_logstd": "q_logstd",
+    grads = {k: torch.empty_like(t[{"dq_mean": "q_mean", "dq_logstd": "q_logstd",
                                     "dW": "W", "dbias": "bias", "dC": "C"}[k]]) for k in GRADS}
     stream = torch.cuda.current_stream(dev)
 
@@ -313,6 +345,15 @@ def run_ours(args):
                 "peak_source": "bf16_tflops (%s)" % src}
     total_launches = int(sum(v[1] for v in prof.values()))
 
+    # ---- the same step on the FP32 CUDA-core path, and the log P agreement ------------
+    fp32 = None
+    if args.precision != "fp32" and not args.no_fp32_compare:
+        lp_ours = out_lp.cpu().numpy()
+        ms32, lp32 = time_plan_steps(p, "fp32", dev, steps=3, warmup=1)
+        fp32 = {"value": entries / (ms32 * 1e-3), "ms_per_step": ms32,
+                "speedup": ms32 / ms_step,
+                "max_abs_dlogp_vs_fp32": float(np.max(np.abs(lp_ours - lp32)))}
+
     # ---- CPU baseline (oracle on a bounded sample) ------------------------------------
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
@@ -335,6 +376,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": {"value": entries * ws / (e2e_ms * 1e-3), "unit": "entries/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "fp32_path": fp32,
         "gpu_launches": total_launches,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "clocks": clk.summary(),
@@ -349,8 +391,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--precision", default=os.environ.get("TMC_BENCH_PRECISION", "fp32"),
+    ap.add_argument("--precision", default=os.environ.get("TMC_BENCH_PRECISION", "fp16"),
                     choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()

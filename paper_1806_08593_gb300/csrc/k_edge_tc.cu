@@ -1,19 +1,1134 @@
-// k_edge_tc.cu -- tcgen05 tensor-core edge kernels (not built yet: reports unsupported).
+// k_edge_tc.cu -- tcgen05 tensor-core path of the TMC hot path (sm_103a).
+//
+// Edge p -> i of the elimination (Section 2.2; factors of the Appendix), centred samples
+// z~ = z - m_i and conditional means mu~^k = W_i z~_p^k + c_i (c_i = W_i m_p + bias_i - m_i):
+//   log P(z_i^{k'} | z_p^k) = (mu~^k . z~^{k'} - |z~^{k'}|^2/2 - |mu~^k|^2/2) / var + const.
+//
+// Forward (k_edge_fwd_tc): a CTA owns 128 parent samples k.  Prologue: mu~ tile = Z~_p W_i^T
+//   on the tensor core (split operands), + c_i, |mu~|^2 in FP32, split again into the
+//   A operand.  Main loop over 128-sample chunks of the child: S = mu~ z~^T (3 split MMAs into
+//   TMEM, double-buffered), then 4 warps run an online log-sum-exp over k' (base 2) giving
+//   lam_i[k] = log sum_k' exp(F[k,k'] + beta_i[k']).
+//
+// Adjoint (k_edge_bwd_tc): a CTA owns 128 child samples k'.  With the weight of an entry
+//   pi[k,k'] = q_p[k] exp(F[k,k'] + beta_i[k'] - lam_i[k])  (Section 2.2, d log P / d log f),
+//   S^T[k',k] = (Z~_i W_i)[k'] . z~_p^k is formed from A' = Z~_i W_i (prologue) against chunks
+//   of the parent's samples; the CTA accumulates
+//     q_i[k']  = sum_k pi                    (row sums, in registers)
+//     V[k']    = sum_k pi z~_p^k             (tensor core, P from TMEM)
+//   and its epilogue reduces   G_i  = sum_k' V[k'] z~_i^{k'T}  (edge moment)
+//                              M2_i = sum_k' q_i[k'] z~_i^{k'} z~_i^{k'T},  zbar_i = sum q z~
+//   into global accumulators.  All parameter and proposal gradients follow from these d x d
+//   moments (k_asm_*), so no K x d gradient tensor is formed.
+//
+// Roles (256 threads): warp 0 issues TMA, warp 1 issues MMAs, warp 2 owns the TMEM
+// allocation, warps 4..7 (128 threads, one sample row each) run the exponentials.
+// Every mbarrier wait is bounded; on a timeout the kernel records kErrTimeout and winds down.
+#include <cstdio>
+#include <cstring>
+
+#include "simt_tile.cuh"
+#include "tc_ptx.cuh"
 #include "tmc_tc.cuh"
 
 namespace tmc {
 namespace tc {
 
-tmc_status supported(const std::vector<NodeInfo>&, int) { return TMC_ERR_UNSUPPORTED; }
-void workspace_layout(TcWork&, const std::vector<NodeInfo>&, long long, long long, std::vector<TcSub>&) {}
-tmc_status prepare(TcWork&, const std::vector<NodeInfo>&, const std::vector<Tile>&, int, int) {
-  return TMC_ERR_UNSUPPORTED;
+namespace {
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+constexpr int kThreadsTc = 256;
+constexpr int kBox = 16384;  // bytes of one 128-row x 128-byte swizzled box
+
+__device__ __forceinline__ int slot_of(const Dev& D, const NodeInfo& nd, int g) {
+  return D.shared ? nd.i : g;
 }
-void release(TcWork&) {}
-void launch_pack(TcWork&, const Dev&, cudaStream_t) {}
-void launch_edge_fwd(TcWork&, const Dev&, int, cudaStream_t) {}
-void launch_edge_bwd(TcWork&, const Dev&, int, cudaStream_t) {}
-void launch_unpack_grads(TcWork&, const Dev&, cudaStream_t) {}
+
+// Named barrier among the 128 exponential threads (warps 4..7).
+__device__ __forceinline__ void sync_math() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Writes 8 consecutive values of row r (columns 8*chunk .. 8*chunk+7) of a [128 x DP]
+// 128-byte-swizzled fp16 tile as hi / lo splits.
+__device__ __forceinline__ void store_split8(unsigned char* th, unsigned char* tl, int r, int chunk,
+                                             const float* v) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float h0, l0, h1, l1;
+    split_half(v[2 * q], h0, l0);
+    split_half(v[2 * q + 1], h1, l1);
+    h[q] = pack_half2(h0, h1);
+    l[q] = pack_half2(l0, l1);
+  }
+  const uint32_t off = (uint32_t)(chunk >> 3) * kBox + sw128_offset(r, chunk & 7);
+  *reinterpret_cast<uint4*>(th + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(tl + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+__device__ __forceinline__ void store_half8(unsigned char* t, int r, int chunk, const float* v) {
+  uint32_t h[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) h[q] = pack_half2(v[2 * q], v[2 * q + 1]);
+  const uint32_t off = (uint32_t)(chunk >> 3) * kBox + sw128_offset(r, chunk & 7);
+  *reinterpret_cast<uint4*>(t + off) = make_uint4(h[0], h[1], h[2], h[3]);
+}
+__device__ __forceinline__ void load_half8(const unsigned char* t, int r, int chunk, float* v) {
+  const uint32_t off = (uint32_t)(chunk >> 3) * kBox + sw128_offset(r, chunk & 7);
+  const uint4 u = *reinterpret_cast<const uint4*>(t + off);
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    __half2 hh = *reinterpret_cast<const __half2*>(&w[q]);
+    float2 f = __half22float2(hh);
+    v[2 * q] = f.x;
+    v[2 * q + 1] = f.y;
+  }
+}
+
+// K-major descriptor of K-step kk (16 fp16) of a [rows x DP] swizzled tile.
+__device__ __forceinline__ uint64_t kdesc(const unsigned char* base, int kk) {
+  return smem_desc_sw128(smem_u32(base) + (kk >> 2) * kBox + (kk & 3) * 32, 16, 1024);
+}
+// MN-major descriptor of K-step kk (16 rows) of a [128 rows (K) x N] swizzled tile.
+__device__ __forceinline__ uint64_t mndesc(const unsigned char* base, int kk) {
+  return smem_desc_sw128(smem_u32(base) + kk * 2048, kBox, 1024);
+}
+
+__device__ __forceinline__ void set_timeout(const Dev& D) { atomicOr(D.err, kErrTimeout); }
+
+// Bytes of the streaming ring: two stages of (hi, lo) sample tiles, and large enough for the
+// adjoint epilogue (Z~ hi, ones atom, Z~ lo, q z~ tile of two atoms).
+__host__ __device__ constexpr int ring_bytes(int DP) {
+  return (4 * kRows * DP * 2 > 2 * kRows * DP * 2 + 3 * kBox) ? 4 * kRows * DP * 2
+                                                              : 2 * kRows * DP * 2 + 3 * kBox;
+}
+}  // namespace
+
+// =======================================================================================
+// Samples for the tensor-core path: z~ = exp(logs) eps split into fp16 hi / lo rows of the
+// packed operand array, |z~|^2 and the per-sample node term (as in the FP32 path); FP32
+// samples are kept for the root and the leaves (prior / observation terms).
+// =======================================================================================
+__global__ void k_sample_tc(Dev D, TcDev T, const Tile* __restrict__ tiles) {
+  extern __shared__ float sm[];
+  const Tile t = tiles[blockIdx.x];
+  const NodeInfo nd = D.nodes[t.node];
+  const int d = nd.d;
+  float* s_std = sm;
+  float* s_off = sm + kTcMaxD;
+  const bool root = nd.parent < 0, keep32 = root || nd.leaf_slot >= 0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    s_std[j] = expf(D.q_logstd[nd.off_q + j]);
+    s_off[j] = root ? D.q_mean[nd.off_q + j] - D.bias[nd.off_bias + j] : 0.f;
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  bool bad = false;
+  for (int r = w; r < kTile; r += blockDim.x / 32) {
+    const int k = t.row0 + r;
+    if (k >= nd.K) break;
+    const long long base = nd.off_nkd + (long long)k * d;
+    const long long prow = (nd.off_nk + k) * kLdp;
+    float se = 0.f, sz = 0.f, sr = 0.f;
+    for (int j = lane; j < kLdp; j += 32) {
+      float z = 0.f;
+      if (j < d) {
+        const float e = D.eps[base + j];
+        z = s_std[j] * e;
+        bad |= !isfinite(z);
+        if (keep32) D.zt[base + j] = z;
+        se = fmaf(e, e, se);
+        sz = fmaf(z, z, sz);
+        const float rr = z + s_off[j];
+        sr = fmaf(rr, rr, sr);
+      }
+      float hi, lo;
+      split_half(z, hi, lo);
+      T.ZH[prow + j] = __float2half_rn(hi);
+      T.ZL[prow + j] = __float2half_rn(lo);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      se += __shfl_xor_sync(0xffffffffu, se, o);
+      sz += __shfl_xor_sync(0xffffffffu, sz, o);
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    }
+    if (lane == 0) {
+      float u = 0.5f * se;
+      if (root) u -= 0.5f * sr * D.inv_var;
+      D.u[nd.off_nk + k] = u;
+      D.zn[nd.off_nk + k] = sz;
+    }
+  }
+  if (bad) atomicOr(D.err, kErrNumeric);
+}
+
+// Split W_i (and its transpose) into padded fp16 hi / lo blocks, one 128 x 128 block per slot.
+__global__ void k_pack_w(Dev D, TcDev T, const int* __restrict__ nonroot) {
+  const int g = nonroot[blockIdx.x];
+  const NodeInfo nd = D.nodes[g];
+  if (D.shared && nd.b != 0) return;  // shared parameters: pack once (instance 0's nodes)
+  const int slot = slot_of(D, nd, g), d = nd.d;
+  const float* Wi = D.W + nd.off_W;
+  for (int e = threadIdx.x; e < kLdp * kLdp; e += blockDim.x) {
+    const int r = e / kLdp, c = e % kLdp;
+    const float v = (r < d && c < d) ? Wi[(long long)r * d + c] : 0.f;
+    float hi, lo;
+    split_half(v, hi, lo);
+    const long long o = (long long)slot * kLdp * kLdp;
+    T.WH[o + (long long)r * kLdp + c] = __float2half_rn(hi);
+    T.WL[o + (long long)r * kLdp + c] = __float2half_rn(lo);
+    T.WTH[o + (long long)c * kLdp + r] = __float2half_rn(hi);
+    T.WTL[o + (long long)c * kLdp + r] = __float2half_rn(lo);
+  }
+}
+
+// c_i = W_i m_p + bias_i - m_i per non-root node.
+__global__ void k_pack_c(Dev D, TcDev T, const int* __restrict__ nonroot) {
+  const int g = nonroot[blockIdx.x];
+  const NodeInfo nd = D.nodes[g];
+  const NodeInfo pn = D.nodes[nd.parent];
+  const int d = nd.d;
+  for (int r = threadIdx.x; r < kLdp; r += blockDim.x) {
+    float s = 0.f;
+    if (r < d) {
+      const float* w = D.W + nd.off_W + (long long)r * d;
+      for (int c = 0; c < d; ++c) s = fmaf(w[c], D.q_mean[pn.off_q + c], s);
+      s += D.bias[nd.off_bias + r] - D.q_mean[nd.off_q + r];
+    }
+    T.cvec[(long long)g * kLdp + r] = s;
+  }
+}
+
+// =======================================================================================
+// Forward edge kernel.
+// =======================================================================================
+template <int DP>
+__global__ void __launch_bounds__(kThreadsTc, 1)
+    k_edge_fwd_tc(Dev D, TcDev T, const Tile* __restrict__ tiles,
+                  const __grid_constant__ CUtensorMap mZH, const __grid_constant__ CUtensorMap mZL,
+                  const __grid_constant__ CUtensorMap mWH, const __grid_constant__ CUtensorMap mWL) {
+  constexpr int TB = kRows * DP * 2;  // bytes of one [128 x DP] fp16 tile
+  constexpr int NB = DP / 64;         // 64-column boxes per tile
+  constexpr int KS = DP / 16;         // K-steps over the latent dimension
+  extern __shared__ unsigned char smraw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sAH = sm;
+  unsigned char* sAL = sm + TB;
+  unsigned char* ring = sm + 2 * TB;  // 2 stages x (hi, lo)
+  float* cb = reinterpret_cast<float*>(ring + ring_bytes(DP));
+  __shared__ uint64_t bar_pro, bar_mu, bar_A, full[2], empty[2], sfull[2], sfree[2], bar_done;
+  __shared__ uint32_t tbase;
+  __shared__ float red[4];
+  __shared__ float cv[kTcMaxD];
+
+  const Tile t = tiles[blockIdx.x];
+  const NodeInfo nd = D.nodes[t.node];
+  const NodeInfo pn = D.nodes[nd.parent];
+  const int K = nd.K, nch = (K + kRows - 1) / kRows;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float iv = D.inv_var;
+
+  if (warp == 2) tmem_alloc(&tbase, 512);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar_pro, 1);
+    mbar_init(&bar_mu, 1);
+    mbar_init(&bar_A, 128);
+    mbar_init(&bar_done, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+      mbar_init(&sfull[i], 1);
+      mbar_init(&sfree[i], 128);
+    }
+    fence_barrier_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tb = tbase;
+  const uint32_t tS[2] = {tb, tb + 128}, tMU = tb + 256;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------------ TMA producer
+    prefetch_tmap(&mZH);
+    prefetch_tmap(&mZL);
+    const int slot = slot_of(D, nd, t.node);
+    mbar_arrive_expect_tx(&bar_pro, 4 * TB);
+    for (int b = 0; b < NB; ++b) {
+      const int prow = (int)(pn.off_nk + t.row0);
+      tma_load_2d(ring + b * kBox, &mZH, &bar_pro, b * 64, prow);
+      tma_load_2d(ring + TB + b * kBox, &mZL, &bar_pro, b * 64, prow);
+      tma_load_2d(ring + 2 * TB + b * kBox, &mWH, &bar_pro, b * 64, slot * kLdp);
+      tma_load_2d(ring + 3 * TB + b * kBox, &mWL, &bar_pro, b * 64, slot * kLdp);
+    }
+    bool ok = mbar_wait(&bar_mu, 0);  // prologue MMAs have read the ring
+    int issued = 0;
+    for (int c = 0; ok && c < nch; ++c) {
+      const int s = c & 1;
+      if (c >= 2 && !mbar_wait(&empty[s], ((c >> 1) + 1) & 1)) { ok = false; break; }
+      unsigned char* st = ring + s * 2 * TB;
+      mbar_arrive_expect_tx(&full[s], 2 * TB);
+      const int row = (int)(nd.off_nk + c * kRows);
+      for (int b = 0; b < NB; ++b) {
+        tma_load_2d(st + b * kBox, &mZH, &full[s], b * 64, row);
+        tma_load_2d(st + TB + b * kBox, &mZL, &full[s], b * 64, row);
+      }
+      issued = c + 1;
+    }
+    if (!ok) set_timeout(D);
+    // drain: every issued load has landed before the CTA may exit
+    for (int c = (issued > 2 ? issued - 2 : 0); c < issued; ++c) mbar_wait(&full[c & 1], (c >> 1) & 1);
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------------ MMA issuer
+    bool ok = mbar_wait(&bar_pro, 0);
+    if (ok) {
+      tc_fence_after();
+      const uint32_t id_mu = idesc_f16(kRows, DP, false, false, false);
+      unsigned char *zh = ring, *zl = ring + TB, *wh = ring + 2 * TB, *wl = ring + 3 * TB;
+      for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zh, kk), kdesc(wh, kk), id_mu, kk > 0);
+      for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zl, kk), kdesc(wh, kk), id_mu, 1);
+      for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zh, kk), kdesc(wl, kk), id_mu, 1);
+      mma_commit(&bar_mu);
+      ok = mbar_wait(&bar_A, 0);
+    }
+    const uint32_t id_s = idesc_f16(kRows, kRows, false, false, false);
+    for (int c = 0; ok && c < nch; ++c) {
+      const int s = c & 1, b = c & 1;
+      if (!mbar_wait(&full[s], (c >> 1) & 1)) { ok = false; break; }
+      if (c >= 2 && !mbar_wait(&sfree[b], ((c >> 1) + 1) & 1)) { ok = false; break; }
+      tc_fence_after();
+      unsigned char *bh = ring + s * 2 * TB, *bl = bh + TB;
+      for (int kk = 0; kk < KS; ++kk) mma_ss(tS[b], kdesc(sAH, kk), kdesc(bh, kk), id_s, kk > 0);
+      for (int kk = 0; kk < KS; ++kk) mma_ss(tS[b], kdesc(sAL, kk), kdesc(bh, kk), id_s, 1);
+      for (int kk = 0; kk < KS; ++kk) mma_ss(tS[b], kdesc(sAH, kk), kdesc(bl, kk), id_s, 1);
+      mma_commit(&sfull[b]);
+      mma_commit(&empty[s]);
+    }
+    if (!ok) set_timeout(D);
+    mma_commit(&bar_done);
+    mbar_wait(&bar_done, 0);
+  } else if (warp >= 4) {
+    // ------------------------------------------------------------------ exponentials
+    const int r = threadIdx.x - 128;           // tile row = TMEM lane
+    const uint32_t lane_off = (uint32_t)((warp - 4) * 32) << 16;
+    const int k = t.row0 + r;
+    // beta_i (normalised) for all K child samples, and cb = (beta - |z~|^2 / (2 var)) log2 e
+    float mx = -INFINITY;
+    for (int j = r; j < K; j += 128) {
+      float v = D.u[nd.off_nk + j];
+      for (int c = nd.child_begin; c < nd.child_end; ++c) v += D.lam[D.nodes[D.children[c]].off_nk + j];
+      cb[j] = v;
+      mx = fmaxf(mx, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[warp - 4] = mx;
+    for (int j = r; j < kLdp; j += 128) cv[j] = T.cvec[(long long)t.node * kLdp + j];
+    sync_math();
+    mx = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+    const bool store = (t.row0 == 0);
+    for (int j = r; j < nch * kRows; j += 128) {
+      if (j < K) {
+        const float bb = cb[j] - mx;
+        if (store) D.beta[nd.off_nk + j] = bb;
+        cb[j] = (bb - 0.5f * D.zn[nd.off_nk + j] * iv) * kLog2e;
+      } else {
+        cb[j] = -INFINITY;
+      }
+    }
+    if (store && r == 0) D.nodemax[t.node] = mx;
+    // prologue result: mu~ row, its norm, split into the A operand
+    bool ok = mbar_wait(&bar_mu, 0);
+    float nrm = 0.f;
+    if (ok) {
+      tc_fence_after();
+#pragma unroll 1
+      for (int g = 0; g < DP / 32; ++g) {
+        uint32_t v[32];
+        tmem_ld32(tMU + lane_off + g * 32, v);
+        tmem_wait_ld();
+        float f[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          f[j] = __uint_as_float(v[j]) + cv[g * 32 + j];
+          nrm = fmaf(f[j], f[j], nrm);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) store_split8(sAH, sAL, r, g * 4 + q, f + 8 * q);
+      }
+      if (k < K) D.mun[nd.off_nk + k] = nrm;
+      fence_proxy_async_smem();
+      tc_fence_before();
+    }
+    mbar_arrive(&bar_A);
+    sync_math();  // cb complete before the main loop reads it
+    const float sc = iv * kLog2e;
+    float m = -INFINITY, ssum = 0.f;
+    for (int c = 0; ok && c < nch; ++c) {
+      const int b = c & 1;
+      if (!mbar_wait(&sfull[b], (c >> 1) & 1)) { ok = false; break; }
+      tc_fence_after();
+      const float* cbc = cb + c * kRows;
+#pragma unroll 1
+      for (int g = 0; g < 4; ++g) {
+        uint32_t v[32];
+        tmem_ld32(tS[b] + lane_off + g * 32, v);
+        tmem_wait_ld();
+        float e[32], gm = -INFINITY;
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          const float4 c4 = *reinterpret_cast<const float4*>(cbc + g * 32 + j);
+          e[j] = fmaf(__uint_as_float(v[j]), sc, c4.x);
+          e[j + 1] = fmaf(__uint_as_float(v[j + 1]), sc, c4.y);
+          e[j + 2] = fmaf(__uint_as_float(v[j + 2]), sc, c4.z);
+          e[j + 3] = fmaf(__uint_as_float(v[j + 3]), sc, c4.w);
+          gm = fmaxf(gm, fmaxf(fmaxf(e[j], e[j + 1]), fmaxf(e[j + 2], e[j + 3])));
+        }
+        if (gm > m) {
+          ssum *= exp2f(m - gm);
+          m = gm;
+        }
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; j += 2) {
+          s0 += exp2f(e[j] - m);
+          s1 += exp2f(e[j + 1] - m);
+        }
+        ssum += s0 + s1;
+      }
+      tc_fence_before();
+      mbar_arrive(&sfree[b]);
+    }
+    if (!ok) set_timeout(D);
+    if (ok && k < K) D.lam[nd.off_nk + k] = (m + log2f(ssum)) * kLn2 - 0.5f * nrm * iv;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    tmem_dealloc(tb, 512);
+  }
+}
+
+// =======================================================================================
+// Adjoint edge kernel.
+// =======================================================================================
+template <int DP>
+__global__ void __launch_bounds__(kThreadsTc, 1)
+    k_edge_bwd_tc(Dev D, TcDev T, const Tile* __restrict__ tiles,
+                  const __grid_constant__ CUtensorMap mZH, const __grid_constant__ CUtensorMap mZL,
+                  const __grid_constant__ CUtensorMap mWTH, const __grid_constant__ CUtensorMap mWTL) {
+  constexpr int TB = kRows * DP * 2;
+  constexpr int NB = DP / 64;
+  constexpr int KS = DP / 16;
+  extern __shared__ unsigned char smraw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sAH = sm;            // A' = Z~_i W_i split (K-major)
+  unsigned char* sAL = sm + TB;
+  unsigned char* ring = sm + 2 * TB;  // 2 stages x (hi, lo) of parent sample chunks
+  float* ak = reinterpret_cast<float*>(ring + ring_bytes(DP));
+  // epilogue re-use of the ring / A regions
+  unsigned char* eZH = ring;                 // Z~_i tile hi  (N atoms at +0, +16K)
+  unsigned char* eOnes = ring + TB;          // ones atom: directly after the Z~ atoms
+  unsigned char* eZL = ring + TB + kBox;     // Z~_i tile lo
+  unsigned char* eQZ = ring + 2 * TB + kBox; // q z~ tile (A of M2, 2 atoms)
+  unsigned char* eSV = sm;                   // V tile (A of G, 2 atoms)
+  __shared__ uint64_t bar_pro, bar_mu, bar_A, full[2], empty[2], sfull[2], pready[2], sfree[2];
+  __shared__ uint64_t bar_v, bar_etma, bar_eready, bar_gm;
+  __shared__ uint32_t tbase;
+  __shared__ float cv[kTcMaxD];
+
+  const Tile t = tiles[blockIdx.x];
+  const NodeInfo nd = D.nodes[t.node];
+  const NodeInfo pn = D.nodes[nd.parent];
+  const int K = nd.K, nch = (K + kRows - 1) / kRows, d = nd.d;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float iv = D.inv_var;
+
+  if (warp == 2) tmem_alloc(&tbase, 512);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar_pro, 1);
+    mbar_init(&bar_mu, 1);
+    mbar_init(&bar_A, 128);
+    mbar_init(&bar_v, 1);
+    mbar_init(&bar_etma, 1);
+    mbar_init(&bar_eready, 128);
+    mbar_init(&bar_gm, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+      mbar_init(&sfull[i], 1);
+      mbar_init(&pready[i], 128);
+      mbar_init(&sfree[i], 1);
+    }
+    fence_barrier_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tb = tbase;
+  const uint32_t tS[2] = {tb, tb + 128}, tV = tb + 256, tG = tb, tM2 = tb + 128;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------------ TMA producer
+    prefetch_tmap(&mZH);
+    prefetch_tmap(&mZL);
+    const int slot = slot_of(D, nd, t.node);
+    const int own = (int)(nd.off_nk + t.row0);
+    mbar_arrive_expect_tx(&bar_pro, 4 * TB);
+    for (int b = 0; b < NB; ++b) {
+      tma_load_2d(ring + b * kBox, &mZH, &bar_pro, b * 64, own);
+      tma_load_2d(ring + TB + b * kBox, &mZL, &bar_pro, b * 64, own);
+      tma_load_2d(ring + 2 * TB + b * kBox, &mWTH, &bar_pro, b * 64, slot * kLdp);
+      tma_load_2d(ring + 3 * TB + b * kBox, &mWTL, &bar_pro, b * 64, slot * kLdp);
+    }
+    bool ok = mbar_wait(&bar_mu, 0);
+    int issued = 0;
+    for (int c = 0; ok && c < nch; ++c) {
+      const int s = c & 1;
+      if (c >= 2 && !mbar_wait(&empty[s], ((c >> 1) + 1) & 1)) { ok = false; break; }
+      unsigned char* st = ring + s * 2 * TB;
+      mbar_arrive_expect_tx(&full[s], 2 * TB);
+      const int row = (int)(pn.off_nk + c * kRows);
+      for (int b = 0; b < NB; ++b) {
+        tma_load_2d(st + b * kBox, &mZH, &full[s], b * 64, row);
+        tma_load_2d(st + TB + b * kBox, &mZL, &full[s], b * 64, row);
+      }
+      issued = c + 1;
+    }
+    for (int c = (issued > 2 ? issued - 2 : 0); c < issued; ++c) mbar_wait(&full[c & 1], (c >> 1) & 1);
+    // epilogue operands: this CTA's own Z~ tile again
+    if (ok) ok = mbar_wait(&bar_v, 0);
+    if (ok) {
+      mbar_arrive_expect_tx(&bar_etma, 2 * TB);
+      for (int b = 0; b < NB; ++b) {
+        tma_load_2d(eZH + b * kBox, &mZH, &bar_etma, b * 64, own);
+        tma_load_2d(eZL + b * kBox, &mZL, &bar_etma, b * 64, own);
+      }
+      mbar_wait(&bar_etma, 0);
+    }
+    if (!ok) set_timeout(D);
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------------ MMA issuer
+    bool ok = mbar_wait(&bar_pro, 0);
+    if (ok) {
+      tc_fence_after();
+      const uint32_t id_a = idesc_f16(kRows, DP, false, false, false);
+      unsigned char *zh = ring, *zl = ring + TB, *wh = ring + 2 * TB, *wl = ring + 3 * TB;
+      for (int kk = 0; kk < KS; ++kk) mma_ss(tS[0], kdesc(zh, kk), kdesc(wh, kk), id_a, kk > 0);
+      for (int kk = 0; kk < KS; ++kk) mma_ss(tS[0], kdesc(zl, kk), kdesc(wh, kk), id_a, 1);
+      for (int kk = 0; kk < KS; ++kk) mma_ss(tS[0], kdesc(zh, kk), kdesc(wl, kk), id_a, 1);
+      mma_commit(&bar_mu);
+      ok = mbar_wait(&bar_A, 0);
+    }
+    const uint32_t id_s = idesc_f16(kRows, kRows, false, false, false);
+    const uint32_t id_v = idesc_f16(kRows, DP, false, false, true);
+    for (int c = 0; ok && c <= nch; ++c) {
+      if (c < nch) {
+        const int s = c & 1, b = c & 1;
+        if (!mbar_wait(&full[s], (c >> 1) & 1)) { ok = false; break; }
+        if (c >= 2 && !mbar_wait(&sfree[b], ((c >> 1) + 1) & 1)) { ok = false; break; }
+        tc_fence_after();
+        unsigned char *bh = ring + s * 2 * TB, *bl = bh + TB;
+        for (int kk = 0; kk < KS; ++kk) mma_ss(tS[b], kdesc(sAH, kk), kdesc(bh, kk), id_s, kk > 0);
+        for (int kk = 0; kk < KS; ++kk) mma_ss(tS[b], kdesc(sAL, kk), kdesc(bh, kk), id_s, 1);
+        for (int kk = 0; kk < KS; ++kk) mma_ss(tS[b], kdesc(sAH, kk), kdesc(bl, kk), id_s, 1);
+        mma_commit(&sfull[b]);
+      }
+      if (c >= 1) {
+        const int cp = c - 1, s = cp & 1, b = cp & 1;
+        if (!mbar_wait(&pready[b], (cp >> 1) & 1)) { ok = false; break; }
+        tc_fence_after();
+        unsigned char* bh = ring + s * 2 * TB;
+        // V[k'][:] += sum_k P[k'][k] z~_p^k   (P: fp16 in the S buffer, 2 per column)
+        for (int kk = 0; kk < kRows / 16; ++kk)
+          mma_ts(tV, tS[b] + kk * 8, mndesc(bh, kk), id_v, (cp > 0 || kk > 0) ? 1u : 0u);
+        mma_commit(&empty[s]);
+        mma_commit(&sfree[b]);
+      }
+    }
+    mma_commit(&bar_v);
+    if (ok) ok = mbar_wait(&bar_v, 0);
+    if (ok) ok = mbar_wait(&bar_etma, 0) && mbar_wait(&bar_eready, 0);
+    if (ok) {
+      tc_fence_after();
+      // G[a][b]  = sum_k' V[k'][a] z~[k'][b];   M2[a][b] = sum_k' q z~[k'][a] [z~ | 1][k'][b]
+      const uint32_t id_g = idesc_f16(kRows, DP, false, true, true);
+      const uint32_t id_m = idesc_f16(kRows, DP + 16, false, true, true);
+      for (int kk = 0; kk < kRows / 16; ++kk) mma_ss(tG, mndesc(eSV, kk), mndesc(eZH, kk), id_g, kk > 0);
+      for (int kk = 0; kk < kRows / 16; ++kk) mma_ss(tG, mndesc(eSV, kk), mndesc(eZL, kk), id_g, 1);
+      for (int kk = 0; kk < kRows / 16; ++kk) mma_ss(tM2, mndesc(eQZ, kk), mndesc(eZH, kk), id_m, kk > 0);
+      mma_commit(&bar_gm);
+      mbar_wait(&bar_gm, 0);
+    } else {
+      set_timeout(D);
+      mma_commit(&bar_gm);
+      mbar_wait(&bar_gm, 0);
+    }
+  } else if (warp >= 4) {
+    // ------------------------------------------------------------------ exponentials
+    const int r = threadIdx.x - 128;
+    const uint32_t lane_off = (uint32_t)((warp - 4) * 32) << 16;
+    const int kq = t.row0 + r;  // child sample owned by this thread
+    const bool valid = kq < K;
+    // column (parent sample) terms: (log q_p - lam_i - |mu~|^2 / (2 var)) log2 e
+    for (int j = r; j < nch * kRows; j += 128) {
+      float a = -INFINITY;
+      if (j < K)
+        a = (logf(D.q[pn.off_nk + j]) - D.lam[nd.off_nk + j] - 0.5f * D.mun[nd.off_nk + j] * iv) * kLog2e;
+      ak[j] = a;
+    }
+    for (int j = r; j < kLdp; j += 128) cv[j] = T.cvec[(long long)t.node * kLdp + j];
+    sync_math();
+    // row term: (beta_i - |z~|^2 / (2 var) + z~ . c_i / var) log2 e
+    float crow = -INFINITY;
+    if (valid) {
+      const float* e = D.eps + nd.off_nkd + (long long)kq * d;
+      float zc = 0.f;
+      for (int j = 0; j < d; ++j) zc = fmaf(expf(D.q_logstd[nd.off_q + j]) * e[j], cv[j], zc);
+      crow = (D.beta[nd.off_nk + kq] - 0.5f * D.zn[nd.off_nk + kq] * iv + zc * iv) * kLog2e;
+    }
+    // prologue result A' = Z~_i W_i -> split A operand
+    bool ok = mbar_wait(&bar_mu, 0);
+    if (ok) {
+      tc_fence_after();
+#pragma unroll 1
+      for (int g = 0; g < DP / 32; ++g) {
+        uint32_t v[32];
+        tmem_ld32(tS[0] + lane_off + g * 32, v);
+        tmem_wait_ld();
+        float f[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v[j]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) store_split8(sAH, sAL, r, g * 4 + q, f + 8 * q);
+      }
+      fence_proxy_async_smem();
+      tc_fence_before();
+    }
+    mbar_arrive(&bar_A);
+    const float sc = iv * kLog2e;
+    float qacc = 0.f;
+    for (int c = 0; ok && c < nch; ++c) {
+      const int b = c & 1;
+      if (!mbar_wait(&sfull[b], (c >> 1) & 1)) { ok = false; break; }
+      tc_fence_after();
+      const float* akc = ak + c * kRows;
+#pragma unroll 1
+      for (int g = 0; g < 4; ++g) {
+        uint32_t v[32];
+        tmem_ld32(tS[b] + lane_off + g * 32, v);
+        tmem_wait_ld();
+        uint32_t pk[16];
+        float s0 = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          const float4 a4 = *reinterpret_cast<const float4*>(akc + g * 32 + j);
+          const float p0 = exp2f(fmaf(__uint_as_float(v[j]), sc, crow + a4.x));
+          const float p1 = exp2f(fmaf(__uint_as_float(v[j + 1]), sc, crow + a4.y));
+          const float p2 = exp2f(fmaf(__uint_as_float(v[j + 2]), sc, crow + a4.z));
+          const float p3 = exp2f(fmaf(__uint_as_float(v[j + 3]), sc, crow + a4.w));
+          s0 += (p0 + p1) + (p2 + p3);
+          pk[j / 2] = pack_half2(p0, p1);
+          pk[j / 2 + 1] = pack_half2(p2, p3);
+        }
+        qacc += s0;
+        // P columns 16g .. 16g+15 of this buffer (the S values there were read already)
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%"
+            "13,%14,%15,%16};" ::"r"(tS[b] + lane_off + g * 16),
+            "r"(pk[0]), "r"(pk[1]), "r"(pk[2]), "r"(pk[3]), "r"(pk[4]), "r"(pk[5]), "r"(pk[6]),
+            "r"(pk[7]), "r"(pk[8]), "r"(pk[9]), "r"(pk[10]), "r"(pk[11]), "r"(pk[12]), "r"(pk[13]),
+            "r"(pk[14]), "r"(pk[15])
+            : "memory");
+      }
+      tmem_wait_st();
+      tc_fence_before();
+      mbar_arrive(&pready[b]);
+    }
+    if (ok && valid) D.q[nd.off_nk + kq] = qacc;
+    // epilogue: V row -> fp16 A tile of G; q z~ row -> A tile of M2; ones atom row
+    if (ok) ok = mbar_wait(&bar_v, 0);
+    if (ok) {
+      tc_fence_after();
+#pragma unroll 1
+      for (int g = 0; g < kRows / 32; ++g) {
+        float f[32];
+        if (g < DP / 32) {
+          uint32_t v[32];
+          tmem_ld32(tV + lane_off + g * 32, v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) f[j] = 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) store_half8(eSV, r, g * 4 + q, f + 8 * q);
+      }
+      ok = mbar_wait(&bar_etma, 0);
+    }
+    if (ok) {
+      const float qv = valid ? qacc : 0.f;
+#pragma unroll 1
+      for (int ch = 0; ch < kRows / 8; ++ch) {
+        float f[8];
+        if (ch < DP / 8) {
+          float h[8], l[8];
+          load_half8(eZH, r, ch, h);
+          load_half8(eZL, r, ch, l);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) f[j] = qv * (h[j] + l[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) f[j] = 0.f;
+        }
+        store_half8(eQZ, r, ch, f);
+      }
+      // ones atom row r: element 0 = 1, the rest 0
+      float o8[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      store_half8(eOnes, r, 0, o8);
+      for (int ch = 1; ch < 8; ++ch) store_half8(eOnes, r, ch, z8);
+      fence_proxy_async_smem();
+      tc_fence_before();
+    }
+    mbar_arrive(&bar_eready);
+    if (ok) ok = mbar_wait(&bar_gm, 0);
+    if (ok) {
+      tc_fence_after();
+      const int a = r;  // TMEM lane = output row a (latent dimension of the parent / node)
+      const bool arow = a < d;
+      float* Gi = T.G + (long long)t.node * kLdp * kLdp + (long long)a * kLdp;
+      float* Mi = T.M2 + (long long)t.node * kLdp * kLdp + (long long)a * kLdp;
+#pragma unroll 1
+      for (int g = 0; g < DP / 32; ++g) {
+        uint32_t v[32];
+        tmem_ld32(tG + lane_off + g * 32, v);
+        tmem_wait_ld();
+        if (arow)
+          for (int j = 0; j < 32; ++j)
+            if (g * 32 + j < d) atomicAdd(Gi + g * 32 + j, __uint_as_float(v[j]));
+        tmem_ld32(tM2 + lane_off + g * 32, v);
+        tmem_wait_ld();
+        if (arow)
+          for (int j = 0; j < 32; ++j)
+            if (g * 32 + j < d) atomicAdd(Mi + g * 32 + j, __uint_as_float(v[j]));
+      }
+      uint32_t v[32];
+      tmem_ld32(tM2 + lane_off + DP, v);  // column DP: sum_k' q z~[k'][a]
+      tmem_wait_ld();
+      if (arow) atomicAdd(T.zbar + (long long)t.node * kLdp + a, __uint_as_float(v[0]));
+    }
+    if (!ok) set_timeout(D);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    tmem_dealloc(tb, 512);
+  }
+}
+
+// =======================================================================================
+// Root moments: zbar_0 = sum_k q_0 z~_0, M2_0 = sum_k q_0 z~_0 z~_0^T (FP32 samples).
+// Grid: (instance, 64-row tile, 64-col tile).
+// =======================================================================================
+__global__ void __launch_bounds__(kThreads) k_root_moments(Dev D, TcDev T) {
+  __shared__ TileSmem sm;
+  __shared__ float qz[kTile * kLd];
+  const InstInfo in = D.insts[blockIdx.x];
+  const NodeInfo nd = D.nodes[in.node0];
+  const int d = nd.d, K = nd.K;
+  const int a0 = blockIdx.y * kTile, b0 = blockIdx.z * kTile;
+  if (a0 >= d || b0 >= d) return;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  float acc[4][4];
+  zero_acc(acc);
+  float zs = 0.f;
+  for (int k0 = 0; k0 < K; k0 += kTile) {
+    const int rows = min(kTile, K - k0);
+    // qz[l = k][m = a] = q[k] z~[k][a0 + m]
+    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+      const int l = e >> 6, m = e & 63;
+      float v = 0.f;
+      if (l < rows && a0 + m < d) v = D.q[nd.off_nk + k0 + l] * D.zt[nd.off_nkd + (long long)(k0 + l) * d + a0 + m];
+      qz[l * kLd + m] = v;
+    }
+    __syncthreads();
+    if (b0 == 0 && threadIdx.x < kTile)
+      for (int l = 0; l < rows; ++l) zs += qz[l * kLd + threadIdx.x];
+    for (int l0 = 0; l0 < rows; l0 += kSlice) {
+      load_slice<false>(sm.b, D.zt + nd.off_nkd + (long long)k0 * d + b0, d, min(kTile, d - b0), l0, rows);
+      __syncthreads();
+      slice_fma(acc, qz + l0 * kLd, sm.b);
+      __syncthreads();
+    }
+  }
+  float* M = T.M2 + (long long)in.node0 * kLdp * kLdp;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int a = a0 + ty * 4 + i, b = b0 + tx * 4 + j;
+      if (a < d && b < d) M[(long long)a * kLdp + b] = acc[i][j];
+    }
+  if (b0 == 0 && threadIdx.x < kTile && a0 + threadIdx.x < d)
+    T.zbar[(long long)in.node0 * kLdp + a0 + threadIdx.x] = zs;
+}
+
+// =======================================================================================
+// Gradient assembly from the moments.  For the edge c (parent p):
+//   db'_c = (zbar_c - W_c zbar_p - c_c) / var                      (= sum_k dmu_c[k])
+//   D_c   = (G_c^T - W_c M2_p - c_c zbar_p^T) / var                (= sum_k dmu_c[k] z~_p^k^T)
+//   dW_c  = grad_out (D_c + db'_c m_p^T),  dbias_c = grad_out db'_c
+// and the edge's parts of the proposal-gradient sums of its two nodes:
+//   child c  : sum_k' g = -db'_c,  sum_k' g z~ = (diag(W_c G_c) + c_c zbar_c - diag(M2_c)) / var
+//   parent p : sum_k g = W_c^T db'_c,  sum_k g z~ = diag(W_c^T D_c)
+// One CTA per non-root node, 128 threads: thread a first forms db'_c[a] and the child-side
+// sums; then thread b walks column b of D_c (so the parent-side sums need no cross-thread
+// reduction).
+// =======================================================================================
+__global__ void __launch_bounds__(128) k_asm_edge(Dev D, TcDev T, const int* __restrict__ nonroot) {
+  __shared__ float zp[kTcMaxD], dbs[kTcMaxD], cs[kTcMaxD];
+  const int g = nonroot[blockIdx.x];
+  const NodeInfo nd = D.nodes[g];
+  const NodeInfo pn = D.nodes[nd.parent];
+  const int d = nd.d;
+  const float iv = D.inv_var;
+  const float go = D.grad_out ? (float)D.grad_out[nd.b] : 1.f;
+  const float* W = D.W + nd.off_W;
+  const float* Gc = T.G + (long long)g * kLdp * kLdp;
+  const float* M2p = T.M2 + (long long)nd.parent * kLdp * kLdp;
+  const float* M2c = T.M2 + (long long)g * kLdp * kLdp;
+  const float* zbc = T.zbar + (long long)g * kLdp;
+  const float* cc = T.cvec + (long long)g * kLdp;
+  const int a = threadIdx.x;
+  if (a < d) {
+    zp[a] = T.zbar[(long long)nd.parent * kLdp + a];
+    cs[a] = cc[a];
+  }
+  __syncthreads();
+  if (a < d) {
+    float s = 0.f, wg = 0.f;
+    for (int j = 0; j < d; ++j) {
+      s = fmaf(W[(long long)a * d + j], zp[j], s);
+      wg = fmaf(W[(long long)a * d + j], Gc[(long long)j * kLdp + a], wg);
+    }
+    const float db = (zbc[a] - s - cs[a]) * iv;
+    dbs[a] = db;
+    T.sgC[(long long)g * kLdp + a] = -db;
+    T.tgC[(long long)g * kLdp + a] = (wg + cs[a] * zbc[a] - M2c[(long long)a * kLdp + a]) * iv;
+    if (D.shared) { if (D.pbias) D.pbias[nd.off_q + a] = go * db; }
+    else if (D.dbias) D.dbias[nd.off_bias + a] = go * db;
+  }
+  __syncthreads();
+  const int b = threadIdx.x;
+  if (b >= d) return;
+  const float mpb = D.q_mean[pn.off_q + b];
+  float sg = 0.f, tg = 0.f;
+  for (int r = 0; r < d; ++r) {
+    const float* Wr = W + (long long)r * d;
+    float s = 0.f;
+    for (int j = 0; j < d; ++j) s = fmaf(Wr[j], M2p[(long long)j * kLdp + b], s);
+    const float Drb = (Gc[(long long)b * kLdp + r] - s - cs[r] * zp[b]) * iv;
+    tg = fmaf(Wr[b], Drb, tg);
+    sg = fmaf(Wr[b], dbs[r], sg);
+    const float v = go * (Drb + dbs[r] * mpb);
+    if (D.shared) { if (D.pW) D.pW[nd.off_pW + (long long)r * d + b] = v; }
+    else if (D.dW) D.dW[nd.off_W + (long long)r * d + b] = v;
+  }
+  T.sgP[(long long)g * kLdp + b] = sg;
+  T.tgP[(long long)g * kLdp + b] = tg;
+}
+
+// Node sums and outputs: dm_i = grad_out * Sg,  dlogs_i = grad_out * (sum_k q_i + Tg), with
+//   Sg, Tg = [edge as child] + sum over child edges + [root prior] + [leaf observation]
+//   root : Sg -= (zbar + m_0 - bias_0)/var,  Tg -= (diag M2 + (m_0 - bias_0) zbar)/var,
+//          dbias_0 = grad_out (zbar + m_0 - bias_0)/var
+//   leaf : Sg += C^T (x~ - C zbar)/obs_var,  Tg += ((C^T x~) zbar - diag(C^T C M2))/obs_var
+__global__ void __launch_bounds__(128) k_asm_node(Dev D, TcDev T) {
+  __shared__ float xs[kMaxD];
+  __shared__ float zb[kTcMaxD], ctx[kTcMaxD];
+  __shared__ float qred[4];
+  const int g = blockIdx.x;
+  const NodeInfo nd = D.nodes[g];
+  const int d = nd.d, K = nd.K;
+  const float go = D.grad_out ? (float)D.grad_out[nd.b] : 1.f;
+  const float* M2 = T.M2 + (long long)g * kLdp * kLdp;
+  const int j = threadIdx.x;
+  float qs = 0.f;
+  for (int k = j; k < K; k += blockDim.x) qs += D.q[nd.off_nk + k];
+  for (int o = 16; o > 0; o >>= 1) qs += __shfl_xor_sync(0xffffffffu, qs, o);
+  if ((j & 31) == 0) qred[j >> 5] = qs;
+  if (j < d) zb[j] = T.zbar[(long long)g * kLdp + j];
+  const bool leaf = nd.leaf_slot >= 0, root = nd.parent < 0;
+  if (leaf) {
+    for (int o = j; o < nd.obs; o += blockDim.x) {
+      const float* c = D.C + nd.off_C + (long long)o * d;
+      float s = 0.f;
+      for (int i = 0; i < d; ++i) s = fmaf(c[i], D.q_mean[nd.off_q + i], s);
+      xs[o] = D.x[nd.off_x + o] - s;
+    }
+  }
+  __syncthreads();
+  const float qtot = qred[0] + qred[1] + qred[2] + qred[3];
+  if (leaf && j < d) {
+    float s = 0.f;
+    for (int o = 0; o < nd.obs; ++o) s = fmaf(D.C[nd.off_C + (long long)o * d + j], xs[o], s);
+    ctx[j] = s;
+  }
+  __syncthreads();
+  if (j >= d) return;
+  float Sg = 0.f, Tg = 0.f;
+  if (!root) {
+    Sg += T.sgC[(long long)g * kLdp + j];
+    Tg += T.tgC[(long long)g * kLdp + j];
+  }
+  for (int ci = nd.child_begin; ci < nd.child_end; ++ci) {
+    const int c = D.children[ci];
+    Sg += T.sgP[(long long)c * kLdp + j];
+    Tg += T.tgP[(long long)c * kLdp + j];
+  }
+  if (root) {
+    const float off = D.q_mean[nd.off_q + j] - D.bias[nd.off_bias + j];
+    const float t = zb[j] + off;
+    Sg -= t * D.inv_var;
+    Tg -= (M2[(long long)j * kLdp + j] + off * zb[j]) * D.inv_var;
+    const float db = go * t * D.inv_var;
+    if (D.shared) { if (D.pbias) D.pbias[nd.off_q + j] = db; }
+    else if (D.dbias) D.dbias[nd.off_bias + j] = db;
+    if (!D.shared && D.dW)
+      for (int c = 0; c < d; ++c) D.dW[nd.off_W + (long long)j * d + c] = 0.f;
+  }
+  if (leaf) {
+    // (C^T C) row j, then C^T C zbar and diag(C^T C M2)
+    const float* C = D.C + nd.off_C;
+    float czb = 0.f, dg = 0.f;
+    for (int a = 0; a < d; ++a) {
+      float ctc = 0.f;
+      for (int o = 0; o < nd.obs; ++o) ctc = fmaf(C[(long long)o * d + j], C[(long long)o * d + a], ctc);
+      czb = fmaf(ctc, zb[a], czb);
+      dg = fmaf(ctc, M2[(long long)a * kLdp + j], dg);
+    }
+    Sg += (ctx[j] - czb) * D.inv_obs_var;
+    Tg += (ctx[j] * zb[j] - dg) * D.inv_obs_var;
+  }
+  if (D.dq_mean) D.dq_mean[nd.off_q + j] = go * Sg;
+  if (D.dq_logstd) D.dq_logstd[nd.off_q + j] = go * (qtot + Tg);
+}
+
+// dC = grad_out / obs_var * sum_leaves [ x~ (zbar + m)^T - C (M2 + zbar m^T) ]
+// Grid: (instance, 64-row tile of observation dims); thread per (o, c) element loop.
+__global__ void __launch_bounds__(256) k_asm_dC(Dev D, TcDev T) {
+  const InstInfo in = D.insts[blockIdx.x];
+  const int d = in.d, obs = in.obs;
+  const float go = D.grad_out ? (float)D.grad_out[blockIdx.x] : 1.f;
+  const int o0 = blockIdx.y * 64;
+  if (o0 >= obs) return;
+  const int rows = min(64, obs - o0);
+  for (int e = threadIdx.x; e < rows * d; e += blockDim.x) {
+    const int o = o0 + e / d, c = e % d;
+    float acc = 0.f;
+    for (int gi = in.node0; gi < in.node0 + in.n; ++gi) {
+      const NodeInfo nd = D.nodes[gi];
+      if (nd.leaf_slot < 0) continue;
+      const float* C = D.C + nd.off_C;
+      const float* M2 = T.M2 + (long long)gi * kLdp * kLdp;
+      const float* zb = T.zbar + (long long)gi * kLdp;
+      const float* m = D.q_mean + nd.off_q;
+      float cm = 0.f, cmz = 0.f, czb = 0.f;
+      for (int a = 0; a < d; ++a) {
+        const float ca = C[(long long)o * d + a];
+        cm = fmaf(ca, m[a], cm);
+        cmz = fmaf(ca, M2[(long long)a * kLdp + c], cmz);
+        czb = fmaf(ca, zb[a], czb);
+      }
+      const float xt_o = D.x[nd.off_x + o] - cm;
+      acc += xt_o * (zb[c] + m[c]) - (cmz + czb * m[c]);
+    }
+    const float v = go * acc * D.inv_obs_var;
+    if (D.shared) { if (D.pC) D.pC[in.off_pC + (long long)o * d + c] = v; }
+    else if (D.dC) D.dC[in.off_C + (long long)o * d + c] = v;
+  }
+}
+
+// =======================================================================================
+// host side
+// =======================================================================================
+namespace {
+typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                             const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                             CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                             CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = (EncodeFn)p;
+  }
+  return fn;
+}
+
+// [rows][128] fp16 array, box 64 columns x 128 rows, 128-byte swizzle.
+bool make_map(CUtensorMap* m, void* ptr, long long rows) {
+  EncodeFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kLdp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kLdp * 2};
+  cuuint32_t box[2] = {64, (cuuint32_t)kRows};
+  cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ptr, dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int DP>
+size_t fwd_smem(int maxK) {
+  const size_t need = 1024 + 2 * (size_t)(kRows * DP * 2) + ring_bytes(DP) +
+                      4 * (size_t)(((maxK + kRows - 1) / kRows) * kRows);
+  // at least half of the SM's shared memory: one CTA per SM, so the 512-column TMEM
+  // allocation never waits on a co-resident CTA
+  return need > 120 * 1024 ? need : 120 * 1024;
+}
+}  // namespace
+
+tmc_status supported(const std::vector<NodeInfo>& nodes, int precision) {
+  if (precision != TMC_PREC_FP16_TC) return TMC_ERR_UNSUPPORTED;  // split-fp16 kernels only
+  for (const NodeInfo& nd : nodes)
+    if (nd.d > kTcMaxD || nd.K > kTcMaxK) return TMC_ERR_UNSUPPORTED;
+  return TMC_OK;
+}
+
+void workspace_layout(TcWork& w, const std::vector<NodeInfo>& nodes, long long nk, long long,
+                      std::vector<TcSub>& subs) {
+  w.num_nodes = (int)nodes.size();
+  int slots = 0;
+  for (const NodeInfo& nd : nodes) slots = std::max(slots, (w.t.shared ? nd.i : (int)(&nd - nodes.data())) + 1);
+  w.num_slots = slots;
+  w.rows = nk + kRows;  // one spare tile of rows so a ragged last tile stays inside the map
+  const size_t pk = (size_t)w.rows * kLdp * sizeof(__half);
+  const size_t pw = (size_t)slots * kLdp * kLdp * sizeof(__half);
+  const size_t nv = (size_t)w.num_nodes * kLdp * sizeof(float);
+  const size_t nm = (size_t)w.num_nodes * kLdp * kLdp * sizeof(float);
+  subs.push_back({(void**)&w.t.ZH, pk});
+  subs.push_back({(void**)&w.t.ZL, pk});
+  subs.push_back({(void**)&w.t.WH, pw});
+  subs.push_back({(void**)&w.t.WL, pw});
+  subs.push_back({(void**)&w.t.WTH, pw});
+  subs.push_back({(void**)&w.t.WTL, pw});
+  subs.push_back({(void**)&w.t.cvec, nv});
+  subs.push_back({(void**)&w.t.G, nm});
+  subs.push_back({(void**)&w.t.M2, nm});
+  subs.push_back({(void**)&w.t.zbar, nv});
+  subs.push_back({(void**)&w.t.sgC, nv});
+  subs.push_back({(void**)&w.t.tgC, nv});
+  subs.push_back({(void**)&w.t.sgP, nv});
+  subs.push_back({(void**)&w.t.tgP, nv});
+}
+
+tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vector<Tile>&, int maxK,
+                   int) {
+  w.maxK = maxK;
+  if (!make_map(&w.mZH, w.t.ZH, w.rows) || !make_map(&w.mZL, w.t.ZL, w.rows) ||
+      !make_map(&w.mWH, w.t.WH, (long long)w.num_slots * kLdp) ||
+      !make_map(&w.mWL, w.t.WL, (long long)w.num_slots * kLdp) ||
+      !make_map(&w.mWTH, w.t.WTH, (long long)w.num_slots * kLdp) ||
+      !make_map(&w.mWTL, w.t.WTL, (long long)w.num_slots * kLdp))
+    return TMC_ERR_CUDA;
+  int maxlevel = 0;
+  for (const NodeInfo& nd : nodes) maxlevel = std::max(maxlevel, nd.level);
+  w.maxlevel = maxlevel;
+  w.tiles.clear();
+  for (int c = 0; c < 2; ++c) {
+    w.lv_b[c].assign(maxlevel + 1, 0);
+    w.lv_e[c].assign(maxlevel + 1, 0);
+  }
+  for (int L = 1; L <= maxlevel; ++L)
+    for (int c = 0; c < 2; ++c) {
+      w.lv_b[c][L] = (int)w.tiles.size();
+      for (int g = 0; g < (int)nodes.size(); ++g) {
+        const NodeInfo& nd = nodes[g];
+        if (nd.level != L || ((nd.d > 64) ? 1 : 0) != c) continue;
+        for (int r = 0; r < nd.K; r += kRows) w.tiles.push_back(Tile{g, r});
+      }
+      w.lv_e[c][L] = (int)w.tiles.size();
+    }
+  w.nonroot.clear();
+  for (int g = 0; g < (int)nodes.size(); ++g)
+    if (nodes[g].parent >= 0) w.nonroot.push_back(g);
+  if (!w.tiles.empty()) {
+    if (cudaMalloc(&w.d_tiles, sizeof(Tile) * w.tiles.size()) != cudaSuccess) return TMC_ERR_NOMEM;
+    cudaMemcpy(w.d_tiles, w.tiles.data(), sizeof(Tile) * w.tiles.size(), cudaMemcpyHostToDevice);
+  }
+  if (!w.nonroot.empty()) {
+    if (cudaMalloc(&w.d_nonroot, sizeof(int) * w.nonroot.size()) != cudaSuccess) return TMC_ERR_NOMEM;
+    cudaMemcpy(w.d_nonroot, w.nonroot.data(), sizeof(int) * w.nonroot.size(), cudaMemcpyHostToDevice);
+  }
+  // zero the packed operand arrays once: padding columns / spare rows are read by the MMAs
+  cudaMemset(w.t.ZH, 0, (size_t)w.rows * kLdp * sizeof(__half));
+  cudaMemset(w.t.ZL, 0, (size_t)w.rows * kLdp * sizeof(__half));
+  const size_t f64 = fwd_smem<64>(maxK), f128 = fwd_smem<128>(maxK);
+  cudaFuncSetAttribute(k_edge_fwd_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f64);
+  cudaFuncSetAttribute(k_edge_fwd_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f128);
+  cudaFuncSetAttribute(k_edge_bwd_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f64);
+  cudaFuncSetAttribute(k_edge_bwd_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f128);
+  return cudaGetLastError() == cudaSuccess ? TMC_OK : TMC_ERR_CUDA;
+}
+
+void release(TcWork& w) {
+  cudaFree(w.d_tiles);
+  cudaFree(w.d_nonroot);
+  w.d_tiles = nullptr;
+  w.d_nonroot = nullptr;
+}
+
+void launch_sample(TcWork& w, const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s) {
+  if (ntiles) k_sample_tc<<<ntiles, 256, 2 * kTcMaxD * sizeof(float), s>>>(D, w.t, tiles);
+}
+
+void launch_pack(TcWork& w, const Dev& D, cudaStream_t s) {
+  const int n = (int)w.nonroot.size();
+  if (!n) return;
+  k_pack_w<<<n, 256, 0, s>>>(D, w.t, w.d_nonroot);
+  k_pack_c<<<n, 128, 0, s>>>(D, w.t, w.d_nonroot);
+}
+
+void launch_edge_fwd(TcWork& w, const Dev& D, int L, cudaStream_t s) {
+  for (int c = 0; c < 2; ++c) {
+    const int b = w.lv_b[c][L], n = w.lv_e[c][L] - b;
+    if (!n) continue;
+    if (c == 0)
+      k_edge_fwd_tc<64><<<n, kThreadsTc, fwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, w.mZH, w.mZL, w.mWH, w.mWL);
+    else
+      k_edge_fwd_tc<128><<<n, kThreadsTc, fwd_smem<128>(w.maxK), s>>>(D, w.t, w.d_tiles + b, w.mZH, w.mZL, w.mWH, w.mWL);
+  }
+}
+
+void launch_edge_bwd(TcWork& w, const Dev& D, int L, cudaStream_t s) {
+  if (L == 1) {
+    cudaMemsetAsync(w.t.G, 0, (size_t)w.num_nodes * kLdp * kLdp * sizeof(float), s);
+    cudaMemsetAsync(w.t.M2, 0, (size_t)w.num_nodes * kLdp * kLdp * sizeof(float), s);
+    cudaMemsetAsync(w.t.zbar, 0, (size_t)w.num_nodes * kLdp * sizeof(float), s);
+  }
+  for (int c = 0; c < 2; ++c) {
+    const int b = w.lv_b[c][L], n = w.lv_e[c][L] - b;
+    if (!n) continue;
+    if (c == 0)
+      k_edge_bwd_tc<64><<<n, kThreadsTc, fwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, w.mZH, w.mZL, w.mWTH, w.mWTL);
+    else
+      k_edge_bwd_tc<128><<<n, kThreadsTc, fwd_smem<128>(w.maxK), s>>>(D, w.t, w.d_tiles + b, w.mZH, w.mZL, w.mWTH, w.mWTL);
+  }
+}
+
+void launch_unpack_grads(TcWork& w, const Dev& D, cudaStream_t s) {
+  k_root_moments<<<dim3(D.num_inst, 2, 2), kThreads, 0, s>>>(D, w.t);
+  if (!w.nonroot.empty()) k_asm_edge<<<(int)w.nonroot.size(), 128, 0, s>>>(D, w.t, w.d_nonroot);
+  k_asm_node<<<D.num_nodes, 128, 0, s>>>(D, w.t);
+  k_asm_dC<<<dim3(D.num_inst, (kMaxD + 63) / 64), 256, 0, s>>>(D, w.t);
+}
 
 }  // namespace tc
 }  // namespace tmc

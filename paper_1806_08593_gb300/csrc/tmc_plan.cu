@@ -271,6 +271,8 @@ tmc_status alloc_device(tmc_plan p) {
       {(void**)&pC, sizeof(float) * nC},
   };
   std::vector<tc::TcSub> tsubs;
+  p->tcw.t.shared = p->shared;
+  p->tcw.precision = p->precision;
   if (p->precision != TMC_PREC_FP32) tc::workspace_layout(p->tcw, p->nodes, nk, nkd, tsubs);
   size_t total = 0;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -378,10 +380,15 @@ tmc_status tmc_log_marginal(tmc_plan p, const tmc_inputs* in, double* log_phat, 
   const Tile* T = p->d_tiles;
   const bool tc_path = p->precision != TMC_PREC_FP32;
   TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_node_const(D, s); }));
-  TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_sample(D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
+  if (tc_path)
+    TRY(timed(p, TMC_KC_SAMPLE, s, [&] { tc::launch_sample(p->tcw, D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
+  else
+    TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_sample(D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
   TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_obs_fwd(D, T + p->t_leaf_b, p->t_leaf_e - p->t_leaf_b, s); }));
-  TRY(timed(p, TMC_KC_PROJECT, s, [&] { launch_project(D, T + p->t_proj_b, p->t_proj_e - p->t_proj_b, s); }));
-  if (tc_path) TRY(timed(p, TMC_KC_PROJECT, s, [&] { tc::launch_pack(p->tcw, D, s); }));
+  if (tc_path)  // the conditional means are formed inside the edge kernels
+    TRY(timed(p, TMC_KC_PROJECT, s, [&] { tc::launch_pack(p->tcw, D, s); }));
+  else
+    TRY(timed(p, TMC_KC_PROJECT, s, [&] { launch_project(D, T + p->t_proj_b, p->t_proj_e - p->t_proj_b, s); }));
   for (int L = p->maxlevel; L >= 1; --L) {
     const int b = p->t_level_b[L], e = p->t_level_e[L];
     if (tc_path)
@@ -399,6 +406,10 @@ tmc_status tmc_backward(tmc_plan p, const tmc_inputs* in, const double* grad_out
                         const tmc_grads* g, void* stream) {
   if (!p || !inputs_ok(in) || !g) return TMC_ERR_INVALID_ARG;
   if (!p->fwd_done || std::memcmp(&p->last_in, in, sizeof(tmc_inputs)) != 0) return TMC_ERR_STATE;
+  const bool tc_path = p->precision != TMC_PREC_FP32;
+  // the tensor-core adjoint reduces the factors to d x d moments and forms no per-sample
+  // gradient; dz / deps are available on the FP32 path
+  if (tc_path && (g->dz || g->deps)) return TMC_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   Dev D = p->dev;
   D.eps = in->eps; D.q_mean = in->q_mean; D.q_logstd = in->q_logstd;
@@ -407,7 +418,6 @@ tmc_status tmc_backward(tmc_plan p, const tmc_inputs* in, const double* grad_out
   D.dz = g->dz; D.deps = g->deps; D.dq_mean = g->dq_mean; D.dq_logstd = g->dq_logstd;
   D.dW = g->dW; D.dbias = g->dbias; D.dC = g->dC;
   const Tile* T = p->d_tiles;
-  const bool tc_path = p->precision != TMC_PREC_FP32;
   for (int L = 1; L <= p->maxlevel; ++L) {
     const int b = p->t_level_b[L], e = p->t_level_e[L];
     if (tc_path) {
@@ -417,12 +427,15 @@ tmc_status tmc_backward(tmc_plan p, const tmc_inputs* in, const double* grad_out
       TRY(timed(p, TMC_KC_EDGE_BWD, s, [&] { launch_edge_bwd_rows_f32(D, T + b, e - b, p->maxK, s); }));
     }
   }
-  if (tc_path) TRY(timed(p, TMC_KC_PARAM, s, [&] { tc::launch_unpack_grads(p->tcw, D, s); }));
-  TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_node_grad(D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
-  TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_node_reduce(D, s); }));
-  if (g->dW || g->dbias)
-    TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_param_dW(D, p->d_nonroot, (int)p->nonroot.size(), p->maxd, s); }));
-  if (g->dC) TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_param_dC(D, p->maxd, p->maxobs, s); }));
+  if (tc_path) {
+    TRY(timed(p, TMC_KC_PARAM, s, [&] { tc::launch_unpack_grads(p->tcw, D, s); }));
+  } else {
+    TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_node_grad(D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
+    TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_node_reduce(D, s); }));
+    if (g->dW || g->dbias)
+      TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_param_dW(D, p->d_nonroot, (int)p->nonroot.size(), p->maxd, s); }));
+    if (g->dC) TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_param_dC(D, p->maxd, p->maxobs, s); }));
+  }
   if (p->shared && (g->dW || g->dbias || g->dC))
     TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_shared_reduce(D, p->shared_n, p->shared_d, p->shared_obs, s); }));
   return TMC_OK;

@@ -1,5 +1,13 @@
-// tmc_tc.cuh -- tensor-core (tcgen05) path: workspace, packing and launchers.
+// tmc_tc.cuh -- tensor-core (tcgen05) path: packed operands, tile lists and launchers.
+//
+// Operands of the pairwise contraction are carried as split fp16 pairs (x = hi + lo, both
+// fp16), and every product that feeds an exponent is formed as hi*hi + lo*hi + hi*lo with
+// FP32 accumulation (about 22 significant bits), which keeps |delta log P| far below the
+// tolerance of the reduced-precision path at d = 128.
 #pragma once
+#include <cuda.h>
+#include <cuda_fp16.h>
+
 #include <vector>
 
 #include "../../include/tmc.h"
@@ -8,13 +16,45 @@
 namespace tmc {
 namespace tc {
 
+constexpr int kRows = 128;      // rows of a tensor-core tile (samples)
+constexpr int kLdp = 128;       // row stride (elements) of every packed fp16 operand array
+constexpr int kTcMaxD = 128;    // latent dimension covered by the tensor-core kernels
+constexpr int kTcMaxK = 4096;   // samples per latent covered by the tensor-core kernels
+
 struct TcSub {
   void** dst;
   size_t bytes;
 };
 
+// Device pointers of the tensor-core path (part of the plan's workspace).
+struct TcDev {
+  __half *ZH, *ZL;             // [rows][128] split centred samples, row = node.off_nk + k
+  __half *WH, *WL;             // [slots*128][128] split W_i   ([r][c])
+  __half *WTH, *WTL;           // [slots*128][128] split W_i^T ([c][r])
+  float* cvec;                 // [nodes][128]  c_i = W_i m_p + bias_i - m_i
+  float* G;                    // [nodes][128*128] edge moment sum pi z~_p z~_i^T (child node)
+  float* M2;                   // [nodes][128*128] sum_k q_i[k] z~_i^k z~_i^k^T
+  float* zbar;                 // [nodes][128]  sum_k q_i[k] z~_i^k
+  float* sgC;                  // [nodes][128]  per-edge parts of the node gradient sums
+  float* tgC;
+  float* sgP;
+  float* tgP;
+  int shared;
+};
+
 struct TcWork {
   int precision = 0;
+  int num_nodes = 0, num_slots = 0, maxlevel = 0;
+  long long rows = 0;
+  TcDev t{};
+  CUtensorMap mZH, mZL, mWH, mWL, mWTH, mWTL;
+  // tile lists: [level][class] ranges into d_tiles; class 0 = d <= 64, 1 = d <= 128
+  std::vector<Tile> tiles;
+  std::vector<int> lv_b[2], lv_e[2];
+  Tile* d_tiles = nullptr;
+  std::vector<int> nonroot;
+  int* d_nonroot = nullptr;
+  int maxK = 0;
 };
 
 tmc_status supported(const std::vector<NodeInfo>& nodes, int precision);
@@ -23,6 +63,7 @@ void workspace_layout(TcWork& w, const std::vector<NodeInfo>& nodes, long long n
 tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vector<Tile>& tiles,
                    int maxK, int maxd);
 void release(TcWork& w);
+void launch_sample(TcWork& w, const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s);
 void launch_pack(TcWork& w, const Dev& D, cudaStream_t s);
 void launch_edge_fwd(TcWork& w, const Dev& D, int level, cudaStream_t s);
 void launch_edge_bwd(TcWork& w, const Dev& D, int level, cudaStream_t s);

@@ -1,0 +1,83 @@
+"""Tensor-core (tcgen05, split-fp16) path vs the FP64 oracle through the C-ABI.
+
+Tolerances: |delta log P| <= 2e-2 nats per instance (reduced-precision path) and gradients
+within 1e-3 relative per tensor.  The split hi/lo fp16 operands give ~22-bit products, so
+the measured errors are far smaller; TOL_LOGP_DESIGN (1e-3) pins that design margin.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_08593_gb300 import workload as wl
+from paper_1806_08593_gb300.tmc import TMCError
+from tests.parity import compare, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+TOL_LOGP = 2e-2
+TOL_LOGP_DESIGN = 1e-3
+TOL_GRAD = 1e-3
+PARAM_GRADS = ("dq_mean", "dq_logstd", "dW", "dbias", "dC")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1806_08593_gb300.build import build
+    build()
+
+
+def _check(p, grad_out=None):
+    got = gpu_run(p, "fp16", grad_out=grad_out, want=PARAM_GRADS)
+    ref = oracle_run(p, grad_out=grad_out)
+    rep = compare(p, got, ref, TOL_LOGP_DESIGN, TOL_GRAD, keys=list(PARAM_GRADS))
+    assert rep["log_phat_max_abs"] <= TOL_LOGP
+    return rep
+
+
+def test_config1_tc():
+    _check(wl.chain_config("chain_n3_K4_d2_B8"))
+
+
+@pytest.mark.parametrize("n,K,d,obs,B", [
+    (5, 100, 24, 40, 3),      # ragged K, d in the 64-wide class
+    (4, 300, 64, 50, 2),      # three chunks, d exactly 64
+    (3, 260, 100, 129, 2),    # d in the 128-wide class, obs > 128
+    (4, 128, 128, 256, 2),    # exact tiles, d = 128
+    (1, 77, 9, 5, 3),         # single latent
+    (6, 1, 3, 4, 2),          # K = 1
+])
+def test_chains_tc(n, K, d, obs, B):
+    _check(wl.make_chain(n, K, d, obs, B, seed=2000 + n * 7 + K + d), grad_out=np.linspace(0.5, 1.5, B))
+
+
+def test_uneven_trees_tc():
+    _check(wl.tree_batch(B=10, seed=777))
+
+
+def test_star_fig2_tc():
+    parent = np.array([-1] + [0] * 9, dtype=np.int32)
+    _check(wl.make_problem([parent] * 3, [200] * 3, [20] * 3, [7] * 3, shared=True, seed=98))
+
+
+def test_config3_tc_sampled():
+    p = wl.chain_config("chain_n8_K256_d64_B128")
+    idx = [0, 64, 127]
+    go = np.zeros(p.B)
+    go[idx] = 1.0
+    got = gpu_run(p, "fp16", grad_out=go, want=PARAM_GRADS)
+    sub = oracle.subset(p, idx)
+    ref = oracle_run(sub)
+    err = np.abs(got["log_phat"][idx] - ref["log_phat"]).max()
+    assert err <= TOL_LOGP_DESIGN, err
+    for k in ("dW", "dbias", "dC"):
+        e = np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k])
+        assert e <= TOL_GRAD, (k, e)
+
+
+def test_sample_gradients_are_fp32_only():
+    p = wl.make_chain(3, 8, 4, 4, 2, seed=5)
+    with pytest.raises(TMCError) as ei:
+        gpu_run(p, "fp16", want=("deps",))
+    assert ei.value.status == 2
