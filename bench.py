@@ -6,7 +6,7 @@
 A step is one full pass of the hot path over one batch of synthetic linear-Gaussian
 instances: samples and node terms, conditional means, the fused pairwise-factor +
 log-sum-exp messages from the leaves to the root, the FP64 root reduction, the fused
-adjoint, and the gradients w.r.t. eps, the proposal (m, logs) and the model (W, bias, C).
+adjoint, and the gradients w.r.t. the proposal (m, logs) and the model (W, bias, C).
 Unit of work: B*n*K^2 factor entries per step (summed over instances).
 
 Prints ONE JSON line (rank 0).  Under torchrun each rank runs an independent replica of
@@ -47,11 +47,18 @@ def load_peaks():
 
 
 def make_workload(name):
+    """A named workload, or 'chain:n=..,K=..,d=..,obs=..,B=..' (same generator, seed 1)."""
     from paper_1806_08593_gb300 import workload as wl
     if name in wl.CHAIN_CONFIGS:
         return wl.chain_config(name)
     if name.startswith("trees"):
         return wl.tree_batch()
+    if name.startswith("chain:"):
+        kv = dict(x.split("=") for x in name[6:].split(","))
+        c = {k: int(v) for k, v in kv.items()}
+        p = wl.make_chain(c["n"], c["K"], c["d"], c.get("obs", 2 * c["d"]), c["B"], seed=1)
+        p.name = name
+        return p
     raise SystemExit("unknown workload %s" % name)
 
 

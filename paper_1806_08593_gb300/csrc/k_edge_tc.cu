@@ -95,6 +95,19 @@ __device__ __forceinline__ uint64_t mndesc(const unsigned char* base, int kk) {
 
 __device__ __forceinline__ void set_timeout(const Dev& D) { atomicOr(D.err, kErrTimeout); }
 
+// dst[0..n) += v[0..n) for n <= 32 (16-byte vector reductions where the row is complete).
+__device__ __forceinline__ void red_add_row32(float* dst, const uint32_t (&v)[32], int n) {
+  if (n >= 32) {
+#pragma unroll
+    for (int j = 0; j < 32; j += 4)
+      asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + j), "f"(__uint_as_float(v[j])),
+                   "f"(__uint_as_float(v[j + 1])), "f"(__uint_as_float(v[j + 2])), "f"(__uint_as_float(v[j + 3]))
+                   : "memory");
+  } else {
+    for (int j = 0; j < n; ++j) atomicAdd(dst + j, __uint_as_float(v[j]));
+  }
+}
+
 // Bytes of the streaming ring: two stages of (hi, lo) sample tiles, and large enough for the
 // adjoint epilogue (Z~ hi, ones atom, Z~ lo, q z~ tile of two atoms).
 __host__ __device__ constexpr int ring_bytes(int DP) {
@@ -116,12 +129,13 @@ __global__ void k_sample_tc(Dev D, TcDev T, const Tile* __restrict__ tiles) {
   float* s_std = sm;
   float* s_off = sm + kTcMaxD;
   const bool root = nd.parent < 0, keep32 = root || nd.leaf_slot >= 0;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) {
-    s_std[j] = expf(D.q_logstd[nd.off_q + j]);
-    s_off[j] = root ? D.q_mean[nd.off_q + j] - D.bias[nd.off_bias + j] : 0.f;
+  for (int j = threadIdx.x; j < kTcMaxD; j += blockDim.x) {
+    s_std[j] = j < d ? expf(D.q_logstd[nd.off_q + j]) : 0.f;
+    s_off[j] = (root && j < d) ? D.q_mean[nd.off_q + j] - D.bias[nd.off_bias + j] : 0.f;
   }
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool vec = (d & 3) == 0 && (nd.off_nkd & 3) == 0;
   bool bad = false;
   for (int r = w; r < kTile; r += blockDim.x / 32) {
     const int k = t.row0 + r;
@@ -129,23 +143,35 @@ __global__ void k_sample_tc(Dev D, TcDev T, const Tile* __restrict__ tiles) {
     const long long base = nd.off_nkd + (long long)k * d;
     const long long prow = (nd.off_nk + k) * kLdp;
     float se = 0.f, sz = 0.f, sr = 0.f;
-    for (int j = lane; j < kLdp; j += 32) {
-      float z = 0.f;
-      if (j < d) {
-        const float e = D.eps[base + j];
-        z = s_std[j] * e;
-        bad |= !isfinite(z);
-        if (keep32) D.zt[base + j] = z;
-        se = fmaf(e, e, se);
-        sz = fmaf(z, z, sz);
-        const float rr = z + s_off[j];
-        sr = fmaf(rr, rr, sr);
+    // lane owns columns 4*lane .. 4*lane+3 of the 128-wide packed row
+    const int j0 = 4 * lane;
+    float e[4] = {0.f, 0.f, 0.f, 0.f};
+    if (vec) {
+      if (j0 < d) {
+        const float4 v = *reinterpret_cast<const float4*>(D.eps + base + j0);
+        e[0] = v.x; e[1] = v.y; e[2] = v.z; e[3] = v.w;
       }
-      float hi, lo;
-      split_half(z, hi, lo);
-      T.ZH[prow + j] = __float2half_rn(hi);
-      T.ZL[prow + j] = __float2half_rn(lo);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (j0 + q < d) e[q] = D.eps[base + j0 + q];
     }
+    float z[4], hi[4], lo[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      z[q] = s_std[j0 + q] * e[q];
+      bad |= !isfinite(z[q]);
+      se = fmaf(e[q], e[q], se);
+      sz = fmaf(z[q], z[q], sz);
+      const float rr = (j0 + q < d) ? z[q] + s_off[j0 + q] : 0.f;
+      sr = fmaf(rr, rr, sr);
+      split_half(z[q], hi[q], lo[q]);
+    }
+    if (keep32)
+      for (int q = 0; q < 4; ++q)
+        if (j0 + q < d) D.zt[base + j0 + q] = z[q];
+    *reinterpret_cast<uint2*>(T.ZH + prow + j0) = make_uint2(pack_half2(hi[0], hi[1]), pack_half2(hi[2], hi[3]));
+    *reinterpret_cast<uint2*>(T.ZL + prow + j0) = make_uint2(pack_half2(lo[0], lo[1]), pack_half2(lo[2], lo[3]));
     for (int o = 16; o > 0; o >>= 1) {
       se += __shfl_xor_sync(0xffffffffu, se, o);
       sz += __shfl_xor_sync(0xffffffffu, sz, o);
@@ -168,7 +194,7 @@ __global__ void k_pack_w(Dev D, TcDev T, const int* __restrict__ nonroot) {
   if (D.shared && nd.b != 0) return;  // shared parameters: pack once (instance 0's nodes)
   const int slot = slot_of(D, nd, g), d = nd.d;
   const float* Wi = D.W + nd.off_W;
-  for (int e = threadIdx.x; e < kLdp * kLdp; e += blockDim.x) {
+  for (int e = blockIdx.y * 1024 + threadIdx.x; e < (blockIdx.y + 1) * 1024; e += blockDim.x) {
     const int r = e / kLdp, c = e % kLdp;
     const float v = (r < d && c < d) ? Wi[(long long)r * d + c] : 0.f;
     float hi, lo;
@@ -187,14 +213,16 @@ __global__ void k_pack_c(Dev D, TcDev T, const int* __restrict__ nonroot) {
   const NodeInfo nd = D.nodes[g];
   const NodeInfo pn = D.nodes[nd.parent];
   const int d = nd.d;
-  for (int r = threadIdx.x; r < kLdp; r += blockDim.x) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = w; r < kLdp; r += blockDim.x / 32) {
     float s = 0.f;
     if (r < d) {
-      const float* w = D.W + nd.off_W + (long long)r * d;
-      for (int c = 0; c < d; ++c) s = fmaf(w[c], D.q_mean[pn.off_q + c], s);
+      const float* wr = D.W + nd.off_W + (long long)r * d;
+      for (int c = lane; c < d; c += 32) s = fmaf(wr[c], D.q_mean[pn.off_q + c], s);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       s += D.bias[nd.off_bias + r] - D.q_mean[nd.off_q + r];
     }
-    T.cvec[(long long)g * kLdp + r] = s;
+    if (lane == 0) T.cvec[(long long)g * kLdp + r] = s;
   }
 }
 
@@ -704,14 +732,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         uint32_t v[32];
         tmem_ld32(tG + lane_off + g * 32, v);
         tmem_wait_ld();
-        if (arow)
-          for (int j = 0; j < 32; ++j)
-            if (g * 32 + j < d) atomicAdd(Gi + g * 32 + j, __uint_as_float(v[j]));
+        if (arow) red_add_row32(Gi + g * 32, v, d - g * 32);
         tmem_ld32(tM2 + lane_off + g * 32, v);
         tmem_wait_ld();
-        if (arow)
-          for (int j = 0; j < 32; ++j)
-            if (g * 32 + j < d) atomicAdd(Mi + g * 32 + j, __uint_as_float(v[j]));
+        if (arow) red_add_row32(Mi + g * 32, v, d - g * 32);
       }
       uint32_t v[32];
       tmem_ld32(tM2 + lane_off + DP, v);  // column DP: sum_k' q z~[k'][a]
@@ -783,61 +807,120 @@ __global__ void __launch_bounds__(kThreads) k_root_moments(Dev D, TcDev T) {
 // and the edge's parts of the proposal-gradient sums of its two nodes:
 //   child c  : sum_k' g = -db'_c,  sum_k' g z~ = (diag(W_c G_c) + c_c zbar_c - diag(M2_c)) / var
 //   parent p : sum_k g = W_c^T db'_c,  sum_k g z~ = diag(W_c^T D_c)
-// One CTA per non-root node, 128 threads: thread a first forms db'_c[a] and the child-side
-// sums; then thread b walks column b of D_c (so the parent-side sums need no cross-thread
-// reduction).
+// k_asm_edge_vec: one CTA (128 threads) per edge -- the vector quantities (db', child-side
+// sums, parent-side sum_k g, dbias).  k_asm_edge_mat: (edge, 64x64 tile of D_c) -- the d x d
+// part on the tiled FP32 GEMM (D_c needs W_c M2_p), dW and the parent-side diag(W_c^T D_c).
 // =======================================================================================
-__global__ void __launch_bounds__(128) k_asm_edge(Dev D, TcDev T, const int* __restrict__ nonroot) {
-  __shared__ float zp[kTcMaxD], dbs[kTcMaxD], cs[kTcMaxD];
+__global__ void __launch_bounds__(128) k_asm_edge_vec(Dev D, TcDev T, const int* __restrict__ nonroot) {
+  __shared__ float zp[kTcMaxD], dbs[kTcMaxD];
   const int g = nonroot[blockIdx.x];
   const NodeInfo nd = D.nodes[g];
-  const NodeInfo pn = D.nodes[nd.parent];
   const int d = nd.d;
   const float iv = D.inv_var;
   const float go = D.grad_out ? (float)D.grad_out[nd.b] : 1.f;
   const float* W = D.W + nd.off_W;
   const float* Gc = T.G + (long long)g * kLdp * kLdp;
-  const float* M2p = T.M2 + (long long)nd.parent * kLdp * kLdp;
   const float* M2c = T.M2 + (long long)g * kLdp * kLdp;
   const float* zbc = T.zbar + (long long)g * kLdp;
   const float* cc = T.cvec + (long long)g * kLdp;
-  const int a = threadIdx.x;
-  if (a < d) {
-    zp[a] = T.zbar[(long long)nd.parent * kLdp + a];
-    cs[a] = cc[a];
-  }
+  const int j = threadIdx.x;
+  if (j < d) zp[j] = T.zbar[(long long)nd.parent * kLdp + j];
   __syncthreads();
-  if (a < d) {
-    float s = 0.f, wg = 0.f;
-    for (int j = 0; j < d; ++j) {
-      s = fmaf(W[(long long)a * d + j], zp[j], s);
-      wg = fmaf(W[(long long)a * d + j], Gc[(long long)j * kLdp + a], wg);
-    }
-    const float db = (zbc[a] - s - cs[a]) * iv;
-    dbs[a] = db;
-    T.sgC[(long long)g * kLdp + a] = -db;
-    T.tgC[(long long)g * kLdp + a] = (wg + cs[a] * zbc[a] - M2c[(long long)a * kLdp + a]) * iv;
-    if (D.shared) { if (D.pbias) D.pbias[nd.off_q + a] = go * db; }
-    else if (D.dbias) D.dbias[nd.off_bias + a] = go * db;
-  }
-  __syncthreads();
-  const int b = threadIdx.x;
-  if (b >= d) return;
-  const float mpb = D.q_mean[pn.off_q + b];
-  float sg = 0.f, tg = 0.f;
-  for (int r = 0; r < d; ++r) {
-    const float* Wr = W + (long long)r * d;
+  if (j < d) {
     float s = 0.f;
-    for (int j = 0; j < d; ++j) s = fmaf(Wr[j], M2p[(long long)j * kLdp + b], s);
-    const float Drb = (Gc[(long long)b * kLdp + r] - s - cs[r] * zp[b]) * iv;
-    tg = fmaf(Wr[b], Drb, tg);
-    sg = fmaf(Wr[b], dbs[r], sg);
-    const float v = go * (Drb + dbs[r] * mpb);
-    if (D.shared) { if (D.pW) D.pW[nd.off_pW + (long long)r * d + b] = v; }
-    else if (D.dW) D.dW[nd.off_W + (long long)r * d + b] = v;
+    for (int c = 0; c < d; ++c) s = fmaf(W[(long long)j * d + c], zp[c], s);
+    const float db = (zbc[j] - s - cc[j]) * iv;
+    dbs[j] = db;
+    T.sgC[(long long)g * kLdp + j] = -db;
+    if (D.shared) { if (D.pbias) D.pbias[nd.off_q + j] = go * db; }
+    else if (D.dbias) D.dbias[nd.off_bias + j] = go * db;
   }
-  T.sgP[(long long)g * kLdp + b] = sg;
-  T.tgP[(long long)g * kLdp + b] = tg;
+  __syncthreads();
+  if (j >= d) return;
+  // diag(W_c G_c)[j] = sum_a W[j][a] G[a][j];  (W^T db')[j] = sum_a W[a][j] db'[a]
+  float wg = 0.f, sg = 0.f;
+  for (int a = 0; a < d; ++a) {
+    wg = fmaf(W[(long long)j * d + a], Gc[(long long)a * kLdp + j], wg);
+    sg = fmaf(W[(long long)a * d + j], dbs[a], sg);
+  }
+  T.tgC[(long long)g * kLdp + j] = (wg + cc[j] * zbc[j] - M2c[(long long)j * kLdp + j]) * iv;
+  T.sgP[(long long)g * kLdp + j] = sg;
+}
+
+__global__ void __launch_bounds__(kThreads) k_asm_edge_mat(Dev D, TcDev T, const int* __restrict__ nonroot) {
+  __shared__ TileSmem sm;
+  __shared__ float colpart[16][kTile + 1];
+  const int g = nonroot[blockIdx.x];
+  const NodeInfo nd = D.nodes[g];
+  const NodeInfo pn = D.nodes[nd.parent];
+  const int d = nd.d;
+  const int a0 = blockIdx.y * kTile, b0 = blockIdx.z * kTile;
+  if (a0 >= d || b0 >= d) return;
+  const float iv = D.inv_var;
+  const float go = D.grad_out ? (float)D.grad_out[nd.b] : 1.f;
+  const float* W = D.W + nd.off_W;
+  const float* Gc = T.G + (long long)g * kLdp * kLdp;
+  const float* M2p = T.M2 + (long long)nd.parent * kLdp * kLdp;
+  const float* zbp = T.zbar + (long long)nd.parent * kLdp;
+  const float* zbc = T.zbar + (long long)g * kLdp;
+  const float* cc = T.cvec + (long long)g * kLdp;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  float acc[4][4];
+  zero_acc(acc);
+  // acc[a][b] = sum_j W[a][j] M2_p[j][b]
+  tile_gemm<true, false>(acc, W + (long long)a0 * d, d, min(kTile, d - a0), M2p + b0, kLdp,
+                         min(kTile, d - b0), d, sm);
+  float tcol[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int a = a0 + ty * 4 + i;
+    if (a >= d) continue;
+    // db'[a] recomputed locally (d FMAs): (zbar_c - W zbar_p - c)[a] / var
+    float s = 0.f;
+    for (int c = 0; c < d; ++c) s = fmaf(W[(long long)a * d + c], zbp[c], s);
+    const float db = (zbc[a] - s - cc[a]) * iv;
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int bb = b0 + tx * 4 + jj;
+      if (bb >= d) continue;
+      const float Dab = (Gc[(long long)bb * kLdp + a] - acc[i][jj] - cc[a] * zbp[bb]) * iv;
+      tcol[jj] = fmaf(W[(long long)a * d + bb], Dab, tcol[jj]);
+      const float v = go * (Dab + db * D.q_mean[pn.off_q + bb]);
+      if (D.shared) { if (D.pW) D.pW[nd.off_pW + (long long)a * d + bb] = v; }
+      else if (D.dW) D.dW[nd.off_W + (long long)a * d + bb] = v;
+    }
+  }
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) colpart[ty][tx * 4 + jj] = tcol[jj];
+  __syncthreads();
+  if (threadIdx.x < kTile && b0 + threadIdx.x < d) {
+    float s = 0.f;
+    for (int i = 0; i < 16; ++i) s += colpart[i][threadIdx.x];
+    // at most two row tiles per column: the two additions commute exactly
+    atomicAdd(T.tgP + (long long)g * kLdp + b0 + threadIdx.x, s);
+  }
+}
+
+// C^T C per distinct observation matrix (one for shared parameters, else one per instance).
+__global__ void __launch_bounds__(kThreads) k_ctc(Dev D, TcDev T) {
+  __shared__ TileSmem sm;
+  const InstInfo in = D.insts[blockIdx.x];
+  const int d = in.d, obs = in.obs;
+  const int a0 = blockIdx.y * kTile, b0 = blockIdx.z * kTile;
+  if (a0 >= d || b0 >= d) return;
+  const float* C = D.C + in.off_C;
+  float acc[4][4];
+  zero_acc(acc);
+  tile_gemm<false, false>(acc, C + a0, d, min(kTile, d - a0), C + b0, d, min(kTile, d - b0), obs, sm);
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  float* out = T.CtC + (long long)blockIdx.x * kLdp * kLdp;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int a = a0 + ty * 4 + i, b = b0 + tx * 4 + j;
+      if (a < d && b < d) out[(long long)a * kLdp + b] = acc[i][j];
+    }
 }
 
 // Node sums and outputs: dm_i = grad_out * Sg,  dlogs_i = grad_out * (sum_k q_i + Tg), with
@@ -900,14 +983,13 @@ __global__ void __launch_bounds__(128) k_asm_node(Dev D, TcDev T) {
       for (int c = 0; c < d; ++c) D.dW[nd.off_W + (long long)j * d + c] = 0.f;
   }
   if (leaf) {
-    // (C^T C) row j, then C^T C zbar and diag(C^T C M2)
-    const float* C = D.C + nd.off_C;
+    // C^T C is symmetric: row j read as column j (coalesced over threads)
+    const float* ctc = T.CtC + (long long)(D.shared ? 0 : nd.b) * kLdp * kLdp;
     float czb = 0.f, dg = 0.f;
     for (int a = 0; a < d; ++a) {
-      float ctc = 0.f;
-      for (int o = 0; o < nd.obs; ++o) ctc = fmaf(C[(long long)o * d + j], C[(long long)o * d + a], ctc);
-      czb = fmaf(ctc, zb[a], czb);
-      dg = fmaf(ctc, M2[(long long)a * kLdp + j], dg);
+      const float v = ctc[(long long)a * kLdp + j];
+      czb = fmaf(v, zb[a], czb);
+      dg = fmaf(v, M2[(long long)a * kLdp + j], dg);
     }
     Sg += (ctx[j] - czb) * D.inv_obs_var;
     Tg += (ctx[j] * zb[j] - dg) * D.inv_obs_var;
@@ -917,38 +999,62 @@ __global__ void __launch_bounds__(128) k_asm_node(Dev D, TcDev T) {
 }
 
 // dC = grad_out / obs_var * sum_leaves [ x~ (zbar + m)^T - C (M2 + zbar m^T) ]
-// Grid: (instance, 64-row tile of observation dims); thread per (o, c) element loop.
-__global__ void __launch_bounds__(256) k_asm_dC(Dev D, TcDev T) {
+// Grid: (instance, 64-row tile of observation dims, 64-col tile of latent dims).
+__global__ void __launch_bounds__(kThreads) k_asm_dC(Dev D, TcDev T) {
+  __shared__ TileSmem sm;
+  __shared__ float xo[kTile], czo[kTile];
   const InstInfo in = D.insts[blockIdx.x];
   const int d = in.d, obs = in.obs;
+  const int o0 = blockIdx.y * kTile, c0 = blockIdx.z * kTile;
+  if (o0 >= obs || c0 >= d) return;
+  const int rows = min(kTile, obs - o0), cols = min(kTile, d - c0);
   const float go = D.grad_out ? (float)D.grad_out[blockIdx.x] : 1.f;
-  const int o0 = blockIdx.y * 64;
-  if (o0 >= obs) return;
-  const int rows = min(64, obs - o0);
-  for (int e = threadIdx.x; e < rows * d; e += blockDim.x) {
-    const int o = o0 + e / d, c = e % d;
-    float acc = 0.f;
-    for (int gi = in.node0; gi < in.node0 + in.n; ++gi) {
-      const NodeInfo nd = D.nodes[gi];
-      if (nd.leaf_slot < 0) continue;
-      const float* C = D.C + nd.off_C;
-      const float* M2 = T.M2 + (long long)gi * kLdp * kLdp;
-      const float* zb = T.zbar + (long long)gi * kLdp;
-      const float* m = D.q_mean + nd.off_q;
-      float cm = 0.f, cmz = 0.f, czb = 0.f;
-      for (int a = 0; a < d; ++a) {
-        const float ca = C[(long long)o * d + a];
-        cm = fmaf(ca, m[a], cm);
-        cmz = fmaf(ca, M2[(long long)a * kLdp + c], cmz);
-        czb = fmaf(ca, zb[a], czb);
-      }
-      const float xt_o = D.x[nd.off_x + o] - cm;
-      acc += xt_o * (zb[c] + m[c]) - (cmz + czb * m[c]);
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  float out[4][4];
+  zero_acc(out);
+  for (int gi = in.node0; gi < in.node0 + in.n; ++gi) {
+    const NodeInfo nd = D.nodes[gi];
+    if (nd.leaf_slot < 0) continue;
+    const float* C = D.C + nd.off_C;
+    const float* M2 = T.M2 + (long long)gi * kLdp * kLdp;
+    const float* zb = T.zbar + (long long)gi * kLdp;
+    const float* m = D.q_mean + nd.off_q;
+    __syncthreads();
+    if (threadIdx.x < kTile) {
+      const int o = o0 + threadIdx.x;
+      float cm = 0.f, cz = 0.f;
+      if (o < obs)
+        for (int a = 0; a < d; ++a) {
+          const float ca = C[(long long)o * d + a];
+          cm = fmaf(ca, m[a], cm);
+          cz = fmaf(ca, zb[a], cz);
+        }
+      xo[threadIdx.x] = (o < obs) ? D.x[nd.off_x + o] - cm : 0.f;
+      czo[threadIdx.x] = cz;
     }
-    const float v = go * acc * D.inv_obs_var;
-    if (D.shared) { if (D.pC) D.pC[in.off_pC + (long long)o * d + c] = v; }
-    else if (D.dC) D.dC[in.off_C + (long long)o * d + c] = v;
+    float acc[4][4];
+    zero_acc(acc);
+    tile_gemm<true, false>(acc, C + (long long)o0 * d, d, rows, M2 + c0, kLdp, cols, d, sm);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = c0 + tx * 4 + j;
+        if (c >= d) continue;
+        const int oi = ty * 4 + i;
+        out[i][j] += xo[oi] * (zb[c] + m[c]) - acc[i][j] - czo[oi] * m[c];
+      }
   }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int o = o0 + ty * 4 + i, c = c0 + tx * 4 + j;
+      if (o >= obs || c >= d) continue;
+      const float v = go * out[i][j] * D.inv_obs_var;
+      if (D.shared) { if (D.pC) D.pC[in.off_pC + (long long)o * d + c] = v; }
+      else if (D.dC) D.dC[in.off_C + (long long)o * d + c] = v;
+    }
 }
 
 // =======================================================================================
@@ -1005,6 +1111,7 @@ tmc_status supported(const std::vector<NodeInfo>& nodes, int precision) {
 void workspace_layout(TcWork& w, const std::vector<NodeInfo>& nodes, long long nk, long long,
                       std::vector<TcSub>& subs) {
   w.num_nodes = (int)nodes.size();
+  w.num_inst = nodes.empty() ? 0 : nodes.back().b + 1;
   int slots = 0;
   for (const NodeInfo& nd : nodes) slots = std::max(slots, (w.t.shared ? nd.i : (int)(&nd - nodes.data())) + 1);
   w.num_slots = slots;
@@ -1027,11 +1134,13 @@ void workspace_layout(TcWork& w, const std::vector<NodeInfo>& nodes, long long n
   subs.push_back({(void**)&w.t.tgC, nv});
   subs.push_back({(void**)&w.t.sgP, nv});
   subs.push_back({(void**)&w.t.tgP, nv});
+  subs.push_back({(void**)&w.t.CtC, (size_t)(w.t.shared ? 1 : w.num_inst) * kLdp * kLdp * sizeof(float)});
 }
 
 tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vector<Tile>&, int maxK,
                    int) {
   w.maxK = maxK;
+  for (const NodeInfo& nd : nodes) w.maxobs = std::max(w.maxobs, nd.obs);
   if (!make_map(&w.mZH, w.t.ZH, w.rows) || !make_map(&w.mZL, w.t.ZL, w.rows) ||
       !make_map(&w.mWH, w.t.WH, (long long)w.num_slots * kLdp) ||
       !make_map(&w.mWL, w.t.WL, (long long)w.num_slots * kLdp) ||
@@ -1092,8 +1201,8 @@ void launch_sample(TcWork& w, const Dev& D, const Tile* tiles, int ntiles, cudaS
 void launch_pack(TcWork& w, const Dev& D, cudaStream_t s) {
   const int n = (int)w.nonroot.size();
   if (!n) return;
-  k_pack_w<<<n, 256, 0, s>>>(D, w.t, w.d_nonroot);
-  k_pack_c<<<n, 128, 0, s>>>(D, w.t, w.d_nonroot);
+  k_pack_w<<<dim3(n, kLdp * kLdp / 1024), 256, 0, s>>>(D, w.t, w.d_nonroot);
+  k_pack_c<<<n, 256, 0, s>>>(D, w.t, w.d_nonroot);
 }
 
 void launch_edge_fwd(TcWork& w, const Dev& D, int L, cudaStream_t s) {
@@ -1124,10 +1233,16 @@ void launch_edge_bwd(TcWork& w, const Dev& D, int L, cudaStream_t s) {
 }
 
 void launch_unpack_grads(TcWork& w, const Dev& D, cudaStream_t s) {
+  const int nr = (int)w.nonroot.size();
   k_root_moments<<<dim3(D.num_inst, 2, 2), kThreads, 0, s>>>(D, w.t);
-  if (!w.nonroot.empty()) k_asm_edge<<<(int)w.nonroot.size(), 128, 0, s>>>(D, w.t, w.d_nonroot);
+  k_ctc<<<dim3(D.shared ? 1 : D.num_inst, 2, 2), kThreads, 0, s>>>(D, w.t);
+  cudaMemsetAsync(w.t.tgP, 0, (size_t)w.num_nodes * kLdp * sizeof(float), s);
+  if (nr) {
+    k_asm_edge_vec<<<nr, 128, 0, s>>>(D, w.t, w.d_nonroot);
+    k_asm_edge_mat<<<dim3(nr, 2, 2), kThreads, 0, s>>>(D, w.t, w.d_nonroot);
+  }
   k_asm_node<<<D.num_nodes, 128, 0, s>>>(D, w.t);
-  k_asm_dC<<<dim3(D.num_inst, (kMaxD + 63) / 64), 256, 0, s>>>(D, w.t);
+  k_asm_dC<<<dim3(D.num_inst, (w.maxobs + kTile - 1) / kTile, 2), kThreads, 0, s>>>(D, w.t);
 }
 
 }  // namespace tc

@@ -39,12 +39,13 @@ struct TcDev {
   float* tgC;
   float* sgP;
   float* tgP;
+  float* CtC;                  // [1 or B][128*128]  C^T C per observation matrix
   int shared;
 };
 
 struct TcWork {
   int precision = 0;
-  int num_nodes = 0, num_slots = 0, maxlevel = 0;
+  int num_nodes = 0, num_slots = 0, maxlevel = 0, num_inst = 0, maxobs = 0;
   long long rows = 0;
   TcDev t{};
   CUtensorMap mZH, mZL, mWH, mWL, mWTH, mWTL;
