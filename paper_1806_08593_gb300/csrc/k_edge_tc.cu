@@ -37,15 +37,16 @@ namespace tc {
 namespace {
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
-constexpr int kThreadsTc = 256;
+constexpr int kThreadsTc = 384;  // 4 control warps + 8 math warps
+constexpr int kMath = 256;       // math threads
 constexpr int kBox = 16384;  // bytes of one 128-row x 128-byte swizzled box
 
 __device__ __forceinline__ int slot_of(const Dev& D, const NodeInfo& nd, int g) {
   return D.shared ? nd.i : g;
 }
 
-// Named barrier among the 128 exponential threads (warps 4..7).
-__device__ __forceinline__ void sync_math() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// Named barrier among the 256 math threads (warps 4..11).
+__device__ __forceinline__ void sync_math() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 // Writes 8 consecutive values of row r (columns 8*chunk .. 8*chunk+7) of a [128 x DP]
 // 128-byte-swizzled fp16 tile as hi / lo splits.
@@ -128,10 +129,12 @@ __global__ void k_sample_tc(Dev D, TcDev T, const Tile* __restrict__ tiles) {
   const int d = nd.d;
   float* s_std = sm;
   float* s_off = sm + kTcMaxD;
+  float* s_c = sm + 2 * kTcMaxD;
   const bool root = nd.parent < 0, keep32 = root || nd.leaf_slot >= 0;
   for (int j = threadIdx.x; j < kTcMaxD; j += blockDim.x) {
     s_std[j] = j < d ? expf(D.q_logstd[nd.off_q + j]) : 0.f;
     s_off[j] = (root && j < d) ? D.q_mean[nd.off_q + j] - D.bias[nd.off_bias + j] : 0.f;
+    s_c[j] = root ? 0.f : T.cvec[(long long)t.node * kLdp + j];
   }
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -142,7 +145,7 @@ __global__ void k_sample_tc(Dev D, TcDev T, const Tile* __restrict__ tiles) {
     if (k >= nd.K) break;
     const long long base = nd.off_nkd + (long long)k * d;
     const long long prow = (nd.off_nk + k) * kLdp;
-    float se = 0.f, sz = 0.f, sr = 0.f;
+    float se = 0.f, sz = 0.f, sr = 0.f, szc = 0.f;
     // lane owns columns 4*lane .. 4*lane+3 of the 128-wide packed row
     const int j0 = 4 * lane;
     float e[4] = {0.f, 0.f, 0.f, 0.f};
@@ -163,6 +166,7 @@ __global__ void k_sample_tc(Dev D, TcDev T, const Tile* __restrict__ tiles) {
       bad |= !isfinite(z[q]);
       se = fmaf(e[q], e[q], se);
       sz = fmaf(z[q], z[q], sz);
+      szc = fmaf(z[q], s_c[j0 + q], szc);
       const float rr = (j0 + q < d) ? z[q] + s_off[j0 + q] : 0.f;
       sr = fmaf(rr, rr, sr);
       split_half(z[q], hi[q], lo[q]);
@@ -176,12 +180,14 @@ __global__ void k_sample_tc(Dev D, TcDev T, const Tile* __restrict__ tiles) {
       se += __shfl_xor_sync(0xffffffffu, se, o);
       sz += __shfl_xor_sync(0xffffffffu, sz, o);
       sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      szc += __shfl_xor_sync(0xffffffffu, szc, o);
     }
     if (lane == 0) {
       float u = 0.5f * se;
       if (root) u -= 0.5f * sr * D.inv_var;
       D.u[nd.off_nk + k] = u;
       D.zn[nd.off_nk + k] = sz;
+      T.zc[nd.off_nk + k] = szc;
     }
   }
   if (bad) atomicOr(D.err, kErrNumeric);
@@ -228,6 +234,8 @@ __global__ void k_pack_c(Dev D, TcDev T, const int* __restrict__ nonroot) {
 
 // =======================================================================================
 // Forward edge kernel.
+// Math warps 4..11: warp w serves TMEM lanes 32*(w%4).. (tile rows) and half h = (w-4)/4 of
+// the columns of every S chunk (and of the latent dimension in the prologue).
 // =======================================================================================
 template <int DP>
 __global__ void __launch_bounds__(kThreadsTc, 1)
@@ -237,6 +245,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   constexpr int TB = kRows * DP * 2;  // bytes of one [128 x DP] fp16 tile
   constexpr int NB = DP / 64;         // 64-column boxes per tile
   constexpr int KS = DP / 16;         // K-steps over the latent dimension
+  constexpr int GH = DP / 64;         // 32-column groups of the latent dimension per half
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   unsigned char* sAH = sm;
@@ -245,8 +254,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   float* cb = reinterpret_cast<float*>(ring + ring_bytes(DP));
   __shared__ uint64_t bar_pro, bar_mu, bar_A, full[2], empty[2], sfull[2], sfree[2], bar_done;
   __shared__ uint32_t tbase;
-  __shared__ float red[4];
+  __shared__ float red[8];
   __shared__ float cv[kTcMaxD];
+  __shared__ float nrm_h[2][kRows], m_h[2][kRows], s_h[2][kRows];
 
   const Tile t = tiles[blockIdx.x];
   const NodeInfo nd = D.nodes[t.node];
@@ -259,13 +269,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   if (threadIdx.x == 0) {
     mbar_init(&bar_pro, 1);
     mbar_init(&bar_mu, 1);
-    mbar_init(&bar_A, 128);
+    mbar_init(&bar_A, kMath);
     mbar_init(&bar_done, 1);
     for (int i = 0; i < 2; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
       mbar_init(&sfull[i], 1);
-      mbar_init(&sfree[i], 128);
+      mbar_init(&sfree[i], kMath);
     }
     fence_barrier_init();
   }
@@ -303,7 +313,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       issued = c + 1;
     }
     if (!ok) set_timeout(D);
-    // drain: every issued load has landed before the CTA may exit
     for (int c = (issued > 2 ? issued - 2 : 0); c < issued; ++c) mbar_wait(&full[c & 1], (c >> 1) & 1);
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------------ MMA issuer
@@ -336,12 +345,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     mbar_wait(&bar_done, 0);
   } else if (warp >= 4) {
     // ------------------------------------------------------------------ exponentials
-    const int r = threadIdx.x - 128;           // tile row = TMEM lane
-    const uint32_t lane_off = (uint32_t)((warp - 4) * 32) << 16;
+    const int mt = threadIdx.x - 128;
+    const int qd = warp & 3, h = (warp - 4) >> 2;
+    const int r = 32 * qd + lane;               // tile row = TMEM lane
+    const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
     const int k = t.row0 + r;
-    // beta_i (normalised) for all K child samples, and cb = (beta - |z~|^2 / (2 var)) log2 e
     float mx = -INFINITY;
-    for (int j = r; j < K; j += 128) {
+    for (int j = mt; j < K; j += kMath) {
       float v = D.u[nd.off_nk + j];
       for (int c = nd.child_begin; c < nd.child_end; ++c) v += D.lam[D.nodes[D.children[c]].off_nk + j];
       cb[j] = v;
@@ -349,11 +359,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) red[warp - 4] = mx;
-    for (int j = r; j < kLdp; j += 128) cv[j] = T.cvec[(long long)t.node * kLdp + j];
+    for (int j = mt; j < kLdp; j += kMath) cv[j] = T.cvec[(long long)t.node * kLdp + j];
     sync_math();
-    mx = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+    mx = red[0];
+#pragma unroll
+    for (int i = 1; i < 8; ++i) mx = fmaxf(mx, red[i]);
     const bool store = (t.row0 == 0);
-    for (int j = r; j < nch * kRows; j += 128) {
+    for (int j = mt; j < nch * kRows; j += kMath) {
       if (j < K) {
         const float bb = cb[j] - mx;
         if (store) D.beta[nd.off_nk + j] = bb;
@@ -362,14 +374,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         cb[j] = -INFINITY;
       }
     }
-    if (store && r == 0) D.nodemax[t.node] = mx;
-    // prologue result: mu~ row, its norm, split into the A operand
+    if (store && mt == 0) D.nodemax[t.node] = mx;
+    // prologue: this half of the mu~ row, its squared norm, split into the A operand
     bool ok = mbar_wait(&bar_mu, 0);
     float nrm = 0.f;
     if (ok) {
       tc_fence_after();
 #pragma unroll 1
-      for (int g = 0; g < DP / 32; ++g) {
+      for (int gg = 0; gg < GH; ++gg) {
+        const int g = h * GH + gg;
         uint32_t v[32];
         tmem_ld32(tMU + lane_off + g * 32, v);
         tmem_wait_ld();
@@ -382,34 +395,40 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 #pragma unroll
         for (int q = 0; q < 4; ++q) store_split8(sAH, sAL, r, g * 4 + q, f + 8 * q);
       }
-      if (k < K) D.mun[nd.off_nk + k] = nrm;
       fence_proxy_async_smem();
       tc_fence_before();
     }
+    nrm_h[h][r] = nrm;
     mbar_arrive(&bar_A);
-    sync_math();  // cb complete before the main loop reads it
+    sync_math();  // cb and the half norms are complete
+    const float nrm_all = nrm_h[0][r] + nrm_h[1][r];
+    if (h == 0 && ok && k < K) D.mun[nd.off_nk + k] = nrm_all;
     const float sc = iv * kLog2e;
     float m = -INFINITY, ssum = 0.f;
     for (int c = 0; ok && c < nch; ++c) {
       const int b = c & 1;
       if (!mbar_wait(&sfull[b], (c >> 1) & 1)) { ok = false; break; }
       tc_fence_after();
-      const float* cbc = cb + c * kRows;
-#pragma unroll 1
-      for (int g = 0; g < 4; ++g) {
-        uint32_t v[32];
-        tmem_ld32(tS[b] + lane_off + g * 32, v);
-        tmem_wait_ld();
+      uint32_t v[2][32];
+      tmem_ld32(tS[b] + lane_off + 64 * h, v[0]);
+      tmem_ld32(tS[b] + lane_off + 64 * h + 32, v[1]);
+      tmem_wait_ld();
+      tc_fence_before();
+      mbar_arrive(&sfree[b]);  // the MMA may overwrite this S buffer now
+      const float* cbc = cb + c * kRows + 64 * h;
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
         float e[32], gm = -INFINITY;
 #pragma unroll
         for (int j = 0; j < 32; j += 4) {
           const float4 c4 = *reinterpret_cast<const float4*>(cbc + g * 32 + j);
-          e[j] = fmaf(__uint_as_float(v[j]), sc, c4.x);
-          e[j + 1] = fmaf(__uint_as_float(v[j + 1]), sc, c4.y);
-          e[j + 2] = fmaf(__uint_as_float(v[j + 2]), sc, c4.z);
-          e[j + 3] = fmaf(__uint_as_float(v[j + 3]), sc, c4.w);
+          e[j] = fmaf(__uint_as_float(v[g][j]), sc, c4.x);
+          e[j + 1] = fmaf(__uint_as_float(v[g][j + 1]), sc, c4.y);
+          e[j + 2] = fmaf(__uint_as_float(v[g][j + 2]), sc, c4.z);
+          e[j + 3] = fmaf(__uint_as_float(v[g][j + 3]), sc, c4.w);
           gm = fmaxf(gm, fmaxf(fmaxf(e[j], e[j + 1]), fmaxf(e[j + 2], e[j + 3])));
         }
+        if (gm == -INFINITY) continue;  // every column of the group lies past K
         if (gm > m) {
           ssum *= exp2f(m - gm);
           m = gm;
@@ -422,11 +441,17 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         }
         ssum += s0 + s1;
       }
-      tc_fence_before();
-      mbar_arrive(&sfree[b]);
     }
     if (!ok) set_timeout(D);
-    if (ok && k < K) D.lam[nd.off_nk + k] = (m + log2f(ssum)) * kLn2 - 0.5f * nrm * iv;
+    m_h[h][r] = m;
+    s_h[h][r] = ssum;
+    sync_math();
+    if (h == 0 && ok && k < K) {
+      const float m0 = m_h[0][r], m1 = m_h[1][r];
+      const float M = fmaxf(m0, m1);
+      const float S = s_h[0][r] * exp2f(m0 - M) + (m1 == -INFINITY ? 0.f : s_h[1][r] * exp2f(m1 - M));
+      D.lam[nd.off_nk + k] = (M + log2f(S)) * kLn2 - 0.5f * nrm_all * iv;
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -438,6 +463,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 
 // =======================================================================================
 // Adjoint edge kernel.
+// TMEM: S double buffer [0,256), V [256, 256+DP), P double buffer [384, 512) (fp16 pairs).
 // =======================================================================================
 template <int DP>
 __global__ void __launch_bounds__(kThreadsTc, 1)
@@ -447,6 +473,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   constexpr int TB = kRows * DP * 2;
   constexpr int NB = DP / 64;
   constexpr int KS = DP / 16;
+  constexpr int GH = DP / 64;
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   unsigned char* sAH = sm;            // A' = Z~_i W_i split (K-major)
@@ -459,10 +486,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   unsigned char* eZL = ring + TB + kBox;     // Z~_i tile lo
   unsigned char* eQZ = ring + 2 * TB + kBox; // q z~ tile (A of M2, 2 atoms)
   unsigned char* eSV = sm;                   // V tile (A of G, 2 atoms)
-  __shared__ uint64_t bar_pro, bar_mu, bar_A, full[2], empty[2], sfull[2], pready[2], sfree[2];
+  __shared__ uint64_t bar_pro, bar_mu, bar_A, full[2], empty[2], sfull[2], sfree[2], pready[2], pfree[2];
   __shared__ uint64_t bar_v, bar_etma, bar_eready, bar_gm;
   __shared__ uint32_t tbase;
-  __shared__ float cv[kTcMaxD];
+  __shared__ float q_h[2][kRows];
 
   const Tile t = tiles[blockIdx.x];
   const NodeInfo nd = D.nodes[t.node];
@@ -475,17 +502,18 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   if (threadIdx.x == 0) {
     mbar_init(&bar_pro, 1);
     mbar_init(&bar_mu, 1);
-    mbar_init(&bar_A, 128);
+    mbar_init(&bar_A, kMath);
     mbar_init(&bar_v, 1);
     mbar_init(&bar_etma, 1);
-    mbar_init(&bar_eready, 128);
+    mbar_init(&bar_eready, kMath);
     mbar_init(&bar_gm, 1);
     for (int i = 0; i < 2; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
       mbar_init(&sfull[i], 1);
-      mbar_init(&pready[i], 128);
-      mbar_init(&sfree[i], 1);
+      mbar_init(&sfree[i], kMath);
+      mbar_init(&pready[i], kMath);
+      mbar_init(&pfree[i], 1);
     }
     fence_barrier_init();
   }
@@ -493,7 +521,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tb = tbase;
-  const uint32_t tS[2] = {tb, tb + 128}, tV = tb + 256, tG = tb, tM2 = tb + 128;
+  const uint32_t tS[2] = {tb, tb + 128}, tV = tb + 256, tP[2] = {tb + 384, tb + 448};
+  const uint32_t tG = tb, tM2 = tb + 128;
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------------ TMA producer
@@ -566,11 +595,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         if (!mbar_wait(&pready[b], (cp >> 1) & 1)) { ok = false; break; }
         tc_fence_after();
         unsigned char* bh = ring + s * 2 * TB;
-        // V[k'][:] += sum_k P[k'][k] z~_p^k   (P: fp16 in the S buffer, 2 per column)
+        // V[k'][:] += sum_k P[k'][k] z~_p^k   (P: fp16 pairs in tensor memory)
         for (int kk = 0; kk < kRows / 16; ++kk)
-          mma_ts(tV, tS[b] + kk * 8, mndesc(bh, kk), id_v, (cp > 0 || kk > 0) ? 1u : 0u);
+          mma_ts(tV, tP[b] + kk * 8, mndesc(bh, kk), id_v, (cp > 0 || kk > 0) ? 1u : 0u);
         mma_commit(&empty[s]);
-        mma_commit(&sfree[b]);
+        mma_commit(&pfree[b]);
       }
     }
     mma_commit(&bar_v);
@@ -593,33 +622,30 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     }
   } else if (warp >= 4) {
     // ------------------------------------------------------------------ exponentials
-    const int r = threadIdx.x - 128;
-    const uint32_t lane_off = (uint32_t)((warp - 4) * 32) << 16;
-    const int kq = t.row0 + r;  // child sample owned by this thread
+    const int mt = threadIdx.x - 128;
+    const int qd = warp & 3, h = (warp - 4) >> 2;
+    const int r = 32 * qd + lane;
+    const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
+    const int kq = t.row0 + r;  // child sample owned by this thread's row
     const bool valid = kq < K;
     // column (parent sample) terms: (log q_p - lam_i - |mu~|^2 / (2 var)) log2 e
-    for (int j = r; j < nch * kRows; j += 128) {
+    for (int j = mt; j < nch * kRows; j += kMath) {
       float a = -INFINITY;
       if (j < K)
         a = (logf(D.q[pn.off_nk + j]) - D.lam[nd.off_nk + j] - 0.5f * D.mun[nd.off_nk + j] * iv) * kLog2e;
       ak[j] = a;
     }
-    for (int j = r; j < kLdp; j += 128) cv[j] = T.cvec[(long long)t.node * kLdp + j];
-    sync_math();
     // row term: (beta_i - |z~|^2 / (2 var) + z~ . c_i / var) log2 e
-    float crow = -INFINITY;
-    if (valid) {
-      const float* e = D.eps + nd.off_nkd + (long long)kq * d;
-      float zc = 0.f;
-      for (int j = 0; j < d; ++j) zc = fmaf(expf(D.q_logstd[nd.off_q + j]) * e[j], cv[j], zc);
-      crow = (D.beta[nd.off_nk + kq] - 0.5f * D.zn[nd.off_nk + kq] * iv + zc * iv) * kLog2e;
-    }
-    // prologue result A' = Z~_i W_i -> split A operand
+    const float crow = valid ? (D.beta[nd.off_nk + kq] - 0.5f * D.zn[nd.off_nk + kq] * iv +
+                                T.zc[nd.off_nk + kq] * iv) * kLog2e
+                             : -INFINITY;
+    // prologue result A' = Z~_i W_i -> this half of the split A operand
     bool ok = mbar_wait(&bar_mu, 0);
     if (ok) {
       tc_fence_after();
 #pragma unroll 1
-      for (int g = 0; g < DP / 32; ++g) {
+      for (int gg = 0; gg < GH; ++gg) {
+        const int g = h * GH + gg;
         uint32_t v[32];
         tmem_ld32(tS[0] + lane_off + g * 32, v);
         tmem_wait_ld();
@@ -633,52 +659,56 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       tc_fence_before();
     }
     mbar_arrive(&bar_A);
+    sync_math();  // ak complete
     const float sc = iv * kLog2e;
     float qacc = 0.f;
     for (int c = 0; ok && c < nch; ++c) {
       const int b = c & 1;
       if (!mbar_wait(&sfull[b], (c >> 1) & 1)) { ok = false; break; }
       tc_fence_after();
-      const float* akc = ak + c * kRows;
-#pragma unroll 1
-      for (int g = 0; g < 4; ++g) {
-        uint32_t v[32];
-        tmem_ld32(tS[b] + lane_off + g * 32, v);
-        tmem_wait_ld();
-        uint32_t pk[16];
-        float s0 = 0.f;
+      uint32_t v[2][32];
+      tmem_ld32(tS[b] + lane_off + 64 * h, v[0]);
+      tmem_ld32(tS[b] + lane_off + 64 * h + 32, v[1]);
+      tmem_wait_ld();
+      tc_fence_before();
+      mbar_arrive(&sfree[b]);
+      const float* akc = ak + c * kRows + 64 * h;
+      uint32_t pk[32];
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
 #pragma unroll
         for (int j = 0; j < 32; j += 4) {
           const float4 a4 = *reinterpret_cast<const float4*>(akc + g * 32 + j);
-          const float p0 = exp2f(fmaf(__uint_as_float(v[j]), sc, crow + a4.x));
-          const float p1 = exp2f(fmaf(__uint_as_float(v[j + 1]), sc, crow + a4.y));
-          const float p2 = exp2f(fmaf(__uint_as_float(v[j + 2]), sc, crow + a4.z));
-          const float p3 = exp2f(fmaf(__uint_as_float(v[j + 3]), sc, crow + a4.w));
-          s0 += (p0 + p1) + (p2 + p3);
-          pk[j / 2] = pack_half2(p0, p1);
-          pk[j / 2 + 1] = pack_half2(p2, p3);
+          const float p0 = exp2f(fmaf(__uint_as_float(v[g][j]), sc, crow + a4.x));
+          const float p1 = exp2f(fmaf(__uint_as_float(v[g][j + 1]), sc, crow + a4.y));
+          const float p2 = exp2f(fmaf(__uint_as_float(v[g][j + 2]), sc, crow + a4.z));
+          const float p3 = exp2f(fmaf(__uint_as_float(v[g][j + 3]), sc, crow + a4.w));
+          s0 += p0 + p1;
+          s1 += p2 + p3;
+          pk[g * 16 + j / 2] = pack_half2(p0, p1);
+          pk[g * 16 + j / 2 + 1] = pack_half2(p2, p3);
         }
-        qacc += s0;
-        // P columns 16g .. 16g+15 of this buffer (the S values there were read already)
-        asm volatile(
-            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%"
-            "13,%14,%15,%16};" ::"r"(tS[b] + lane_off + g * 16),
-            "r"(pk[0]), "r"(pk[1]), "r"(pk[2]), "r"(pk[3]), "r"(pk[4]), "r"(pk[5]), "r"(pk[6]),
-            "r"(pk[7]), "r"(pk[8]), "r"(pk[9]), "r"(pk[10]), "r"(pk[11]), "r"(pk[12]), "r"(pk[13]),
-            "r"(pk[14]), "r"(pk[15])
-            : "memory");
       }
+      qacc += s0 + s1;
+      if (c >= 2 && !mbar_wait(&pfree[b], ((c >> 1) + 1) & 1)) { ok = false; break; }
+      tc_fence_after();
+      tmem_st32(tP[b] + lane_off + 32 * h, pk);
       tmem_wait_st();
       tc_fence_before();
       mbar_arrive(&pready[b]);
     }
-    if (ok && valid) D.q[nd.off_nk + kq] = qacc;
-    // epilogue: V row -> fp16 A tile of G; q z~ row -> A tile of M2; ones atom row
+    q_h[h][r] = qacc;
+    sync_math();
+    const float qtot = q_h[0][r] + q_h[1][r];
+    if (ok && valid && h == 0) D.q[nd.off_nk + kq] = qtot;
+    // epilogue: V row -> fp16 A tile of G; q z~ row -> A tile of M2; ones atom
     if (ok) ok = mbar_wait(&bar_v, 0);
     if (ok) {
       tc_fence_after();
 #pragma unroll 1
-      for (int g = 0; g < kRows / 32; ++g) {
+      for (int gg = 0; gg < 2; ++gg) {
+        const int g = 2 * h + gg;  // 32-column group of the 128-wide tile
         float f[32];
         if (g < DP / 32) {
           uint32_t v[32];
@@ -696,16 +726,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       ok = mbar_wait(&bar_etma, 0);
     }
     if (ok) {
-      const float qv = valid ? qacc : 0.f;
+      const float qv = valid ? qtot : 0.f;
 #pragma unroll 1
-      for (int ch = 0; ch < kRows / 8; ++ch) {
+      for (int ch = 8 * h; ch < 8 * h + 8; ++ch) {
         float f[8];
         if (ch < DP / 8) {
-          float h[8], l[8];
-          load_half8(eZH, r, ch, h);
-          load_half8(eZL, r, ch, l);
+          float hv[8], lv[8];
+          load_half8(eZH, r, ch, hv);
+          load_half8(eZL, r, ch, lv);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) f[j] = qv * (h[j] + l[j]);
+          for (int j = 0; j < 8; ++j) f[j] = qv * (hv[j] + lv[j]);
         } else {
 #pragma unroll
           for (int j = 0; j < 8; ++j) f[j] = 0.f;
@@ -713,9 +743,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         store_half8(eQZ, r, ch, f);
       }
       // ones atom row r: element 0 = 1, the rest 0
-      float o8[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      store_half8(eOnes, r, 0, o8);
-      for (int ch = 1; ch < 8; ++ch) store_half8(eOnes, r, ch, z8);
+      for (int ch = 4 * h; ch < 4 * h + 4; ++ch) {
+        float o8[8] = {ch == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        store_half8(eOnes, r, ch, o8);
+      }
       fence_proxy_async_smem();
       tc_fence_before();
     }
@@ -723,12 +754,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     if (ok) ok = mbar_wait(&bar_gm, 0);
     if (ok) {
       tc_fence_after();
-      const int a = r;  // TMEM lane = output row a (latent dimension of the parent / node)
+      const int a = r;  // TMEM lane = output row a
       const bool arow = a < d;
       float* Gi = T.G + (long long)t.node * kLdp * kLdp + (long long)a * kLdp;
       float* Mi = T.M2 + (long long)t.node * kLdp * kLdp + (long long)a * kLdp;
 #pragma unroll 1
-      for (int g = 0; g < DP / 32; ++g) {
+      for (int gg = 0; gg < GH; ++gg) {
+        const int g = h * GH + gg;
         uint32_t v[32];
         tmem_ld32(tG + lane_off + g * 32, v);
         tmem_wait_ld();
@@ -737,10 +769,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         tmem_wait_ld();
         if (arow) red_add_row32(Mi + g * 32, v, d - g * 32);
       }
-      uint32_t v[32];
-      tmem_ld32(tM2 + lane_off + DP, v);  // column DP: sum_k' q z~[k'][a]
-      tmem_wait_ld();
-      if (arow) atomicAdd(T.zbar + (long long)t.node * kLdp + a, __uint_as_float(v[0]));
+      if (h == 0) {
+        uint32_t v[32];
+        tmem_ld32(tM2 + lane_off + DP, v);  // column DP: sum_k' q z~[k'][a]
+        tmem_wait_ld();
+        if (arow) atomicAdd(T.zbar + (long long)t.node * kLdp + a, __uint_as_float(v[0]));
+      }
     }
     if (!ok) set_timeout(D);
   }
@@ -1122,6 +1156,7 @@ void workspace_layout(TcWork& w, const std::vector<NodeInfo>& nodes, long long n
   const size_t nm = (size_t)w.num_nodes * kLdp * kLdp * sizeof(float);
   subs.push_back({(void**)&w.t.ZH, pk});
   subs.push_back({(void**)&w.t.ZL, pk});
+  subs.push_back({(void**)&w.t.zc, (size_t)nk * sizeof(float)});
   subs.push_back({(void**)&w.t.WH, pw});
   subs.push_back({(void**)&w.t.WL, pw});
   subs.push_back({(void**)&w.t.WTH, pw});
@@ -1195,7 +1230,7 @@ void release(TcWork& w) {
 }
 
 void launch_sample(TcWork& w, const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s) {
-  if (ntiles) k_sample_tc<<<ntiles, 256, 2 * kTcMaxD * sizeof(float), s>>>(D, w.t, tiles);
+  if (ntiles) k_sample_tc<<<ntiles, 256, 3 * kTcMaxD * sizeof(float), s>>>(D, w.t, tiles);
 }
 
 void launch_pack(TcWork& w, const Dev& D, cudaStream_t s) {

@@ -380,15 +380,17 @@ tmc_status tmc_log_marginal(tmc_plan p, const tmc_inputs* in, double* log_phat, 
   const Tile* T = p->d_tiles;
   const bool tc_path = p->precision != TMC_PREC_FP32;
   TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_node_const(D, s); }));
-  if (tc_path)
-    TRY(timed(p, TMC_KC_SAMPLE, s, [&] { tc::launch_sample(p->tcw, D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
-  else
-    TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_sample(D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
-  TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_obs_fwd(D, T + p->t_leaf_b, p->t_leaf_e - p->t_leaf_b, s); }));
-  if (tc_path)  // the conditional means are formed inside the edge kernels
+  if (tc_path) {
+    // split W_i and c_i first: the sampling kernel forms z~ . c_i, the conditional means are
+    // formed inside the edge kernels
     TRY(timed(p, TMC_KC_PROJECT, s, [&] { tc::launch_pack(p->tcw, D, s); }));
-  else
+    TRY(timed(p, TMC_KC_SAMPLE, s, [&] { tc::launch_sample(p->tcw, D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
+    TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_obs_fwd(D, T + p->t_leaf_b, p->t_leaf_e - p->t_leaf_b, s); }));
+  } else {
+    TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_sample(D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
+    TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_obs_fwd(D, T + p->t_leaf_b, p->t_leaf_e - p->t_leaf_b, s); }));
     TRY(timed(p, TMC_KC_PROJECT, s, [&] { launch_project(D, T + p->t_proj_b, p->t_proj_e - p->t_proj_b, s); }));
+  }
   for (int L = p->maxlevel; L >= 1; --L) {
     const int b = p->t_level_b[L], e = p->t_level_e[L];
     if (tc_path)

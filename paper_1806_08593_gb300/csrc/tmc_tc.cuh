@@ -29,6 +29,7 @@ struct TcSub {
 // Device pointers of the tensor-core path (part of the plan's workspace).
 struct TcDev {
   __half *ZH, *ZL;             // [rows][128] split centred samples, row = node.off_nk + k
+  float* zc;                   // [nk]  z~_i^k . c_i  (row term of the adjoint exponent)
   __half *WH, *WL;             // [slots*128][128] split W_i   ([r][c])
   __half *WTH, *WTL;           // [slots*128][128] split W_i^T ([c][r])
   float* cvec;                 // [nodes][128]  c_i = W_i m_p + bias_i - m_i
