@@ -121,6 +121,27 @@ tmc_status tmc_log_marginal(tmc_plan plan, const tmc_inputs* in, double* log_pha
 tmc_status tmc_backward(tmc_plan plan, const tmc_inputs* in, const double* grad_out,
                         const tmc_grads* grads, void* stream);
 
+/* log P_TMC per instance for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of tmc_log_marginal (FP32 path, forward only).
+ * It is for code that must not call cudaMalloc -- running inside a real-time loop, under a
+ * memory pool that owns the whole device, or in a host process whose allocator is not
+ * CUDA's -- and so cannot hold a plan.  It takes no plan: the description (HOST memory, as
+ * for tmc_plan_create, precision TMC_PREC_FP32) and the DEVICE inputs / output are passed
+ * per call, and all scratch lives in one fixed-size file-scope device array of 10,330,368
+ * bytes (~9.9 MiB) that every GPU running this call holds until the process exits.  Nothing
+ * here calls cudaMalloc, cudaFree or any allocating routine.
+ *   Limits of one call: at most 2048 latents and 1024 instances in total, sum of n_b*K_b <=
+ *   65536, sum of n_b*K_b*d_b <= 1048576, 8192 64-sample tiles; beyond them the call returns
+ *   TMC_ERR_UNSUPPORTED before any device work.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress with
+ *   that device current); make that first call before any stream capture.
+ *   Every call reuses the same array, and its contents are left from the last call: calls
+ *   whose GPU work overlaps (different streams or host threads) race and must be serialised.
+ *   Device-side numeric errors are not reported; a non-finite input gives a non-finite result.
+ * log_phat: DEVICE double[B], written on `stream`. */
+tmc_status tmc_log_marginal_noalloc(const tmc_problem_desc* desc, const tmc_inputs* in,
+                                    double* log_phat, void* stream);
+
 /* Waits for the plan's outstanding work on `stream` and reports device-side errors recorded
  * since the last call (TMC_ERR_NUMERIC for non-finite values, TMC_ERR_TIMEOUT), clearing
  * them.  TMC_OK if none. */

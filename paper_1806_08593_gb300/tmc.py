@@ -25,7 +25,7 @@ STATUS = {0: "TMC_OK", 1: "TMC_ERR_INVALID_ARG", 2: "TMC_ERR_UNSUPPORTED", 3: "T
 KERNEL_CLASSES = ["sample", "project", "edge_fwd", "root", "edge_bwd", "param"]
 EXPORTS = ["tmc_plan_create", "tmc_log_marginal", "tmc_backward", "tmc_plan_sync_status",
            "tmc_plan_workspace_bytes", "tmc_plan_destroy", "tmc_status_string",
-           "tmc_profile_enable", "tmc_profile_read"]
+           "tmc_profile_enable", "tmc_profile_read", "tmc_log_marginal_noalloc"]
 
 
 class TMCError(RuntimeError):
@@ -76,8 +76,10 @@ def load_library(path: str = LIB_PATH):
     lib.tmc_profile_enable.argtypes = [P, ctypes.c_int]
     lib.tmc_profile_read.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_longlong)]
+    lib.tmc_log_marginal_noalloc.argtypes = [ctypes.POINTER(ProblemDesc), ctypes.POINTER(Inputs), P, V]
     for f in ("tmc_plan_create", "tmc_log_marginal", "tmc_backward", "tmc_plan_sync_status",
-              "tmc_plan_workspace_bytes", "tmc_plan_destroy", "tmc_profile_enable", "tmc_profile_read"):
+              "tmc_plan_workspace_bytes", "tmc_plan_destroy", "tmc_profile_enable", "tmc_profile_read",
+              "tmc_log_marginal_noalloc"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -193,6 +195,24 @@ class Plan:
                    "tmc_profile_read")
             res[name] = (ms.value, n.value)
         return res
+
+
+def log_marginal_noalloc(p, t: dict, out=None, stream=None):
+    """log P_TMC (FP32 path, forward only) through tmc_log_marginal_noalloc: for callers that
+    cannot allocate device memory.  ``p`` supplies the description (a workload.Problem or
+    anything with n, parent, K, d, obs, shared, prior_var, obs_var); ``t`` the CUDA inputs.
+    ``out`` must be preallocated by such callers; if omitted, torch allocates it here."""
+    import torch
+    lib = load_library()
+    keep = [np.ascontiguousarray(a, dtype=np.int32) for a in (p.n, p.parent, p.K, p.d, p.obs)]
+    desc = ProblemDesc(len(keep[0]), *[a.ctypes.data for a in keep], int(bool(p.shared)),
+                       float(p.prior_var), float(p.obs_var), PRECISIONS["fp32"])
+    if out is None:
+        out = torch.empty(len(keep[0]), dtype=torch.float64, device=t["eps"].device)
+    inp = Inputs(*[_ptr(t[k]) for k in INPUT_NAMES])
+    _check(lib.tmc_log_marginal_noalloc(ctypes.byref(desc), ctypes.byref(inp), _ptr(out), _stream(stream)),
+           "tmc_log_marginal_noalloc")
+    return out
 
 
 def _autograd():
