@@ -39,6 +39,7 @@ constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 constexpr int kThreadsTc = 384;  // 4 control warps + 8 math warps
 constexpr int kMath = 256;       // math threads
+constexpr int kJt = kTcMaxK / kMath;  // per-thread share of a K-long prologue vector
 constexpr int kBox = 16384;  // bytes of one 128-row x 128-byte swizzled box
 
 __device__ __forceinline__ int slot_of(const Dev& D, const NodeInfo& nd, int g) {
@@ -85,6 +86,27 @@ __device__ __forceinline__ void load_half8(const unsigned char* t, int r, int ch
   }
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%"
+      "15,%16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+
+// 32 FP32 values -> split fp16 pairs packed two per 32-bit word (hi[16], lo[16]).
+__device__ __forceinline__ void split_pack32(const float* f, uint32_t* hi, uint32_t* lo) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    float h0, l0, h1, l1;
+    split_half(f[2 * q], h0, l0);
+    split_half(f[2 * q + 1], h1, l1);
+    hi[q] = pack_half2(h0, h1);
+    lo[q] = pack_half2(l0, l1);
+  }
+}
+
 // K-major descriptor of K-step kk (16 fp16) of a [rows x DP] swizzled tile.
 __device__ __forceinline__ uint64_t kdesc(const unsigned char* base, int kk) {
   return smem_desc_sw128(smem_u32(base) + (kk >> 2) * kBox + (kk & 3) * 32, 16, 1024);
@@ -95,6 +117,27 @@ __device__ __forceinline__ uint64_t mndesc(const unsigned char* base, int kk) {
 }
 
 __device__ __forceinline__ void set_timeout(const Dev& D) { atomicOr(D.err, kErrTimeout); }
+
+// Cross-CTA completion counters of the persistent edge kernels (per node, per launch).
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Bounded wait until *p >= need (about a second of polling); false on timeout.
+__device__ __forceinline__ bool wait_count(const int* p, int need) {
+  if (ld_acquire(p) >= need) return true;
+  const long long t0 = clock64();
+  while (ld_acquire(p) < need) {
+    if (clock64() - t0 > (1ll << 31)) return false;
+    __nanosleep(64);
+  }
+  return true;
+}
+__host__ __device__ constexpr int tiles_of(int K) { return (K + kRows - 1) / kRows; }
 
 // dst[0..n) += v[0..n) for n <= 32 (16-byte vector reductions where the row is complete).
 __device__ __forceinline__ void red_add_row32(float* dst, const uint32_t (&v)[32], int n) {
@@ -112,8 +155,9 @@ __device__ __forceinline__ void red_add_row32(float* dst, const uint32_t (&v)[32
 // Bytes of the streaming ring: two stages of (hi, lo) sample tiles, and large enough for the
 // adjoint epilogue (Z~ hi, ones atom, Z~ lo, q z~ tile of two atoms).
 __host__ __device__ constexpr int ring_bytes(int DP) {
-  return (4 * kRows * DP * 2 > 2 * kRows * DP * 2 + 3 * kBox) ? 4 * kRows * DP * 2
-                                                              : 2 * kRows * DP * 2 + 3 * kBox;
+  // epilogue: Z~ hi (TB), ones atom, Z~ lo (TB), q z~ tile (2 atoms), V tile (2 atoms)
+  return (4 * kRows * DP * 2 > 2 * kRows * DP * 2 + 5 * kBox) ? 4 * kRows * DP * 2
+                                                              : 2 * kRows * DP * 2 + 5 * kBox;
 }
 }  // namespace
 
@@ -239,41 +283,57 @@ __global__ void k_pack_c(Dev D, TcDev T, const int* __restrict__ nonroot) {
 // =======================================================================================
 template <int DP>
 __global__ void __launch_bounds__(kThreadsTc, 1)
-    k_edge_fwd_tc(Dev D, TcDev T, const Tile* __restrict__ tiles,
+    k_edge_fwd_tc(Dev D, TcDev T, const Tile* __restrict__ tiles, int ntiles, int* __restrict__ done,
                   const __grid_constant__ CUtensorMap mZH, const __grid_constant__ CUtensorMap mZL,
                   const __grid_constant__ CUtensorMap mWH, const __grid_constant__ CUtensorMap mWL) {
   constexpr int TB = kRows * DP * 2;  // bytes of one [128 x DP] fp16 tile
   constexpr int NB = DP / 64;         // 64-column boxes per tile
   constexpr int KS = DP / 16;         // K-steps over the latent dimension
   constexpr int GH = DP / 64;         // 32-column groups of the latent dimension per half
+  constexpr int NS = 3;               // ring stages
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sAH = sm;
-  unsigned char* sAL = sm + TB;
-  unsigned char* ring = sm + 2 * TB;  // 2 stages x (hi, lo)
-  float* cb = reinterpret_cast<float*>(ring + ring_bytes(DP));
-  __shared__ uint64_t bar_pro, bar_mu, bar_A, full[2], empty[2], sfull[2], sfree[2], bar_done;
+  unsigned char* ring = sm;           // NS stages x (hi, lo)
+  float* cb = reinterpret_cast<float*>(ring + NS * 2 * TB);
+  __shared__ uint64_t bar_pro, bar_mu, bar_A, full[NS], empty[NS], sfull[2], sfree[2], bar_done;
   __shared__ uint32_t tbase;
   __shared__ float red[8];
   __shared__ float cv[kTcMaxD];
   __shared__ float nrm_h[2][kRows], m_h[2][kRows], s_h[2][kRows];
 
-  const Tile t = tiles[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float iv = D.inv_var;
+  if (warp == 2) tmem_alloc(&tbase, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tb = tbase;
+  // TMEM: S double buffer [0,256), mu~ accumulator [256,384), A operand hi [384,448) lo [448,512)
+  const uint32_t tS[2] = {tb, tb + 128}, tMU = tb + 256, tAH = tb + 384, tAL = tb + 448;
+
+  // persistent loop over the edge tiles of every level, deepest level first
+  for (int item = blockIdx.x; item < ntiles; item += gridDim.x) {
+  const Tile t = tiles[item];
   const NodeInfo nd = D.nodes[t.node];
   const NodeInfo pn = D.nodes[nd.parent];
   const int K = nd.K, nch = (K + kRows - 1) / kRows;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const float iv = D.inv_var;
-
-  if (warp == 2) tmem_alloc(&tbase, 512);
   if (threadIdx.x == 0) {
+    // every child of the edge's child node must have sent its message (all its tiles)
+    bool dep_ok = true;
+    for (int c = nd.child_begin; c < nd.child_end; ++c) {
+      const int cg = D.children[c];
+      dep_ok = wait_count(done + cg, tiles_of(D.nodes[cg].K)) && dep_ok;
+    }
+    if (!dep_ok) set_timeout(D);
     mbar_init(&bar_pro, 1);
     mbar_init(&bar_mu, 1);
     mbar_init(&bar_A, kMath);
     mbar_init(&bar_done, 1);
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < NS; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(&sfull[i], 1);
       mbar_init(&sfree[i], kMath);
     }
@@ -282,13 +342,17 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tb = tbase;
-  const uint32_t tS[2] = {tb, tb + 128}, tMU = tb + 256;
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------------ TMA producer
     prefetch_tmap(&mZH);
     prefetch_tmap(&mZL);
+    // The 8 row tiles of an edge walk the child's chunks in the same order; each CTA pulls
+    // "its" chunk (index = its row tile) into L2 up front so the ring loads hit L2.
+    for (int b = 0; b < NB; ++b) {
+      tma_prefetch_l2_2d(&mZH, b * 64, (int)(nd.off_nk + t.row0));
+      tma_prefetch_l2_2d(&mZL, b * 64, (int)(nd.off_nk + t.row0));
+    }
     const int slot = slot_of(D, nd, t.node);
     mbar_arrive_expect_tx(&bar_pro, 4 * TB);
     for (int b = 0; b < NB; ++b) {
@@ -301,8 +365,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     bool ok = mbar_wait(&bar_mu, 0);  // prologue MMAs have read the ring
     int issued = 0;
     for (int c = 0; ok && c < nch; ++c) {
-      const int s = c & 1;
-      if (c >= 2 && !mbar_wait(&empty[s], ((c >> 1) + 1) & 1)) { ok = false; break; }
+      const int s = c % NS;
+      if (c >= NS && !mbar_wait(&empty[s], ((c / NS) + 1) & 1)) { ok = false; break; }
       unsigned char* st = ring + s * 2 * TB;
       mbar_arrive_expect_tx(&full[s], 2 * TB);
       const int row = (int)(nd.off_nk + c * kRows);
@@ -313,7 +377,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       issued = c + 1;
     }
     if (!ok) set_timeout(D);
-    for (int c = (issued > 2 ? issued - 2 : 0); c < issued; ++c) mbar_wait(&full[c & 1], (c >> 1) & 1);
+    for (int c = (issued > NS ? issued - NS : 0); c < issued; ++c) mbar_wait(&full[c % NS], (c / NS) & 1);
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------------ MMA issuer
     bool ok = mbar_wait(&bar_pro, 0);
@@ -329,14 +393,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     }
     const uint32_t id_s = idesc_f16(kRows, kRows, false, false, false);
     for (int c = 0; ok && c < nch; ++c) {
-      const int s = c & 1, b = c & 1;
-      if (!mbar_wait(&full[s], (c >> 1) & 1)) { ok = false; break; }
+      const int s = c % NS, b = c & 1;
+      if (!mbar_wait(&full[s], (c / NS) & 1)) { ok = false; break; }
       if (c >= 2 && !mbar_wait(&sfree[b], ((c >> 1) + 1) & 1)) { ok = false; break; }
       tc_fence_after();
       unsigned char *bh = ring + s * 2 * TB, *bl = bh + TB;
-      for (int kk = 0; kk < KS; ++kk) mma_ss(tS[b], kdesc(sAH, kk), kdesc(bh, kk), id_s, kk > 0);
-      for (int kk = 0; kk < KS; ++kk) mma_ss(tS[b], kdesc(sAL, kk), kdesc(bh, kk), id_s, 1);
-      for (int kk = 0; kk < KS; ++kk) mma_ss(tS[b], kdesc(sAH, kk), kdesc(bl, kk), id_s, 1);
+      // S = (A_hi + A_lo)(B_hi + B_lo)^T without lo*lo; A from tensor memory (2 fp16 / column)
+      for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kdesc(bh, kk), id_s, kk > 0);
+      for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAL + kk * 8, kdesc(bh, kk), id_s, 1);
+      for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kdesc(bl, kk), id_s, 1);
       mma_commit(&sfull[b]);
       mma_commit(&empty[s]);
     }
@@ -350,13 +415,28 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     const int r = 32 * qd + lane;               // tile row = TMEM lane
     const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
     const int k = t.row0 + r;
-    float mx = -INFINITY;
-    for (int j = mt; j < K; j += kMath) {
-      float v = D.u[nd.off_nk + j];
-      for (int c = nd.child_begin; c < nd.child_end; ++c) v += D.lam[D.nodes[D.children[c]].off_nk + j];
-      cb[j] = v;
-      mx = fmaxf(mx, v);
+    // beta_i over all K child samples: every load of this thread is issued before any use
+    // (the prologue is latency-bound otherwise); child message offsets are read once.
+    float bv[kJt], zv[kJt];
+#pragma unroll
+    for (int i = 0; i < kJt; ++i) {
+      const int j = mt + i * kMath;
+      const bool in = j < K;
+      bv[i] = in ? D.u[nd.off_nk + j] : 0.f;
+      zv[i] = in ? D.zn[nd.off_nk + j] : 0.f;
     }
+    for (int c = nd.child_begin; c < nd.child_end; ++c) {
+      const long long co = D.nodes[D.children[c]].off_nk;
+#pragma unroll
+      for (int i = 0; i < kJt; ++i) {
+        const int j = mt + i * kMath;
+        if (j < K) bv[i] += __ldcg(D.lam + co + j);  // written by other CTAs of this launch
+      }
+    }
+    float mx = -INFINITY;
+#pragma unroll
+    for (int i = 0; i < kJt; ++i)
+      if (mt + i * kMath < K) mx = fmaxf(mx, bv[i]);
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) red[warp - 4] = mx;
     for (int j = mt; j < kLdp; j += kMath) cv[j] = T.cvec[(long long)t.node * kLdp + j];
@@ -365,11 +445,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 #pragma unroll
     for (int i = 1; i < 8; ++i) mx = fmaxf(mx, red[i]);
     const bool store = (t.row0 == 0);
-    for (int j = mt; j < nch * kRows; j += kMath) {
+#pragma unroll
+    for (int i = 0; i < kJt; ++i) {
+      const int j = mt + i * kMath;
+      if (j >= nch * kRows) break;
       if (j < K) {
-        const float bb = cb[j] - mx;
+        const float bb = bv[i] - mx;
         if (store) D.beta[nd.off_nk + j] = bb;
-        cb[j] = (bb - 0.5f * D.zn[nd.off_nk + j] * iv) * kLog2e;
+        cb[j] = (bb - 0.5f * zv[i] * iv) * kLog2e;
       } else {
         cb[j] = -INFINITY;
       }
@@ -392,10 +475,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           f[j] = __uint_as_float(v[j]) + cv[g * 32 + j];
           nrm = fmaf(f[j], f[j], nrm);
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) store_split8(sAH, sAL, r, g * 4 + q, f + 8 * q);
+        uint32_t hi[16], lo[16];
+        split_pack32(f, hi, lo);
+        tmem_st16(tAH + lane_off + g * 16, hi);
+        tmem_st16(tAL + lane_off + g * 16, lo);
       }
-      fence_proxy_async_smem();
+      tmem_wait_st();
       tc_fence_before();
     }
     nrm_h[h][r] = nrm;
@@ -430,14 +515,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         }
         if (gm == -INFINITY) continue;  // every column of the group lies past K
         if (gm > m) {
-          ssum *= exp2f(m - gm);
+          ssum *= ex2_ftz(m - gm);
           m = gm;
         }
         float s0 = 0.f, s1 = 0.f;
 #pragma unroll
         for (int j = 0; j < 32; j += 2) {
-          s0 += exp2f(e[j] - m);
-          s1 += exp2f(e[j + 1] - m);
+          s0 += ex2_ftz(e[j] - m);
+          s1 += ex2_ftz(e[j + 1] - m);
         }
         ssum += s0 + s1;
       }
@@ -449,12 +534,17 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     if (h == 0 && ok && k < K) {
       const float m0 = m_h[0][r], m1 = m_h[1][r];
       const float M = fmaxf(m0, m1);
-      const float S = s_h[0][r] * exp2f(m0 - M) + (m1 == -INFINITY ? 0.f : s_h[1][r] * exp2f(m1 - M));
+      const float S = s_h[0][r] * ex2_ftz(m0 - M) + (m1 == -INFINITY ? 0.f : s_h[1][r] * ex2_ftz(m1 - M));
       D.lam[nd.off_nk + k] = (M + log2f(S)) * kLn2 - 0.5f * nrm_all * iv;
     }
+    __threadfence();  // messages visible device-wide before the completion count moves
   }
+  // item end: every role is done with this item's barriers, tensor memory and ring
   tc_fence_before();
   __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x == 0) red_release_add(done + t.node, 1);
+  }  // items
   if (warp == 2) {
     tc_fence_after();
     tmem_dealloc(tb, 512);
@@ -467,7 +557,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 // =======================================================================================
 template <int DP>
 __global__ void __launch_bounds__(kThreadsTc, 1)
-    k_edge_bwd_tc(Dev D, TcDev T, const Tile* __restrict__ tiles,
+    k_edge_bwd_tc(Dev D, TcDev T, const Tile* __restrict__ tiles, int ntiles, int* __restrict__ done,
                   const __grid_constant__ CUtensorMap mZH, const __grid_constant__ CUtensorMap mZL,
                   const __grid_constant__ CUtensorMap mWTH, const __grid_constant__ CUtensorMap mWTL) {
   constexpr int TB = kRows * DP * 2;
@@ -476,30 +566,40 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   constexpr int GH = DP / 64;
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sAH = sm;            // A' = Z~_i W_i split (K-major)
-  unsigned char* sAL = sm + TB;
-  unsigned char* ring = sm + 2 * TB;  // 2 stages x (hi, lo) of parent sample chunks
+  unsigned char* sAL = sm;            // lo part of A' = Z~_i W_i (K-major); hi part is in TMEM
+  unsigned char* ring = sm + TB;      // 2 stages x (hi, lo) of parent sample chunks
   float* ak = reinterpret_cast<float*>(ring + ring_bytes(DP));
   // epilogue re-use of the ring / A regions
   unsigned char* eZH = ring;                 // Z~_i tile hi  (N atoms at +0, +16K)
   unsigned char* eOnes = ring + TB;          // ones atom: directly after the Z~ atoms
   unsigned char* eZL = ring + TB + kBox;     // Z~_i tile lo
   unsigned char* eQZ = ring + 2 * TB + kBox; // q z~ tile (A of M2, 2 atoms)
-  unsigned char* eSV = sm;                   // V tile (A of G, 2 atoms)
+  unsigned char* eSV = ring + 2 * TB + 3 * kBox;  // V tile (A of G, 2 atoms)
   __shared__ uint64_t bar_pro, bar_mu, bar_A, full[2], empty[2], sfull[2], sfree[2], pready[2], pfree[2];
   __shared__ uint64_t bar_v, bar_etma, bar_eready, bar_gm;
   __shared__ uint32_t tbase;
   __shared__ float q_h[2][kRows];
 
-  const Tile t = tiles[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float iv = D.inv_var;
+  if (warp == 2) tmem_alloc(&tbase, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tb = tbase;
+  // TMEM: S double buffer [0,256), V [256,384), A'_hi [384,448), P (fp16 pairs) [448,512)
+  const uint32_t tS[2] = {tb, tb + 128}, tV = tb + 256, tAH = tb + 384, tP = tb + 448;
+  const uint32_t tG = tb, tM2 = tb + 128;
+
+  // persistent loop over the edge tiles of every level, root side first
+  for (int item = blockIdx.x; item < ntiles; item += gridDim.x) {
+  const Tile t = tiles[item];
   const NodeInfo nd = D.nodes[t.node];
   const NodeInfo pn = D.nodes[nd.parent];
   const int K = nd.K, nch = (K + kRows - 1) / kRows, d = nd.d;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const float iv = D.inv_var;
-
-  if (warp == 2) tmem_alloc(&tbase, 512);
   if (threadIdx.x == 0) {
+    // the parent's sample weights must be final (the root's come from an earlier launch)
+    if (pn.parent >= 0 && !wait_count(done + nd.parent, tiles_of(pn.K))) set_timeout(D);
     mbar_init(&bar_pro, 1);
     mbar_init(&bar_mu, 1);
     mbar_init(&bar_A, kMath);
@@ -520,14 +620,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tb = tbase;
-  const uint32_t tS[2] = {tb, tb + 128}, tV = tb + 256, tP[2] = {tb + 384, tb + 448};
-  const uint32_t tG = tb, tM2 = tb + 128;
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------------ TMA producer
     prefetch_tmap(&mZH);
     prefetch_tmap(&mZL);
+    // pull the parent's chunk with this CTA's tile index into L2 (see the forward kernel)
+    for (int b = 0; b < NB; ++b) {
+      tma_prefetch_l2_2d(&mZH, b * 64, (int)(pn.off_nk + t.row0));
+      tma_prefetch_l2_2d(&mZL, b * 64, (int)(pn.off_nk + t.row0));
+    }
     const int slot = slot_of(D, nd, t.node);
     const int own = (int)(nd.off_nk + t.row0);
     mbar_arrive_expect_tx(&bar_pro, 4 * TB);
@@ -585,21 +687,21 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         if (c >= 2 && !mbar_wait(&sfree[b], ((c >> 1) + 1) & 1)) { ok = false; break; }
         tc_fence_after();
         unsigned char *bh = ring + s * 2 * TB, *bl = bh + TB;
-        for (int kk = 0; kk < KS; ++kk) mma_ss(tS[b], kdesc(sAH, kk), kdesc(bh, kk), id_s, kk > 0);
+        for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kdesc(bh, kk), id_s, kk > 0);
         for (int kk = 0; kk < KS; ++kk) mma_ss(tS[b], kdesc(sAL, kk), kdesc(bh, kk), id_s, 1);
-        for (int kk = 0; kk < KS; ++kk) mma_ss(tS[b], kdesc(sAH, kk), kdesc(bl, kk), id_s, 1);
+        for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kdesc(bl, kk), id_s, 1);
         mma_commit(&sfull[b]);
       }
       if (c >= 1) {
-        const int cp = c - 1, s = cp & 1, b = cp & 1;
-        if (!mbar_wait(&pready[b], (cp >> 1) & 1)) { ok = false; break; }
+        const int cp = c - 1, s = cp & 1;
+        if (!mbar_wait(&pready[0], cp & 1)) { ok = false; break; }
         tc_fence_after();
         unsigned char* bh = ring + s * 2 * TB;
         // V[k'][:] += sum_k P[k'][k] z~_p^k   (P: fp16 pairs in tensor memory)
         for (int kk = 0; kk < kRows / 16; ++kk)
-          mma_ts(tV, tP[b] + kk * 8, mndesc(bh, kk), id_v, (cp > 0 || kk > 0) ? 1u : 0u);
+          mma_ts(tV, tP + kk * 8, mndesc(bh, kk), id_v, (cp > 0 || kk > 0) ? 1u : 0u);
         mma_commit(&empty[s]);
-        mma_commit(&pfree[b]);
+        mma_commit(&pfree[0]);
       }
     }
     mma_commit(&bar_v);
@@ -628,12 +730,23 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
     const int kq = t.row0 + r;  // child sample owned by this thread's row
     const bool valid = kq < K;
-    // column (parent sample) terms: (log q_p - lam_i - |mu~|^2 / (2 var)) log2 e
-    for (int j = mt; j < nch * kRows; j += kMath) {
-      float a = -INFINITY;
-      if (j < K)
-        a = (logf(D.q[pn.off_nk + j]) - D.lam[nd.off_nk + j] - 0.5f * D.mun[nd.off_nk + j] * iv) * kLog2e;
-      ak[j] = a;
+    // column (parent sample) terms: (log q_p - lam_i - |mu~|^2 / (2 var)) log2 e; all loads first
+    {
+      float qv[kJt], lv[kJt], mv[kJt];
+#pragma unroll
+      for (int i = 0; i < kJt; ++i) {
+        const int j = mt + i * kMath;
+        const bool in = j < K;
+        qv[i] = in ? __ldcg(D.q + pn.off_nk + j) : 0.f;  // may come from this launch
+        lv[i] = in ? D.lam[nd.off_nk + j] : 0.f;
+        mv[i] = in ? D.mun[nd.off_nk + j] : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < kJt; ++i) {
+        const int j = mt + i * kMath;
+        if (j >= nch * kRows) break;
+        ak[j] = (j < K) ? (logf(qv[i]) - lv[i] - 0.5f * mv[i] * iv) * kLog2e : -INFINITY;
+      }
     }
     // row term: (beta_i - |z~|^2 / (2 var) + z~ . c_i / var) log2 e
     const float crow = valid ? (D.beta[nd.off_nk + kq] - 0.5f * D.zn[nd.off_nk + kq] * iv +
@@ -652,9 +765,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         float f[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v[j]);
+        uint32_t hi[16], lo[16];
+        split_pack32(f, hi, lo);
+        tmem_st16(tAH + lane_off + g * 16, hi);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) store_split8(sAH, sAL, r, g * 4 + q, f + 8 * q);
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4*>(sAL + (uint32_t)((g * 4 + q) >> 3) * kBox + sw128_offset(r, (g * 4 + q) & 7)) =
+              make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
       }
+      tmem_wait_st();
       fence_proxy_async_smem();
       tc_fence_before();
     }
@@ -680,10 +799,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 #pragma unroll
         for (int j = 0; j < 32; j += 4) {
           const float4 a4 = *reinterpret_cast<const float4*>(akc + g * 32 + j);
-          const float p0 = exp2f(fmaf(__uint_as_float(v[g][j]), sc, crow + a4.x));
-          const float p1 = exp2f(fmaf(__uint_as_float(v[g][j + 1]), sc, crow + a4.y));
-          const float p2 = exp2f(fmaf(__uint_as_float(v[g][j + 2]), sc, crow + a4.z));
-          const float p3 = exp2f(fmaf(__uint_as_float(v[g][j + 3]), sc, crow + a4.w));
+          const float p0 = ex2_ftz(fmaf(__uint_as_float(v[g][j]), sc, crow + a4.x));
+          const float p1 = ex2_ftz(fmaf(__uint_as_float(v[g][j + 1]), sc, crow + a4.y));
+          const float p2 = ex2_ftz(fmaf(__uint_as_float(v[g][j + 2]), sc, crow + a4.z));
+          const float p3 = ex2_ftz(fmaf(__uint_as_float(v[g][j + 3]), sc, crow + a4.w));
           s0 += p0 + p1;
           s1 += p2 + p3;
           pk[g * 16 + j / 2] = pack_half2(p0, p1);
@@ -691,17 +810,18 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         }
       }
       qacc += s0 + s1;
-      if (c >= 2 && !mbar_wait(&pfree[b], ((c >> 1) + 1) & 1)) { ok = false; break; }
+      if (c >= 1 && !mbar_wait(&pfree[0], (c - 1) & 1)) { ok = false; break; }
       tc_fence_after();
-      tmem_st32(tP[b] + lane_off + 32 * h, pk);
+      tmem_st32(tP + lane_off + 32 * h, pk);
       tmem_wait_st();
       tc_fence_before();
-      mbar_arrive(&pready[b]);
+      mbar_arrive(&pready[0]);
     }
     q_h[h][r] = qacc;
     sync_math();
     const float qtot = q_h[0][r] + q_h[1][r];
     if (ok && valid && h == 0) D.q[nd.off_nk + kq] = qtot;
+    __threadfence();  // weights visible device-wide before the completion count moves
     // epilogue: V row -> fp16 A tile of G; q z~ row -> A tile of M2; ones atom
     if (ok) ok = mbar_wait(&bar_v, 0);
     if (ok) {
@@ -778,8 +898,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     }
     if (!ok) set_timeout(D);
   }
+  // item end: every role is done with this item's barriers, tensor memory and ring
   tc_fence_before();
   __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x == 0) red_release_add(done + t.node, 1);
+  }  // items
   if (warp == 2) {
     tc_fence_after();
     tmem_dealloc(tb, 512);
@@ -909,10 +1033,7 @@ __global__ void __launch_bounds__(kThreads) k_asm_edge_mat(Dev D, TcDev T, const
   for (int i = 0; i < 4; ++i) {
     const int a = a0 + ty * 4 + i;
     if (a >= d) continue;
-    // db'[a] recomputed locally (d FMAs): (zbar_c - W zbar_p - c)[a] / var
-    float s = 0.f;
-    for (int c = 0; c < d; ++c) s = fmaf(W[(long long)a * d + c], zbp[c], s);
-    const float db = (zbc[a] - s - cc[a]) * iv;
+    const float db = -T.sgC[(long long)g * kLdp + a];  // db'[a], stored by k_asm_edge_vec
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
       const int bb = b0 + tx * 4 + jj;
@@ -1125,12 +1246,17 @@ bool make_map(CUtensorMap* m, void* ptr, long long rows) {
              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Dynamic shared memory, at least half of the SM's: one CTA per SM, so the 512-column TMEM
+// allocation never waits on a co-resident CTA.
 template <int DP>
 size_t fwd_smem(int maxK) {
-  const size_t need = 1024 + 2 * (size_t)(kRows * DP * 2) + ring_bytes(DP) +
+  const size_t need = 1024 + 3 * 2 * (size_t)(kRows * DP * 2) + 4 * (size_t)(((maxK + kRows - 1) / kRows) * kRows);
+  return need > 120 * 1024 ? need : 120 * 1024;
+}
+template <int DP>
+size_t bwd_smem(int maxK) {
+  const size_t need = 1024 + (size_t)(kRows * DP * 2) + ring_bytes(DP) +
                       4 * (size_t)(((maxK + kRows - 1) / kRows) * kRows);
-  // at least half of the SM's shared memory: one CTA per SM, so the 512-column TMEM
-  // allocation never waits on a co-resident CTA
   return need > 120 * 1024 ? need : 120 * 1024;
 }
 }  // namespace
@@ -1157,6 +1283,7 @@ void workspace_layout(TcWork& w, const std::vector<NodeInfo>& nodes, long long n
   subs.push_back({(void**)&w.t.ZH, pk});
   subs.push_back({(void**)&w.t.ZL, pk});
   subs.push_back({(void**)&w.t.zc, (size_t)nk * sizeof(float)});
+  subs.push_back({(void**)&w.t.done, (size_t)w.num_nodes * sizeof(int)});
   subs.push_back({(void**)&w.t.WH, pw});
   subs.push_back({(void**)&w.t.WL, pw});
   subs.push_back({(void**)&w.t.WTH, pw});
@@ -1186,20 +1313,25 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
   for (const NodeInfo& nd : nodes) maxlevel = std::max(maxlevel, nd.level);
   w.maxlevel = maxlevel;
   w.tiles.clear();
-  for (int c = 0; c < 2; ++c) {
-    w.lv_b[c].assign(maxlevel + 1, 0);
-    w.lv_e[c].assign(maxlevel + 1, 0);
-  }
-  for (int L = 1; L <= maxlevel; ++L)
+  // forward items: deepest level first; backward items: level 1 first (per d class)
+  for (int dir = 0; dir < 2; ++dir)
     for (int c = 0; c < 2; ++c) {
-      w.lv_b[c][L] = (int)w.tiles.size();
-      for (int g = 0; g < (int)nodes.size(); ++g) {
-        const NodeInfo& nd = nodes[g];
-        if (nd.level != L || ((nd.d > 64) ? 1 : 0) != c) continue;
-        for (int r = 0; r < nd.K; r += kRows) w.tiles.push_back(Tile{g, r});
+      w.it_b[dir][c] = (int)w.tiles.size();
+      for (int step = 0; step < maxlevel; ++step) {
+        const int L = dir == 0 ? maxlevel - step : 1 + step;
+        for (int g = 0; g < (int)nodes.size(); ++g) {
+          const NodeInfo& nd = nodes[g];
+          if (nd.level != L || ((nd.d > 64) ? 1 : 0) != c) continue;
+          for (int r = 0; r < nd.K; r += kRows) w.tiles.push_back(Tile{g, r});
+        }
       }
-      w.lv_e[c][L] = (int)w.tiles.size();
+      w.it_e[dir][c] = (int)w.tiles.size();
     }
+  cudaDeviceGetAttribute(&w.num_sms, cudaDevAttrMultiProcessorCount, 0);
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&w.num_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
   w.nonroot.clear();
   for (int g = 0; g < (int)nodes.size(); ++g)
     if (nodes[g].parent >= 0) w.nonroot.push_back(g);
@@ -1217,8 +1349,8 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
   const size_t f64 = fwd_smem<64>(maxK), f128 = fwd_smem<128>(maxK);
   cudaFuncSetAttribute(k_edge_fwd_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f64);
   cudaFuncSetAttribute(k_edge_fwd_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f128);
-  cudaFuncSetAttribute(k_edge_bwd_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f64);
-  cudaFuncSetAttribute(k_edge_bwd_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f128);
+  cudaFuncSetAttribute(k_edge_bwd_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<64>(maxK));
+  cudaFuncSetAttribute(k_edge_bwd_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<128>(maxK));
   return cudaGetLastError() == cudaSuccess ? TMC_OK : TMC_ERR_CUDA;
 }
 
@@ -1240,30 +1372,32 @@ void launch_pack(TcWork& w, const Dev& D, cudaStream_t s) {
   k_pack_c<<<n, 256, 0, s>>>(D, w.t, w.d_nonroot);
 }
 
-void launch_edge_fwd(TcWork& w, const Dev& D, int L, cudaStream_t s) {
+void launch_edge_fwd(TcWork& w, const Dev& D, cudaStream_t s) {
+  cudaMemsetAsync(w.t.done, 0, (size_t)w.num_nodes * sizeof(int), s);
   for (int c = 0; c < 2; ++c) {
-    const int b = w.lv_b[c][L], n = w.lv_e[c][L] - b;
+    const int b = w.it_b[0][c], n = w.it_e[0][c] - b;
     if (!n) continue;
+    const int grid = n < w.num_sms ? n : w.num_sms;
     if (c == 0)
-      k_edge_fwd_tc<64><<<n, kThreadsTc, fwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, w.mZH, w.mZL, w.mWH, w.mWL);
+      k_edge_fwd_tc<64><<<grid, kThreadsTc, fwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH, w.mZL, w.mWH, w.mWL);
     else
-      k_edge_fwd_tc<128><<<n, kThreadsTc, fwd_smem<128>(w.maxK), s>>>(D, w.t, w.d_tiles + b, w.mZH, w.mZL, w.mWH, w.mWL);
+      k_edge_fwd_tc<128><<<grid, kThreadsTc, fwd_smem<128>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH, w.mZL, w.mWH, w.mWL);
   }
 }
 
-void launch_edge_bwd(TcWork& w, const Dev& D, int L, cudaStream_t s) {
-  if (L == 1) {
-    cudaMemsetAsync(w.t.G, 0, (size_t)w.num_nodes * kLdp * kLdp * sizeof(float), s);
-    cudaMemsetAsync(w.t.M2, 0, (size_t)w.num_nodes * kLdp * kLdp * sizeof(float), s);
-    cudaMemsetAsync(w.t.zbar, 0, (size_t)w.num_nodes * kLdp * sizeof(float), s);
-  }
+void launch_edge_bwd(TcWork& w, const Dev& D, cudaStream_t s) {
+  cudaMemsetAsync(w.t.G, 0, (size_t)w.num_nodes * kLdp * kLdp * sizeof(float), s);
+  cudaMemsetAsync(w.t.M2, 0, (size_t)w.num_nodes * kLdp * kLdp * sizeof(float), s);
+  cudaMemsetAsync(w.t.zbar, 0, (size_t)w.num_nodes * kLdp * sizeof(float), s);
+  cudaMemsetAsync(w.t.done, 0, (size_t)w.num_nodes * sizeof(int), s);
   for (int c = 0; c < 2; ++c) {
-    const int b = w.lv_b[c][L], n = w.lv_e[c][L] - b;
+    const int b = w.it_b[1][c], n = w.it_e[1][c] - b;
     if (!n) continue;
+    const int grid = n < w.num_sms ? n : w.num_sms;
     if (c == 0)
-      k_edge_bwd_tc<64><<<n, kThreadsTc, fwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, w.mZH, w.mZL, w.mWTH, w.mWTL);
+      k_edge_bwd_tc<64><<<grid, kThreadsTc, bwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH, w.mZL, w.mWTH, w.mWTL);
     else
-      k_edge_bwd_tc<128><<<n, kThreadsTc, fwd_smem<128>(w.maxK), s>>>(D, w.t, w.d_tiles + b, w.mZH, w.mZL, w.mWTH, w.mWTL);
+      k_edge_bwd_tc<128><<<grid, kThreadsTc, bwd_smem<128>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH, w.mZL, w.mWTH, w.mWTL);
   }
 }
 

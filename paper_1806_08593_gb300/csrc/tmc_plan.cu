@@ -391,12 +391,13 @@ tmc_status tmc_log_marginal(tmc_plan p, const tmc_inputs* in, double* log_phat, 
     TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_obs_fwd(D, T + p->t_leaf_b, p->t_leaf_e - p->t_leaf_b, s); }));
     TRY(timed(p, TMC_KC_PROJECT, s, [&] { launch_project(D, T + p->t_proj_b, p->t_proj_e - p->t_proj_b, s); }));
   }
-  for (int L = p->maxlevel; L >= 1; --L) {
-    const int b = p->t_level_b[L], e = p->t_level_e[L];
-    if (tc_path)
-      TRY(timed(p, TMC_KC_EDGE_FWD, s, [&] { tc::launch_edge_fwd(p->tcw, D, L, s); }));
-    else
+  if (tc_path) {
+    if (p->maxlevel >= 1) TRY(timed(p, TMC_KC_EDGE_FWD, s, [&] { tc::launch_edge_fwd(p->tcw, D, s); }));
+  } else {
+    for (int L = p->maxlevel; L >= 1; --L) {
+      const int b = p->t_level_b[L], e = p->t_level_e[L];
       TRY(timed(p, TMC_KC_EDGE_FWD, s, [&] { launch_edge_fwd_f32(D, T + b, e - b, p->maxK, s); }));
+    }
   }
   TRY(timed(p, TMC_KC_ROOT, s, [&] { launch_root(D, p->maxK, s); }));
   p->fwd_done = true;
@@ -420,11 +421,11 @@ tmc_status tmc_backward(tmc_plan p, const tmc_inputs* in, const double* grad_out
   D.dz = g->dz; D.deps = g->deps; D.dq_mean = g->dq_mean; D.dq_logstd = g->dq_logstd;
   D.dW = g->dW; D.dbias = g->dbias; D.dC = g->dC;
   const Tile* T = p->d_tiles;
-  for (int L = 1; L <= p->maxlevel; ++L) {
-    const int b = p->t_level_b[L], e = p->t_level_e[L];
-    if (tc_path) {
-      TRY(timed(p, TMC_KC_EDGE_BWD, s, [&] { tc::launch_edge_bwd(p->tcw, D, L, s); }));
-    } else {
+  if (tc_path) {
+    if (p->maxlevel >= 1) TRY(timed(p, TMC_KC_EDGE_BWD, s, [&] { tc::launch_edge_bwd(p->tcw, D, s); }));
+  } else {
+    for (int L = 1; L <= p->maxlevel; ++L) {
+      const int b = p->t_level_b[L], e = p->t_level_e[L];
       TRY(timed(p, TMC_KC_EDGE_BWD, s, [&] { launch_edge_bwd_cols_f32(D, T + b, e - b, p->maxK, s); }));
       TRY(timed(p, TMC_KC_EDGE_BWD, s, [&] { launch_edge_bwd_rows_f32(D, T + b, e - b, p->maxK, s); }));
     }

@@ -41,6 +41,7 @@ struct TcDev {
   float* sgP;
   float* tgP;
   float* CtC;                  // [1 or B][128*128]  C^T C per observation matrix
+  int* done;                   // [nodes] tiles finished per node in the running edge launch
   int shared;
 };
 
@@ -50,9 +51,11 @@ struct TcWork {
   long long rows = 0;
   TcDev t{};
   CUtensorMap mZH, mZL, mWH, mWL, mWTH, mWTL;
-  // tile lists: [level][class] ranges into d_tiles; class 0 = d <= 64, 1 = d <= 128
+  // edge tiles in dependency order: [direction][class] ranges into d_tiles; direction 0 =
+  // forward (deepest level first), 1 = adjoint (level 1 first); class 0: d <= 64, 1: d <= 128
   std::vector<Tile> tiles;
-  std::vector<int> lv_b[2], lv_e[2];
+  int it_b[2][2] = {{0, 0}, {0, 0}}, it_e[2][2] = {{0, 0}, {0, 0}};
+  int num_sms = 148;
   Tile* d_tiles = nullptr;
   std::vector<int> nonroot;
   int* d_nonroot = nullptr;
@@ -67,8 +70,8 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
 void release(TcWork& w);
 void launch_sample(TcWork& w, const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s);
 void launch_pack(TcWork& w, const Dev& D, cudaStream_t s);
-void launch_edge_fwd(TcWork& w, const Dev& D, int level, cudaStream_t s);
-void launch_edge_bwd(TcWork& w, const Dev& D, int level, cudaStream_t s);
+void launch_edge_fwd(TcWork& w, const Dev& D, cudaStream_t s);  // one persistent launch per d class
+void launch_edge_bwd(TcWork& w, const Dev& D, cudaStream_t s);
 void launch_unpack_grads(TcWork& w, const Dev& D, cudaStream_t s);
 
 }  // namespace tc
