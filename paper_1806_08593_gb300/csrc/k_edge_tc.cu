@@ -362,11 +362,24 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       tma_load_2d(ring + 2 * TB + b * kBox, &mWH, &bar_pro, b * 64, slot * kLdp);
       tma_load_2d(ring + 3 * TB + b * kBox, &mWL, &bar_pro, b * 64, slot * kLdp);
     }
-    bool ok = mbar_wait(&bar_mu, 0);  // prologue MMAs have read the ring
+    // chunk c uses stage (c + 2) % NS: chunk 0 goes to the stage the prologue leaves free and
+    // is in flight together with the prologue operands
+    bool ok = true;
     int issued = 0;
+    // the next item's prologue operands into L2 while this item runs
+    if (item + (int)gridDim.x < ntiles) {
+      const Tile tn = tiles[item + gridDim.x];
+      const NodeInfo nn = D.nodes[tn.node];
+      const int prow_n = (int)(D.nodes[nn.parent].off_nk + tn.row0);
+      for (int b = 0; b < NB; ++b) {
+        tma_prefetch_l2_2d(&mZH, b * 64, prow_n);
+        tma_prefetch_l2_2d(&mZL, b * 64, prow_n);
+      }
+    }
     for (int c = 0; ok && c < nch; ++c) {
-      const int s = c % NS;
-      if (c >= NS && !mbar_wait(&empty[s], ((c / NS) + 1) & 1)) { ok = false; break; }
+      const int s = (c + 2) % NS, fill = c / NS;  // chunk c is the fill-th use of stage s
+      if (c == 1 && !mbar_wait(&bar_mu, 0)) { ok = false; break; }  // prologue read stages 0, 1
+      if (fill >= 1 && !mbar_wait(&empty[s], (fill - 1) & 1)) { ok = false; break; }
       unsigned char* st = ring + s * 2 * TB;
       mbar_arrive_expect_tx(&full[s], 2 * TB);
       const int row = (int)(nd.off_nk + c * kRows);
@@ -377,7 +390,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       issued = c + 1;
     }
     if (!ok) set_timeout(D);
-    for (int c = (issued > NS ? issued - NS : 0); c < issued; ++c) mbar_wait(&full[c % NS], (c / NS) & 1);
+    for (int c = (issued > NS ? issued - NS : 0); c < issued; ++c) mbar_wait(&full[(c + 2) % NS], (c / NS) & 1);
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------------ MMA issuer
     bool ok = mbar_wait(&bar_pro, 0);
@@ -393,7 +406,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     }
     const uint32_t id_s = idesc_f16(kRows, kRows, false, false, false);
     for (int c = 0; ok && c < nch; ++c) {
-      const int s = c % NS, b = c & 1;
+      const int s = (c + 2) % NS, b = c & 1;
       if (!mbar_wait(&full[s], (c / NS) & 1)) { ok = false; break; }
       if (c >= 2 && !mbar_wait(&sfree[b], ((c >> 1) + 1) & 1)) { ok = false; break; }
       tc_fence_after();
@@ -638,6 +651,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       tma_load_2d(ring + TB + b * kBox, &mZL, &bar_pro, b * 64, own);
       tma_load_2d(ring + 2 * TB + b * kBox, &mWTH, &bar_pro, b * 64, slot * kLdp);
       tma_load_2d(ring + 3 * TB + b * kBox, &mWTL, &bar_pro, b * 64, slot * kLdp);
+    }
+    if (item + (int)gridDim.x < ntiles) {  // next item's own tile into L2 while this one runs
+      const Tile tn = tiles[item + gridDim.x];
+      const int row_n = (int)(D.nodes[tn.node].off_nk + tn.row0);
+      for (int b = 0; b < NB; ++b) {
+        tma_prefetch_l2_2d(&mZH, b * 64, row_n);
+        tma_prefetch_l2_2d(&mZL, b * 64, row_n);
+      }
     }
     bool ok = mbar_wait(&bar_mu, 0);
     int issued = 0;
