@@ -216,6 +216,31 @@ def algorithmic_flops(p, precision):
     return {"edge_fwd": 2.0 * float(e.sum()), "edge_bwd": 4.0 * float(e.sum())}
 
 
+def time_forward(p, precision, dev, steps, warmup):
+    """Device time per forward pass of a plan (log P only)."""
+    import torch
+    from paper_1806_08593_gb300.tmc import Plan
+    plan = Plan.from_problem(p, precision)
+    t = plan.to_device(p, dev)
+    out = torch.empty(p.B, dtype=torch.float64, device=dev)
+    for _ in range(warmup):
+        plan.forward(t, out=out)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        plan.forward(t, out=out)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    plan.sync_status()
+    ms = e0.elapsed_time(e1) / steps
+    lp = out.cpu().numpy()
+    plan.close()
+    del t
+    torch.cuda.empty_cache()
+    return ms, lp
+
+
 def time_plan_steps(p, precision, dev, steps, warmup):
     """Device time per fwd+bwd step of a plan at the given precision (for the comparison)."""
     import torch
@@ -361,6 +386,17 @@ def run_ours(args):
                 "speedup": ms32 / ms_step,
                 "max_abs_dlogp_vs_fp32": float(np.max(np.abs(lp_ours - lp32)))}
 
+    # ---- materialised-factor baseline (forward only, FP32) ----------------------------
+    unfused = None
+    if args.compare_unfused:
+        ms_f, lp_f = time_forward(p, "fp32", dev, steps=max(3, args.steps), warmup=3)
+        ms_u, lp_u = time_forward(p, "fp32_unfused", dev, steps=max(3, args.steps), warmup=3)
+        ms_t, lp_t = time_forward(p, args.precision, dev, steps=max(3, args.steps), warmup=3)
+        unfused = {"fused_fp32_fwd_ms": ms_f, "unfused_fp32_fwd_ms": ms_u,
+                   "fused_speedup": ms_u / ms_f, "%s_fwd_ms" % args.precision: ms_t,
+                   "factor_bytes_written": 4 * p.edge_entries(),
+                   "max_abs_dlogp_unfused_vs_fused": float(np.max(np.abs(lp_u - lp_f)))}
+
     # ---- CPU baseline (oracle on a bounded sample) ------------------------------------
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
@@ -384,6 +420,7 @@ def run_ours(args):
         "e2e": {"value": entries * ws / (e2e_ms * 1e-3), "unit": "entries/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "fp32_path": fp32,
+        "unfused_baseline": unfused,
         "gpu_launches": total_launches,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "clocks": clk.summary(),
@@ -401,6 +438,8 @@ def main():
     ap.add_argument("--precision", default=os.environ.get("TMC_BENCH_PRECISION", "fp16"),
                     choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--compare-unfused", action="store_true",
+                    help="also time the FP32 forward with every K x K factor materialised")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()

@@ -52,7 +52,10 @@ typedef enum {
 typedef enum {
   TMC_PREC_FP32 = 0,    /* CUDA-core FP32 contractions                                     */
   TMC_PREC_BF16_TC = 1, /* tcgen05 tensor cores, bf16 operands, FP32 accumulate            */
-  TMC_PREC_FP16_TC = 2  /* tcgen05 tensor cores, fp16 operands, FP32 accumulate            */
+  TMC_PREC_FP16_TC = 2, /* tcgen05 tensor cores, fp16 operands, FP32 accumulate            */
+  TMC_PREC_FP32_UNFUSED = 3 /* FP32, every K x K log-factor written to device memory before a
+                               separate row log-sum-exp pass (the materialised baseline of
+                               Section 2.2's sums; adjoint as TMC_PREC_FP32)                  */
 } tmc_precision;
 
 typedef struct tmc_plan_s* tmc_plan;

@@ -78,6 +78,8 @@ struct Dev {
   float* pbias;   // per-(instance, node) dbias partials (shared params only)
   float* pC;      // per-instance dC partials (shared params only)
   int* err;       // device error word
+  float* fac;             // unfused baseline: every edge's K x K log-factors (relative)
+  const long long* fac_off;  // per node: start of its edge's block in fac
 
   // outputs of the current call
   double* log_phat;
@@ -92,6 +94,8 @@ void launch_sample(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s);
 void launch_obs_fwd(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s);
 void launch_project(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s);
 void launch_edge_fwd_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK, cudaStream_t s);
+void launch_factors_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK, cudaStream_t s);
+void launch_lse_rows_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK, cudaStream_t s);
 void launch_root(const Dev& D, int maxK, cudaStream_t s);
 void launch_edge_bwd_rows_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK,
                               cudaStream_t s);

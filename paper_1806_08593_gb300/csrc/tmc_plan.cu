@@ -39,6 +39,9 @@ struct tmc_plan_s {
   std::vector<NodeInfo> nodes;
   std::vector<InstInfo> insts;
   std::vector<int> children, nonroot;
+  std::vector<long long> fac_off;  // unfused baseline: start of each edge's K x K factor block
+  long long fac_total = 0;
+  long long* d_fac_off = nullptr;
 
   // tile lists: [begin, end) ranges into one device array
   std::vector<Tile> tiles;
@@ -122,7 +125,7 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
   if (!(ds->prior_var > 0.0) || !(ds->obs_var > 0.0) || !std::isfinite(ds->prior_var) ||
       !std::isfinite(ds->obs_var))
     return TMC_ERR_INVALID_ARG;
-  if (ds->precision < TMC_PREC_FP32 || ds->precision > TMC_PREC_FP16_TC) return TMC_ERR_INVALID_ARG;
+  if (ds->precision < TMC_PREC_FP32 || ds->precision > TMC_PREC_FP32_UNFUSED) return TMC_ERR_INVALID_ARG;
   p->B = B;
   p->shared = ds->shared_params ? 1 : 0;
   p->precision = ds->precision;
@@ -232,6 +235,14 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
       p->nonroot.push_back(g);
     }
   p->t_proj_e = (int)p->tiles.size();
+  if (p->precision == TMC_PREC_FP32_UNFUSED) {
+    p->fac_off.assign(G, 0);
+    for (int g = 0; g < G; ++g)
+      if (p->nodes[g].parent >= 0) {
+        p->fac_off[g] = p->fac_total;
+        p->fac_total += (long long)p->nodes[g].K * p->nodes[g].K;
+      }
+  }
   p->t_level_b.assign(p->maxlevel + 1, 0);
   p->t_level_e.assign(p->maxlevel + 1, 0);
   for (int L = 1; L <= p->maxlevel; ++L) {
@@ -249,6 +260,7 @@ tmc_status alloc_device(tmc_plan p) {
   TRY(upload(&p->d_children, p->children));
   TRY(upload(&p->d_nonroot, p->nonroot));
   TRY(upload(&p->d_tiles, p->tiles));
+  TRY(upload(&p->d_fac_off, p->fac_off));
   if (cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess) return TMC_ERR_NOMEM;
   if (cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) return TMC_ERR_CUDA;
 
@@ -258,7 +270,7 @@ tmc_status alloc_device(tmc_plan p) {
   const long long nC = p->shared ? (long long)p->B * p->shared_obs * p->shared_d : 0;
   // layout: 256-byte aligned sub-buffers
   struct Sub { void** dst; size_t bytes; };
-  float *zt, *mut, *zn, *mun, *u, *beta, *lam, *q, *nodemax, *dmu, *gz, *pW, *pbias, *pC;
+  float *zt, *mut, *zn, *mun, *u, *beta, *lam, *q, *nodemax, *dmu, *gz, *pW, *pbias, *pC, *fac;
   double* nodeconst;
   std::vector<Sub> subs = {
       {(void**)&zt, sizeof(float) * nkd},      {(void**)&mut, sizeof(float) * nkd},
@@ -269,11 +281,13 @@ tmc_status alloc_device(tmc_plan p) {
       {(void**)&nodemax, sizeof(float) * G},   {(void**)&nodeconst, sizeof(double) * G},
       {(void**)&pW, sizeof(float) * nW},       {(void**)&pbias, sizeof(float) * nb},
       {(void**)&pC, sizeof(float) * nC},
+      {(void**)&fac, sizeof(float) * p->fac_total},
   };
   std::vector<tc::TcSub> tsubs;
   p->tcw.t.shared = p->shared;
   p->tcw.precision = p->precision;
-  if (p->precision != TMC_PREC_FP32) tc::workspace_layout(p->tcw, p->nodes, nk, nkd, tsubs);
+  const bool tc_plan = p->precision == TMC_PREC_FP16_TC || p->precision == TMC_PREC_BF16_TC;
+  if (tc_plan) tc::workspace_layout(p->tcw, p->nodes, nk, nkd, tsubs);
   size_t total = 0;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   for (auto& s : subs) total += al(s.bytes);
@@ -299,7 +313,9 @@ tmc_status alloc_device(tmc_plan p) {
   D.nodemax = nodemax; D.nodeconst = nodeconst; D.dmu = dmu; D.gz = gz;
   D.pW = nW ? pW : nullptr; D.pbias = nb ? pbias : nullptr; D.pC = nC ? pC : nullptr;
   D.err = p->d_err;
-  if (p->precision != TMC_PREC_FP32) TRY(tc::prepare(p->tcw, p->nodes, p->tiles, p->maxK, p->maxd));
+  D.fac = p->fac_total ? fac : nullptr;
+  D.fac_off = p->d_fac_off;
+  if (tc_plan) TRY(tc::prepare(p->tcw, p->nodes, p->tiles, p->maxK, p->maxd));
   return TMC_OK;
 }
 
@@ -309,6 +325,7 @@ void free_plan(tmc_plan p) {
   cudaFree(p->d_children);
   cudaFree(p->d_nonroot);
   cudaFree(p->d_tiles);
+  cudaFree(p->d_fac_off);
   cudaFree(p->d_err);
   cudaFree(p->ws);
   tc::release(p->tcw);
@@ -347,7 +364,8 @@ tmc_status tmc_plan_create(const tmc_problem_desc* desc, tmc_plan* out) {
   tmc_plan p = new (std::nothrow) tmc_plan_s();
   if (!p) return TMC_ERR_NOMEM;
   tmc_status st = build_plan(desc, p);
-  if (st == TMC_OK && p->precision != TMC_PREC_FP32) st = tc::supported(p->nodes, p->precision);
+  if (st == TMC_OK && (p->precision == TMC_PREC_FP16_TC || p->precision == TMC_PREC_BF16_TC))
+    st = tc::supported(p->nodes, p->precision);
   if (st == TMC_OK) st = alloc_device(p);
   if (st != TMC_OK) {
     free_plan(p);
@@ -378,7 +396,7 @@ tmc_status tmc_log_marginal(tmc_plan p, const tmc_inputs* in, double* log_phat, 
   D.W = in->W; D.bias = in->bias; D.C = in->C; D.x = in->x;
   D.log_phat = log_phat;
   const Tile* T = p->d_tiles;
-  const bool tc_path = p->precision != TMC_PREC_FP32;
+  const bool tc_path = p->precision == TMC_PREC_FP16_TC || p->precision == TMC_PREC_BF16_TC;
   TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_node_const(D, s); }));
   if (tc_path) {
     // split W_i and c_i first: the sampling kernel forms z~ . c_i, the conditional means are
@@ -394,9 +412,15 @@ tmc_status tmc_log_marginal(tmc_plan p, const tmc_inputs* in, double* log_phat, 
   if (tc_path) {
     if (p->maxlevel >= 1) TRY(timed(p, TMC_KC_EDGE_FWD, s, [&] { tc::launch_edge_fwd(p->tcw, D, s); }));
   } else {
+    const bool unfused = p->precision == TMC_PREC_FP32_UNFUSED;
+    if (unfused)  // every pairwise log-factor of every edge into device memory first
+      TRY(timed(p, TMC_KC_EDGE_FWD, s, [&] { launch_factors_f32(D, T + p->t_proj_b, p->t_proj_e - p->t_proj_b, p->maxK, s); }));
     for (int L = p->maxlevel; L >= 1; --L) {
       const int b = p->t_level_b[L], e = p->t_level_e[L];
-      TRY(timed(p, TMC_KC_EDGE_FWD, s, [&] { launch_edge_fwd_f32(D, T + b, e - b, p->maxK, s); }));
+      if (unfused)
+        TRY(timed(p, TMC_KC_EDGE_FWD, s, [&] { launch_lse_rows_f32(D, T + b, e - b, p->maxK, s); }));
+      else
+        TRY(timed(p, TMC_KC_EDGE_FWD, s, [&] { launch_edge_fwd_f32(D, T + b, e - b, p->maxK, s); }));
     }
   }
   TRY(timed(p, TMC_KC_ROOT, s, [&] { launch_root(D, p->maxK, s); }));
@@ -409,7 +433,7 @@ tmc_status tmc_backward(tmc_plan p, const tmc_inputs* in, const double* grad_out
                         const tmc_grads* g, void* stream) {
   if (!p || !inputs_ok(in) || !g) return TMC_ERR_INVALID_ARG;
   if (!p->fwd_done || std::memcmp(&p->last_in, in, sizeof(tmc_inputs)) != 0) return TMC_ERR_STATE;
-  const bool tc_path = p->precision != TMC_PREC_FP32;
+  const bool tc_path = p->precision == TMC_PREC_FP16_TC || p->precision == TMC_PREC_BF16_TC;
   // the tensor-core adjoint reduces the factors to d x d moments and forms no per-sample
   // gradient; dz / deps are available on the FP32 path
   if (tc_path && (g->dz || g->deps)) return TMC_ERR_UNSUPPORTED;

@@ -19,7 +19,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libtmc_gb300.so")
 
-PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "fp32_unfused": 3}
 STATUS = {0: "TMC_OK", 1: "TMC_ERR_INVALID_ARG", 2: "TMC_ERR_UNSUPPORTED", 3: "TMC_ERR_NOMEM",
           4: "TMC_ERR_CUDA", 5: "TMC_ERR_NUMERIC", 6: "TMC_ERR_TIMEOUT", 7: "TMC_ERR_STATE"}
 KERNEL_CLASSES = ["sample", "project", "edge_fwd", "root", "edge_bwd", "param"]

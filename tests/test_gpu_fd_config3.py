@@ -1,0 +1,47 @@
+"""Gradients of the FP32 CUDA path on the K=256, d=64, n=8, B=128 chain (full launch) against
+central finite differences (step 1e-3) of the FP64 oracle on a seeded 1% subsample of every
+parameter tensor (W, bias, C, proposal mean and log-std) and a few noise entries.
+grad_out selects instance 0, so the differences need only that instance's oracle value."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_08593_gb300 import workload as wl
+from tests.parity import gpu_run
+
+pytestmark = pytest.mark.gpu
+H = 1e-3
+TOL_GRAD = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1806_08593_gb300.build import build
+    build()
+
+
+def test_config3_fp32_gradients_vs_central_differences():
+    p = wl.chain_config("chain_n8_K256_d64_B128")
+    go = np.zeros(p.B)
+    go[0] = 1.0
+    got = gpu_run(p, "fp32", grad_out=go, want=("deps", "dq_mean", "dq_logstd", "dW", "dbias", "dC"))
+    sub = oracle.subset(p, [0])
+    n, K, d = 8, 256, 64
+    rng = np.random.default_rng(20181806)
+    checks = {"W": "dW", "bias": "dbias", "C": "dC", "q_mean": "dq_mean", "q_logstd": "dq_logstd", "eps": "deps"}
+    for name, gk in checks.items():
+        base = getattr(sub, name).astype(np.float64)
+        size = base.size
+        k = 16 if name == "eps" else max(4, size // 100)
+        idx = rng.choice(size, size=k, replace=False)
+        fd = np.empty(k)
+        for j, i in enumerate(idx):
+            a = base.copy(); a[i] += H
+            b = base.copy(); b[i] -= H
+            fd[j] = (oracle.log_marginal(sub, **{name: a})[0] - oracle.log_marginal(sub, **{name: b})[0]) / (2 * H)
+        g = got[gk][:size][idx] if name in ("q_mean", "q_logstd", "eps") else got[gk][idx]
+        err = np.linalg.norm(g - fd) / np.linalg.norm(fd)
+        assert err <= TOL_GRAD, (name, err)
