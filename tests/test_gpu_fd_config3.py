@@ -32,11 +32,21 @@ def test_config3_fp32_gradients_vs_central_differences():
     n, K, d = 8, 256, 64
     rng = np.random.default_rng(20181806)
     checks = {"W": "dW", "bias": "dbias", "C": "dC", "q_mean": "dq_mean", "q_logstd": "dq_logstd", "eps": "deps"}
+    # most samples carry negligible weight (the posterior is peaked), so their noise
+    # gradients are below FP64 resolution of log P; check the largest ones (ranked by the
+    # oracle's analytic gradient) together with random ones
+    ana = oracle.grad(sub)
+    s_ = np.exp(sub.q_logstd.astype(np.float64)).reshape(n, 1, d)
+    deps_ref = (ana["dz"].reshape(n, K, d) * s_).ravel()
     for name, gk in checks.items():
         base = getattr(sub, name).astype(np.float64)
         size = base.size
-        k = 16 if name == "eps" else max(4, size // 100)
-        idx = rng.choice(size, size=k, replace=False)
+        if name == "eps":
+            idx = np.concatenate([np.argsort(-np.abs(deps_ref))[:16], rng.choice(size, size=16, replace=False)])
+            idx = np.unique(idx)
+        else:
+            idx = rng.choice(size, size=max(4, size // 100), replace=False)
+        k = len(idx)
         fd = np.empty(k)
         for j, i in enumerate(idx):
             a = base.copy(); a[i] += H
