@@ -303,21 +303,52 @@ def run_ours(args):
     plan.sync_status()
 
     # ---- device-resident timed region (CUDA events on the launch stream) ---------------
-    plan.profile_enable(True)
+    graph = None
+    if args.graph:
+        # the whole step (all launches, memsets) captured once and replayed
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            step()
+        stream.wait_stream(side)
+        torch.cuda.synchronize(dev)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        torch.cuda.synchronize(dev)
+        graph.replay()
+        torch.cuda.synchronize(dev)
+    else:
+        plan.profile_enable(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local if ws > 1 else 0) as clk:
         barrier()
         torch.cuda.synchronize(dev)
         ev0.record(stream)
         for _ in range(args.steps):
-            step()
+            if graph is not None:
+                graph.replay()
+            else:
+                step()
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
     ms = ev0.elapsed_time(ev1)
+    if graph is not None:  # kernel-class times from a separate, uncaptured pass
+        plan.profile_enable(True)
+        for _ in range(args.steps):
+            step()
     prof = plan.profile_read()
     plan.profile_enable(False)
     plan.sync_status()
+    latency = None
+    if args.precision in ("fp16", "bf16"):
+        step()
+        f_us, b_us = plan.instance_times()
+        latency = {"unit": "us", "fwd_p50": float(np.percentile(f_us, 50)), "fwd_p99": float(np.percentile(f_us, 99)),
+                   "bwd_p50": float(np.percentile(b_us, 50)), "bwd_p99": float(np.percentile(b_us, 99)),
+                   "definition": "time from the first edge tile of the persistent edge launch to the "
+                                 "instance's last tile, per direction"}
     ms_max = max_over_ranks(ms, dev)
     ms_step = ms_max / args.steps
     entries = p.entries()
@@ -412,6 +443,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "B": int(p.B), "n": int(p.n[0]), "K": int(p.K[0]),
                    "d": int(p.d[0]), "obs": int(p.obs[0]), "precision": args.precision,
+                   "cuda_graph": bool(args.graph),
                    "entries_per_step": entries, "grads": list(GRADS),
                    "l2": "inputs larger than L2 (eps %.0f MB per step)" % (p.eps.nbytes / 1e6),
                    "parallelism": "replicas" if ws > 1 else "single"},
@@ -421,6 +453,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "fp32_path": fp32,
         "unfused_baseline": unfused,
+        "instance_latency": latency,
         "gpu_launches": total_launches,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "clocks": clk.summary(),
@@ -438,6 +471,8 @@ def main():
     ap.add_argument("--precision", default=os.environ.get("TMC_BENCH_PRECISION", "fp16"),
                     choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--graph", action="store_true",
+                    help="capture one step in a CUDA graph and time graph replays")
     ap.add_argument("--compare-unfused", action="store_true",
                     help="also time the FP32 forward with every K x K factor materialised")
     ap.add_argument("--no-cpu-baseline", action="store_true")

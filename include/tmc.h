@@ -159,6 +159,13 @@ tmc_status tmc_plan_destroy(tmc_plan plan);
 /* Static, human-readable name of a status code. */
 const char* tmc_status_string(tmc_status s);
 
+/* Per-instance completion times of the last tmc_log_marginal / tmc_backward on a tensor-core
+ * plan: the time (microseconds) from the first edge tile of the persistent edge launch to
+ * the moment the instance's last edge tile finished, in each direction.  HOST double[B]
+ * outputs (either may be NULL); synchronises the device.  TMC_ERR_UNSUPPORTED on the FP32
+ * paths (their edge kernels run one launch per tree level). */
+tmc_status tmc_plan_instance_times(tmc_plan plan, double* fwd_us, double* bwd_us);
+
 /* ---- kernel timing (library-internal CUDA events on the launch stream) ----------------
  * Kernel classes, in the order of the hot path: */
 enum {

@@ -138,6 +138,19 @@ __device__ __forceinline__ bool wait_count(const int* p, int need) {
   return true;
 }
 __host__ __device__ constexpr int tiles_of(int K) { return (K + kRows - 1) / kRows; }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Per-instance completion stamps of a persistent edge launch (direction dir).
+__device__ __forceinline__ void stamp_item_start(TcDev& T, int dir, int item) {
+  if (item == (int)blockIdx.x) atomicMin(T.t_start + dir, global_ns());
+}
+__device__ __forceinline__ void stamp_item_end(const Dev& D, TcDev& T, int dir, int b) {
+  if (atomicSub(T.inst_left + (long long)dir * D.num_inst + b, 1) == 1)
+    T.inst_t[(long long)dir * D.num_inst + b] = global_ns();
+}
 
 // dst[0..n) += v[0..n) for n <= 32 (16-byte vector reductions where the row is complete).
 __device__ __forceinline__ void red_add_row32(float* dst, const uint32_t (&v)[32], int n) {
@@ -325,6 +338,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       dep_ok = wait_count(done + cg, tiles_of(D.nodes[cg].K)) && dep_ok;
     }
     if (!dep_ok) set_timeout(D);
+    stamp_item_start(T, 0, item);
     mbar_init(&bar_pro, 1);
     mbar_init(&bar_mu, 1);
     mbar_init(&bar_A, kMath);
@@ -556,7 +570,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (threadIdx.x == 0) red_release_add(done + t.node, 1);
+  if (threadIdx.x == 0) {
+    red_release_add(done + t.node, 1);
+    stamp_item_end(D, T, 0, nd.b);
+  }
   }  // items
   if (warp == 2) {
     tc_fence_after();
@@ -613,6 +630,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   if (threadIdx.x == 0) {
     // the parent's sample weights must be final (the root's come from an earlier launch)
     if (pn.parent >= 0 && !wait_count(done + nd.parent, tiles_of(pn.K))) set_timeout(D);
+    stamp_item_start(T, 1, item);
     mbar_init(&bar_pro, 1);
     mbar_init(&bar_mu, 1);
     mbar_init(&bar_A, kMath);
@@ -923,7 +941,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (threadIdx.x == 0) red_release_add(done + t.node, 1);
+  if (threadIdx.x == 0) {
+    red_release_add(done + t.node, 1);
+    stamp_item_end(D, T, 1, nd.b);
+  }
   }  // items
   if (warp == 2) {
     tc_fence_after();
@@ -1305,6 +1326,10 @@ void workspace_layout(TcWork& w, const std::vector<NodeInfo>& nodes, long long n
   subs.push_back({(void**)&w.t.ZL, pk});
   subs.push_back({(void**)&w.t.zc, (size_t)nk * sizeof(float)});
   subs.push_back({(void**)&w.t.done, (size_t)w.num_nodes * sizeof(int)});
+  subs.push_back({(void**)&w.t.inst_left, (size_t)2 * w.num_inst * sizeof(int)});
+  subs.push_back({(void**)&w.inst_init_dev, (size_t)2 * w.num_inst * sizeof(int)});
+  subs.push_back({(void**)&w.t.inst_t, (size_t)2 * w.num_inst * sizeof(unsigned long long)});
+  subs.push_back({(void**)&w.t.t_start, 2 * sizeof(unsigned long long)});
   subs.push_back({(void**)&w.t.WH, pw});
   subs.push_back({(void**)&w.t.WL, pw});
   subs.push_back({(void**)&w.t.WTH, pw});
@@ -1353,6 +1378,16 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&w.num_sms, cudaDevAttrMultiProcessorCount, dev);
   }
+  {  // per-instance tile counts per direction (same tiles both ways)
+    std::vector<int> init(2 * (size_t)w.num_inst, 0);
+    for (const NodeInfo& nd : nodes)
+      if (nd.parent >= 0) {
+        init[nd.b] += tiles_of(nd.K);
+        init[(size_t)w.num_inst + nd.b] += tiles_of(nd.K);
+      }
+    cudaMemcpy(w.inst_init_dev, init.data(), sizeof(int) * init.size(), cudaMemcpyHostToDevice);
+    w.t.inst_left_init = w.inst_init_dev;
+  }
   w.nonroot.clear();
   for (int g = 0; g < (int)nodes.size(); ++g)
     if (nodes[g].parent >= 0) w.nonroot.push_back(g);
@@ -1375,6 +1410,19 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
   return cudaGetLastError() == cudaSuccess ? TMC_OK : TMC_ERR_CUDA;
 }
 
+tmc_status instance_times(TcWork& w, int B, double* fwd_us, double* bwd_us) {
+  if (cudaDeviceSynchronize() != cudaSuccess) return TMC_ERR_CUDA;
+  std::vector<unsigned long long> t(2 * (size_t)B), st(2);
+  if (cudaMemcpy(t.data(), w.t.inst_t, sizeof(unsigned long long) * t.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(st.data(), w.t.t_start, sizeof(unsigned long long) * 2, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return TMC_ERR_CUDA;
+  for (int b = 0; b < B; ++b) {
+    if (fwd_us) fwd_us[b] = t[b] >= st[0] ? (double)(t[b] - st[0]) * 1e-3 : 0.0;
+    if (bwd_us) bwd_us[b] = t[B + b] >= st[1] ? (double)(t[B + b] - st[1]) * 1e-3 : 0.0;
+  }
+  return TMC_OK;
+}
+
 void release(TcWork& w) {
   cudaFree(w.d_tiles);
   cudaFree(w.d_nonroot);
@@ -1395,6 +1443,8 @@ void launch_pack(TcWork& w, const Dev& D, cudaStream_t s) {
 
 void launch_edge_fwd(TcWork& w, const Dev& D, cudaStream_t s) {
   cudaMemsetAsync(w.t.done, 0, (size_t)w.num_nodes * sizeof(int), s);
+  cudaMemcpyAsync(w.t.inst_left, w.inst_init_dev, sizeof(int) * w.num_inst, cudaMemcpyDeviceToDevice, s);
+  cudaMemsetAsync(w.t.t_start, 0xFF, sizeof(unsigned long long), s);
   for (int c = 0; c < 2; ++c) {
     const int b = w.it_b[0][c], n = w.it_e[0][c] - b;
     if (!n) continue;
@@ -1411,6 +1461,9 @@ void launch_edge_bwd(TcWork& w, const Dev& D, cudaStream_t s) {
   cudaMemsetAsync(w.t.M2, 0, (size_t)w.num_nodes * kLdp * kLdp * sizeof(float), s);
   cudaMemsetAsync(w.t.zbar, 0, (size_t)w.num_nodes * kLdp * sizeof(float), s);
   cudaMemsetAsync(w.t.done, 0, (size_t)w.num_nodes * sizeof(int), s);
+  cudaMemcpyAsync(w.t.inst_left + w.num_inst, w.inst_init_dev + w.num_inst, sizeof(int) * w.num_inst,
+                  cudaMemcpyDeviceToDevice, s);
+  cudaMemsetAsync(w.t.t_start + 1, 0xFF, sizeof(unsigned long long), s);
   for (int c = 0; c < 2; ++c) {
     const int b = w.it_b[1][c], n = w.it_e[1][c] - b;
     if (!n) continue;

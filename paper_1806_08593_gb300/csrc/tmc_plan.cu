@@ -480,6 +480,12 @@ tmc_status tmc_plan_sync_status(tmc_plan p, void* stream) {
   return TMC_OK;
 }
 
+tmc_status tmc_plan_instance_times(tmc_plan p, double* fwd_us, double* bwd_us) {
+  if (!p || (!fwd_us && !bwd_us)) return TMC_ERR_INVALID_ARG;
+  if (!(p->precision == TMC_PREC_FP16_TC || p->precision == TMC_PREC_BF16_TC)) return TMC_ERR_UNSUPPORTED;
+  return tc::instance_times(p->tcw, p->B, fwd_us, bwd_us);
+}
+
 tmc_status tmc_profile_enable(tmc_plan p, int enable) {
   if (!p) return TMC_ERR_INVALID_ARG;
   if (enable && p->slots.empty()) {

@@ -42,6 +42,10 @@ struct TcDev {
   float* tgP;
   float* CtC;                  // [1 or B][128*128]  C^T C per observation matrix
   int* done;                   // [nodes] tiles finished per node in the running edge launch
+  int* inst_left;              // [2][B] edge tiles still to run per instance (fwd, adjoint)
+  const int* inst_left_init;   // [2][B] their initial values
+  unsigned long long* inst_t;  // [2][B] %globaltimer when an instance's last tile finished
+  unsigned long long* t_start; // [2]    %globaltimer at the first tile of each launch
   int shared;
 };
 
@@ -60,9 +64,11 @@ struct TcWork {
   std::vector<int> nonroot;
   int* d_nonroot = nullptr;
   int maxK = 0;
+  int* inst_init_dev = nullptr;  // workspace copy of the per-instance tile counts
 };
 
 tmc_status supported(const std::vector<NodeInfo>& nodes, int precision);
+tmc_status instance_times(TcWork& w, int B, double* fwd_us, double* bwd_us);
 void workspace_layout(TcWork& w, const std::vector<NodeInfo>& nodes, long long nk, long long nkd,
                       std::vector<TcSub>& subs);
 tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vector<Tile>& tiles,

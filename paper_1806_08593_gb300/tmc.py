@@ -25,7 +25,8 @@ STATUS = {0: "TMC_OK", 1: "TMC_ERR_INVALID_ARG", 2: "TMC_ERR_UNSUPPORTED", 3: "T
 KERNEL_CLASSES = ["sample", "project", "edge_fwd", "root", "edge_bwd", "param"]
 EXPORTS = ["tmc_plan_create", "tmc_log_marginal", "tmc_backward", "tmc_plan_sync_status",
            "tmc_plan_workspace_bytes", "tmc_plan_destroy", "tmc_status_string",
-           "tmc_profile_enable", "tmc_profile_read", "tmc_log_marginal_noalloc"]
+           "tmc_profile_enable", "tmc_profile_read", "tmc_log_marginal_noalloc",
+           "tmc_plan_instance_times"]
 
 
 class TMCError(RuntimeError):
@@ -77,6 +78,8 @@ def load_library(path: str = LIB_PATH):
     lib.tmc_profile_read.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_longlong)]
     lib.tmc_log_marginal_noalloc.argtypes = [ctypes.POINTER(ProblemDesc), ctypes.POINTER(Inputs), P, V]
+    lib.tmc_plan_instance_times.argtypes = [P, P, P]
+    lib.tmc_plan_instance_times.restype = ctypes.c_int
     for f in ("tmc_plan_create", "tmc_log_marginal", "tmc_backward", "tmc_plan_sync_status",
               "tmc_plan_workspace_bytes", "tmc_plan_destroy", "tmc_profile_enable", "tmc_profile_read",
               "tmc_log_marginal_noalloc"):
@@ -183,6 +186,14 @@ class Plan:
         v = ctypes.c_size_t()
         _check(self._lib.tmc_plan_workspace_bytes(self._h, ctypes.byref(v)), "tmc_plan_workspace_bytes")
         return int(v.value)
+
+    def instance_times(self):
+        """(fwd_us, bwd_us): per-instance completion times of the last persistent edge launches."""
+        f = np.zeros(self.B)
+        b = np.zeros(self.B)
+        _check(self._lib.tmc_plan_instance_times(self._h, f.ctypes.data_as(ctypes.c_void_p),
+                                                 b.ctypes.data_as(ctypes.c_void_p)), "tmc_plan_instance_times")
+        return f, b
 
     def profile_enable(self, on: bool = True):
         _check(self._lib.tmc_profile_enable(self._h, int(on)), "tmc_profile_enable")
