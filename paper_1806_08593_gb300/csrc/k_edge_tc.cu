@@ -231,8 +231,10 @@ __global__ void k_sample_tc(Dev D, TcDev T, const Tile* __restrict__ tiles) {
     if (keep32)
       for (int q = 0; q < 4; ++q)
         if (j0 + q < d) D.zt[base + j0 + q] = z[q];
-    *reinterpret_cast<uint2*>(T.ZH + prow + j0) = make_uint2(pack_half2(hi[0], hi[1]), pack_half2(hi[2], hi[3]));
-    *reinterpret_cast<uint2*>(T.ZL + prow + j0) = make_uint2(pack_half2(lo[0], lo[1]), pack_half2(lo[2], lo[3]));
+    if (j0 < d) {  // padding columns stay zero from plan creation
+      *reinterpret_cast<uint2*>(T.ZH + prow + j0) = make_uint2(pack_half2(hi[0], hi[1]), pack_half2(hi[2], hi[3]));
+      *reinterpret_cast<uint2*>(T.ZL + prow + j0) = make_uint2(pack_half2(lo[0], lo[1]), pack_half2(lo[2], lo[3]));
+    }
     for (int o = 16; o > 0; o >>= 1) {
       se += __shfl_xor_sync(0xffffffffu, se, o);
       sz += __shfl_xor_sync(0xffffffffu, sz, o);
@@ -250,21 +252,37 @@ __global__ void k_sample_tc(Dev D, TcDev T, const Tile* __restrict__ tiles) {
   if (bad) atomicOr(D.err, kErrNumeric);
 }
 
-// Split W_i (and its transpose) into padded fp16 hi / lo blocks, one 128 x 128 block per slot.
+// Split W_i (and its transpose) into fp16 hi / lo blocks, one 128-row slot per W_i; only the
+// d_pad x d_pad corner is read by the kernels (the rest of a slot stays zero from creation).
+// Grid: (non-root node, 32-row tile, 32-column tile) of that corner; the transpose goes
+// through shared memory so both writes are coalesced.
 __global__ void k_pack_w(Dev D, TcDev T, const int* __restrict__ nonroot) {
+  __shared__ float tile[32][33];
   const int g = nonroot[blockIdx.x];
   const NodeInfo nd = D.nodes[g];
   if (D.shared && nd.b != 0) return;  // shared parameters: pack once (instance 0's nodes)
-  const int slot = slot_of(D, nd, g), d = nd.d;
+  const int d = nd.d, dp = d > 64 ? 128 : 64;
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.z * 32;
+  if (r0 >= dp || c0 >= dp) return;
+  const int slot = slot_of(D, nd, g);
+  const long long o = (long long)slot * kLdp * kLdp;
   const float* Wi = D.W + nd.off_W;
-  for (int e = blockIdx.y * 1024 + threadIdx.x; e < (blockIdx.y + 1) * 1024; e += blockDim.x) {
-    const int r = e / kLdp, c = e % kLdp;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int i = ty; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + tx;
     const float v = (r < d && c < d) ? Wi[(long long)r * d + c] : 0.f;
+    tile[i][tx] = v;
     float hi, lo;
     split_half(v, hi, lo);
-    const long long o = (long long)slot * kLdp * kLdp;
     T.WH[o + (long long)r * kLdp + c] = __float2half_rn(hi);
     T.WL[o + (long long)r * kLdp + c] = __float2half_rn(lo);
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {  // WT[c][r] = W[r][c]
+    const float v = tile[tx][i];
+    float hi, lo;
+    split_half(v, hi, lo);
+    const int c = c0 + i, r = r0 + tx;
     T.WTH[o + (long long)c * kLdp + r] = __float2half_rn(hi);
     T.WTL[o + (long long)c * kLdp + r] = __float2half_rn(lo);
   }
@@ -1402,6 +1420,7 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
   // zero the packed operand arrays once: padding columns / spare rows are read by the MMAs
   cudaMemset(w.t.ZH, 0, (size_t)w.rows * kLdp * sizeof(__half));
   cudaMemset(w.t.ZL, 0, (size_t)w.rows * kLdp * sizeof(__half));
+  for (__half* a : {w.t.WH, w.t.WL, w.t.WTH, w.t.WTL}) cudaMemset(a, 0, (size_t)w.num_slots * kLdp * kLdp * sizeof(__half));
   const size_t f64 = fwd_smem<64>(maxK), f128 = fwd_smem<128>(maxK);
   cudaFuncSetAttribute(k_edge_fwd_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f64);
   cudaFuncSetAttribute(k_edge_fwd_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f128);
@@ -1437,7 +1456,7 @@ void launch_sample(TcWork& w, const Dev& D, const Tile* tiles, int ntiles, cudaS
 void launch_pack(TcWork& w, const Dev& D, cudaStream_t s) {
   const int n = (int)w.nonroot.size();
   if (!n) return;
-  k_pack_w<<<dim3(n, kLdp * kLdp / 1024), 256, 0, s>>>(D, w.t, w.d_nonroot);
+  k_pack_w<<<dim3(n, kLdp / 32, kLdp / 32), 256, 0, s>>>(D, w.t, w.d_nonroot);
   k_pack_c<<<n, 256, 0, s>>>(D, w.t, w.d_nonroot);
 }
 
