@@ -159,6 +159,17 @@ tmc_status tmc_plan_destroy(tmc_plan plan);
 /* Static, human-readable name of a status code. */
 const char* tmc_status_string(tmc_status s);
 
+/* Work order of the persistent edge launches of a tensor-core plan (the tunable of the
+ * autotuner in the Python binding).  Every order keeps each tile after all tiles it depends
+ * on (the next tree level), so none can deadlock:
+ *   0 (default) level by level, the tiles of one edge adjacent (instance by instance);
+ *   1 level by level, tile index major (tile r of every edge, then tile r+1);
+ *   2 level by level, instances with more edge work (sum of K^2 d) first.
+ * set: synchronises the device and rewrites the plan's tile list (no allocation);
+ * TMC_ERR_UNSUPPORTED on FP32 plans, TMC_ERR_INVALID_ARG for an unknown order. */
+tmc_status tmc_plan_set_schedule(tmc_plan plan, int schedule);
+tmc_status tmc_plan_get_schedule(tmc_plan plan, int* schedule);
+
 /* Per-instance completion times of the last tmc_log_marginal / tmc_backward on a tensor-core
  * plan: the time (microseconds) from the first edge tile of the persistent edge launch to
  * the moment the instance's last edge tile finished, in each direction.  HOST double[B]

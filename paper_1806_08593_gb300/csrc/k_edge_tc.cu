@@ -24,6 +24,7 @@
 // Roles (256 threads): warp 0 issues TMA, warp 1 issues MMAs, warp 2 owns the TMEM
 // allocation, warps 4..7 (128 threads, one sample row each) run the exponentials.
 // Every mbarrier wait is bounded; on a timeout the kernel records kErrTimeout and winds down.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 
@@ -1321,6 +1322,53 @@ size_t bwd_smem(int maxK) {
 }
 }  // namespace
 
+// Edge tiles of both persistent launches in dependency order (every tile's dependencies sit
+// at an earlier level, hence earlier in the list).  Within a level:
+//   schedule 0: instance by instance (the tiles of one edge are adjacent)
+//   schedule 1: tile index major (tile r of every edge, then tile r+1, ...)
+//   schedule 2: instances with more edge work first
+void build_items(TcWork& w, const std::vector<NodeInfo>& nodes, int schedule) {
+  w.tiles.clear();
+  w.schedule = schedule;
+  std::vector<double> work(w.num_inst, 0.0);
+  for (const NodeInfo& nd : nodes)
+    if (nd.parent >= 0) work[nd.b] += (double)nd.K * nd.K * nd.d;
+  for (int dir = 0; dir < 2; ++dir)
+    for (int c = 0; c < 2; ++c) {
+      w.it_b[dir][c] = (int)w.tiles.size();
+      for (int step = 0; step < w.maxlevel; ++step) {
+        const int L = dir == 0 ? w.maxlevel - step : 1 + step;
+        std::vector<int> lv;
+        for (int g = 0; g < (int)nodes.size(); ++g)
+          if (nodes[g].level == L && ((nodes[g].d > 64) ? 1 : 0) == c) lv.push_back(g);
+        if (schedule == 2)
+          std::stable_sort(lv.begin(), lv.end(), [&](int x, int y) { return work[nodes[x].b] > work[nodes[y].b]; });
+        if (schedule == 1) {
+          for (int r = 0;; r += kRows) {
+            bool any = false;
+            for (int g : lv)
+              if (r < nodes[g].K) { w.tiles.push_back(Tile{g, r}); any = true; }
+            if (!any) break;
+          }
+        } else {
+          for (int g : lv)
+            for (int r = 0; r < nodes[g].K; r += kRows) w.tiles.push_back(Tile{g, r});
+        }
+      }
+      w.it_e[dir][c] = (int)w.tiles.size();
+    }
+}
+
+tmc_status set_schedule(TcWork& w, const std::vector<NodeInfo>& nodes, int schedule) {
+  if (schedule < 0 || schedule > 2) return TMC_ERR_INVALID_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return TMC_ERR_CUDA;
+  build_items(w, nodes, schedule);
+  if (!w.tiles.empty() &&
+      cudaMemcpy(w.d_tiles, w.tiles.data(), sizeof(Tile) * w.tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return TMC_ERR_CUDA;
+  return TMC_OK;
+}
+
 tmc_status supported(const std::vector<NodeInfo>& nodes, int precision) {
   if (precision != TMC_PREC_FP16_TC) return TMC_ERR_UNSUPPORTED;  // split-fp16 kernels only
   for (const NodeInfo& nd : nodes)
@@ -1376,21 +1424,7 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
   int maxlevel = 0;
   for (const NodeInfo& nd : nodes) maxlevel = std::max(maxlevel, nd.level);
   w.maxlevel = maxlevel;
-  w.tiles.clear();
-  // forward items: deepest level first; backward items: level 1 first (per d class)
-  for (int dir = 0; dir < 2; ++dir)
-    for (int c = 0; c < 2; ++c) {
-      w.it_b[dir][c] = (int)w.tiles.size();
-      for (int step = 0; step < maxlevel; ++step) {
-        const int L = dir == 0 ? maxlevel - step : 1 + step;
-        for (int g = 0; g < (int)nodes.size(); ++g) {
-          const NodeInfo& nd = nodes[g];
-          if (nd.level != L || ((nd.d > 64) ? 1 : 0) != c) continue;
-          for (int r = 0; r < nd.K; r += kRows) w.tiles.push_back(Tile{g, r});
-        }
-      }
-      w.it_e[dir][c] = (int)w.tiles.size();
-    }
+  build_items(w, nodes, 0);
   cudaDeviceGetAttribute(&w.num_sms, cudaDevAttrMultiProcessorCount, 0);
   {
     int dev = 0;

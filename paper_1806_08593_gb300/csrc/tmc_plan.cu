@@ -480,6 +480,18 @@ tmc_status tmc_plan_sync_status(tmc_plan p, void* stream) {
   return TMC_OK;
 }
 
+tmc_status tmc_plan_set_schedule(tmc_plan p, int schedule) {
+  if (!p) return TMC_ERR_INVALID_ARG;
+  if (!(p->precision == TMC_PREC_FP16_TC || p->precision == TMC_PREC_BF16_TC)) return TMC_ERR_UNSUPPORTED;
+  return tc::set_schedule(p->tcw, p->nodes, schedule);
+}
+
+tmc_status tmc_plan_get_schedule(tmc_plan p, int* schedule) {
+  if (!p || !schedule) return TMC_ERR_INVALID_ARG;
+  *schedule = p->tcw.schedule;
+  return TMC_OK;
+}
+
 tmc_status tmc_plan_instance_times(tmc_plan p, double* fwd_us, double* bwd_us) {
   if (!p || (!fwd_us && !bwd_us)) return TMC_ERR_INVALID_ARG;
   if (!(p->precision == TMC_PREC_FP16_TC || p->precision == TMC_PREC_BF16_TC)) return TMC_ERR_UNSUPPORTED;

@@ -65,9 +65,12 @@ struct TcWork {
   int* d_nonroot = nullptr;
   int maxK = 0;
   int* inst_init_dev = nullptr;  // workspace copy of the per-instance tile counts
+  int schedule = 0;              // work order of the persistent launches (see build_items)
 };
 
 tmc_status supported(const std::vector<NodeInfo>& nodes, int precision);
+void build_items(TcWork& w, const std::vector<NodeInfo>& nodes, int schedule);
+tmc_status set_schedule(TcWork& w, const std::vector<NodeInfo>& nodes, int schedule);
 tmc_status instance_times(TcWork& w, int B, double* fwd_us, double* bwd_us);
 void workspace_layout(TcWork& w, const std::vector<NodeInfo>& nodes, long long nk, long long nkd,
                       std::vector<TcSub>& subs);

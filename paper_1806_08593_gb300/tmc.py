@@ -26,7 +26,7 @@ KERNEL_CLASSES = ["sample", "project", "edge_fwd", "root", "edge_bwd", "param"]
 EXPORTS = ["tmc_plan_create", "tmc_log_marginal", "tmc_backward", "tmc_plan_sync_status",
            "tmc_plan_workspace_bytes", "tmc_plan_destroy", "tmc_status_string",
            "tmc_profile_enable", "tmc_profile_read", "tmc_log_marginal_noalloc",
-           "tmc_plan_instance_times"]
+           "tmc_plan_instance_times", "tmc_plan_set_schedule", "tmc_plan_get_schedule"]
 
 
 class TMCError(RuntimeError):
@@ -80,6 +80,10 @@ def load_library(path: str = LIB_PATH):
     lib.tmc_log_marginal_noalloc.argtypes = [ctypes.POINTER(ProblemDesc), ctypes.POINTER(Inputs), P, V]
     lib.tmc_plan_instance_times.argtypes = [P, P, P]
     lib.tmc_plan_instance_times.restype = ctypes.c_int
+    lib.tmc_plan_set_schedule.argtypes = [P, ctypes.c_int]
+    lib.tmc_plan_set_schedule.restype = ctypes.c_int
+    lib.tmc_plan_get_schedule.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
+    lib.tmc_plan_get_schedule.restype = ctypes.c_int
     for f in ("tmc_plan_create", "tmc_log_marginal", "tmc_backward", "tmc_plan_sync_status",
               "tmc_plan_workspace_bytes", "tmc_plan_destroy", "tmc_profile_enable", "tmc_profile_read",
               "tmc_log_marginal_noalloc"):
@@ -185,6 +189,14 @@ class Plan:
     def workspace_bytes(self) -> int:
         v = ctypes.c_size_t()
         _check(self._lib.tmc_plan_workspace_bytes(self._h, ctypes.byref(v)), "tmc_plan_workspace_bytes")
+        return int(v.value)
+
+    def set_schedule(self, schedule: int):
+        _check(self._lib.tmc_plan_set_schedule(self._h, int(schedule)), "tmc_plan_set_schedule")
+
+    def get_schedule(self) -> int:
+        v = ctypes.c_int()
+        _check(self._lib.tmc_plan_get_schedule(self._h, ctypes.byref(v)), "tmc_plan_get_schedule")
         return int(v.value)
 
     def instance_times(self):
