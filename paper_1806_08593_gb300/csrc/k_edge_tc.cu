@@ -177,10 +177,17 @@ __host__ __device__ constexpr int ring_bytes(int DP) {
 
 // =======================================================================================
 // Samples for the tensor-core path: z~ = exp(logs) eps split into fp16 hi / lo rows of the
-// packed operand array, |z~|^2 and the per-sample node term (as in the FP32 path); FP32
-// samples are kept for the root and the leaves (prior / observation terms).
+// packed operand array, |z~|^2, z~ . c_i and the per-sample node term (as in the FP32 path);
+// FP32 samples are kept for the root (its moments are formed from them).
 // =======================================================================================
-__global__ void k_sample_tc(Dev D, TcDev T, const Tile* __restrict__ tiles) {
+// Lane mapping: a row of d floats is served by L = 2^ceil(log2(ceil(d / 4))) lanes (float4
+// each), so a warp covers 32 / L rows per pass, and every thread loads kSampleU rows before it
+// computes (several 16-byte loads in flight per lane).
+constexpr int kSampleU = 4;
+// Sample rows per CTA: 64 at d > 64, doubling as d halves (512 at d <= 16), so a CTA streams
+// a similar number of bytes whatever d is.
+__host__ __device__ constexpr int sample_rows(int d) { return d > 64 ? 64 : d > 32 ? 128 : d > 16 ? 256 : 512; }
+__global__ void __launch_bounds__(256) k_sample_tc(Dev D, TcDev T, const Tile* __restrict__ tiles) {
   extern __shared__ float sm[];
   const Tile t = tiles[blockIdx.x];
   const NodeInfo nd = D.nodes[t.node];
@@ -188,66 +195,78 @@ __global__ void k_sample_tc(Dev D, TcDev T, const Tile* __restrict__ tiles) {
   float* s_std = sm;
   float* s_off = sm + kTcMaxD;
   float* s_c = sm + 2 * kTcMaxD;
-  const bool root = nd.parent < 0, keep32 = root || nd.leaf_slot >= 0;
+  const bool root = nd.parent < 0;
   for (int j = threadIdx.x; j < kTcMaxD; j += blockDim.x) {
     s_std[j] = j < d ? expf(D.q_logstd[nd.off_q + j]) : 0.f;
     s_off[j] = (root && j < d) ? D.q_mean[nd.off_q + j] - D.bias[nd.off_bias + j] : 0.f;
-    s_c[j] = root ? 0.f : T.cvec[(long long)t.node * kLdp + j];
+    s_c[j] = (root || j >= d) ? 0.f : T.cvec[(long long)t.node * kLdp + j];
   }
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lg = d > 64 ? 5 : d > 32 ? 4 : d > 16 ? 3 : d > 8 ? 2 : d > 4 ? 1 : 0;
+  const int L = 1 << lg, rpw = 32 >> lg, pass = (blockDim.x >> 5) * rpw;
+  const int j0 = 4 * (lane & (L - 1));
+  const int rlane = w * rpw + (lane >> lg);
   const bool vec = (d & 3) == 0 && (nd.off_nkd & 3) == 0;
+  const int rows = min(sample_rows(d), nd.K - t.row0);
   bool bad = false;
-  for (int r = w; r < kTile; r += blockDim.x / 32) {
-    const int k = t.row0 + r;
-    if (k >= nd.K) break;
-    const long long base = nd.off_nkd + (long long)k * d;
-    const long long prow = (nd.off_nk + k) * kLdp;
-    float se = 0.f, sz = 0.f, sr = 0.f, szc = 0.f;
-    // lane owns columns 4*lane .. 4*lane+3 of the 128-wide packed row
-    const int j0 = 4 * lane;
-    float e[4] = {0.f, 0.f, 0.f, 0.f};
-    if (vec) {
-      if (j0 < d) {
-        const float4 v = *reinterpret_cast<const float4*>(D.eps + base + j0);
-        e[0] = v.x; e[1] = v.y; e[2] = v.z; e[3] = v.w;
+  for (int base = 0; base < rows; base += kSampleU * pass) {
+    float e[kSampleU][4];
+#pragma unroll
+    for (int u = 0; u < kSampleU; ++u) {
+      const int r = base + u * pass + rlane;
+      const long long off = nd.off_nkd + (long long)(t.row0 + r) * d + j0;
+      e[u][0] = e[u][1] = e[u][2] = e[u][3] = 0.f;
+      if (r < rows && j0 < d) {
+        if (vec) {
+          const float4 v = __ldcs(reinterpret_cast<const float4*>(D.eps + off));
+          e[u][0] = v.x; e[u][1] = v.y; e[u][2] = v.z; e[u][3] = v.w;
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (j0 + q < d) e[u][q] = D.eps[off + q];
+        }
       }
-    } else {
+    }
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (j0 + q < d) e[q] = D.eps[base + j0 + q];
-    }
-    float z[4], hi[4], lo[4];
+    for (int u = 0; u < kSampleU; ++u) {
+      const int r = base + u * pass + rlane;
+      const int k = t.row0 + r;
+      float se = 0.f, sz = 0.f, sr = 0.f, szc = 0.f;
+      float z[4], hi[4], lo[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      z[q] = s_std[j0 + q] * e[q];
-      bad |= !isfinite(z[q]);
-      se = fmaf(e[q], e[q], se);
-      sz = fmaf(z[q], z[q], sz);
-      szc = fmaf(z[q], s_c[j0 + q], szc);
-      const float rr = (j0 + q < d) ? z[q] + s_off[j0 + q] : 0.f;
-      sr = fmaf(rr, rr, sr);
-      split_half(z[q], hi[q], lo[q]);
-    }
-    if (keep32)
-      for (int q = 0; q < 4; ++q)
-        if (j0 + q < d) D.zt[base + j0 + q] = z[q];
-    if (j0 < d) {  // padding columns stay zero from plan creation
-      *reinterpret_cast<uint2*>(T.ZH + prow + j0) = make_uint2(pack_half2(hi[0], hi[1]), pack_half2(hi[2], hi[3]));
-      *reinterpret_cast<uint2*>(T.ZL + prow + j0) = make_uint2(pack_half2(lo[0], lo[1]), pack_half2(lo[2], lo[3]));
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      se += __shfl_xor_sync(0xffffffffu, se, o);
-      sz += __shfl_xor_sync(0xffffffffu, sz, o);
-      sr += __shfl_xor_sync(0xffffffffu, sr, o);
-      szc += __shfl_xor_sync(0xffffffffu, szc, o);
-    }
-    if (lane == 0) {
-      float u = 0.5f * se;
-      if (root) u -= 0.5f * sr * D.inv_var;
-      D.u[nd.off_nk + k] = u;
-      D.zn[nd.off_nk + k] = sz;
-      T.zc[nd.off_nk + k] = szc;
+      for (int q = 0; q < 4; ++q) {
+        z[q] = s_std[j0 + q] * e[u][q];
+        bad |= !isfinite(z[q]);
+        se = fmaf(e[u][q], e[u][q], se);
+        sz = fmaf(z[q], z[q], sz);
+        szc = fmaf(z[q], s_c[j0 + q], szc);
+        const float rr = (j0 + q < d) ? z[q] + s_off[j0 + q] : 0.f;
+        sr = fmaf(rr, rr, sr);
+        split_half(z[q], hi[q], lo[q]);
+      }
+      const bool live = r < rows;
+      if (live && j0 < d) {  // padding columns stay zero from plan creation
+        if (root)
+          for (int q = 0; q < 4; ++q)
+            if (j0 + q < d) D.zt[nd.off_nkd + (long long)k * d + j0 + q] = z[q];
+        const long long prow = (nd.off_nk + k) * kLdp;
+        *reinterpret_cast<uint2*>(T.ZH + prow + j0) = make_uint2(pack_half2(hi[0], hi[1]), pack_half2(hi[2], hi[3]));
+        *reinterpret_cast<uint2*>(T.ZL + prow + j0) = make_uint2(pack_half2(lo[0], lo[1]), pack_half2(lo[2], lo[3]));
+      }
+      for (int o = L >> 1; o > 0; o >>= 1) {
+        se += __shfl_xor_sync(0xffffffffu, se, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        szc += __shfl_xor_sync(0xffffffffu, szc, o);
+      }
+      if (live && (lane & (L - 1)) == 0) {
+        float uu = 0.5f * se;
+        if (root) uu -= 0.5f * sr * D.inv_var;
+        D.u[nd.off_nk + k] = uu;
+        D.zn[nd.off_nk + k] = sz;
+        T.zc[nd.off_nk + k] = szc;
+      }
     }
   }
   if (bad) atomicOr(D.err, kErrNumeric);
@@ -264,7 +283,7 @@ __global__ void k_pack_w(Dev D, TcDev T, const int* __restrict__ nonroot) {
   if (D.shared && nd.b != 0) return;  // shared parameters: pack once (instance 0's nodes)
   const int d = nd.d, dp = d > 64 ? 128 : 64;
   const int r0 = blockIdx.y * 32, c0 = blockIdx.z * 32;
-  if (r0 >= dp || c0 >= dp) return;
+  if (r0 >= d || c0 >= d) return;  // tiles beyond d stay zero from plan creation
   const int slot = slot_of(D, nd, g);
   const long long o = (long long)slot * kLdp * kLdp;
   const float* Wi = D.W + nd.off_W;
@@ -289,22 +308,196 @@ __global__ void k_pack_w(Dev D, TcDev T, const int* __restrict__ nonroot) {
   }
 }
 
-// c_i = W_i m_p + bias_i - m_i per non-root node.
-__global__ void k_pack_c(Dev D, TcDev T, const int* __restrict__ nonroot) {
+// c_i = W_i m_p + bias_i - m_i per non-root node (zero in the padding up to d_pad).  One
+// thread per row of W_i, each streaming its own row (independent loads).
+__global__ void __launch_bounds__(128) k_pack_c(Dev D, TcDev T, const int* __restrict__ nonroot) {
+  __shared__ __align__(16) float mp[kTcMaxD];
   const int g = nonroot[blockIdx.x];
   const NodeInfo nd = D.nodes[g];
   const NodeInfo pn = D.nodes[nd.parent];
-  const int d = nd.d;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int r = w; r < kLdp; r += blockDim.x / 32) {
+  const int d = nd.d, dp = d > 64 ? 128 : 64;
+  for (int j = threadIdx.x; j < kTcMaxD; j += blockDim.x) mp[j] = j < d ? D.q_mean[pn.off_q + j] : 0.f;
+  __syncthreads();
+  const bool vec = (d & 3) == 0 && (nd.off_W & 3) == 0;
+  for (int r = threadIdx.x; r < dp; r += blockDim.x) {
     float s = 0.f;
     if (r < d) {
       const float* wr = D.W + nd.off_W + (long long)r * d;
-      for (int c = lane; c < d; c += 32) s = fmaf(wr[c], D.q_mean[pn.off_q + c], s);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      s += D.bias[nd.off_bias + r] - D.q_mean[nd.off_q + r];
+      float s0 = 0.f, s1 = 0.f;
+      if (vec) {
+        for (int c = 0; c < d; c += 8) {
+          const float4 a = *reinterpret_cast<const float4*>(wr + c);
+          s0 = fmaf(a.x, mp[c], s0); s0 = fmaf(a.y, mp[c + 1], s0);
+          s0 = fmaf(a.z, mp[c + 2], s0); s0 = fmaf(a.w, mp[c + 3], s0);
+          if (c + 4 < d) {
+            const float4 b = *reinterpret_cast<const float4*>(wr + c + 4);
+            s1 = fmaf(b.x, mp[c + 4], s1); s1 = fmaf(b.y, mp[c + 5], s1);
+            s1 = fmaf(b.z, mp[c + 6], s1); s1 = fmaf(b.w, mp[c + 7], s1);
+          }
+        }
+      } else {
+        for (int c = 0; c < d; ++c) s0 = fmaf(wr[c], mp[c], s0);
+      }
+      s = (s0 + s1) + D.bias[nd.off_bias + r] - D.q_mean[nd.off_q + r];
     }
-    if (lane == 0) T.cvec[(long long)g * kLdp + r] = s;
+    T.cvec[(long long)g * kLdp + r] = s;
+  }
+}
+
+// Centred observations of the leaves, x~_l = x_l - C m_l, kept for the observation kernel
+// and the gradient assembly.  Grid: one CTA per leaf; thread per observation row, each thread
+// streaming its own row of C (independent loads, no per-row reduction chain).
+__global__ void __launch_bounds__(128) k_obs_center(Dev D, TcDev T, const int* __restrict__ leaves) {
+  __shared__ __align__(16) float m[kTcMaxD];
+  const NodeInfo nd = D.nodes[leaves[blockIdx.x]];
+  const int d = nd.d;
+  for (int j = threadIdx.x; j < kTcMaxD; j += blockDim.x) m[j] = j < d ? D.q_mean[nd.off_q + j] : 0.f;
+  __syncthreads();
+  const bool vec = (d & 3) == 0 && (nd.off_C & 3) == 0;
+  for (int o = threadIdx.x; o < nd.obs; o += blockDim.x) {
+    const float* c = D.C + nd.off_C + (long long)o * d;
+    float s0 = 0.f, s1 = 0.f;
+    if (vec) {
+      for (int i = 0; i < d; i += 8) {
+        const float4 a = *reinterpret_cast<const float4*>(c + i);
+        s0 = fmaf(a.x, m[i], s0); s0 = fmaf(a.y, m[i + 1], s0);
+        s0 = fmaf(a.z, m[i + 2], s0); s0 = fmaf(a.w, m[i + 3], s0);
+        if (i + 4 < d) {
+          const float4 b = *reinterpret_cast<const float4*>(c + i + 4);
+          s1 = fmaf(b.x, m[i + 4], s1); s1 = fmaf(b.y, m[i + 5], s1);
+          s1 = fmaf(b.z, m[i + 6], s1); s1 = fmaf(b.w, m[i + 7], s1);
+        }
+      }
+    } else {
+      for (int i = 0; i < d; ++i) s0 = fmaf(c[i], m[i], s0);
+    }
+    T.xs[nd.off_x + o] = D.x[nd.off_x + o] - (s0 + s1);
+  }
+}
+
+// Split observation matrices: CH / CL row c_row[b] + o = C_b[o][0..d) as fp16 hi / lo, zero
+// beyond d.  Grid: (distinct matrix, pair of rows); thread = (row of the pair, column).
+__global__ void __launch_bounds__(256) k_pack_cobs(Dev D, TcDev T) {
+  const InstInfo in = D.insts[blockIdx.x];
+  const int o = blockIdx.y * 2 + (threadIdx.x >> 7), j = threadIdx.x & 127;
+  if (o >= in.obs) return;
+  const float v = j < in.d ? D.C[in.off_C + (long long)o * in.d + j] : 0.f;
+  float hi, lo;
+  split_half(v, hi, lo);
+  const long long r = (long long)T.c_row[blockIdx.x] + o;
+  T.CH[r * kLdp + j] = __float2half_rn(hi);
+  T.CL[r * kLdp + j] = __float2half_rn(lo);
+}
+
+// =======================================================================================
+// Observation term of the leaves on the tensor cores:
+//   u_l[k] -= |x~ - C z~^k|^2 / (2 obs_var),   x~ = x - C m_l   (z = m_l + z~),
+// with C z~^k formed as split-fp16 products (hi*hi + lo*hi + hi*lo, FP32 accumulation) in
+// 128-observation chunks.  Grid: one CTA per 128-sample tile of a leaf; 128 threads: thread 0
+// issues the TMA loads and the MMAs, all four warps form x~ and reduce the accumulator rows
+// (thread t owns sample row t = TMEM lane t).
+// =======================================================================================
+template <int DP>
+__global__ void __launch_bounds__(128) k_obs_tc(Dev D, TcDev T, const Tile* __restrict__ tiles,
+                                                 const __grid_constant__ CUtensorMap mZH,
+                                                 const __grid_constant__ CUtensorMap mZL,
+                                                 const __grid_constant__ CUtensorMap mCH,
+                                                 const __grid_constant__ CUtensorMap mCL) {
+  constexpr int TB = kRows * DP * 2;
+  constexpr int NB = DP / 64;
+  constexpr int KS = DP / 16;
+  extern __shared__ unsigned char smraw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  unsigned char *ah = sm, *al = sm + TB, *bh = sm + 2 * TB, *bl = sm + 3 * TB;
+  float* xs = reinterpret_cast<float*>(sm + 4 * TB);  // centred observation (obs floats)
+  __shared__ uint64_t bar_ld, bar_mma;
+  __shared__ uint32_t tbase;
+  __shared__ int s_ok;
+  const Tile t = tiles[blockIdx.x];
+  const NodeInfo nd = D.nodes[t.node];
+  const int obs = nd.obs;
+  const int nchunk = (obs + kRows - 1) / kRows;
+  const int crow = T.c_row[D.shared ? 0 : nd.b];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) tmem_alloc(&tbase, 128);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar_ld, 1);
+    mbar_init(&bar_mma, 1);
+    fence_barrier_init();
+    s_ok = 1;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tb = tbase;
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(&bar_ld, 4 * TB);
+    const int arow = (int)(nd.off_nk + t.row0);
+    for (int b = 0; b < NB; ++b) {
+      tma_load_2d(ah + b * kBox, &mZH, &bar_ld, b * 64, arow);
+      tma_load_2d(al + b * kBox, &mZL, &bar_ld, b * 64, arow);
+      tma_load_2d(bh + b * kBox, &mCH, &bar_ld, b * 64, crow);
+      tma_load_2d(bl + b * kBox, &mCL, &bar_ld, b * 64, crow);
+    }
+  }
+  for (int o = threadIdx.x; o < obs; o += blockDim.x) xs[o] = T.xs[nd.off_x + o];  // x~ = x - C m
+  __syncthreads();
+  const uint32_t idesc = idesc_f16(kRows, kRows, false, false, false);
+  float rs = 0.f;
+  for (int c = 0; c < nchunk; ++c) {
+    if (threadIdx.x == 0) {
+      if (c > 0) {
+        mbar_arrive_expect_tx(&bar_ld, 2 * TB);
+        for (int b = 0; b < NB; ++b) {
+          tma_load_2d(bh + b * kBox, &mCH, &bar_ld, b * 64, crow + c * kRows);
+          tma_load_2d(bl + b * kBox, &mCL, &bar_ld, b * 64, crow + c * kRows);
+        }
+      }
+      if (mbar_wait(&bar_ld, c & 1)) {
+        tc_fence_after();
+        for (int kk = 0; kk < KS; ++kk) mma_ss(tb, kdesc(ah, kk), kdesc(bh, kk), idesc, kk > 0);
+        for (int kk = 0; kk < KS; ++kk) mma_ss(tb, kdesc(al, kk), kdesc(bh, kk), idesc, 1);
+        for (int kk = 0; kk < KS; ++kk) mma_ss(tb, kdesc(ah, kk), kdesc(bl, kk), idesc, 1);
+        mma_commit(&bar_mma);
+      } else {
+        set_timeout(D);
+        mbar_wait(&bar_ld, c & 1);  // once more (bounded) for the copies still in flight
+        s_ok = 0;
+      }
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&bar_mma, c & 1));
+    tc_fence_after();
+    if (ok) {
+#pragma unroll 1
+      for (int q = 0; q < 4; ++q) {
+        const int o0 = c * kRows + q * 32;
+        if (o0 >= obs) break;
+        uint32_t v[32];
+        tmem_ld32(tb + ((uint32_t)(warp * 32) << 16) + q * 32, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float r = (o0 + j < obs) ? xs[o0 + j] - __uint_as_float(v[j]) : 0.f;
+          rs = fmaf(r, r, rs);
+        }
+      }
+    } else {
+      if (lane == 0) set_timeout(D);
+      mbar_wait(&bar_mma, c & 1);  // once more (bounded) before the accumulator is released
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (!ok) break;
+  }
+  const int k = t.row0 + threadIdx.x;
+  if (s_ok && k < nd.K) D.u[nd.off_nk + k] -= 0.5f * rs * D.inv_obs_var;
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tb, 128);
   }
 }
 
@@ -973,22 +1166,25 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 
 // =======================================================================================
 // Root moments: zbar_0 = sum_k q_0 z~_0, M2_0 = sum_k q_0 z~_0 z~_0^T (FP32 samples).
-// Grid: (instance, 64-row tile, 64-col tile).
+// Grid: (instance, 64x64 tile of M2 (2 x 2), 256-sample slab); slabs add into M2 / zbar,
+// which start at zero.
 // =======================================================================================
+constexpr int kRootSlab = 256;
 __global__ void __launch_bounds__(kThreads) k_root_moments(Dev D, TcDev T) {
   __shared__ TileSmem sm;
   __shared__ float qz[kTile * kLd];
   const InstInfo in = D.insts[blockIdx.x];
   const NodeInfo nd = D.nodes[in.node0];
   const int d = nd.d, K = nd.K;
-  const int a0 = blockIdx.y * kTile, b0 = blockIdx.z * kTile;
-  if (a0 >= d || b0 >= d) return;
+  const int a0 = (blockIdx.y >> 1) * kTile, b0 = (blockIdx.y & 1) * kTile;
+  const int kb = blockIdx.z * kRootSlab, ke = min(K, kb + kRootSlab);
+  if (a0 >= d || b0 >= d || kb >= K) return;
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
   float acc[4][4];
   zero_acc(acc);
   float zs = 0.f;
-  for (int k0 = 0; k0 < K; k0 += kTile) {
-    const int rows = min(kTile, K - k0);
+  for (int k0 = kb; k0 < ke; k0 += kTile) {
+    const int rows = min(kTile, ke - k0);
     // qz[l = k][m = a] = q[k] z~[k][a0 + m]
     for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
       const int l = e >> 6, m = e & 63;
@@ -1012,10 +1208,10 @@ __global__ void __launch_bounds__(kThreads) k_root_moments(Dev D, TcDev T) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int a = a0 + ty * 4 + i, b = b0 + tx * 4 + j;
-      if (a < d && b < d) M[(long long)a * kLdp + b] = acc[i][j];
+      if (a < d && b < d) atomicAdd(M + (long long)a * kLdp + b, acc[i][j]);
     }
   if (b0 == 0 && threadIdx.x < kTile && a0 + threadIdx.x < d)
-    T.zbar[(long long)in.node0 * kLdp + a0 + threadIdx.x] = zs;
+    atomicAdd(T.zbar + (long long)in.node0 * kLdp + a0 + threadIdx.x, zs);
 }
 
 // =======================================================================================
@@ -1038,42 +1234,44 @@ __global__ void __launch_bounds__(128) k_asm_edge_vec(Dev D, TcDev T, const int*
   const float iv = D.inv_var;
   const float go = D.grad_out ? (float)D.grad_out[nd.b] : 1.f;
   const float* W = D.W + nd.off_W;
-  const float* Gc = T.G + (long long)g * kLdp * kLdp;
-  const float* M2c = T.M2 + (long long)g * kLdp * kLdp;
   const float* zbc = T.zbar + (long long)g * kLdp;
   const float* cc = T.cvec + (long long)g * kLdp;
-  const int j = threadIdx.x;
+  const int j = threadIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (j < d) zp[j] = T.zbar[(long long)nd.parent * kLdp + j];
   __syncthreads();
-  if (j < d) {
+  // (W_c zbar_p)[r]: one warp per row, lanes along the row (coalesced)
+  for (int r = w; r < d; r += 4) {
     float s = 0.f;
-    for (int c = 0; c < d; ++c) s = fmaf(W[(long long)j * d + c], zp[c], s);
-    const float db = (zbc[j] - s - cc[j]) * iv;
-    dbs[j] = db;
-    T.sgC[(long long)g * kLdp + j] = -db;
-    if (D.shared) { if (D.pbias) D.pbias[nd.off_q + j] = go * db; }
-    else if (D.dbias) D.dbias[nd.off_bias + j] = go * db;
+    for (int c = lane; c < d; c += 32) s = fmaf(W[(long long)r * d + c], zp[c], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) dbs[r] = (zbc[r] - s - cc[r]) * iv;
   }
   __syncthreads();
   if (j >= d) return;
-  // diag(W_c G_c)[j] = sum_a W[j][a] G[a][j];  (W^T db')[j] = sum_a W[a][j] db'[a]
-  float wg = 0.f, sg = 0.f;
-  for (int a = 0; a < d; ++a) {
-    wg = fmaf(W[(long long)j * d + a], Gc[(long long)a * kLdp + j], wg);
-    sg = fmaf(W[(long long)a * d + j], dbs[a], sg);
-  }
-  T.tgC[(long long)g * kLdp + j] = (wg + cc[j] * zbc[j] - M2c[(long long)j * kLdp + j]) * iv;
+  const float db = dbs[j];
+  T.sgC[(long long)g * kLdp + j] = -db;
+  if (D.shared) { if (D.pbias) D.pbias[nd.off_q + j] = go * db; }
+  else if (D.dbias) D.dbias[nd.off_bias + j] = go * db;
+  // (W^T db')[j] = sum_a W[a][j] db'[a] (coalesced over j).  The child-side sum of g z~ is
+  // diag(W_c G_c) / var (k_asm_edge_mat, which holds both tiles, into the zeroed tgC) plus
+  // (c_c zbar_c - diag M2_c) / var (added by k_asm_node)
+  float sg = 0.f;
+  for (int a = 0; a < d; ++a) sg = fmaf(W[(long long)a * d + j], dbs[a], sg);
   T.sgP[(long long)g * kLdp + j] = sg;
 }
 
+// Grid: (edge, 64x64 tile of D_c (2 x 2)).  The W_c and G_c^T tiles are staged through
+// shared memory (coalesced reads of both); row sums of W_c o G_c^T give diag(W_c G_c), column
+// sums of W_c o D_c give diag(W_c^T D_c).
 __global__ void __launch_bounds__(kThreads) k_asm_edge_mat(Dev D, TcDev T, const int* __restrict__ nonroot) {
   __shared__ TileSmem sm;
+  __shared__ float sW[kTile][kTile + 1], sG[kTile][kTile + 1];
   __shared__ float colpart[16][kTile + 1];
   const int g = nonroot[blockIdx.x];
   const NodeInfo nd = D.nodes[g];
   const NodeInfo pn = D.nodes[nd.parent];
   const int d = nd.d;
-  const int a0 = blockIdx.y * kTile, b0 = blockIdx.z * kTile;
+  const int a0 = (blockIdx.y >> 1) * kTile, b0 = (blockIdx.y & 1) * kTile;
   if (a0 >= d || b0 >= d) return;
   const float iv = D.inv_var;
   const float go = D.grad_out ? (float)D.grad_out[nd.b] : 1.f;
@@ -1081,30 +1279,46 @@ __global__ void __launch_bounds__(kThreads) k_asm_edge_mat(Dev D, TcDev T, const
   const float* Gc = T.G + (long long)g * kLdp * kLdp;
   const float* M2p = T.M2 + (long long)nd.parent * kLdp * kLdp;
   const float* zbp = T.zbar + (long long)nd.parent * kLdp;
-  const float* zbc = T.zbar + (long long)g * kLdp;
   const float* cc = T.cvec + (long long)g * kLdp;
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  // sW[r][c] = W[a0 + r][b0 + c],  sG[r][c] = G[b0 + r][a0 + c]  (so G^T[a][b] = sG[b][a])
+  for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+    const int r = e >> 6, c = e & 63;
+    sW[r][c] = (a0 + r < d && b0 + c < d) ? W[(long long)(a0 + r) * d + b0 + c] : 0.f;
+    sG[r][c] = (b0 + r < d && a0 + c < d) ? Gc[(long long)(b0 + r) * kLdp + a0 + c] : 0.f;
+  }
   float acc[4][4];
   zero_acc(acc);
-  // acc[a][b] = sum_j W[a][j] M2_p[j][b]
+  // acc[a][b] = sum_j W[a][j] M2_p[j][b]   (tile_gemm synchronises before its first read)
   tile_gemm<true, false>(acc, W + (long long)a0 * d, d, min(kTile, d - a0), M2p + b0, kLdp,
                          min(kTile, d - b0), d, sm);
   float tcol[4] = {0.f, 0.f, 0.f, 0.f};
+  float wrow[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int a = a0 + ty * 4 + i;
-    if (a >= d) continue;
-    const float db = -T.sgC[(long long)g * kLdp + a];  // db'[a], stored by k_asm_edge_vec
+    const int al = ty * 4 + i, a = a0 + al;
+    const float db = a < d ? -T.sgC[(long long)g * kLdp + a] : 0.f;  // db'[a], from k_asm_edge_vec
+    const float ca = a < d ? cc[a] : 0.f;
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
-      const int bb = b0 + tx * 4 + jj;
-      if (bb >= d) continue;
-      const float Dab = (Gc[(long long)bb * kLdp + a] - acc[i][jj] - cc[a] * zbp[bb]) * iv;
-      tcol[jj] = fmaf(W[(long long)a * d + bb], Dab, tcol[jj]);
+      const int bl = tx * 4 + jj, bb = b0 + bl;
+      if (a >= d || bb >= d) continue;
+      const float wab = sW[al][bl], gt = sG[bl][al];
+      const float Dab = (gt - acc[i][jj] - ca * zbp[bb]) * iv;
+      tcol[jj] = fmaf(wab, Dab, tcol[jj]);
+      wrow[i] = fmaf(wab, gt, wrow[i]);
       const float v = go * (Dab + db * D.q_mean[pn.off_q + bb]);
       if (D.shared) { if (D.pW) D.pW[nd.off_pW + (long long)a * d + bb] = v; }
       else if (D.dW) D.dW[nd.off_W + (long long)a * d + bb] = v;
     }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {  // the 16 threads of one ty sit in one half-warp
+    float v = wrow[i];
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int a = a0 + ty * 4 + i;
+    // two column tiles per row into a zeroed entry: the two additions commute exactly
+    if (tx == 0 && a < d) atomicAdd(T.tgC + (long long)g * kLdp + a, v * iv);
   }
 #pragma unroll
   for (int jj = 0; jj < 4; ++jj) colpart[ty][tx * 4 + jj] = tcol[jj];
@@ -1112,22 +1326,23 @@ __global__ void __launch_bounds__(kThreads) k_asm_edge_mat(Dev D, TcDev T, const
   if (threadIdx.x < kTile && b0 + threadIdx.x < d) {
     float s = 0.f;
     for (int i = 0; i < 16; ++i) s += colpart[i][threadIdx.x];
-    // at most two row tiles per column: the two additions commute exactly
     atomicAdd(T.tgP + (long long)g * kLdp + b0 + threadIdx.x, s);
   }
 }
 
 // C^T C per distinct observation matrix (one for shared parameters, else one per instance).
+// Grid: (matrix, 64x64 tile (2 x 2), 64-row slab of C); slabs add into the zeroed C^T C.
 __global__ void __launch_bounds__(kThreads) k_ctc(Dev D, TcDev T) {
   __shared__ TileSmem sm;
   const InstInfo in = D.insts[blockIdx.x];
   const int d = in.d, obs = in.obs;
-  const int a0 = blockIdx.y * kTile, b0 = blockIdx.z * kTile;
-  if (a0 >= d || b0 >= d) return;
-  const float* C = D.C + in.off_C;
+  const int a0 = (blockIdx.y >> 1) * kTile, b0 = (blockIdx.y & 1) * kTile, o0 = blockIdx.z * kTile;
+  if (a0 >= d || b0 >= d || o0 >= obs) return;
+  const float* C = D.C + in.off_C + (long long)o0 * d;
   float acc[4][4];
   zero_acc(acc);
-  tile_gemm<false, false>(acc, C + a0, d, min(kTile, d - a0), C + b0, d, min(kTile, d - b0), obs, sm);
+  tile_gemm<false, false>(acc, C + a0, d, min(kTile, d - a0), C + b0, d, min(kTile, d - b0),
+                          min(kTile, obs - o0), sm);
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
   float* out = T.CtC + (long long)blockIdx.x * kLdp * kLdp;
 #pragma unroll
@@ -1135,7 +1350,7 @@ __global__ void __launch_bounds__(kThreads) k_ctc(Dev D, TcDev T) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int a = a0 + ty * 4 + i, b = b0 + tx * 4 + j;
-      if (a < d && b < d) out[(long long)a * kLdp + b] = acc[i][j];
+      if (a < d && b < d) atomicAdd(out + (long long)a * kLdp + b, acc[i][j]);
     }
 }
 
@@ -1160,14 +1375,8 @@ __global__ void __launch_bounds__(128) k_asm_node(Dev D, TcDev T) {
   if ((j & 31) == 0) qred[j >> 5] = qs;
   if (j < d) zb[j] = T.zbar[(long long)g * kLdp + j];
   const bool leaf = nd.leaf_slot >= 0, root = nd.parent < 0;
-  if (leaf) {
-    for (int o = j; o < nd.obs; o += blockDim.x) {
-      const float* c = D.C + nd.off_C + (long long)o * d;
-      float s = 0.f;
-      for (int i = 0; i < d; ++i) s = fmaf(c[i], D.q_mean[nd.off_q + i], s);
-      xs[o] = D.x[nd.off_x + o] - s;
-    }
-  }
+  if (leaf)  // x~ = x - C m, formed in the forward pass
+    for (int o = j; o < nd.obs; o += blockDim.x) xs[o] = T.xs[nd.off_x + o];
   __syncthreads();
   const float qtot = qred[0] + qred[1] + qred[2] + qred[3];
   if (leaf && j < d) {
@@ -1180,7 +1389,8 @@ __global__ void __launch_bounds__(128) k_asm_node(Dev D, TcDev T) {
   float Sg = 0.f, Tg = 0.f;
   if (!root) {
     Sg += T.sgC[(long long)g * kLdp + j];
-    Tg += T.tgC[(long long)g * kLdp + j];
+    Tg += T.tgC[(long long)g * kLdp + j] +
+          (T.cvec[(long long)g * kLdp + j] * zb[j] - M2[(long long)j * kLdp + j]) * D.inv_var;
   }
   for (int ci = nd.child_begin; ci < nd.child_end; ++ci) {
     const int c = D.children[ci];
@@ -1195,8 +1405,8 @@ __global__ void __launch_bounds__(128) k_asm_node(Dev D, TcDev T) {
     const float db = go * t * D.inv_var;
     if (D.shared) { if (D.pbias) D.pbias[nd.off_q + j] = db; }
     else if (D.dbias) D.dbias[nd.off_bias + j] = db;
-    if (!D.shared && D.dW)
-      for (int c = 0; c < d; ++c) D.dW[nd.off_W + (long long)j * d + c] = 0.f;
+    if (!D.shared && D.dW)  // the root has no incoming edge: its W slot gets zero
+      for (int e = j; e < d * d; e += d) D.dW[nd.off_W + e] = 0.f;
   }
   if (leaf) {
     // C^T C is symmetric: row j read as column j (coalesced over threads)
@@ -1215,10 +1425,41 @@ __global__ void __launch_bounds__(128) k_asm_node(Dev D, TcDev T) {
 }
 
 // dC = grad_out / obs_var * sum_leaves [ x~ (zbar + m)^T - C (M2 + zbar m^T) ]
+//    = grad_out / obs_var * ( X - C S ),   X = sum_l x~_l (zbar_l + m_l)^T,
+//                                          S = sum_l (M2_l + zbar_l m_l^T)   (d x d)
+// k_leaf_S: grid (instance, 64x64 tile of S (2 x 2)).
+__global__ void __launch_bounds__(kThreads) k_leaf_S(Dev D, TcDev T) {
+  const InstInfo in = D.insts[blockIdx.x];
+  const int d = in.d;
+  const int a0 = (blockIdx.y >> 1) * kTile, b0 = (blockIdx.y & 1) * kTile;
+  if (a0 >= d || b0 >= d) return;
+  const int c = threadIdx.x & 63, r0 = threadIdx.x >> 6;  // 4 rows per pass, column c
+  float acc[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+  for (int gi = in.node0; gi < in.node0 + in.n; ++gi) {
+    const NodeInfo nd = D.nodes[gi];
+    if (nd.leaf_slot < 0) continue;
+    const float* M2 = T.M2 + (long long)gi * kLdp * kLdp;
+    const float* zb = T.zbar + (long long)gi * kLdp;
+    const float mb = b0 + c < d ? D.q_mean[nd.off_q + b0 + c] : 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int a = a0 + r0 + 4 * i;
+      if (a < d && b0 + c < d) acc[i] += M2[(long long)a * kLdp + b0 + c] + zb[a] * mb;
+    }
+  }
+  float* S = T.S + (long long)blockIdx.x * kLdp * kLdp;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int a = a0 + r0 + 4 * i;
+    if (a < d && b0 + c < d) S[(long long)a * kLdp + b0 + c] = acc[i];
+  }
+}
+
 // Grid: (instance, 64-row tile of observation dims, 64-col tile of latent dims).
 __global__ void __launch_bounds__(kThreads) k_asm_dC(Dev D, TcDev T) {
   __shared__ TileSmem sm;
-  __shared__ float xo[kTile], czo[kTile];
   const InstInfo in = D.insts[blockIdx.x];
   const int d = in.d, obs = in.obs;
   const int o0 = blockIdx.y * kTile, c0 = blockIdx.z * kTile;
@@ -1226,40 +1467,32 @@ __global__ void __launch_bounds__(kThreads) k_asm_dC(Dev D, TcDev T) {
   const int rows = min(kTile, obs - o0), cols = min(kTile, d - c0);
   const float go = D.grad_out ? (float)D.grad_out[blockIdx.x] : 1.f;
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  float out[4][4];
-  zero_acc(out);
+  const float* C = D.C + in.off_C;
+  float acc[4][4];
+  zero_acc(acc);
+  // acc = C[o0.., :] S[:, c0..]
+  tile_gemm<true, false>(acc, C + (long long)o0 * d, d, rows, T.S + (long long)blockIdx.x * kLdp * kLdp + c0,
+                         kLdp, cols, d, sm);
+  float X[4][4];
+  zero_acc(X);
   for (int gi = in.node0; gi < in.node0 + in.n; ++gi) {
     const NodeInfo nd = D.nodes[gi];
     if (nd.leaf_slot < 0) continue;
-    const float* C = D.C + nd.off_C;
-    const float* M2 = T.M2 + (long long)gi * kLdp * kLdp;
-    const float* zb = T.zbar + (long long)gi * kLdp;
-    const float* m = D.q_mean + nd.off_q;
-    __syncthreads();
-    if (threadIdx.x < kTile) {
-      const int o = o0 + threadIdx.x;
-      float cm = 0.f, cz = 0.f;
-      if (o < obs)
-        for (int a = 0; a < d; ++a) {
-          const float ca = C[(long long)o * d + a];
-          cm = fmaf(ca, m[a], cm);
-          cz = fmaf(ca, zb[a], cz);
-        }
-      xo[threadIdx.x] = (o < obs) ? D.x[nd.off_x + o] - cm : 0.f;
-      czo[threadIdx.x] = cz;
+    float xo[4], zm[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int o = o0 + ty * 4 + i;
+      xo[i] = o < obs ? T.xs[nd.off_x + o] : 0.f;
     }
-    float acc[4][4];
-    zero_acc(acc);
-    tile_gemm<true, false>(acc, C + (long long)o0 * d, d, rows, M2 + c0, kLdp, cols, d, sm);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + tx * 4 + j;
+      zm[j] = c < d ? T.zbar[(long long)gi * kLdp + c] + D.q_mean[nd.off_q + c] : 0.f;
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = c0 + tx * 4 + j;
-        if (c >= d) continue;
-        const int oi = ty * 4 + i;
-        out[i][j] += xo[oi] * (zb[c] + m[c]) - acc[i][j] - czo[oi] * m[c];
-      }
+      for (int j = 0; j < 4; ++j) X[i][j] = fmaf(xo[i], zm[j], X[i][j]);
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -1267,7 +1500,7 @@ __global__ void __launch_bounds__(kThreads) k_asm_dC(Dev D, TcDev T) {
     for (int j = 0; j < 4; ++j) {
       const int o = o0 + ty * 4 + i, c = c0 + tx * 4 + j;
       if (o >= obs || c >= d) continue;
-      const float v = go * out[i][j] * D.inv_obs_var;
+      const float v = go * (X[i][j] - acc[i][j]) * D.inv_obs_var;
       if (D.shared) { if (D.pC) D.pC[in.off_pC + (long long)o * d + c] = v; }
       else if (D.dC) D.dC[in.off_C + (long long)o * d + c] = v;
     }
@@ -1313,6 +1546,10 @@ template <int DP>
 size_t fwd_smem(int maxK) {
   const size_t need = 1024 + 3 * 2 * (size_t)(kRows * DP * 2) + 4 * (size_t)(((maxK + kRows - 1) / kRows) * kRows);
   return need > 120 * 1024 ? need : 120 * 1024;
+}
+template <int DP>
+size_t obs_smem() {
+  return 1024 + 4 * (size_t)(kRows * DP * 2) + sizeof(float) * kMaxD;
 }
 template <int DP>
 size_t bwd_smem(int maxK) {
@@ -1409,18 +1646,72 @@ void workspace_layout(TcWork& w, const std::vector<NodeInfo>& nodes, long long n
   subs.push_back({(void**)&w.t.sgP, nv});
   subs.push_back({(void**)&w.t.tgP, nv});
   subs.push_back({(void**)&w.t.CtC, (size_t)(w.t.shared ? 1 : w.num_inst) * kLdp * kLdp * sizeof(float)});
+  w.num_c = w.t.shared ? 1 : w.num_inst;
+  long long cr = 0;
+  for (const NodeInfo& nd : nodes)
+    if (nd.parent < 0 && (!w.t.shared || nd.b == 0)) cr += nd.obs;
+  w.c_rows = cr + kRows;  // one spare tile of rows: chunk tails stay inside the map
+  subs.push_back({(void**)&w.t.CH, (size_t)w.c_rows * kLdp * sizeof(__half)});
+  subs.push_back({(void**)&w.t.CL, (size_t)w.c_rows * kLdp * sizeof(__half)});
+  subs.push_back({(void**)&w.t.c_row, (size_t)w.num_c * sizeof(int)});
+  long long nx = 0;
+  for (const NodeInfo& nd : nodes)
+    if (nd.leaf_slot >= 0) nx = std::max(nx, nd.off_x + nd.obs);
+  subs.push_back({(void**)&w.t.xs, (size_t)std::max(nx, 1ll) * sizeof(float)});
+  subs.push_back({(void**)&w.t.S, (size_t)w.num_inst * kLdp * kLdp * sizeof(float)});
 }
 
 tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vector<Tile>&, int maxK,
-                   int) {
+                   int maxd) {
   w.maxK = maxK;
+  w.maxdp = maxd > 64 ? 128 : 64;
   for (const NodeInfo& nd : nodes) w.maxobs = std::max(w.maxobs, nd.obs);
   if (!make_map(&w.mZH, w.t.ZH, w.rows) || !make_map(&w.mZL, w.t.ZL, w.rows) ||
       !make_map(&w.mWH, w.t.WH, (long long)w.num_slots * kLdp) ||
       !make_map(&w.mWL, w.t.WL, (long long)w.num_slots * kLdp) ||
       !make_map(&w.mWTH, w.t.WTH, (long long)w.num_slots * kLdp) ||
-      !make_map(&w.mWTL, w.t.WTL, (long long)w.num_slots * kLdp))
+      !make_map(&w.mWTL, w.t.WTL, (long long)w.num_slots * kLdp) ||
+      !make_map(&w.mCH, w.t.CH, w.c_rows) || !make_map(&w.mCL, w.t.CL, w.c_rows))
     return TMC_ERR_CUDA;
+  {  // observation matrices' first rows, and the leaf tiles of the observation kernel
+    std::vector<int> crow(w.num_c, 0);
+    int next = 0;
+    for (const NodeInfo& nd : nodes)
+      if (nd.parent < 0 && nd.b < w.num_c) {
+        crow[nd.b] = next;
+        next += nd.obs;
+      }
+    cudaMemcpy(w.t.c_row, crow.data(), sizeof(int) * crow.size(), cudaMemcpyHostToDevice);
+    w.obs_tiles.clear();
+    for (int c = 0; c < 2; ++c) {
+      w.ob_b[c] = (int)w.obs_tiles.size();
+      for (int g = 0; g < (int)nodes.size(); ++g)
+        if (nodes[g].leaf_slot >= 0 && nodes[g].obs > 0 && ((nodes[g].d > 64) ? 1 : 0) == c)
+          for (int r = 0; r < nodes[g].K; r += kRows) w.obs_tiles.push_back(Tile{g, r});
+      w.ob_e[c] = (int)w.obs_tiles.size();
+    }
+    w.leaves.clear();
+    for (int g = 0; g < (int)nodes.size(); ++g)
+      if (nodes[g].leaf_slot >= 0) w.leaves.push_back(g);
+    w.sample_tiles.clear();
+    for (int g = 0; g < (int)nodes.size(); ++g)
+      for (int r = 0; r < nodes[g].K; r += sample_rows(nodes[g].d)) w.sample_tiles.push_back(Tile{g, r});
+    if (!w.obs_tiles.empty()) {
+      if (cudaMalloc(&w.d_obs_tiles, sizeof(Tile) * w.obs_tiles.size()) != cudaSuccess) return TMC_ERR_NOMEM;
+      cudaMemcpy(w.d_obs_tiles, w.obs_tiles.data(), sizeof(Tile) * w.obs_tiles.size(), cudaMemcpyHostToDevice);
+    }
+    if (!w.leaves.empty()) {
+      if (cudaMalloc(&w.d_leaves, sizeof(int) * w.leaves.size()) != cudaSuccess) return TMC_ERR_NOMEM;
+      cudaMemcpy(w.d_leaves, w.leaves.data(), sizeof(int) * w.leaves.size(), cudaMemcpyHostToDevice);
+    }
+    if (!w.sample_tiles.empty()) {
+      if (cudaMalloc(&w.d_sample_tiles, sizeof(Tile) * w.sample_tiles.size()) != cudaSuccess) return TMC_ERR_NOMEM;
+      cudaMemcpy(w.d_sample_tiles, w.sample_tiles.data(), sizeof(Tile) * w.sample_tiles.size(),
+                 cudaMemcpyHostToDevice);
+    }
+    cudaMemset(w.t.CH, 0, (size_t)w.c_rows * kLdp * sizeof(__half));
+    cudaMemset(w.t.CL, 0, (size_t)w.c_rows * kLdp * sizeof(__half));
+  }
   int maxlevel = 0;
   for (const NodeInfo& nd : nodes) maxlevel = std::max(maxlevel, nd.level);
   w.maxlevel = maxlevel;
@@ -1441,8 +1732,13 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
     w.t.inst_left_init = w.inst_init_dev;
   }
   w.nonroot.clear();
+  w.n_pack_w = 0;
   for (int g = 0; g < (int)nodes.size(); ++g)
-    if (nodes[g].parent >= 0) w.nonroot.push_back(g);
+    if (nodes[g].parent >= 0) {
+      w.nonroot.push_back(g);
+      // shared parameters: instance 0's edges hold every distinct W (they come first)
+      if (!w.t.shared || nodes[g].b == 0) ++w.n_pack_w;
+    }
   if (!w.tiles.empty()) {
     if (cudaMalloc(&w.d_tiles, sizeof(Tile) * w.tiles.size()) != cudaSuccess) return TMC_ERR_NOMEM;
     cudaMemcpy(w.d_tiles, w.tiles.data(), sizeof(Tile) * w.tiles.size(), cudaMemcpyHostToDevice);
@@ -1460,6 +1756,8 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
   cudaFuncSetAttribute(k_edge_fwd_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f128);
   cudaFuncSetAttribute(k_edge_bwd_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<64>(maxK));
   cudaFuncSetAttribute(k_edge_bwd_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<128>(maxK));
+  cudaFuncSetAttribute(k_obs_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)obs_smem<64>());
+  cudaFuncSetAttribute(k_obs_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)obs_smem<128>());
   return cudaGetLastError() == cudaSuccess ? TMC_OK : TMC_ERR_CUDA;
 }
 
@@ -1479,19 +1777,40 @@ tmc_status instance_times(TcWork& w, int B, double* fwd_us, double* bwd_us) {
 void release(TcWork& w) {
   cudaFree(w.d_tiles);
   cudaFree(w.d_nonroot);
+  cudaFree(w.d_obs_tiles);
+  cudaFree(w.d_leaves);
+  cudaFree(w.d_sample_tiles);
   w.d_tiles = nullptr;
   w.d_nonroot = nullptr;
+  w.d_obs_tiles = nullptr;
+  w.d_leaves = nullptr;
+  w.d_sample_tiles = nullptr;
 }
 
-void launch_sample(TcWork& w, const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s) {
-  if (ntiles) k_sample_tc<<<ntiles, 256, 3 * kTcMaxD * sizeof(float), s>>>(D, w.t, tiles);
+void launch_sample(TcWork& w, const Dev& D, cudaStream_t s) {
+  if (!w.sample_tiles.empty())
+    k_sample_tc<<<(int)w.sample_tiles.size(), 256, 3 * kTcMaxD * sizeof(float), s>>>(D, w.t, w.d_sample_tiles);
 }
 
 void launch_pack(TcWork& w, const Dev& D, cudaStream_t s) {
   const int n = (int)w.nonroot.size();
   if (!n) return;
-  k_pack_w<<<dim3(n, kLdp / 32, kLdp / 32), 256, 0, s>>>(D, w.t, w.d_nonroot);
-  k_pack_c<<<n, 256, 0, s>>>(D, w.t, w.d_nonroot);
+  if (w.n_pack_w) k_pack_w<<<dim3(w.n_pack_w, w.maxdp / 32, w.maxdp / 32), 256, 0, s>>>(D, w.t, w.d_nonroot);
+  k_pack_c<<<n, 128, 0, s>>>(D, w.t, w.d_nonroot);
+}
+
+void launch_obs(TcWork& w, const Dev& D, cudaStream_t s) {
+  if (w.obs_tiles.empty()) return;
+  k_obs_center<<<(int)w.leaves.size(), 128, 0, s>>>(D, w.t, w.d_leaves);
+  k_pack_cobs<<<dim3(w.num_c, (w.maxobs + 1) / 2), 256, 0, s>>>(D, w.t);
+  for (int c = 0; c < 2; ++c) {
+    const int b = w.ob_b[c], n = w.ob_e[c] - b;
+    if (!n) continue;
+    if (c == 0)
+      k_obs_tc<64><<<n, 128, obs_smem<64>(), s>>>(D, w.t, w.d_obs_tiles + b, w.mZH, w.mZL, w.mCH, w.mCL);
+    else
+      k_obs_tc<128><<<n, 128, obs_smem<128>(), s>>>(D, w.t, w.d_obs_tiles + b, w.mZH, w.mZL, w.mCH, w.mCL);
+  }
 }
 
 void launch_edge_fwd(TcWork& w, const Dev& D, cudaStream_t s) {
@@ -1530,15 +1849,22 @@ void launch_edge_bwd(TcWork& w, const Dev& D, cudaStream_t s) {
 
 void launch_unpack_grads(TcWork& w, const Dev& D, cudaStream_t s) {
   const int nr = (int)w.nonroot.size();
-  k_root_moments<<<dim3(D.num_inst, 2, 2), kThreads, 0, s>>>(D, w.t);
-  k_ctc<<<dim3(D.shared ? 1 : D.num_inst, 2, 2), kThreads, 0, s>>>(D, w.t);
+  if (w.maxlevel == 0) {  // no adjoint edge launch zeroed the moments
+    cudaMemsetAsync(w.t.M2, 0, (size_t)w.num_nodes * kLdp * kLdp * sizeof(float), s);
+    cudaMemsetAsync(w.t.zbar, 0, (size_t)w.num_nodes * kLdp * sizeof(float), s);
+  }
+  k_root_moments<<<dim3(D.num_inst, 4, (w.maxK + kRootSlab - 1) / kRootSlab), kThreads, 0, s>>>(D, w.t);
+  cudaMemsetAsync(w.t.CtC, 0, (size_t)(D.shared ? 1 : D.num_inst) * kLdp * kLdp * sizeof(float), s);
+  k_ctc<<<dim3(D.shared ? 1 : D.num_inst, w.maxdp > 64 ? 4 : 1, (w.maxobs + kTile - 1) / kTile), kThreads, 0, s>>>(D, w.t);
   cudaMemsetAsync(w.t.tgP, 0, (size_t)w.num_nodes * kLdp * sizeof(float), s);
+  cudaMemsetAsync(w.t.tgC, 0, (size_t)w.num_nodes * kLdp * sizeof(float), s);
   if (nr) {
     k_asm_edge_vec<<<nr, 128, 0, s>>>(D, w.t, w.d_nonroot);
-    k_asm_edge_mat<<<dim3(nr, 2, 2), kThreads, 0, s>>>(D, w.t, w.d_nonroot);
+    k_asm_edge_mat<<<dim3(nr, w.maxdp > 64 ? 4 : 1), kThreads, 0, s>>>(D, w.t, w.d_nonroot);
   }
   k_asm_node<<<D.num_nodes, 128, 0, s>>>(D, w.t);
-  k_asm_dC<<<dim3(D.num_inst, (w.maxobs + kTile - 1) / kTile, 2), kThreads, 0, s>>>(D, w.t);
+  k_leaf_S<<<dim3(D.num_inst, w.maxdp > 64 ? 4 : 1), kThreads, 0, s>>>(D, w.t);
+  k_asm_dC<<<dim3(D.num_inst, (w.maxobs + kTile - 1) / kTile, w.maxdp / kTile), kThreads, 0, s>>>(D, w.t);
 }
 
 }  // namespace tc

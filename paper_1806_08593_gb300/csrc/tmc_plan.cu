@@ -402,8 +402,8 @@ tmc_status tmc_log_marginal(tmc_plan p, const tmc_inputs* in, double* log_phat, 
     // split W_i and c_i first: the sampling kernel forms z~ . c_i, the conditional means are
     // formed inside the edge kernels
     TRY(timed(p, TMC_KC_PROJECT, s, [&] { tc::launch_pack(p->tcw, D, s); }));
-    TRY(timed(p, TMC_KC_SAMPLE, s, [&] { tc::launch_sample(p->tcw, D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
-    TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_obs_fwd(D, T + p->t_leaf_b, p->t_leaf_e - p->t_leaf_b, s); }));
+    TRY(timed(p, TMC_KC_SAMPLE, s, [&] { tc::launch_sample(p->tcw, D, s); }));
+    TRY(timed(p, TMC_KC_SAMPLE, s, [&] { tc::launch_obs(p->tcw, D, s); }));
   } else {
     TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_sample(D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
     TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_obs_fwd(D, T + p->t_leaf_b, p->t_leaf_e - p->t_leaf_b, s); }));

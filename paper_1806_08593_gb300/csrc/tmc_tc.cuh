@@ -41,6 +41,10 @@ struct TcDev {
   float* sgP;
   float* tgP;
   float* CtC;                  // [1 or B][128*128]  C^T C per observation matrix
+  __half *CH, *CL;             // [c_rows][128] split observation matrices, row = c_row[b] + o
+  int* c_row;                  // [1 or B] first row of each observation matrix in CH / CL
+  float* xs;                   // centred observations x - C m of the leaves (layout of x)
+  float* S;                    // [B][128*128] sum over an instance's leaves of M2 + zbar m^T
   int* done;                   // [nodes] tiles finished per node in the running edge launch
   int* inst_left;              // [2][B] edge tiles still to run per instance (fwd, adjoint)
   const int* inst_left_init;   // [2][B] their initial values
@@ -65,7 +69,20 @@ struct TcWork {
   int* d_nonroot = nullptr;
   int maxK = 0;
   int* inst_init_dev = nullptr;  // workspace copy of the per-instance tile counts
-  int schedule = 0;              // work order of the persistent launches (see build_items)
+  int schedule = 0;               // work order of the persistent launches (see build_items)
+  int maxdp = 128;                // widest padded latent dimension (64 or 128)
+  int n_pack_w = 0;               // leading non-root nodes whose W is packed
+  // observation term: split C rows and the 128-sample leaf tiles per d class
+  long long c_rows = 0;
+  int num_c = 0;                  // distinct observation matrices (1 when shared)
+  CUtensorMap mCH, mCL;
+  std::vector<Tile> obs_tiles;
+  int ob_b[2] = {0, 0}, ob_e[2] = {0, 0};
+  Tile* d_obs_tiles = nullptr;
+  std::vector<int> leaves;        // leaf nodes
+  int* d_leaves = nullptr;
+  std::vector<Tile> sample_tiles; // sampler tiles (rows per tile grow as d shrinks)
+  Tile* d_sample_tiles = nullptr;
 };
 
 tmc_status supported(const std::vector<NodeInfo>& nodes, int precision);
@@ -77,8 +94,9 @@ void workspace_layout(TcWork& w, const std::vector<NodeInfo>& nodes, long long n
 tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vector<Tile>& tiles,
                    int maxK, int maxd);
 void release(TcWork& w);
-void launch_sample(TcWork& w, const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s);
+void launch_sample(TcWork& w, const Dev& D, cudaStream_t s);
 void launch_pack(TcWork& w, const Dev& D, cudaStream_t s);
+void launch_obs(TcWork& w, const Dev& D, cudaStream_t s);  // leaf observation term
 void launch_edge_fwd(TcWork& w, const Dev& D, cudaStream_t s);  // one persistent launch per d class
 void launch_edge_bwd(TcWork& w, const Dev& D, cudaStream_t s);
 void launch_unpack_grads(TcWork& w, const Dev& D, cudaStream_t s);
