@@ -180,96 +180,197 @@ __host__ __device__ constexpr int ring_bytes(int DP) {
 // packed operand array, |z~|^2, z~ . c_i and the per-sample node term (as in the FP32 path);
 // FP32 samples are kept for the root (its moments are formed from them).
 // =======================================================================================
-// Lane mapping: a row of d floats is served by L = 2^ceil(log2(ceil(d / 4))) lanes (float4
-// each), so a warp covers 32 / L rows per pass, and every thread loads kSampleU rows before it
-// computes (several 16-byte loads in flight per lane).
-constexpr int kSampleU = 4;
-// Sample rows per CTA: 64 at d > 64, doubling as d halves (512 at d <= 16), so a CTA streams
-// a similar number of bytes whatever d is.
+// Persistent, warp-specialised sampler.  A tile is a node and up to sample_rows(d) of its
+// rows (32 KB of eps whatever d is).  Warp 0 is the producer: for each tile of the CTA it
+// reads the tile's node record, forms the per-dimension vectors (exp(logs), m - bias at the
+// root, c_i), and bulk-copies the tile's eps rows into a ring stage; warps 1..7 consume the
+// stages: split z~ = exp(logs) eps into fp16 hi / lo rows and form the row sums.  Tiles whose
+// eps rows are not 16-byte aligned (d not a multiple of 4) are read from global memory by the
+// consumers instead.
+// Consumer lane mapping: 2^LG lanes per sample row (4 at d <= 16, else 8); lane `sub` owns the
+// float4 groups at columns 4 sub + 4 L q (q < Q), so a row sum needs LG shuffle steps per
+// 32 / L rows.
 __host__ __device__ constexpr int sample_rows(int d) { return d > 64 ? 64 : d > 32 ? 128 : d > 16 ? 256 : 512; }
-__global__ void __launch_bounds__(256) k_sample_tc(Dev D, TcDev T, const Tile* __restrict__ tiles) {
-  extern __shared__ float sm[];
-  const Tile t = tiles[blockIdx.x];
-  const NodeInfo nd = D.nodes[t.node];
-  const int d = nd.d;
-  float* s_std = sm;
-  float* s_off = sm + kTcMaxD;
-  float* s_c = sm + 2 * kTcMaxD;
-  const bool root = nd.parent < 0;
-  for (int j = threadIdx.x; j < kTcMaxD; j += blockDim.x) {
-    s_std[j] = j < d ? expf(D.q_logstd[nd.off_q + j]) : 0.f;
-    s_off[j] = (root && j < d) ? D.q_mean[nd.off_q + j] - D.bias[nd.off_bias + j] : 0.f;
-    s_c[j] = (root || j >= d) ? 0.f : T.cvec[(long long)t.node * kLdp + j];
-  }
-  __syncthreads();
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int lg = d > 64 ? 5 : d > 32 ? 4 : d > 16 ? 3 : d > 8 ? 2 : d > 4 ? 1 : 0;
-  const int L = 1 << lg, rpw = 32 >> lg, pass = (blockDim.x >> 5) * rpw;
-  const int j0 = 4 * (lane & (L - 1));
-  const int rlane = w * rpw + (lane >> lg);
-  const bool vec = (d & 3) == 0 && (nd.off_nkd & 3) == 0;
-  const int rows = min(sample_rows(d), nd.K - t.row0);
+constexpr int kSampleStage = 64 * kTcMaxD * 4;  // bytes of one eps stage (= rows x d x 4 at most)
+constexpr int kSampleNS = 3;                    // ring stages
+constexpr int kSampleConsumers = 7;             // consumer warps
+
+struct __align__(16) SampleStage {  // 16-byte aligned: the vectors are read as float4
+  float std_[kTcMaxD], off[kTcMaxD], c[kTcMaxD];
+  long long off_nk, off_nkd;
+  int d, row0, rows, root, bulk;
+};
+constexpr size_t kSampleSmem = kSampleNS * (kSampleStage + sizeof(SampleStage)) + 64;
+static_assert(sizeof(SampleStage) % 16 == 0 && kSampleStage % 64 == 0, "sampler stage alignment");
+
+__device__ __forceinline__ bool sample_bulk_ok(const Dev& D, const NodeInfo& nd) {
+  return (nd.d & 3) == 0 && (nd.off_nkd & 3) == 0 && ((uintptr_t)D.eps & 15) == 0;
+}
+
+// Rows of one stage; element (r, col) of the tile is src[r * d + col].
+template <int LG, int Q>
+__device__ __forceinline__ bool sample_stage(const Dev& D, const TcDev& T, const SampleStage& st, const float* src) {
+  constexpr int L = 1 << LG, RPW = 32 >> LG, PASS = kSampleConsumers * RPW;
+  const int w = (threadIdx.x >> 5) - 1, lane = threadIdx.x & 31;
+  const int sub = lane & (L - 1), rl = w * RPW + (lane >> LG);
+  const int d = st.d, rows = st.rows;
+  const bool root = st.root != 0;
+  const bool vec = (d & 3) == 0 && ((uintptr_t)src & 15) == 0;
   bool bad = false;
-  for (int base = 0; base < rows; base += kSampleU * pass) {
-    float e[kSampleU][4];
+  for (int base = 0; base < rows; base += PASS) {
+    const int r = base + rl;
+    const long long k = st.row0 + r;
+    const bool live = r < rows;
+    float se = 0.f, sz = 0.f, sr = 0.f, szc = 0.f;
 #pragma unroll
-    for (int u = 0; u < kSampleU; ++u) {
-      const int r = base + u * pass + rlane;
-      const long long off = nd.off_nkd + (long long)(t.row0 + r) * d + j0;
-      e[u][0] = e[u][1] = e[u][2] = e[u][3] = 0.f;
-      if (r < rows && j0 < d) {
+    for (int q = 0; q < Q; ++q) {
+      const int col = 4 * sub + 4 * L * q;
+      float e[4] = {0.f, 0.f, 0.f, 0.f};
+      if (live && col < d) {
         if (vec) {
-          const float4 v = __ldcs(reinterpret_cast<const float4*>(D.eps + off));
-          e[u][0] = v.x; e[u][1] = v.y; e[u][2] = v.z; e[u][3] = v.w;
+          const float4 x = *reinterpret_cast<const float4*>(src + (long long)r * d + col);
+          e[0] = x.x; e[1] = x.y; e[2] = x.z; e[3] = x.w;
         } else {
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (j0 + q < d) e[u][q] = D.eps[off + q];
+          for (int x = 0; x < 4; ++x)
+            if (col + x < d) e[x] = src[(long long)r * d + col + x];
+        }
+      }
+      const float4 sd = *reinterpret_cast<const float4*>(st.std_ + col);
+      const float4 sc = *reinterpret_cast<const float4*>(st.c + col);
+      const float z[4] = {sd.x * e[0], sd.y * e[1], sd.z * e[2], sd.w * e[3]};
+      const float cv[4] = {sc.x, sc.y, sc.z, sc.w};
+      float hi[4], lo[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        se = fmaf(e[x], e[x], se);
+        sz = fmaf(z[x], z[x], sz);
+        szc = fmaf(z[x], cv[x], szc);
+        split_half(z[x], hi[x], lo[x]);
+      }
+      if (root) {
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const float rr = (col + x < d) ? z[x] + st.off[col + x] : 0.f;
+          sr = fmaf(rr, rr, sr);
+        }
+      }
+      if (live && col < d) {  // padding columns stay zero from plan creation
+        if (root)
+          for (int x = 0; x < 4; ++x)
+            if (col + x < d) D.zt[st.off_nkd + k * d + col + x] = z[x];
+        const long long prow = (st.off_nk + k) * kLdp + col;
+        *reinterpret_cast<uint2*>(T.ZH + prow) = make_uint2(pack_half2(hi[0], hi[1]), pack_half2(hi[2], hi[3]));
+        *reinterpret_cast<uint2*>(T.ZL + prow) = make_uint2(pack_half2(lo[0], lo[1]), pack_half2(lo[2], lo[3]));
+      }
+    }
+#pragma unroll
+    for (int o = L >> 1; o > 0; o >>= 1) {
+      se += __shfl_xor_sync(0xffffffffu, se, o);
+      sz += __shfl_xor_sync(0xffffffffu, sz, o);
+      szc += __shfl_xor_sync(0xffffffffu, szc, o);
+      if (root) sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    }
+    if (live && sub == 0) {
+      bad |= !isfinite(sz) || !isfinite(se);
+      float uu = 0.5f * se;
+      if (root) uu -= 0.5f * sr * D.inv_var;
+      D.u[st.off_nk + k] = uu;
+      D.zn[st.off_nk + k] = sz;
+      T.zc[st.off_nk + k] = szc;
+    }
+  }
+  return bad;
+}
+
+__global__ void __launch_bounds__(256) k_sample_tc(Dev D, TcDev T, const Tile* __restrict__ tiles, int ntiles) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 63) & ~(uintptr_t)63);
+  float* buf = reinterpret_cast<float*>(sm);                                        // [NS][stage]
+  SampleStage* st = reinterpret_cast<SampleStage*>(sm + kSampleNS * kSampleStage);  // [NS]
+  __shared__ uint64_t full[kSampleNS], empty[kSampleNS];
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSampleNS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kSampleConsumers);
+    }
+    fence_barrier_init();
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    // ------------------------------------------------------------------ producer
+    int n = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < ntiles; item += gridDim.x, ++n) {
+      const int s = n % kSampleNS, fill = n / kSampleNS;
+      if (fill >= 1 && !mbar_wait(&empty[s], (fill - 1) & 1)) { ok = false; break; }
+      const Tile t = tiles[item];
+      const NodeInfo nd = D.nodes[t.node];
+      const bool root = nd.parent < 0;
+      float lsv[4], ofv[4], ccv[4];  // every load before the first store
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const int j = lane + 32 * x;
+        lsv[x] = j < nd.d ? __ldg(D.q_logstd + nd.off_q + j) : 0.f;
+        ofv[x] = (root && j < nd.d) ? __ldg(D.q_mean + nd.off_q + j) - __ldg(D.bias + nd.off_bias + j) : 0.f;
+        ccv[x] = (root || j >= nd.d) ? 0.f : __ldg(T.cvec + (long long)t.node * kLdp + j);
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const int j = lane + 32 * x;
+        st[s].std_[j] = j < nd.d ? expf(lsv[x]) : 0.f;
+        st[s].off[j] = ofv[x];
+        st[s].c[j] = ccv[x];
+      }
+      const bool bulk = sample_bulk_ok(D, nd);
+      const int rows = min(sample_rows(nd.d), nd.K - t.row0);
+      if (lane == 0) {
+        st[s].off_nk = nd.off_nk;
+        st[s].off_nkd = nd.off_nkd;
+        st[s].d = nd.d;
+        st[s].row0 = t.row0;
+        st[s].rows = rows;
+        st[s].root = root ? 1 : 0;
+        st[s].bulk = bulk ? 1 : 0;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        if (bulk) {
+          const uint32_t bytes = (uint32_t)rows * nd.d * 4;
+          mbar_arrive_expect_tx(&full[s], bytes);
+          bulk_load(buf + (size_t)s * (kSampleStage / 4), D.eps + nd.off_nkd + (long long)t.row0 * nd.d, bytes,
+                    &full[s]);
+        } else {
+          mbar_arrive(&full[s]);  // release of the stage record; the rows are read from global
         }
       }
     }
-#pragma unroll
-    for (int u = 0; u < kSampleU; ++u) {
-      const int r = base + u * pass + rlane;
-      const int k = t.row0 + r;
-      float se = 0.f, sz = 0.f, sr = 0.f, szc = 0.f;
-      float z[4], hi[4], lo[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        z[q] = s_std[j0 + q] * e[u][q];
-        bad |= !isfinite(z[q]);
-        se = fmaf(e[u][q], e[u][q], se);
-        sz = fmaf(z[q], z[q], sz);
-        szc = fmaf(z[q], s_c[j0 + q], szc);
-        const float rr = (j0 + q < d) ? z[q] + s_off[j0 + q] : 0.f;
-        sr = fmaf(rr, rr, sr);
-        split_half(z[q], hi[q], lo[q]);
-      }
-      const bool live = r < rows;
-      if (live && j0 < d) {  // padding columns stay zero from plan creation
-        if (root)
-          for (int q = 0; q < 4; ++q)
-            if (j0 + q < d) D.zt[nd.off_nkd + (long long)k * d + j0 + q] = z[q];
-        const long long prow = (nd.off_nk + k) * kLdp;
-        *reinterpret_cast<uint2*>(T.ZH + prow + j0) = make_uint2(pack_half2(hi[0], hi[1]), pack_half2(hi[2], hi[3]));
-        *reinterpret_cast<uint2*>(T.ZL + prow + j0) = make_uint2(pack_half2(lo[0], lo[1]), pack_half2(lo[2], lo[3]));
-      }
-      for (int o = L >> 1; o > 0; o >>= 1) {
-        se += __shfl_xor_sync(0xffffffffu, se, o);
-        sz += __shfl_xor_sync(0xffffffffu, sz, o);
-        sr += __shfl_xor_sync(0xffffffffu, sr, o);
-        szc += __shfl_xor_sync(0xffffffffu, szc, o);
-      }
-      if (live && (lane & (L - 1)) == 0) {
-        float uu = 0.5f * se;
-        if (root) uu -= 0.5f * sr * D.inv_var;
-        D.u[nd.off_nk + k] = uu;
-        D.zn[nd.off_nk + k] = sz;
-        T.zc[nd.off_nk + k] = szc;
-      }
+    if (!ok && lane == 0) set_timeout(D);
+    // the last fills still in flight land before the CTA exits
+    if (lane == 0)
+      for (int m = (n > kSampleNS ? n - kSampleNS : 0); m < n; ++m)
+        mbar_wait(&full[m % kSampleNS], (m / kSampleNS) & 1);
+  } else {
+    // ------------------------------------------------------------------ consumers
+    int n = 0;
+    bool bad = false, ok = true;
+    for (int item = blockIdx.x; item < ntiles; item += gridDim.x, ++n) {
+      const int s = n % kSampleNS;
+      if (!mbar_wait(&full[s], (n / kSampleNS) & 1)) { ok = false; break; }
+      const SampleStage& stg = st[s];
+      const float* src = stg.bulk ? buf + (size_t)s * (kSampleStage / 4) : D.eps + stg.off_nkd + (long long)stg.row0 * stg.d;
+      const int d = stg.d;
+      if (d > 64) bad |= sample_stage<3, 4>(D, T, stg, src);
+      else if (d > 32) bad |= sample_stage<3, 2>(D, T, stg, src);
+      else if (d > 16) bad |= sample_stage<3, 1>(D, T, stg, src);
+      else bad |= sample_stage<2, 1>(D, T, stg, src);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
     }
+    if (!ok && lane == 0) set_timeout(D);
+    if (bad) atomicOr(D.err, kErrNumeric);
   }
-  if (bad) atomicOr(D.err, kErrNumeric);
 }
 
 // Split W_i (and its transpose) into fp16 hi / lo blocks, one 128-row slot per W_i; only the
@@ -288,12 +389,18 @@ __global__ void k_pack_w(Dev D, TcDev T, const int* __restrict__ nonroot) {
   const long long o = (long long)slot * kLdp * kLdp;
   const float* Wi = D.W + nd.off_W;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-  for (int i = ty; i < 32; i += 8) {
-    const int r = r0 + i, c = c0 + tx;
-    const float v = (r < d && c < d) ? Wi[(long long)r * d + c] : 0.f;
-    tile[i][tx] = v;
+  float v[4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {  // every load before the first store
+    const int r = r0 + ty + 8 * x, c = c0 + tx;
+    v[x] = (r < d && c < d) ? __ldg(Wi + (long long)r * d + c) : 0.f;
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int i = ty + 8 * x, r = r0 + i, c = c0 + tx;
+    tile[i][tx] = v[x];
     float hi, lo;
-    split_half(v, hi, lo);
+    split_half(v[x], hi, lo);
     T.WH[o + (long long)r * kLdp + c] = __float2half_rn(hi);
     T.WL[o + (long long)r * kLdp + c] = __float2half_rn(lo);
   }
@@ -376,17 +483,26 @@ __global__ void __launch_bounds__(128) k_obs_center(Dev D, TcDev T, const int* _
 }
 
 // Split observation matrices: CH / CL row c_row[b] + o = C_b[o][0..d) as fp16 hi / lo, zero
-// beyond d.  Grid: (distinct matrix, pair of rows); thread = (row of the pair, column).
+// beyond d.  Grid: (distinct matrix, 8 rows); thread = (row parity, column), 4 rows each.
 __global__ void __launch_bounds__(256) k_pack_cobs(Dev D, TcDev T) {
   const InstInfo in = D.insts[blockIdx.x];
-  const int o = blockIdx.y * 2 + (threadIdx.x >> 7), j = threadIdx.x & 127;
-  if (o >= in.obs) return;
-  const float v = j < in.d ? D.C[in.off_C + (long long)o * in.d + j] : 0.f;
-  float hi, lo;
-  split_half(v, hi, lo);
-  const long long r = (long long)T.c_row[blockIdx.x] + o;
-  T.CH[r * kLdp + j] = __float2half_rn(hi);
-  T.CL[r * kLdp + j] = __float2half_rn(lo);
+  const int j = threadIdx.x & 127;
+  const long long r0 = T.c_row[blockIdx.x];
+  float v[4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {  // rows 8 y + 2 x + (thread >> 7); every load before the first store
+    const int o = blockIdx.y * 8 + 2 * x + (threadIdx.x >> 7);
+    v[x] = (o < in.obs && j < in.d) ? __ldg(D.C + in.off_C + (long long)o * in.d + j) : 0.f;
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int o = blockIdx.y * 8 + 2 * x + (threadIdx.x >> 7);
+    if (o >= in.obs) break;
+    float hi, lo;
+    split_half(v[x], hi, lo);
+    T.CH[(r0 + o) * kLdp + j] = __float2half_rn(hi);
+    T.CL[(r0 + o) * kLdp + j] = __float2half_rn(lo);
+  }
 }
 
 // =======================================================================================
@@ -398,7 +514,7 @@ __global__ void __launch_bounds__(256) k_pack_cobs(Dev D, TcDev T) {
 // (thread t owns sample row t = TMEM lane t).
 // =======================================================================================
 template <int DP>
-__global__ void __launch_bounds__(128) k_obs_tc(Dev D, TcDev T, const Tile* __restrict__ tiles,
+__global__ void __launch_bounds__(128) k_obs_tc(Dev D, TcDev T, const Tile* __restrict__ tiles, int ntiles,
                                                  const __grid_constant__ CUtensorMap mZH,
                                                  const __grid_constant__ CUtensorMap mZL,
                                                  const __grid_constant__ CUtensorMap mCH,
@@ -413,11 +529,6 @@ __global__ void __launch_bounds__(128) k_obs_tc(Dev D, TcDev T, const Tile* __re
   __shared__ uint64_t bar_ld, bar_mma;
   __shared__ uint32_t tbase;
   __shared__ int s_ok;
-  const Tile t = tiles[blockIdx.x];
-  const NodeInfo nd = D.nodes[t.node];
-  const int obs = nd.obs;
-  const int nchunk = (obs + kRows - 1) / kRows;
-  const int crow = T.c_row[D.shared ? 0 : nd.b];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) tmem_alloc(&tbase, 128);
   if (threadIdx.x == 0) {
@@ -430,69 +541,81 @@ __global__ void __launch_bounds__(128) k_obs_tc(Dev D, TcDev T, const Tile* __re
   __syncthreads();
   tc_fence_after();
   const uint32_t tb = tbase;
-  if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(&bar_ld, 4 * TB);
-    const int arow = (int)(nd.off_nk + t.row0);
-    for (int b = 0; b < NB; ++b) {
-      tma_load_2d(ah + b * kBox, &mZH, &bar_ld, b * 64, arow);
-      tma_load_2d(al + b * kBox, &mZL, &bar_ld, b * 64, arow);
-      tma_load_2d(bh + b * kBox, &mCH, &bar_ld, b * 64, crow);
-      tma_load_2d(bl + b * kBox, &mCL, &bar_ld, b * 64, crow);
-    }
-  }
-  for (int o = threadIdx.x; o < obs; o += blockDim.x) xs[o] = T.xs[nd.off_x + o];  // x~ = x - C m
-  __syncthreads();
   const uint32_t idesc = idesc_f16(kRows, kRows, false, false, false);
-  float rs = 0.f;
-  for (int c = 0; c < nchunk; ++c) {
+  uint32_t nld = 0, nmma = 0;  // completed phases of the two barriers (same in every thread)
+  bool run = true;
+  // persistent loop over the leaf tiles
+  for (int item = blockIdx.x; run && item < ntiles; item += gridDim.x) {
+    const Tile t = tiles[item];
+    const NodeInfo nd = D.nodes[t.node];
+    const int obs = nd.obs;
+    const int nchunk = (obs + kRows - 1) / kRows;
+    const int crow = T.c_row[D.shared ? 0 : nd.b];
     if (threadIdx.x == 0) {
-      if (c > 0) {
-        mbar_arrive_expect_tx(&bar_ld, 2 * TB);
-        for (int b = 0; b < NB; ++b) {
-          tma_load_2d(bh + b * kBox, &mCH, &bar_ld, b * 64, crow + c * kRows);
-          tma_load_2d(bl + b * kBox, &mCL, &bar_ld, b * 64, crow + c * kRows);
-        }
-      }
-      if (mbar_wait(&bar_ld, c & 1)) {
-        tc_fence_after();
-        for (int kk = 0; kk < KS; ++kk) mma_ss(tb, kdesc(ah, kk), kdesc(bh, kk), idesc, kk > 0);
-        for (int kk = 0; kk < KS; ++kk) mma_ss(tb, kdesc(al, kk), kdesc(bh, kk), idesc, 1);
-        for (int kk = 0; kk < KS; ++kk) mma_ss(tb, kdesc(ah, kk), kdesc(bl, kk), idesc, 1);
-        mma_commit(&bar_mma);
-      } else {
-        set_timeout(D);
-        mbar_wait(&bar_ld, c & 1);  // once more (bounded) for the copies still in flight
-        s_ok = 0;
+      mbar_arrive_expect_tx(&bar_ld, 4 * TB);
+      const int arow = (int)(nd.off_nk + t.row0);
+      for (int b = 0; b < NB; ++b) {
+        tma_load_2d(ah + b * kBox, &mZH, &bar_ld, b * 64, arow);
+        tma_load_2d(al + b * kBox, &mZL, &bar_ld, b * 64, arow);
+        tma_load_2d(bh + b * kBox, &mCH, &bar_ld, b * 64, crow);
+        tma_load_2d(bl + b * kBox, &mCL, &bar_ld, b * 64, crow);
       }
     }
+    for (int o = threadIdx.x; o < obs; o += blockDim.x) xs[o] = __ldg(T.xs + nd.off_x + o);  // x~ = x - C m
     __syncthreads();
-    if (!s_ok) break;
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(&bar_mma, c & 1));
-    tc_fence_after();
-    if (ok) {
+    float rs = 0.f;
+    for (int c = 0; c < nchunk; ++c) {
+      if (threadIdx.x == 0) {
+        if (c > 0) {
+          mbar_arrive_expect_tx(&bar_ld, 2 * TB);
+          for (int b = 0; b < NB; ++b) {
+            tma_load_2d(bh + b * kBox, &mCH, &bar_ld, b * 64, crow + c * kRows);
+            tma_load_2d(bl + b * kBox, &mCL, &bar_ld, b * 64, crow + c * kRows);
+          }
+        }
+        if (mbar_wait(&bar_ld, nld & 1)) {
+          tc_fence_after();
+          for (int kk = 0; kk < KS; ++kk) mma_ss(tb, kdesc(ah, kk), kdesc(bh, kk), idesc, kk > 0);
+          for (int kk = 0; kk < KS; ++kk) mma_ss(tb, kdesc(al, kk), kdesc(bh, kk), idesc, 1);
+          for (int kk = 0; kk < KS; ++kk) mma_ss(tb, kdesc(ah, kk), kdesc(bl, kk), idesc, 1);
+          mma_commit(&bar_mma);
+        } else {
+          set_timeout(D);
+          mbar_wait(&bar_ld, nld & 1);  // once more (bounded) for the copies still in flight
+          s_ok = 0;
+        }
+      }
+      ++nld;
+      __syncthreads();
+      if (!s_ok) { run = false; break; }
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&bar_mma, nmma & 1));
+      tc_fence_after();
+      if (ok) {
 #pragma unroll 1
-      for (int q = 0; q < 4; ++q) {
-        const int o0 = c * kRows + q * 32;
-        if (o0 >= obs) break;
-        uint32_t v[32];
-        tmem_ld32(tb + ((uint32_t)(warp * 32) << 16) + q * 32, v);
-        tmem_wait_ld();
+        for (int q = 0; q < 4; ++q) {
+          const int o0 = c * kRows + q * 32;
+          if (o0 >= obs) break;
+          uint32_t v[32];
+          tmem_ld32(tb + ((uint32_t)(warp * 32) << 16) + q * 32, v);
+          tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float r = (o0 + j < obs) ? xs[o0 + j] - __uint_as_float(v[j]) : 0.f;
-          rs = fmaf(r, r, rs);
+          for (int j = 0; j < 32; ++j) {
+            const float r = (o0 + j < obs) ? xs[o0 + j] - __uint_as_float(v[j]) : 0.f;
+            rs = fmaf(r, r, rs);
+          }
         }
+      } else {
+        if (lane == 0) set_timeout(D);
+        mbar_wait(&bar_mma, nmma & 1);  // once more (bounded) before the accumulator is reused
       }
-    } else {
-      if (lane == 0) set_timeout(D);
-      mbar_wait(&bar_mma, c & 1);  // once more (bounded) before the accumulator is released
+      ++nmma;
+      tc_fence_before();
+      if (!__syncthreads_and(ok)) { run = false; break; }  // block-uniform
     }
-    tc_fence_before();
-    __syncthreads();
-    if (!ok) break;
+    const int k = t.row0 + threadIdx.x;
+    if (run && k < nd.K) D.u[nd.off_nk + k] -= 0.5f * rs * D.inv_obs_var;
+    __syncthreads();  // xs and the operand tiles are free for the next item
   }
-  const int k = t.row0 + threadIdx.x;
-  if (s_ok && k < nd.K) D.u[nd.off_nk + k] -= 0.5f * rs * D.inv_obs_var;
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -1166,52 +1289,82 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 
 // =======================================================================================
 // Root moments: zbar_0 = sum_k q_0 z~_0, M2_0 = sum_k q_0 z~_0 z~_0^T (FP32 samples).
-// Grid: (instance, 64x64 tile of M2 (2 x 2), 256-sample slab); slabs add into M2 / zbar,
-// which start at zero.
+// Grid: (instance, 128-sample slab).  A slab is staged in shared memory 64 rows at a time
+// (all loads of a stage issued before any store); each thread accumulates an R x R block of
+// M2 (R = 8 for d > 64, else 4: a 128x128 or 64x64 corner); slabs add into the zeroed M2 and
+// zbar.
 // =======================================================================================
-constexpr int kRootSlab = 256;
-__global__ void __launch_bounds__(kThreads) k_root_moments(Dev D, TcDev T) {
-  __shared__ TileSmem sm;
-  __shared__ float qz[kTile * kLd];
-  const InstInfo in = D.insts[blockIdx.x];
-  const NodeInfo nd = D.nodes[in.node0];
-  const int d = nd.d, K = nd.K;
-  const int a0 = (blockIdx.y >> 1) * kTile, b0 = (blockIdx.y & 1) * kTile;
-  const int kb = blockIdx.z * kRootSlab, ke = min(K, kb + kRootSlab);
-  if (a0 >= d || b0 >= d || kb >= K) return;
+constexpr int kRootSlab = 128;
+constexpr int kRootLd = kTcMaxD + 4;
+template <int R>
+__device__ __forceinline__ void root_moments_slab(const Dev& D, const TcDev& T, const NodeInfo& nd, int g,
+                                                  int kb, int ke, float (*zs)[kRootLd], float* qs) {
+  constexpr int DP = 16 * R;          // corner covered by the 16 x 16 threads
+  constexpr int NV = 64 * DP / 256;   // staged values per thread per 64-row stage
+  const int d = nd.d;
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  float acc[4][4];
-  zero_acc(acc);
-  float zs = 0.f;
-  for (int k0 = kb; k0 < ke; k0 += kTile) {
-    const int rows = min(kTile, ke - k0);
-    // qz[l = k][m = a] = q[k] z~[k][a0 + m]
-    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
-      const int l = e >> 6, m = e & 63;
-      float v = 0.f;
-      if (l < rows && a0 + m < d) v = D.q[nd.off_nk + k0 + l] * D.zt[nd.off_nkd + (long long)(k0 + l) * d + a0 + m];
-      qz[l * kLd + m] = v;
+  const float* __restrict__ zt = D.zt + nd.off_nkd;
+  float acc[R][R];
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) acc[i][j] = 0.f;
+  float zsum = 0.f;
+  for (int k0 = kb; k0 < ke; k0 += 64) {
+    const int rows = min(64, ke - k0);
+    float v[NV];
+#pragma unroll
+    for (int x = 0; x < NV; ++x) {
+      const int e = threadIdx.x + x * 256, l = e / DP, c = e % DP;
+      v[x] = (l < rows && c < d) ? zt[(long long)(k0 + l) * d + c] : 0.f;
     }
+    const float qv = threadIdx.x < rows ? D.q[nd.off_nk + k0 + threadIdx.x] : 0.f;
+    __syncthreads();  // the previous stage has been consumed
+#pragma unroll
+    for (int x = 0; x < NV; ++x) {
+      const int e = threadIdx.x + x * 256;
+      zs[e / DP][e % DP] = v[x];
+    }
+    if (threadIdx.x < 64) qs[threadIdx.x] = qv;
     __syncthreads();
-    if (b0 == 0 && threadIdx.x < kTile)
-      for (int l = 0; l < rows; ++l) zs += qz[l * kLd + threadIdx.x];
-    for (int l0 = 0; l0 < rows; l0 += kSlice) {
-      load_slice<false>(sm.b, D.zt + nd.off_nkd + (long long)k0 * d + b0, d, min(kTile, d - b0), l0, rows);
-      __syncthreads();
-      slice_fma(acc, qz + l0 * kLd, sm.b);
-      __syncthreads();
+    for (int l = 0; l < rows; ++l) {
+      const float q = qs[l];
+      float a[R], b[R];
+#pragma unroll
+      for (int i = 0; i < R; i += 4) {
+        const float4 av = *reinterpret_cast<const float4*>(&zs[l][ty * R + i]);
+        const float4 bv = *reinterpret_cast<const float4*>(&zs[l][tx * R + i]);
+        a[i] = q * av.x; a[i + 1] = q * av.y; a[i + 2] = q * av.z; a[i + 3] = q * av.w;
+        b[i] = bv.x; b[i + 1] = bv.y; b[i + 2] = bv.z; b[i + 3] = bv.w;
+      }
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
+    if (threadIdx.x < DP)
+      for (int l = 0; l < rows; ++l) zsum = fmaf(qs[l], zs[l][threadIdx.x], zsum);
   }
-  float* M = T.M2 + (long long)in.node0 * kLdp * kLdp;
+  float* M = T.M2 + (long long)g * kLdp * kLdp;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int a = a0 + ty * 4 + i, b = b0 + tx * 4 + j;
+    for (int j = 0; j < R; ++j) {
+      const int a = ty * R + i, b = tx * R + j;
       if (a < d && b < d) atomicAdd(M + (long long)a * kLdp + b, acc[i][j]);
     }
-  if (b0 == 0 && threadIdx.x < kTile && a0 + threadIdx.x < d)
-    atomicAdd(T.zbar + (long long)in.node0 * kLdp + a0 + threadIdx.x, zs);
+  if (threadIdx.x < d) atomicAdd(T.zbar + (long long)g * kLdp + threadIdx.x, zsum);
+}
+
+__global__ void __launch_bounds__(256) k_root_moments(Dev D, TcDev T) {
+  __shared__ __align__(16) float zs[64][kRootLd];
+  __shared__ float qs[64];
+  const InstInfo in = D.insts[blockIdx.x];
+  const NodeInfo nd = D.nodes[in.node0];
+  const int kb = blockIdx.y * kRootSlab, ke = min(nd.K, kb + kRootSlab);
+  if (kb >= nd.K) return;
+  if (nd.d > 64) root_moments_slab<8>(D, T, nd, in.node0, kb, ke, zs, qs);
+  else root_moments_slab<4>(D, T, nd, in.node0, kb, ke, zs, qs);
 }
 
 // =======================================================================================
@@ -1237,14 +1390,14 @@ __global__ void __launch_bounds__(128) k_asm_edge_vec(Dev D, TcDev T, const int*
   const float* zbc = T.zbar + (long long)g * kLdp;
   const float* cc = T.cvec + (long long)g * kLdp;
   const int j = threadIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (j < d) zp[j] = T.zbar[(long long)nd.parent * kLdp + j];
+  if (j < d) zp[j] = __ldg(T.zbar + (long long)nd.parent * kLdp + j);
   __syncthreads();
   // (W_c zbar_p)[r]: one warp per row, lanes along the row (coalesced)
   for (int r = w; r < d; r += 4) {
     float s = 0.f;
-    for (int c = lane; c < d; c += 32) s = fmaf(W[(long long)r * d + c], zp[c], s);
+    for (int c = lane; c < d; c += 32) s = fmaf(__ldg(W + (long long)r * d + c), zp[c], s);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) dbs[r] = (zbc[r] - s - cc[r]) * iv;
+    if (lane == 0) dbs[r] = (__ldg(zbc + r) - s - __ldg(cc + r)) * iv;
   }
   __syncthreads();
   if (j >= d) return;
@@ -1256,7 +1409,7 @@ __global__ void __launch_bounds__(128) k_asm_edge_vec(Dev D, TcDev T, const int*
   // diag(W_c G_c) / var (k_asm_edge_mat, which holds both tiles, into the zeroed tgC) plus
   // (c_c zbar_c - diag M2_c) / var (added by k_asm_node)
   float sg = 0.f;
-  for (int a = 0; a < d; ++a) sg = fmaf(W[(long long)a * d + j], dbs[a], sg);
+  for (int a = 0; a < d; ++a) sg = fmaf(__ldg(W + (long long)a * d + j), dbs[a], sg);
   T.sgP[(long long)g * kLdp + j] = sg;
 }
 
@@ -1281,11 +1434,23 @@ __global__ void __launch_bounds__(kThreads) k_asm_edge_mat(Dev D, TcDev T, const
   const float* zbp = T.zbar + (long long)nd.parent * kLdp;
   const float* cc = T.cvec + (long long)g * kLdp;
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  // sW[r][c] = W[a0 + r][b0 + c],  sG[r][c] = G[b0 + r][a0 + c]  (so G^T[a][b] = sG[b][a])
-  for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
-    const int r = e >> 6, c = e & 63;
-    sW[r][c] = (a0 + r < d && b0 + c < d) ? W[(long long)(a0 + r) * d + b0 + c] : 0.f;
-    sG[r][c] = (b0 + r < d && a0 + c < d) ? Gc[(long long)(b0 + r) * kLdp + a0 + c] : 0.f;
+  // sW[r][c] = W[a0 + r][b0 + c],  sG[r][c] = G[b0 + r][a0 + c]  (so G^T[a][b] = sG[b][a]);
+  // every load of the stage is issued before the first shared-memory store
+  {
+    constexpr int NV = kTile * kTile / kThreads;
+    float wv[NV], gv[NV];
+#pragma unroll
+    for (int x = 0; x < NV; ++x) {
+      const int e = threadIdx.x + x * kThreads, r = e >> 6, c = e & 63;
+      wv[x] = (a0 + r < d && b0 + c < d) ? __ldg(W + (long long)(a0 + r) * d + b0 + c) : 0.f;
+      gv[x] = (b0 + r < d && a0 + c < d) ? __ldg(Gc + (long long)(b0 + r) * kLdp + a0 + c) : 0.f;
+    }
+#pragma unroll
+    for (int x = 0; x < NV; ++x) {
+      const int e = threadIdx.x + x * kThreads, r = e >> 6, c = e & 63;
+      sW[r][c] = wv[x];
+      sG[r][c] = gv[x];
+    }
   }
   float acc[4][4];
   zero_acc(acc);
@@ -1294,20 +1459,29 @@ __global__ void __launch_bounds__(kThreads) k_asm_edge_mat(Dev D, TcDev T, const
                          min(kTile, d - b0), d, sm);
   float tcol[4] = {0.f, 0.f, 0.f, 0.f};
   float wrow[4] = {0.f, 0.f, 0.f, 0.f};
+  // every vector operand of the epilogue in registers before the first store
+  float dbv[4], cav[4], zpv[4], mpv[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int a = a0 + ty * 4 + i, bb = b0 + tx * 4 + i;
+    dbv[i] = a < d ? -__ldg(T.sgC + (long long)g * kLdp + a) : 0.f;  // db'[a], from k_asm_edge_vec
+    cav[i] = a < d ? __ldg(cc + a) : 0.f;
+    zpv[i] = bb < d ? __ldg(zbp + bb) : 0.f;
+    mpv[i] = bb < d ? __ldg(D.q_mean + pn.off_q + bb) : 0.f;
+  }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int al = ty * 4 + i, a = a0 + al;
-    const float db = a < d ? -T.sgC[(long long)g * kLdp + a] : 0.f;  // db'[a], from k_asm_edge_vec
-    const float ca = a < d ? cc[a] : 0.f;
+    const float db = dbv[i], ca = cav[i];
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
       const int bl = tx * 4 + jj, bb = b0 + bl;
       if (a >= d || bb >= d) continue;
       const float wab = sW[al][bl], gt = sG[bl][al];
-      const float Dab = (gt - acc[i][jj] - ca * zbp[bb]) * iv;
+      const float Dab = (gt - acc[i][jj] - ca * zpv[jj]) * iv;
       tcol[jj] = fmaf(wab, Dab, tcol[jj]);
       wrow[i] = fmaf(wab, gt, wrow[i]);
-      const float v = go * (Dab + db * D.q_mean[pn.off_q + bb]);
+      const float v = go * (Dab + db * mpv[jj]);
       if (D.shared) { if (D.pW) D.pW[nd.off_pW + (long long)a * d + bb] = v; }
       else if (D.dW) D.dW[nd.off_W + (long long)a * d + bb] = v;
     }
@@ -1370,19 +1544,26 @@ __global__ void __launch_bounds__(128) k_asm_node(Dev D, TcDev T) {
   const float* M2 = T.M2 + (long long)g * kLdp * kLdp;
   const int j = threadIdx.x;
   float qs = 0.f;
-  for (int k = j; k < K; k += blockDim.x) qs += D.q[nd.off_nk + k];
+#pragma unroll 8
+  for (int k = j; k < K; k += blockDim.x) qs += __ldg(D.q + nd.off_nk + k);
   for (int o = 16; o > 0; o >>= 1) qs += __shfl_xor_sync(0xffffffffu, qs, o);
   if ((j & 31) == 0) qred[j >> 5] = qs;
-  if (j < d) zb[j] = T.zbar[(long long)g * kLdp + j];
+  if (j < d) zb[j] = __ldg(T.zbar + (long long)g * kLdp + j);
   const bool leaf = nd.leaf_slot >= 0, root = nd.parent < 0;
   if (leaf)  // x~ = x - C m, formed in the forward pass
-    for (int o = j; o < nd.obs; o += blockDim.x) xs[o] = T.xs[nd.off_x + o];
+    for (int o = j; o < nd.obs; o += blockDim.x) xs[o] = __ldg(T.xs + nd.off_x + o);
   __syncthreads();
   const float qtot = qred[0] + qred[1] + qred[2] + qred[3];
   if (leaf && j < d) {
-    float s = 0.f;
-    for (int o = 0; o < nd.obs; ++o) s = fmaf(D.C[nd.off_C + (long long)o * d + j], xs[o], s);
-    ctx[j] = s;
+    float s0 = 0.f, s1 = 0.f;
+    const float* c = D.C + nd.off_C + j;
+#pragma unroll 4
+    for (int o = 0; o < nd.obs - 1; o += 2) {
+      s0 = fmaf(__ldg(c + (long long)o * d), xs[o], s0);
+      s1 = fmaf(__ldg(c + (long long)(o + 1) * d), xs[o + 1], s1);
+    }
+    if (nd.obs & 1) s0 = fmaf(__ldg(c + (long long)(nd.obs - 1) * d), xs[nd.obs - 1], s0);
+    ctx[j] = s0 + s1;
   }
   __syncthreads();
   if (j >= d) return;
@@ -1412,10 +1593,11 @@ __global__ void __launch_bounds__(128) k_asm_node(Dev D, TcDev T) {
     // C^T C is symmetric: row j read as column j (coalesced over threads)
     const float* ctc = T.CtC + (long long)(D.shared ? 0 : nd.b) * kLdp * kLdp;
     float czb = 0.f, dg = 0.f;
+#pragma unroll 8
     for (int a = 0; a < d; ++a) {
-      const float v = ctc[(long long)a * kLdp + j];
+      const float v = __ldg(ctc + (long long)a * kLdp + j);
       czb = fmaf(v, zb[a], czb);
-      dg = fmaf(v, M2[(long long)a * kLdp + j], dg);
+      dg = fmaf(v, __ldg(M2 + (long long)a * kLdp + j), dg);
     }
     Sg += (ctx[j] - czb) * D.inv_obs_var;
     Tg += (ctx[j] * zb[j] - dg) * D.inv_obs_var;
@@ -1442,11 +1624,11 @@ __global__ void __launch_bounds__(kThreads) k_leaf_S(Dev D, TcDev T) {
     if (nd.leaf_slot < 0) continue;
     const float* M2 = T.M2 + (long long)gi * kLdp * kLdp;
     const float* zb = T.zbar + (long long)gi * kLdp;
-    const float mb = b0 + c < d ? D.q_mean[nd.off_q + b0 + c] : 0.f;
+    const float mb = b0 + c < d ? __ldg(D.q_mean + nd.off_q + b0 + c) : 0.f;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const int a = a0 + r0 + 4 * i;
-      if (a < d && b0 + c < d) acc[i] += M2[(long long)a * kLdp + b0 + c] + zb[a] * mb;
+      if (a < d && b0 + c < d) acc[i] += __ldg(M2 + (long long)a * kLdp + b0 + c) + __ldg(zb + a) * mb;
     }
   }
   float* S = T.S + (long long)blockIdx.x * kLdp * kLdp;
@@ -1482,12 +1664,12 @@ __global__ void __launch_bounds__(kThreads) k_asm_dC(Dev D, TcDev T) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int o = o0 + ty * 4 + i;
-      xo[i] = o < obs ? T.xs[nd.off_x + o] : 0.f;
+      xo[i] = o < obs ? __ldg(T.xs + nd.off_x + o) : 0.f;
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int c = c0 + tx * 4 + j;
-      zm[j] = c < d ? T.zbar[(long long)gi * kLdp + c] + D.q_mean[nd.off_q + c] : 0.f;
+      zm[j] = c < d ? __ldg(T.zbar + (long long)gi * kLdp + c) + __ldg(D.q_mean + nd.off_q + c) : 0.f;
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -1756,6 +1938,7 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
   cudaFuncSetAttribute(k_edge_fwd_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f128);
   cudaFuncSetAttribute(k_edge_bwd_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<64>(maxK));
   cudaFuncSetAttribute(k_edge_bwd_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<128>(maxK));
+  cudaFuncSetAttribute(k_sample_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSampleSmem);
   cudaFuncSetAttribute(k_obs_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)obs_smem<64>());
   cudaFuncSetAttribute(k_obs_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)obs_smem<128>());
   return cudaGetLastError() == cudaSuccess ? TMC_OK : TMC_ERR_CUDA;
@@ -1788,8 +1971,8 @@ void release(TcWork& w) {
 }
 
 void launch_sample(TcWork& w, const Dev& D, cudaStream_t s) {
-  if (!w.sample_tiles.empty())
-    k_sample_tc<<<(int)w.sample_tiles.size(), 256, 3 * kTcMaxD * sizeof(float), s>>>(D, w.t, w.d_sample_tiles);
+  const int n = (int)w.sample_tiles.size();
+  if (n) k_sample_tc<<<std::min(n, 2 * w.num_sms), 256, kSampleSmem, s>>>(D, w.t, w.d_sample_tiles, n);
 }
 
 void launch_pack(TcWork& w, const Dev& D, cudaStream_t s) {
@@ -1802,14 +1985,17 @@ void launch_pack(TcWork& w, const Dev& D, cudaStream_t s) {
 void launch_obs(TcWork& w, const Dev& D, cudaStream_t s) {
   if (w.obs_tiles.empty()) return;
   k_obs_center<<<(int)w.leaves.size(), 128, 0, s>>>(D, w.t, w.d_leaves);
-  k_pack_cobs<<<dim3(w.num_c, (w.maxobs + 1) / 2), 256, 0, s>>>(D, w.t);
+  k_pack_cobs<<<dim3(w.num_c, (w.maxobs + 7) / 8), 256, 0, s>>>(D, w.t);
   for (int c = 0; c < 2; ++c) {
     const int b = w.ob_b[c], n = w.ob_e[c] - b;
     if (!n) continue;
+    // persistent: as many CTAs as fit at once (shared memory bounds them to 3 / 1 per SM)
     if (c == 0)
-      k_obs_tc<64><<<n, 128, obs_smem<64>(), s>>>(D, w.t, w.d_obs_tiles + b, w.mZH, w.mZL, w.mCH, w.mCL);
+      k_obs_tc<64><<<std::min(n, 3 * w.num_sms), 128, obs_smem<64>(), s>>>(D, w.t, w.d_obs_tiles + b, n, w.mZH,
+                                                                            w.mZL, w.mCH, w.mCL);
     else
-      k_obs_tc<128><<<n, 128, obs_smem<128>(), s>>>(D, w.t, w.d_obs_tiles + b, w.mZH, w.mZL, w.mCH, w.mCL);
+      k_obs_tc<128><<<std::min(n, w.num_sms), 128, obs_smem<128>(), s>>>(D, w.t, w.d_obs_tiles + b, n, w.mZH,
+                                                                          w.mZL, w.mCH, w.mCL);
   }
 }
 
@@ -1853,7 +2039,7 @@ void launch_unpack_grads(TcWork& w, const Dev& D, cudaStream_t s) {
     cudaMemsetAsync(w.t.M2, 0, (size_t)w.num_nodes * kLdp * kLdp * sizeof(float), s);
     cudaMemsetAsync(w.t.zbar, 0, (size_t)w.num_nodes * kLdp * sizeof(float), s);
   }
-  k_root_moments<<<dim3(D.num_inst, 4, (w.maxK + kRootSlab - 1) / kRootSlab), kThreads, 0, s>>>(D, w.t);
+  k_root_moments<<<dim3(D.num_inst, (w.maxK + kRootSlab - 1) / kRootSlab), 256, 0, s>>>(D, w.t);
   cudaMemsetAsync(w.t.CtC, 0, (size_t)(D.shared ? 1 : D.num_inst) * kLdp * kLdp * sizeof(float), s);
   k_ctc<<<dim3(D.shared ? 1 : D.num_inst, w.maxdp > 64 ? 4 : 1, (w.maxobs + kTile - 1) / kTile), kThreads, 0, s>>>(D, w.t);
   cudaMemsetAsync(w.t.tgP, 0, (size_t)w.num_nodes * kLdp * sizeof(float), s);

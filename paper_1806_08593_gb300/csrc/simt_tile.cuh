@@ -17,24 +17,42 @@ struct TileSmem {
   float b[kSlice * kLd];
 };
 
-// Loads a 16 x 64 slice into s[l][m].
+// A 16 x 64 slice s[l][m] is fetched into registers (4 values per thread) and then stored to
+// shared memory, so the next slice's loads can be in flight while the current one is used.
 //   TRANS = true : element (m, l) of a row-major matrix src[m * ld + l] ("row m, depth l")
 //   TRANS = false: element (l, m) of a row-major matrix src[l * ld + m]
 // Out-of-range entries (m >= mlim or l0 + l >= llim) are zero.
+constexpr int kSliceVals = kSlice * kTile / kThreads;
 template <bool TRANS>
-__device__ __forceinline__ void load_slice(float* s, const float* __restrict__ src, long long ld,
-                                           int mlim, int l0, int llim) {
-  const int tid = threadIdx.x;
+__device__ __forceinline__ void fetch_slice(float (&r)[kSliceVals], const float* __restrict__ src, long long ld,
+                                            int mlim, int l0, int llim) {
 #pragma unroll
-  for (int e = tid; e < kSlice * kTile; e += kThreads) {
+  for (int x = 0; x < kSliceVals; ++x) {
+    const int e = threadIdx.x + x * kThreads;
     int l, m;
     if (TRANS) { m = e >> 4; l = e & 15; }
     else       { l = e >> 6; m = e & 63; }
     const int gl = l0 + l;
-    float v = 0.f;
-    if (m < mlim && gl < llim) v = TRANS ? src[(long long)m * ld + gl] : src[(long long)gl * ld + m];
-    s[l * kLd + m] = v;
+    r[x] = (m < mlim && gl < llim) ? (TRANS ? src[(long long)m * ld + gl] : src[(long long)gl * ld + m]) : 0.f;
   }
+}
+template <bool TRANS>
+__device__ __forceinline__ void store_slice(float* s, const float (&r)[kSliceVals]) {
+#pragma unroll
+  for (int x = 0; x < kSliceVals; ++x) {
+    const int e = threadIdx.x + x * kThreads;
+    int l, m;
+    if (TRANS) { m = e >> 4; l = e & 15; }
+    else       { l = e >> 6; m = e & 63; }
+    s[l * kLd + m] = r[x];
+  }
+}
+template <bool TRANS>
+__device__ __forceinline__ void load_slice(float* s, const float* __restrict__ src, long long ld,
+                                           int mlim, int l0, int llim) {
+  float r[kSliceVals];
+  fetch_slice<TRANS>(r, src, ld, mlim, l0, llim);
+  store_slice<TRANS>(s, r);
 }
 
 __device__ __forceinline__ void slice_fma(float acc[4][4], const float* sa, const float* sb) {
@@ -56,14 +74,25 @@ __device__ __forceinline__ void slice_fma(float acc[4][4], const float* sa, cons
 //   opA(m, l) = A_TRANS ? A[m*lda + l] : A[l*lda + m]     (m < ma)
 //   opB(n, l) = B_TRANS ? B[n*ldb + l] : B[l*ldb + n]     (n < nb)
 // and the product is sum_l opA(m, l) * opB(n, l).
+// The loads of slice l0 + 16 are issued before slice l0 is multiplied (register double
+// buffering), so the global-memory latency of a slice overlaps the previous slice's FMAs.
 template <bool A_TRANS, bool B_TRANS>
 __device__ __forceinline__ void tile_gemm(float acc[4][4], const float* __restrict__ A,
                                           long long lda, int ma, const float* __restrict__ B,
                                           long long ldb, int nb, int L, TileSmem& sm) {
+  float ra[kSliceVals], rb[kSliceVals];
+  if (L > 0) {
+    fetch_slice<A_TRANS>(ra, A, lda, ma, 0, L);
+    fetch_slice<B_TRANS>(rb, B, ldb, nb, 0, L);
+  }
   for (int l0 = 0; l0 < L; l0 += kSlice) {
-    load_slice<A_TRANS>(sm.a, A, lda, ma, l0, L);
-    load_slice<B_TRANS>(sm.b, B, ldb, nb, l0, L);
+    store_slice<A_TRANS>(sm.a, ra);
+    store_slice<B_TRANS>(sm.b, rb);
     __syncthreads();
+    if (l0 + kSlice < L) {
+      fetch_slice<A_TRANS>(ra, A, lda, ma, l0 + kSlice, L);
+      fetch_slice<B_TRANS>(rb, B, ldb, nb, l0 + kSlice, L);
+    }
     slice_fma(acc, sm.a, sm.b);
     __syncthreads();
   }
