@@ -625,59 +625,65 @@ __global__ void __launch_bounds__(128) k_obs_tc(Dev D, TcDev T, const Tile* __re
 }
 
 // =======================================================================================
-// Forward edge kernel.
-// Math warps 4..11: warp w serves TMEM lanes 32*(w%4).. (tile rows) and half h = (w-4)/4 of
-// the columns of every S chunk (and of the latent dimension in the prologue).
+// Forward edge kernel, pipelined across the CTA's items.
+// Roles: warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs, warp 2 owns the TMEM
+// allocation, warp 3 prepares the next item's message vector (dependency wait, beta_i, its
+// maximum, c_i), warps 4..11 run the exponentials (warp w serves TMEM lanes 32*(w%4).. and half
+// h = (w-4)/4 of the columns of every S chunk and of the latent dimension in the prologue).
+// The barriers are initialised once; every role walks the same item sequence and derives the
+// phase of each barrier from running counters:
+//   ring uses   : per item [Z~_p tile, W_i, chunk 0 .. chunk nch-1], stage = use % NS
+//   S buffers   : running chunk count, buffer = chunk & 1
+//   per item    : mu_full (mu~ in TMEM), a_full (A operand written), phase = item count & 1
+//   beta buffers: NCB (1 or 2) SMEM copies of cb / c_i, written by warp 3, freed by the math warps
+// so the TMA and MMA warps run into item j + 1 (its operands, mu~ = Z~_p W^T into TMEM) while
+// the math warps still finish item j, and warp 3 has item j + 1's message vector ready.
 // =======================================================================================
 template <int DP>
+struct FwdCfg {
+  static constexpr int TB = kRows * DP * 2;  // bytes of one [128 x DP] fp16 tile
+  static constexpr int NB = DP / 64;         // 64-column boxes per tile
+  static constexpr int KS = DP / 16;         // K-steps over the latent dimension
+  static constexpr int GH = DP / 64;         // 32-column groups of the latent dimension per half
+  static constexpr int NS = DP == 64 ? 6 : 3;  // ring stages of (hi, lo) tiles
+};
+
+// Bounded wait that also gives up as soon as another role of the CTA has given up.
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort || clock64() - t0 > (1ll << 31)) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+template <int DP>
 __global__ void __launch_bounds__(kThreadsTc, 1)
-    k_edge_fwd_tc(Dev D, TcDev T, const Tile* __restrict__ tiles, int ntiles, int* __restrict__ done,
+    k_edge_fwd_tc(Dev D, TcDev T, const Tile* __restrict__ tiles, int ntiles, int* __restrict__ done, int ncb, int cbk,
                   const __grid_constant__ CUtensorMap mZH, const __grid_constant__ CUtensorMap mZL,
                   const __grid_constant__ CUtensorMap mWH, const __grid_constant__ CUtensorMap mWL) {
-  constexpr int TB = kRows * DP * 2;  // bytes of one [128 x DP] fp16 tile
-  constexpr int NB = DP / 64;         // 64-column boxes per tile
-  constexpr int KS = DP / 16;         // K-steps over the latent dimension
-  constexpr int GH = DP / 64;         // 32-column groups of the latent dimension per half
-  constexpr int NS = 3;               // ring stages
+  using C = FwdCfg<DP>;
+  constexpr int TB = C::TB, NB = C::NB, KS = C::KS, GH = C::GH, NS = C::NS;
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  unsigned char* ring = sm;           // NS stages x (hi, lo)
-  float* cb = reinterpret_cast<float*>(ring + NS * 2 * TB);
-  __shared__ uint64_t bar_pro, bar_mu, bar_A, full[NS], empty[NS], sfull[2], sfree[2], bar_done;
+  unsigned char* ring = sm;  // NS stages x (hi, lo)
+  float* cbuf = reinterpret_cast<float*>(ring + NS * 2 * TB);  // [ncb][cbk], cbk = max K rounded up to 128
+  __shared__ uint64_t full[NS], empty[NS], sfull[2], sfree[2], mu_full, a_full, cb_full[2], cb_empty[2],
+      bar_done;
   __shared__ uint32_t tbase;
-  __shared__ float red[8];
-  __shared__ float cv[kTcMaxD];
+  __shared__ int s_abort;
+  __shared__ __align__(16) float cvb[2][kTcMaxD];
   __shared__ float nrm_h[2][kRows], m_h[2][kRows], s_h[2][kRows];
+  volatile int* abort = &s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float iv = D.inv_var;
   if (warp == 2) tmem_alloc(&tbase, 512);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tb = tbase;
-  // TMEM: S double buffer [0,256), mu~ accumulator [256,384), A operand hi [384,448) lo [448,512)
-  const uint32_t tS[2] = {tb, tb + 128}, tMU = tb + 256, tAH = tb + 384, tAL = tb + 448;
-
-  // persistent loop over the edge tiles of every level, deepest level first
-  for (int item = blockIdx.x; item < ntiles; item += gridDim.x) {
-  const Tile t = tiles[item];
-  const NodeInfo nd = D.nodes[t.node];
-  const NodeInfo pn = D.nodes[nd.parent];
-  const int K = nd.K, nch = (K + kRows - 1) / kRows;
   if (threadIdx.x == 0) {
-    // every child of the edge's child node must have sent its message (all its tiles)
-    bool dep_ok = true;
-    for (int c = nd.child_begin; c < nd.child_end; ++c) {
-      const int cg = D.children[c];
-      dep_ok = wait_count(done + cg, tiles_of(D.nodes[cg].K)) && dep_ok;
-    }
-    if (!dep_ok) set_timeout(D);
-    stamp_item_start(T, 0, item);
-    mbar_init(&bar_pro, 1);
-    mbar_init(&bar_mu, 1);
-    mbar_init(&bar_A, kMath);
-    mbar_init(&bar_done, 1);
     for (int i = 0; i < NS; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
@@ -685,231 +691,304 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     for (int i = 0; i < 2; ++i) {
       mbar_init(&sfull[i], 1);
       mbar_init(&sfree[i], kMath);
+      mbar_init(&cb_full[i], 1);
+      mbar_init(&cb_empty[i], kMath);
     }
+    mbar_init(&mu_full, 1);
+    mbar_init(&a_full, kMath);
+    mbar_init(&bar_done, 1);
     fence_barrier_init();
+    s_abort = 0;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  const uint32_t tb = tbase;
+  // TMEM: S double buffer [0,256), mu~ accumulator [256,384), A operand hi [384,448) lo [448,512)
+  const uint32_t tS[2] = {tb, tb + 128}, tMU = tb + 256, tAH = tb + 384, tAL = tb + 448;
 
-  if (warp == 0 && lane == 0) {
-    // ------------------------------------------------------------------ TMA producer
-    prefetch_tmap(&mZH);
-    prefetch_tmap(&mZL);
-    // The 8 row tiles of an edge walk the child's chunks in the same order; each CTA pulls
-    // "its" chunk (index = its row tile) into L2 up front so the ring loads hit L2.
-    for (int b = 0; b < NB; ++b) {
-      tma_prefetch_l2_2d(&mZH, b * 64, (int)(nd.off_nk + t.row0));
-      tma_prefetch_l2_2d(&mZL, b * 64, (int)(nd.off_nk + t.row0));
-    }
-    const int slot = slot_of(D, nd, t.node);
-    mbar_arrive_expect_tx(&bar_pro, 4 * TB);
-    for (int b = 0; b < NB; ++b) {
-      const int prow = (int)(pn.off_nk + t.row0);
-      tma_load_2d(ring + b * kBox, &mZH, &bar_pro, b * 64, prow);
-      tma_load_2d(ring + TB + b * kBox, &mZL, &bar_pro, b * 64, prow);
-      tma_load_2d(ring + 2 * TB + b * kBox, &mWH, &bar_pro, b * 64, slot * kLdp);
-      tma_load_2d(ring + 3 * TB + b * kBox, &mWL, &bar_pro, b * 64, slot * kLdp);
-    }
-    // chunk c uses stage (c + 2) % NS: chunk 0 goes to the stage the prologue leaves free and
-    // is in flight together with the prologue operands
-    bool ok = true;
-    int issued = 0;
-    // the next item's prologue operands into L2 while this item runs
-    if (item + (int)gridDim.x < ntiles) {
-      const Tile tn = tiles[item + gridDim.x];
-      const NodeInfo nn = D.nodes[tn.node];
-      const int prow_n = (int)(D.nodes[nn.parent].off_nk + tn.row0);
-      for (int b = 0; b < NB; ++b) {
-        tma_prefetch_l2_2d(&mZH, b * 64, prow_n);
-        tma_prefetch_l2_2d(&mZL, b * 64, prow_n);
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- TMA producer
+      prefetch_tmap(&mZH);
+      prefetch_tmap(&mZL);
+      prefetch_tmap(&mWH);
+      prefetch_tmap(&mWL);
+      long long gu = 0;  // ring uses issued
+      bool ok = true;
+      for (int item = blockIdx.x; ok && item < ntiles; item += gridDim.x) {
+        const Tile t = tiles[item];
+        const NodeInfo nd = D.nodes[t.node];
+        const NodeInfo pn = D.nodes[nd.parent];
+        const int nch = tiles_of(nd.K);
+        if (item == (int)blockIdx.x) stamp_item_start(T, 0, item);
+        // the 8 row tiles of an edge walk the child's chunks in the same order; each pulls
+        // "its" chunk (index = its row tile) into L2 up front
+        for (int b = 0; b < NB; ++b) {
+          tma_prefetch_l2_2d(&mZH, b * 64, (int)(nd.off_nk + t.row0));
+          tma_prefetch_l2_2d(&mZL, b * 64, (int)(nd.off_nk + t.row0));
+        }
+        const int slot = slot_of(D, nd, t.node);
+        for (int u = 0; ok && u < nch + 2; ++u, ++gu) {
+          const int s = (int)(gu % NS);
+          const long long fill = gu / NS;
+          if (fill >= 1 && !mbar_wait_ab(&empty[s], (uint32_t)((fill - 1) & 1), abort)) { ok = false; break; }
+          unsigned char* st = ring + s * 2 * TB;
+          mbar_arrive_expect_tx(&full[s], 2 * TB);
+          int x_map_row;
+          const CUtensorMap *mh, *ml;
+          if (u == 0) { mh = &mZH; ml = &mZL; x_map_row = (int)(pn.off_nk + t.row0); }          // Z~_p tile
+          else if (u == 1) { mh = &mWH; ml = &mWL; x_map_row = slot * kLdp; }                  // W_i
+          else { mh = &mZH; ml = &mZL; x_map_row = (int)(nd.off_nk + (u - 2) * kRows); }      // chunk u - 2
+          for (int b = 0; b < NB; ++b) {
+            tma_load_2d(st + b * kBox, mh, &full[s], b * 64, x_map_row);
+            tma_load_2d(st + TB + b * kBox, ml, &full[s], b * 64, x_map_row);
+          }
+        }
       }
+      if (!ok) set_timeout(D);
+      // the last fills still in flight land before the CTA exits
+      for (long long g = (gu > NS ? gu - NS : 0); g < gu; ++g)
+        mbar_wait(&full[(int)(g % NS)], (uint32_t)((g / NS) & 1));
     }
-    for (int c = 0; ok && c < nch; ++c) {
-      const int s = (c + 2) % NS, fill = c / NS;  // chunk c is the fill-th use of stage s
-      if (c == 1 && !mbar_wait(&bar_mu, 0)) { ok = false; break; }  // prologue read stages 0, 1
-      if (fill >= 1 && !mbar_wait(&empty[s], (fill - 1) & 1)) { ok = false; break; }
-      unsigned char* st = ring + s * 2 * TB;
-      mbar_arrive_expect_tx(&full[s], 2 * TB);
-      const int row = (int)(nd.off_nk + c * kRows);
-      for (int b = 0; b < NB; ++b) {
-        tma_load_2d(st + b * kBox, &mZH, &full[s], b * 64, row);
-        tma_load_2d(st + TB + b * kBox, &mZL, &full[s], b * 64, row);
-      }
-      issued = c + 1;
-    }
-    if (!ok) set_timeout(D);
-    for (int c = (issued > NS ? issued - NS : 0); c < issued; ++c) mbar_wait(&full[(c + 2) % NS], (c / NS) & 1);
-  } else if (warp == 1 && lane == 0) {
-    // ------------------------------------------------------------------ MMA issuer
-    bool ok = mbar_wait(&bar_pro, 0);
-    if (ok) {
-      tc_fence_after();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- MMA issuer
       const uint32_t id_mu = idesc_f16(kRows, DP, false, false, false);
-      unsigned char *zh = ring, *zl = ring + TB, *wh = ring + 2 * TB, *wl = ring + 3 * TB;
-      for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zh, kk), kdesc(wh, kk), id_mu, kk > 0);
-      for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zl, kk), kdesc(wh, kk), id_mu, 1);
-      for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zh, kk), kdesc(wl, kk), id_mu, 1);
-      mma_commit(&bar_mu);
-      ok = mbar_wait(&bar_A, 0);
+      const uint32_t id_s = idesc_f16(kRows, kRows, false, false, false);
+      long long gu = 0, gc = 0;
+      int it = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; ok && item < ntiles; item += gridDim.x, ++it) {
+        const NodeInfo nd = D.nodes[tiles[item].node];
+        const int nch = tiles_of(nd.K);
+        // prologue: mu~ = Z~_p W_i^T (split products) into MU; MU is free once the math warps
+        // have split the previous item's mu~ (a_full of the previous item, waited below)
+        const int sz = (int)(gu % NS), sw = (int)((gu + 1) % NS);
+        if (!mbar_wait_ab(&full[sz], (uint32_t)((gu / NS) & 1), abort) ||
+            !mbar_wait_ab(&full[sw], (uint32_t)(((gu + 1) / NS) & 1), abort)) { ok = false; break; }
+        tc_fence_after();
+        {
+          unsigned char *zh = ring + sz * 2 * TB, *zl = zh + TB, *wh = ring + sw * 2 * TB, *wl = wh + TB;
+          for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zh, kk), kdesc(wh, kk), id_mu, kk > 0);
+          for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zl, kk), kdesc(wh, kk), id_mu, 1);
+          for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zh, kk), kdesc(wl, kk), id_mu, 1);
+        }
+        mma_commit(&mu_full);
+        mma_commit(&empty[sz]);
+        mma_commit(&empty[sw]);
+        gu += 2;
+        if (!mbar_wait_ab(&a_full, (uint32_t)(it & 1), abort)) { ok = false; break; }
+        for (int c = 0; c < nch; ++c, ++gu, ++gc) {
+          const int s = (int)(gu % NS), b = (int)(gc & 1);
+          if (!mbar_wait_ab(&full[s], (uint32_t)((gu / NS) & 1), abort)) { ok = false; break; }
+          if (gc >= 2 && !mbar_wait_ab(&sfree[b], (uint32_t)(((gc >> 1) + 1) & 1), abort)) { ok = false; break; }
+          tc_fence_after();
+          unsigned char *bh = ring + s * 2 * TB, *bl = bh + TB;
+          // S = (A_hi + A_lo)(B_hi + B_lo)^T without lo*lo; A from tensor memory (2 fp16 / column)
+          for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kdesc(bh, kk), id_s, kk > 0);
+          for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAL + kk * 8, kdesc(bh, kk), id_s, 1);
+          for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kdesc(bl, kk), id_s, 1);
+          mma_commit(&sfull[b]);
+          mma_commit(&empty[s]);
+        }
+      }
+      if (!ok) set_timeout(D);
+      mma_commit(&bar_done);
+      mbar_wait(&bar_done, 0);
     }
-    const uint32_t id_s = idesc_f16(kRows, kRows, false, false, false);
-    for (int c = 0; ok && c < nch; ++c) {
-      const int s = (c + 2) % NS, b = c & 1;
-      if (!mbar_wait(&full[s], (c / NS) & 1)) { ok = false; break; }
-      if (c >= 2 && !mbar_wait(&sfree[b], ((c >> 1) + 1) & 1)) { ok = false; break; }
-      tc_fence_after();
-      unsigned char *bh = ring + s * 2 * TB, *bl = bh + TB;
-      // S = (A_hi + A_lo)(B_hi + B_lo)^T without lo*lo; A from tensor memory (2 fp16 / column)
-      for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kdesc(bh, kk), id_s, kk > 0);
-      for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAL + kk * 8, kdesc(bh, kk), id_s, 1);
-      for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kdesc(bl, kk), id_s, 1);
-      mma_commit(&sfull[b]);
-      mma_commit(&empty[s]);
+  } else if (warp == 3) {
+    // ------------------------------------------------------------------ message vectors
+    // cb[k'] = (beta_i[k'] - max beta_i - |z~_i^{k'}|^2 / (2 var)) log2(e), -inf past K; c_i.
+    int it = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; ok && item < ntiles; item += gridDim.x, ++it) {
+      const Tile t = tiles[item];
+      const NodeInfo nd = D.nodes[t.node];
+      const int K = nd.K, nch = tiles_of(K);
+      const int ib = it % ncb;
+      if (it >= ncb && !mbar_wait_ab(&cb_empty[ib], (uint32_t)(((it / ncb) - 1) & 1), abort)) { ok = false; break; }
+      // every child of the edge's child node must have sent its message (all its tiles)
+      bool dep_ok = true;
+      if (lane == 0)
+        for (int c = nd.child_begin; c < nd.child_end; ++c) {
+          const int cg = D.children[c];
+          dep_ok = wait_count(done + cg, tiles_of(D.nodes[cg].K)) && dep_ok;
+        }
+      dep_ok = __shfl_sync(0xffffffffu, dep_ok, 0);
+      __syncwarp();  // lane 0's acquire of the counters orders the other lanes' reads below
+      if (!dep_ok) { *abort = 1; ok = false; break; }
+      float* cb = cbuf + (size_t)ib * cbk;
+      // pass 1: beta = u + sum of the children's messages (into cb), and its maximum
+      float mx = -INFINITY;
+      for (int j0 = 0; j0 < K; j0 += 32 * 4) {
+        float bv[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const int j = j0 + x * 32 + lane;
+          bv[x] = j < K ? __ldg(D.u + nd.off_nk + j) : 0.f;
+        }
+        for (int c = nd.child_begin; c < nd.child_end; ++c) {
+          const long long co = D.nodes[D.children[c]].off_nk;
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            const int j = j0 + x * 32 + lane;
+            if (j < K) bv[x] += __ldcg(D.lam + co + j);  // written by other CTAs of this launch
+          }
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const int j = j0 + x * 32 + lane;
+          if (j < K) {
+            cb[j] = bv[x];
+            mx = fmaxf(mx, bv[x]);
+          }
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      // pass 2: normalise, fold in the row term, pad to whole chunks
+      const bool store = (t.row0 == 0);
+      for (int j0 = 0; j0 < nch * kRows; j0 += 32 * 4) {
+        float zv[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const int j = j0 + x * 32 + lane;
+          zv[x] = j < K ? __ldg(D.zn + nd.off_nk + j) : 0.f;
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const int j = j0 + x * 32 + lane;
+          if (j < K) {
+            const float bb = cb[j] - mx;
+            if (store) D.beta[nd.off_nk + j] = bb;
+            cb[j] = (bb - 0.5f * zv[x] * iv) * kLog2e;
+          } else if (j < nch * kRows) {
+            cb[j] = -INFINITY;
+          }
+        }
+      }
+      if (store && lane == 0) D.nodemax[t.node] = mx;
+      for (int j = lane; j < kTcMaxD; j += 32) cvb[ib][j] = __ldg(T.cvec + (long long)t.node * kLdp + j);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&cb_full[ib]);  // release: cb / c_i visible to the math warps
     }
     if (!ok) set_timeout(D);
-    mma_commit(&bar_done);
-    mbar_wait(&bar_done, 0);
   } else if (warp >= 4) {
     // ------------------------------------------------------------------ exponentials
     const int mt = threadIdx.x - 128;
     const int qd = warp & 3, h = (warp - 4) >> 2;
-    const int r = 32 * qd + lane;               // tile row = TMEM lane
+    const int r = 32 * qd + lane;  // tile row = TMEM lane
     const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
-    const int k = t.row0 + r;
-    // beta_i over all K child samples: every load of this thread is issued before any use
-    // (the prologue is latency-bound otherwise); child message offsets are read once.
-    float bv[kJt], zv[kJt];
-#pragma unroll
-    for (int i = 0; i < kJt; ++i) {
-      const int j = mt + i * kMath;
-      const bool in = j < K;
-      bv[i] = in ? D.u[nd.off_nk + j] : 0.f;
-      zv[i] = in ? D.zn[nd.off_nk + j] : 0.f;
-    }
-    for (int c = nd.child_begin; c < nd.child_end; ++c) {
-      const long long co = D.nodes[D.children[c]].off_nk;
-#pragma unroll
-      for (int i = 0; i < kJt; ++i) {
-        const int j = mt + i * kMath;
-        if (j < K) bv[i] += __ldcg(D.lam + co + j);  // written by other CTAs of this launch
-      }
-    }
-    float mx = -INFINITY;
-#pragma unroll
-    for (int i = 0; i < kJt; ++i)
-      if (mt + i * kMath < K) mx = fmaxf(mx, bv[i]);
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) red[warp - 4] = mx;
-    for (int j = mt; j < kLdp; j += kMath) cv[j] = T.cvec[(long long)t.node * kLdp + j];
-    sync_math();
-    mx = red[0];
-#pragma unroll
-    for (int i = 1; i < 8; ++i) mx = fmaxf(mx, red[i]);
-    const bool store = (t.row0 == 0);
-#pragma unroll
-    for (int i = 0; i < kJt; ++i) {
-      const int j = mt + i * kMath;
-      if (j >= nch * kRows) break;
-      if (j < K) {
-        const float bb = bv[i] - mx;
-        if (store) D.beta[nd.off_nk + j] = bb;
-        cb[j] = (bb - 0.5f * zv[i] * iv) * kLog2e;
-      } else {
-        cb[j] = -INFINITY;
-      }
-    }
-    if (store && mt == 0) D.nodemax[t.node] = mx;
-    // prologue: this half of the mu~ row, its squared norm, split into the A operand
-    bool ok = mbar_wait(&bar_mu, 0);
-    float nrm = 0.f;
-    if (ok) {
-      tc_fence_after();
-#pragma unroll 1
-      for (int gg = 0; gg < GH; ++gg) {
-        const int g = h * GH + gg;
-        uint32_t v[32];
-        tmem_ld32(tMU + lane_off + g * 32, v);
-        tmem_wait_ld();
-        float f[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          f[j] = __uint_as_float(v[j]) + cv[g * 32 + j];
-          nrm = fmaf(f[j], f[j], nrm);
-        }
-        uint32_t hi[16], lo[16];
-        split_pack32(f, hi, lo);
-        tmem_st16(tAH + lane_off + g * 16, hi);
-        tmem_st16(tAL + lane_off + g * 16, lo);
-      }
-      tmem_wait_st();
-      tc_fence_before();
-    }
-    nrm_h[h][r] = nrm;
-    mbar_arrive(&bar_A);
-    sync_math();  // cb and the half norms are complete
-    const float nrm_all = nrm_h[0][r] + nrm_h[1][r];
-    if (h == 0 && ok && k < K) D.mun[nd.off_nk + k] = nrm_all;
     const float sc = iv * kLog2e;
-    float m = -INFINITY, ssum = 0.f;
-    for (int c = 0; ok && c < nch; ++c) {
-      const int b = c & 1;
-      if (!mbar_wait(&sfull[b], (c >> 1) & 1)) { ok = false; break; }
+    // A failed wait leaves `ok` false for this thread: it skips its remaining work of the
+    // item but still reaches every named barrier; after the item's last barrier all math
+    // threads read the shared abort flag and stop together.
+    long long gc = 0;
+    int it = 0;
+    for (int item = blockIdx.x; item < ntiles; item += gridDim.x, ++it) {
+      const Tile t = tiles[item];
+      const NodeInfo nd = D.nodes[t.node];
+      const int K = nd.K, nch = tiles_of(K);
+      const int k = t.row0 + r;
+      const int ib = it % ncb;
+      bool ok = mbar_wait_ab(&cb_full[ib], (uint32_t)((it / ncb) & 1), abort) &&
+                mbar_wait_ab(&mu_full, (uint32_t)(it & 1), abort);
+      const float* cb = cbuf + (size_t)ib * cbk;
+      // prologue: this half of the mu~ row (+ c_i), its squared norm, split into the A operand
       tc_fence_after();
-      uint32_t v[2][32];
-      tmem_ld32(tS[b] + lane_off + 64 * h, v[0]);
-      tmem_ld32(tS[b] + lane_off + 64 * h + 32, v[1]);
-      tmem_wait_ld();
+      float nrm = 0.f;
+      if (ok) {
+#pragma unroll 1
+        for (int gg = 0; gg < GH; ++gg) {
+          const int g = h * GH + gg;
+          uint32_t v[32];
+          tmem_ld32(tMU + lane_off + g * 32, v);
+          tmem_wait_ld();
+          float f[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            f[j] = __uint_as_float(v[j]) + cvb[ib][g * 32 + j];
+            nrm = fmaf(f[j], f[j], nrm);
+          }
+          uint32_t hi[16], lo[16];
+          split_pack32(f, hi, lo);
+          tmem_st16(tAH + lane_off + g * 16, hi);
+          tmem_st16(tAL + lane_off + g * 16, lo);
+        }
+        tmem_wait_st();
+      }
       tc_fence_before();
-      mbar_arrive(&sfree[b]);  // the MMA may overwrite this S buffer now
-      const float* cbc = cb + c * kRows + 64 * h;
+      nrm_h[h][r] = nrm;
+      mbar_arrive(&a_full);
+      sync_math();  // both half norms are complete
+      const float nrm_all = nrm_h[0][r] + nrm_h[1][r];
+      if (ok && h == 0 && k < K) D.mun[nd.off_nk + k] = nrm_all;
+      float m = -INFINITY, ssum = 0.f;
+      for (int c = 0; ok && c < nch; ++c) {
+        const long long gcc = gc + c;
+        const int b = (int)(gcc & 1);
+        if (!mbar_wait_ab(&sfull[b], (uint32_t)((gcc >> 1) & 1), abort)) { ok = false; break; }
+        tc_fence_after();
+        uint32_t v[2][32];
+        tmem_ld32(tS[b] + lane_off + 64 * h, v[0]);
+        tmem_ld32(tS[b] + lane_off + 64 * h + 32, v[1]);
+        tmem_wait_ld();
+        tc_fence_before();
+        mbar_arrive(&sfree[b]);  // the MMA may overwrite this S buffer now
+        const float* cbc = cb + c * kRows + 64 * h;
 #pragma unroll
-      for (int g = 0; g < 2; ++g) {
-        float e[32], gm = -INFINITY;
+        for (int g = 0; g < 2; ++g) {
+          float e[32], gm = -INFINITY;
 #pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-          const float4 c4 = *reinterpret_cast<const float4*>(cbc + g * 32 + j);
-          e[j] = fmaf(__uint_as_float(v[g][j]), sc, c4.x);
-          e[j + 1] = fmaf(__uint_as_float(v[g][j + 1]), sc, c4.y);
-          e[j + 2] = fmaf(__uint_as_float(v[g][j + 2]), sc, c4.z);
-          e[j + 3] = fmaf(__uint_as_float(v[g][j + 3]), sc, c4.w);
-          gm = fmaxf(gm, fmaxf(fmaxf(e[j], e[j + 1]), fmaxf(e[j + 2], e[j + 3])));
-        }
-        if (gm == -INFINITY) continue;  // every column of the group lies past K
-        if (gm > m) {
-          ssum *= ex2_ftz(m - gm);
-          m = gm;
-        }
-        float s0 = 0.f, s1 = 0.f;
+          for (int j = 0; j < 32; j += 4) {
+            const float4 c4 = *reinterpret_cast<const float4*>(cbc + g * 32 + j);
+            e[j] = fmaf(__uint_as_float(v[g][j]), sc, c4.x);
+            e[j + 1] = fmaf(__uint_as_float(v[g][j + 1]), sc, c4.y);
+            e[j + 2] = fmaf(__uint_as_float(v[g][j + 2]), sc, c4.z);
+            e[j + 3] = fmaf(__uint_as_float(v[g][j + 3]), sc, c4.w);
+            gm = fmaxf(gm, fmaxf(fmaxf(e[j], e[j + 1]), fmaxf(e[j + 2], e[j + 3])));
+          }
+          if (gm == -INFINITY) continue;  // every column of the group lies past K
+          if (gm > m) {
+            ssum *= ex2_ftz(m - gm);
+            m = gm;
+          }
+          float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-        for (int j = 0; j < 32; j += 2) {
-          s0 += ex2_ftz(e[j] - m);
-          s1 += ex2_ftz(e[j + 1] - m);
+          for (int j = 0; j < 32; j += 2) {
+            s0 += ex2_ftz(e[j] - m);
+            s1 += ex2_ftz(e[j + 1] - m);
+          }
+          ssum += s0 + s1;
         }
-        ssum += s0 + s1;
+      }
+      gc += nch;
+      m_h[h][r] = m;
+      s_h[h][r] = ssum;
+      mbar_arrive(&cb_empty[ib]);  // cb / c_i of this item are no longer read
+      sync_math();
+      if (ok && h == 0 && k < K) {
+        const float m0 = m_h[0][r], m1 = m_h[1][r];
+        const float M = fmaxf(m0, m1);
+        const float S = s_h[0][r] * ex2_ftz(m0 - M) + (m1 == -INFINITY ? 0.f : s_h[1][r] * ex2_ftz(m1 - M));
+        D.lam[nd.off_nk + k] = (M + log2f(S)) * kLn2 - 0.5f * nrm_all * iv;
+      }
+      __threadfence();  // messages visible device-wide before the completion count moves
+      if (!ok) *abort = 1;
+      sync_math();      // every row's message is out; m_h / s_h / nrm_h free for the next item
+      const bool stop = *abort != 0;  // same value in every math thread (set before the barrier)
+      if (mt == 0 && !stop) {
+        red_release_add(done + t.node, 1);
+        stamp_item_end(D, T, 0, nd.b);
+      }
+      if (stop) {
+        if (mt == 0) set_timeout(D);
+        break;
       }
     }
-    if (!ok) set_timeout(D);
-    m_h[h][r] = m;
-    s_h[h][r] = ssum;
-    sync_math();
-    if (h == 0 && ok && k < K) {
-      const float m0 = m_h[0][r], m1 = m_h[1][r];
-      const float M = fmaxf(m0, m1);
-      const float S = s_h[0][r] * ex2_ftz(m0 - M) + (m1 == -INFINITY ? 0.f : s_h[1][r] * ex2_ftz(m1 - M));
-      D.lam[nd.off_nk + k] = (M + log2f(S)) * kLn2 - 0.5f * nrm_all * iv;
-    }
-    __threadfence();  // messages visible device-wide before the completion count moves
   }
-  // item end: every role is done with this item's barriers, tensor memory and ring
   tc_fence_before();
   __syncthreads();
-  tc_fence_after();
-  if (threadIdx.x == 0) {
-    red_release_add(done + t.node, 1);
-    stamp_item_end(D, T, 0, nd.b);
-  }
-  }  // items
   if (warp == 2) {
     tc_fence_after();
     tmem_dealloc(tb, 512);
@@ -1724,9 +1803,19 @@ bool make_map(CUtensorMap* m, void* ptr, long long rows) {
 
 // Dynamic shared memory, at least half of the SM's: one CTA per SM, so the 512-column TMEM
 // allocation never waits on a co-resident CTA.
+// Dynamic shared memory of the forward kernel: the ring, then one or two cb buffers of the
+// longest K (two when they fit beside the ring: warp 3 then prepares item j + 1's vector
+// while the math warps use item j's).  At least half of the SM's, so one CTA per SM holds
+// the 512-column TMEM allocation.
 template <int DP>
-size_t fwd_smem(int maxK) {
-  const size_t need = 1024 + 3 * 2 * (size_t)(kRows * DP * 2) + 4 * (size_t)(((maxK + kRows - 1) / kRows) * kRows);
+size_t fwd_smem(int maxK, int* ncb_out = nullptr, int* cbk_out = nullptr) {
+  const int cbk = tiles_of(maxK) * kRows;
+  const size_t ring = (size_t)FwdCfg<DP>::NS * 2 * FwdCfg<DP>::TB;
+  const size_t limit = 232448 - 8 * 1024;  // opt-in maximum less a margin for static shared memory
+  const int ncb = (1024 + ring + 2 * (size_t)cbk * 4 <= limit) ? 2 : 1;
+  if (ncb_out) *ncb_out = ncb;
+  if (cbk_out) *cbk_out = cbk;
+  const size_t need = 1024 + ring + (size_t)ncb * cbk * 4;
   return need > 120 * 1024 ? need : 120 * 1024;
 }
 template <int DP>
@@ -2007,10 +2096,16 @@ void launch_edge_fwd(TcWork& w, const Dev& D, cudaStream_t s) {
     const int b = w.it_b[0][c], n = w.it_e[0][c] - b;
     if (!n) continue;
     const int grid = n < w.num_sms ? n : w.num_sms;
-    if (c == 0)
-      k_edge_fwd_tc<64><<<grid, kThreadsTc, fwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH, w.mZL, w.mWH, w.mWL);
-    else
-      k_edge_fwd_tc<128><<<grid, kThreadsTc, fwd_smem<128>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH, w.mZL, w.mWH, w.mWL);
+    int ncb = 1, cbk = 0;
+    if (c == 0) {
+      const size_t sm = fwd_smem<64>(w.maxK, &ncb, &cbk);
+      k_edge_fwd_tc<64><<<grid, kThreadsTc, sm, s>>>(D, w.t, w.d_tiles + b, n, w.t.done, ncb, cbk, w.mZH, w.mZL,
+                                                      w.mWH, w.mWL);
+    } else {
+      const size_t sm = fwd_smem<128>(w.maxK, &ncb, &cbk);
+      k_edge_fwd_tc<128><<<grid, kThreadsTc, sm, s>>>(D, w.t, w.d_tiles + b, n, w.t.done, ncb, cbk, w.mZH, w.mZL,
+                                                       w.mWH, w.mWL);
+    }
   }
 }
 
