@@ -153,19 +153,6 @@ __device__ __forceinline__ void stamp_item_end(const Dev& D, TcDev& T, int dir, 
     T.inst_t[(long long)dir * D.num_inst + b] = global_ns();
 }
 
-// dst[0..n) += v[0..n) for n <= 32 (16-byte vector reductions where the row is complete).
-__device__ __forceinline__ void red_add_row32(float* dst, const uint32_t (&v)[32], int n) {
-  if (n >= 32) {
-#pragma unroll
-    for (int j = 0; j < 32; j += 4)
-      asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + j), "f"(__uint_as_float(v[j])),
-                   "f"(__uint_as_float(v[j + 1])), "f"(__uint_as_float(v[j + 2])), "f"(__uint_as_float(v[j + 3]))
-                   : "memory");
-  } else {
-    for (int j = 0; j < n; ++j) atomicAdd(dst + j, __uint_as_float(v[j]));
-  }
-}
-
 // Bytes of the streaming ring: two stages of (hi, lo) sample tiles, and large enough for the
 // adjoint epilogue (Z~ hi, ones atom, Z~ lo, q z~ tile of two atoms).
 __host__ __device__ constexpr int ring_bytes(int DP) {
@@ -1003,7 +990,8 @@ template <int DP>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     k_edge_bwd_tc(Dev D, TcDev T, const Tile* __restrict__ tiles, int ntiles, int* __restrict__ done,
                   const __grid_constant__ CUtensorMap mZH, const __grid_constant__ CUtensorMap mZL,
-                  const __grid_constant__ CUtensorMap mWTH, const __grid_constant__ CUtensorMap mWTL) {
+                  const __grid_constant__ CUtensorMap mWTH, const __grid_constant__ CUtensorMap mWTL,
+                  const __grid_constant__ CUtensorMap mG, const __grid_constant__ CUtensorMap mM2) {
   constexpr int TB = kRows * DP * 2;
   constexpr int NB = DP / 64;
   constexpr int KS = DP / 16;
@@ -1325,29 +1313,49 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     }
     mbar_arrive(&bar_eready);
     if (ok) ok = mbar_wait(&bar_gm, 0);
+    // The tile's G / M2 partials go to global memory as TMA reductions (the L2 adds whole
+    // lines): TMEM -> 128B-swizzled [128 x 32] fp32 boxes in the (now free) ring -> one
+    // cp.reduce.async.bulk.tensor per box.  Rows / columns past d are zero (padding of z~).
+    unsigned char* eG = ring;                        // DP / 32 boxes of 16 KB
+    unsigned char* eM = ring + (DP / 32) * kBox;     // DP / 32 boxes of 16 KB
     if (ok) {
       tc_fence_after();
       const int a = r;  // TMEM lane = output row a
-      const bool arow = a < d;
-      float* Gi = T.G + (long long)t.node * kLdp * kLdp + (long long)a * kLdp;
-      float* Mi = T.M2 + (long long)t.node * kLdp * kLdp + (long long)a * kLdp;
 #pragma unroll 1
       for (int gg = 0; gg < GH; ++gg) {
-        const int g = h * GH + gg;
+        const int g = h * GH + gg;  // 32-column box
         uint32_t v[32];
         tmem_ld32(tG + lane_off + g * 32, v);
         tmem_wait_ld();
-        if (arow) red_add_row32(Gi + g * 32, v, d - g * 32);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<uint4*>(eG + g * kBox + sw128_offset(a, q)) =
+              make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         tmem_ld32(tM2 + lane_off + g * 32, v);
         tmem_wait_ld();
-        if (arow) red_add_row32(Mi + g * 32, v, d - g * 32);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<uint4*>(eM + g * kBox + sw128_offset(a, q)) =
+              make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       }
       if (h == 0) {
         uint32_t v[32];
         tmem_ld32(tM2 + lane_off + DP, v);  // column DP: sum_k' q z~[k'][a]
         tmem_wait_ld();
-        if (arow) atomicAdd(T.zbar + (long long)t.node * kLdp + a, __uint_as_float(v[0]));
+        if (a < d) atomicAdd(T.zbar + (long long)t.node * kLdp + a, __uint_as_float(v[0]));
       }
+      fence_proxy_async_smem();
+    }
+    tc_fence_before();
+    sync_math();  // the boxes are complete
+    if (ok && mt == 0) {
+      const int y = t.node * kLdp;
+      for (int g = 0; g < DP / 32; ++g) {
+        tma_reduce_add_2d(&mG, eG + g * kBox, g * 32, y);
+        tma_reduce_add_2d(&mM2, eM + g * kBox, g * 32, y);
+      }
+      bulk_commit_group();
+      bulk_wait_group_read0();  // the ring is reused by the next item
     }
     if (!ok) set_timeout(D);
   }
@@ -1789,6 +1797,19 @@ EncodeFn encode_fn() {
 }
 
 // [rows][128] fp16 array, box 64 columns x 128 rows, 128-byte swizzle.
+// [rows][128] fp32 array, box 32 columns x 128 rows, 128-byte swizzle (the G / M2 reductions).
+bool make_map_f32(CUtensorMap* m, void* ptr, long long rows) {
+  EncodeFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kLdp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kLdp * 4};
+  cuuint32_t box[2] = {32, (cuuint32_t)kRows};
+  cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptr, dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool make_map(CUtensorMap* m, void* ptr, long long rows) {
   EncodeFn enc = encode_fn();
   if (!enc) return false;
@@ -1942,7 +1963,9 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
       !make_map(&w.mWL, w.t.WL, (long long)w.num_slots * kLdp) ||
       !make_map(&w.mWTH, w.t.WTH, (long long)w.num_slots * kLdp) ||
       !make_map(&w.mWTL, w.t.WTL, (long long)w.num_slots * kLdp) ||
-      !make_map(&w.mCH, w.t.CH, w.c_rows) || !make_map(&w.mCL, w.t.CL, w.c_rows))
+      !make_map(&w.mCH, w.t.CH, w.c_rows) || !make_map(&w.mCL, w.t.CL, w.c_rows) ||
+      !make_map_f32(&w.mG, w.t.G, (long long)w.num_nodes * kLdp) ||
+      !make_map_f32(&w.mM2, w.t.M2, (long long)w.num_nodes * kLdp))
     return TMC_ERR_CUDA;
   {  // observation matrices' first rows, and the leaf tiles of the observation kernel
     std::vector<int> crow(w.num_c, 0);
@@ -2122,9 +2145,11 @@ void launch_edge_bwd(TcWork& w, const Dev& D, cudaStream_t s) {
     if (!n) continue;
     const int grid = n < w.num_sms ? n : w.num_sms;
     if (c == 0)
-      k_edge_bwd_tc<64><<<grid, kThreadsTc, bwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH, w.mZL, w.mWTH, w.mWTL);
+      k_edge_bwd_tc<64><<<grid, kThreadsTc, bwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH, w.mZL,
+                                                                     w.mWTH, w.mWTL, w.mG, w.mM2);
     else
-      k_edge_bwd_tc<128><<<grid, kThreadsTc, bwd_smem<128>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH, w.mZL, w.mWTH, w.mWTL);
+      k_edge_bwd_tc<128><<<grid, kThreadsTc, bwd_smem<128>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH,
+                                                                       w.mZL, w.mWTH, w.mWTL, w.mG, w.mM2);
   }
 }
 

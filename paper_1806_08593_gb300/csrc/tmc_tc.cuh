@@ -76,6 +76,7 @@ struct TcWork {
   long long c_rows = 0;
   int num_c = 0;                  // distinct observation matrices (1 when shared)
   CUtensorMap mCH, mCL;
+  CUtensorMap mG, mM2;            // fp32 [nodes*128][128] views of G / M2 for TMA reductions
   std::vector<Tile> obs_tiles;
   int ob_b[2] = {0, 0}, ob_e[2] = {0, 0};
   Tile* d_obs_tiles = nullptr;
