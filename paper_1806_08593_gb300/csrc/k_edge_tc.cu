@@ -635,6 +635,10 @@ struct FwdCfg {
   static constexpr int NS = DP == 64 ? 6 : 3;  // ring stages of (hi, lo) tiles
 };
 
+// Chunk of an item before which the next item's prologue operands and mu~ MMAs are placed
+// in the ring / MMA order: two chunks before the end, so they overlap this item's tail.
+__host__ __device__ constexpr int pro_slot(int nch) { return nch >= 2 ? nch - 2 : 0; }
+
 // Bounded wait that also gives up as soon as another role of the CTA has given up.
 __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort) {
   if (mbar_try_wait(bar, parity)) return true;
@@ -662,9 +666,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   __shared__ uint64_t full[NS], empty[NS], sfull[2], sfree[2], mu_full, a_full, cb_full[2], cb_empty[2],
       bar_done;
   __shared__ uint32_t tbase;
-  __shared__ int s_abort;
+  __shared__ int s_abort, s_early;
   __shared__ __align__(16) float cvb[2][kTcMaxD];
-  __shared__ float nrm_h[2][kRows], m_h[2][kRows], s_h[2][kRows];
+  __shared__ float nrm_h[2][2][kRows], m_h[2][kRows], s_h[2][kRows];
   volatile int* abort = &s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -703,11 +707,33 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       prefetch_tmap(&mWL);
       long long gu = 0;  // ring uses issued
       bool ok = true;
+      // one ring use: wait for the stage, then load a (hi, lo) pair of [128 x DP] tiles
+      auto load_use = [&](const CUtensorMap* mh, const CUtensorMap* ml, int row) -> bool {
+        const int s = (int)(gu % NS);
+        const long long fill = gu / NS;
+        if (fill >= 1 && !mbar_wait_ab(&empty[s], (uint32_t)((fill - 1) & 1), abort)) return false;
+        unsigned char* st = ring + s * 2 * TB;
+        mbar_arrive_expect_tx(&full[s], 2 * TB);
+        for (int b = 0; b < NB; ++b) {
+          tma_load_2d(st + b * kBox, mh, &full[s], b * 64, row);
+          tma_load_2d(st + TB + b * kBox, ml, &full[s], b * 64, row);
+        }
+        ++gu;
+        return true;
+      };
+      // an item's prologue operands: its Z~_p tile and W_i
+      auto load_pro = [&](int item) -> bool {
+        const Tile t = tiles[item];
+        const NodeInfo nd = D.nodes[t.node];
+        return load_use(&mZH, &mZL, (int)(D.nodes[nd.parent].off_nk + t.row0)) &&
+               load_use(&mWH, &mWL, slot_of(D, nd, t.node) * kLdp);
+      };
+      if (blockIdx.x < ntiles) ok = load_pro(blockIdx.x);
       for (int item = blockIdx.x; ok && item < ntiles; item += gridDim.x) {
         const Tile t = tiles[item];
         const NodeInfo nd = D.nodes[t.node];
-        const NodeInfo pn = D.nodes[nd.parent];
         const int nch = tiles_of(nd.K);
+        const int nxt = item + (int)gridDim.x;
         if (item == (int)blockIdx.x) stamp_item_start(T, 0, item);
         // the 8 row tiles of an edge walk the child's chunks in the same order; each pulls
         // "its" chunk (index = its row tile) into L2 up front
@@ -715,22 +741,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           tma_prefetch_l2_2d(&mZH, b * 64, (int)(nd.off_nk + t.row0));
           tma_prefetch_l2_2d(&mZL, b * 64, (int)(nd.off_nk + t.row0));
         }
-        const int slot = slot_of(D, nd, t.node);
-        for (int u = 0; ok && u < nch + 2; ++u, ++gu) {
-          const int s = (int)(gu % NS);
-          const long long fill = gu / NS;
-          if (fill >= 1 && !mbar_wait_ab(&empty[s], (uint32_t)((fill - 1) & 1), abort)) { ok = false; break; }
-          unsigned char* st = ring + s * 2 * TB;
-          mbar_arrive_expect_tx(&full[s], 2 * TB);
-          int x_map_row;
-          const CUtensorMap *mh, *ml;
-          if (u == 0) { mh = &mZH; ml = &mZL; x_map_row = (int)(pn.off_nk + t.row0); }          // Z~_p tile
-          else if (u == 1) { mh = &mWH; ml = &mWL; x_map_row = slot * kLdp; }                  // W_i
-          else { mh = &mZH; ml = &mZL; x_map_row = (int)(nd.off_nk + (u - 2) * kRows); }      // chunk u - 2
-          for (int b = 0; b < NB; ++b) {
-            tma_load_2d(st + b * kBox, mh, &full[s], b * 64, x_map_row);
-            tma_load_2d(st + TB + b * kBox, ml, &full[s], b * 64, x_map_row);
-          }
+        for (int c = 0; ok && c < nch; ++c) {
+          if (c == pro_slot(nch) && nxt < ntiles) ok = load_pro(nxt);
+          ok = ok && load_use(&mZH, &mZL, (int)(nd.off_nk + c * kRows));
         }
       }
       if (!ok) set_timeout(D);
@@ -746,27 +759,34 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       long long gu = 0, gc = 0;
       int it = 0;
       bool ok = true;
-      for (int item = blockIdx.x; ok && item < ntiles; item += gridDim.x, ++it) {
-        const NodeInfo nd = D.nodes[tiles[item].node];
-        const int nch = tiles_of(nd.K);
-        // prologue: mu~ = Z~_p W_i^T (split products) into MU; MU is free once the math warps
-        // have split the previous item's mu~ (a_full of the previous item, waited below)
+      // mu~ = Z~_p W_i^T (split products) from the next two ring uses into MU
+      auto mu_mmas = [&]() -> bool {
         const int sz = (int)(gu % NS), sw = (int)((gu + 1) % NS);
         if (!mbar_wait_ab(&full[sz], (uint32_t)((gu / NS) & 1), abort) ||
-            !mbar_wait_ab(&full[sw], (uint32_t)(((gu + 1) / NS) & 1), abort)) { ok = false; break; }
+            !mbar_wait_ab(&full[sw], (uint32_t)(((gu + 1) / NS) & 1), abort))
+          return false;
         tc_fence_after();
-        {
-          unsigned char *zh = ring + sz * 2 * TB, *zl = zh + TB, *wh = ring + sw * 2 * TB, *wl = wh + TB;
-          for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zh, kk), kdesc(wh, kk), id_mu, kk > 0);
-          for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zl, kk), kdesc(wh, kk), id_mu, 1);
-          for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zh, kk), kdesc(wl, kk), id_mu, 1);
-        }
+        unsigned char *zh = ring + sz * 2 * TB, *zl = zh + TB, *wh = ring + sw * 2 * TB, *wl = wh + TB;
+        for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zh, kk), kdesc(wh, kk), id_mu, kk > 0);
+        for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zl, kk), kdesc(wh, kk), id_mu, 1);
+        for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zh, kk), kdesc(wl, kk), id_mu, 1);
         mma_commit(&mu_full);
         mma_commit(&empty[sz]);
         mma_commit(&empty[sw]);
         gu += 2;
+        return true;
+      };
+      if (blockIdx.x < ntiles) ok = mu_mmas();
+      for (int item = blockIdx.x; ok && item < ntiles; item += gridDim.x, ++it) {
+        const NodeInfo nd = D.nodes[tiles[item].node];
+        const int nch = tiles_of(nd.K);
+        const bool has_next = item + (int)gridDim.x < ntiles;
+        // A of this item written by the math warps (they have also read MU, so the next
+        // item's mu~ may go there)
         if (!mbar_wait_ab(&a_full, (uint32_t)(it & 1), abort)) { ok = false; break; }
         for (int c = 0; c < nch; ++c, ++gu, ++gc) {
+          // the next item's mu~ between this item's chunks, where the tensor pipe has room
+          if (c == pro_slot(nch) && has_next && !mu_mmas()) { ok = false; break; }
           const int s = (int)(gu % NS), b = (int)(gc & 1);
           if (!mbar_wait_ab(&full[s], (uint32_t)((gu / NS) & 1), abort)) { ok = false; break; }
           if (gc >= 2 && !mbar_wait_ab(&sfree[b], (uint32_t)(((gc >> 1) + 1) & 1), abort)) { ok = false; break; }
@@ -870,18 +890,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     // A failed wait leaves `ok` false for this thread: it skips its remaining work of the
     // item but still reaches every named barrier; after the item's last barrier all math
     // threads read the shared abort flag and stop together.
-    long long gc = 0;
-    int it = 0;
-    for (int item = blockIdx.x; item < ntiles; item += gridDim.x, ++it) {
-      const Tile t = tiles[item];
-      const NodeInfo nd = D.nodes[t.node];
-      const int K = nd.K, nch = tiles_of(K);
-      const int k = t.row0 + r;
-      const int ib = it % ncb;
-      bool ok = mbar_wait_ab(&cb_full[ib], (uint32_t)((it / ncb) & 1), abort) &&
-                mbar_wait_ab(&mu_full, (uint32_t)(it & 1), abort);
-      const float* cb = cbuf + (size_t)ib * cbk;
-      // prologue: this half of the mu~ row (+ c_i), its squared norm, split into the A operand
+    // Per item: the chunk loop, then (as soon as the last S has been read, so every MMA of
+    // the item is complete) the next item's mu~ is split into A and a_full released, and only
+    // then this item's messages are combined and published.
+    bool ok = true;
+    // mu~ of item `it` (+ c_i) -> A operand halves; its squared norm into nrm_h[it & 1]
+    auto split = [&](int it_s) {
+      const int ibs = it_s % ncb;
+      ok = ok && mbar_wait_ab(&cb_full[ibs], (uint32_t)((it_s / ncb) & 1), abort) &&
+           mbar_wait_ab(&mu_full, (uint32_t)(it_s & 1), abort);
       tc_fence_after();
       float nrm = 0.f;
       if (ok) {
@@ -894,7 +911,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           float f[32];
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            f[j] = __uint_as_float(v[j]) + cvb[ib][g * 32 + j];
+            f[j] = __uint_as_float(v[j]) + cvb[ibs][g * 32 + j];
             nrm = fmaf(f[j], f[j], nrm);
           }
           uint32_t hi[16], lo[16];
@@ -905,10 +922,21 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         tmem_wait_st();
       }
       tc_fence_before();
-      nrm_h[h][r] = nrm;
+      nrm_h[it_s & 1][h][r] = nrm;
       mbar_arrive(&a_full);
-      sync_math();  // both half norms are complete
-      const float nrm_all = nrm_h[0][r] + nrm_h[1][r];
+    };
+    long long gc = 0;
+    int it = 0;
+    if (blockIdx.x < ntiles) split(0);
+    for (int item = blockIdx.x; item < ntiles; item += gridDim.x, ++it) {
+      const Tile t = tiles[item];
+      const NodeInfo nd = D.nodes[t.node];
+      const int K = nd.K, nch = tiles_of(K);
+      const int k = t.row0 + r;
+      const int ib = it % ncb;
+      const float* cb = cbuf + (size_t)ib * cbk;
+      sync_math();  // both half norms of this item are complete
+      const float nrm_all = nrm_h[it & 1][0][r] + nrm_h[it & 1][1][r];
       if (ok && h == 0 && k < K) D.mun[nd.off_nk + k] = nrm_all;
       float m = -INFINITY, ssum = 0.f;
       for (int c = 0; ok && c < nch; ++c) {
@@ -950,21 +978,29 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         }
       }
       gc += nch;
+      mbar_arrive(&cb_empty[ib]);  // cb of this item is no longer read (c_i was read by its split)
       m_h[h][r] = m;
       s_h[h][r] = ssum;
-      mbar_arrive(&cb_empty[ib]);  // cb / c_i of this item are no longer read
-      sync_math();
+      // The next item's split may run before this item's messages are published only when its
+      // message vector is already prepared (warp 3 has passed its dependency wait); otherwise the
+      // next item may depend on this one, and the split waits until after the release below.
+      const bool has_next = item + (int)gridDim.x < ntiles;
+      if (mt == 0)
+        s_early = has_next && mbar_try_wait(&cb_full[(it + 1) % ncb], (uint32_t)(((it + 1) / ncb) & 1));
+      sync_math();  // m_h / s_h complete, s_early published
+      const bool early = s_early != 0;
+      if (early) split(it + 1);
       if (ok && h == 0 && k < K) {
         const float m0 = m_h[0][r], m1 = m_h[1][r];
         const float M = fmaxf(m0, m1);
         const float S = s_h[0][r] * ex2_ftz(m0 - M) + (m1 == -INFINITY ? 0.f : s_h[1][r] * ex2_ftz(m1 - M));
         D.lam[nd.off_nk + k] = (M + log2f(S)) * kLn2 - 0.5f * nrm_all * iv;
       }
-      __threadfence();  // messages visible device-wide before the completion count moves
       if (!ok) *abort = 1;
-      sync_math();      // every row's message is out; m_h / s_h / nrm_h free for the next item
+      sync_math();  // every row's message is written; m_h / s_h free for the next item
       const bool stop = *abort != 0;  // same value in every math thread (set before the barrier)
       if (mt == 0 && !stop) {
+        __threadfence();  // the CTA's messages visible device-wide before the count moves
         red_release_add(done + t.node, 1);
         stamp_item_end(D, T, 0, nd.b);
       }
@@ -972,6 +1008,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         if (mt == 0) set_timeout(D);
         break;
       }
+      if (has_next && !early) split(it + 1);
     }
   }
   tc_fence_before();
@@ -998,8 +1035,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   constexpr int GH = DP / 64;
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sAL = sm;            // lo part of A' = Z~_i W_i (K-major); hi part is in TMEM
-  unsigned char* ring = sm + TB;      // 2 stages x (hi, lo) of parent sample chunks
+  unsigned char* ring = sm;           // 2 stages x (hi, lo) of parent sample chunks
   float* ak = reinterpret_cast<float*>(ring + ring_bytes(DP));
   // epilogue re-use of the ring / A regions
   unsigned char* eZH = ring;                 // Z~_i tile hi  (N atoms at +0, +16K)
@@ -1007,7 +1043,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   unsigned char* eZL = ring + TB + kBox;     // Z~_i tile lo
   unsigned char* eQZ = ring + 2 * TB + kBox; // q z~ tile (A of M2, 2 atoms)
   unsigned char* eSV = ring + 2 * TB + 3 * kBox;  // V tile (A of G, 2 atoms)
-  __shared__ uint64_t bar_pro, bar_mu, bar_A, full[2], empty[2], sfull[2], sfree[2], pready[2], pfree[2];
+  __shared__ uint64_t bar_pro, bar_mu, bar_A, full[2], empty[2], sfull[2], pready;
   __shared__ uint64_t bar_v, bar_etma, bar_eready, bar_gm;
   __shared__ uint32_t tbase;
   __shared__ float q_h[2][kRows];
@@ -1019,8 +1055,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tb = tbase;
-  // TMEM: S double buffer [0,256), V [256,384), A'_hi [384,448), P (fp16 pairs) [448,512)
-  const uint32_t tS[2] = {tb, tb + 128}, tV = tb + 256, tAH = tb + 384, tP = tb + 448;
+  // TMEM: S double buffer [0,256), V [256,384), A'_hi [384,448), A'_lo [448,512).  P of a chunk
+  // (fp16 pairs) overwrites the S buffer it came from: the math thread of (row, half h) reads
+  // S columns [64h, 64h+64) and writes its P pairs to [64h, 64h+32), so no thread overwrites
+  // columns another thread still has to read; the MMA warp issues V(c) before S(c+2) into the
+  // same buffer, and tcgen05 MMAs of one thread run in issue order.
+  const uint32_t tS[2] = {tb, tb + 128}, tV = tb + 256, tAH = tb + 384, tAL = tb + 448;
   const uint32_t tG = tb, tM2 = tb + 128;
 
   // persistent loop over the edge tiles of every level, root side first
@@ -1044,10 +1084,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
       mbar_init(&sfull[i], 1);
-      mbar_init(&sfree[i], kMath);
-      mbar_init(&pready[i], kMath);
-      mbar_init(&pfree[i], 1);
     }
+    mbar_init(&pready, kMath);
     fence_barrier_init();
   }
   tc_fence_before();
@@ -1125,24 +1163,23 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       if (c < nch) {
         const int s = c & 1, b = c & 1;
         if (!mbar_wait(&full[s], (c >> 1) & 1)) { ok = false; break; }
-        if (c >= 2 && !mbar_wait(&sfree[b], ((c >> 1) + 1) & 1)) { ok = false; break; }
         tc_fence_after();
         unsigned char *bh = ring + s * 2 * TB, *bl = bh + TB;
         for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kdesc(bh, kk), id_s, kk > 0);
-        for (int kk = 0; kk < KS; ++kk) mma_ss(tS[b], kdesc(sAL, kk), kdesc(bh, kk), id_s, 1);
+        for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAL + kk * 8, kdesc(bh, kk), id_s, 1);
         for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kdesc(bl, kk), id_s, 1);
         mma_commit(&sfull[b]);
       }
       if (c >= 1) {
         const int cp = c - 1, s = cp & 1;
-        if (!mbar_wait(&pready[0], cp & 1)) { ok = false; break; }
+        if (!mbar_wait(&pready, cp & 1)) { ok = false; break; }
         tc_fence_after();
         unsigned char* bh = ring + s * 2 * TB;
-        // V[k'][:] += sum_k P[k'][k] z~_p^k   (P: fp16 pairs in tensor memory)
+        // V[k'][:] += sum_k P[k'][k] z~_p^k   (P: fp16 pairs in S buffer cp & 1, K-steps 0..3
+        // at columns 0.., K-steps 4..7 at columns 64..)
         for (int kk = 0; kk < kRows / 16; ++kk)
-          mma_ts(tV, tP + kk * 8, mndesc(bh, kk), id_v, (cp > 0 || kk > 0) ? 1u : 0u);
+          mma_ts(tV, tS[s] + (kk >> 2) * 64 + (kk & 3) * 8, mndesc(bh, kk), id_v, (cp > 0 || kk > 0) ? 1u : 0u);
         mma_commit(&empty[s]);
-        mma_commit(&pfree[0]);
       }
     }
     mma_commit(&bar_v);
@@ -1209,13 +1246,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         uint32_t hi[16], lo[16];
         split_pack32(f, hi, lo);
         tmem_st16(tAH + lane_off + g * 16, hi);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          *reinterpret_cast<uint4*>(sAL + (uint32_t)((g * 4 + q) >> 3) * kBox + sw128_offset(r, (g * 4 + q) & 7)) =
-              make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
+        tmem_st16(tAL + lane_off + g * 16, lo);
       }
       tmem_wait_st();
-      fence_proxy_async_smem();
       tc_fence_before();
     }
     mbar_arrive(&bar_A);
@@ -1230,8 +1263,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       tmem_ld32(tS[b] + lane_off + 64 * h, v[0]);
       tmem_ld32(tS[b] + lane_off + 64 * h + 32, v[1]);
       tmem_wait_ld();
-      tc_fence_before();
-      mbar_arrive(&sfree[b]);
       const float* akc = ak + c * kRows + 64 * h;
       uint32_t pk[32];
       float s0 = 0.f, s1 = 0.f;
@@ -1251,12 +1282,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         }
       }
       qacc += s0 + s1;
-      if (c >= 1 && !mbar_wait(&pfree[0], (c - 1) & 1)) { ok = false; break; }
-      tc_fence_after();
-      tmem_st32(tP + lane_off + 32 * h, pk);
+      tmem_st32(tS[b] + lane_off + 64 * h, pk);  // P over this thread's own S columns
       tmem_wait_st();
       tc_fence_before();
-      mbar_arrive(&pready[0]);
+      mbar_arrive(&pready);
     }
     q_h[h][r] = qacc;
     sync_math();
@@ -1845,7 +1874,7 @@ size_t obs_smem() {
 }
 template <int DP>
 size_t bwd_smem(int maxK) {
-  const size_t need = 1024 + (size_t)(kRows * DP * 2) + ring_bytes(DP) +
+  const size_t need = 1024 + ring_bytes(DP) +
                       4 * (size_t)(((maxK + kRows - 1) / kRows) * kRows);
   return need > 120 * 1024 ? need : 120 * 1024;
 }
