@@ -613,10 +613,11 @@ __global__ void __launch_bounds__(128) k_obs_tc(Dev D, TcDev T, const Tile* __re
 
 // =======================================================================================
 // Forward edge kernel, pipelined across the CTA's items.
-// Roles: warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs, warp 2 owns the TMEM
-// allocation, warp 3 prepares the next item's message vector (dependency wait, beta_i, its
-// maximum, c_i), warps 4..11 run the exponentials (warp w serves TMEM lanes 32*(w%4).. and half
-// h = (w-4)/4 of the columns of every S chunk and of the latent dimension in the prologue).
+// Roles: warp 0 lane 0 issues TMA; warp 1 lane 0 issues MMAs; warp 2 owns the TMEM
+// allocation; warp 3 prepares the next item's message vector (dependency
+// wait, beta_i, its maximum, c_i); warps 4..11 run the exponentials in two groups: group h =
+// (w-4)/4 takes the chunks in S buffer h (warp w serves TMEM lanes 32*(w%4)..) and half h of
+// the latent dimension in the prologue split.
 // The barriers are initialised once; every role walks the same item sequence and derives the
 // phase of each barrier from running counters:
 //   ring uses   : per item [Z~_p tile, W_i, chunk 0 .. chunk nch-1], stage = use % NS
@@ -641,7 +642,7 @@ __host__ __device__ constexpr int pro_slot(int nch) { return nch >= 2 ? nch - 2 
 
 // Bounded wait that also gives up as soon as another role of the CTA has given up.
 __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort) {
-  if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_test_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort || clock64() - t0 > (1ll << 31)) {
@@ -681,7 +682,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&sfull[i], 1);
-      mbar_init(&sfree[i], kMath);
+      mbar_init(&sfree[i], kMath / 2);  // the warp group of buffer i
       mbar_init(&cb_full[i], 1);
       mbar_init(&cb_empty[i], kMath);
     }
@@ -939,42 +940,51 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       const float nrm_all = nrm_h[it & 1][0][r] + nrm_h[it & 1][1][r];
       if (ok && h == 0 && k < K) D.mun[nd.off_nk + k] = nrm_all;
       float m = -INFINITY, ssum = 0.f;
+      // the two warp groups take alternate chunks (group h: the chunks in S buffer h), each
+      // thread a whole 128-column row of its chunks, so one group's TMEM loads and
+      // exponentials overlap the other's
       for (int c = 0; ok && c < nch; ++c) {
         const long long gcc = gc + c;
         const int b = (int)(gcc & 1);
+        if (b != h) continue;
         if (!mbar_wait_ab(&sfull[b], (uint32_t)((gcc >> 1) & 1), abort)) { ok = false; break; }
         tc_fence_after();
-        uint32_t v[2][32];
-        tmem_ld32(tS[b] + lane_off + 64 * h, v[0]);
-        tmem_ld32(tS[b] + lane_off + 64 * h + 32, v[1]);
-        tmem_wait_ld();
-        tc_fence_before();
-        mbar_arrive(&sfree[b]);  // the MMA may overwrite this S buffer now
-        const float* cbc = cb + c * kRows + 64 * h;
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
-          float e[32], gm = -INFINITY;
-#pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            const float4 c4 = *reinterpret_cast<const float4*>(cbc + g * 32 + j);
-            e[j] = fmaf(__uint_as_float(v[g][j]), sc, c4.x);
-            e[j + 1] = fmaf(__uint_as_float(v[g][j + 1]), sc, c4.y);
-            e[j + 2] = fmaf(__uint_as_float(v[g][j + 2]), sc, c4.z);
-            e[j + 3] = fmaf(__uint_as_float(v[g][j + 3]), sc, c4.w);
-            gm = fmaxf(gm, fmaxf(fmaxf(e[j], e[j + 1]), fmaxf(e[j + 2], e[j + 3])));
+#pragma unroll 1
+        for (int hh = 0; hh < 2; ++hh) {
+          uint32_t v[2][32];
+          tmem_ld32(tS[b] + lane_off + 64 * hh, v[0]);
+          tmem_ld32(tS[b] + lane_off + 64 * hh + 32, v[1]);
+          tmem_wait_ld();
+          if (hh == 1) {
+            tc_fence_before();
+            mbar_arrive(&sfree[b]);  // the MMA may overwrite this S buffer now
           }
-          if (gm == -INFINITY) continue;  // every column of the group lies past K
-          if (gm > m) {
-            ssum *= ex2_ftz(m - gm);
-            m = gm;
-          }
-          float s0 = 0.f, s1 = 0.f;
+          const float* cbc = cb + c * kRows + 64 * hh;
 #pragma unroll
-          for (int j = 0; j < 32; j += 2) {
-            s0 += ex2_ftz(e[j] - m);
-            s1 += ex2_ftz(e[j + 1] - m);
+          for (int g = 0; g < 2; ++g) {
+            float e[32], gm = -INFINITY;
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              const float4 c4 = *reinterpret_cast<const float4*>(cbc + g * 32 + j);
+              e[j] = fmaf(__uint_as_float(v[g][j]), sc, c4.x);
+              e[j + 1] = fmaf(__uint_as_float(v[g][j + 1]), sc, c4.y);
+              e[j + 2] = fmaf(__uint_as_float(v[g][j + 2]), sc, c4.z);
+              e[j + 3] = fmaf(__uint_as_float(v[g][j + 3]), sc, c4.w);
+              gm = fmaxf(gm, fmaxf(fmaxf(e[j], e[j + 1]), fmaxf(e[j + 2], e[j + 3])));
+            }
+            if (gm == -INFINITY) continue;  // every column of the group lies past K
+            if (gm > m) {
+              ssum *= ex2_ftz(m - gm);
+              m = gm;
+            }
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+              s0 += ex2_ftz(e[j] - m);
+              s1 += ex2_ftz(e[j + 1] - m);
+            }
+            ssum += s0 + s1;
           }
-          ssum += s0 + s1;
         }
       }
       gc += nch;
@@ -1043,7 +1053,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   unsigned char* eZL = ring + TB + kBox;     // Z~_i tile lo
   unsigned char* eQZ = ring + 2 * TB + kBox; // q z~ tile (A of M2, 2 atoms)
   unsigned char* eSV = ring + 2 * TB + 3 * kBox;  // V tile (A of G, 2 atoms)
-  __shared__ uint64_t bar_pro, bar_mu, bar_A, full[2], empty[2], sfull[2], pready;
+  __shared__ uint64_t bar_pro, bar_mu, bar_A, full[2], empty[2], sfull[2], pready[2];
   __shared__ uint64_t bar_v, bar_etma, bar_eready, bar_gm;
   __shared__ uint32_t tbase;
   __shared__ float q_h[2][kRows];
@@ -1055,11 +1065,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tb = tbase;
-  // TMEM: S double buffer [0,256), V [256,384), A'_hi [384,448), A'_lo [448,512).  P of a chunk
-  // (fp16 pairs) overwrites the S buffer it came from: the math thread of (row, half h) reads
-  // S columns [64h, 64h+64) and writes its P pairs to [64h, 64h+32), so no thread overwrites
-  // columns another thread still has to read; the MMA warp issues V(c) before S(c+2) into the
-  // same buffer, and tcgen05 MMAs of one thread run in issue order.
+  // TMEM: S double buffer [0,256), V [256,384), A'_hi [384,448), A'_lo [448,512).  The two math
+  // warp groups take alternate chunks (group h: the chunks in S buffer h), one thread per row.
+  // P of a chunk (fp16 pairs) overwrites the S row it came from: the thread reads S columns
+  // [0,64) and writes P pairs to [0,32), then reads [64,128) and writes [32,64); the MMA warp
+  // issues V(c) before S(c+2) into the same buffer, and tcgen05 MMAs of one thread run in
+  // issue order.
   const uint32_t tS[2] = {tb, tb + 128}, tV = tb + 256, tAH = tb + 384, tAL = tb + 448;
   const uint32_t tG = tb, tM2 = tb + 128;
 
@@ -1085,7 +1096,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       mbar_init(&empty[i], 1);
       mbar_init(&sfull[i], 1);
     }
-    mbar_init(&pready, kMath);
+    mbar_init(&pready[0], kMath / 2);
+    mbar_init(&pready[1], kMath / 2);
     fence_barrier_init();
   }
   tc_fence_before();
@@ -1172,13 +1184,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       }
       if (c >= 1) {
         const int cp = c - 1, s = cp & 1;
-        if (!mbar_wait(&pready, cp & 1)) { ok = false; break; }
+        if (!mbar_wait(&pready[cp & 1], (cp >> 1) & 1)) { ok = false; break; }
         tc_fence_after();
         unsigned char* bh = ring + s * 2 * TB;
-        // V[k'][:] += sum_k P[k'][k] z~_p^k   (P: fp16 pairs in S buffer cp & 1, K-steps 0..3
-        // at columns 0.., K-steps 4..7 at columns 64..)
+        // V[k'][:] += sum_k P[k'][k] z~_p^k   (P: fp16 pairs in columns [0,64) of S buffer cp & 1)
         for (int kk = 0; kk < kRows / 16; ++kk)
-          mma_ts(tV, tS[s] + (kk >> 2) * 64 + (kk & 3) * 8, mndesc(bh, kk), id_v, (cp > 0 || kk > 0) ? 1u : 0u);
+          mma_ts(tV, tS[s] + kk * 8, mndesc(bh, kk), id_v, (cp > 0 || kk > 0) ? 1u : 0u);
         mma_commit(&empty[s]);
       }
     }
@@ -1255,37 +1266,40 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     sync_math();  // ak complete
     const float sc = iv * kLog2e;
     float qacc = 0.f;
-    for (int c = 0; ok && c < nch; ++c) {
+    for (int c = h; ok && c < nch; c += 2) {  // this group's chunks: S buffer h
       const int b = c & 1;
       if (!mbar_wait(&sfull[b], (c >> 1) & 1)) { ok = false; break; }
       tc_fence_after();
-      uint32_t v[2][32];
-      tmem_ld32(tS[b] + lane_off + 64 * h, v[0]);
-      tmem_ld32(tS[b] + lane_off + 64 * h + 32, v[1]);
-      tmem_wait_ld();
-      const float* akc = ak + c * kRows + 64 * h;
-      uint32_t pk[32];
-      float s0 = 0.f, s1 = 0.f;
+#pragma unroll 1
+      for (int hh = 0; hh < 2; ++hh) {
+        uint32_t v[2][32];
+        tmem_ld32(tS[b] + lane_off + 64 * hh, v[0]);
+        tmem_ld32(tS[b] + lane_off + 64 * hh + 32, v[1]);
+        tmem_wait_ld();
+        const float* akc = ak + c * kRows + 64 * hh;
+        uint32_t pk[32];
+        float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-      for (int g = 0; g < 2; ++g) {
+        for (int g = 0; g < 2; ++g) {
 #pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-          const float4 a4 = *reinterpret_cast<const float4*>(akc + g * 32 + j);
-          const float p0 = ex2_ftz(fmaf(__uint_as_float(v[g][j]), sc, crow + a4.x));
-          const float p1 = ex2_ftz(fmaf(__uint_as_float(v[g][j + 1]), sc, crow + a4.y));
-          const float p2 = ex2_ftz(fmaf(__uint_as_float(v[g][j + 2]), sc, crow + a4.z));
-          const float p3 = ex2_ftz(fmaf(__uint_as_float(v[g][j + 3]), sc, crow + a4.w));
-          s0 += p0 + p1;
-          s1 += p2 + p3;
-          pk[g * 16 + j / 2] = pack_half2(p0, p1);
-          pk[g * 16 + j / 2 + 1] = pack_half2(p2, p3);
+          for (int j = 0; j < 32; j += 4) {
+            const float4 a4 = *reinterpret_cast<const float4*>(akc + g * 32 + j);
+            const float p0 = ex2_ftz(fmaf(__uint_as_float(v[g][j]), sc, crow + a4.x));
+            const float p1 = ex2_ftz(fmaf(__uint_as_float(v[g][j + 1]), sc, crow + a4.y));
+            const float p2 = ex2_ftz(fmaf(__uint_as_float(v[g][j + 2]), sc, crow + a4.z));
+            const float p3 = ex2_ftz(fmaf(__uint_as_float(v[g][j + 3]), sc, crow + a4.w));
+            s0 += p0 + p1;
+            s1 += p2 + p3;
+            pk[g * 16 + j / 2] = pack_half2(p0, p1);
+            pk[g * 16 + j / 2 + 1] = pack_half2(p2, p3);
+          }
         }
+        qacc += s0 + s1;
+        tmem_st32(tS[b] + lane_off + 32 * hh, pk);  // P over S columns this thread has read
       }
-      qacc += s0 + s1;
-      tmem_st32(tS[b] + lane_off + 64 * h, pk);  // P over this thread's own S columns
       tmem_wait_st();
       tc_fence_before();
-      mbar_arrive(&pready);
+      mbar_arrive(&pready[b]);
     }
     q_h[h][r] = qacc;
     sync_math();
