@@ -827,25 +827,30 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       __syncwarp();  // lane 0's acquire of the counters orders the other lanes' reads below
       if (!dep_ok) { *abort = 1; ok = false; break; }
       float* cb = cbuf + (size_t)ib * cbk;
-      // pass 1: beta = u + sum of the children's messages (into cb), and its maximum
+      // pass 1: beta = u + sum of the children's messages (into cb), and its maximum; 32
+      // values per lane per batch, every load of a batch issued before the first use
+      constexpr int kB = 32;
       float mx = -INFINITY;
-      for (int j0 = 0; j0 < K; j0 += 32 * 4) {
-        float bv[4];
+      for (int j0 = 0; j0 < K; j0 += 32 * kB) {
+        float bv[kB];
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
+        for (int x = 0; x < kB; ++x) {
           const int j = j0 + x * 32 + lane;
           bv[x] = j < K ? __ldg(D.u + nd.off_nk + j) : 0.f;
         }
         for (int c = nd.child_begin; c < nd.child_end; ++c) {
           const long long co = D.nodes[D.children[c]].off_nk;
+          float lv[kB];
 #pragma unroll
-          for (int x = 0; x < 4; ++x) {
+          for (int x = 0; x < kB; ++x) {
             const int j = j0 + x * 32 + lane;
-            if (j < K) bv[x] += __ldcg(D.lam + co + j);  // written by other CTAs of this launch
+            lv[x] = j < K ? __ldcg(D.lam + co + j) : 0.f;  // written by other CTAs of this launch
           }
+#pragma unroll
+          for (int x = 0; x < kB; ++x) bv[x] += lv[x];
         }
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
+        for (int x = 0; x < kB; ++x) {
           const int j = j0 + x * 32 + lane;
           if (j < K) {
             cb[j] = bv[x];
@@ -856,15 +861,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       // pass 2: normalise, fold in the row term, pad to whole chunks
       const bool store = (t.row0 == 0);
-      for (int j0 = 0; j0 < nch * kRows; j0 += 32 * 4) {
-        float zv[4];
+      for (int j0 = 0; j0 < nch * kRows; j0 += 32 * kB) {
+        float zv[kB];
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
+        for (int x = 0; x < kB; ++x) {
           const int j = j0 + x * 32 + lane;
           zv[x] = j < K ? __ldg(D.zn + nd.off_nk + j) : 0.f;
         }
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
+        for (int x = 0; x < kB; ++x) {
           const int j = j0 + x * 32 + lane;
           if (j < K) {
             const float bb = cb[j] - mx;
