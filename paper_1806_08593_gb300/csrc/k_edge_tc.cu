@@ -116,6 +116,13 @@ __device__ __forceinline__ uint64_t kdesc(const unsigned char* base, int kk) {
 __device__ __forceinline__ uint64_t mndesc(const unsigned char* base, int kk) {
   return smem_desc_sw128(smem_u32(base) + kk * 2048, kBox, 1024);
 }
+// The same descriptors from the K-step-0 descriptor of the tile: the start-address field holds
+// the byte address >> 4 and every tile lies below 256 KB, so adding the step offset cannot
+// carry out of the field.  One 64-bit add per MMA instead of a descriptor build.
+__device__ __forceinline__ uint64_t kstep(uint64_t d0, int kk) {
+  return d0 + (uint64_t)((((kk >> 2) * kBox) + (kk & 3) * 32) >> 4);
+}
+__device__ __forceinline__ uint64_t mnstep(uint64_t d0, int kk) { return d0 + (uint64_t)((kk * 2048) >> 4); }
 
 __device__ __forceinline__ void set_timeout(const Dev& D) { atomicOr(D.err, kErrTimeout); }
 
@@ -767,10 +774,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
             !mbar_wait_ab(&full[sw], (uint32_t)(((gu + 1) / NS) & 1), abort))
           return false;
         tc_fence_after();
-        unsigned char *zh = ring + sz * 2 * TB, *zl = zh + TB, *wh = ring + sw * 2 * TB, *wl = wh + TB;
-        for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zh, kk), kdesc(wh, kk), id_mu, kk > 0);
-        for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zl, kk), kdesc(wh, kk), id_mu, 1);
-        for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kdesc(zh, kk), kdesc(wl, kk), id_mu, 1);
+        unsigned char *zh = ring + sz * 2 * TB, *wh = ring + sw * 2 * TB;
+        const uint64_t dzh = kdesc(zh, 0), dzl = kdesc(zh + TB, 0), dwh = kdesc(wh, 0), dwl = kdesc(wh + TB, 0);
+        for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kstep(dzh, kk), kstep(dwh, kk), id_mu, kk > 0);
+        for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kstep(dzl, kk), kstep(dwh, kk), id_mu, 1);
+        for (int kk = 0; kk < KS; ++kk) mma_ss(tMU, kstep(dzh, kk), kstep(dwl, kk), id_mu, 1);
         mma_commit(&mu_full);
         mma_commit(&empty[sz]);
         mma_commit(&empty[sw]);
@@ -792,11 +800,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           if (!mbar_wait_ab(&full[s], (uint32_t)((gu / NS) & 1), abort)) { ok = false; break; }
           if (gc >= 2 && !mbar_wait_ab(&sfree[b], (uint32_t)(((gc >> 1) + 1) & 1), abort)) { ok = false; break; }
           tc_fence_after();
-          unsigned char *bh = ring + s * 2 * TB, *bl = bh + TB;
+          const uint64_t dbh = kdesc(ring + s * 2 * TB, 0), dbl = kdesc(ring + s * 2 * TB + TB, 0);
           // S = (A_hi + A_lo)(B_hi + B_lo)^T without lo*lo; A from tensor memory (2 fp16 / column)
-          for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kdesc(bh, kk), id_s, kk > 0);
-          for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAL + kk * 8, kdesc(bh, kk), id_s, 1);
-          for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kdesc(bl, kk), id_s, 1);
+          for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kstep(dbh, kk), id_s, kk > 0);
+          for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAL + kk * 8, kstep(dbh, kk), id_s, 1);
+          for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kstep(dbl, kk), id_s, 1);
           mma_commit(&sfull[b]);
           mma_commit(&empty[s]);
         }
@@ -1167,10 +1175,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     if (ok) {
       tc_fence_after();
       const uint32_t id_a = idesc_f16(kRows, DP, false, false, false);
-      unsigned char *zh = ring, *zl = ring + TB, *wh = ring + 2 * TB, *wl = ring + 3 * TB;
-      for (int kk = 0; kk < KS; ++kk) mma_ss(tS[0], kdesc(zh, kk), kdesc(wh, kk), id_a, kk > 0);
-      for (int kk = 0; kk < KS; ++kk) mma_ss(tS[0], kdesc(zl, kk), kdesc(wh, kk), id_a, 1);
-      for (int kk = 0; kk < KS; ++kk) mma_ss(tS[0], kdesc(zh, kk), kdesc(wl, kk), id_a, 1);
+      const uint64_t dzh = kdesc(ring, 0), dzl = kdesc(ring + TB, 0), dwh = kdesc(ring + 2 * TB, 0),
+                     dwl = kdesc(ring + 3 * TB, 0);
+      for (int kk = 0; kk < KS; ++kk) mma_ss(tS[0], kstep(dzh, kk), kstep(dwh, kk), id_a, kk > 0);
+      for (int kk = 0; kk < KS; ++kk) mma_ss(tS[0], kstep(dzl, kk), kstep(dwh, kk), id_a, 1);
+      for (int kk = 0; kk < KS; ++kk) mma_ss(tS[0], kstep(dzh, kk), kstep(dwl, kk), id_a, 1);
       mma_commit(&bar_mu);
       ok = mbar_wait(&bar_A, 0);
     }
@@ -1181,20 +1190,20 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         const int s = c & 1, b = c & 1;
         if (!mbar_wait(&full[s], (c >> 1) & 1)) { ok = false; break; }
         tc_fence_after();
-        unsigned char *bh = ring + s * 2 * TB, *bl = bh + TB;
-        for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kdesc(bh, kk), id_s, kk > 0);
-        for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAL + kk * 8, kdesc(bh, kk), id_s, 1);
-        for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kdesc(bl, kk), id_s, 1);
+        const uint64_t dbh = kdesc(ring + s * 2 * TB, 0), dbl = kdesc(ring + s * 2 * TB + TB, 0);
+        for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kstep(dbh, kk), id_s, kk > 0);
+        for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAL + kk * 8, kstep(dbh, kk), id_s, 1);
+        for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kstep(dbl, kk), id_s, 1);
         mma_commit(&sfull[b]);
       }
       if (c >= 1) {
         const int cp = c - 1, s = cp & 1;
         if (!mbar_wait(&pready[cp & 1], (cp >> 1) & 1)) { ok = false; break; }
         tc_fence_after();
-        unsigned char* bh = ring + s * 2 * TB;
+        const uint64_t dv = mndesc(ring + s * 2 * TB, 0);
         // V[k'][:] += sum_k P[k'][k] z~_p^k   (P: fp16 pairs in columns [0,64) of S buffer cp & 1)
         for (int kk = 0; kk < kRows / 16; ++kk)
-          mma_ts(tV, tS[s] + kk * 8, mndesc(bh, kk), id_v, (cp > 0 || kk > 0) ? 1u : 0u);
+          mma_ts(tV, tS[s] + kk * 8, mnstep(dv, kk), id_v, (cp > 0 || kk > 0) ? 1u : 0u);
         mma_commit(&empty[s]);
       }
     }
