@@ -1763,12 +1763,13 @@ __global__ void __launch_bounds__(kThreads) k_leaf_S(Dev D, TcDev T) {
   float acc[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) acc[i] = 0.f;
-  for (int gi = in.node0; gi < in.node0 + in.n; ++gi) {
-    const NodeInfo nd = D.nodes[gi];
-    if (nd.leaf_slot < 0) continue;
+#pragma unroll 2
+  for (int l = T.leaf_off[blockIdx.x]; l < T.leaf_off[blockIdx.x + 1]; ++l) {
+    const LeafInfo li = T.leaf_info[l];
+    const int gi = li.node;
     const float* M2 = T.M2 + (long long)gi * kLdp * kLdp;
     const float* zb = T.zbar + (long long)gi * kLdp;
-    const float mb = b0 + c < d ? __ldg(D.q_mean + nd.off_q + b0 + c) : 0.f;
+    const float mb = b0 + c < d ? __ldg(D.q_mean + li.off_q + b0 + c) : 0.f;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const int a = a0 + r0 + 4 * i;
@@ -1801,19 +1802,20 @@ __global__ void __launch_bounds__(kThreads) k_asm_dC(Dev D, TcDev T) {
                          kLdp, cols, d, sm);
   float X[4][4];
   zero_acc(X);
-  for (int gi = in.node0; gi < in.node0 + in.n; ++gi) {
-    const NodeInfo nd = D.nodes[gi];
-    if (nd.leaf_slot < 0) continue;
+#pragma unroll 2
+  for (int l = T.leaf_off[blockIdx.x]; l < T.leaf_off[blockIdx.x + 1]; ++l) {
+    const LeafInfo li = T.leaf_info[l];
+    const int gi = li.node;
     float xo[4], zm[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int o = o0 + ty * 4 + i;
-      xo[i] = o < obs ? __ldg(T.xs + nd.off_x + o) : 0.f;
+      xo[i] = o < obs ? __ldg(T.xs + li.off_x + o) : 0.f;
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int c = c0 + tx * 4 + j;
-      zm[j] = c < d ? __ldg(T.zbar + (long long)gi * kLdp + c) + __ldg(D.q_mean + nd.off_q + c) : 0.f;
+      zm[j] = c < d ? __ldg(T.zbar + (long long)gi * kLdp + c) + __ldg(D.q_mean + li.off_q + c) : 0.f;
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -2055,6 +2057,24 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
       if (cudaMalloc(&w.d_leaves, sizeof(int) * w.leaves.size()) != cudaSuccess) return TMC_ERR_NOMEM;
       cudaMemcpy(w.d_leaves, w.leaves.data(), sizeof(int) * w.leaves.size(), cudaMemcpyHostToDevice);
     }
+    {  // leaves grouped by instance (node order keeps each instance's leaves contiguous)
+      std::vector<LeafInfo> li(w.leaves.size());
+      std::vector<int> off(w.num_inst + 1, 0);
+      for (size_t l = 0; l < w.leaves.size(); ++l) {
+        const NodeInfo& nd = nodes[w.leaves[l]];
+        li[l] = LeafInfo{w.leaves[l], 0, nd.off_q, nd.off_x};
+        ++off[nd.b + 1];
+      }
+      for (int b = 0; b < w.num_inst; ++b) off[b + 1] += off[b];
+      if (cudaMalloc(&w.d_leaf_off, sizeof(int) * off.size()) != cudaSuccess) return TMC_ERR_NOMEM;
+      cudaMemcpy(w.d_leaf_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
+      if (!li.empty()) {
+        if (cudaMalloc(&w.d_leaf_info, sizeof(LeafInfo) * li.size()) != cudaSuccess) return TMC_ERR_NOMEM;
+        cudaMemcpy(w.d_leaf_info, li.data(), sizeof(LeafInfo) * li.size(), cudaMemcpyHostToDevice);
+      }
+      w.t.leaf_info = w.d_leaf_info;
+      w.t.leaf_off = w.d_leaf_off;
+    }
     if (!w.sample_tiles.empty()) {
       if (cudaMalloc(&w.d_sample_tiles, sizeof(Tile) * w.sample_tiles.size()) != cudaSuccess) return TMC_ERR_NOMEM;
       cudaMemcpy(w.d_sample_tiles, w.sample_tiles.data(), sizeof(Tile) * w.sample_tiles.size(),
@@ -2131,11 +2151,15 @@ void release(TcWork& w) {
   cudaFree(w.d_nonroot);
   cudaFree(w.d_obs_tiles);
   cudaFree(w.d_leaves);
+  cudaFree(w.d_leaf_info);
+  cudaFree(w.d_leaf_off);
   cudaFree(w.d_sample_tiles);
   w.d_tiles = nullptr;
   w.d_nonroot = nullptr;
   w.d_obs_tiles = nullptr;
   w.d_leaves = nullptr;
+  w.d_leaf_info = nullptr;
+  w.d_leaf_off = nullptr;
   w.d_sample_tiles = nullptr;
 }
 

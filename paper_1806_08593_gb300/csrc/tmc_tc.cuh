@@ -21,6 +21,15 @@ constexpr int kLdp = 128;       // row stride (elements) of every packed fp16 op
 constexpr int kTcMaxD = 128;    // latent dimension covered by the tensor-core kernels
 constexpr int kTcMaxK = 4096;   // samples per latent covered by the tensor-core kernels
 
+// A leaf of the tensor-core assembly: node id and the offsets of its proposal mean and
+// observation (the leaves of an instance are contiguous, leaf_off[b] .. leaf_off[b + 1]).
+struct LeafInfo {
+  int node;
+  int pad;
+  long long off_q;
+  long long off_x;
+};
+
 struct TcSub {
   void** dst;
   size_t bytes;
@@ -44,6 +53,8 @@ struct TcDev {
   __half *CH, *CL;             // [c_rows][128] split observation matrices, row = c_row[b] + o
   int* c_row;                  // [1 or B] first row of each observation matrix in CH / CL
   float* xs;                   // centred observations x - C m of the leaves (layout of x)
+  const LeafInfo* leaf_info;   // [leaves] in node order
+  const int* leaf_off;         // [B + 1] leaves of instance b: leaf_off[b] .. leaf_off[b + 1]
   float* S;                    // [B][128*128] sum over an instance's leaves of M2 + zbar m^T
   int* done;                   // [nodes] tiles finished per node in the running edge launch
   int* inst_left;              // [2][B] edge tiles still to run per instance (fwd, adjoint)
@@ -82,6 +93,8 @@ struct TcWork {
   Tile* d_obs_tiles = nullptr;
   std::vector<int> leaves;        // leaf nodes
   int* d_leaves = nullptr;
+  LeafInfo* d_leaf_info = nullptr;
+  int* d_leaf_off = nullptr;
   std::vector<Tile> sample_tiles; // sampler tiles (rows per tile grow as d shrinks)
   Tile* d_sample_tiles = nullptr;
 };
