@@ -66,6 +66,8 @@ def make_workload(name):
 # clocks during the timed region
 # ---------------------------------------------------------------------------------------
 class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 20 ms with host timestamps; summary()
+    keeps the samples taken inside the timed window (mark_start / mark_end)."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -74,22 +76,32 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
+            deadline = time.time() + 10.0  # the timed window opens once sampling runs
+            while not self.lines and time.time() < deadline and self.proc.poll() is None:
+                time.sleep(0.01)
         except OSError:
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def __exit__(self, *a):
         if self.proc:
@@ -102,7 +114,11 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines
+        if self.t0 is not None and self.t1 is not None:
+            inside = [x for x in lines if self.t0 <= x[0] <= self.t1 + 0.02]
+            lines = inside if inside else sorted(lines, key=lambda x: abs(x[0] - self.t1))[:1]
+        for _, ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -348,6 +364,7 @@ def run_ours(args):
     with ClockSampler(local if ws > 1 else 0) as clk:
         barrier()
         torch.cuda.synchronize(dev)
+        clk.mark_start()
         ev0.record(stream)
         for _ in range(args.steps):
             if graph is not None:
@@ -356,6 +373,7 @@ def run_ours(args):
                 step()
         ev1.record(stream)
         torch.cuda.synchronize(dev)
+        clk.mark_end()
         barrier()
     ms = ev0.elapsed_time(ev1)
     if graph is not None:  # kernel-class times from a separate, uncaptured pass
