@@ -161,11 +161,10 @@ __device__ __forceinline__ void stamp_item_end(const Dev& D, TcDev& T, int dir, 
 }
 
 // Bytes of the streaming ring: two stages of (hi, lo) sample tiles, and large enough for the
-// adjoint epilogue (Z~ hi, ones atom, Z~ lo, q z~ tile of two atoms).
+// adjoint epilogue (Z~ hi, Z~ lo, V tile of two atoms).
 __host__ __device__ constexpr int ring_bytes(int DP) {
-  // epilogue: Z~ hi (TB), ones atom, Z~ lo (TB), q z~ tile (2 atoms), V tile (2 atoms)
-  return (4 * kRows * DP * 2 > 2 * kRows * DP * 2 + 5 * kBox) ? 4 * kRows * DP * 2
-                                                              : 2 * kRows * DP * 2 + 5 * kBox;
+  return (4 * kRows * DP * 2 > 2 * kRows * DP * 2 + 2 * kBox) ? 4 * kRows * DP * 2
+                                                              : 2 * kRows * DP * 2 + 2 * kBox;
 }
 }  // namespace
 
@@ -1051,7 +1050,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     k_edge_bwd_tc(Dev D, TcDev T, const Tile* __restrict__ tiles, int ntiles, int* __restrict__ done,
                   const __grid_constant__ CUtensorMap mZH, const __grid_constant__ CUtensorMap mZL,
                   const __grid_constant__ CUtensorMap mWTH, const __grid_constant__ CUtensorMap mWTL,
-                  const __grid_constant__ CUtensorMap mG, const __grid_constant__ CUtensorMap mM2) {
+                  const __grid_constant__ CUtensorMap mG) {
   constexpr int TB = kRows * DP * 2;
   constexpr int NB = DP / 64;
   constexpr int KS = DP / 16;
@@ -1061,11 +1060,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   unsigned char* ring = sm;           // 2 stages x (hi, lo) of parent sample chunks
   float* ak = reinterpret_cast<float*>(ring + ring_bytes(DP));
   // epilogue re-use of the ring / A regions
-  unsigned char* eZH = ring;                 // Z~_i tile hi  (N atoms at +0, +16K)
-  unsigned char* eOnes = ring + TB;          // ones atom: directly after the Z~ atoms
-  unsigned char* eZL = ring + TB + kBox;     // Z~_i tile lo
-  unsigned char* eQZ = ring + 2 * TB + kBox; // q z~ tile (A of M2, 2 atoms)
-  unsigned char* eSV = ring + 2 * TB + 3 * kBox;  // V tile (A of G, 2 atoms)
+  unsigned char* eZH = ring;           // Z~_i tile hi  (N atoms at +0, +16K)
+  unsigned char* eZL = ring + TB;      // Z~_i tile lo
+  unsigned char* eSV = ring + 2 * TB;  // V tile (A of G, 2 atoms)
   __shared__ uint64_t bar_pro, bar_mu, bar_A, full[2], empty[2], sfull[2], pready[2];
   __shared__ uint64_t bar_v, bar_etma, bar_eready, bar_gm;
   __shared__ uint32_t tbase;
@@ -1085,7 +1082,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   // issues V(c) before S(c+2) into the same buffer, and tcgen05 MMAs of one thread run in
   // issue order.
   const uint32_t tS[2] = {tb, tb + 128}, tV = tb + 256, tAH = tb + 384, tAL = tb + 448;
-  const uint32_t tG = tb, tM2 = tb + 128;
+  const uint32_t tG = tb;
 
   // persistent loop over the edge tiles of every level, root side first
   for (int item = blockIdx.x; item < ntiles; item += gridDim.x) {
@@ -1212,12 +1209,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     if (ok) ok = mbar_wait(&bar_etma, 0) && mbar_wait(&bar_eready, 0);
     if (ok) {
       tc_fence_after();
-      // G[a][b]  = sum_k' V[k'][a] z~[k'][b];   M2[a][b] = sum_k' q z~[k'][a] [z~ | 1][k'][b]
+      // G[a][b] = sum_k' V[k'][a] z~[k'][b]   (the node moments M2, zbar: k_moments_tc)
       const uint32_t id_g = idesc_f16(kRows, DP, false, true, true);
-      const uint32_t id_m = idesc_f16(kRows, DP + 16, false, true, true);
       for (int kk = 0; kk < kRows / 16; ++kk) mma_ss(tG, mndesc(eSV, kk), mndesc(eZH, kk), id_g, kk > 0);
       for (int kk = 0; kk < kRows / 16; ++kk) mma_ss(tG, mndesc(eSV, kk), mndesc(eZL, kk), id_g, 1);
-      for (int kk = 0; kk < kRows / 16; ++kk) mma_ss(tM2, mndesc(eQZ, kk), mndesc(eZH, kk), id_m, kk > 0);
       mma_commit(&bar_gm);
       mbar_wait(&bar_gm, 0);
     } else {
@@ -1320,7 +1315,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     const float qtot = q_h[0][r] + q_h[1][r];
     if (ok && valid && h == 0) D.q[nd.off_nk + kq] = qtot;
     __threadfence();  // weights visible device-wide before the completion count moves
-    // epilogue: V row -> fp16 A tile of G; q z~ row -> A tile of M2; ones atom
+    // epilogue: V row -> fp16 A tile of G
     if (ok) ok = mbar_wait(&bar_v, 0);
     if (ok) {
       tc_fence_after();
@@ -1344,37 +1339,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       ok = mbar_wait(&bar_etma, 0);
     }
     if (ok) {
-      const float qv = valid ? qtot : 0.f;
-#pragma unroll 1
-      for (int ch = 8 * h; ch < 8 * h + 8; ++ch) {
-        float f[8];
-        if (ch < DP / 8) {
-          float hv[8], lv[8];
-          load_half8(eZH, r, ch, hv);
-          load_half8(eZL, r, ch, lv);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) f[j] = qv * (hv[j] + lv[j]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) f[j] = 0.f;
-        }
-        store_half8(eQZ, r, ch, f);
-      }
-      // ones atom row r: element 0 = 1, the rest 0
-      for (int ch = 4 * h; ch < 4 * h + 4; ++ch) {
-        float o8[8] = {ch == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        store_half8(eOnes, r, ch, o8);
-      }
       fence_proxy_async_smem();
       tc_fence_before();
     }
     mbar_arrive(&bar_eready);
     if (ok) ok = mbar_wait(&bar_gm, 0);
-    // The tile's G / M2 partials go to global memory as TMA reductions (the L2 adds whole
+    // The tile's G partial goes to global memory as TMA reductions (the L2 adds whole
     // lines): TMEM -> 128B-swizzled [128 x 32] fp32 boxes in the (now free) ring -> one
     // cp.reduce.async.bulk.tensor per box.  Rows / columns past d are zero (padding of z~).
     unsigned char* eG = ring;                        // DP / 32 boxes of 16 KB
-    unsigned char* eM = ring + (DP / 32) * kBox;     // DP / 32 boxes of 16 KB
     if (ok) {
       tc_fence_after();
       const int a = r;  // TMEM lane = output row a
@@ -1388,18 +1361,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         for (int q = 0; q < 8; ++q)
           *reinterpret_cast<uint4*>(eG + g * kBox + sw128_offset(a, q)) =
               make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        tmem_ld32(tM2 + lane_off + g * 32, v);
-        tmem_wait_ld();
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          *reinterpret_cast<uint4*>(eM + g * kBox + sw128_offset(a, q)) =
-              make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-      }
-      if (h == 0) {
-        uint32_t v[32];
-        tmem_ld32(tM2 + lane_off + DP, v);  // column DP: sum_k' q z~[k'][a]
-        tmem_wait_ld();
-        if (a < d) atomicAdd(T.zbar + (long long)t.node * kLdp + a, __uint_as_float(v[0]));
       }
       fence_proxy_async_smem();
     }
@@ -1407,10 +1368,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     sync_math();  // the boxes are complete
     if (ok && mt == 0) {
       const int y = t.node * kLdp;
-      for (int g = 0; g < DP / 32; ++g) {
-        tma_reduce_add_2d(&mG, eG + g * kBox, g * 32, y);
-        tma_reduce_add_2d(&mM2, eM + g * kBox, g * 32, y);
-      }
+      for (int g = 0; g < DP / 32; ++g) tma_reduce_add_2d(&mG, eG + g * kBox, g * 32, y);
       bulk_commit_group();
       bulk_wait_group_read0();  // the ring is reused by the next item
     }
@@ -1432,83 +1390,403 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 }
 
 // =======================================================================================
-// Root moments: zbar_0 = sum_k q_0 z~_0, M2_0 = sum_k q_0 z~_0 z~_0^T (FP32 samples).
-// Grid: (instance, 128-sample slab).  A slab is staged in shared memory 64 rows at a time
-// (all loads of a stage issued before any store); each thread accumulates an R x R block of
-// M2 (R = 8 for d > 64, else 4: a 128x128 or 64x64 corner); slabs add into the zeroed M2 and
-// zbar.
+// Node moments on the tensor core, for every node:
+//   M2_g = sum_k q_g[k] z~_g^k z~_g^k^T,   zbar_g = sum_k q_g[k] z~_g^k.
+// With the samples as the contraction index, A = (q Z~)^T and B = Z~ are MN-major views of
+// [samples x DP] fp16 tiles; zbar is the same A against a B whose first column is 1.  q z~ and
+// z~ are both split (hi + lo), which keeps about 22 bits.
+// Work moves in units of 64 samples: TMA streams each unit's Z~ hi / lo into an NS-stage ring,
+// warps 0-7 form the unit's q Z~ into one of NQ buffers, warp 9 issues its MMAs, warp 8 the
+// TMA.  An item (up to kMoSlabs x 128 samples of one node) accumulates in one of two TMEM
+// accumulators (M2 in columns [0, DP), zbar in column DP); its epilogue (TMEM -> vector
+// atomics into M2 and zbar, rows a < d, columns < d) runs a few units into the next item,
+// under that item's MMAs.
+// Shared-memory bandwidth bounds this kernel (TMA writes, the q Z~ pass, the operand reads of
+// the MMAs), so every MMA reads its A once against as wide a B as fits: each ring stage holds
+// a constant ones atom next to the Z~ atoms, and B = [Z~ hi | Z~ lo | 1] (DP = 64, N = 144)
+// or [Z~ hi | 1] (DP = 128, N = 144) plus Z~ lo (N = 128).
+// DP = 64: hi and lo of q Z~ are stacked along M (A rows 0-63 hi, 64-127 lo): one MMA per
+// K-step gives qz_hi z~_hi, qz_hi z~_lo, qz_lo z~_hi, qz_lo z~_lo and both zbar halves; the
+// epilogue adds the column blocks and the two TMEM halves.  DP = 128: A rows are the 128
+// entries of q z~, hi and lo in separate tiles, three MMAs per K-step.
 // =======================================================================================
-constexpr int kRootSlab = 128;
-constexpr int kRootLd = kTcMaxD + 4;
-template <int R>
-__device__ __forceinline__ void root_moments_slab(const Dev& D, const TcDev& T, const NodeInfo& nd, int g,
-                                                  int kb, int ke, float (*zs)[kRootLd], float* qs) {
-  constexpr int DP = 16 * R;          // corner covered by the 16 x 16 threads
-  constexpr int NV = 64 * DP / 256;   // staged values per thread per 64-row stage
-  const int d = nd.d;
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  const float* __restrict__ zt = D.zt + nd.off_nkd;
-  float acc[R][R];
-#pragma unroll
-  for (int i = 0; i < R; ++i)
-#pragma unroll
-    for (int j = 0; j < R; ++j) acc[i][j] = 0.f;
-  float zsum = 0.f;
-  for (int k0 = kb; k0 < ke; k0 += 64) {
-    const int rows = min(64, ke - k0);
-    float v[NV];
-#pragma unroll
-    for (int x = 0; x < NV; ++x) {
-      const int e = threadIdx.x + x * 256, l = e / DP, c = e % DP;
-      v[x] = (l < rows && c < d) ? zt[(long long)(k0 + l) * d + c] : 0.f;
-    }
-    const float qv = threadIdx.x < rows ? D.q[nd.off_nk + k0 + threadIdx.x] : 0.f;
-    __syncthreads();  // the previous stage has been consumed
-#pragma unroll
-    for (int x = 0; x < NV; ++x) {
-      const int e = threadIdx.x + x * 256;
-      zs[e / DP][e % DP] = v[x];
-    }
-    if (threadIdx.x < 64) qs[threadIdx.x] = qv;
-    __syncthreads();
-    for (int l = 0; l < rows; ++l) {
-      const float q = qs[l];
-      float a[R], b[R];
-#pragma unroll
-      for (int i = 0; i < R; i += 4) {
-        const float4 av = *reinterpret_cast<const float4*>(&zs[l][ty * R + i]);
-        const float4 bv = *reinterpret_cast<const float4*>(&zs[l][tx * R + i]);
-        a[i] = q * av.x; a[i + 1] = q * av.y; a[i + 2] = q * av.z; a[i + 3] = q * av.w;
-        b[i] = bv.x; b[i + 1] = bv.y; b[i + 2] = bv.z; b[i + 3] = bv.w;
-      }
-#pragma unroll
-      for (int i = 0; i < R; ++i)
-#pragma unroll
-        for (int j = 0; j < R; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    if (threadIdx.x < DP)
-      for (int l = 0; l < rows; ++l) zsum = fmaf(qs[l], zs[l][threadIdx.x], zsum);
-  }
-  float* M = T.M2 + (long long)g * kLdp * kLdp;
-#pragma unroll
-  for (int i = 0; i < R; ++i)
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-      const int a = ty * R + i, b = tx * R + j;
-      if (a < d && b < d) atomicAdd(M + (long long)a * kLdp + b, acc[i][j]);
-    }
-  if (threadIdx.x < d) atomicAdd(T.zbar + (long long)g * kLdp + threadIdx.x, zsum);
+constexpr int kMoSlabs = 8;
+constexpr int kMoThreads = 448;
+constexpr int kMoMath = 256;
+constexpr int kMoPrefetch = 6;               // units prefetched into L2 ahead of the ring loads
+constexpr int kMoUnit = 64;                  // samples per unit
+constexpr int kMoAtom = kMoUnit * 128;       // one 64-row, 128-byte-swizzled atom
+constexpr int kMoXLd = 68;                   // row stride (floats) of the epilogue scratch
+constexpr int kMoXBytes = (64 * kMoXLd + 64) * 4;  // one scratch: 64 x 64 block + 64 zbar
+template <int DP>
+struct MoCfg {
+  static constexpr bool STK = DP == 64;        // q Z~ hi / lo stacked along M
+  static constexpr int UT = kMoUnit * DP * 2;  // one [64 x DP] fp16 tile (DP / 64 atoms)
+  // ring stage: STK [Z~ hi | Z~ lo | ones], else [Z~ hi (2 atoms) | ones | Z~ lo (2 atoms)]
+  static constexpr int ZL_OFF = STK ? kMoAtom : 3 * kMoAtom;
+  static constexpr int ONES_OFF = STK ? 2 * kMoAtom : 2 * kMoAtom;
+  static constexpr int SB = 2 * UT + kMoAtom;
+  static constexpr int QB = STK ? 2 * kMoAtom : 4 * kMoAtom;  // q Z~ buffer
+  static constexpr int NQ = STK ? 4 : 2;
+  static constexpr int XB = STK ? 2 * kMoXBytes : 0;  // epilogue scratch (two buffers)
+  // the opt-in maximum (227 KB) less the alignment pad and 2 KB of static shared memory
+  static constexpr int NS0 = (232448 - 1024 - 2048 - NQ * QB - XB) / SB;
+  static constexpr int NS = NS0 > 6 ? 6 : NS0;
+  static constexpr size_t smem = 1024 + (size_t)NS * SB + (size_t)NQ * QB + XB;
+  static constexpr int CPT = DP / 32;          // 16-byte chunks of a q Z~ row per math thread
+  static_assert(NS >= 2, "moments ring");
+};
+
+__device__ __forceinline__ uint32_t mo_off(int rr, int chunk) {
+  return (uint32_t)(chunk >> 3) * kMoAtom + sw128_offset(rr, chunk & 7);
+}
+__device__ __forceinline__ uint64_t mo_desc(const unsigned char* p) {
+  return smem_desc_sw128(smem_u32(p), kMoAtom, 1024);
 }
 
-__global__ void __launch_bounds__(256) k_root_moments(Dev D, TcDev T) {
-  __shared__ __align__(16) float zs[64][kRootLd];
-  __shared__ float qs[64];
-  const InstInfo in = D.insts[blockIdx.x];
-  const NodeInfo nd = D.nodes[in.node0];
-  const int kb = blockIdx.y * kRootSlab, ke = min(nd.K, kb + kRootSlab);
-  if (kb >= nd.K) return;
-  if (nd.d > 64) root_moments_slab<8>(D, T, nd, in.node0, kb, ke, zs, qs);
-  else root_moments_slab<4>(D, T, nd, in.node0, kb, ke, zs, qs);
+template <int DP>
+__global__ void __launch_bounds__(kMoThreads, 1)
+    k_moments_tc(Dev D, TcDev T, const MoItem* __restrict__ items, int nitems,
+                 const __grid_constant__ CUtensorMap mZH, const __grid_constant__ CUtensorMap mZL) {
+  using C = MoCfg<DP>;
+  constexpr int SB = C::SB, QB = C::QB, NQ = C::NQ, NS = C::NS, NB = DP / 64, CPT = C::CPT;
+  constexpr int ZL_OFF = C::ZL_OFF, ONES_OFF = C::ONES_OFF;
+  constexpr bool STK = C::STK;
+  extern __shared__ unsigned char smraw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  unsigned char* ring = sm;                   // NS x (Z~ hi, Z~ lo, ones) of a unit
+  unsigned char* qz = ring + NS * SB;         // NQ x q Z~
+  float* xs = reinterpret_cast<float*>(qz + NQ * QB);  // DP = 64: lo-half partials, 2 buffers
+  __shared__ uint64_t full[NS], empty[NS], qready[NQ], qfree[NQ], accdone[2], accfree[2], fin;
+  __shared__ float qs[NS][kMoUnit];             // the unit's sample weights, beside its ring stage
+  __shared__ uint32_t tbase;
+  __shared__ int abort_;
+  volatile int* abort = &abort_;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 9) tmem_alloc(&tbase, 512);
+  // the ones atom of every stage: row k = (1, 0, ..., 0)
+  for (int i = threadIdx.x; i < NS * kMoUnit * 8; i += blockDim.x) {
+    const int r = i % kMoUnit, ch = (i / kMoUnit) % 8, st = i / (kMoUnit * 8);
+    const uint32_t one = ch == 0 ? 0x3C00u : 0u;  // fp16 1.0 in the low half
+    *reinterpret_cast<uint4*>(ring + st * SB + ONES_OFF + mo_off(r, ch)) = make_uint4(one, 0u, 0u, 0u);
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < NQ; ++i) {
+      mbar_init(&qready[i], kMoMath / 32);  // one arrival per math warp
+      mbar_init(&qfree[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&accdone[i], 1);
+      mbar_init(&accfree[i], 4);  // one arrival per epilogue warp
+    }
+    mbar_init(&fin, 1);
+    fence_barrier_init();
+    abort_ = 0;
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tb = tbase;
+
+  if (warp == 8) {
+    // ---------------- producer: 64-sample units of Z~ hi / lo into the ring (TMA, lane 0) and
+    // their sample weights into qs (the whole warp, loaded ahead of the wait for the stage).
+    // The warp loads the records of its next 32 items at once (lane i: item i).
+    if (lane == 0) {
+      prefetch_tmap(&mZH);
+      prefetch_tmap(&mZL);
+    }
+    int gu = 0;
+    bool ok = true;
+    for (int base = blockIdx.x; base < nitems && ok; base += 32 * gridDim.x) {
+      const int mine = base + lane * gridDim.x;
+      const MoItem rec = mine < nitems ? items[mine] : MoItem{};
+      const int nb = min(32, (nitems - base + (int)gridDim.x - 1) / (int)gridDim.x);
+      // L2 prefetch cursor kMoPrefetch units ahead of the loads (within the batch): the ring
+      // holds too few bytes to cover the DRAM latency on its own
+      int pj = 0, pu = 0;
+      auto pf_step = [&]() {
+        if (pj >= nb) return;
+        const long long prow = __shfl_sync(0xffffffffu, rec.row, pj);
+        const int pnr = __shfl_sync(0xffffffffu, rec.nrows, pj);
+        if (lane == 0)
+          for (int b = 0; b < NB; ++b) {
+            tma_prefetch_l2_2d(&mZH, b * 64, (int)(prow + pu * kMoUnit));
+            tma_prefetch_l2_2d(&mZL, b * 64, (int)(prow + pu * kMoUnit));
+          }
+        if (++pu * kMoUnit >= pnr) {
+          pu = 0;
+          ++pj;
+        }
+      };
+      for (int i = 0; i < kMoPrefetch; ++i) pf_step();
+      // the sample weights of a unit are loaded one unit ahead of its stage
+      auto q_load = [&](int jj, int uu, float& x0, float& x1) {
+        const long long r = __shfl_sync(0xffffffffu, rec.row, jj);
+        const int nr = __shfl_sync(0xffffffffu, rec.nrows, jj);
+        const int k0 = uu * kMoUnit + lane;
+        x0 = k0 < nr ? __ldg(D.q + r + k0) : 0.f;
+        x1 = k0 + 32 < nr ? __ldg(D.q + r + k0 + 32) : 0.f;
+      };
+      float q0 = 0.f, q1 = 0.f;
+      if (nb > 0) q_load(0, 0, q0, q1);
+      for (int j = 0, u = 0; j < nb && ok;) {
+        const long long row = __shfl_sync(0xffffffffu, rec.row, j);
+        const int nrows = __shfl_sync(0xffffffffu, rec.nrows, j);
+        const int nu = (nrows + kMoUnit - 1) / kMoUnit;
+        int j2 = j, u2 = u + 1;  // the next unit
+        if (u2 >= nu) {
+          j2 = j + 1;
+          u2 = 0;
+        }
+        float n0 = 0.f, n1 = 0.f;
+        if (j2 < nb) q_load(j2, u2, n0, n1);
+        pf_step();
+        const int st = gu % NS, use = gu / NS;
+        bool w = true;
+        if (lane == 0) w = use < 1 || mbar_wait_ab(&empty[st], (uint32_t)((use - 1) & 1), abort);
+        if (!__shfl_sync(0xffffffffu, w, 0)) {
+          ok = false;
+          break;
+        }
+        qs[st][lane] = q0;
+        qs[st][lane + 32] = q1;
+        __syncwarp();  // orders the weights before lane 0's arrival (release) on full
+        if (lane == 0) {
+          mbar_arrive_expect_tx(&full[st], 2 * C::UT);
+          for (int b = 0; b < NB; ++b) {
+            tma_load_2d(ring + st * SB + b * kMoAtom, &mZH, &full[st], b * 64, (int)(row + u * kMoUnit));
+            tma_load_2d(ring + st * SB + ZL_OFF + b * kMoAtom, &mZL, &full[st], b * 64, (int)(row + u * kMoUnit));
+          }
+        }
+        ++gu;
+        q0 = n0;
+        q1 = n1;
+        j = j2;
+        u = u2;
+      }
+    }
+    // the copies still in flight land before the CTA leaves (bounded)
+    if (lane == 0)
+      for (int i = gu - 1; i >= 0 && i >= gu - NS; --i) mbar_wait(&full[i % NS], (uint32_t)((i / NS) & 1));
+  } else if (warp == 9) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t id_w = idesc_f16(kRows, 144, false, true, true);  // [hi | lo | 1] or [hi | 1]
+      const uint32_t id_l = idesc_f16(kRows, DP, false, true, true);    // DP = 128: Z~ lo
+      int gu = 0, it = 0;
+      bool issued = false;
+      MoItem mn = blockIdx.x < nitems ? items[blockIdx.x] : MoItem{};
+      for (int item = blockIdx.x; item < nitems && !*abort; item += gridDim.x, ++it) {
+        const MoItem m = mn;
+        if (item + gridDim.x < nitems) mn = items[item + gridDim.x];
+        const int nu = (m.nrows + kMoUnit - 1) / kMoUnit;
+        const int ab = it & 1;
+        const uint32_t acc = tb + ab * 256;
+        if (it >= 2 && !mbar_wait_ab(&accfree[ab], (uint32_t)(((it >> 1) - 1) & 1), abort)) break;
+        bool ok = true;
+        for (int u = 0; u < nu; ++u, ++gu) {
+          const int st = gu % NS, qb = gu % NQ;
+          if (!mbar_wait_ab(&full[st], (uint32_t)((gu / NS) & 1), abort) ||
+              !mbar_wait_ab(&qready[qb], (uint32_t)((gu / NQ) & 1), abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t dbw = mo_desc(ring + st * SB), dzl = mo_desc(ring + st * SB + ZL_OFF);
+          const uint64_t dqh = mo_desc(qz + qb * QB), dql = mo_desc(qz + qb * QB + 2 * kMoAtom);
+          for (int kk = 0; kk < kMoUnit / 16; ++kk) {
+            const uint32_t first = (u == 0 && kk == 0) ? 0u : 1u;
+            mma_ss(acc, mnstep(dqh, kk), mnstep(dbw, kk), id_w, first);
+            if (!STK) {
+              mma_ss(acc, mnstep(dql, kk), mnstep(dbw, kk), id_w, 1u);
+              mma_ss(acc, mnstep(dqh, kk), mnstep(dzl, kk), id_l, 1u);
+            }
+          }
+          issued = true;
+          mma_commit(&empty[st]);
+          mma_commit(&qfree[qb]);
+        }
+        if (!ok) break;
+        mma_commit(&accdone[ab]);
+      }
+      if (issued) {  // every MMA issued has completed before TMEM is released
+        mma_commit(&fin);
+        mbar_wait(&fin, 0);
+      }
+    }
+  } else if (warp < 8) {
+    // ---------------- warps 0-7: q Z~ units (thread: sample rr of the unit, chunk group cq).
+    const int rr = threadIdx.x & (kMoUnit - 1), cq = threadIdx.x / kMoUnit;
+    bool ok = true;
+    int gu = 0, it = 0;
+    // item records are loaded one item ahead; the sample weights come with the ring stage
+    MoItem m = blockIdx.x < nitems ? items[blockIdx.x] : MoItem{};
+    MoItem mn = blockIdx.x + gridDim.x < nitems ? items[blockIdx.x + gridDim.x] : MoItem{};
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++it) {
+      const int nu = (m.nrows + kMoUnit - 1) / kMoUnit;
+      for (int u = 0; u < nu; ++u, ++gu) {
+        const int st = gu % NS, qb = gu % NQ;
+        const int k = u * kMoUnit + rr;  // sample within the item
+        ok = ok && mbar_wait_ab(&full[st], (uint32_t)((gu / NS) & 1), abort);
+        ok = ok && (gu < NQ || mbar_wait_ab(&qfree[qb], (uint32_t)(((gu / NQ) - 1) & 1), abort));
+        ok = __all_sync(0xffffffffu, ok);  // one arrival per warp below
+        if (ok) {
+          const float q = k < m.nrows ? qs[st][rr] : 0.f;
+          const unsigned char* zt = ring + st * SB;
+          unsigned char* qh = qz + qb * QB;
+          unsigned char* ql = qh + (STK ? kMoAtom : 2 * kMoAtom);
+#pragma unroll
+          for (int i = 0; i < CPT; ++i) {
+            const int ch = cq * CPT + i;
+            const uint32_t off = mo_off(rr, ch);
+            const uint4 uh = *reinterpret_cast<const uint4*>(zt + off);
+            const uint4 ul = *reinterpret_cast<const uint4*>(zt + ZL_OFF + off);
+            const uint32_t wh[4] = {uh.x, uh.y, uh.z, uh.w}, wl[4] = {ul.x, ul.y, ul.z, ul.w};
+            uint32_t hh[4], ll[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float2 fh = __half22float2(*reinterpret_cast<const __half2*>(&wh[e]));
+              const float2 fl = __half22float2(*reinterpret_cast<const __half2*>(&wl[e]));
+              split_pack2(q * (fh.x + fl.x), q * (fh.y + fl.y), hh[e], ll[e]);
+            }
+            *reinterpret_cast<uint4*>(qh + off) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+            *reinterpret_cast<uint4*>(ql + off) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
+          }
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&qready[qb]);
+        }
+      }
+      m = mn;
+      if (item + 2 * gridDim.x < nitems) mn = items[item + 2 * gridDim.x];
+    }
+    if (!ok) set_timeout(D);
+  } else {
+    // ---------------- warps 10-13: the epilogue of every item, in item order, as soon as its
+    // accumulator is complete (TMEM lane quarter = warp % 4).
+    bool ok = true;
+    // Epilogue of an item: TMEM lane a holds row a of M2 in columns [0, DP) (DP = 64: the sum
+    // of column blocks [0, 64) and [64, 128), and lanes 64-127 the lo-half partial of row
+    // a - 64) and entry a of zbar in column 128.  An item that covers its node stores M2 and
+    // zbar (the lo-half partials pass through shared memory to the hi-half warps); a node split
+    // over several items accumulates with atomics into the zeroed M2 / zbar.  Only rows and
+    // columns < d are written: no reader looks past them.
+    auto ld_m2 = [&](uint32_t acc, int g, float (&f)[32]) {  // 32 columns of M2, warp-collective
+      uint32_t v[32];
+      tmem_ld32(acc + g * 32, v);
+      tmem_wait_ld();
+#pragma unroll
+      for (int c = 0; c < 32; ++c) f[c] = __uint_as_float(v[c]);
+      if (STK) {
+        tmem_ld32(acc + 64 + g * 32, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 32; ++c) f[c] += __uint_as_float(v[c]);
+      }
+    };
+    auto ld_zbar = [&](uint32_t acc) {  // warp-collective
+      uint32_t v[32];
+      tmem_ld32(acc + 128, v);
+      tmem_wait_ld();
+      return __uint_as_float(v[0]);
+    };
+    auto epilogue = [&](const MoItem& m, int pit) {
+      const int ab = pit & 1;
+      ok = ok && mbar_wait_ab(&accdone[ab], (uint32_t)((pit >> 1) & 1), abort);
+      ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+      const int quarter = warp & 3;
+      const int abase = STK ? (quarter & 1) * 32 : quarter * 32;
+      const int a = abase + lane;
+      const bool lo_half = STK && quarter >= 2;
+      const uint32_t acc = tb + ab * 256 + ((uint32_t)(quarter * 32) << 16);
+      float* M2row = T.M2 + ((long long)m.node * kLdp + a) * kLdp;
+      float* zb = T.zbar + (long long)m.node * kLdp;
+      float* x = xs + ab * (kMoXBytes / 4);
+      const bool combine = STK && m.whole;
+      if (ok) tc_fence_after();
+      if (combine) {
+        if (ok && lo_half && abase < m.d) {
+          for (int part = 0; part < DP / 32 && part * 32 < m.d; ++part) {
+            float f[32];
+            ld_m2(acc, part, f);
+#pragma unroll
+            for (int c4 = 0; c4 < 8; ++c4)
+              *reinterpret_cast<float4*>(x + a * kMoXLd + part * 32 + c4 * 4) =
+                  make_float4(f[4 * c4], f[4 * c4 + 1], f[4 * c4 + 2], f[4 * c4 + 3]);
+          }
+          x[64 * kMoXLd + a] = ld_zbar(acc);
+        }
+        asm volatile("bar.sync 2, 128;" ::: "memory");  // every epilogue warp, whatever ok says
+        if (ok && !lo_half && abase < m.d) {
+          for (int part = 0; part < DP / 32 && part * 32 < m.d; ++part) {
+            float f[32];
+            ld_m2(acc, part, f);
+            if (a < m.d)
+#pragma unroll
+              for (int c4 = 0; c4 < 8; ++c4)
+                if (part * 32 + c4 * 4 < m.d) {
+                  const float4 o = *reinterpret_cast<const float4*>(x + a * kMoXLd + part * 32 + c4 * 4);
+                  *reinterpret_cast<float4*>(M2row + part * 32 + c4 * 4) =
+                      make_float4(f[4 * c4] + o.x, f[4 * c4 + 1] + o.y, f[4 * c4 + 2] + o.z, f[4 * c4 + 3] + o.w);
+                }
+          }
+          const float z = ld_zbar(acc);
+          if (a < m.d) zb[a] = z + x[64 * kMoXLd + a];
+        }
+      } else {
+        // (DP = 64: the scratch buffers are reused two items on, with this barrier between)
+        if (STK) asm volatile("bar.sync 2, 128;" ::: "memory");
+      }
+      if (!combine && ok && abase < m.d) {  // warp-uniform
+        for (int g = 0; g < DP / 32; ++g) {
+          if (g * 32 >= m.d) break;
+          float f[32];
+          ld_m2(acc, g, f);
+          if (a < m.d)
+#pragma unroll
+            for (int c4 = 0; c4 < 8; ++c4)
+              if (g * 32 + c4 * 4 < m.d) {
+                const float4 v4 = make_float4(f[4 * c4], f[4 * c4 + 1], f[4 * c4 + 2], f[4 * c4 + 3]);
+                if (m.whole) *reinterpret_cast<float4*>(M2row + g * 32 + c4 * 4) = v4;
+                else atomicAdd(reinterpret_cast<float4*>(M2row + g * 32 + c4 * 4), v4);
+              }
+        }
+        const float z = ld_zbar(acc);
+        if (a < m.d) {
+          if (m.whole) zb[a] = z;
+          else atomicAdd(zb + a, z);
+        }
+      }
+      if (ok) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&accfree[ab]);
+      }
+    };
+    int it = 0;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++it) epilogue(items[item], it);
+    if (!ok) set_timeout(D);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 9) {
+    tc_fence_after();
+    tmem_dealloc(tb, 512);
+  }
+}
+
+// Zeroes the d x d block of every node in a [node][128][128] array (the part the readers use;
+// the adjoint launch adds its tile partials of G into it).
+__global__ void __launch_bounds__(256) k_zero_dd(Dev D, float* __restrict__ base) {
+  const int d = D.nodes[blockIdx.x].d;
+  float* blk = base + (long long)blockIdx.x * kLdp * kLdp;
+  for (int i = threadIdx.x; i < d * d; i += blockDim.x) blk[(i / d) * kLdp + i % d] = 0.f;
 }
 
 // =======================================================================================
@@ -1869,12 +2147,12 @@ bool make_map_f32(CUtensorMap* m, void* ptr, long long rows) {
              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool make_map(CUtensorMap* m, void* ptr, long long rows) {
+bool make_map(CUtensorMap* m, void* ptr, long long rows, int box_rows = kRows) {
   EncodeFn enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)kLdp, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)kLdp * 2};
-  cuuint32_t box[2] = {64, (cuuint32_t)kRows};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ptr, dims, strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -2023,8 +2301,8 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
       !make_map(&w.mWTH, w.t.WTH, (long long)w.num_slots * kLdp) ||
       !make_map(&w.mWTL, w.t.WTL, (long long)w.num_slots * kLdp) ||
       !make_map(&w.mCH, w.t.CH, w.c_rows) || !make_map(&w.mCL, w.t.CL, w.c_rows) ||
-      !make_map_f32(&w.mG, w.t.G, (long long)w.num_nodes * kLdp) ||
-      !make_map_f32(&w.mM2, w.t.M2, (long long)w.num_nodes * kLdp))
+      !make_map(&w.mZH64, w.t.ZH, w.rows, kMoUnit) || !make_map(&w.mZL64, w.t.ZL, w.rows, kMoUnit) ||
+      !make_map_f32(&w.mG, w.t.G, (long long)w.num_nodes * kLdp))
     return TMC_ERR_CUDA;
   {  // observation matrices' first rows, and the leaf tiles of the observation kernel
     std::vector<int> crow(w.num_c, 0);
@@ -2046,6 +2324,22 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
     w.leaves.clear();
     for (int g = 0; g < (int)nodes.size(); ++g)
       if (nodes[g].leaf_slot >= 0) w.leaves.push_back(g);
+    w.mo_items.clear();  // node-moment items: every node, kMoSlabs x 128 samples each, per d class
+    for (int c = 0; c < 2; ++c) {
+      w.mo_b[c] = (int)w.mo_items.size();
+      for (int g = 0; g < (int)nodes.size(); ++g)
+        if (((nodes[g].d > 64) ? 1 : 0) == c)
+          for (int r = 0; r < nodes[g].K; r += kMoSlabs * kRows)
+            w.mo_items.push_back(MoItem{nodes[g].off_nk + r, g, std::min(nodes[g].K - r, kMoSlabs * kRows), nodes[g].d,
+                                        nodes[g].K <= kMoSlabs * kRows ? 1 : 0});
+      w.mo_e[c] = (int)w.mo_items.size();
+    }
+    w.mo_split = false;
+    for (const NodeInfo& nd : nodes) w.mo_split = w.mo_split || nd.K > kMoSlabs * kRows;
+    if (!w.mo_items.empty()) {
+      if (cudaMalloc(&w.d_mo_items, sizeof(MoItem) * w.mo_items.size()) != cudaSuccess) return TMC_ERR_NOMEM;
+      cudaMemcpy(w.d_mo_items, w.mo_items.data(), sizeof(MoItem) * w.mo_items.size(), cudaMemcpyHostToDevice);
+    }
     w.sample_tiles.clear();
     for (int g = 0; g < (int)nodes.size(); ++g)
       for (int r = 0; r < nodes[g].K; r += sample_rows(nodes[g].d)) w.sample_tiles.push_back(Tile{g, r});
@@ -2128,6 +2422,8 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
   cudaFuncSetAttribute(k_edge_bwd_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<64>(maxK));
   cudaFuncSetAttribute(k_edge_bwd_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<128>(maxK));
   cudaFuncSetAttribute(k_sample_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSampleSmem);
+  cudaFuncSetAttribute(k_moments_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MoCfg<64>::smem);
+  cudaFuncSetAttribute(k_moments_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MoCfg<128>::smem);
   cudaFuncSetAttribute(k_obs_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)obs_smem<64>());
   cudaFuncSetAttribute(k_obs_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)obs_smem<128>());
   return cudaGetLastError() == cudaSuccess ? TMC_OK : TMC_ERR_CUDA;
@@ -2153,6 +2449,7 @@ void release(TcWork& w) {
   cudaFree(w.d_leaves);
   cudaFree(w.d_leaf_info);
   cudaFree(w.d_leaf_off);
+  cudaFree(w.d_mo_items);
   cudaFree(w.d_sample_tiles);
   w.d_tiles = nullptr;
   w.d_nonroot = nullptr;
@@ -2160,6 +2457,7 @@ void release(TcWork& w) {
   w.d_leaves = nullptr;
   w.d_leaf_info = nullptr;
   w.d_leaf_off = nullptr;
+  w.d_mo_items = nullptr;
   w.d_sample_tiles = nullptr;
 }
 
@@ -2214,9 +2512,7 @@ void launch_edge_fwd(TcWork& w, const Dev& D, cudaStream_t s) {
 }
 
 void launch_edge_bwd(TcWork& w, const Dev& D, cudaStream_t s) {
-  cudaMemsetAsync(w.t.G, 0, (size_t)w.num_nodes * kLdp * kLdp * sizeof(float), s);
-  cudaMemsetAsync(w.t.M2, 0, (size_t)w.num_nodes * kLdp * kLdp * sizeof(float), s);
-  cudaMemsetAsync(w.t.zbar, 0, (size_t)w.num_nodes * kLdp * sizeof(float), s);
+  k_zero_dd<<<w.num_nodes, 256, 0, s>>>(D, w.t.G);
   cudaMemsetAsync(w.t.done, 0, (size_t)w.num_nodes * sizeof(int), s);
   cudaMemcpyAsync(w.t.inst_left + w.num_inst, w.inst_init_dev + w.num_inst, sizeof(int) * w.num_inst,
                   cudaMemcpyDeviceToDevice, s);
@@ -2227,20 +2523,30 @@ void launch_edge_bwd(TcWork& w, const Dev& D, cudaStream_t s) {
     const int grid = n < w.num_sms ? n : w.num_sms;
     if (c == 0)
       k_edge_bwd_tc<64><<<grid, kThreadsTc, bwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH, w.mZL,
-                                                                     w.mWTH, w.mWTL, w.mG, w.mM2);
+                                                                     w.mWTH, w.mWTL, w.mG);
     else
       k_edge_bwd_tc<128><<<grid, kThreadsTc, bwd_smem<128>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH,
-                                                                       w.mZL, w.mWTH, w.mWTL, w.mG, w.mM2);
+                                                                       w.mZL, w.mWTH, w.mWTL, w.mG);
   }
 }
 
 void launch_unpack_grads(TcWork& w, const Dev& D, cudaStream_t s) {
   const int nr = (int)w.nonroot.size();
-  if (w.maxlevel == 0) {  // no adjoint edge launch zeroed the moments
+  if (w.mo_split) {  // a node split over several moment items accumulates with atomics
     cudaMemsetAsync(w.t.M2, 0, (size_t)w.num_nodes * kLdp * kLdp * sizeof(float), s);
     cudaMemsetAsync(w.t.zbar, 0, (size_t)w.num_nodes * kLdp * sizeof(float), s);
   }
-  k_root_moments<<<dim3(D.num_inst, (w.maxK + kRootSlab - 1) / kRootSlab), 256, 0, s>>>(D, w.t);
+  for (int c = 0; c < 2; ++c) {  // node moments M2, zbar of every node (roots included)
+    const int b = w.mo_b[c], n = w.mo_e[c] - b;
+    if (!n) continue;
+    const MoItem* it = w.d_mo_items + b;
+    if (c == 0)
+      k_moments_tc<64><<<std::min(n, w.num_sms), kMoThreads, MoCfg<64>::smem, s>>>(D, w.t, it, n, w.mZH64, w.mZL64);
+    else
+      k_moments_tc<128><<<std::min(n, w.num_sms), kMoThreads, MoCfg<128>::smem, s>>>(D, w.t, it, n, w.mZH64,
+                                                                                   w.mZL64);
+  }
+
   cudaMemsetAsync(w.t.CtC, 0, (size_t)(D.shared ? 1 : D.num_inst) * kLdp * kLdp * sizeof(float), s);
   k_ctc<<<dim3(D.shared ? 1 : D.num_inst, w.maxdp > 64 ? 4 : 1, (w.maxobs + kTile - 1) / kTile), kThreads, 0, s>>>(D, w.t);
   cudaMemsetAsync(w.t.tgP, 0, (size_t)w.num_nodes * kLdp * sizeof(float), s);

@@ -245,5 +245,15 @@ __device__ __forceinline__ void split_half(float x, float& hi, float& lo) {
   lo = x - hi;
 }
 
+// The hi / lo fp16 pairs of two floats, packed: the same values as split_half + pack_half2,
+// with one conversion per pack.
+__device__ __forceinline__ void split_pack2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(a, b);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
 }  // namespace tc
 }  // namespace tmc

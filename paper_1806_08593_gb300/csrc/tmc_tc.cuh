@@ -23,6 +23,12 @@ constexpr int kTcMaxK = 4096;   // samples per latent covered by the tensor-core
 
 // A leaf of the tensor-core assembly: node id and the offsets of its proposal mean and
 // observation (the leaves of an instance are contiguous, leaf_off[b] .. leaf_off[b + 1]).
+// One item of the node-moment launch: up to 1024 consecutive samples of one node.
+struct MoItem {
+  long long row;  // first sample row of the item in the packed sample tensors
+  int node, nrows, d;
+  int whole;      // the item covers every sample of its node
+};
 struct LeafInfo {
   int node;
   int pad;
@@ -70,6 +76,7 @@ struct TcWork {
   long long rows = 0;
   TcDev t{};
   CUtensorMap mZH, mZL, mWH, mWL, mWTH, mWTL;
+  CUtensorMap mZH64, mZL64;       // the sample tiles in 64-row boxes (node moments)
   // edge tiles in dependency order: [direction][class] ranges into d_tiles; direction 0 =
   // forward (deepest level first), 1 = adjoint (level 1 first); class 0: d <= 64, 1: d <= 128
   std::vector<Tile> tiles;
@@ -87,13 +94,17 @@ struct TcWork {
   long long c_rows = 0;
   int num_c = 0;                  // distinct observation matrices (1 when shared)
   CUtensorMap mCH, mCL;
-  CUtensorMap mG, mM2;            // fp32 [nodes*128][128] views of G / M2 for TMA reductions
+  CUtensorMap mG;                 // fp32 [nodes*128][128] view of G for TMA reductions
   std::vector<Tile> obs_tiles;
   int ob_b[2] = {0, 0}, ob_e[2] = {0, 0};
   Tile* d_obs_tiles = nullptr;
   std::vector<int> leaves;        // leaf nodes
   int* d_leaves = nullptr;
   LeafInfo* d_leaf_info = nullptr;
+  std::vector<MoItem> mo_items;   // node-moment items (every node, up to 1024 samples), per d class
+  int mo_b[2] = {0, 0}, mo_e[2] = {0, 0};
+  bool mo_split = false;          // some node spans several moment items
+  MoItem* d_mo_items = nullptr;
   int* d_leaf_off = nullptr;
   std::vector<Tile> sample_tiles; // sampler tiles (rows per tile grow as d shrinks)
   Tile* d_sample_tiles = nullptr;
