@@ -160,12 +160,18 @@ __device__ __forceinline__ void stamp_item_end(const Dev& D, TcDev& T, int dir, 
     T.inst_t[(long long)dir * D.num_inst + b] = global_ns();
 }
 
-// Bytes of the streaming ring: two stages of (hi, lo) sample tiles, and large enough for the
-// adjoint epilogue (Z~ hi, Z~ lo, V tile of two atoms).
+// Stages of the adjoint kernel's ring of (hi, lo) parent sample chunks (192 KB either way).
+__host__ __device__ constexpr int bwd_stages(int DP) { return DP == 64 ? 6 : 3; }
+// Use index of chunk c's stage within an item (stages 0 and 1 start with the prologue).
+__host__ __device__ constexpr int bwd_use(int c, int NS) { return (c + 2) / NS - ((c + 2) % NS < 2 ? 1 : 0); }
+// Bytes of that ring: the stages, and at least the prologue operands (Z~ hi / lo, W^T hi / lo)
+// and the epilogue's (Z~ hi, Z~ lo, V tile of two atoms).
 __host__ __device__ constexpr int ring_bytes(int DP) {
-  return (4 * kRows * DP * 2 > 2 * kRows * DP * 2 + 2 * kBox) ? 4 * kRows * DP * 2
-                                                              : 2 * kRows * DP * 2 + 2 * kBox;
+  return bwd_stages(DP) * 2 * kRows * DP * 2 > 4 * kRows * DP * 2 ? bwd_stages(DP) * 2 * kRows * DP * 2
+                                                                   : 4 * kRows * DP * 2;
 }
+static_assert(ring_bytes(64) >= 2 * kRows * 64 * 2 + 2 * kBox && ring_bytes(128) >= 2 * kRows * 128 * 2 + 2 * kBox,
+              "adjoint epilogue fits in the ring");
 }  // namespace
 
 // =======================================================================================
@@ -1055,15 +1061,19 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   constexpr int NB = DP / 64;
   constexpr int KS = DP / 16;
   constexpr int GH = DP / 64;
+  constexpr int NS = bwd_stages(DP);
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  unsigned char* ring = sm;           // 2 stages x (hi, lo) of parent sample chunks
+  // NS stages x (hi, lo) of parent sample chunks.  Chunk c of an item goes to stage
+  // (c + 2) % NS: stages 0 and 1 hold the prologue operands until its MMAs complete, so the
+  // first NS - 2 chunks stream in beside them.
+  unsigned char* ring = sm;
   float* ak = reinterpret_cast<float*>(ring + ring_bytes(DP));
   // epilogue re-use of the ring / A regions
   unsigned char* eZH = ring;           // Z~_i tile hi  (N atoms at +0, +16K)
   unsigned char* eZL = ring + TB;      // Z~_i tile lo
   unsigned char* eSV = ring + 2 * TB;  // V tile (A of G, 2 atoms)
-  __shared__ uint64_t bar_pro, bar_mu, bar_A, full[2], empty[2], sfull[2], pready[2];
+  __shared__ uint64_t bar_pro, bar_mu, bar_A, full[NS], empty[NS], sfull[2], pready[2];
   __shared__ uint64_t bar_v, bar_etma, bar_eready, bar_gm;
   __shared__ uint32_t tbase;
   __shared__ float q_h[2][kRows];
@@ -1101,11 +1111,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     mbar_init(&bar_etma, 1);
     mbar_init(&bar_eready, kMath);
     mbar_init(&bar_gm, 1);
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < NS; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
-      mbar_init(&sfull[i], 1);
     }
+    for (int i = 0; i < 2; ++i) mbar_init(&sfull[i], 1);
     mbar_init(&pready[0], kMath / 2);
     mbar_init(&pready[1], kMath / 2);
     fence_barrier_init();
@@ -1140,11 +1150,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         tma_prefetch_l2_2d(&mZL, b * 64, row_n);
       }
     }
-    bool ok = mbar_wait(&bar_mu, 0);
+    bool ok = true, mu_seen = false;
     int issued = 0;
     for (int c = 0; ok && c < nch; ++c) {
-      const int s = c & 1;
-      if (c >= 2 && !mbar_wait(&empty[s], ((c >> 1) + 1) & 1)) { ok = false; break; }
+      const int s = (c + 2) % NS, ui = bwd_use(c, NS);
+      if (ui >= 1) {
+        if (!mbar_wait(&empty[s], (ui - 1) & 1)) { ok = false; break; }
+      } else if (s < 2 && !mu_seen) {  // first use of a prologue stage
+        if (!mbar_wait(&bar_mu, 0)) { ok = false; break; }
+        mu_seen = true;
+      }
       unsigned char* st = ring + s * 2 * TB;
       mbar_arrive_expect_tx(&full[s], 2 * TB);
       const int row = (int)(pn.off_nk + c * kRows);
@@ -1154,7 +1169,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       }
       issued = c + 1;
     }
-    for (int c = (issued > 2 ? issued - 2 : 0); c < issued; ++c) mbar_wait(&full[c & 1], (c >> 1) & 1);
+    for (int c = (issued > NS ? issued - NS : 0); c < issued; ++c)
+      mbar_wait(&full[(c + 2) % NS], bwd_use(c, NS) & 1);
     // epilogue operands: this CTA's own Z~ tile again
     if (ok) ok = mbar_wait(&bar_v, 0);
     if (ok) {
@@ -1184,8 +1200,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     const uint32_t id_v = idesc_f16(kRows, DP, false, false, true);
     for (int c = 0; ok && c <= nch; ++c) {
       if (c < nch) {
-        const int s = c & 1, b = c & 1;
-        if (!mbar_wait(&full[s], (c >> 1) & 1)) { ok = false; break; }
+        const int s = (c + 2) % NS, b = c & 1;
+        if (!mbar_wait(&full[s], bwd_use(c, NS) & 1)) { ok = false; break; }
         tc_fence_after();
         const uint64_t dbh = kdesc(ring + s * 2 * TB, 0), dbl = kdesc(ring + s * 2 * TB + TB, 0);
         for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kstep(dbh, kk), id_s, kk > 0);
@@ -1194,13 +1210,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         mma_commit(&sfull[b]);
       }
       if (c >= 1) {
-        const int cp = c - 1, s = cp & 1;
+        const int cp = c - 1, s = (cp + 2) % NS;
         if (!mbar_wait(&pready[cp & 1], (cp >> 1) & 1)) { ok = false; break; }
         tc_fence_after();
         const uint64_t dv = mndesc(ring + s * 2 * TB, 0);
         // V[k'][:] += sum_k P[k'][k] z~_p^k   (P: fp16 pairs in columns [0,64) of S buffer cp & 1)
         for (int kk = 0; kk < kRows / 16; ++kk)
-          mma_ts(tV, tS[s] + kk * 8, mnstep(dv, kk), id_v, (cp > 0 || kk > 0) ? 1u : 0u);
+          mma_ts(tV, tS[cp & 1] + kk * 8, mnstep(dv, kk), id_v, (cp > 0 || kk > 0) ? 1u : 0u);
         mma_commit(&empty[s]);
       }
     }
