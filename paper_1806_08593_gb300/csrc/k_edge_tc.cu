@@ -159,6 +159,10 @@ __device__ __forceinline__ void stamp_item_end(const Dev& D, TcDev& T, int dir, 
   if (atomicSub(T.inst_left + (long long)dir * D.num_inst + b, 1) == 1)
     T.inst_t[(long long)dir * D.num_inst + b] = global_ns();
 }
+// The same with the end time taken earlier.
+__device__ __forceinline__ void stamp_item_end_at(const Dev& D, TcDev& T, int dir, int b, unsigned long long t) {
+  if (atomicSub(T.inst_left + (long long)dir * D.num_inst + b, 1) == 1) T.inst_t[(long long)dir * D.num_inst + b] = t;
+}
 
 // Stages of the adjoint kernel's ring of (hi, lo) parent sample chunks (192 KB either way).
 __host__ __device__ constexpr int bwd_stages(int DP) { return DP == 64 ? 6 : 3; }
@@ -172,6 +176,10 @@ __host__ __device__ constexpr int ring_bytes(int DP) {
 }
 static_assert(ring_bytes(64) >= 2 * kRows * 64 * 2 + 2 * kBox && ring_bytes(128) >= 2 * kRows * 128 * 2 + 2 * kBox,
               "adjoint epilogue fits in the ring");
+// the G boxes (DP / 32 of them) fill stage 2, beyond the epilogue operands
+static_assert(4 * kRows * 64 * 2 >= 2 * kRows * 64 * 2 + 2 * kBox && 4 * kRows * 64 * 2 + 2 * kBox <= ring_bytes(64) &&
+                  4 * kRows * 128 * 2 >= 2 * kRows * 128 * 2 + 2 * kBox && 4 * kRows * 128 * 2 + 4 * kBox <= ring_bytes(128),
+              "adjoint G boxes fit in stage 2");
 }  // namespace
 
 // =======================================================================================
@@ -1073,14 +1081,28 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   unsigned char* eZH = ring;           // Z~_i tile hi  (N atoms at +0, +16K)
   unsigned char* eZL = ring + TB;      // Z~_i tile lo
   unsigned char* eSV = ring + 2 * TB;  // V tile (A of G, 2 atoms)
+  unsigned char* eG = ring + 4 * TB;   // G boxes: DP / 32 x [128 x 32] fp32 in stage 2
   __shared__ uint64_t bar_pro, bar_mu, bar_A, full[NS], empty[NS], sfull[2], pready[2];
-  __shared__ uint64_t bar_v, bar_etma, bar_eready, bar_gm;
+  __shared__ uint64_t bar_v, bar_etma, bar_eready, bar_gm, bar_gst;
   __shared__ uint32_t tbase;
   __shared__ float q_h[2][kRows];
+  // the records of this item and the next (slot = item iteration & 1), loaded by warp 3 while
+  // the item before runs, and whether the next item's dependency was already seen satisfied
+  __shared__ Tile s_tile[2];
+  __shared__ NodeInfo s_nd[2], s_pn[2];
+  __shared__ int s_dep[2];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float iv = D.inv_var;
+  int prev_b = -1;  // warp 3: instance and end time of the item before
+  unsigned long long prev_t = 0;
   if (warp == 2) tmem_alloc(&tbase, 512);
+  if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) {
+    s_tile[0] = tiles[blockIdx.x];
+    s_nd[0] = D.nodes[s_tile[0].node];
+    s_pn[0] = D.nodes[s_nd[0].parent];
+    s_dep[0] = 0;
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1095,14 +1117,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   const uint32_t tG = tb;
 
   // persistent loop over the edge tiles of every level, root side first
-  for (int item = blockIdx.x; item < ntiles; item += gridDim.x) {
-  const Tile t = tiles[item];
-  const NodeInfo nd = D.nodes[t.node];
-  const NodeInfo pn = D.nodes[nd.parent];
+  for (int item = blockIdx.x, iter = 0; item < ntiles; item += gridDim.x, ++iter) {
+  const int sl = iter & 1;
+  const Tile t = s_tile[sl];
+  const NodeInfo nd = s_nd[sl];
+  const NodeInfo pn = s_pn[sl];
   const int K = nd.K, nch = (K + kRows - 1) / kRows, d = nd.d;
   if (threadIdx.x == 0) {
     // the parent's sample weights must be final (the root's come from an earlier launch)
-    if (pn.parent >= 0 && !wait_count(done + nd.parent, tiles_of(pn.K))) set_timeout(D);
+    if (pn.parent >= 0 && !s_dep[sl] && !wait_count(done + nd.parent, tiles_of(pn.K))) set_timeout(D);
     stamp_item_start(T, 1, item);
     mbar_init(&bar_pro, 1);
     mbar_init(&bar_mu, 1);
@@ -1111,6 +1134,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     mbar_init(&bar_etma, 1);
     mbar_init(&bar_eready, kMath);
     mbar_init(&bar_gm, 1);
+    mbar_init(&bar_gst, kMath);
     for (int i = 0; i < NS; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
@@ -1161,6 +1185,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         mu_seen = true;
       }
       unsigned char* st = ring + s * 2 * TB;
+      if (c == 0) bulk_wait_group_read0();  // stage 2 held the last item's G boxes
       mbar_arrive_expect_tx(&full[s], 2 * TB);
       const int row = (int)(pn.off_nk + c * kRows);
       for (int b = 0; b < NB; ++b) {
@@ -1180,6 +1205,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         tma_load_2d(eZL + b * kBox, &mZL, &bar_etma, b * 64, own);
       }
       mbar_wait(&bar_etma, 0);
+    }
+    // this tile's G partial, staged by the math warps, goes out as TMA reductions; their
+    // reads of stage 2 are waited for before the next item's first chunk lands there
+    if (ok) ok = mbar_wait(&bar_gst, 0);
+    if (ok) {
+      const int y = t.node * kLdp;
+      for (int g = 0; g < DP / 32; ++g) tma_reduce_add_2d(&mG, eG + g * kBox, g * 32, y);
+      bulk_commit_group();
     }
     if (!ok) set_timeout(D);
   } else if (warp == 1 && lane == 0) {
@@ -1235,6 +1268,24 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       set_timeout(D);
       mma_commit(&bar_gm);
       mbar_wait(&bar_gm, 0);
+    }
+  } else if (warp == 3 && lane == 0) {
+    // ------------------------------------------------------------------ the last item's
+    // instance bookkeeping (an atomic round trip, off the item boundary)
+    if (prev_b >= 0) stamp_item_end_at(D, T, 1, prev_b, prev_t);
+    // ------------------------------------------------------------------ next item's records
+    // (three dependent loads) and one look at its dependency, while this item runs; if the
+    // dependency is not met yet (it may be this very item), thread 0 waits for it at the
+    // next item's start.
+    const int nx = item + (int)gridDim.x;
+    if (nx < ntiles) {
+      const Tile tn = tiles[nx];
+      const NodeInfo ndn = D.nodes[tn.node];
+      const NodeInfo pnn = D.nodes[ndn.parent];
+      s_tile[sl ^ 1] = tn;
+      s_nd[sl ^ 1] = ndn;
+      s_pn[sl ^ 1] = pnn;
+      s_dep[sl ^ 1] = pnn.parent < 0 || ld_acquire(done + ndn.parent) >= tiles_of(pnn.K);
     }
   } else if (warp >= 4) {
     // ------------------------------------------------------------------ exponentials
@@ -1361,9 +1412,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     mbar_arrive(&bar_eready);
     if (ok) ok = mbar_wait(&bar_gm, 0);
     // The tile's G partial goes to global memory as TMA reductions (the L2 adds whole
-    // lines): TMEM -> 128B-swizzled [128 x 32] fp32 boxes in the (now free) ring -> one
-    // cp.reduce.async.bulk.tensor per box.  Rows / columns past d are zero (padding of z~).
-    unsigned char* eG = ring;                        // DP / 32 boxes of 16 KB
+    // lines): TMEM -> 128B-swizzled [128 x 32] fp32 boxes in ring stage 2 (free once the V
+    // MMAs are done) -> one cp.reduce.async.bulk.tensor per box, issued by the producer.
+    // Rows / columns past d are zero (padding of z~).
     if (ok) {
       tc_fence_after();
       const int a = r;  // TMEM lane = output row a
@@ -1381,24 +1432,21 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       fence_proxy_async_smem();
     }
     tc_fence_before();
-    sync_math();  // the boxes are complete
-    if (ok && mt == 0) {
-      const int y = t.node * kLdp;
-      for (int g = 0; g < DP / 32; ++g) tma_reduce_add_2d(&mG, eG + g * kBox, g * 32, y);
-      bulk_commit_group();
-      bulk_wait_group_read0();  // the ring is reused by the next item
-    }
+    mbar_arrive(&bar_gst);  // (release) this thread's rows of the boxes are written
     if (!ok) set_timeout(D);
   }
   // item end: every role is done with this item's barriers, tensor memory and ring
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (threadIdx.x == 0) {
+  if (warp == 3 && lane == 0) {  // thread 0 goes straight on to the next item's setup
     red_release_add(done + t.node, 1);
-    stamp_item_end(D, T, 1, nd.b);
+    prev_t = global_ns();
+    prev_b = nd.b;
   }
   }  // items
+  if (warp == 3 && lane == 0 && prev_b >= 0) stamp_item_end_at(D, T, 1, prev_b, prev_t);
+  if (warp == 0 && lane == 0) bulk_wait_group0();  // the last G reductions are done
   if (warp == 2) {
     tc_fence_after();
     tmem_dealloc(tb, 512);
