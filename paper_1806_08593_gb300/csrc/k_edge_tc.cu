@@ -155,13 +155,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ void stamp_item_start(TcDev& T, int dir, int item) {
   if (item == (int)blockIdx.x) atomicMin(T.t_start + dir, global_ns());
 }
+// An instance's end time is the latest end time of its tiles (a fire-and-forget max).
 __device__ __forceinline__ void stamp_item_end(const Dev& D, TcDev& T, int dir, int b) {
-  if (atomicSub(T.inst_left + (long long)dir * D.num_inst + b, 1) == 1)
-    T.inst_t[(long long)dir * D.num_inst + b] = global_ns();
-}
-// The same with the end time taken earlier.
-__device__ __forceinline__ void stamp_item_end_at(const Dev& D, TcDev& T, int dir, int b, unsigned long long t) {
-  if (atomicSub(T.inst_left + (long long)dir * D.num_inst + b, 1) == 1) T.inst_t[(long long)dir * D.num_inst + b] = t;
+  atomicMax(T.inst_t + (long long)dir * D.num_inst + b, global_ns());
 }
 
 // Stages of the adjoint kernel's ring of (hi, lo) parent sample chunks (192 KB either way).
@@ -921,26 +917,32 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     // the item is complete) the next item's mu~ is split into A and a_full released, and only
     // then this item's messages are combined and published.
     bool ok = true;
-    // mu~ of item `it` (+ c_i) -> A operand halves; its squared norm into nrm_h[it & 1]
-    auto split = [&](int it_s) {
+    // mu~ of item `it` (+ c_i) -> A operand; its squared norm into nrm_h[it & 1].  Each group
+    // splits its half of the columns, or (all) one group splits every column and arrives on
+    // a_full for the other group's threads too.
+    auto split = [&](int it_s, bool all) {
       const int ibs = it_s % ncb;
       ok = ok && mbar_wait_ab(&cb_full[ibs], (uint32_t)((it_s / ncb) & 1), abort) &&
            mbar_wait_ab(&mu_full, (uint32_t)(it_s & 1), abort);
       tc_fence_after();
-      float nrm = 0.f;
+      // the two column halves keep separate norm partials, so the norm is the same sum
+      // whichever way the split ran (the results do not depend on the work order)
+      float nrm_lo = 0.f, nrm_hi = 0.f;  // columns [0, DP/2) and [DP/2, DP)
       if (ok) {
+        const int g0 = all ? 0 : h * GH, g1 = all ? 2 * GH : (h + 1) * GH;
 #pragma unroll 1
-        for (int gg = 0; gg < GH; ++gg) {
-          const int g = h * GH + gg;
+        for (int g = g0; g < g1; ++g) {
           uint32_t v[32];
           tmem_ld32(tMU + lane_off + g * 32, v);
           tmem_wait_ld();
-          float f[32];
+          float f[32], nrm = g >= GH ? nrm_hi : nrm_lo;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             f[j] = __uint_as_float(v[j]) + cvb[ibs][g * 32 + j];
             nrm = fmaf(f[j], f[j], nrm);
           }
+          if (g >= GH) nrm_hi = nrm;
+          else nrm_lo = nrm;
           uint32_t hi[16], lo[16];
           split_pack32(f, hi, lo);
           tmem_st16(tAH + lane_off + g * 16, hi);
@@ -949,12 +951,18 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         tmem_wait_st();
       }
       tc_fence_before();
-      nrm_h[it_s & 1][h][r] = nrm;
+      if (all) {
+        nrm_h[it_s & 1][0][r] = nrm_lo;
+        nrm_h[it_s & 1][1][r] = nrm_hi;
+      } else {
+        nrm_h[it_s & 1][h][r] = h ? nrm_hi : nrm_lo;
+      }
       mbar_arrive(&a_full);
+      if (all) mbar_arrive(&a_full);
     };
     long long gc = 0;
     int it = 0;
-    if (blockIdx.x < ntiles) split(0);
+    if (blockIdx.x < ntiles) split(0, false);
     for (int item = blockIdx.x; item < ntiles; item += gridDim.x, ++it) {
       const Tile t = tiles[item];
       const NodeInfo nd = D.nodes[t.node];
@@ -1013,19 +1021,28 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           }
         }
       }
+      // The group that does not hold the last chunk splits the next item's mu~ (every column)
+      // as soon as the last S MMAs, which read A, are complete -- while the other group still
+      // works on the last chunk.  It may do so before this item's messages are published only
+      // when the next item's message vector is already prepared (warp 3 has passed its
+      // dependency wait); otherwise the next item may depend on this one, and the split waits
+      // until after the release below.  The decision is published in s_early.
+      const bool has_next = item + (int)gridDim.x < ntiles;
+      const long long glast = gc + nch - 1;
+      const int blast = (int)(glast & 1);
+      if (h != blast) {
+        if (has_next) ok = ok && mbar_wait_ab(&sfull[blast], (uint32_t)((glast >> 1) & 1), abort);
+        if (mt == h * (kMath / 2))
+          s_early = has_next && ok && mbar_try_wait(&cb_full[(it + 1) % ncb], (uint32_t)(((it + 1) / ncb) & 1));
+        asm volatile("bar.sync 3, 128;" ::: "memory");  // this group only, whatever ok says
+        if (s_early) split(it + 1, true);
+      }
       gc += nch;
       mbar_arrive(&cb_empty[ib]);  // cb of this item is no longer read (c_i was read by its split)
       m_h[h][r] = m;
       s_h[h][r] = ssum;
-      // The next item's split may run before this item's messages are published only when its
-      // message vector is already prepared (warp 3 has passed its dependency wait); otherwise the
-      // next item may depend on this one, and the split waits until after the release below.
-      const bool has_next = item + (int)gridDim.x < ntiles;
-      if (mt == 0)
-        s_early = has_next && mbar_try_wait(&cb_full[(it + 1) % ncb], (uint32_t)(((it + 1) / ncb) & 1));
       sync_math();  // m_h / s_h complete, s_early published
       const bool early = s_early != 0;
-      if (early) split(it + 1);
       if (ok && h == 0 && k < K) {
         const float m0 = m_h[0][r], m1 = m_h[1][r];
         const float M = fmaxf(m0, m1);
@@ -1044,7 +1061,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         if (mt == 0) set_timeout(D);
         break;
       }
-      if (has_next && !early) split(it + 1);
+      if (has_next && !early) split(it + 1, false);
     }
   }
   tc_fence_before();
@@ -1094,8 +1111,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float iv = D.inv_var;
-  int prev_b = -1;  // warp 3: instance and end time of the item before
-  unsigned long long prev_t = 0;
   if (warp == 2) tmem_alloc(&tbase, 512);
   if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) {
     s_tile[0] = tiles[blockIdx.x];
@@ -1270,9 +1285,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       mbar_wait(&bar_gm, 0);
     }
   } else if (warp == 3 && lane == 0) {
-    // ------------------------------------------------------------------ the last item's
-    // instance bookkeeping (an atomic round trip, off the item boundary)
-    if (prev_b >= 0) stamp_item_end_at(D, T, 1, prev_b, prev_t);
     // ------------------------------------------------------------------ next item's records
     // (three dependent loads) and one look at its dependency, while this item runs; if the
     // dependency is not met yet (it may be this very item), thread 0 waits for it at the
@@ -1441,11 +1453,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   tc_fence_after();
   if (warp == 3 && lane == 0) {  // thread 0 goes straight on to the next item's setup
     red_release_add(done + t.node, 1);
-    prev_t = global_ns();
-    prev_b = nd.b;
+    stamp_item_end(D, T, 1, nd.b);
   }
   }  // items
-  if (warp == 3 && lane == 0 && prev_b >= 0) stamp_item_end_at(D, T, 1, prev_b, prev_t);
   if (warp == 0 && lane == 0) bulk_wait_group0();  // the last G reductions are done
   if (warp == 2) {
     tc_fence_after();
@@ -2322,8 +2332,6 @@ void workspace_layout(TcWork& w, const std::vector<NodeInfo>& nodes, long long n
   subs.push_back({(void**)&w.t.ZL, pk});
   subs.push_back({(void**)&w.t.zc, (size_t)nk * sizeof(float)});
   subs.push_back({(void**)&w.t.done, (size_t)w.num_nodes * sizeof(int)});
-  subs.push_back({(void**)&w.t.inst_left, (size_t)2 * w.num_inst * sizeof(int)});
-  subs.push_back({(void**)&w.inst_init_dev, (size_t)2 * w.num_inst * sizeof(int)});
   subs.push_back({(void**)&w.t.inst_t, (size_t)2 * w.num_inst * sizeof(unsigned long long)});
   subs.push_back({(void**)&w.t.t_start, 2 * sizeof(unsigned long long)});
   subs.push_back({(void**)&w.t.WH, pw});
@@ -2450,16 +2458,6 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&w.num_sms, cudaDevAttrMultiProcessorCount, dev);
   }
-  {  // per-instance tile counts per direction (same tiles both ways)
-    std::vector<int> init(2 * (size_t)w.num_inst, 0);
-    for (const NodeInfo& nd : nodes)
-      if (nd.parent >= 0) {
-        init[nd.b] += tiles_of(nd.K);
-        init[(size_t)w.num_inst + nd.b] += tiles_of(nd.K);
-      }
-    cudaMemcpy(w.inst_init_dev, init.data(), sizeof(int) * init.size(), cudaMemcpyHostToDevice);
-    w.t.inst_left_init = w.inst_init_dev;
-  }
   w.nonroot.clear();
   w.n_pack_w = 0;
   for (int g = 0; g < (int)nodes.size(); ++g)
@@ -2556,7 +2554,7 @@ void launch_obs(TcWork& w, const Dev& D, cudaStream_t s) {
 
 void launch_edge_fwd(TcWork& w, const Dev& D, cudaStream_t s) {
   cudaMemsetAsync(w.t.done, 0, (size_t)w.num_nodes * sizeof(int), s);
-  cudaMemcpyAsync(w.t.inst_left, w.inst_init_dev, sizeof(int) * w.num_inst, cudaMemcpyDeviceToDevice, s);
+  cudaMemsetAsync(w.t.inst_t, 0, sizeof(unsigned long long) * w.num_inst, s);
   cudaMemsetAsync(w.t.t_start, 0xFF, sizeof(unsigned long long), s);
   for (int c = 0; c < 2; ++c) {
     const int b = w.it_b[0][c], n = w.it_e[0][c] - b;
@@ -2578,8 +2576,7 @@ void launch_edge_fwd(TcWork& w, const Dev& D, cudaStream_t s) {
 void launch_edge_bwd(TcWork& w, const Dev& D, cudaStream_t s) {
   k_zero_dd<<<w.num_nodes, 256, 0, s>>>(D, w.t.G);
   cudaMemsetAsync(w.t.done, 0, (size_t)w.num_nodes * sizeof(int), s);
-  cudaMemcpyAsync(w.t.inst_left + w.num_inst, w.inst_init_dev + w.num_inst, sizeof(int) * w.num_inst,
-                  cudaMemcpyDeviceToDevice, s);
+  cudaMemsetAsync(w.t.inst_t + w.num_inst, 0, sizeof(unsigned long long) * w.num_inst, s);
   cudaMemsetAsync(w.t.t_start + 1, 0xFF, sizeof(unsigned long long), s);
   for (int c = 0; c < 2; ++c) {
     const int b = w.it_b[1][c], n = w.it_e[1][c] - b;

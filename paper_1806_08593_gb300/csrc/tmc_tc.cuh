@@ -63,9 +63,7 @@ struct TcDev {
   const int* leaf_off;         // [B + 1] leaves of instance b: leaf_off[b] .. leaf_off[b + 1]
   float* S;                    // [B][128*128] sum over an instance's leaves of M2 + zbar m^T
   int* done;                   // [nodes] tiles finished per node in the running edge launch
-  int* inst_left;              // [2][B] edge tiles still to run per instance (fwd, adjoint)
-  const int* inst_left_init;   // [2][B] their initial values
-  unsigned long long* inst_t;  // [2][B] %globaltimer when an instance's last tile finished
+  unsigned long long* inst_t;  // [2][B] %globaltimer when an instance's last tile finished (fwd, adjoint)
   unsigned long long* t_start; // [2]    %globaltimer at the first tile of each launch
   int shared;
 };
@@ -86,7 +84,6 @@ struct TcWork {
   std::vector<int> nonroot;
   int* d_nonroot = nullptr;
   int maxK = 0;
-  int* inst_init_dev = nullptr;  // workspace copy of the per-instance tile counts
   int schedule = 0;               // work order of the persistent launches (see build_items)
   int maxdp = 128;                // widest padded latent dimension (64 or 128)
   int n_pack_w = 0;               // leading non-root nodes whose W is packed
