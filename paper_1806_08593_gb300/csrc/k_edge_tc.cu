@@ -2029,40 +2029,87 @@ __global__ void __launch_bounds__(kThreads) k_ctc(Dev D, TcDev T) {
 //   root : Sg -= (zbar + m_0 - bias_0)/var,  Tg -= (diag M2 + (m_0 - bias_0) zbar)/var,
 //          dbias_0 = grad_out (zbar + m_0 - bias_0)/var
 //   leaf : Sg += C^T (x~ - C zbar)/obs_var,  Tg += ((C^T x~) zbar - diag(C^T C M2))/obs_var
-__global__ void __launch_bounds__(128) k_asm_node(Dev D, TcDev T) {
+// One CTA of P x 128 threads per node: thread (part, j) owns latent entry j; with P > 1 the
+// leaf sums over the observation rows and over C^T C's rows are split P ways and reduced in
+// shared memory, so wide leaves do not run long serial loops.
+template <int P>
+__global__ void __launch_bounds__(P * kTcMaxD) k_asm_node(Dev D, TcDev T) {
   __shared__ float xs[kMaxD];
   __shared__ float zb[kTcMaxD], ctx[kTcMaxD];
-  __shared__ float qred[4];
+  __shared__ float qred[P * kTcMaxD / 32];
+  __shared__ float part_a[P][kTcMaxD], part_b[P][kTcMaxD];
   const int g = blockIdx.x;
   const NodeInfo nd = D.nodes[g];
   const int d = nd.d, K = nd.K;
   const float go = D.grad_out ? (float)D.grad_out[nd.b] : 1.f;
   const float* M2 = T.M2 + (long long)g * kLdp * kLdp;
-  const int j = threadIdx.x;
+  const int tid = threadIdx.x, j = tid % kTcMaxD, part = tid / kTcMaxD;
   float qs = 0.f;
-#pragma unroll 8
-  for (int k = j; k < K; k += blockDim.x) qs += __ldg(D.q + nd.off_nk + k);
+#pragma unroll 4
+  for (int k = tid; k < K; k += P * kTcMaxD) qs += __ldg(D.q + nd.off_nk + k);
   for (int o = 16; o > 0; o >>= 1) qs += __shfl_xor_sync(0xffffffffu, qs, o);
-  if ((j & 31) == 0) qred[j >> 5] = qs;
-  if (j < d) zb[j] = __ldg(T.zbar + (long long)g * kLdp + j);
+  if ((tid & 31) == 0) qred[tid >> 5] = qs;
+  if (part == 0 && j < d) zb[j] = __ldg(T.zbar + (long long)g * kLdp + j);
   const bool leaf = nd.leaf_slot >= 0, root = nd.parent < 0;
   if (leaf)  // x~ = x - C m, formed in the forward pass
-    for (int o = j; o < nd.obs; o += blockDim.x) xs[o] = __ldg(T.xs + nd.off_x + o);
+    for (int o = tid; o < nd.obs; o += P * kTcMaxD) xs[o] = __ldg(T.xs + nd.off_x + o);
   __syncthreads();
-  const float qtot = qred[0] + qred[1] + qred[2] + qred[3];
-  if (leaf && j < d) {
+  float qtot = 0.f;
+#pragma unroll
+  for (int w = 0; w < P * kTcMaxD / 32; ++w) qtot += qred[w];
+  float czb = 0.f, dg = 0.f;
+  if (leaf) {
+    // (C^T x~)[j] over this part's observation rows
     float s0 = 0.f, s1 = 0.f;
-    const float* c = D.C + nd.off_C + j;
+    if (j < d) {
+      const int ob = (nd.obs * part) / P, oe = (nd.obs * (part + 1)) / P;
+      const float* c = D.C + nd.off_C + j;
+      int o = ob;
 #pragma unroll 4
-    for (int o = 0; o < nd.obs - 1; o += 2) {
-      s0 = fmaf(__ldg(c + (long long)o * d), xs[o], s0);
-      s1 = fmaf(__ldg(c + (long long)(o + 1) * d), xs[o + 1], s1);
+      for (; o + 1 < oe; o += 2) {
+        s0 = fmaf(__ldg(c + (long long)o * d), xs[o], s0);
+        s1 = fmaf(__ldg(c + (long long)(o + 1) * d), xs[o + 1], s1);
+      }
+      if (o < oe) s0 = fmaf(__ldg(c + (long long)o * d), xs[o], s0);
+      // (C^T C zbar)[j] and (C^T C M2)[j][j] over this part's rows of C^T C (symmetric: row
+      // j read as column j, coalesced over threads)
+      const float* ctc = T.CtC + (long long)(D.shared ? 0 : nd.b) * kLdp * kLdp;
+      const int ab = (d * part) / P, ae = (d * (part + 1)) / P;
+#pragma unroll 4
+      for (int a = ab; a < ae; ++a) {
+        const float v = __ldg(ctc + (long long)a * kLdp + j);
+        czb = fmaf(v, zb[a], czb);
+        dg = fmaf(v, __ldg(M2 + (long long)a * kLdp + j), dg);
+      }
     }
-    if (nd.obs & 1) s0 = fmaf(__ldg(c + (long long)(nd.obs - 1) * d), xs[nd.obs - 1], s0);
-    ctx[j] = s0 + s1;
+    if (P == 1) {
+      ctx[j] = s0 + s1;
+    } else {
+      part_a[part][j] = s0 + s1;
+      part_b[part][j] = czb;
+      __syncthreads();
+      if (part == 0) {
+        float c = 0.f, z = 0.f;
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          c += part_a[q][j];
+          z += part_b[q][j];
+        }
+        ctx[j] = c;
+        czb = z;
+      }
+      __syncthreads();  // part_a reused for dg
+      part_a[part][j] = dg;
+      __syncthreads();
+      if (part == 0) {
+        float t = 0.f;
+#pragma unroll
+        for (int q = 0; q < P; ++q) t += part_a[q][j];
+        dg = t;
+      }
+    }
   }
-  __syncthreads();
-  if (j >= d) return;
+  if (part != 0 || j >= d) return;
   float Sg = 0.f, Tg = 0.f;
   if (!root) {
     Sg += T.sgC[(long long)g * kLdp + j];
@@ -2086,15 +2133,6 @@ __global__ void __launch_bounds__(128) k_asm_node(Dev D, TcDev T) {
       for (int e = j; e < d * d; e += d) D.dW[nd.off_W + e] = 0.f;
   }
   if (leaf) {
-    // C^T C is symmetric: row j read as column j (coalesced over threads)
-    const float* ctc = T.CtC + (long long)(D.shared ? 0 : nd.b) * kLdp * kLdp;
-    float czb = 0.f, dg = 0.f;
-#pragma unroll 8
-    for (int a = 0; a < d; ++a) {
-      const float v = __ldg(ctc + (long long)a * kLdp + j);
-      czb = fmaf(v, zb[a], czb);
-      dg = fmaf(v, __ldg(M2 + (long long)a * kLdp + j), dg);
-    }
     Sg += (ctx[j] - czb) * D.inv_obs_var;
     Tg += (ctx[j] * zb[j] - dg) * D.inv_obs_var;
   }
@@ -2616,7 +2654,8 @@ void launch_unpack_grads(TcWork& w, const Dev& D, cudaStream_t s) {
     k_asm_edge_vec<<<nr, 128, 0, s>>>(D, w.t, w.d_nonroot);
     k_asm_edge_mat<<<dim3(nr, w.maxdp > 64 ? 4 : 1), kThreads, 0, s>>>(D, w.t, w.d_nonroot);
   }
-  k_asm_node<<<D.num_nodes, 128, 0, s>>>(D, w.t);
+  if (w.maxdp > 64) k_asm_node<4><<<D.num_nodes, 4 * kTcMaxD, 0, s>>>(D, w.t);
+  else k_asm_node<1><<<D.num_nodes, kTcMaxD, 0, s>>>(D, w.t);
   k_leaf_S<<<dim3(D.num_inst, w.maxdp > 64 ? 4 : 1), kThreads, 0, s>>>(D, w.t);
   k_asm_dC<<<dim3(D.num_inst, (w.maxobs + kTile - 1) / kTile, w.maxdp / kTile), kThreads, 0, s>>>(D, w.t);
 }
