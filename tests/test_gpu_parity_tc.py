@@ -47,6 +47,8 @@ def test_config1_tc():
     (4, 128, 128, 256, 2),    # exact tiles, d = 128
     (1, 77, 9, 5, 3),         # single latent
     (6, 1, 3, 4, 2),          # K = 1
+    (3, 1100, 24, 40, 2),     # K > 1024: node moments over two items (atomics), ragged unit
+    (2, 1300, 100, 64, 1),    # the same in the 128-wide class
 ])
 def test_chains_tc(n, K, d, obs, B):
     _check(wl.make_chain(n, K, d, obs, B, seed=2000 + n * 7 + K + d), grad_out=np.linspace(0.5, 1.5, B))
