@@ -1469,14 +1469,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 // With the samples as the contraction index, A = (q Z~)^T and B = Z~ are MN-major views of
 // [samples x DP] fp16 tiles; zbar is the same A against a B whose first column is 1.  q z~ and
 // z~ are both split (hi + lo), which keeps about 22 bits.
-// Work moves in units of 64 samples: TMA streams each unit's Z~ hi / lo into an NS-stage ring,
-// warps 0-7 form the unit's q Z~ into one of NQ buffers, warp 9 issues its MMAs, warp 8 the
-// TMA.  An item (up to kMoSlabs x 128 samples of one node) accumulates in one of two TMEM
-// accumulators (M2 in columns [0, DP), zbar in column DP); its epilogue (TMEM -> vector
-// atomics into M2 and zbar, rows a < d, columns < d) runs a few units into the next item,
-// under that item's MMAs.
-// Shared-memory bandwidth bounds this kernel (TMA writes, the q Z~ pass, the operand reads of
-// the MMAs), so every MMA reads its A once against as wide a B as fits: each ring stage holds
+// Work moves in units of 64 samples: the producer warp streams each unit's Z~ hi / lo (TMA)
+// and its weights into an NS-stage ring, the math warps form the unit's q Z~ into one of NQ
+// buffers, the MMA warp issues its products.  An item (up to kMoSlabs x 128 samples of one
+// node) accumulates in one of two TMEM accumulators; four epilogue warps store its M2 and zbar
+// (rows a < d, columns < d) while the next item's units run.
+// Both MMA operands come from shared memory (about twice the cycles of a TMEM-operand MMA),
+// and those MMAs bound the kernel, so every MMA reads its A once against as wide a B as fits: each ring stage holds
 // a constant ones atom next to the Z~ atoms, and B = [Z~ hi | Z~ lo | 1] (DP = 64, N = 144)
 // or [Z~ hi | 1] (DP = 128, N = 144) plus Z~ lo (N = 128).
 // DP = 64: hi and lo of q Z~ are stacked along M (A rows 0-63 hi, 64-127 lo): one MMA per
@@ -1485,8 +1484,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 // entries of q z~, hi and lo in separate tiles, three MMAs per K-step.
 // =======================================================================================
 constexpr int kMoSlabs = 8;
-constexpr int kMoThreads = 448;
-constexpr int kMoMath = 256;
+constexpr int kMoMath = 256;                 // math warps 0-7
+constexpr int kMoProd = kMoMath / 32;        // producer warp; the MMA warp follows, then 4 epilogue warps
+constexpr int kMoThreads = kMoMath + 6 * 32;
 constexpr int kMoPrefetch = 6;               // units prefetched into L2 ahead of the ring loads
 constexpr int kMoUnit = 64;                  // samples per unit
 constexpr int kMoAtom = kMoUnit * 128;       // one 64-row, 128-byte-swizzled atom
@@ -1537,7 +1537,7 @@ __global__ void __launch_bounds__(kMoThreads, 1)
   __shared__ int abort_;
   volatile int* abort = &abort_;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp == 9) tmem_alloc(&tbase, 512);
+  if (warp == kMoProd + 1) tmem_alloc(&tbase, 512);
   // the ones atom of every stage: row k = (1, 0, ..., 0)
   for (int i = threadIdx.x; i < NS * kMoUnit * 8; i += blockDim.x) {
     const int r = i % kMoUnit, ch = (i / kMoUnit) % 8, st = i / (kMoUnit * 8);
@@ -1567,7 +1567,7 @@ __global__ void __launch_bounds__(kMoThreads, 1)
   tc_fence_after();
   const uint32_t tb = tbase;
 
-  if (warp == 8) {
+  if (warp == kMoProd) {
     // ---------------- producer: 64-sample units of Z~ hi / lo into the ring (TMA, lane 0) and
     // their sample weights into qs (the whole warp, loaded ahead of the wait for the stage).
     // The warp loads the records of its next 32 items at once (lane i: item i).
@@ -1648,7 +1648,7 @@ __global__ void __launch_bounds__(kMoThreads, 1)
     // the copies still in flight land before the CTA leaves (bounded)
     if (lane == 0)
       for (int i = gu - 1; i >= 0 && i >= gu - NS; --i) mbar_wait(&full[i % NS], (uint32_t)((i / NS) & 1));
-  } else if (warp == 9) {
+  } else if (warp == kMoProd + 1) {
     // ---------------- MMA issuer
     if (lane == 0) {
       const uint32_t id_w = idesc_f16(kRows, 144, false, true, true);  // [hi | lo | 1] or [hi | 1]
@@ -1694,8 +1694,8 @@ __global__ void __launch_bounds__(kMoThreads, 1)
         mbar_wait(&fin, 0);
       }
     }
-  } else if (warp < 8) {
-    // ---------------- warps 0-7: q Z~ units (thread: sample rr of the unit, chunk group cq).
+  } else if (warp < kMoProd) {
+    // ---------------- math warps: q Z~ units (thread: sample rr of the unit, chunk group cq).
     const int rr = threadIdx.x & (kMoUnit - 1), cq = threadIdx.x / kMoUnit;
     bool ok = true;
     int gu = 0, it = 0;
@@ -1742,8 +1742,8 @@ __global__ void __launch_bounds__(kMoThreads, 1)
     }
     if (!ok) set_timeout(D);
   } else {
-    // ---------------- warps 10-13: the epilogue of every item, in item order, as soon as its
-    // accumulator is complete (TMEM lane quarter = warp % 4).
+    // ---------------- epilogue warps: every item, in item order, as soon as its accumulator
+    // is complete (TMEM lane quarter = warp % 4; the four warps cover the four quarters).
     bool ok = true;
     // Epilogue of an item: TMEM lane a holds row a of M2 in columns [0, DP) (DP = 64: the sum
     // of column blocks [0, 64) and [64, 128), and lanes 64-127 the lo-half partial of row
@@ -1849,7 +1849,7 @@ __global__ void __launch_bounds__(kMoThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 9) {
+  if (warp == kMoProd + 1) {
     tc_fence_after();
     tmem_dealloc(tb, 512);
   }
