@@ -4,25 +4,27 @@
 // z~ = z - m_i and conditional means mu~^k = W_i z~_p^k + c_i (c_i = W_i m_p + bias_i - m_i):
 //   log P(z_i^{k'} | z_p^k) = (mu~^k . z~^{k'} - |z~^{k'}|^2/2 - |mu~^k|^2/2) / var + const.
 //
-// Forward (k_edge_fwd_tc): a CTA owns 128 parent samples k.  Prologue: mu~ tile = Z~_p W_i^T
-//   on the tensor core (split operands), + c_i, |mu~|^2 in FP32, split again into the
-//   A operand.  Main loop over 128-sample chunks of the child: S = mu~ z~^T (3 split MMAs into
-//   TMEM, double-buffered), then 4 warps run an online log-sum-exp over k' (base 2) giving
-//   lam_i[k] = log sum_k' exp(F[k,k'] + beta_i[k']).
+// Forward (k_edge_fwd_tc): an item is 128 parent samples k of one edge.  Prologue: mu~ tile =
+//   Z~_p W_i^T on the tensor core (split operands), + c_i, |mu~|^2 in FP32, split again into
+//   the A operand.  Main loop over 128-sample chunks of the child: S = mu~ z~^T (3 split MMAs
+//   into TMEM, double-buffered), then the math warps run an online log-sum-exp over k' (base
+//   2) giving lam_i[k] = log sum_k' exp(F[k,k'] + beta_i[k']).
 //
-// Adjoint (k_edge_bwd_tc): a CTA owns 128 child samples k'.  With the weight of an entry
+// Adjoint (k_edge_bwd_tc): an item is 128 child samples k'.  With the weight of an entry
 //   pi[k,k'] = q_p[k] exp(F[k,k'] + beta_i[k'] - lam_i[k])  (Section 2.2, d log P / d log f),
 //   S^T[k',k] = (Z~_i W_i)[k'] . z~_p^k is formed from A' = Z~_i W_i (prologue) against chunks
 //   of the parent's samples; the CTA accumulates
 //     q_i[k']  = sum_k pi                    (row sums, in registers)
 //     V[k']    = sum_k pi z~_p^k             (tensor core, P from TMEM)
-//   and its epilogue reduces   G_i  = sum_k' V[k'] z~_i^{k'T}  (edge moment)
-//                              M2_i = sum_k' q_i[k'] z~_i^{k'} z~_i^{k'T},  zbar_i = sum q z~
-//   into global accumulators.  All parameter and proposal gradients follow from these d x d
-//   moments (k_asm_*), so no K x d gradient tensor is formed.
+//   and its epilogue adds the edge moment  G_i = sum_k' V[k'] z~_i^{k'T}  into a global
+//   accumulator (TMA reductions).  The node moments M2_i = sum_k' q_i[k'] z~_i^{k'} z~_i^{k'T}
+//   and zbar_i = sum q z~ come from k_moments_tc; every parameter and proposal gradient
+//   follows from these d x d moments (k_asm_*), so no K x d gradient tensor is formed.
 //
-// Roles (256 threads): warp 0 issues TMA, warp 1 issues MMAs, warp 2 owns the TMEM
-// allocation, warps 4..7 (128 threads, one sample row each) run the exponentials.
+// Both edge kernels are persistent (one CTA per SM, 384 threads): warp 0 issues TMA, warp 1
+// issues MMAs, warp 2 owns the TMEM allocation, warp 3 prepares per-item vectors (forward:
+// messages of the next item; adjoint: the next item's records), warps 4..11 (two groups of 128
+// threads, one sample row each) run the exponentials on alternate chunks.
 // Every mbarrier wait is bounded; on a timeout the kernel records kErrTimeout and winds down.
 #include <algorithm>
 #include <cstdio>
