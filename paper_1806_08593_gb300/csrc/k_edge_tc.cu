@@ -1096,10 +1096,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   // first NS - 2 chunks stream in beside them.
   unsigned char* ring = sm;
   float* ak = reinterpret_cast<float*>(ring + ring_bytes(DP));
-  // epilogue re-use of the ring / A regions
-  unsigned char* eZH = ring;           // Z~_i tile hi  (N atoms at +0, +16K)
-  unsigned char* eZL = ring + TB;      // Z~_i tile lo
-  unsigned char* eSV = ring + 2 * TB;  // V tile (A of G, 2 atoms)
   unsigned char* eG = ring + 4 * TB;   // G boxes: DP / 32 x [128 x 32] fp32 in stage 2
   __shared__ uint64_t bar_pro, bar_mu, bar_A, full[NS], empty[NS], sfull[2], pready[2];
   __shared__ uint64_t bar_v, bar_etma, bar_eready, bar_gm, bar_gst;
@@ -1140,6 +1136,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   const NodeInfo nd = s_nd[sl];
   const NodeInfo pn = s_pn[sl];
   const int K = nd.K, nch = (K + kRows - 1) / kRows, d = nd.d;
+  // Epilogue operands in the ring.  With 3 or more chunks this CTA's own Z~ tile is loaded
+  // into the stage of chunk nch - 3 as soon as its V MMAs are done (no later chunk uses that
+  // stage), under the last two chunks, and the V tile goes to the last chunk's stage; with
+  // fewer chunks both sit at the ring start, loaded after every V MMA.
+  const bool early_ez = nch >= 3;
+  unsigned char* eZH = early_ez ? ring + ((nch - 1) % NS) * 2 * TB : ring;  // Z~_i hi (N atoms)
+  unsigned char* eZL = eZH + TB;                                            // Z~_i lo
+  unsigned char* eSV = early_ez ? ring + ((nch + 1) % NS) * 2 * TB : ring + 2 * TB;  // V tile
   if (threadIdx.x == 0) {
     // the parent's sample weights must be final (the root's come from an earlier launch)
     if (pn.parent >= 0 && !s_dep[sl] && !wait_count(done + nd.parent, tiles_of(pn.K))) set_timeout(D);
@@ -1211,18 +1215,30 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       }
       issued = c + 1;
     }
-    for (int c = (issued > NS ? issued - NS : 0); c < issued; ++c)
-      mbar_wait(&full[(c + 2) % NS], bwd_use(c, NS) & 1);
-    // epilogue operands: this CTA's own Z~ tile again
-    if (ok) ok = mbar_wait(&bar_v, 0);
-    if (ok) {
+    // epilogue operands: this CTA's own Z~ tile again (early: once V(nch - 3) is done)
+    auto load_ez = [&]() {
       mbar_arrive_expect_tx(&bar_etma, 2 * TB);
       for (int b = 0; b < NB; ++b) {
         tma_load_2d(eZH + b * kBox, &mZH, &bar_etma, b * 64, own);
         tma_load_2d(eZL + b * kBox, &mZL, &bar_etma, b * 64, own);
       }
-      mbar_wait(&bar_etma, 0);
+    };
+    bool ez_issued = false;
+    if (ok && early_ez) {
+      ok = mbar_wait(&empty[(nch - 1) % NS], bwd_use(nch - 3, NS) & 1);
+      if (ok) {
+        load_ez();
+        ez_issued = true;
+      }
     }
+    for (int c = (issued > NS ? issued - NS : 0); c < issued; ++c)
+      mbar_wait(&full[(c + 2) % NS], bwd_use(c, NS) & 1);
+    if (ok) ok = mbar_wait(&bar_v, 0);
+    if (ok && !ez_issued) {
+      load_ez();
+      ez_issued = true;
+    }
+    if (ez_issued) ok = mbar_wait(&bar_etma, 0) && ok;
     // this tile's G partial, staged by the math warps, goes out as TMA reductions; their
     // reads of stage 2 are waited for before the next item's first chunk lands there
     if (ok) ok = mbar_wait(&bar_gst, 0);
