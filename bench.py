@@ -288,9 +288,9 @@ def time_plan_steps(p, precision, dev, steps, warmup):
 
 # DRAM bytes per 128-row edge tile of the persistent edge kernels, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of chain n=3, K=1024, d=128, obs=256, B=64:
-# 1024 tiles per launch, forward 113.7 MB, adjoint 125.7 MB.  Scaled by the tiles of a launch;
+# 1024 tiles per launch, forward 113.2 MB, adjoint 126.2 MB.  Scaled by the tiles of a launch;
 # only quoted for that K and d, and only while the kernels are the captured ones.
-TRAFFIC_PER_TILE = {("edge_fwd", 1024, 128): 113.7e6 / 1024, ("edge_bwd", 1024, 128): 125.7e6 / 1024}
+TRAFFIC_PER_TILE = {("edge_fwd", 1024, 128): 113.2e6 / 1024, ("edge_bwd", 1024, 128): 126.2e6 / 1024}
 
 
 def edge_tiles(p):
