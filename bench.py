@@ -47,12 +47,19 @@ def load_peaks():
 
 
 def make_workload(name):
-    """A named workload, or 'chain:n=..,K=..,d=..,obs=..,B=..' (same generator, seed 1)."""
+    """A named workload, 'chain:n=..,K=..,d=..,obs=..,B=..' (same generator, seed 1), or
+    'star:N=..,K=..,d=..,B=..' (one latent with N observed children)."""
     from paper_1806_08593_gb300 import workload as wl
     if name in wl.CHAIN_CONFIGS:
         return wl.chain_config(name)
     if name.startswith("trees"):
         return wl.tree_batch()
+    if name.startswith("star:"):  # the Section 3.1 toy at scale: N children of one latent
+        kv = dict(x.split("=") for x in name[5:].split(","))
+        c = {k: int(v) for k, v in kv.items()}
+        p = wl.star(c["N"], c["K"], c.get("d", 1), c.get("obs"), c.get("B", 1))
+        p.name = name
+        return p
     if name.startswith("chain:"):
         kv = dict(x.split("=") for x in name[6:].split(","))
         c = {k: int(v) for k, v in kv.items()}

@@ -2127,17 +2127,39 @@ __global__ void __launch_bounds__(P * kTcMaxD) k_asm_node(Dev D, TcDev T) {
       }
     }
   }
+  // the children's edge sums (a node may have thousands of children): thread t takes entry
+  // t % d of children t / d, t / d + G, ... (G = blockDim / d); the partials are then summed in
+  // a fixed order (a node with children is no leaf, so part_a / part_b are free)
+  float csg = 0.f, ctg = 0.f;
+  if (nd.child_end > nd.child_begin) {
+    const int G = (P * kTcMaxD) / d, jj = tid % d, grp = tid / d;
+    float* pa = &part_a[0][0];
+    float* pb = &part_b[0][0];
+    float a = 0.f, b = 0.f;
+    if (grp < G)
+#pragma unroll 4
+      for (int ci = nd.child_begin + grp; ci < nd.child_end; ci += G) {
+        const int c = D.children[ci];
+        a += T.sgP[(long long)c * kLdp + jj];
+        b += T.tgP[(long long)c * kLdp + jj];
+      }
+    if (grp < G) {
+      pa[grp * d + jj] = a;
+      pb[grp * d + jj] = b;
+    }
+    __syncthreads();
+    if (part == 0 && j < d)
+      for (int g2 = 0; g2 < G; ++g2) {
+        csg += pa[g2 * d + j];
+        ctg += pb[g2 * d + j];
+      }
+  }
   if (part != 0 || j >= d) return;
-  float Sg = 0.f, Tg = 0.f;
+  float Sg = csg, Tg = ctg;
   if (!root) {
     Sg += T.sgC[(long long)g * kLdp + j];
     Tg += T.tgC[(long long)g * kLdp + j] +
           (T.cvec[(long long)g * kLdp + j] * zb[j] - M2[(long long)j * kLdp + j]) * D.inv_var;
-  }
-  for (int ci = nd.child_begin; ci < nd.child_end; ++ci) {
-    const int c = D.children[ci];
-    Sg += T.sgP[(long long)c * kLdp + j];
-    Tg += T.tgP[(long long)c * kLdp + j];
   }
   if (root) {
     const float off = D.q_mean[nd.off_q + j] - D.bias[nd.off_bias + j];
@@ -2162,11 +2184,38 @@ __global__ void __launch_bounds__(P * kTcMaxD) k_asm_node(Dev D, TcDev T) {
 //    = grad_out / obs_var * ( X - C S ),   X = sum_l x~_l (zbar_l + m_l)^T,
 //                                          S = sum_l (M2_l + zbar_l m_l^T)   (d x d)
 // k_leaf_S: grid (instance, 64x64 tile of S (2 x 2)).
+// A tile with fewer entries than threads (small d) splits the leaves instead: thread t takes
+// entry t % np of leaves t / np, t / np + G, ... (G = threads / np), and the group partials are
+// summed in a fixed order -- an instance may have thousands of leaves.
+__device__ __forceinline__ float leaf_S_entry(const Dev& D, const TcDev& T, const LeafInfo& li, int a, int c) {
+  return __ldg(T.M2 + ((long long)li.node * kLdp + a) * kLdp + c) +
+         __ldg(T.zbar + (long long)li.node * kLdp + a) * __ldg(D.q_mean + li.off_q + c);
+}
 __global__ void __launch_bounds__(kThreads) k_leaf_S(Dev D, TcDev T) {
+  __shared__ float part[kThreads];
   const InstInfo in = D.insts[blockIdx.x];
   const int d = in.d;
   const int a0 = (blockIdx.y >> 1) * kTile, b0 = (blockIdx.y & 1) * kTile;
   if (a0 >= d || b0 >= d) return;
+  const int rt = min(kTile, d - a0), ct = min(kTile, d - b0), np = rt * ct;
+  float* S = T.S + (long long)blockIdx.x * kLdp * kLdp;
+  if (np < kThreads) {
+    const int G = kThreads / np, e = threadIdx.x % np, grp = threadIdx.x / np;
+    const int a = a0 + e / ct, cc = b0 + e % ct;
+    float acc = 0.f;
+    if (grp < G)
+#pragma unroll 4
+      for (int l = T.leaf_off[blockIdx.x] + grp; l < T.leaf_off[blockIdx.x + 1]; l += G)
+        acc += leaf_S_entry(D, T, T.leaf_info[l], a, cc);
+    if (grp < G) part[grp * np + e] = acc;
+    __syncthreads();
+    if (threadIdx.x < np) {
+      float v = 0.f;
+      for (int g = 0; g < G; ++g) v += part[g * np + threadIdx.x];
+      S[(long long)a * kLdp + cc] = v;
+    }
+    return;
+  }
   const int c = threadIdx.x & 63, r0 = threadIdx.x >> 6;  // 4 rows per pass, column c
   float acc[16];
 #pragma unroll
@@ -2184,7 +2233,6 @@ __global__ void __launch_bounds__(kThreads) k_leaf_S(Dev D, TcDev T) {
       if (a < d && b0 + c < d) acc[i] += __ldg(M2 + (long long)a * kLdp + b0 + c) + __ldg(zb + a) * mb;
     }
   }
-  float* S = T.S + (long long)blockIdx.x * kLdp * kLdp;
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
     const int a = a0 + r0 + 4 * i;
@@ -2193,8 +2241,11 @@ __global__ void __launch_bounds__(kThreads) k_leaf_S(Dev D, TcDev T) {
 }
 
 // Grid: (instance, 64-row tile of observation dims, 64-col tile of latent dims).
+// X = sum_leaves x~ (zbar + m)^T is split over the leaves like k_leaf_S when the tile has
+// fewer entries than threads.
 __global__ void __launch_bounds__(kThreads) k_asm_dC(Dev D, TcDev T) {
   __shared__ TileSmem sm;
+  __shared__ float part[kThreads];
   const InstInfo in = D.insts[blockIdx.x];
   const int d = in.d, obs = in.obs;
   const int o0 = blockIdx.y * kTile, c0 = blockIdx.z * kTile;
@@ -2210,6 +2261,34 @@ __global__ void __launch_bounds__(kThreads) k_asm_dC(Dev D, TcDev T) {
                          kLdp, cols, d, sm);
   float X[4][4];
   zero_acc(X);
+  const int np = rows * cols;
+  if (np < kThreads) {
+    const int G = kThreads / np, e = threadIdx.x % np, grp = threadIdx.x / np;
+    const int o = o0 + e / cols, c = c0 + e % cols;
+    float x = 0.f;
+    if (grp < G)
+#pragma unroll 4
+      for (int l = T.leaf_off[blockIdx.x] + grp; l < T.leaf_off[blockIdx.x + 1]; l += G) {
+        const LeafInfo li = T.leaf_info[l];
+        x += __ldg(T.xs + li.off_x + o) *
+             (__ldg(T.zbar + (long long)li.node * kLdp + c) + __ldg(D.q_mean + li.off_q + c));
+      }
+    if (grp < G) part[grp * np + e] = x;
+    __syncthreads();
+    if (threadIdx.x < np) {
+      float v = 0.f;
+      for (int g = 0; g < G; ++g) v += part[g * np + threadIdx.x];
+      part[threadIdx.x] = v;  // each thread rewrites only its own group-0 entry after reading
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int oo = ty * 4 + i, cc = tx * 4 + j;
+        if (oo < rows && cc < cols) X[i][j] = part[oo * cols + cc];
+      }
+  } else
 #pragma unroll 2
   for (int l = T.leaf_off[blockIdx.x]; l < T.leaf_off[blockIdx.x + 1]; ++l) {
     const LeafInfo li = T.leaf_info[l];

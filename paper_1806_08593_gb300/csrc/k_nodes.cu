@@ -27,6 +27,16 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
   for (int i = 0; i < nw; ++i) t += red[i];
   return t;
 }
+__device__ __forceinline__ double block_max_d(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = -INFINITY;
+  for (int i = 0; i < nw; ++i) t = fmax(t, red[i]);
+  return t;
+}
 __device__ __forceinline__ float block_max_f(float v, float* red) {
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -219,42 +229,62 @@ __global__ void __launch_bounds__(kThreads) k_project(Dev D, const Tile* __restr
   }
 }
 
+constexpr int kRootThreads = 1024;
 // ---------------------------------------------------------------------------------------
 // Root: closes the sum of Eq. (is) in FP64.
-//   beta'_0 = u_0 + sum_children lam_c,  M_0 = max beta'_0,  beta_0 = beta'_0 - M_0,
+//   beta'_0 = u_0 + sum_children lam_c (FP64: a root may have thousands of children),
+//   M_0 = max beta'_0,  beta_0 = beta'_0 - M_0,
 //   log P = sum_nodes (nodeconst + M) + sum_{i>=1} (-(d/2) log(2 pi prior_var) - log K)
 //           + log sum_k exp(beta_0[k]) - log K_0,
 // and the root's sample weights q_0[k] = exp(beta_0[k] - logsumexp(beta_0)).
 // ---------------------------------------------------------------------------------------
+// The children's messages are summed by G = blockDim / K groups of threads when K < blockDim
+// (group g takes children g, g + G, ...; a root may have thousands), the group partials then
+// in a fixed order, so the result does not depend on timing.
 __global__ void k_root(Dev D) {
-  extern __shared__ float sb[];
+  extern __shared__ double sbd[];  // [K] beta'_0, then [G][Kb] group partials
   __shared__ double redd[32];
   __shared__ float redf[32];
   const InstInfo in = D.insts[blockIdx.x];
   const NodeInfo nd = D.nodes[in.node0];
   const int K = nd.K;
-  float mx = -INFINITY;
+  const int Kb = K < (int)blockDim.x ? K : (int)blockDim.x;
+  const int G = (int)blockDim.x / Kb, grp = (int)threadIdx.x / Kb, kt = (int)threadIdx.x % Kb;
+  double* part = sbd + K;
+  if (grp < G)
+    for (int k = kt; k < K; k += Kb) {
+      double v = 0.0;
+#pragma unroll 4
+      for (int c = nd.child_begin + grp; c < nd.child_end; c += G)
+        v += D.lam[D.nodes[D.children[c]].off_nk + k];
+      if (G == 1) sbd[k] = v;
+      else part[grp * Kb + kt] = v;  // K == Kb here
+    }
+  __syncthreads();
+  double mxd = -INFINITY;
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    float v = D.u[nd.off_nk + k];
-    for (int c = nd.child_begin; c < nd.child_end; ++c) v += D.lam[D.nodes[D.children[c]].off_nk + k];
-    sb[k] = v;
-    mx = fmaxf(mx, v);
+    double v = D.u[nd.off_nk + k];
+    if (G == 1) v += sbd[k];
+    else
+      for (int g = 0; g < G; ++g) v += part[g * Kb + k];
+    sbd[k] = v;
+    mxd = fmax(mxd, v);
   }
-  mx = block_max_f(mx, redf);
+  mxd = block_max_d(mxd, redd);
+  const float mx = (float)mxd;
   float s = 0.f;
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    const float b = sb[k] - mx;
-    sb[k] = b;
+    const float b = (float)(sbd[k] - mxd);
     D.beta[nd.off_nk + k] = b;
     s += expf(b);
   }
   s = block_sum_f(s, redf);
   const float lse = logf(s);
-  for (int k = threadIdx.x; k < K; k += blockDim.x) D.q[nd.off_nk + k] = expf(sb[k] - lse);
+  for (int k = threadIdx.x; k < K; k += blockDim.x) D.q[nd.off_nk + k] = expf((float)(sbd[k] - mxd) - lse);
   double acc = 0.0;
   for (int g = in.node0 + threadIdx.x; g < in.node0 + in.n; g += blockDim.x) {
     const NodeInfo ng = D.nodes[g];
-    double m = (g == in.node0) ? (double)mx : (double)D.nodemax[g];
+    double m = (g == in.node0) ? mxd : (double)D.nodemax[g];
     acc += D.nodeconst[g] + m;
     if (ng.parent >= 0) acc += -0.5 * ng.d * (kLog2Pi + log(D.prior_var)) - log((double)ng.K);
   }
@@ -594,11 +624,12 @@ void launch_obs_fwd(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s)
 void launch_project(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s) {
   if (ntiles) k_project<<<ntiles, kThreads, kMaxD * sizeof(float), s>>>(D, tiles);
 }
-void launch_root(const Dev& D, int maxK, cudaStream_t s) {
+void launch_root(const Dev& D, int maxK, int root_fanout, cudaStream_t s) {
   static bool once = (cudaFuncSetAttribute(k_root, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           kMaxK * (int)sizeof(float)), true);
+                                           (kMaxK + kRootThreads) * (int)sizeof(double)), true);
   (void)once;
-  k_root<<<D.num_inst, 256, maxK * sizeof(float), s>>>(D);
+  const int threads = root_fanout > 32 ? kRootThreads : 256;
+  k_root<<<D.num_inst, threads, (maxK + threads) * sizeof(double), s>>>(D);
 }
 void launch_node_grad(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s) {
   k_node_grad<<<ntiles, kThreads, kMaxD * sizeof(float), s>>>(D, tiles);

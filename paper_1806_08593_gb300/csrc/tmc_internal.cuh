@@ -96,7 +96,8 @@ void launch_project(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s)
 void launch_edge_fwd_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK, cudaStream_t s);
 void launch_factors_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK, cudaStream_t s);
 void launch_lse_rows_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK, cudaStream_t s);
-void launch_root(const Dev& D, int maxK, cudaStream_t s);
+// root_fanout: most children of any root (wide roots get a 1024-thread block)
+void launch_root(const Dev& D, int maxK, int root_fanout, cudaStream_t s);
 void launch_edge_bwd_rows_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK,
                               cudaStream_t s);
 void launch_edge_bwd_cols_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK,

@@ -243,6 +243,6 @@ extern "C" tmc_status tmc_log_marginal_noalloc(const tmc_problem_desc* desc, con
   launch_project(D, T + L.t_proj_b, L.t_proj_e - L.t_proj_b, s);
   for (int lv = L.maxlevel; lv >= 1; --lv)
     launch_edge_fwd_f32(D, T + L.lv_b[lv], L.lv_e[lv] - L.lv_b[lv], L.maxK, s);
-  launch_root(D, L.maxK, s);
+  launch_root(D, L.maxK, 0, s);
   return cudaGetLastError() == cudaSuccess ? TMC_OK : TMC_ERR_CUDA;
 }

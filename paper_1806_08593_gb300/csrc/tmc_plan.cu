@@ -34,6 +34,7 @@ struct tmc_plan_s {
   int B = 0, shared = 0, precision = 0;
   double prior_var = 1.0, obs_var = 1.0;
   int maxK = 0, maxd = 0, maxobs = 0, maxlevel = 0, shared_n = 0, shared_d = 0, shared_obs = 0;
+  int root_fanout = 0;  // most children of any instance's root
   long long tot_nk = 0, tot_nkd = 0, tot_q = 0, tot_W = 0;
 
   std::vector<NodeInfo> nodes;
@@ -171,6 +172,7 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
       nd.child_begin = (int)p->children.size();
       for (int c : ch[i]) p->children.push_back(node0 + c);
       nd.child_end = (int)p->children.size();
+      if (i == 0) p->root_fanout = std::max(p->root_fanout, nd.child_end - nd.child_begin);
       nd.level = level[i];
       nd.root = node0;
       nd.off_nk = off_nk + (long long)i * K;
@@ -423,7 +425,7 @@ tmc_status tmc_log_marginal(tmc_plan p, const tmc_inputs* in, double* log_phat, 
         TRY(timed(p, TMC_KC_EDGE_FWD, s, [&] { launch_edge_fwd_f32(D, T + b, e - b, p->maxK, s); }));
     }
   }
-  TRY(timed(p, TMC_KC_ROOT, s, [&] { launch_root(D, p->maxK, s); }));
+  TRY(timed(p, TMC_KC_ROOT, s, [&] { launch_root(D, p->maxK, p->root_fanout, s); }));
   p->fwd_done = true;
   p->last_in = *in;
   return TMC_OK;

@@ -330,6 +330,19 @@ def tree_batch(B: int | None = None, seed: int | None = None, **kw) -> Problem:
     return p
 
 
+def star(N: int, K: int, d: int = 1, obs: int | None = None, B: int = 1, seed: int | None = None,
+         **kw) -> Problem:
+    """The toy of Section 3.1 at scale: one global latent (the root) with N children, each
+    child observed (one observation per leaf), K samples per latent.  Per-instance models,
+    so the exact posterior comes from belief propagation (no dense factorisation)."""
+    seed = SEED_BASE + 6 if seed is None else seed
+    parent = np.array([-1] + [0] * N, dtype=np.int32)
+    obs = 2 * d if obs is None else obs
+    p = make_problem([parent] * B, [K] * B, [d] * B, [obs] * B, shared=False, seed=seed, **kw)
+    p.name = "star_N%d_K%d_d%d_B%d" % (N, K, d, B)
+    return p
+
+
 def redraw_eps(p: Problem, seed: int) -> np.ndarray:
     """Fresh proposal noise for the same model/x/proposal (used for unbiasedness checks)."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -54,6 +54,11 @@ def test_uneven_trees_fp32():
     compare(p, got, ref, TOL_LOGP_F32, TOL_GRAD)
 
 
+def test_large_star_fp32():
+    p = wl.star(2000, 128, 1, B=2, seed=1234)
+    compare(p, gpu_run(p, "fp32"), oracle_run(p), TOL_LOGP_F32, TOL_GRAD)
+
+
 def test_star_fig2_fp32():
     parent = np.array([-1] + [0] * 9, dtype=np.int32)
     p = wl.make_problem([parent] * 3, [70] * 3, [5] * 3, [7] * 3, shared=True, seed=99)

@@ -63,6 +63,11 @@ def test_star_fig2_tc():
     _check(wl.make_problem([parent] * 3, [200] * 3, [20] * 3, [7] * 3, shared=True, seed=98))
 
 
+def test_large_star_tc():
+    # the Section 3.1 toy at scale: one latent with 2000 observed children, d = 1
+    _check(wl.star(2000, 128, 1, B=2, seed=1234))
+
+
 def test_config3_tc_sampled():
     p = wl.chain_config("chain_n8_K256_d64_B128")
     idx = [0, 64, 127]
