@@ -238,7 +238,22 @@ constexpr int kRootThreads = 1024;
 //           + log sum_k exp(beta_0[k]) - log K_0,
 // and the root's sample weights q_0[k] = exp(beta_0[k] - logsumexp(beta_0)).
 // ---------------------------------------------------------------------------------------
-// The children's messages are summed by G = blockDim / K groups of threads when K < blockDim
+// A chunk of a wide root's children: their messages summed per sample, in child order.
+__global__ void __launch_bounds__(256) k_root_children(Dev D) {
+  const int4 ch = D.root_chunks[blockIdx.x];
+  const int K = D.nodes[D.insts[ch.x].node0].K;
+  double* out = D.root_part + (long long)blockIdx.x * D.root_ld;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double v = 0.0;
+#pragma unroll 4
+    for (int c = ch.y; c < ch.z; ++c) v += D.lam[D.nodes[D.children[c]].off_nk + k];
+    out[k] = v;
+  }
+}
+
+// The children's messages come from the chunk sums of k_root_children when the plan made
+// them (summed in chunk order); otherwise they are summed here by G = blockDim / K groups of
+// threads when K < blockDim
 // (group g takes children g, g + G, ...; a root may have thousands), the group partials then
 // in a fixed order, so the result does not depend on timing.
 __global__ void k_root(Dev D) {
@@ -251,7 +266,8 @@ __global__ void k_root(Dev D) {
   const int Kb = K < (int)blockDim.x ? K : (int)blockDim.x;
   const int G = (int)blockDim.x / Kb, grp = (int)threadIdx.x / Kb, kt = (int)threadIdx.x % Kb;
   double* part = sbd + K;
-  if (grp < G)
+  const bool chunked = D.root_part != nullptr;
+  if (!chunked && grp < G)
     for (int k = kt; k < K; k += Kb) {
       double v = 0.0;
 #pragma unroll 4
@@ -264,7 +280,12 @@ __global__ void k_root(Dev D) {
   double mxd = -INFINITY;
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     double v = D.u[nd.off_nk + k];
-    if (G == 1) v += sbd[k];
+    if (chunked) {
+      const int c0 = D.root_chunk_off[blockIdx.x], c1 = D.root_chunk_off[blockIdx.x + 1];
+#pragma unroll 8
+      for (int ci = c0; ci < c1; ++ci) v += D.root_part[(long long)ci * D.root_ld + k];
+    }
+    else if (G == 1) v += sbd[k];
     else
       for (int g = 0; g < G; ++g) v += part[g * Kb + k];
     sbd[k] = v;
@@ -628,7 +649,8 @@ void launch_root(const Dev& D, int maxK, int root_fanout, cudaStream_t s) {
   static bool once = (cudaFuncSetAttribute(k_root, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (kMaxK + kRootThreads) * (int)sizeof(double)), true);
   (void)once;
-  const int threads = root_fanout > 32 ? kRootThreads : 256;
+  if (D.root_part) k_root_children<<<D.root_nchunk, 256, 0, s>>>(D);
+  const int threads = (root_fanout > 32 && !D.root_part) ? kRootThreads : 256;
   k_root<<<D.num_inst, threads, (maxK + threads) * sizeof(double), s>>>(D);
 }
 void launch_node_grad(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s) {

@@ -80,6 +80,12 @@ struct Dev {
   int* err;       // device error word
   float* fac;             // unfused baseline: every edge's K x K log-factors (relative)
   const long long* fac_off;  // per node: start of its edge's block in fac
+  // roots with more than kRootChunk children: their messages are summed in chunks of children
+  // by k_root_children (one CTA per chunk) into root_part, then in a fixed order by k_root
+  const int4* root_chunks;   // per chunk: instance, first and end index into children
+  const int* root_chunk_off; // [B + 1] first chunk of each instance
+  double* root_part;         // [chunks][root_ld] partial sums over a chunk's children
+  int root_nchunk, root_ld;
 
   // outputs of the current call
   double* log_phat;
@@ -96,7 +102,9 @@ void launch_project(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s)
 void launch_edge_fwd_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK, cudaStream_t s);
 void launch_factors_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK, cudaStream_t s);
 void launch_lse_rows_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK, cudaStream_t s);
-// root_fanout: most children of any root (wide roots get a 1024-thread block)
+constexpr int kRootChunk = 64;  // children per chunk of a wide root's message sum
+// root_fanout: most children of any root (wide roots get a 1024-thread block; with chunks
+// prepared in D, the chunk sums run first)
 void launch_root(const Dev& D, int maxK, int root_fanout, cudaStream_t s);
 void launch_edge_bwd_rows_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK,
                               cudaStream_t s);

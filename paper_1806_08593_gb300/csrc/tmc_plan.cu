@@ -41,6 +41,10 @@ struct tmc_plan_s {
   std::vector<InstInfo> insts;
   std::vector<int> children, nonroot;
   std::vector<long long> fac_off;  // unfused baseline: start of each edge's K x K factor block
+  std::vector<int4> root_chunks;     // wide roots: chunks of children (instance, begin, end)
+  std::vector<int> root_chunk_off;   // [B + 1]
+  int4* d_root_chunks = nullptr;
+  int* d_root_chunk_off = nullptr;
   long long fac_total = 0;
   long long* d_fac_off = nullptr;
 
@@ -257,6 +261,19 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
 }
 
 tmc_status alloc_device(tmc_plan p) {
+  if (p->root_fanout > kRootChunk) {  // chunks of every root's children (fixed summation order)
+    p->root_chunks.clear();
+    p->root_chunk_off.assign(p->B + 1, 0);
+    for (int b = 0; b < p->B; ++b) {
+      p->root_chunk_off[b] = (int)p->root_chunks.size();
+      const NodeInfo& r = p->nodes[p->insts[b].node0];
+      for (int c = r.child_begin; c < r.child_end; c += kRootChunk)
+        p->root_chunks.push_back(int4{b, c, std::min(r.child_end, c + kRootChunk), 0});
+    }
+    p->root_chunk_off[p->B] = (int)p->root_chunks.size();
+    TRY(upload(&p->d_root_chunks, p->root_chunks));
+    TRY(upload(&p->d_root_chunk_off, p->root_chunk_off));
+  }
   TRY(upload(&p->d_nodes, p->nodes));
   TRY(upload(&p->d_insts, p->insts));
   TRY(upload(&p->d_children, p->children));
@@ -273,7 +290,7 @@ tmc_status alloc_device(tmc_plan p) {
   // layout: 256-byte aligned sub-buffers
   struct Sub { void** dst; size_t bytes; };
   float *zt, *mut, *zn, *mun, *u, *beta, *lam, *q, *nodemax, *dmu, *gz, *pW, *pbias, *pC, *fac;
-  double* nodeconst;
+  double *nodeconst, *root_part;
   std::vector<Sub> subs = {
       {(void**)&zt, sizeof(float) * nkd},      {(void**)&mut, sizeof(float) * nkd},
       {(void**)&dmu, sizeof(float) * nkd},     {(void**)&gz, sizeof(float) * nkd},
@@ -284,6 +301,7 @@ tmc_status alloc_device(tmc_plan p) {
       {(void**)&pW, sizeof(float) * nW},       {(void**)&pbias, sizeof(float) * nb},
       {(void**)&pC, sizeof(float) * nC},
       {(void**)&fac, sizeof(float) * p->fac_total},
+      {(void**)&root_part, sizeof(double) * p->root_chunks.size() * p->maxK},
   };
   std::vector<tc::TcSub> tsubs;
   p->tcw.t.shared = p->shared;
@@ -317,6 +335,11 @@ tmc_status alloc_device(tmc_plan p) {
   D.err = p->d_err;
   D.fac = p->fac_total ? fac : nullptr;
   D.fac_off = p->d_fac_off;
+  D.root_chunks = p->d_root_chunks;
+  D.root_chunk_off = p->d_root_chunk_off;
+  D.root_part = p->root_chunks.empty() ? nullptr : root_part;
+  D.root_nchunk = (int)p->root_chunks.size();
+  D.root_ld = p->maxK;
   if (tc_plan) TRY(tc::prepare(p->tcw, p->nodes, p->tiles, p->maxK, p->maxd));
   return TMC_OK;
 }
@@ -328,6 +351,8 @@ void free_plan(tmc_plan p) {
   cudaFree(p->d_nonroot);
   cudaFree(p->d_tiles);
   cudaFree(p->d_fac_off);
+  cudaFree(p->d_root_chunks);
+  cudaFree(p->d_root_chunk_off);
   cudaFree(p->d_err);
   cudaFree(p->ws);
   tc::release(p->tcw);
