@@ -47,6 +47,14 @@ def test_brute_force_star_of_fig2():
 # ---------------------------------------------------------------------------------------
 # K = 1 reduces to the single-sample (VAE) importance weight P(x, z) / Q(z) (Section 1).
 # ---------------------------------------------------------------------------------------
+def test_brute_force_star_workload():
+    # the large-star workload's generator (per-instance models, belief-propagation proposal)
+    # at a size brute force can enumerate: 3^5 combinations
+    p = wl.star(4, 3, 2, B=2, seed=31)
+    assert list(p.n) == [5, 5]
+    np.testing.assert_allclose(oracle.log_marginal(p), oracle.brute_force(p), rtol=0, atol=1e-11)
+
+
 def test_k1_is_single_sample_weight():
     rng = np.random.default_rng(3)
     parents = [wl.random_tree(rng, n, 8) for n in (1, 2, 7, 12)]
