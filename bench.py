@@ -1,7 +1,7 @@
 """TMC hot-path benchmark: forward + backward factor entries per second.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload chain_n16_K1024_d128_B64] [--precision fp32|bf16|fp16]
+                    [--workload chain_n16_K1024_d128_B64] [--precision fp32|fp16]
 
 A step is one full pass of the hot path over one batch of synthetic linear-Gaussian
 instances: samples and node terms, conditional means, the fused pairwise-factor +
@@ -180,20 +180,22 @@ def time_oracle_sample(p, target_s=15.0, max_inst=None):
     entries_per_inst = p.entries() / p.B
     n_inst, elapsed, done = 1, 0.0, 0
     t_all = 0.0
+    logp = []
     while True:
         idx = list(range(done, min(p.B, done + n_inst)))
         if not idx:
             break
         sub = oracle.subset(p, idx)
         t0 = time.perf_counter()
-        oracle.grad(sub)
+        g = oracle.grad(sub)
         dt = time.perf_counter() - t0
+        logp.extend(g["log_phat"].tolist())
         t_all += dt
         done += len(idx)
         if t_all >= target_s or done >= p.B or (max_inst and done >= max_inst):
             break
         n_inst = max(1, int(len(idx) * min(4.0, (target_s - t_all) / max(dt, 1e-3))))
-    return entries_per_inst * done / t_all, done, t_all
+    return entries_per_inst * done / t_all, done, t_all, np.array(logp)
 
 
 def run_reference(args):
@@ -340,7 +342,7 @@ def run_ours(args):
         plan.backward(t, out=grads, want=GRADS)
 
     tuned = None
-    if args.autotune and args.precision in ("fp16", "bf16"):
+    if args.autotune and args.precision == "fp16":
         from paper_1806_08593_gb300.autotune import autotune
         tuned = autotune(plan, p, t, cache_path=None)
 
@@ -390,7 +392,7 @@ def run_ours(args):
     plan.profile_enable(False)
     plan.sync_status()
     latency = None
-    if args.precision in ("fp16", "bf16"):
+    if args.precision == "fp16":
         step()
         f_us, b_us = plan.instance_times()
         latency = {"unit": "us", "fwd_p50": float(np.percentile(f_us, 50)), "fwd_p99": float(np.percentile(f_us, 99)),
@@ -496,27 +498,33 @@ def run_ours(args):
 
     # ---- CPU baseline (oracle on a bounded sample) ------------------------------------
     cpu = None
+    vs_oracle = None
     if not args.no_cpu_baseline and ws == 1:
-        v, ninst, secs = time_oracle_sample(p, target_s=args.cpu_seconds)
+        v, ninst, secs, ref_lp = time_oracle_sample(p, target_s=args.cpu_seconds)
         cpu = {"value": v, "unit": "entries/s", "cores": oracle_cores(), "kind": "oracle",
                "sample": "%d of %d instances, fwd+bwd FP64, %.1f s" % (ninst, p.B, secs)}
+        # the oracle's log P of those instances against this run's (same inputs)
+        d_lp = np.abs(out_lp.cpu().numpy()[:ninst] - ref_lp)
+        vs_oracle = {"max_abs_dlogp": float(d_lp.max()), "median_abs_dlogp": float(np.median(d_lp)),
+                     "instances": int(ninst), "tolerance": 2e-2 if args.precision == "fp16" else 1e-4}
 
     line = {
         "metric": "tmc_fwd_bwd_factor_entries_per_s", "value": value, "unit": "entries/s",
         "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16"}[args.precision],
+        "dtype": {"fp32": "f32", "fp16": "f16"}[args.precision],
         "data": "synthetic",
         "config": {"workload": args.workload, "B": int(p.B), "n": int(p.n[0]), "K": int(p.K[0]),
                    "d": int(p.d[0]), "obs": int(p.obs[0]), "precision": args.precision,
                    "cuda_graph": bool(args.graph),
-                   "schedule": plan.get_schedule() if args.precision in ("fp16", "bf16") else None,
+                   "schedule": plan.get_schedule() if args.precision == "fp16" else None,
                    "autotune": tuned,
                    "entries_per_step": entries, "grads": list(GRADS),
                    "l2": "inputs larger than L2 (eps %.0f MB per step)" % (p.eps.nbytes / 1e6),
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roof,
         "cpu_baseline": cpu,
+        "vs_oracle": vs_oracle,
         "e2e": {"value": entries * ws / (e2e_ms * 1e-3), "unit": "entries/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "fp32_path": fp32,
@@ -537,7 +545,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--precision", default=os.environ.get("TMC_BENCH_PRECISION", "fp16"),
-                    choices=["fp32", "bf16", "fp16"])
+                    choices=["fp32", "fp16"])
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--autotune", action="store_true",
                     help="time every persistent work order on the workload first and keep the fastest")

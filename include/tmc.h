@@ -49,10 +49,14 @@ typedef enum {
   TMC_ERR_STATE = 7        /* call order violated (e.g. backward before forward)           */
 } tmc_status;
 
+/* Value 1 is reserved and rejected (TMC_ERR_INVALID_ARG): single bf16 operands cannot hold the
+ * pairwise exponent to the reduced-precision tolerance (errors of 0.2-1.3 nats at K = 1024,
+ * d = 128), and a bf16 hi/lo split keeps fewer bits (16) than the fp16 split (22). */
 typedef enum {
   TMC_PREC_FP32 = 0,    /* CUDA-core FP32 contractions                                     */
-  TMC_PREC_BF16_TC = 1, /* tcgen05 tensor cores, bf16 operands, FP32 accumulate            */
-  TMC_PREC_FP16_TC = 2, /* tcgen05 tensor cores, fp16 operands, FP32 accumulate            */
+  TMC_PREC_FP16_TC = 2, /* tcgen05 tensor cores; every product feeding an exponent is formed
+                           from split fp16 operands (x = hi + lo) as hi*hi + lo*hi + hi*lo
+                           with FP32 accumulation (about 22 significant bits)             */
   TMC_PREC_FP32_UNFUSED = 3 /* FP32, every K x K log-factor written to device memory before a
                                separate row log-sum-exp pass (the materialised baseline of
                                Section 2.2's sums; adjoint as TMC_PREC_FP32)                  */
@@ -90,14 +94,18 @@ typedef struct {
 } tmc_inputs;
 
 /* Device gradient outputs (same layouts as the inputs).  Every non-NULL buffer is
- * OVERWRITTEN with d(sum_b grad_out[b] * log P_TMC_b)/d(input); NULL skips that output.
+ * OVERWRITTEN with d(sum_b grad_out[b] * log P_TMC_b)/d(input) -- whatever it held before is
+ * ignored, so the caller need not zero it; NULL skips that output.  (Overwriting rather than
+ * adding into the buffer lets a training loop reuse one set of gradient buffers per step
+ * without a memset; a caller that accumulates adds the result itself.)
  *   dz         gradient w.r.t. the samples z_i^k (proposal density evaluated at z, its
  *              parameters held fixed)
- *   deps       gradient w.r.t. the noise eps (= exp(logs) * dz), same layout as eps
  *   dq_mean, dq_logstd   reparameterisation gradients w.r.t. m_i and logs_i
- *   dW, dbias, dC        model gradients (summed over instances when shared)            */
+ *   dW, dbias, dC        model gradients (summed over instances when shared)
+ *   deps       gradient w.r.t. the noise eps (= exp(logs) * dz), same layout as eps; last, so
+ *              the fields before it keep the order dz, dq_mean, dq_logstd, dW, dbias, dC */
 typedef struct {
-  float *dz, *deps, *dq_mean, *dq_logstd, *dW, *dbias, *dC;
+  float *dz, *dq_mean, *dq_logstd, *dW, *dbias, *dC, *deps;
 } tmc_grads;
 
 /* Builds a plan: validates the description (tree shape, sizes), derives the
@@ -137,7 +145,10 @@ tmc_status tmc_backward(tmc_plan plan, const tmc_inputs* in, const double* grad_
  *   65536, sum of n_b*K_b*d_b <= 1048576, 8192 64-sample tiles; beyond them the call returns
  *   TMC_ERR_UNSUPPORTED before any device work.
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress with
- *   that device current); make that first call before any stream capture.
+ *   that device current).
+ *   A call on a stream that is being captured into a CUDA graph returns TMC_ERR_UNSUPPORTED
+ *   and enqueues nothing: each call uploads its node and tile tables from static host arrays
+ *   that the next call rewrites, so a captured upload would replay another call's tables.
  *   Every call reuses the same array, and its contents are left from the last call: calls
  *   whose GPU work overlaps (different streams or host threads) race and must be serialised.
  *   Device-side numeric errors are not reported; a non-finite input gives a non-finite result.
@@ -149,6 +160,22 @@ tmc_status tmc_log_marginal_noalloc(const tmc_problem_desc* desc, const tmc_inpu
  * since the last call (TMC_ERR_NUMERIC for non-finite values, TMC_ERR_TIMEOUT), clearing
  * them.  TMC_OK if none. */
 tmc_status tmc_plan_sync_status(tmc_plan plan, void* stream);
+
+/* Budget, in SM clock cycles, of every cross-CTA dependency wait of the persistent edge
+ * launches (a tile waiting for the tiles whose messages or weights it reads).  Default 2^31
+ * (about a second at 2 GHz); a wait that runs out makes the kernel record TMC_ERR_TIMEOUT and
+ * return.  Takes effect from the next call.  TMC_ERR_INVALID_ARG for cycles < 1.
+ *
+ * Fault injection for tests of the error paths, read from the environment variable TMC_FAULT
+ * when a plan is created (host side; nothing here makes a GPU fault, trap or hang):
+ *   "alloc"   tmc_plan_create returns TMC_ERR_NOMEM before allocating anything;
+ *   "launch"  tmc_log_marginal / tmc_backward return TMC_ERR_CUDA before enqueuing any work;
+ *   "stall"   (tensor-core plans) the persistent forward edge launch leaves out the tiles of
+ *             the deepest latent of instance 0, so its parent's tiles wait on a completion
+ *             count that never arrives: the wait runs out after the wait limit, the kernel
+ *             records the timeout and returns, and tmc_plan_sync_status reports
+ *             TMC_ERR_TIMEOUT (the results of that call are meaningless). */
+tmc_status tmc_plan_set_wait_limit(tmc_plan plan, long long cycles);
 
 /* Bytes of device workspace owned by the plan. */
 tmc_status tmc_plan_workspace_bytes(tmc_plan plan, size_t* bytes);

@@ -51,6 +51,17 @@ __device__ __forceinline__ int slot_of(const Dev& D, const NodeInfo& nd, int g) 
 
 // Named barrier among the 256 math threads (warps 4..11).
 __device__ __forceinline__ void sync_math() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// The same barrier, returning the OR of `v` over the 256 math threads (the same value in each).
+__device__ __forceinline__ bool sync_math_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 256, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
 
 // Writes 8 consecutive values of row r (columns 8*chunk .. 8*chunk+7) of a [128 x DP]
 // 128-byte-swizzled fp16 tile as hi / lo splits.
@@ -137,12 +148,13 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 __device__ __forceinline__ void red_release_add(int* p, int v) {
   asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-// Bounded wait until *p >= need (about a second of polling); false on timeout.
-__device__ __forceinline__ bool wait_count(const int* p, int need) {
+// Bounded wait until *p >= need (`limit` cycles of polling, the plan's wait limit); false on
+// timeout.
+__device__ __forceinline__ bool wait_count(const int* p, int need, long long limit) {
   if (ld_acquire(p) >= need) return true;
   const long long t0 = clock64();
   while (ld_acquire(p) < need) {
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > limit) return false;
     __nanosleep(64);
   }
   return true;
@@ -840,7 +852,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       if (lane == 0)
         for (int c = nd.child_begin; c < nd.child_end; ++c) {
           const int cg = D.children[c];
-          dep_ok = wait_count(done + cg, tiles_of(D.nodes[cg].K)) && dep_ok;
+          dep_ok = wait_count(done + cg, tiles_of(D.nodes[cg].K), D.wait_limit) && dep_ok;
         }
       dep_ok = __shfl_sync(0xffffffffu, dep_ok, 0);
       __syncwarp();  // lane 0's acquire of the counters orders the other lanes' reads below
@@ -1051,9 +1063,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         const float S = s_h[0][r] * ex2_ftz(m0 - M) + (m1 == -INFINITY ? 0.f : s_h[1][r] * ex2_ftz(m1 - M));
         D.lam[nd.off_nk + k] = (M + log2f(S)) * kLn2 - 0.5f * nrm_all * iv;
       }
-      if (!ok) *abort = 1;
-      sync_math();  // every row's message is written; m_h / s_h free for the next item
-      const bool stop = *abort != 0;  // same value in every math thread (set before the barrier)
+      // Every row's message is written; m_h / s_h are free for the next item.  Whether to stop
+      // is an OR over the math threads taken inside the barrier, so all of them take the same
+      // branch even when another role raises the abort flag meanwhile.
+      const bool stop = sync_math_or(!ok || *abort != 0);
+      if (stop) *abort = 1;
       if (mt == 0 && !stop) {
         __threadfence();  // the CTA's messages visible device-wide before the count moves
         red_release_add(done + t.node, 1);
@@ -1146,7 +1160,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   unsigned char* eSV = early_ez ? ring + ((nch + 1) % NS) * 2 * TB : ring + 2 * TB;  // V tile
   if (threadIdx.x == 0) {
     // the parent's sample weights must be final (the root's come from an earlier launch)
-    if (pn.parent >= 0 && !s_dep[sl] && !wait_count(done + nd.parent, tiles_of(pn.K))) set_timeout(D);
+    if (pn.parent >= 0 && !s_dep[sl] && !wait_count(done + nd.parent, tiles_of(pn.K), D.wait_limit))
+      set_timeout(D);
     stamp_item_start(T, 1, item);
     mbar_init(&bar_pro, 1);
     mbar_init(&bar_mu, 1);
@@ -2422,12 +2437,13 @@ void build_items(TcWork& w, const std::vector<NodeInfo>& nodes, int schedule) {
           for (int r = 0;; r += kRows) {
             bool any = false;
             for (int g : lv)
-              if (r < nodes[g].K) { w.tiles.push_back(Tile{g, r}); any = true; }
+              if (r < nodes[g].K && !(dir == 0 && g == w.stall_node)) { w.tiles.push_back(Tile{g, r}); any = true; }
             if (!any) break;
           }
         } else {
           for (int g : lv)
-            for (int r = 0; r < nodes[g].K; r += kRows) w.tiles.push_back(Tile{g, r});
+            if (!(dir == 0 && g == w.stall_node))  // (the stall fault drops one node's tiles)
+              for (int r = 0; r < nodes[g].K; r += kRows) w.tiles.push_back(Tile{g, r});
         }
       }
       w.it_e[dir][c] = (int)w.tiles.size();

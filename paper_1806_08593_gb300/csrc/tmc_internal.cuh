@@ -47,6 +47,8 @@ struct Tile {
 
 // Device-side error word bits.
 enum : int { kErrNumeric = 1, kErrTimeout = 2 };
+// Default budget of a cross-CTA dependency wait: 2^31 cycles, about a second at 2 GHz.
+constexpr long long kWaitLimitDefault = 1ll << 31;
 
 // Everything a kernel may touch, passed by value.
 struct Dev {
@@ -78,6 +80,7 @@ struct Dev {
   float* pbias;   // per-(instance, node) dbias partials (shared params only)
   float* pC;      // per-instance dC partials (shared params only)
   int* err;       // device error word
+  long long wait_limit;   // clock cycles a cross-CTA dependency wait polls before giving up
   float* fac;             // unfused baseline: every edge's K x K log-factors (relative)
   const long long* fac_off;  // per node: start of its edge's block in fac
   // roots with more than kRootChunk children: their messages are summed in chunks of children

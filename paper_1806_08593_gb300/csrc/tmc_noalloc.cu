@@ -184,6 +184,17 @@ extern "C" tmc_status tmc_log_marginal_noalloc(const tmc_problem_desc* desc, con
   if (!desc || !in || !log_phat || !in->eps || !in->q_mean || !in->q_logstd || !in->W || !in->bias ||
       !in->C || !in->x)
     return TMC_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  // Refused under stream capture: the tables below are uploaded from static host arrays that
+  // the next call rewrites, so a captured copy would replay another call's tables under this
+  // call's grid sizes.  (The legacy stream reports an implicit capture as an error.)
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+  if (ce != cudaSuccess) {
+    (void)cudaGetLastError();  // not sticky: leave no error behind for the caller
+    return ce == cudaErrorStreamCaptureImplicit ? TMC_ERR_UNSUPPORTED : TMC_ERR_CUDA;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return TMC_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_mu);
   Layout& L = h_lay;
   tmc_status st = build_tables(desc, L);
@@ -198,7 +209,6 @@ extern "C" tmc_status tmc_log_marginal_noalloc(const tmc_problem_desc* desc, con
     g_addr[dev] = p;
   }
   unsigned char* base = static_cast<unsigned char*>(g_addr[dev]);
-  cudaStream_t s = (cudaStream_t)stream;
 
   // tables -> scratch (copies from static host arrays; no staging allocation by us)
   if (cudaMemcpyAsync(base + kOffNodes, h_nodes, sizeof(NodeInfo) * L.G, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -234,6 +244,7 @@ extern "C" tmc_status tmc_log_marginal_noalloc(const tmc_problem_desc* desc, con
   D.nodemax = reinterpret_cast<float*>(base + kOffNodemax);
   D.nodeconst = reinterpret_cast<double*>(base + kOffNodeconst);
   D.err = reinterpret_cast<int*>(base + kOffErr);
+  D.wait_limit = kWaitLimitDefault;
   D.log_phat = log_phat;
 
   const Tile* T = reinterpret_cast<const Tile*>(base + kOffTiles);

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -65,6 +66,10 @@ struct tmc_plan_s {
   Dev dev{};
   tc::TcWork tcw{};
 
+  // fault injection (TMC_FAULT, read at creation) and the dependency-wait budget
+  int fault = 0;
+  long long wait_limit = kWaitLimitDefault;
+
   // state
   bool fwd_done = false;
   tmc_inputs last_in{};
@@ -80,6 +85,17 @@ struct tmc_plan_s {
 namespace {
 
 tmc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TMC_OK : TMC_ERR_CUDA; }
+
+// Host-side fault injection for tests of the error paths (nothing here makes a GPU fault).
+enum { kFaultNone = 0, kFaultAlloc = 1, kFaultLaunch = 2, kFaultStall = 3 };
+int fault_from_env() {
+  const char* f = std::getenv("TMC_FAULT");
+  if (!f) return kFaultNone;
+  if (!std::strcmp(f, "alloc")) return kFaultAlloc;
+  if (!std::strcmp(f, "launch")) return kFaultLaunch;
+  if (!std::strcmp(f, "stall")) return kFaultStall;
+  return kFaultNone;
+}
 
 void drain_profile(tmc_plan p) {
   for (size_t i = 0; i < p->slot_next; ++i) {
@@ -130,7 +146,9 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
   if (!(ds->prior_var > 0.0) || !(ds->obs_var > 0.0) || !std::isfinite(ds->prior_var) ||
       !std::isfinite(ds->obs_var))
     return TMC_ERR_INVALID_ARG;
-  if (ds->precision < TMC_PREC_FP32 || ds->precision > TMC_PREC_FP32_UNFUSED) return TMC_ERR_INVALID_ARG;
+  if (ds->precision != TMC_PREC_FP32 && ds->precision != TMC_PREC_FP16_TC &&
+      ds->precision != TMC_PREC_FP32_UNFUSED)
+    return TMC_ERR_INVALID_ARG;
   p->B = B;
   p->shared = ds->shared_params ? 1 : 0;
   p->precision = ds->precision;
@@ -261,6 +279,7 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
 }
 
 tmc_status alloc_device(tmc_plan p) {
+  if (p->fault == kFaultAlloc) return TMC_ERR_NOMEM;  // as if the first cudaMalloc failed
   if (p->root_fanout > kRootChunk) {  // chunks of every root's children (fixed summation order)
     p->root_chunks.clear();
     p->root_chunk_off.assign(p->B + 1, 0);
@@ -306,7 +325,7 @@ tmc_status alloc_device(tmc_plan p) {
   std::vector<tc::TcSub> tsubs;
   p->tcw.t.shared = p->shared;
   p->tcw.precision = p->precision;
-  const bool tc_plan = p->precision == TMC_PREC_FP16_TC || p->precision == TMC_PREC_BF16_TC;
+  const bool tc_plan = p->precision == TMC_PREC_FP16_TC;
   if (tc_plan) tc::workspace_layout(p->tcw, p->nodes, nk, nkd, tsubs);
   size_t total = 0;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -333,6 +352,7 @@ tmc_status alloc_device(tmc_plan p) {
   D.nodemax = nodemax; D.nodeconst = nodeconst; D.dmu = dmu; D.gz = gz;
   D.pW = nW ? pW : nullptr; D.pbias = nb ? pbias : nullptr; D.pC = nC ? pC : nullptr;
   D.err = p->d_err;
+  D.wait_limit = p->wait_limit;
   D.fac = p->fac_total ? fac : nullptr;
   D.fac_off = p->d_fac_off;
   D.root_chunks = p->d_root_chunks;
@@ -340,6 +360,14 @@ tmc_status alloc_device(tmc_plan p) {
   D.root_part = p->root_chunks.empty() ? nullptr : root_part;
   D.root_nchunk = (int)p->root_chunks.size();
   D.root_ld = p->maxK;
+  if (tc_plan && p->fault == kFaultStall) {
+    // the deepest non-root node of instance 0: its forward tiles are left out of the
+    // persistent launch, so its parent's tiles wait on a count that never arrives
+    for (int i = p->insts[0].n - 1; i >= 1; --i) {
+      const int g = p->insts[0].node0 + i;
+      if (p->tcw.stall_node < 0 || p->nodes[g].level > p->nodes[p->tcw.stall_node].level) p->tcw.stall_node = g;
+    }
+  }
   if (tc_plan) TRY(tc::prepare(p->tcw, p->nodes, p->tiles, p->maxK, p->maxd));
   return TMC_OK;
 }
@@ -390,8 +418,9 @@ tmc_status tmc_plan_create(const tmc_problem_desc* desc, tmc_plan* out) {
   *out = nullptr;
   tmc_plan p = new (std::nothrow) tmc_plan_s();
   if (!p) return TMC_ERR_NOMEM;
+  p->fault = fault_from_env();
   tmc_status st = build_plan(desc, p);
-  if (st == TMC_OK && (p->precision == TMC_PREC_FP16_TC || p->precision == TMC_PREC_BF16_TC))
+  if (st == TMC_OK && (p->precision == TMC_PREC_FP16_TC))
     st = tc::supported(p->nodes, p->precision);
   if (st == TMC_OK) st = alloc_device(p);
   if (st != TMC_OK) {
@@ -417,13 +446,14 @@ tmc_status tmc_plan_workspace_bytes(tmc_plan p, size_t* bytes) {
 
 tmc_status tmc_log_marginal(tmc_plan p, const tmc_inputs* in, double* log_phat, void* stream) {
   if (!p || !inputs_ok(in) || !log_phat) return TMC_ERR_INVALID_ARG;
+  if (p->fault == kFaultLaunch) return TMC_ERR_CUDA;  // as if the first launch failed
   cudaStream_t s = (cudaStream_t)stream;
   Dev D = p->dev;
   D.eps = in->eps; D.q_mean = in->q_mean; D.q_logstd = in->q_logstd;
   D.W = in->W; D.bias = in->bias; D.C = in->C; D.x = in->x;
   D.log_phat = log_phat;
   const Tile* T = p->d_tiles;
-  const bool tc_path = p->precision == TMC_PREC_FP16_TC || p->precision == TMC_PREC_BF16_TC;
+  const bool tc_path = p->precision == TMC_PREC_FP16_TC;
   TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_node_const(D, s); }));
   if (tc_path) {
     // split W_i and c_i first: the sampling kernel forms z~ . c_i, the conditional means are
@@ -460,7 +490,8 @@ tmc_status tmc_backward(tmc_plan p, const tmc_inputs* in, const double* grad_out
                         const tmc_grads* g, void* stream) {
   if (!p || !inputs_ok(in) || !g) return TMC_ERR_INVALID_ARG;
   if (!p->fwd_done || std::memcmp(&p->last_in, in, sizeof(tmc_inputs)) != 0) return TMC_ERR_STATE;
-  const bool tc_path = p->precision == TMC_PREC_FP16_TC || p->precision == TMC_PREC_BF16_TC;
+  if (p->fault == kFaultLaunch) return TMC_ERR_CUDA;
+  const bool tc_path = p->precision == TMC_PREC_FP16_TC;
   // the tensor-core adjoint reduces the factors to d x d moments and forms no per-sample
   // gradient; dz / deps are available on the FP32 path
   if (tc_path && (g->dz || g->deps)) return TMC_ERR_UNSUPPORTED;
@@ -507,9 +538,16 @@ tmc_status tmc_plan_sync_status(tmc_plan p, void* stream) {
   return TMC_OK;
 }
 
+tmc_status tmc_plan_set_wait_limit(tmc_plan p, long long cycles) {
+  if (!p || cycles < 1) return TMC_ERR_INVALID_ARG;
+  p->wait_limit = cycles;
+  p->dev.wait_limit = cycles;
+  return TMC_OK;
+}
+
 tmc_status tmc_plan_set_schedule(tmc_plan p, int schedule) {
   if (!p) return TMC_ERR_INVALID_ARG;
-  if (!(p->precision == TMC_PREC_FP16_TC || p->precision == TMC_PREC_BF16_TC)) return TMC_ERR_UNSUPPORTED;
+  if (!(p->precision == TMC_PREC_FP16_TC)) return TMC_ERR_UNSUPPORTED;
   return tc::set_schedule(p->tcw, p->nodes, schedule);
 }
 
@@ -521,7 +559,7 @@ tmc_status tmc_plan_get_schedule(tmc_plan p, int* schedule) {
 
 tmc_status tmc_plan_instance_times(tmc_plan p, double* fwd_us, double* bwd_us) {
   if (!p || (!fwd_us && !bwd_us)) return TMC_ERR_INVALID_ARG;
-  if (!(p->precision == TMC_PREC_FP16_TC || p->precision == TMC_PREC_BF16_TC)) return TMC_ERR_UNSUPPORTED;
+  if (!(p->precision == TMC_PREC_FP16_TC)) return TMC_ERR_UNSUPPORTED;
   return tc::instance_times(p->tcw, p->B, fwd_us, bwd_us);
 }
 

@@ -85,6 +85,7 @@ struct TcWork {
   int* d_nonroot = nullptr;
   int maxK = 0;
   int schedule = 0;               // work order of the persistent launches (see build_items)
+  int stall_node = -1;            // fault injection: node whose forward tiles are left out
   int maxdp = 128;                // widest padded latent dimension (64 or 128)
   int n_pack_w = 0;               // leading non-root nodes whose W is packed
   // observation term: split C rows and the 128-sample leaf tiles per d class

@@ -19,14 +19,15 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libtmc_gb300.so")
 
-PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "fp32_unfused": 3}
+PRECISIONS = {"fp32": 0, "fp16": 2, "fp32_unfused": 3}
 STATUS = {0: "TMC_OK", 1: "TMC_ERR_INVALID_ARG", 2: "TMC_ERR_UNSUPPORTED", 3: "TMC_ERR_NOMEM",
           4: "TMC_ERR_CUDA", 5: "TMC_ERR_NUMERIC", 6: "TMC_ERR_TIMEOUT", 7: "TMC_ERR_STATE"}
 KERNEL_CLASSES = ["sample", "project", "edge_fwd", "root", "edge_bwd", "param"]
 EXPORTS = ["tmc_plan_create", "tmc_log_marginal", "tmc_backward", "tmc_plan_sync_status",
            "tmc_plan_workspace_bytes", "tmc_plan_destroy", "tmc_status_string",
            "tmc_profile_enable", "tmc_profile_read", "tmc_log_marginal_noalloc",
-           "tmc_plan_instance_times", "tmc_plan_set_schedule", "tmc_plan_get_schedule"]
+           "tmc_plan_instance_times", "tmc_plan_set_schedule", "tmc_plan_get_schedule",
+           "tmc_plan_set_wait_limit"]
 
 
 class TMCError(RuntimeError):
@@ -48,7 +49,7 @@ class Inputs(ctypes.Structure):
 
 
 class Grads(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_void_p) for k in ("dz", "deps", "dq_mean", "dq_logstd", "dW", "dbias", "dC")]
+    _fields_ = [(k, ctypes.c_void_p) for k in ("dz", "dq_mean", "dq_logstd", "dW", "dbias", "dC", "deps")]
 
 
 INPUT_NAMES = [f[0] for f in Inputs._fields_]
@@ -84,6 +85,8 @@ def load_library(path: str = LIB_PATH):
     lib.tmc_plan_set_schedule.restype = ctypes.c_int
     lib.tmc_plan_get_schedule.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
     lib.tmc_plan_get_schedule.restype = ctypes.c_int
+    lib.tmc_plan_set_wait_limit.argtypes = [P, ctypes.c_longlong]
+    lib.tmc_plan_set_wait_limit.restype = ctypes.c_int
     for f in ("tmc_plan_create", "tmc_log_marginal", "tmc_backward", "tmc_plan_sync_status",
               "tmc_plan_workspace_bytes", "tmc_plan_destroy", "tmc_profile_enable", "tmc_profile_read",
               "tmc_log_marginal_noalloc"):
@@ -193,6 +196,9 @@ class Plan:
 
     def set_schedule(self, schedule: int):
         _check(self._lib.tmc_plan_set_schedule(self._h, int(schedule)), "tmc_plan_set_schedule")
+
+    def set_wait_limit(self, cycles: int):
+        _check(self._lib.tmc_plan_set_wait_limit(self._h, int(cycles)), "tmc_plan_set_wait_limit")
 
     def get_schedule(self) -> int:
         v = ctypes.c_int()

@@ -63,3 +63,18 @@ def compare(p, got, ref, tol_logp, tol_grad, keys=None):
         assert np.all(np.isfinite(got[k])), k
         assert e <= tol_grad, (k, e)
     return report
+
+
+def mixed_roots_problem(seed=31337):
+    """One batch whose instances reach the root kernel in different ways: two wide roots (100
+    and 70 children, so the plan sums every root's children in chunks), small uneven trees, a
+    chain, and a single latent (a root with no children), with a different K and d per
+    instance (so the chunk sums' row stride, the largest K, exceeds most roots' K)."""
+    from paper_1806_08593_gb300 import workload as wl
+    rng = np.random.default_rng(seed)
+    parents = [np.array([-1] + [0] * 100, dtype=np.int32), wl.random_tree(rng, 7, 3),
+               np.array([-1], dtype=np.int32), wl.chain_parents(3),
+               np.array([-1] + [0] * 70, dtype=np.int32), wl.random_tree(rng, 5, 2)]
+    Ks = [96, 40, 33, 128, 17, 64]
+    ds = [2, 5, 3, 8, 1, 70]
+    return wl.make_problem(parents, Ks, ds, [2 * d for d in ds], shared=False, seed=seed)

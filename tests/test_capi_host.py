@@ -53,6 +53,7 @@ def _desc(n, parent, K, d, obs, shared=0, pv=1.0, ov=0.1, prec=0):
     dict(n=[0], parent=[], K=[4], d=[2], obs=[2]),                 # empty instance
     dict(n=[2], parent=[-1, 0], K=[4], d=[2], obs=[2], pv=0.0),    # zero variance
     dict(n=[2], parent=[-1, 0], K=[4], d=[2], obs=[2], prec=9),    # unknown precision
+    dict(n=[2], parent=[-1, 0], K=[4], d=[2], obs=[2], prec=1),    # reserved (no bf16 path)
     dict(n=[2, 3], parent=[-1, 0, -1, 0, 0], K=[4, 4], d=[2, 2], obs=[2, 2], shared=1),  # shared mismatch
 ])
 def test_invalid_descriptions_rejected(lib, case):
@@ -78,3 +79,17 @@ def test_null_arguments(lib):
     assert lib.tmc_backward(None, None, None, None, None) == 1
     assert lib.tmc_plan_destroy(None) == 0
     assert lib.tmc_plan_sync_status(None, None) == 1
+
+
+def test_alloc_fault_is_reported(lib, monkeypatch):
+    """TMC_FAULT=alloc: plan creation fails as if the workspace allocation had, before any
+    device allocation (so this runs without a GPU)."""
+    monkeypatch.setenv("TMC_FAULT", "alloc")
+    desc, keep = _desc([3], [-1, 0, 1], [4], [2], [2])
+    h = ctypes.c_void_p()
+    assert lib.tmc_plan_create(ctypes.byref(desc), ctypes.byref(h)) == 3
+    assert not h.value
+
+
+def test_wait_limit_arguments(lib):
+    assert lib.tmc_plan_set_wait_limit(None, 1 << 20) == 1

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_1806_08593_gb300 import workload as wl
-from tests.parity import compare, gpu_run, oracle_run
+from tests.parity import compare, gpu_run, mixed_roots_problem, oracle_run
 
 pytestmark = pytest.mark.gpu
 TOL_LOGP_F32 = 1e-4
@@ -56,6 +56,11 @@ def test_uneven_trees_fp32():
 
 def test_large_star_fp32():
     p = wl.star(2000, 128, 1, B=2, seed=1234)
+    compare(p, gpu_run(p, "fp32"), oracle_run(p), TOL_LOGP_F32, TOL_GRAD)
+
+
+def test_mixed_roots_fp32():
+    p = mixed_roots_problem()
     compare(p, gpu_run(p, "fp32"), oracle_run(p), TOL_LOGP_F32, TOL_GRAD)
 
 

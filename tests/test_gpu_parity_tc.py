@@ -10,7 +10,7 @@ import pytest
 import oracle
 from paper_1806_08593_gb300 import workload as wl
 from paper_1806_08593_gb300.tmc import TMCError
-from tests.parity import compare, gpu_run, oracle_run
+from tests.parity import compare, gpu_run, mixed_roots_problem, oracle_run
 
 pytestmark = pytest.mark.gpu
 TOL_LOGP = 2e-2
@@ -66,6 +66,10 @@ def test_star_fig2_tc():
 def test_large_star_tc():
     # the Section 3.1 toy at scale: one latent with 2000 observed children, d = 1
     _check(wl.star(2000, 128, 1, B=2, seed=1234))
+
+
+def test_mixed_roots_tc():
+    _check(mixed_roots_problem())
 
 
 def test_config3_tc_sampled():

@@ -44,9 +44,6 @@ def test_brute_force_star_of_fig2():
     np.testing.assert_allclose(oracle.log_marginal(p), oracle.brute_force(p), rtol=0, atol=1e-11)
 
 
-# ---------------------------------------------------------------------------------------
-# K = 1 reduces to the single-sample (VAE) importance weight P(x, z) / Q(z) (Section 1).
-# ---------------------------------------------------------------------------------------
 def test_brute_force_star_workload():
     # the large-star workload's generator (per-instance models, belief-propagation proposal)
     # at a size brute force can enumerate: 3^5 combinations
@@ -55,6 +52,9 @@ def test_brute_force_star_workload():
     np.testing.assert_allclose(oracle.log_marginal(p), oracle.brute_force(p), rtol=0, atol=1e-11)
 
 
+# ---------------------------------------------------------------------------------------
+# K = 1 reduces to the single-sample (VAE) importance weight P(x, z) / Q(z) (Section 1).
+# ---------------------------------------------------------------------------------------
 def test_k1_is_single_sample_weight():
     rng = np.random.default_rng(3)
     parents = [wl.random_tree(rng, n, 8) for n in (1, 2, 7, 12)]
