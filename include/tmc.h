@@ -213,7 +213,8 @@ enum {
   TMC_KC_ROOT = 3,    /* root reduction to log P_TMC (FP64)                                 */
   TMC_KC_EDGE_BWD = 4,/* fused adjoint of the messages (factors recomputed)                 */
   TMC_KC_PARAM = 5,   /* parameter / proposal gradient assembly                             */
-  TMC_KC_COUNT = 6
+  TMC_KC_SAMPLE_GRAD = 6, /* per-sample gradients dz / deps beyond the above (tensor-core path) */
+  TMC_KC_COUNT = 7
 };
 /* Turns event timing of every launch on (1) or off (0); resets the accumulators. */
 tmc_status tmc_profile_enable(tmc_plan plan, int enable);

@@ -100,6 +100,13 @@ __device__ __forceinline__ void load_half8(const unsigned char* t, int r, int ch
   }
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%"
@@ -1089,10 +1096,21 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 }
 
 // =======================================================================================
-// Adjoint edge kernel.
+// Adjoint edge kernel (ROWS = false) and its row-direction twin (ROWS = true).
 // TMEM: S double buffer [0,256), V [256, 256+DP), P double buffer [384, 512) (fp16 pairs).
+//
+// ROWS: the parent-side part of the sample gradient.  An item is 128 PARENT samples k of edge
+// p -> i (tile.node = i, tile.row0 = first parent row); the prologue forms mu~ = Z~_p W_i^T + c_i
+// (the forward's A operand), the chunks run over the child's samples k', and with the weights
+// normalised per parent sample (P[k,k'] = exp(F[k,k'] + beta_i[k'] - lam_i[k]), known from the
+// forward) the same TS MMA accumulates R[k] = sum_k' P[k,k'] z~_i^{k'}.  The epilogue stores
+// E[k] = R[k] - mu~^k (split fp16) for the sample-gradient assembly (k_dz_tc), which forms
+// q_p[k] E[k] W_i (d log P / d z_p^k through this edge).  The weights of this direction need
+// nothing of the adjoint, so the items carry no dependencies.
+// In ROWS mode the mWTH / mWTL arguments carry W itself (B operand of Z~_p W_i^T) and mG is
+// unused.
 // =======================================================================================
-template <int DP>
+template <int DP, bool ROWS>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     k_edge_bwd_tc(Dev D, TcDev T, const Tile* __restrict__ tiles, int ntiles, int* __restrict__ done,
                   const __grid_constant__ CUtensorMap mZH, const __grid_constant__ CUtensorMap mZL,
@@ -1150,6 +1168,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   const NodeInfo nd = s_nd[sl];
   const NodeInfo pn = s_pn[sl];
   const int K = nd.K, nch = (K + kRows - 1) / kRows, d = nd.d;
+  // the node whose samples fill the chunks, and the node whose 128 rows the item owns
+  const NodeInfo& chn = ROWS ? nd : pn;
+  const long long own_off = ROWS ? pn.off_nk : nd.off_nk;
   // Epilogue operands in the ring.  With 3 or more chunks this CTA's own Z~ tile is loaded
   // into the stage of chunk nch - 3 as soon as its V MMAs are done (no later chunk uses that
   // stage), under the last two chunks, and the V tile goes to the last chunk's stage; with
@@ -1160,9 +1181,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   unsigned char* eSV = early_ez ? ring + ((nch + 1) % NS) * 2 * TB : ring + 2 * TB;  // V tile
   if (threadIdx.x == 0) {
     // the parent's sample weights must be final (the root's come from an earlier launch)
-    if (pn.parent >= 0 && !s_dep[sl] && !wait_count(done + nd.parent, tiles_of(pn.K), D.wait_limit))
-      set_timeout(D);
-    stamp_item_start(T, 1, item);
+    if (!ROWS) {
+      if (pn.parent >= 0 && !s_dep[sl] && !wait_count(done + nd.parent, tiles_of(pn.K), D.wait_limit))
+        set_timeout(D);
+      stamp_item_start(T, 1, item);
+    }
     mbar_init(&bar_pro, 1);
     mbar_init(&bar_mu, 1);
     mbar_init(&bar_A, kMath);
@@ -1188,13 +1211,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     // ------------------------------------------------------------------ TMA producer
     prefetch_tmap(&mZH);
     prefetch_tmap(&mZL);
-    // pull the parent's chunk with this CTA's tile index into L2 (see the forward kernel)
+    // pull the chunk with this CTA's tile index into L2 (see the forward kernel)
     for (int b = 0; b < NB; ++b) {
-      tma_prefetch_l2_2d(&mZH, b * 64, (int)(pn.off_nk + t.row0));
-      tma_prefetch_l2_2d(&mZL, b * 64, (int)(pn.off_nk + t.row0));
+      tma_prefetch_l2_2d(&mZH, b * 64, (int)(chn.off_nk + t.row0));
+      tma_prefetch_l2_2d(&mZL, b * 64, (int)(chn.off_nk + t.row0));
     }
     const int slot = slot_of(D, nd, t.node);
-    const int own = (int)(nd.off_nk + t.row0);
+    const int own = (int)(own_off + t.row0);
     mbar_arrive_expect_tx(&bar_pro, 4 * TB);
     for (int b = 0; b < NB; ++b) {
       tma_load_2d(ring + b * kBox, &mZH, &bar_pro, b * 64, own);
@@ -1204,7 +1227,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     }
     if (item + (int)gridDim.x < ntiles) {  // next item's own tile into L2 while this one runs
       const Tile tn = tiles[item + gridDim.x];
-      const int row_n = (int)(D.nodes[tn.node].off_nk + tn.row0);
+      const NodeInfo& nn = D.nodes[tn.node];
+      const int row_n = (int)((ROWS ? D.nodes[nn.parent].off_nk : nn.off_nk) + tn.row0);
       for (int b = 0; b < NB; ++b) {
         tma_prefetch_l2_2d(&mZH, b * 64, row_n);
         tma_prefetch_l2_2d(&mZL, b * 64, row_n);
@@ -1221,15 +1245,21 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         mu_seen = true;
       }
       unsigned char* st = ring + s * 2 * TB;
-      if (c == 0) bulk_wait_group_read0();  // stage 2 held the last item's G boxes
+      if (!ROWS && c == 0) bulk_wait_group_read0();  // stage 2 held the last item's G boxes
       mbar_arrive_expect_tx(&full[s], 2 * TB);
-      const int row = (int)(pn.off_nk + c * kRows);
+      const int row = (int)(chn.off_nk + c * kRows);
       for (int b = 0; b < NB; ++b) {
         tma_load_2d(st + b * kBox, &mZH, &full[s], b * 64, row);
         tma_load_2d(st + TB + b * kBox, &mZL, &full[s], b * 64, row);
       }
       issued = c + 1;
     }
+    if constexpr (ROWS) {
+      // the last fills land before the item ends; the epilogue needs no operands
+      for (int c = (issued > NS ? issued - NS : 0); c < issued; ++c)
+        mbar_wait(&full[(c + 2) % NS], bwd_use(c, NS) & 1);
+      if (!ok) set_timeout(D);
+    } else {
     // epilogue operands: this CTA's own Z~ tile again (early: once V(nch - 3) is done)
     auto load_ez = [&]() {
       mbar_arrive_expect_tx(&bar_etma, 2 * TB);
@@ -1263,6 +1293,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       bulk_commit_group();
     }
     if (!ok) set_timeout(D);
+    }  // !ROWS
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------------ MMA issuer
     bool ok = mbar_wait(&bar_pro, 0);
@@ -1302,6 +1333,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       }
     }
     mma_commit(&bar_v);
+    if constexpr (ROWS) {
+      if (ok) ok = mbar_wait(&bar_v, 0);
+      if (!ok) set_timeout(D);
+    } else {
     if (ok) ok = mbar_wait(&bar_v, 0);
     if (ok) ok = mbar_wait(&bar_etma, 0) && mbar_wait(&bar_eready, 0);
     if (ok) {
@@ -1317,6 +1352,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       mma_commit(&bar_gm);
       mbar_wait(&bar_gm, 0);
     }
+    }  // !ROWS
   } else if (warp == 3 && lane == 0) {
     // ------------------------------------------------------------------ next item's records
     // (three dependent loads) and one look at its dependency, while this item runs; if the
@@ -1330,7 +1366,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       s_tile[sl ^ 1] = tn;
       s_nd[sl ^ 1] = ndn;
       s_pn[sl ^ 1] = pnn;
-      s_dep[sl ^ 1] = pnn.parent < 0 || ld_acquire(done + ndn.parent) >= tiles_of(pnn.K);
+      s_dep[sl ^ 1] = ROWS || pnn.parent < 0 || ld_acquire(done + ndn.parent) >= tiles_of(pnn.K);
     }
   } else if (warp >= 4) {
     // ------------------------------------------------------------------ exponentials
@@ -1338,10 +1374,26 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     const int qd = warp & 3, h = (warp - 4) >> 2;
     const int r = 32 * qd + lane;
     const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
-    const int kq = t.row0 + r;  // child sample owned by this thread's row
+    const int kq = t.row0 + r;  // sample owned by this thread's row (ROWS: a parent sample)
     const bool valid = kq < K;
-    // column (parent sample) terms: (log q_p - lam_i - |mu~|^2 / (2 var)) log2 e; all loads first
-    {
+    if constexpr (ROWS) {
+      // column (child sample) terms: (beta_i - |z~_i|^2 / (2 var)) log2 e, as in the forward
+      float bv[kJt], zv[kJt];
+#pragma unroll
+      for (int i = 0; i < kJt; ++i) {
+        const int j = mt + i * kMath;
+        const bool in = j < K;
+        bv[i] = in ? D.beta[nd.off_nk + j] : 0.f;
+        zv[i] = in ? D.zn[nd.off_nk + j] : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < kJt; ++i) {
+        const int j = mt + i * kMath;
+        if (j >= nch * kRows) break;
+        ak[j] = (j < K) ? (bv[i] - 0.5f * zv[i] * iv) * kLog2e : -INFINITY;
+      }
+    } else {
+      // column (parent sample) terms: (log q_p - lam_i - |mu~|^2 / (2 var)) log2 e; all loads first
       float qv[kJt], lv[kJt], mv[kJt];
 #pragma unroll
       for (int i = 0; i < kJt; ++i) {
@@ -1358,10 +1410,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         ak[j] = (j < K) ? (logf(qv[i]) - lv[i] - 0.5f * mv[i] * iv) * kLog2e : -INFINITY;
       }
     }
-    // row term: (beta_i - |z~|^2 / (2 var) + z~ . c_i / var) log2 e
-    const float crow = valid ? (D.beta[nd.off_nk + kq] - 0.5f * D.zn[nd.off_nk + kq] * iv +
-                                T.zc[nd.off_nk + kq] * iv) * kLog2e
-                             : -INFINITY;
+    // row term: adjoint (beta_i - |z~|^2 / (2 var) + z~ . c_i / var) log2 e; ROWS the row
+    // normaliser -(lam_i[k] + |mu~^k|^2 / (2 var)) log2 e of the forward's log-sum-exp
+    const float crow = !valid ? -INFINITY
+                       : ROWS ? -(D.lam[nd.off_nk + kq] + 0.5f * D.mun[nd.off_nk + kq] * iv) * kLog2e
+                              : (D.beta[nd.off_nk + kq] - 0.5f * D.zn[nd.off_nk + kq] * iv +
+                                 T.zc[nd.off_nk + kq] * iv) * kLog2e;
     // prologue result A' = Z~_i W_i -> this half of the split A operand
     bool ok = mbar_wait(&bar_mu, 0);
     if (ok) {
@@ -1373,8 +1427,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         tmem_ld32(tS[0] + lane_off + g * 32, v);
         tmem_wait_ld();
         float f[32];
+        const float* cv = T.cvec + (long long)t.node * kLdp + g * 32;  // ROWS: mu~ = Z~_p W^T + c_i
 #pragma unroll
-        for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v[j]);
+        for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v[j]) + (ROWS ? __ldg(cv + j) : 0.f);
         uint32_t hi[16], lo[16];
         split_pack32(f, hi, lo);
         tmem_st16(tAH + lane_off + g * 16, hi);
@@ -1422,11 +1477,52 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       tc_fence_before();
       mbar_arrive(&pready[b]);
     }
+    if constexpr (ROWS) {
+      // E[k] = R[k] - mu~^k (R in V's columns, mu~ = A hi + lo), split, to the E rows
+      (void)qacc;
+      if (ok) ok = mbar_wait(&bar_v, 0);
+      if (ok) {
+        tc_fence_after();
+        __half* eh = T.EH + (nd.off_nk + kq) * kLdp;
+        __half* el = T.EL + (nd.off_nk + kq) * kLdp;
+#pragma unroll 1
+        for (int gg = 0; gg < GH; ++gg) {
+          const int g = h * GH + gg;
+          uint32_t v[32], ah[16], al[16];
+          tmem_ld32(tV + lane_off + g * 32, v);
+          tmem_ld16(tAH + lane_off + g * 16, ah);
+          tmem_ld16(tAL + lane_off + g * 16, al);
+          tmem_wait_ld();
+          float e[32];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const float2 fh = __half22float2(*reinterpret_cast<const __half2*>(&ah[q]));
+            const float2 fl = __half22float2(*reinterpret_cast<const __half2*>(&al[q]));
+            e[2 * q] = __uint_as_float(v[2 * q]) - (fh.x + fl.x);
+            e[2 * q + 1] = __uint_as_float(v[2 * q + 1]) - (fh.y + fl.y);
+          }
+          uint32_t hi[16], lo[16];
+          split_pack32(e, hi, lo);
+          if (valid)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              reinterpret_cast<uint4*>(eh + g * 32)[q] = make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
+              reinterpret_cast<uint4*>(el + g * 32)[q] = make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
+            }
+        }
+      }
+      tc_fence_before();
+      if (!ok) set_timeout(D);
+    } else {
     q_h[h][r] = qacc;
     sync_math();
     const float qtot = q_h[0][r] + q_h[1][r];
     if (ok && valid && h == 0) D.q[nd.off_nk + kq] = qtot;
     __threadfence();  // weights visible device-wide before the completion count moves
+    // sample gradients requested: V / q (the conditional mean of the parent's samples given
+    // this child sample) to the V rows, split, for the sample-gradient assembly
+    const bool want_v = D.dz != nullptr || D.deps != nullptr;
+    const float rq = qtot > 0.f ? 1.f / qtot : 0.f;
     // epilogue: V row -> fp16 A tile of G
     if (ok) ok = mbar_wait(&bar_v, 0);
     if (ok) {
@@ -1447,6 +1543,20 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) store_half8(eSV, r, g * 4 + q, f + 8 * q);
+        if (want_v && valid && g < DP / 32) {
+          float fv[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) fv[j] = f[j] * rq;
+          uint32_t hi[16], lo[16];
+          split_pack32(fv, hi, lo);
+          uint4* vh = reinterpret_cast<uint4*>(T.VH + (nd.off_nk + kq) * kLdp + g * 32);
+          uint4* vl = reinterpret_cast<uint4*>(T.VL + (nd.off_nk + kq) * kLdp + g * 32);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            vh[q] = make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
+            vl[q] = make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
+          }
+        }
       }
       ok = mbar_wait(&bar_etma, 0);
     }
@@ -1479,17 +1589,18 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     tc_fence_before();
     mbar_arrive(&bar_gst);  // (release) this thread's rows of the boxes are written
     if (!ok) set_timeout(D);
+    }  // !ROWS
   }
   // item end: every role is done with this item's barriers, tensor memory and ring
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 3 && lane == 0) {  // thread 0 goes straight on to the next item's setup
+  if (!ROWS && warp == 3 && lane == 0) {  // thread 0 goes straight on to the next item's setup
     red_release_add(done + t.node, 1);
     stamp_item_end(D, T, 1, nd.b);
   }
   }  // items
-  if (warp == 0 && lane == 0) bulk_wait_group0();  // the last G reductions are done
+  if (!ROWS && warp == 0 && lane == 0) bulk_wait_group0();  // the last G reductions are done
   if (warp == 2) {
     tc_fence_after();
     tmem_dealloc(tb, 512);
@@ -2511,6 +2622,12 @@ void workspace_layout(TcWork& w, const std::vector<NodeInfo>& nodes, long long n
     if (nd.leaf_slot >= 0) nx = std::max(nx, nd.off_x + nd.obs);
   subs.push_back({(void**)&w.t.xs, (size_t)std::max(nx, 1ll) * sizeof(float)});
   subs.push_back({(void**)&w.t.S, (size_t)w.num_inst * kLdp * kLdp * sizeof(float)});
+  subs.push_back({(void**)&w.t.VH, pk});
+  subs.push_back({(void**)&w.t.VL, pk});
+  subs.push_back({(void**)&w.t.EH, pk});
+  subs.push_back({(void**)&w.t.EL, pk});
+  subs.push_back({(void**)&w.t.CCH, (size_t)w.num_c * kLdp * kLdp * sizeof(__half)});
+  subs.push_back({(void**)&w.t.CCL, (size_t)w.num_c * kLdp * kLdp * sizeof(__half)});
 }
 
 tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vector<Tile>&, int maxK,
@@ -2525,7 +2642,11 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
       !make_map(&w.mWTL, w.t.WTL, (long long)w.num_slots * kLdp) ||
       !make_map(&w.mCH, w.t.CH, w.c_rows) || !make_map(&w.mCL, w.t.CL, w.c_rows) ||
       !make_map(&w.mZH64, w.t.ZH, w.rows, kMoUnit) || !make_map(&w.mZL64, w.t.ZL, w.rows, kMoUnit) ||
-      !make_map_f32(&w.mG, w.t.G, (long long)w.num_nodes * kLdp))
+      !make_map_f32(&w.mG, w.t.G, (long long)w.num_nodes * kLdp) ||
+      !make_map(&w.mVH, w.t.VH, w.rows) || !make_map(&w.mVL, w.t.VL, w.rows) ||
+      !make_map(&w.mEH, w.t.EH, w.rows) || !make_map(&w.mEL, w.t.EL, w.rows) ||
+      !make_map(&w.mCCH, w.t.CCH, (long long)w.num_c * kLdp) ||
+      !make_map(&w.mCCL, w.t.CCL, (long long)w.num_c * kLdp))
     return TMC_ERR_CUDA;
   {  // observation matrices' first rows, and the leaf tiles of the observation kernel
     std::vector<int> crow(w.num_c, 0);
@@ -2632,14 +2753,17 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
   const size_t f64 = fwd_smem<64>(maxK), f128 = fwd_smem<128>(maxK);
   cudaFuncSetAttribute(k_edge_fwd_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f64);
   cudaFuncSetAttribute(k_edge_fwd_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f128);
-  cudaFuncSetAttribute(k_edge_bwd_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<64>(maxK));
-  cudaFuncSetAttribute(k_edge_bwd_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<128>(maxK));
+  cudaFuncSetAttribute(k_edge_bwd_tc<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<64>(maxK));
+  cudaFuncSetAttribute(k_edge_bwd_tc<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<128>(maxK));
+  cudaFuncSetAttribute(k_edge_bwd_tc<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<64>(maxK));
+  cudaFuncSetAttribute(k_edge_bwd_tc<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<128>(maxK));
   cudaFuncSetAttribute(k_sample_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSampleSmem);
   cudaFuncSetAttribute(k_moments_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MoCfg<64>::smem);
   cudaFuncSetAttribute(k_moments_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MoCfg<128>::smem);
   cudaFuncSetAttribute(k_obs_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)obs_smem<64>());
   cudaFuncSetAttribute(k_obs_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)obs_smem<128>());
-  return cudaGetLastError() == cudaSuccess ? TMC_OK : TMC_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return TMC_ERR_CUDA;
+  return prepare_dz(w, nodes);
 }
 
 tmc_status instance_times(TcWork& w, int B, double* fwd_us, double* bwd_us) {
@@ -2656,6 +2780,7 @@ tmc_status instance_times(TcWork& w, int B, double* fwd_us, double* bwd_us) {
 }
 
 void release(TcWork& w) {
+  release_dz(w);
   cudaFree(w.d_tiles);
   cudaFree(w.d_nonroot);
   cudaFree(w.d_obs_tiles);
@@ -2734,11 +2859,27 @@ void launch_edge_bwd(TcWork& w, const Dev& D, cudaStream_t s) {
     if (!n) continue;
     const int grid = n < w.num_sms ? n : w.num_sms;
     if (c == 0)
-      k_edge_bwd_tc<64><<<grid, kThreadsTc, bwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH, w.mZL,
+      k_edge_bwd_tc<64, false><<<grid, kThreadsTc, bwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH, w.mZL,
                                                                      w.mWTH, w.mWTL, w.mG);
     else
-      k_edge_bwd_tc<128><<<grid, kThreadsTc, bwd_smem<128>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH,
+      k_edge_bwd_tc<128, false><<<grid, kThreadsTc, bwd_smem<128>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH,
                                                                        w.mZL, w.mWTH, w.mWTL, w.mG);
+  }
+}
+
+void launch_edge_rows(TcWork& w, const Dev& D, cudaStream_t s) {
+  // the adjoint's tile list serves: tile r of edge p -> i names parent rows r .. r + 127
+  // (the same K on both sides); no item depends on another
+  for (int c = 0; c < 2; ++c) {
+    const int b = w.it_b[1][c], n = w.it_e[1][c] - b;
+    if (!n) continue;
+    const int grid = n < w.num_sms ? n : w.num_sms;
+    if (c == 0)
+      k_edge_bwd_tc<64, true><<<grid, kThreadsTc, bwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH,
+                                                                           w.mZL, w.mWH, w.mWL, w.mG);
+    else
+      k_edge_bwd_tc<128, true><<<grid, kThreadsTc, bwd_smem<128>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done,
+                                                                             w.mZH, w.mZL, w.mWH, w.mWL, w.mG);
   }
 }
 

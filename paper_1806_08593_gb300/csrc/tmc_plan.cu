@@ -310,9 +310,11 @@ tmc_status alloc_device(tmc_plan p) {
   struct Sub { void** dst; size_t bytes; };
   float *zt, *mut, *zn, *mun, *u, *beta, *lam, *q, *nodemax, *dmu, *gz, *pW, *pbias, *pC, *fac;
   double *nodeconst, *root_part;
+  const bool tc_plan = p->precision == TMC_PREC_FP16_TC;
+  const long long nkd32 = tc_plan ? 0 : nkd;  // FP32-path sample vectors (unused on the tc path)
   std::vector<Sub> subs = {
-      {(void**)&zt, sizeof(float) * nkd},      {(void**)&mut, sizeof(float) * nkd},
-      {(void**)&dmu, sizeof(float) * nkd},     {(void**)&gz, sizeof(float) * nkd},
+      {(void**)&zt, sizeof(float) * nkd},      {(void**)&mut, sizeof(float) * nkd32},
+      {(void**)&dmu, sizeof(float) * nkd32},   {(void**)&gz, sizeof(float) * nkd32},
       {(void**)&zn, sizeof(float) * nk},       {(void**)&mun, sizeof(float) * nk},
       {(void**)&u, sizeof(float) * nk},        {(void**)&beta, sizeof(float) * nk},
       {(void**)&lam, sizeof(float) * nk},      {(void**)&q, sizeof(float) * nk},
@@ -325,7 +327,6 @@ tmc_status alloc_device(tmc_plan p) {
   std::vector<tc::TcSub> tsubs;
   p->tcw.t.shared = p->shared;
   p->tcw.precision = p->precision;
-  const bool tc_plan = p->precision == TMC_PREC_FP16_TC;
   if (tc_plan) tc::workspace_layout(p->tcw, p->nodes, nk, nkd, tsubs);
   size_t total = 0;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -492,9 +493,6 @@ tmc_status tmc_backward(tmc_plan p, const tmc_inputs* in, const double* grad_out
   if (!p->fwd_done || std::memcmp(&p->last_in, in, sizeof(tmc_inputs)) != 0) return TMC_ERR_STATE;
   if (p->fault == kFaultLaunch) return TMC_ERR_CUDA;
   const bool tc_path = p->precision == TMC_PREC_FP16_TC;
-  // the tensor-core adjoint reduces the factors to d x d moments and forms no per-sample
-  // gradient; dz / deps are available on the FP32 path
-  if (tc_path && (g->dz || g->deps)) return TMC_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   Dev D = p->dev;
   D.eps = in->eps; D.q_mean = in->q_mean; D.q_logstd = in->q_logstd;
@@ -503,8 +501,11 @@ tmc_status tmc_backward(tmc_plan p, const tmc_inputs* in, const double* grad_out
   D.dz = g->dz; D.deps = g->deps; D.dq_mean = g->dq_mean; D.dq_logstd = g->dq_logstd;
   D.dW = g->dW; D.dbias = g->dbias; D.dC = g->dC;
   const Tile* T = p->d_tiles;
+  const bool sample_grads = g->dz || g->deps;
   if (tc_path) {
     if (p->maxlevel >= 1) TRY(timed(p, TMC_KC_EDGE_BWD, s, [&] { tc::launch_edge_bwd(p->tcw, D, s); }));
+    if (sample_grads && p->maxlevel >= 1)
+      TRY(timed(p, TMC_KC_SAMPLE_GRAD, s, [&] { tc::launch_edge_rows(p->tcw, D, s); }));
   } else {
     for (int L = 1; L <= p->maxlevel; ++L) {
       const int b = p->t_level_b[L], e = p->t_level_e[L];
@@ -514,6 +515,7 @@ tmc_status tmc_backward(tmc_plan p, const tmc_inputs* in, const double* grad_out
   }
   if (tc_path) {
     TRY(timed(p, TMC_KC_PARAM, s, [&] { tc::launch_unpack_grads(p->tcw, D, s); }));
+    if (sample_grads) TRY(timed(p, TMC_KC_SAMPLE_GRAD, s, [&] { tc::launch_dz(p->tcw, D, s); }));
   } else {
     TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_node_grad(D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
     TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_node_reduce(D, s); }));

@@ -62,6 +62,10 @@ struct TcDev {
   const LeafInfo* leaf_info;   // [leaves] in node order
   const int* leaf_off;         // [B + 1] leaves of instance b: leaf_off[b] .. leaf_off[b + 1]
   float* S;                    // [B][128*128] sum over an instance's leaves of M2 + zbar m^T
+  // sample gradients (dz, deps): written only when they are requested
+  __half *VH, *VL;             // [rows][128] split V / q = E[z~_p | sample] of the adjoint (non-root)
+  __half *EH, *EL;             // [rows][128] split R - mu~ per edge, rows = the parent's samples
+  __half *CCH, *CCL;           // [num_c*128][128] split -(prior_var / obs_var) C^T C
   int* done;                   // [nodes] tiles finished per node in the running edge launch
   unsigned long long* inst_t;  // [2][B] %globaltimer when an instance's last tile finished (fwd, adjoint)
   unsigned long long* t_start; // [2]    %globaltimer at the first tile of each launch
@@ -93,6 +97,10 @@ struct TcWork {
   int num_c = 0;                  // distinct observation matrices (1 when shared)
   CUtensorMap mCH, mCL;
   CUtensorMap mG;                 // fp32 [nodes*128][128] view of G for TMA reductions
+  CUtensorMap mVH, mVL, mEH, mEL, mCCH, mCCL;  // sample-gradient operands
+  std::vector<Tile> dz_tiles;     // 128-row tiles of every node, per d class
+  int dz_b[2] = {0, 0}, dz_e[2] = {0, 0};
+  Tile* d_dz_tiles = nullptr;
   std::vector<Tile> obs_tiles;
   int ob_b[2] = {0, 0}, ob_e[2] = {0, 0};
   Tile* d_obs_tiles = nullptr;
@@ -123,6 +131,13 @@ void launch_obs(TcWork& w, const Dev& D, cudaStream_t s);  // leaf observation t
 void launch_edge_fwd(TcWork& w, const Dev& D, cudaStream_t s);  // one persistent launch per d class
 void launch_edge_bwd(TcWork& w, const Dev& D, cudaStream_t s);
 void launch_unpack_grads(TcWork& w, const Dev& D, cudaStream_t s);
+// Sample gradients dz / deps (after launch_edge_bwd, which stores V / q when D.dz or D.deps is
+// set, and launch_unpack_grads, which forms C^T C): the row-direction edge pass, then the
+// assembly (k_dz_tc.cu).
+void launch_edge_rows(TcWork& w, const Dev& D, cudaStream_t s);
+void launch_dz(TcWork& w, const Dev& D, cudaStream_t s);
+tmc_status prepare_dz(TcWork& w, const std::vector<NodeInfo>& nodes);
+void release_dz(TcWork& w);
 
 }  // namespace tc
 }  // namespace tmc

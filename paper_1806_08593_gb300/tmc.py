@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libtmc_gb300.so")
 PRECISIONS = {"fp32": 0, "fp16": 2, "fp32_unfused": 3}
 STATUS = {0: "TMC_OK", 1: "TMC_ERR_INVALID_ARG", 2: "TMC_ERR_UNSUPPORTED", 3: "TMC_ERR_NOMEM",
           4: "TMC_ERR_CUDA", 5: "TMC_ERR_NUMERIC", 6: "TMC_ERR_TIMEOUT", 7: "TMC_ERR_STATE"}
-KERNEL_CLASSES = ["sample", "project", "edge_fwd", "root", "edge_bwd", "param"]
+KERNEL_CLASSES = ["sample", "project", "edge_fwd", "root", "edge_bwd", "param", "sample_grad"]
 EXPORTS = ["tmc_plan_create", "tmc_log_marginal", "tmc_backward", "tmc_plan_sync_status",
            "tmc_plan_workspace_bytes", "tmc_plan_destroy", "tmc_status_string",
            "tmc_profile_enable", "tmc_profile_read", "tmc_log_marginal_noalloc",

@@ -52,7 +52,7 @@ def _check(p, precision, grad_idx, tol_logp, ref_logp=None, logp_idx=None):
     oracle's forward, gradients of grad_idx against the oracle's adjoint."""
     go = np.zeros(p.B)
     go[grad_idx] = 1.0
-    got = gpu_run(p, precision, grad_out=go, want=PARAM_GRADS)
+    got = gpu_run(p, precision, grad_out=go, want=PARAM_GRADS + ("dz", "deps"))
     assert np.all(np.isfinite(got["log_phat"]))
     logp_idx = np.arange(p.B) if logp_idx is None else np.asarray(logp_idx)
     if ref_logp is None:
@@ -68,7 +68,12 @@ def _check(p, precision, grad_idx, tol_logp, ref_logp=None, logp_idx=None):
         for k in ("dW", "dbias", "dC"):
             assert rel_err(got[k], ref[k]) <= TOL_GRAD, (k, rel_err(got[k], ref[k]))
     qw = lambda b: int(p.n[b]) * int(p.d[b])
+    zw = lambda b: int(p.n[b]) * int(p.K[b]) * int(p.d[b])
     for j, b in enumerate(grad_idx):
+        for k in ("dz", "deps"):  # per-sample gradients of the sampled instances
+            g = _per_instance(p, got[k], b, zw)
+            r = _per_instance(sub, ref[k], j, lambda i: int(sub.n[i]) * int(sub.K[i]) * int(sub.d[i]))
+            assert rel_err(g, r) <= TOL_GRAD, (k, b, rel_err(g, r))
         for k in ("dq_mean", "dq_logstd"):
             g = _per_instance(p, got[k], b, qw)
             r = _per_instance(sub, ref[k], j, lambda i: int(sub.n[i]) * int(sub.d[i]))

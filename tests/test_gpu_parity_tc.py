@@ -1,15 +1,15 @@
 """Tensor-core (tcgen05, split-fp16) path vs the FP64 oracle through the C-ABI.
 
 Tolerances: |delta log P| <= 2e-2 nats per instance (reduced-precision path) and gradients
-within 1e-3 relative per tensor.  The split hi/lo fp16 operands give ~22-bit products, so
-the measured errors are far smaller; TOL_LOGP_DESIGN (1e-3) pins that design margin.
+within 1e-3 relative per tensor -- the parameter and proposal gradients and the per-sample
+gradients dz and deps.  The split hi/lo fp16 operands give ~22-bit products, so the measured
+errors are far smaller; TOL_LOGP_DESIGN (1e-3) pins that design margin.
 """
 import numpy as np
 import pytest
 
 import oracle
 from paper_1806_08593_gb300 import workload as wl
-from paper_1806_08593_gb300.tmc import TMCError
 from tests.parity import compare, gpu_run, mixed_roots_problem, oracle_run
 
 pytestmark = pytest.mark.gpu
@@ -17,6 +17,7 @@ TOL_LOGP = 2e-2
 TOL_LOGP_DESIGN = 1e-3
 TOL_GRAD = 1e-3
 PARAM_GRADS = ("dq_mean", "dq_logstd", "dW", "dbias", "dC")
+ALL_GRADS = PARAM_GRADS + ("dz", "deps")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -28,10 +29,11 @@ def _built():
     build()
 
 
-def _check(p, grad_out=None):
-    got = gpu_run(p, "fp16", grad_out=grad_out, want=PARAM_GRADS)
+def _check(p, grad_out=None, want=ALL_GRADS):
+    got = gpu_run(p, "fp16", grad_out=grad_out, want=want)
     ref = oracle_run(p, grad_out=grad_out)
-    rep = compare(p, got, ref, TOL_LOGP_DESIGN, TOL_GRAD, keys=list(PARAM_GRADS))
+    rep = compare(p, got, ref, TOL_LOGP_DESIGN, TOL_GRAD, keys=list(want))
+    print(p.name or "problem", {k: "%.1e" % v for k, v in rep.items()})
     assert rep["log_phat_max_abs"] <= TOL_LOGP
     return rep
 
@@ -87,8 +89,31 @@ def test_config3_tc_sampled():
         assert e <= TOL_GRAD, (k, e)
 
 
-def test_sample_gradients_are_fp32_only():
-    p = wl.make_chain(3, 8, 4, 4, 2, seed=5)
-    with pytest.raises(TMCError) as ei:
-        gpu_run(p, "fp16", want=("deps",))
-    assert ei.value.status == 2
+def test_sample_gradients_alone():
+    """dz / deps requested without any parameter gradient (and the converse, earlier)."""
+    p = wl.make_chain(3, 200, 16, 32, 2, seed=5)
+    _check(p, want=("dz",))
+    _check(p, want=("deps",))
+
+
+def test_autograd_fp16_plan():
+    """torch.autograd through an fp16 plan: every input's gradient, the noise included."""
+    import torch
+    from paper_1806_08593_gb300.tmc import Plan, tmc_log_marginal
+    p = wl.make_chain(4, 150, 12, 20, 3, seed=17)
+    ref = oracle_run(p)
+    plan = Plan.from_problem(p, "fp16")
+    t = plan.to_device(p)
+    for k in ("eps", "q_mean", "q_logstd", "W", "bias", "C"):
+        t[k].requires_grad_(True)
+    lp = tmc_log_marginal(plan, **t)
+    lp.sum().backward()
+    torch.cuda.synchronize()
+    plan.sync_status()
+    assert np.abs(lp.detach().cpu().numpy() - ref["log_phat"]).max() <= TOL_LOGP_DESIGN
+    for name, key in (("eps", "deps"), ("q_mean", "dq_mean"), ("q_logstd", "dq_logstd"), ("W", "dW"),
+                      ("bias", "dbias"), ("C", "dC")):
+        g = t[name].grad.double().cpu().numpy()
+        e = np.linalg.norm(g - ref[key]) / np.linalg.norm(ref[key])
+        assert e <= TOL_GRAD, (name, e)
+    plan.close()
