@@ -485,6 +485,38 @@ def run_ours(args):
                 "speedup": ms32 / ms_step,
                 "max_abs_dlogp_vs_fp32": float(np.max(np.abs(lp_ours - lp32)))}
 
+    # ---- the same step with the per-sample gradients dz / deps as well -----------------
+    sample_grads = None
+    if args.precision == "fp16" and not args.no_sample_grads:
+        want = GRADS + ("dz", "deps")
+        gz = dict(grads)
+        gz["dz"] = torch.empty_like(t["eps"])
+        gz["deps"] = torch.empty_like(t["eps"])
+        for _ in range(2):
+            plan.forward(t, out=out_lp)
+            plan.backward(t, out=gz, want=want)
+        torch.cuda.synchronize(dev)
+        nz = max(3, args.steps // 5)
+        ev0.record(stream)
+        for _ in range(nz):
+            plan.forward(t, out=out_lp)
+            plan.backward(t, out=gz, want=want)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_z = ev0.elapsed_time(ev1) / nz
+        plan.profile_enable(True)
+        for _ in range(nz):
+            plan.forward(t, out=out_lp)
+            plan.backward(t, out=gz, want=want)
+        pz = plan.profile_read()
+        plan.profile_enable(False)
+        plan.sync_status()
+        sample_grads = {"ms_per_step": ms_z, "extra_ms_per_step": ms_z - ms_step,
+                        "value": entries / (ms_z * 1e-3), "grads": list(want), "steps": nz,
+                        "graph": False,
+                        "kernel_ms_per_step": {k: v[0] / nz for k, v in pz.items()}}
+        del gz
+
     # ---- materialised-factor baseline (forward only, FP32) ----------------------------
     unfused = None
     if args.compare_unfused:
@@ -529,6 +561,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "fp32_path": fp32,
         "unfused_baseline": unfused,
+        "sample_grads": sample_grads,
         "instance_latency": latency,
         "gpu_launches": total_launches,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
@@ -555,6 +588,8 @@ def main():
     ap.add_argument("--compare-unfused", action="store_true",
                     help="also time the FP32 forward with every K x K factor materialised")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sample-grads", action="store_true",
+                    help="skip the extra timing of the step with the per-sample gradients dz, deps")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.impl == "reference":
