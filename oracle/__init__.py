@@ -69,7 +69,8 @@ def _common(p, overrides=None):
     o = dict(overrides or {})
     i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
     f64 = lambda k: np.ascontiguousarray(o.get(k, getattr(p, k)), dtype=np.float64)
-    arrs = dict(n=i32(p.n), parent=i32(p.parent), K=i32(p.K), d=i32(p.d), obs=i32(p.obs),
+    # per-latent K_i and d_i (the oracle's layout); uniform problems repeat K[b], d[b]
+    arrs = dict(n=i32(p.n), parent=i32(p.parent), K=i32(p.K_nodes()), d=i32(p.d_nodes()), obs=i32(p.obs),
                 eps=f64("eps"), q_mean=f64("q_mean"), q_logstd=f64("q_logstd"), W=f64("W"),
                 bias=f64("bias"), C=f64("C"), x=f64("x"))
     args = [p.B, _ptr(arrs["n"]), _ptr(arrs["parent"]), _ptr(arrs["K"]), _ptr(arrs["d"]),
@@ -125,6 +126,9 @@ def subset(p, idx):
     kw = dict(n=p.n[idx].copy(), K=p.K[idx].copy(), d=p.d[idx].copy(), obs=p.obs[idx].copy(),
               parent=cat("parent", "parent"), eps=cat("eps", "eps"), q_mean=cat("q", "q_mean"),
               q_logstd=cat("q", "q_logstd"), x=cat("x", "x"))
+    if p.ragged:
+        kw.update(Kn=np.concatenate([p.K_nodes()[s["parent"][0]:s["parent"][1]] for s in sl]),
+                  dn=np.concatenate([p.d_nodes()[s["parent"][0]:s["parent"][1]] for s in sl]))
     if p.shared:
         kw.update(W=p.W.copy(), bias=p.bias.copy(), C=p.C.copy())
     else:

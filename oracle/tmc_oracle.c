@@ -9,6 +9,9 @@
  *
  *   Eq. (is):  P_TMC = 1/prod_i K_i * sum_{k_1..k_n} P(x, z_1^{k_1},..,z_n^{k_n}) / prod_i Q(z_i^{k_i})
  *
+ *   with K_i samples of latent i (the number may differ from latent to latent, as Eq. (is)
+ *   allows) and latent i of dimension d_i.
+ *
  *   tmc_oracle_brute_force    -- that sum enumerated literally over all prod_i K_i sample
  *                                combinations (log-sum-exp over combinations).
  *   tmc_oracle_log_marginal   -- the same quantity by summing out one index at a time
@@ -22,7 +25,7 @@
  *                                parameters under the reparameterisation z = m + exp(logs)*eps.
  *
  * Model: z_0 ~ N(bias_0, prior_var I); z_i | z_p ~ N(W_i z_p + bias_i, prior_var I) for i >= 1
- * with p = parent[i] < i; every leaf l carries x_l ~ N(C z_l, obs_var I).
+ * with p = parent[i] < i (W_i is d_i x d_p); every leaf l carries x_l ~ N(C z_l, obs_var I).
  * Proposal: Q_i(z) = N(z; m_i, diag(exp(2 logs_i))), samples z_i^k = m_i + exp(logs_i) eps_i^k.
  *
  * Factors (Appendix):  f_i^{(k_i, k_p)} = P(z_i^{k_i} | z_p^{k_p}) / Q_i(z_i^{k_i})   (i >= 1)
@@ -43,19 +46,26 @@
 #define LOG_2PI 1.8378770664093454835606594728112
 
 /* ---------------------------------------------------------------------------------------
- * Instance view: pointers into the flat arrays for one instance b.
+ * Instance view: pointers into the flat arrays for one instance b, and per-latent offsets.
+ *   oz[i]  start of latent i's [K_i][d_i] block (eps, z, dz)
+ *   oq[i]  start of latent i's [d_i] vectors (m, logs, bias)
+ *   ow[i]  start of W_i, [d_i][d_p] (the root's block is [d_0][d_0] and unused)
+ *   ok[i]  start of latent i's [K_i] per-sample scalars
+ *   oe[i]  start of edge p -> i's blocks indexed by the PARENT's samples: messages [K_p] and
+ *          conditional means [K_p][d_i] (i >= 1)
  * ------------------------------------------------------------------------------------- */
 typedef struct {
-  int n, K, d, obs;
-  const int* parent;
+  int n, obs, dl; /* latents, observation dimension, the leaves' latent dimension */
+  const int *parent, *K, *d;
+  long long *oz, *oq, *ow, *ok, *oe, *oed;
   const double *eps, *m, *logs, *W, *bias, *C, *x;
   double prior_var, obs_var;
   int* leaf_slot; /* leaf_slot[i] = index of leaf i among the instance's leaves, or -1 */
-  int n_children_max;
+  long long nz, nq, nw, nk, ne, ned;
 } inst_t;
 
 typedef struct {
-  long long eps, q, x, W, bias, C, parent;
+  long long eps, q, x, W, C, parent;
 } offs_t;
 
 static int count_leaves(int n, const int* parent, int* leaf_slot) {
@@ -72,22 +82,39 @@ static int count_leaves(int n, const int* parent, int* leaf_slot) {
 static int validate(int B, const int* n, const int* parent, const int* K, const int* d,
                     const int* obs) {
   long long off = 0;
-  int b, i;
+  int b, i, dl;
   for (b = 0; b < B; ++b) {
-    if (n[b] < 1 || K[b] < 1 || d[b] < 1 || obs[b] < 1) return TMC_ORACLE_BAD_ARG;
+    if (n[b] < 1 || obs[b] < 1) return TMC_ORACLE_BAD_ARG;
     if (parent[off] != -1) return TMC_ORACLE_BAD_ARG;
+    for (i = 0; i < n[b]; ++i)
+      if (K[off + i] < 1 || d[off + i] < 1) return TMC_ORACLE_BAD_ARG;
     for (i = 1; i < n[b]; ++i)
       if (parent[off + i] < 0 || parent[off + i] >= i) return TMC_ORACLE_BAD_ARG;
+    /* the leaves of an instance share one dimension (one observation matrix C) */
+    dl = -1;
+    for (i = 0; i < n[b]; ++i) {
+      int j, leaf = 1;
+      for (j = i + 1; j < n[b]; ++j)
+        if (parent[off + j] == i) leaf = 0;
+      if (leaf) {
+        if (dl < 0) dl = d[off + i];
+        else if (dl != d[off + i]) return TMC_ORACLE_BAD_ARG;
+      }
+    }
     off += n[b];
   }
   return TMC_ORACLE_OK;
 }
 
+#define KI(I, i) ((I)->K[i])
+#define DI(I, i) ((I)->d[i])
+#define DP(I, i) ((i) ? (I)->d[(I)->parent[i]] : (I)->d[0])
+
 /* z_i^k = m_i + exp(logs_i) * eps_i^k (reparameterised sample). */
 static void sample(const inst_t* I, int i, int k, double* z) {
-  int j;
-  const double* e = I->eps + ((long long)i * I->K + k) * I->d;
-  for (j = 0; j < I->d; ++j) z[j] = I->m[i * I->d + j] + exp(I->logs[i * I->d + j]) * e[j];
+  int j, d = DI(I, i);
+  const double* e = I->eps + I->oz[i] + (long long)k * d;
+  for (j = 0; j < d; ++j) z[j] = I->m[I->oq[i] + j] + exp(I->logs[I->oq[i] + j]) * e[j];
 }
 
 /* log N(y; mean, var I) in dimension dim. */
@@ -105,9 +132,9 @@ static double log_normal_iso(const double* y, const double* mean, int dim, doubl
 static double log_q(const inst_t* I, int i, const double* z) {
   double s = 0.0;
   int j;
-  for (j = 0; j < I->d; ++j) {
-    double ls = I->logs[i * I->d + j];
-    double r = (z[j] - I->m[i * I->d + j]) * exp(-ls);
+  for (j = 0; j < DI(I, i); ++j) {
+    double ls = I->logs[I->oq[i] + j];
+    double r = (z[j] - I->m[I->oq[i] + j]) * exp(-ls);
     s += -0.5 * r * r - ls - 0.5 * LOG_2PI;
   }
   return s;
@@ -115,11 +142,11 @@ static double log_q(const inst_t* I, int i, const double* z) {
 
 /* mean of z_i given its parent sample: W_i zp + bias_i (i >= 1), or bias_0 for the root. */
 static void cond_mean(const inst_t* I, int i, const double* zp, double* mu) {
-  int r, c, d = I->d;
+  int r, c, d = DI(I, i), dp = DP(I, i);
   for (r = 0; r < d; ++r) {
-    double s = I->bias[i * d + r];
+    double s = I->bias[I->oq[i] + r];
     if (i > 0)
-      for (c = 0; c < d; ++c) s += I->W[((long long)i * d + r) * d + c] * zp[c];
+      for (c = 0; c < dp; ++c) s += I->W[I->ow[i] + (long long)r * dp + c] * zp[c];
     mu[r] = s;
   }
 }
@@ -130,7 +157,7 @@ static double log_obs(const inst_t* I, int leaf_slot, const double* z, double* p
   const double* xl = I->x + (long long)leaf_slot * I->obs;
   for (o = 0; o < I->obs; ++o) {
     double s = 0.0;
-    for (c = 0; c < I->d; ++c) s += I->C[(long long)o * I->d + c] * z[c];
+    for (c = 0; c < I->dl; ++c) s += I->C[(long long)o * I->dl + c] * z[c];
     pred[o] = s;
   }
   return log_normal_iso(xl, pred, I->obs, I->obs_var);
@@ -153,7 +180,7 @@ static double logsumexp(const double* v, int len) {
  *   node[i][k]      log of everything indexed by k_i alone: -log Q_i, plus log P(z_0) at the
  *                   root, plus log P(x_i | z_i) at a leaf
  *   logg[i][k]      node[i][k] + sum over children c of logmsg[c][k]
- *   logmsg[i][kp]   message of node i to its parent: log(1/K sum_k f_i^{(k,kp)} * children)
+ *   logmsg[i][kp]   message of node i to its parent: log(1/K_i sum_k f_i^{(k,kp)} * children)
  * ------------------------------------------------------------------------------------- */
 typedef struct {
   double *z, *mu, *node, *logg, *logmsg;
@@ -161,12 +188,11 @@ typedef struct {
 } ws_t;
 
 static int ws_alloc(ws_t* w, const inst_t* I) {
-  long long nkd = (long long)I->n * I->K * I->d, nk = (long long)I->n * I->K;
-  w->z = (double*)calloc(nkd, sizeof(double));
-  w->mu = (double*)calloc(nkd, sizeof(double));
-  w->node = (double*)calloc(nk, sizeof(double));
-  w->logg = (double*)calloc(nk, sizeof(double));
-  w->logmsg = (double*)calloc(nk, sizeof(double));
+  w->z = (double*)calloc(I->nz, sizeof(double));
+  w->mu = (double*)calloc(I->ned > 0 ? I->ned : 1, sizeof(double));
+  w->node = (double*)calloc(I->nk, sizeof(double));
+  w->logg = (double*)calloc(I->nk, sizeof(double));
+  w->logmsg = (double*)calloc(I->ne > 0 ? I->ne : 1, sizeof(double));
   w->pred = (double*)calloc(I->obs, sizeof(double));
   return (w->z && w->mu && w->node && w->logg && w->logmsg && w->pred) ? 0 : -1;
 }
@@ -175,82 +201,104 @@ static void ws_free(ws_t* w) {
   free(w->z); free(w->mu); free(w->node); free(w->logg); free(w->logmsg); free(w->pred);
 }
 
-#define Z(w, I, i, k) ((w)->z + ((long long)(i) * (I)->K + (k)) * (I)->d)
-#define MU(w, I, i, k) ((w)->mu + ((long long)(i) * (I)->K + (k)) * (I)->d)
+#define Z(w, I, i, k) ((w)->z + (I)->oz[i] + (long long)(k) * DI(I, i))
+#define MU(w, I, i, kp) ((w)->mu + (I)->oed[i] + (long long)(kp) * DI(I, i))
+#define LOGG(w, I, i, k) ((w)->logg[(I)->ok[i] + (k)])
+#define MSG(w, I, i, kp) ((w)->logmsg[(I)->oe[i] + (kp)])
 
 /* log f_i^{(k, kp)} for i >= 1: log P(z_i^k | z_p^kp) (the -log Q_i part lives in node[]). */
 static double log_pair(const ws_t* w, const inst_t* I, int i, int k, int kp) {
-  return log_normal_iso(Z(w, I, i, k), MU(w, I, i, kp), I->d, I->prior_var);
+  return log_normal_iso(Z(w, I, i, k), MU(w, I, i, kp), DI(I, i), I->prior_var);
 }
 
 /* Forward recursion; returns log P_TMC of the instance. */
 static double instance_forward(const inst_t* I, ws_t* w) {
-  int n = I->n, K = I->K, d = I->d, i, k, kp;
-  double root_mean_dummy = 0.0;
-  (void)root_mean_dummy;
+  int n = I->n, i, k, kp;
   for (i = 0; i < n; ++i)
-    for (k = 0; k < K; ++k) sample(I, i, k, Z(w, I, i, k));
+    for (k = 0; k < KI(I, i); ++k) sample(I, i, k, Z(w, I, i, k));
   for (i = 1; i < n; ++i) {
     int p = I->parent[i];
-    for (kp = 0; kp < K; ++kp) cond_mean(I, i, Z(w, I, p, kp), MU(w, I, i, kp));
+    for (kp = 0; kp < KI(I, p); ++kp) cond_mean(I, i, Z(w, I, p, kp), MU(w, I, i, kp));
   }
   for (i = 0; i < n; ++i)
-    for (k = 0; k < K; ++k) {
+    for (k = 0; k < KI(I, i); ++k) {
       const double* z = Z(w, I, i, k);
       double v = -log_q(I, i, z);
-      if (i == 0) v += log_normal_iso(z, I->bias, d, I->prior_var);
+      if (i == 0) v += log_normal_iso(z, I->bias + I->oq[0], DI(I, 0), I->prior_var);
       if (I->leaf_slot[i] >= 0) v += log_obs(I, I->leaf_slot[i], z, w->pred);
-      w->node[(long long)i * K + k] = v;
+      w->node[I->ok[i] + k] = v;
     }
   /* logg starts as node; children (larger index) add their messages before the parent's
      own message is formed because we sweep i from n-1 down to 0. */
-  memcpy(w->logg, w->node, sizeof(double) * (size_t)n * K);
+  memcpy(w->logg, w->node, sizeof(double) * (size_t)I->nk);
   for (i = n - 1; i >= 1; --i) {
-    int p = I->parent[i];
-#pragma omp parallel for if (K >= 64) schedule(static)
-    for (kp = 0; kp < K; ++kp) {
-      double* t = (double*)malloc(sizeof(double) * K);
+    int p = I->parent[i], Ki = KI(I, i), Kp = KI(I, p);
+#pragma omp parallel for if (Kp >= 64) schedule(static)
+    for (kp = 0; kp < Kp; ++kp) {
+      double* t = (double*)malloc(sizeof(double) * Ki);
       int kk;
-      for (kk = 0; kk < K; ++kk)
-        t[kk] = log_pair(w, I, i, kk, kp) + w->logg[(long long)i * K + kk];
-      w->logmsg[(long long)i * K + kp] = logsumexp(t, K) - log((double)K);
+      for (kk = 0; kk < Ki; ++kk) t[kk] = log_pair(w, I, i, kk, kp) + LOGG(w, I, i, kk);
+      MSG(w, I, i, kp) = logsumexp(t, Ki) - log((double)Ki);
       free(t);
     }
-    for (kp = 0; kp < K; ++kp) w->logg[(long long)p * K + kp] += w->logmsg[(long long)i * K + kp];
+    for (kp = 0; kp < Kp; ++kp) LOGG(w, I, p, kp) += MSG(w, I, i, kp);
   }
-  return logsumexp(w->logg, K) - log((double)K);
+  return logsumexp(w->logg + I->ok[0], KI(I, 0)) - log((double)KI(I, 0));
 }
 
-static void make_instance(inst_t* I, int b, const offs_t* o, const int* n, const int* parent,
-                          const int* K, const int* d, const int* obs, double prior_var,
-                          double obs_var, const double* eps, const double* q_mean,
-                          const double* q_logstd, const double* W, const double* bias,
-                          const double* C, const double* x, int* leaf_slot) {
-  (void)b;
-  I->n = n[b]; I->K = K[b]; I->d = d[b]; I->obs = obs[b];
+/* Fills the instance view of instance b and its per-latent offset tables (allocated here,
+   released by inst_free). */
+static int make_instance(inst_t* I, int b, const offs_t* o, int shared, const int* n, const int* parent,
+                         const int* K, const int* d, const int* obs, double prior_var,
+                         double obs_var, const double* eps, const double* q_mean,
+                         const double* q_logstd, const double* W, const double* bias,
+                         const double* C, const double* x, int* leaf_slot) {
+  int i, nn = n[b];
+  long long z = 0, q = 0, wo = 0, kk = 0, e = 0, ed = 0;
+  I->n = nn;
+  I->obs = obs[b];
   I->parent = parent + o->parent;
+  I->K = K + o->parent;
+  I->d = d + o->parent;
+  I->oz = (long long*)malloc(sizeof(long long) * 6 * (size_t)nn);
+  if (!I->oz) return -1;
+  I->oq = I->oz + nn; I->ow = I->oq + nn; I->ok = I->ow + nn; I->oe = I->ok + nn; I->oed = I->oe + nn;
+  for (i = 0; i < nn; ++i) {
+    int Ki = I->K[i], di = I->d[i], dp = i ? I->d[I->parent[i]] : di, Kp = i ? I->K[I->parent[i]] : 0;
+    I->oz[i] = z; I->oq[i] = q; I->ow[i] = wo; I->ok[i] = kk; I->oe[i] = e; I->oed[i] = ed;
+    z += (long long)Ki * di; q += di; wo += (long long)di * dp; kk += Ki;
+    e += Kp; ed += (long long)Kp * di;
+  }
+  I->nz = z; I->nq = q; I->nw = wo; I->nk = kk; I->ne = e; I->ned = ed;
+  I->dl = 1;
+  for (i = 0; i < nn; ++i)
+    if (leaf_slot[i] >= 0) I->dl = I->d[i];
   I->eps = eps + o->eps;
   I->m = q_mean + o->q;
   I->logs = q_logstd + o->q;
   I->W = W + o->W;
-  I->bias = bias + o->bias;
+  I->bias = shared ? bias : bias + o->q; /* bias shares q_mean's offsets unless shared */
   I->C = C + o->C;
   I->x = x + o->x;
   I->prior_var = prior_var;
   I->obs_var = obs_var;
   I->leaf_slot = leaf_slot;
+  return 0;
 }
 
-static void advance(offs_t* o, int b, const int* n, const int* K, const int* d, const int* obs,
-                    int shared, int nleaves) {
-  o->eps += (long long)n[b] * K[b] * d[b];
-  o->q += (long long)n[b] * d[b];
-  o->x += (long long)nleaves * obs[b];
-  o->parent += n[b];
+static void inst_free(inst_t* I) { free(I->oz); }
+
+/* Per-instance offsets into the flat arrays: eps [sum K_i d_i], q_mean / q_logstd / bias
+   [sum d_i], W [sum d_i d_p], C [obs d_leaf], x [leaves obs]; W / bias / C are not advanced
+   when the parameters are shared. */
+static void advance(offs_t* o, const inst_t* I, int shared, int nleaves) {
+  o->eps += I->nz;
+  o->q += I->nq;
+  o->x += (long long)nleaves * I->obs;
+  o->parent += I->n;
   if (!shared) {
-    o->W += (long long)n[b] * d[b] * d[b];
-    o->bias += (long long)n[b] * d[b];
-    o->C += (long long)obs[b] * d[b];
+    o->W += I->nw;
+    o->C += (long long)I->obs * I->dl;
   }
 }
 
@@ -268,13 +316,14 @@ int tmc_oracle_log_marginal(int B, const int* n, const int* parent, const int* K
     ws_t w;
     int* slot = (int*)malloc(sizeof(int) * n[b]);
     int nl = count_leaves(n[b], parent + o.parent, slot);
-    make_instance(&I, b, &o, n, parent, K, d, obs, prior_var, obs_var, eps, q_mean, q_logstd,
-                  W, bias, C, x, slot);
-    if (ws_alloc(&w, &I)) { free(slot); return TMC_ORACLE_NOMEM; }
+    if (make_instance(&I, b, &o, shared, n, parent, K, d, obs, prior_var, obs_var, eps, q_mean,
+                      q_logstd, W, bias, C, x, slot)) { free(slot); return TMC_ORACLE_NOMEM; }
+    if (ws_alloc(&w, &I)) { inst_free(&I); free(slot); return TMC_ORACLE_NOMEM; }
     log_phat[b] = instance_forward(&I, &w);
     ws_free(&w);
+    advance(&o, &I, shared, nl);
+    inst_free(&I);
     free(slot);
-    advance(&o, b, n, K, d, obs, shared, nl);
   }
   return TMC_ORACLE_OK;
 }
@@ -294,107 +343,110 @@ int tmc_oracle_log_marginal(int B, const int* n, const int* parent, const int* K
  * ------------------------------------------------------------------------------------- */
 static void instance_backward(const inst_t* I, ws_t* w, double L, double go, double* dz,
                               double* dm, double* dlogs, double* dW, double* dbias, double* dC) {
-  int n = I->n, K = I->K, d = I->d, i, k, kp, j, c;
+  int n = I->n, i, k, kp, j, c;
+  const int dl = I->dl;
   double var = I->prior_var;
-  double* wt = (double*)calloc((size_t)n * K, sizeof(double));
-  double* dmu = (double*)calloc((size_t)K * d, sizeof(double));
-  double* dzl = (double*)calloc((size_t)n * K * d, sizeof(double));
+  double* wt = (double*)calloc((size_t)I->nk, sizeof(double));
+  double* dzl = (double*)calloc((size_t)I->nz, sizeof(double));
   double* pred = (double*)calloc(I->obs, sizeof(double));
-  for (k = 0; k < K; ++k) wt[k] = exp(w->logg[k] - log((double)K) - L);
+  const int K0 = KI(I, 0);
+  for (k = 0; k < K0; ++k) wt[I->ok[0] + k] = exp(LOGG(w, I, 0, k) - log((double)K0) - L);
   for (i = 1; i < n; ++i) {
-    int p = I->parent[i];
-    memset(dmu, 0, sizeof(double) * (size_t)K * d);
+    int p = I->parent[i], Ki = KI(I, i), Kp = KI(I, p), d = DI(I, i), dp = DI(I, p);
+    double* dmu = (double*)calloc((size_t)Kp * d, sizeof(double));
     /* rows kp: parent sample; columns k: child sample */
-#pragma omp parallel for if (K >= 64) schedule(static) private(k, j)
-    for (kp = 0; kp < K; ++kp) {
+#pragma omp parallel for if (Kp >= 64) schedule(static) private(k, j)
+    for (kp = 0; kp < Kp; ++kp) {
       const double* mu = MU(w, I, i, kp);
-      for (k = 0; k < K; ++k) {
+      for (k = 0; k < Ki; ++k) {
         const double* z = Z(w, I, i, k);
-        double pi = wt[(long long)p * K + kp] *
-                    exp(log_pair(w, I, i, k, kp) + w->logg[(long long)i * K + k] -
-                        log((double)K) - w->logmsg[(long long)i * K + kp]);
+        double pi = wt[I->ok[p] + kp] *
+                    exp(log_pair(w, I, i, k, kp) + LOGG(w, I, i, k) - log((double)Ki) - MSG(w, I, i, kp));
         for (j = 0; j < d; ++j) dmu[(long long)kp * d + j] += pi * (z[j] - mu[j]) / var;
       }
     }
     /* column direction: weights and sample gradients of the child */
-#pragma omp parallel for if (K >= 64) schedule(static) private(kp, j)
-    for (k = 0; k < K; ++k) {
+#pragma omp parallel for if (Ki >= 64) schedule(static) private(kp, j)
+    for (k = 0; k < Ki; ++k) {
       const double* z = Z(w, I, i, k);
       double acc_w = 0.0;
-      for (kp = 0; kp < K; ++kp) {
+      for (kp = 0; kp < Kp; ++kp) {
         const double* mu = MU(w, I, i, kp);
-        double pi = wt[(long long)p * K + kp] *
-                    exp(log_pair(w, I, i, k, kp) + w->logg[(long long)i * K + k] -
-                        log((double)K) - w->logmsg[(long long)i * K + kp]);
+        double pi = wt[I->ok[p] + kp] *
+                    exp(log_pair(w, I, i, k, kp) + LOGG(w, I, i, k) - log((double)Ki) - MSG(w, I, i, kp));
         acc_w += pi;
-        for (j = 0; j < d; ++j) dzl[((long long)i * K + k) * d + j] += pi * (mu[j] - z[j]) / var;
+        for (j = 0; j < d; ++j) dzl[I->oz[i] + (long long)k * d + j] += pi * (mu[j] - z[j]) / var;
       }
-      wt[(long long)i * K + k] = acc_w;
+      wt[I->ok[i] + k] = acc_w;
     }
     /* mu_i^kp = W_i z_p^kp + bias_i */
-    for (kp = 0; kp < K; ++kp) {
+    for (kp = 0; kp < Kp; ++kp) {
       const double* zp = Z(w, I, p, kp);
       for (j = 0; j < d; ++j) {
         double g = dmu[(long long)kp * d + j];
-        dbias[i * d + j] += go * g;
-        for (c = 0; c < d; ++c) {
-          dW[((long long)i * d + j) * d + c] += go * g * zp[c];
-          dzl[((long long)p * K + kp) * d + c] += I->W[((long long)i * d + j) * d + c] * g;
+        dbias[I->oq[i] + j] += go * g;
+        for (c = 0; c < dp; ++c) {
+          dW[I->ow[i] + (long long)j * dp + c] += go * g * zp[c];
+          dzl[I->oz[p] + (long long)kp * dp + c] += I->W[I->ow[i] + (long long)j * dp + c] * g;
         }
       }
     }
+    free(dmu);
   }
   /* node terms */
-  for (i = 0; i < n; ++i)
-    for (k = 0; k < K; ++k) {
+  for (i = 0; i < n; ++i) {
+    int d = DI(I, i);
+    for (k = 0; k < KI(I, i); ++k) {
       const double* z = Z(w, I, i, k);
-      double wk = wt[(long long)i * K + k];
-      double* g = dzl + ((long long)i * K + k) * d;
+      double wk = wt[I->ok[i] + k];
+      double* g = dzl + I->oz[i] + (long long)k * d;
       for (j = 0; j < d; ++j) {
-        double s2 = exp(2.0 * I->logs[i * d + j]);
-        g[j] += wk * (z[j] - I->m[i * d + j]) / s2; /* from -log Q_i(z) */
+        double s2 = exp(2.0 * I->logs[I->oq[i] + j]);
+        g[j] += wk * (z[j] - I->m[I->oq[i] + j]) / s2; /* from -log Q_i(z) */
       }
       if (i == 0)
         for (j = 0; j < d; ++j) {
-          double r = (z[j] - I->bias[j]) / var;
+          double r = (z[j] - I->bias[I->oq[0] + j]) / var;
           g[j] -= wk * r;
-          dbias[j] += go * wk * r;
+          dbias[I->oq[0] + j] += go * wk * r;
         }
       if (I->leaf_slot[i] >= 0) {
         const double* xl = I->x + (long long)I->leaf_slot[i] * I->obs;
         int o;
         for (o = 0; o < I->obs; ++o) {
           double s = 0.0;
-          for (c = 0; c < d; ++c) s += I->C[(long long)o * d + c] * z[c];
+          for (c = 0; c < dl; ++c) s += I->C[(long long)o * dl + c] * z[c];
           pred[o] = (xl[o] - s) / I->obs_var; /* residual / obs_var */
         }
         for (o = 0; o < I->obs; ++o)
-          for (c = 0; c < d; ++c) {
-            g[c] += wk * I->C[(long long)o * d + c] * pred[o];
-            dC[(long long)o * d + c] += go * wk * pred[o] * z[c];
+          for (c = 0; c < dl; ++c) {
+            g[c] += wk * I->C[(long long)o * dl + c] * pred[o];
+            dC[(long long)o * dl + c] += go * wk * pred[o] * z[c];
           }
       }
     }
+  }
   /* outputs */
   for (i = 0; i < n; ++i) {
+    int d = DI(I, i);
     double wsum = 0.0;
-    for (k = 0; k < K; ++k) wsum += wt[(long long)i * K + k];
+    for (k = 0; k < KI(I, i); ++k) wsum += wt[I->ok[i] + k];
     for (j = 0; j < d; ++j) {
-      double s2 = exp(2.0 * I->logs[i * d + j]), am = 0.0, al = 0.0;
-      for (k = 0; k < K; ++k) {
+      double s2 = exp(2.0 * I->logs[I->oq[i] + j]), am = 0.0, al = 0.0;
+      for (k = 0; k < KI(I, i); ++k) {
         const double* z = Z(w, I, i, k);
-        double g = dzl[((long long)i * K + k) * d + j];
-        double zc = z[j] - I->m[i * d + j];
-        double gp = g - wt[(long long)i * K + k] * zc / s2;
+        double g = dzl[I->oz[i] + (long long)k * d + j];
+        double zc = z[j] - I->m[I->oq[i] + j];
+        double gp = g - wt[I->ok[i] + k] * zc / s2;
         am += gp;
         al += gp * zc;
-        if (dz) dz[((long long)i * K + k) * d + j] += go * g;
+        if (dz) dz[I->oz[i] + (long long)k * d + j] += go * g;
       }
-      dm[i * d + j] += go * am;
-      dlogs[i * d + j] += go * (wsum + al);
+      dm[I->oq[i] + j] += go * am;
+      dlogs[I->oq[i] + j] += go * (wsum + al);
     }
   }
-  free(wt); free(dmu); free(dzl); free(pred);
+  free(wt); free(dzl); free(pred);
 }
 
 int tmc_oracle_grad(int B, const int* n, const int* parent, const int* K, const int* d,
@@ -413,16 +465,19 @@ int tmc_oracle_grad(int B, const int* n, const int* parent, const int* K, const 
     double L;
     int* slot = (int*)malloc(sizeof(int) * n[b]);
     int nl = count_leaves(n[b], parent + o.parent, slot);
-    make_instance(&I, b, &o, n, parent, K, d, obs, prior_var, obs_var, eps, q_mean, q_logstd,
-                  W, bias, C, x, slot);
-    if (ws_alloc(&w, &I)) { free(slot); return TMC_ORACLE_NOMEM; }
+    if (make_instance(&I, b, &o, shared, n, parent, K, d, obs, prior_var, obs_var, eps, q_mean,
+                      q_logstd, W, bias, C, x, slot)) { free(slot); return TMC_ORACLE_NOMEM; }
+    if (ws_alloc(&w, &I)) { inst_free(&I); free(slot); return TMC_ORACLE_NOMEM; }
     L = instance_forward(&I, &w);
     if (log_phat) log_phat[b] = L;
+    /* the bias gradient lives where bias does: dbias + 0 (shared) or dbias + o.q */
     instance_backward(&I, &w, L, grad_out ? grad_out[b] : 1.0, dz ? dz + o.eps : NULL,
-                      dq_mean + o.q, dq_logstd + o.q, dW + o.W, dbias + o.bias, dC + o.C);
+                      dq_mean + o.q, dq_logstd + o.q, dW + o.W, shared ? dbias : dbias + o.q,
+                      dC + o.C);
     ws_free(&w);
+    advance(&o, &I, shared, nl);
+    inst_free(&I);
     free(slot);
-    advance(&o, b, n, K, d, obs, shared, nl);
   }
   return TMC_ORACLE_OK;
 }
@@ -445,42 +500,46 @@ int tmc_oracle_brute_force(int B, const int* n, const int* parent, const int* K,
     int* slot = (int*)malloc(sizeof(int) * n[b]);
     int nl = count_leaves(n[b], parent + o.parent, slot);
     long long combos = 1, t;
-    int i, j;
-    make_instance(&I, b, &o, n, parent, K, d, obs, prior_var, obs_var, eps, q_mean, q_logstd,
-                  W, bias, C, x, slot);
+    int i;
+    double lognorm = 0.0;
+    if (make_instance(&I, b, &o, shared, n, parent, K, d, obs, prior_var, obs_var, eps, q_mean,
+                      q_logstd, W, bias, C, x, slot)) { free(slot); return TMC_ORACLE_NOMEM; }
     for (i = 0; i < I.n; ++i) {
-      combos *= I.K;
-      if (combos > max_combos) { free(slot); return TMC_ORACLE_TOO_BIG; }
+      combos *= KI(&I, i);
+      lognorm += log((double)KI(&I, i));
+      if (combos > max_combos) { inst_free(&I); free(slot); return TMC_ORACLE_TOO_BIG; }
     }
     {
       double* lw = (double*)malloc(sizeof(double) * combos);
-      double* zs = (double*)malloc(sizeof(double) * (size_t)I.n * I.d);
-      double* mu = (double*)malloc(sizeof(double) * I.d);
+      double* zs = (double*)malloc(sizeof(double) * (size_t)I.nq);
+      double* mu = (double*)malloc(sizeof(double) * (size_t)I.nq);
       double* pred = (double*)malloc(sizeof(double) * I.obs);
       int* kk = (int*)malloc(sizeof(int) * I.n);
       for (t = 0; t < combos; ++t) {
         long long r = t;
         double v = 0.0;
-        for (i = 0; i < I.n; ++i) { kk[i] = (int)(r % I.K); r /= I.K; }
-        for (i = 0; i < I.n; ++i) sample(&I, i, kk[i], zs + (long long)i * I.d);
+        for (i = 0; i < I.n; ++i) { kk[i] = (int)(r % KI(&I, i)); r /= KI(&I, i); }
+        for (i = 0; i < I.n; ++i) sample(&I, i, kk[i], zs + I.oq[i]);
         /* log P(x, z): root prior, conditionals, observations */
         for (i = 0; i < I.n; ++i) {
+          int j;
           if (i == 0) {
-            for (j = 0; j < I.d; ++j) mu[j] = I.bias[j];
+            for (j = 0; j < DI(&I, 0); ++j) mu[j] = I.bias[I.oq[0] + j];
           } else {
-            cond_mean(&I, i, zs + (long long)I.parent[i] * I.d, mu);
+            cond_mean(&I, i, zs + I.oq[I.parent[i]], mu);
           }
-          v += log_normal_iso(zs + (long long)i * I.d, mu, I.d, I.prior_var);
-          if (slot[i] >= 0) v += log_obs(&I, slot[i], zs + (long long)i * I.d, pred);
-          v -= log_q(&I, i, zs + (long long)i * I.d);
+          v += log_normal_iso(zs + I.oq[i], mu, DI(&I, i), I.prior_var);
+          if (slot[i] >= 0) v += log_obs(&I, slot[i], zs + I.oq[i], pred);
+          v -= log_q(&I, i, zs + I.oq[i]);
         }
         lw[t] = v;
       }
-      log_phat[b] = logsumexp(lw, (int)combos) - I.n * log((double)I.K);
+      log_phat[b] = logsumexp(lw, (int)combos) - lognorm;
       free(lw); free(zs); free(mu); free(pred); free(kk);
     }
+    advance(&o, &I, shared, nl);
+    inst_free(&I);
     free(slot);
-    advance(&o, b, n, K, d, obs, shared, nl);
   }
   return TMC_ORACLE_OK;
 }

@@ -4,18 +4,21 @@
  * TEST INFRASTRUCTURE: only the tests, the smoke check and the benchmark's CPU baseline may
  * call these functions.  Nothing here is shared with the CUDA path.
  *
- * Batch layout (instance b follows instance b-1 in every flat array; all arrays are host
- * memory owned by the caller):
- *   n[B], K[B], d[B], obs[B]          latents, samples per latent, latent dim, obs dim
+ * Batch layout (instance b follows instance b-1 in every flat array, latent i after latent
+ * i-1 within it; all arrays are host memory owned by the caller):
+ *   n[B], obs[B]                      latents and observation dimension of each instance
+ *   K[sum n], d[sum n]                samples K_i and dimension d_i of every latent
  *   parent[sum n]                     local indices; parent[0] = -1, 0 <= parent[i] < i
- *   eps[sum n*K*d]       [i][k][j]    proposal noise
- *   q_mean, q_logstd [sum n*d]        proposal mean / log std, [i][j]
- *   W     [n*d*d]  (shared) or [sum n*d*d]   [i][r][c], W_0 unused
- *   bias  [n*d]    (shared) or [sum n*d]     bias_0 is the root prior mean
- *   C     [obs*d]  (shared) or [sum obs*d]   [o][c]
+ *   eps[sum K_i*d_i]     [i][k][j]    proposal noise
+ *   q_mean, q_logstd [sum d_i]        proposal mean / log std, [i][j]
+ *   W     [sum d_i*d_p]  [i][r][c]    W_i is d_i x d_p (p = parent[i]); the root's block is
+ *                                     d_0 x d_0 and unused
+ *   bias  [sum d_i]                   bias_0 is the root prior mean
+ *   C     [obs*d_leaf] per instance   [o][c]; the leaves of an instance share one dimension
  *   x     [sum leaves*obs]            one observation per leaf, leaves in node order
- * With shared != 0 every instance uses the same W/bias/C (and must have the same n, parent,
- * d, obs); their gradients are summed over instances.
+ * (W, bias and C of one instance only when shared.)  With shared != 0 every instance uses the
+ * same W/bias/C (and must have the same n, parent, d_i, obs); their gradients are summed over
+ * instances.
  *
  * Gradient outputs have the layout of the matching input and are ACCUMULATED (+=), each
  * instance's contribution multiplied by grad_out[b] (grad_out may be NULL: all ones).

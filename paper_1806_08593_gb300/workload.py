@@ -46,12 +46,17 @@ SEED_BASE = 20181806
 
 @dataclass
 class Problem:
-    """A batch of TMC instances in the C-ABI's flat layout (all float32 / int32)."""
+    """A batch of TMC instances in the C-ABI's flat layout (all float32 / int32).
+
+    Sizes: K[b] / d[b] apply to every latent of instance b unless the per-latent arrays Kn /
+    dn ([sum n], node order) are given (Eq. (is) allows a different K_i for every latent; a
+    latent's dimension d_i may differ too, W_i is then d_i x d_parent).  The leaves of an
+    instance share one dimension (one observation matrix C per instance)."""
 
     n: np.ndarray            # [B] int32
     parent: np.ndarray       # [sum n] int32, local indices, parent[0] = -1, parent[i] < i
     K: np.ndarray            # [B] int32
-    d: np.ndarray            # [B] int32
+    d: np.ndarray            # [B] int32 (the leaves' dimension when dn is given)
     obs: np.ndarray          # [B] int32
     shared: bool
     prior_var: float
@@ -65,10 +70,22 @@ class Problem:
     x: np.ndarray
     name: str = ""
     meta: dict = field(default_factory=dict)
+    Kn: np.ndarray | None = None   # [sum n] int32 per-latent K, or None
+    dn: np.ndarray | None = None   # [sum n] int32 per-latent d, or None
 
     @property
     def B(self) -> int:
         return int(self.n.shape[0])
+
+    @property
+    def ragged(self) -> bool:
+        return self.Kn is not None or self.dn is not None
+
+    def K_nodes(self) -> np.ndarray:
+        return self.Kn if self.Kn is not None else np.repeat(self.K, self.n).astype(np.int32)
+
+    def d_nodes(self) -> np.ndarray:
+        return self.dn if self.dn is not None else np.repeat(self.d, self.n).astype(np.int32)
 
     # ---- offsets (pure bookkeeping) -------------------------------------------------
     def parents_of(self, b: int) -> np.ndarray:
@@ -83,68 +100,97 @@ class Problem:
         return [i for i in range(len(par)) if not has_child[i]]
 
     def entries(self) -> int:
-        """Factor entries per call, B*n*K^2 summed over instances (the metric's unit)."""
-        return int(np.sum(self.n.astype(np.int64) * self.K.astype(np.int64) ** 2))
+        """Factor entries per call, B*n*K^2 summed over instances (the metric's unit);
+        sum over latents of K_i^2 with per-latent K."""
+        return int(np.sum(self.K_nodes().astype(np.int64) ** 2))
 
     def edge_entries(self) -> int:
         """Pairwise-factor entries actually formed: sum over edges of K_p*K_i."""
-        return int(np.sum((self.n.astype(np.int64) - 1) * self.K.astype(np.int64) ** 2))
+        Kn = self.K_nodes().astype(np.int64)
+        tot, off = 0, 0
+        for b in range(self.B):
+            par = self.parents_of(b)
+            for i in range(1, len(par)):
+                tot += Kn[off + par[i]] * Kn[off + i]
+            off += len(par)
+        return int(tot)
+
+    def node_sizes(self, b: int):
+        """(K_i, d_i, d_parent(i)) of instance b's latents (the root's parent dimension is its
+        own: its W block is d_0 x d_0 and ignored)."""
+        s = int(np.sum(self.n[:b]))
+        n = int(self.n[b])
+        Kn = self.K_nodes()[s:s + n].astype(np.int64)
+        dn = self.d_nodes()[s:s + n].astype(np.int64)
+        par = self.parents_of(b)
+        dp = np.array([dn[par[i]] if i else dn[0] for i in range(n)], dtype=np.int64)
+        return Kn, dn, dp
 
     def slices(self, b: int) -> dict:
         """Slices of every flat array belonging to instance b."""
-        n, K, d, o = (self.n.astype(np.int64), self.K.astype(np.int64),
-                      self.d.astype(np.int64), self.obs.astype(np.int64))
-        nl = np.array([len(self.leaves_of(i)) for i in range(self.B)], dtype=np.int64)
-        def off(v):
-            return int(np.sum(v[:b])), int(np.sum(v[:b + 1]))
-        out = dict(eps=off(n * K * d), q=off(n * d), x=off(nl * o), parent=off(n))
-        if self.shared:
-            out.update(W=(0, self.W.size), bias=(0, self.bias.size), C=(0, self.C.size))
-        else:
-            out.update(W=off(n * d * d), bias=off(n * d), C=off(o * d))
+        nl = [len(self.leaves_of(i)) for i in range(self.B)]
+        eps = q = w = x = c = 0
+        out = {}
+        for i in range(b + 1):
+            Kn, dn, dp = self.node_sizes(i)
+            dl = int(dn[self.leaves_of(i)[0]])
+            se, sq, sw = int(np.sum(Kn * dn)), int(np.sum(dn)), int(np.sum(dn * dp))
+            sx, sc = nl[i] * int(self.obs[i]), int(self.obs[i]) * dl
+            if i == b:
+                out = dict(eps=(eps, eps + se), q=(q, q + sq), x=(x, x + sx),
+                           parent=(int(np.sum(self.n[:b])), int(np.sum(self.n[:b + 1]))))
+                if self.shared:
+                    out.update(W=(0, self.W.size), bias=(0, self.bias.size), C=(0, self.C.size))
+                else:
+                    out.update(W=(w, w + sw), bias=(q, q + sq), C=(c, c + sc))
+            eps += se; q += sq; w += sw; x += sx; c += sc
         return out
 
 
 # ---------------------------------------------------------------------------------------
 # Exact Gaussian posterior, used only to place the proposal (information form, dense).
+# Latent i has dimension dn[i]; W_i is dn[i] x dn[parent[i]].
 # ---------------------------------------------------------------------------------------
-def _posterior_factor(parent, Ws, C, prior_var, obs_var):
+def _offsets(dn):
+    return np.concatenate([[0], np.cumsum(dn)]).astype(np.int64)
+
+
+def _posterior_factor(parent, Ws, C, prior_var, obs_var, dn):
     """Cholesky factor of the posterior precision and the marginal stds (x-independent)."""
     n = len(parent)
-    d = Ws[0].shape[0]
-    N = n * d
+    o = _offsets(dn)
+    N = int(o[-1])
     A = np.eye(N)
     for i in range(1, n):
         p = parent[i]
-        A[i * d:(i + 1) * d, p * d:(p + 1) * d] -= Ws[i]
+        A[o[i]:o[i + 1], o[p]:o[p + 1]] -= Ws[i]
     Lam = A.T @ A / prior_var
     CtC = C.T @ C / obs_var
     for leaf in _leaves(parent):
-        sl = slice(leaf * d, (leaf + 1) * d)
+        sl = slice(o[leaf], o[leaf + 1])
         Lam[sl, sl] += CtC
     cf = sla.cho_factor(Lam, lower=True)
     Linv = sla.solve_triangular(cf[0], np.eye(N), lower=True)
-    std = np.sqrt(np.sum(Linv * Linv, axis=0)).reshape(n, d)
-    return dict(cf=cf, A=A, std=std, n=n, d=d)
+    stdv = np.sqrt(np.sum(Linv * Linv, axis=0))
+    return dict(cf=cf, A=A, std=[stdv[o[i]:o[i + 1]] for i in range(n)], n=n, o=o)
 
 
 def _posterior_mean(fac, bs, C, xs_by_leaf, prior_var, obs_var):
-    n, d = fac["n"], fac["d"]
+    o = fac["o"]
     h = fac["A"].T @ np.concatenate(bs) / prior_var
     for leaf, xl in xs_by_leaf.items():
-        h[leaf * d:(leaf + 1) * d] += C.T @ xl / obs_var
-    return sla.cho_solve(fac["cf"], h).reshape(n, d)
+        h[o[leaf]:o[leaf + 1]] += C.T @ xl / obs_var
+    v = sla.cho_solve(fac["cf"], h)
+    return [v[o[i]:o[i + 1]] for i in range(fac["n"])]
 
 
-def _posterior_tree_bp(parent, Ws, bs, C, xs_by_leaf, prior_var, obs_var):
+def _posterior_tree_bp(parent, Ws, bs, C, xs_by_leaf, prior_var, obs_var, dn):
     """Exact posterior marginals of the tree by Gaussian belief propagation in information
     form: eliminate latents from the leaves up, then pass means / covariances down.
     O(n d^3) instead of the dense O((n d)^3)."""
     n = len(parent)
-    d = Ws[0].shape[0]
-    I = np.eye(d)
-    J = [I / prior_var for _ in range(n)]          # diagonal precision blocks
-    h = [np.zeros(d) for _ in range(n)]
+    J = [np.eye(int(dn[i])) / prior_var for i in range(n)]  # diagonal precision blocks
+    h = [np.zeros(int(dn[i])) for i in range(n)]
     h[0] = bs[0] / prior_var
     CtC = C.T @ C / obs_var
     for i in range(1, n):
@@ -163,11 +209,11 @@ def _posterior_tree_bp(parent, Ws, bs, C, xs_by_leaf, prior_var, obs_var):
     for i in range(n - 1, 0, -1):
         p = parent[i]
         Jm[i], hm[i] = Jacc[i], hacc[i]
-        L = -Ws[i] / prior_var                       # d x d block (row i, col p)
+        L = -Ws[i] / prior_var                       # d_i x d_p block (row i, col p)
         Jinv_L = np.linalg.solve(Jm[i], L)
         Jacc[p] = Jacc[p] - L.T @ Jinv_L
         hacc[p] = hacc[p] - L.T @ np.linalg.solve(Jm[i], hm[i])
-    mean = np.zeros((n, d))
+    mean = [None] * n
     cov = [None] * n
     cov[0] = np.linalg.inv(Jacc[0])
     mean[0] = cov[0] @ hacc[0]
@@ -178,7 +224,7 @@ def _posterior_tree_bp(parent, Ws, bs, C, xs_by_leaf, prior_var, obs_var):
         A = -Jinv @ L                                # z_i | z_p has mean Jinv (h_i - L z_p)
         mean[i] = Jinv @ hm[i] + A @ mean[p]
         cov[i] = Jinv + A @ cov[p] @ A.T
-    std = np.sqrt(np.stack([np.diag(c) for c in cov]))
+    std = [np.sqrt(np.diag(c)) for c in cov]
     return mean, std
 
 
@@ -190,46 +236,55 @@ def _leaves(parent):
     return [i for i in range(n) if not has_child[i]]
 
 
-def _draw_model(rng, n, d, obs, orth_C=False):
-    Ws = [np.zeros((d, d))] + [rng.standard_normal((d, d)) / np.sqrt(d) for _ in range(1, n)]
-    bs = [np.zeros(d)] + [rng.standard_normal(d) for _ in range(1, n)]
-    C = rng.standard_normal((obs, d)) / np.sqrt(d)
+def _draw_model(rng, parent, dn, obs, orth_C=False):
+    """W_i (d_i x d_p) entries N(0, 1/d_p), b_i ~ N(0, I), C (obs x d_leaf) entries
+    N(0, 1/d_leaf); W_0 = 0 and b_0 = 0 (the root's prior mean)."""
+    n = len(parent)
+    dl = int(dn[_leaves(parent)[0]])
+    Ws = [np.zeros((int(dn[0]), int(dn[0])))] + [
+        rng.standard_normal((int(dn[i]), int(dn[parent[i]]))) / np.sqrt(dn[parent[i]]) for i in range(1, n)]
+    bs = [np.zeros(int(dn[0]))] + [rng.standard_normal(int(dn[i])) for i in range(1, n)]
+    C = rng.standard_normal((obs, dl)) / np.sqrt(dl)
     if orth_C:
         # orthogonal columns (C^T C diagonal), so a leaf's posterior covariance is diagonal
         q, _ = np.linalg.qr(C)
-        C = q * rng.uniform(0.5, 1.5, size=d)
+        C = q * rng.uniform(0.5, 1.5, size=dl)
     return Ws, bs, C
 
 
 def _ancestral_x(rng, parent, Ws, bs, C, prior_var, obs_var):
     n = len(parent)
-    d = bs[0].shape[0]
-    z = np.zeros((n, d))
-    z[0] = bs[0] + np.sqrt(prior_var) * rng.standard_normal(d)
+    z = [None] * n
+    z[0] = bs[0] + np.sqrt(prior_var) * rng.standard_normal(bs[0].shape[0])
     for i in range(1, n):
-        z[i] = Ws[i] @ z[parent[i]] + bs[i] + np.sqrt(prior_var) * rng.standard_normal(d)
+        z[i] = Ws[i] @ z[parent[i]] + bs[i] + np.sqrt(prior_var) * rng.standard_normal(bs[i].shape[0])
     xs = {}
     for leaf in _leaves(parent):
         xs[leaf] = C @ z[leaf] + np.sqrt(obs_var) * rng.standard_normal(C.shape[0])
     return xs
 
 
-def _instance(rng, parent, K, Ws, bs, C, prior_var, obs_var, exact_proposal, mean_noise, std_scale,
-              fac=None):
-    """Draw x, the proposal and eps for one instance (model fixed)."""
+def _instance(rng, parent, Kn, dn, Ws, bs, C, prior_var, obs_var, exact_proposal, mean_noise,
+              std_scale, fac=None):
+    """Draw x, the proposal and eps for one instance (model fixed).  Returns flat arrays."""
     n = len(parent)
-    d = bs[0].shape[0]
+    uniform = len(set(Kn)) == 1 and len(set(dn)) == 1
     xs = _ancestral_x(rng, parent, Ws, bs, C, prior_var, obs_var)
     if fac is None:  # per-instance model: exact marginals by tree belief propagation
-        pm, ps = _posterior_tree_bp(parent, Ws, bs, C, xs, prior_var, obs_var)
+        pm, ps = _posterior_tree_bp(parent, Ws, bs, C, xs, prior_var, obs_var, dn)
     else:            # shared model: one dense factorisation serves every instance
         pm, ps = _posterior_mean(fac, bs, C, xs, prior_var, obs_var), fac["std"]
+    pm, ps = np.concatenate(pm), np.concatenate(ps)
     if exact_proposal:
         m, s = pm, ps
     else:
-        m = pm + mean_noise * rng.standard_normal((n, d))
+        m = pm + mean_noise * rng.standard_normal(pm.shape[0])
         s = std_scale * ps
-    eps = rng.standard_normal((n, K, d), dtype=np.float32)
+    if uniform:
+        eps = rng.standard_normal((n, int(Kn[0]), int(dn[0])), dtype=np.float32).ravel()
+    else:
+        eps = np.concatenate([rng.standard_normal((int(Kn[i]), int(dn[i])), dtype=np.float32).ravel()
+                              for i in range(n)])
     x = np.concatenate([xs[l] for l in sorted(xs)])
     return x, m, np.log(s), eps
 
@@ -237,45 +292,59 @@ def _instance(rng, parent, K, Ws, bs, C, prior_var, obs_var, exact_proposal, mea
 def make_problem(parents, Ks, ds, obss, *, shared, seed, prior_var=1.0, obs_var=0.1,
                  exact_proposal=False, zero_W=False, mean_noise=0.5, std_scale=1.2,
                  name="", model_override=None, orth_C=False) -> Problem:
-    """General batch builder.  parents: list of per-instance parent arrays."""
+    """General batch builder.  parents: list of per-instance parent arrays; Ks[b] / ds[b]: an
+    int (every latent of b) or a list of per-latent values (Eq. (is)'s K_i; d_i with W_i of
+    shape d_i x d_parent; the leaves of an instance must share d)."""
     B = len(parents)
     base = np.random.PCG64(seed)
     model_rng = np.random.Generator(base)
     n_arr = np.array([len(p) for p in parents], dtype=np.int32)
+    per = lambda v, n: [int(v)] * n if np.isscalar(v) else [int(a) for a in v]
+    Kns = [per(Ks[b], len(parents[b])) for b in range(B)]
+    dns = [per(ds[b], len(parents[b])) for b in range(B)]
+    ragged = any(len(set(k)) > 1 for k in Kns) or any(len(set(v)) > 1 for v in dns)
+    for b in range(B):
+        dl = {dns[b][l] for l in _leaves(np.asarray(parents[b]))}
+        assert len(dl) == 1, "the leaves of an instance share one dimension"
     eps_l, m_l, ls_l, x_l, W_l, b_l, C_l = [], [], [], [], [], [], []
     shared_model = None
     if shared:
-        assert len(set(map(tuple, map(list, parents)))) == 1 and len(set(ds)) == 1 and len(set(obss)) == 1
-        shared_model = model_override or _draw_model(model_rng, len(parents[0]), ds[0], obss[0], orth_C)
+        assert len(set(map(tuple, map(list, parents)))) == 1 and len(set(map(tuple, dns))) == 1 \
+            and len(set(obss)) == 1
+        par0 = np.asarray(parents[0], dtype=np.int64)
+        shared_model = model_override or _draw_model(model_rng, par0, dns[0], obss[0], orth_C)
         if zero_W:
             shared_model = ([np.zeros_like(w) for w in shared_model[0]],) + tuple(shared_model[1:])
-        shared_fac = _posterior_factor(np.asarray(parents[0], dtype=np.int64), shared_model[0],
-                                       shared_model[2], prior_var, obs_var)
+        shared_fac = _posterior_factor(par0, shared_model[0], shared_model[2], prior_var, obs_var, dns[0])
     for b in range(B):
         rng = np.random.Generator(base.jumped(b + 1))
         parent = np.asarray(parents[b], dtype=np.int64)
         if shared:
             Ws, bs, C = shared_model
         else:
-            Ws, bs, C = _draw_model(rng, len(parent), ds[b], obss[b], orth_C)
+            Ws, bs, C = _draw_model(rng, parent, dns[b], obss[b], orth_C)
             if zero_W:
                 Ws = [np.zeros_like(w) for w in Ws]
-            W_l.append(np.stack(Ws).ravel()); b_l.append(np.stack(bs).ravel()); C_l.append(C.ravel())
-        x, m, ls, eps = _instance(rng, parent, Ks[b], Ws, bs, C, prior_var, obs_var,
+            W_l.append(np.concatenate([w.ravel() for w in Ws])); b_l.append(np.concatenate(bs))
+            C_l.append(C.ravel())
+        x, m, ls, eps = _instance(rng, parent, Kns[b], dns[b], Ws, bs, C, prior_var, obs_var,
                                   exact_proposal, mean_noise, std_scale,
                                   fac=shared_fac if shared else None)
-        eps_l.append(eps.ravel()); m_l.append(m.ravel()); ls_l.append(ls.ravel()); x_l.append(x)
+        eps_l.append(eps); m_l.append(m); ls_l.append(ls); x_l.append(x)
     if shared:
         Ws, bs, C = shared_model
-        W_l, b_l, C_l = [np.stack(Ws).ravel()], [np.stack(bs).ravel()], [C.ravel()]
+        W_l, b_l, C_l = [np.concatenate([w.ravel() for w in Ws])], [np.concatenate(bs)], [C.ravel()]
     f32 = lambda lst: np.ascontiguousarray(np.concatenate(lst).astype(np.float32))
+    leaf_d = [dns[b][_leaves(np.asarray(parents[b]))[0]] for b in range(B)]
     return Problem(
         n=n_arr, parent=np.concatenate([np.asarray(p, dtype=np.int32) for p in parents]),
-        K=np.asarray(Ks, dtype=np.int32), d=np.asarray(ds, dtype=np.int32),
+        K=np.asarray([k[0] for k in Kns], dtype=np.int32), d=np.asarray(leaf_d, dtype=np.int32),
         obs=np.asarray(obss, dtype=np.int32), shared=bool(shared),
         prior_var=float(prior_var), obs_var=float(obs_var),
         eps=f32(eps_l), q_mean=f32(m_l), q_logstd=f32(ls_l), W=f32(W_l), bias=f32(b_l),
-        C=f32(C_l), x=f32(x_l), name=name)
+        C=f32(C_l), x=f32(x_l), name=name,
+        Kn=np.concatenate([np.asarray(k, dtype=np.int32) for k in Kns]) if ragged else None,
+        dn=np.concatenate([np.asarray(v, dtype=np.int32) for v in dns]) if ragged else None)
 
 
 def chain_parents(n: int) -> np.ndarray:
@@ -341,6 +410,36 @@ def star(N: int, K: int, d: int = 1, obs: int | None = None, B: int = 1, seed: i
     p = make_problem([parent] * B, [K] * B, [d] * B, [obs] * B, shared=False, seed=seed, **kw)
     p.name = "star_N%d_K%d_d%d_B%d" % (N, K, d, B)
     return p
+
+
+def layered_chain(widths, K, obs, B, seed=None, **kw) -> Problem:
+    """A chain whose latents have the given dimensions, root first, each with K samples (or
+    a per-latent list), one model shared by the B instances.  The shape of the paper's
+    five-layer MNIST model (widths 4/8/16/32/64 from the top, K = 20; Section 4), with a
+    synthetic Gaussian observation of dimension obs in place of the images."""
+    n = len(widths)
+    seed = SEED_BASE + 7 if seed is None else seed
+    p = make_problem([chain_parents(n)] * B, [K] * B, [list(widths)] * B, [obs] * B,
+                     shared=True, seed=seed, **kw)
+    p.name = "layered_chain_%s_K%s_B%d" % ("-".join(map(str, widths)), K, B)
+    return p
+
+
+def ragged_trees(B, seed, n_choices=(1, 2, 3, 5, 7), Ks=(1, 2, 3, 4), ds=(1, 2, 3), max_depth=3,
+                 **kw) -> Problem:
+    """Random trees whose latents draw their own K_i and d_i (the leaves of an instance share
+    one d), each instance with its own model."""
+    rng = np.random.Generator(np.random.PCG64(seed + 2_000_003))
+    parents, Kns, dns = [], [], []
+    for _ in range(B):
+        par = random_tree(rng, int(rng.choice(n_choices)), max_depth)
+        leaves = set(_leaves(par))
+        dl = int(rng.choice(ds))
+        parents.append(par)
+        Kns.append([int(rng.choice(Ks)) for _ in range(len(par))])
+        dns.append([dl if i in leaves else int(rng.choice(ds)) for i in range(len(par))])
+    obss = [int(rng.integers(1, 5)) for _ in range(B)]
+    return make_problem(parents, Kns, dns, obss, shared=False, seed=seed, **kw)
 
 
 def redraw_eps(p: Problem, seed: int) -> np.ndarray:

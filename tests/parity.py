@@ -27,16 +27,14 @@ def gpu_run(p, precision="fp32", grads=True, grad_out=None, want=None):
 
 
 def oracle_deps(p, g):
-    """d/d eps = exp(logs) * dz, from the oracle's dz."""
+    """d/d eps = exp(logs) * dz, from the oracle's dz (latent by latent: K_i x d_i blocks)."""
     s = np.exp(p.q_logstd.astype(np.float64))
     out = np.empty_like(g["dz"])
     oe = oq = 0
-    for b in range(p.B):
-        n, K, d = int(p.n[b]), int(p.K[b]), int(p.d[b])
-        out[oe:oe + n * K * d] = (g["dz"][oe:oe + n * K * d].reshape(n, K, d) *
-                                  s[oq:oq + n * d].reshape(n, 1, d)).ravel()
-        oe += n * K * d
-        oq += n * d
+    for K, d in zip(p.K_nodes().astype(int), p.d_nodes().astype(int)):
+        out[oe:oe + K * d] = (g["dz"][oe:oe + K * d].reshape(K, d) * s[oq:oq + d]).ravel()
+        oe += K * d
+        oq += d
     return out
 
 
