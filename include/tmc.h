@@ -65,29 +65,36 @@ typedef enum {
 typedef struct tmc_plan_s* tmc_plan;
 
 /* Problem description; all arrays are HOST memory and are copied into the plan.
- * Section 2.1 fixes what a problem is: the graph (parents), K_i samples per latent, the
- * generative model P and the proposal Q. */
+ * Section 2.1 fixes what a problem is: the graph (parents), K_i samples per latent (Eq. (is)
+ * lets K_i differ from latent to latent), the generative model P and the proposal Q.
+ * Sizes: with K_node == NULL every latent of instance b has K[b] samples, and with d_node ==
+ * NULL dimension d[b]; otherwise K_node / d_node give K_i / d_i latent by latent (then W_i is
+ * d_i x d_parent, and the leaves of an instance must share one dimension, the one C acts on). */
 typedef struct {
   int32_t num_instances;  /* B >= 1                                                        */
   const int32_t* n;       /* [B]    latents per instance, n_b >= 1                          */
   const int32_t* parent;  /* [sum n_b] local parent index, parent[0] = -1, 0<=parent[i]<i   */
-  const int32_t* K;       /* [B]    samples per latent (the same for every latent of b)     */
-  const int32_t* d;       /* [B]    latent dimension                                        */
+  const int32_t* K;       /* [B]    samples per latent (every latent of b; see K_node)      */
+  const int32_t* d;       /* [B]    latent dimension (every latent of b; see d_node)        */
   const int32_t* obs_dim; /* [B]    observation dimension                                   */
-  int32_t shared_params;  /* 1: all instances share W, bias, C (then n, parent, d, obs_dim  */
-                          /*    must agree); 0: each instance has its own                   */
+  int32_t shared_params;  /* 1: all instances share W, bias, C (then n, parent, d_i,       */
+                          /*    obs_dim must agree; K may differ); 0: each has its own      */
   double prior_var;       /* sigma_z^2 > 0                                                  */
   double obs_var;         /* sigma_x^2 > 0                                                  */
   int32_t precision;      /* tmc_precision                                                  */
+  const int32_t* K_node;  /* [sum n_b] per-latent K_i, or NULL                               */
+  const int32_t* d_node;  /* [sum n_b] per-latent d_i, or NULL                               */
 } tmc_problem_desc;
 
-/* Device inputs: contiguous float32, instance b directly after instance b-1.
- *   eps       [sum n_b*K_b*d_b]  [i][k][j]   proposal noise
- *   q_mean    [sum n_b*d_b]      [i][j]      proposal means m_i
- *   q_logstd  [sum n_b*d_b]      [i][j]      proposal log standard deviations
- *   W         [n*d*d] shared, else [sum n_b*d_b*d_b]; [i][r][c]; W_0 is ignored
- *   bias      [n*d]   shared, else [sum n_b*d_b];     bias_0 is the root prior mean
- *   C         [obs*d] shared, else [sum obs_b*d_b];   [o][c]
+/* Device inputs: contiguous float32, instance b directly after instance b-1 and latent i
+ * after latent i-1 within it (sizes K_i, d_i as described above; d_p = the parent's d):
+ *   eps       [sum K_i*d_i]      [i][k][j]   proposal noise
+ *   q_mean    [sum d_i]          [i][j]      proposal means m_i
+ *   q_logstd  [sum d_i]          [i][j]      proposal log standard deviations
+ *   W         [sum d_i*d_p]      [i][r][c]   W_i is d_i x d_p; the root's block is d_0 x d_0
+ *                                            and ignored (one instance's blocks when shared)
+ *   bias      [sum d_i]          bias_0 is the root prior mean (one instance's when shared)
+ *   C         [obs*d_leaf] per instance (one when shared), [o][c]
  *   x         [sum leaves_b*obs_b]  one observation per leaf, leaves in node order */
 typedef struct {
   const float *eps, *q_mean, *q_logstd, *W, *bias, *C, *x;

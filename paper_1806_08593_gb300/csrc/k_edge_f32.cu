@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(kThreads) k_edge_fwd_f32(Dev D, const Tile* __
   __shared__ float red[32];
   const Tile t = tiles[blockIdx.x];
   const NodeInfo nd = D.nodes[t.node];
-  const int K = nd.K, d = nd.d;
+  const int K = nd.K, Kp = nd.Kp, d = nd.d;  // child samples (columns), parent samples (rows)
   const float iv = D.inv_var;
   // beta_i and its max
   float mx = -INFINITY;
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kThreads) k_edge_fwd_f32(Dev D, const Tile* __
   __syncthreads();
 
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  const int rows = min(kTile, K - t.row0);
+  const int rows = min(kTile, Kp - t.row0);
   const float* M = D.mut + nd.off_nkd + (long long)t.row0 * d;
   const float* Z = D.zt + nd.off_nkd;
   float rm[4], rs[4];
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kThreads) k_edge_fwd_f32(Dev D, const Tile* __
     const float gm = row_group_max(rm[a]);
     const float s = row_group_sum(rs[a] * __expf(rm[a] - gm));
     const int k = t.row0 + ty * 4 + a;
-    if (tx == 0 && k < K) D.lam[nd.off_nk + k] = gm + logf(s) - 0.5f * D.mun[nd.off_nk + k] * iv;
+    if (tx == 0 && k < Kp) D.lam[nd.off_nk + k] = gm + logf(s) - 0.5f * D.mun[nd.off_nk + k] * iv;
   }
 }
 
@@ -115,17 +115,17 @@ __global__ void __launch_bounds__(kThreads) k_edge_bwd_rows_f32(Dev D, const Til
   const Tile t = tiles[blockIdx.x];
   const NodeInfo nd = D.nodes[t.node];
   const NodeInfo pn = D.nodes[nd.parent];
-  const int K = nd.K, d = nd.d;
+  const int K = nd.K, Kp = nd.Kp, d = nd.d;  // child samples (columns), parent samples (rows)
   const float iv = D.inv_var;
   for (int k = threadIdx.x; k < K; k += kThreads)
     cb[k] = D.beta[nd.off_nk + k] - 0.5f * D.zn[nd.off_nk + k] * iv;
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  const int rows = min(kTile, K - t.row0);
+  const int rows = min(kTile, Kp - t.row0);
   float ra[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const int k = t.row0 + ty * 4 + a;
-    ra[a] = (k < K) ? adj_row_bias(D, nd, pn, k) : -INFINITY;
+    ra[a] = (k < Kp) ? adj_row_bias(D, nd, pn, k) : -INFINITY;
   }
   __syncthreads();
   const float* M = D.mut + nd.off_nkd + (long long)t.row0 * d;
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kThreads) k_edge_bwd_rows_f32(Dev D, const Til
     for (int a = 0; a < 4; ++a) {
       const float rq = row_group_sum(rsum[a]);
       const int k = t.row0 + ty * 4 + a;
-      if (k >= K) continue;
+      if (k >= Kp) continue;
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         int j = j0 + tx * 4 + b;
@@ -190,9 +190,9 @@ __global__ void __launch_bounds__(kThreads) k_edge_bwd_cols_f32(Dev D, const Til
   const Tile t = tiles[blockIdx.x];
   const NodeInfo nd = D.nodes[t.node];
   const NodeInfo pn = D.nodes[nd.parent];
-  const int K = nd.K, d = nd.d;
+  const int K = nd.K, Kp = nd.Kp, d = nd.d;  // child samples (owned rows), parent samples
   const float iv = D.inv_var;
-  for (int k = threadIdx.x; k < K; k += kThreads) rb[k] = adj_row_bias(D, nd, pn, k);
+  for (int k = threadIdx.x; k < Kp; k += kThreads) rb[k] = adj_row_bias(D, nd, pn, k);
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
   const int cols = min(kTile, K - t.row0);  // child samples owned
   float cva[4];
@@ -208,15 +208,15 @@ __global__ void __launch_bounds__(kThreads) k_edge_bwd_cols_f32(Dev D, const Til
     float o0[4][4], o1[4][4], qsum[4] = {0.f, 0.f, 0.f, 0.f};
     zero_acc(o0);
     zero_acc(o1);
-    for (int r0 = 0; r0 < K; r0 += kTile) {
-      const int rws = min(kTile, K - r0);
+    for (int r0 = 0; r0 < Kp; r0 += kTile) {
+      const int rws = min(kTile, Kp - r0);
       float acc[4][4];  // acc[a][b]: child k' = row0 + ty*4 + a, parent k = r0 + tx*4 + b
       zero_acc(acc);
       tile_gemm<true, true>(acc, Zo, d, cols, M + (long long)r0 * d, d, rws, d, sm);
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const int k = r0 + tx * 4 + b;
-        const float rv = (k < K) ? rb[k] : -INFINITY;
+        const float rv = (k < Kp) ? rb[k] : -INFINITY;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
           const float p = __expf(fmaf(acc[a][b], iv, cva[a] + rv));

@@ -100,10 +100,10 @@ __global__ void k_sample(Dev D, const Tile* __restrict__ tiles) {
   for (int r = w; r < kTile; r += kThreads / 32) {
     const int k = t.row0 + r;
     if (k >= nd.K) break;
-    const long long base = nd.off_nkd + (long long)k * d;
+    const long long base = nd.off_nkd + (long long)k * d, ebase = nd.off_e + (long long)k * d;
     float se = 0.f, sz = 0.f, sr = 0.f;
     for (int j = lane; j < d; j += 32) {
-      const float e = D.eps[base + j];
+      const float e = D.eps[ebase + j];
       const float z = s_std[j] * e;
       bad |= !isfinite(z);
       D.zt[base + j] = z;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kThreads) k_obs_fwd(Dev D, const Tile* __restr
 // ---------------------------------------------------------------------------------------
 // Conditional means (the linear cost of Section 2.4): mu~_i[k] = W_i z_p^k + bias_i - m_i
 //   = W_i z~_p^k + c_i,  c_i = W_i m_p + bias_i - m_i;  also |mu~_i[k]|^2.
-// Grid: (non-root node i, 64-sample tile of the parent's samples).
+// Grid: (non-root node i, 64-sample tile of the parent's samples).  W_i is d_i x d_p.
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_project(Dev D, const Tile* __restrict__ tiles) {
   extern __shared__ float cs[];
@@ -189,31 +189,31 @@ __global__ void __launch_bounds__(kThreads) k_project(Dev D, const Tile* __restr
   const Tile t = tiles[blockIdx.x];
   const NodeInfo nd = D.nodes[t.node];
   const NodeInfo pn = D.nodes[nd.parent];
-  const int d = nd.d;
+  const int d = nd.d, dp = nd.dp, Kp = nd.Kp;
   const float* Wi = D.W + nd.off_W;
   for (int r = threadIdx.x; r < d; r += blockDim.x) {
-    const float* w = Wi + (long long)r * d;
+    const float* w = Wi + (long long)r * dp;
     const float* mp = D.q_mean + pn.off_q;
     float s = 0.f;
-    for (int c = 0; c < d; ++c) s = fmaf(w[c], mp[c], s);
+    for (int c = 0; c < dp; ++c) s = fmaf(w[c], mp[c], s);
     cs[r] = s + D.bias[nd.off_bias + r] - D.q_mean[nd.off_q + r];
   }
   __syncthreads();
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  const int rows = min(kTile, nd.K - t.row0);
-  const float* Zp = D.zt + pn.off_nkd + (long long)t.row0 * d;
+  const int rows = min(kTile, Kp - t.row0);
+  const float* Zp = D.zt + pn.off_nkd + (long long)t.row0 * dp;
   float rs[4] = {0.f, 0.f, 0.f, 0.f};
   for (int r0 = 0; r0 < d; r0 += kTile) {
     float acc[4][4];
     zero_acc(acc);
-    tile_gemm<true, true>(acc, Zp, d, rows, Wi + (long long)r0 * d, d, min(kTile, d - r0), d, sm);
+    tile_gemm<true, true>(acc, Zp, dp, rows, Wi + (long long)r0 * dp, dp, min(kTile, d - r0), dp, sm);
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       const int k = t.row0 + ty * 4 + a;
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const int r = r0 + tx * 4 + b;
-        if (k < nd.K && r < d) {
+        if (k < Kp && r < d) {
           const float v = acc[a][b] + cs[r];
           D.mut[nd.off_nkd + (long long)k * d + r] = v;
           rs[a] = fmaf(v, v, rs[a]);
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kThreads) k_project(Dev D, const Tile* __restr
   for (int a = 0; a < 4; ++a) {
     const float s = row_group_sum(rs[a]);
     const int k = t.row0 + ty * 4 + a;
-    if (tx == 0 && k < nd.K) D.mun[nd.off_nk + k] = s;
+    if (tx == 0 && k < Kp) D.mun[nd.off_nk + k] = s;
   }
 }
 
@@ -352,11 +352,11 @@ __global__ void __launch_bounds__(kThreads) k_node_grad(Dev D, const Tile* __res
     const int ncol = min(kTile, d - c0);
     float acc[4][4];
     zero_acc(acc);
-    // children: out[k][c] += sum_r dmu_c[k][r] W_c[r][c]
+    // children: out[k][c] += sum_r dmu_c[k][r] W_c[r][c]   (W_c is d_c x d)
     for (int ci = nd.child_begin; ci < nd.child_end; ++ci) {
       const NodeInfo ch = D.nodes[D.children[ci]];
-      tile_gemm<true, false>(acc, D.dmu + ch.off_nkd + (long long)t.row0 * d, d, rows,
-                             D.W + ch.off_W + c0, d, ncol, d, sm);
+      tile_gemm<true, false>(acc, D.dmu + ch.off_nkd + (long long)t.row0 * ch.d, ch.d, rows,
+                             D.W + ch.off_W + c0, d, ncol, ch.d, sm);
     }
     if (leaf) {
       // out[k][c] += q[k] / obs_var * sum_o r[k][o] C[o][c],  r = x~ - C z~
@@ -406,10 +406,11 @@ __global__ void __launch_bounds__(kThreads) k_node_grad(Dev D, const Tile* __res
         }
         D.gz[idx] = g;
         if (D.dz || D.deps) {
+          const long long eidx = nd.off_e + (long long)k * d + c;
           const float ls = D.q_logstd[nd.off_q + c];
           const float dzv = go * (g + qk[a] * zt * expf(-2.f * ls));
-          if (D.dz) D.dz[idx] = dzv;
-          if (D.deps) D.deps[idx] = dzv * expf(ls);
+          if (D.dz) D.dz[eidx] = dzv;
+          if (D.deps) D.deps[eidx] = dzv * expf(ls);
         }
       }
     }
@@ -483,9 +484,9 @@ __global__ void __launch_bounds__(kThreads) k_param_dW(Dev D, const int* __restr
   const int g = nonroot[blockIdx.x];
   const NodeInfo nd = D.nodes[g];
   const NodeInfo pn = D.nodes[nd.parent];
-  const int d = nd.d, K = nd.K;
+  const int d = nd.d, dp = nd.dp, K = nd.Kp;  // dmu_i[k] for the parent's samples k
   const int r0 = blockIdx.y * kTile, c0 = blockIdx.z * kTile;
-  if (r0 >= d || c0 >= d) return;
+  if (r0 >= d || c0 >= dp) return;
   const float go = D.grad_out ? (float)D.grad_out[nd.b] : 1.f;
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
   if (threadIdx.x < kTile) {
@@ -499,7 +500,7 @@ __global__ void __launch_bounds__(kThreads) k_param_dW(Dev D, const int* __restr
   zero_acc(acc);
   // opA(m = r, l = k) = dmu[k][r0 + m];  opB(n = c, l = k) = z~_p[k][c0 + n]
   tile_gemm<false, false>(acc, D.dmu + nd.off_nkd + r0, d, min(kTile, d - r0),
-                          D.zt + pn.off_nkd + c0, d, min(kTile, d - c0), K, sm);
+                          D.zt + pn.off_nkd + c0, dp, min(kTile, dp - c0), K, sm);
   __syncthreads();
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
@@ -508,10 +509,10 @@ __global__ void __launch_bounds__(kThreads) k_param_dW(Dev D, const int* __restr
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int c = c0 + tx * 4 + b;
-      if (c >= d) continue;
+      if (c >= dp) continue;
       const float v = go * (acc[a][b] + colsum[ty * 4 + a] * D.q_mean[pn.off_q + c]);
-      if (D.shared) D.pW[nd.off_pW + (long long)r * d + c] = v;
-      else if (D.dW) D.dW[nd.off_W + (long long)r * d + c] = v;
+      if (D.shared) D.pW[nd.off_pW + (long long)r * dp + c] = v;
+      else if (D.dW) D.dW[nd.off_W + (long long)r * dp + c] = v;
     }
   }
   if (c0 == 0 && threadIdx.x < kTile && r0 + threadIdx.x < d) {
@@ -531,7 +532,7 @@ __global__ void __launch_bounds__(kThreads) k_param_dC(Dev D) {
   __shared__ float rsm[kTile * kLd];  // q-weighted residuals, [k][o]
   __shared__ float rsum[kTile];
   const InstInfo in = D.insts[blockIdx.x];
-  const int d = in.d, obs = in.obs, K = in.K;
+  const int d = in.d, obs = in.obs;  // d of the leaves
   const int o0 = blockIdx.y * kTile, c0 = blockIdx.z * kTile;
   if (o0 >= obs || c0 >= d) return;
   const int nob = min(kTile, obs - o0), ncol = min(kTile, d - c0);
@@ -547,6 +548,7 @@ __global__ void __launch_bounds__(kThreads) k_param_dC(Dev D) {
     __syncthreads();
     centred_obs(D, nd, xs);
     __syncthreads();
+    const int K = nd.K;
     float leaf_rsum[4] = {0.f, 0.f, 0.f, 0.f};
     for (int k0 = 0; k0 < K; k0 += kTile) {
       const int rows = min(kTile, K - k0);
@@ -610,14 +612,14 @@ __global__ void __launch_bounds__(kThreads) k_param_dC(Dev D) {
 }
 
 // Shared parameters: dW, dbias, dC = sum over instances of the partials (fixed order).
-__global__ void k_shared_reduce(Dev D, int n, int d, int obs) {
-  const long long nW = (long long)n * d * d, nb = (long long)n * d, nC = (long long)obs * d;
+// nW, nb, nC: one instance's sizes; the root's block of W (the first rootW entries) is zero.
+__global__ void k_shared_reduce(Dev D, long long nW, long long nb, long long nC, long long rootW) {
   const long long total = nW + nb + nC;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     float s = 0.f;
     if (e < nW) {
-      if (e >= (long long)d * d)
+      if (e >= rootW)
         for (int b = 0; b < D.num_inst; ++b) s += D.pW[(long long)b * nW + e];
       if (D.dW) D.dW[e] = s;
     } else if (e < nW + nb) {
@@ -666,10 +668,11 @@ void launch_param_dC(const Dev& D, int maxd, int maxobs, cudaStream_t s) {
   k_param_dC<<<dim3(D.num_inst, (maxobs + kTile - 1) / kTile, (maxd + kTile - 1) / kTile), kThreads,
                kMaxD * sizeof(float), s>>>(D);
 }
-void launch_shared_reduce(const Dev& D, int n, int d, int obs, cudaStream_t s) {
-  const long long total = (long long)n * d * d + (long long)n * d + (long long)obs * d;
+void launch_shared_reduce(const Dev& D, long long nW, long long nb, long long nC, long long rootW,
+                          cudaStream_t s) {
+  const long long total = nW + nb + nC;
   const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
-  k_shared_reduce<<<blocks, 256, 0, s>>>(D, n, d, obs);
+  k_shared_reduce<<<blocks, 256, 0, s>>>(D, nW, nb, nC, rootW);
 }
 void launch_root_bias(const Dev&, cudaStream_t) {}
 

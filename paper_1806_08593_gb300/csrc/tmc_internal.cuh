@@ -17,16 +17,20 @@ constexpr int kMaxD = 1024;     // latent / observation dimension supported
 struct NodeInfo {
   int b, i;            // instance, local node index
   int parent;          // global id of the parent node, -1 for the root
-  int K, d, obs;       // samples, latent dim, observation dim of the instance
+  int K, d, obs;       // samples and dimension of this latent, observation dim of the instance
+  int Kp, dp;          // the parent's K and d (root: 0 and its own d)
   int leaf_slot;       // >= 0: index of this leaf among the instance's leaves; -1 otherwise
   int child_begin;     // children[child_begin .. child_end) are global ids of the children
   int child_end;
   int level;           // depth below the root
   int root;            // global id of the instance's root
-  long long off_nk;    // start of this node's [K] block in per-sample scalar arrays
-  long long off_nkd;   // start of this node's [K][d] block in per-sample vector arrays
+  long long off_nk;    // start of this node's block in per-sample scalar arrays (Kmax entries
+                       // of the instance: its own K values, or the Kp values its edge keeps
+                       // per parent sample: message, |mu~|^2)
+  long long off_nkd;   // start of this node's [Kmax][d] block in per-sample vector arrays
+  long long off_e;     // start of this node's [K][d] block in eps / dz / deps (the caller's layout)
   long long off_q;     // start of m_i / logs_i ([d]) in q_mean / q_logstd
-  long long off_W;     // start of W_i ([d][d]) in W
+  long long off_W;     // start of W_i ([d][dp]) in W
   long long off_bias;  // start of bias_i ([d]) in bias
   long long off_C;     // start of the instance's C ([obs][d])
   long long off_x;     // start of this leaf's observation ([obs]) in x (leaves only)
@@ -35,7 +39,7 @@ struct NodeInfo {
 
 struct InstInfo {
   int node0;           // global id of the root
-  int n, K, d, obs;
+  int n, K, d, obs;    // K of the root, d of the leaves (the dimension C acts on)
   long long off_C, off_pC;  // instance C offset; per-instance dC partial offset
 };
 
@@ -117,7 +121,9 @@ void launch_node_grad(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t 
 void launch_node_reduce(const Dev& D, cudaStream_t s);
 void launch_param_dW(const Dev& D, const int* nonroot, int n_nonroot, int maxd, cudaStream_t s);
 void launch_param_dC(const Dev& D, int maxd, int maxobs, cudaStream_t s);
-void launch_shared_reduce(const Dev& D, int n, int d, int obs, cudaStream_t s);
+// nW, nb, nC: one instance's W, bias, C sizes; rootW: its unused root block of W
+void launch_shared_reduce(const Dev& D, long long nW, long long nb, long long nC, long long rootW,
+                          cudaStream_t s);
 void launch_root_bias(const Dev& D, cudaStream_t s);
 
 }  // namespace tmc

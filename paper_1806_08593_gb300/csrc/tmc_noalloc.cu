@@ -73,6 +73,7 @@ tmc_status build_tables(const tmc_problem_desc* ds, Layout& L) {
   if (B < 1 || !ds->n || !ds->parent || !ds->K || !ds->d || !ds->obs_dim) return TMC_ERR_INVALID_ARG;
   if (!(ds->prior_var > 0.0) || !(ds->obs_var > 0.0)) return TMC_ERR_INVALID_ARG;
   if (ds->precision != TMC_PREC_FP32) return TMC_ERR_UNSUPPORTED;
+  if (ds->K_node || ds->d_node) return TMC_ERR_UNSUPPORTED;  // one K and d per instance here
   if (B > kNaMaxInst) return TMC_ERR_UNSUPPORTED;
   L = Layout();
   L.B = B;
@@ -107,11 +108,14 @@ tmc_status build_tables(const tmc_problem_desc* ds, Layout& L) {
       nd.parent = i ? node0 + par[i] : -1;
       nd.K = K;
       nd.d = d;
+      nd.Kp = i ? K : 0;
+      nd.dp = d;
       nd.obs = obs;
       nd.level = i ? h_nodes[node0 + par[i]].level + 1 : 0;
       nd.root = node0;
       nd.off_nk = off_nk + (long long)i * K;
       nd.off_nkd = off_nkd + (long long)i * K * d;
+      nd.off_e = nd.off_nkd;
       nd.off_q = off_q + (long long)i * d;
       nd.off_W = iW + (long long)i * d * d;
       nd.off_bias = ib + (long long)i * d;

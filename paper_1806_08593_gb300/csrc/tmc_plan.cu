@@ -34,7 +34,9 @@ struct tmc_plan_s {
   // description
   int B = 0, shared = 0, precision = 0;
   double prior_var = 1.0, obs_var = 1.0;
-  int maxK = 0, maxd = 0, maxobs = 0, maxlevel = 0, shared_n = 0, shared_d = 0, shared_obs = 0;
+  int maxK = 0, maxd = 0, maxobs = 0, maxlevel = 0;
+  bool ragged = false;  // some instance has a different K or d from latent to latent
+  long long shared_nW = 0, shared_nb = 0, shared_nC = 0, shared_rootW = 0;  // one instance's parameter sizes
   int root_fanout = 0;  // most children of any instance's root
   long long tot_nk = 0, tot_nkd = 0, tot_q = 0, tot_W = 0;
 
@@ -52,7 +54,8 @@ struct tmc_plan_s {
   // tile lists: [begin, end) ranges into one device array
   std::vector<Tile> tiles;
   int t_sample_b = 0, t_sample_e = 0, t_leaf_b = 0, t_leaf_e = 0, t_proj_b = 0, t_proj_e = 0;
-  std::vector<int> t_level_b, t_level_e;  // per level (index = level), edges whose child is there
+  std::vector<int> t_level_b, t_level_e;    // per level: edges whose child is there, parent rows
+  std::vector<int> t_clevel_b, t_clevel_e;  // the same edges, child rows (columns adjoint pass)
 
   // device
   NodeInfo* d_nodes = nullptr;
@@ -155,40 +158,62 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
   p->prior_var = ds->prior_var;
   p->obs_var = ds->obs_var;
 
-  long long poff = 0, off_nk = 0, off_nkd = 0, off_q = 0, off_W = 0, off_bias = 0, off_C = 0,
-            off_x = 0, off_pW = 0, off_pC = 0;
+  long long poff = 0, off_nk = 0, off_nkd = 0, off_e = 0, off_q = 0, off_W = 0, off_bias = 0,
+            off_C = 0, off_x = 0, off_pW = 0, off_pC = 0;
   for (int b = 0; b < B; ++b) {
-    const int n = ds->n[b], K = ds->K[b], d = ds->d[b], obs = ds->obs_dim[b];
-    if (n < 1 || K < 1 || d < 1 || obs < 1) return TMC_ERR_INVALID_ARG;
-    if (K > kMaxK || d > kMaxD || obs > kMaxD) return TMC_ERR_UNSUPPORTED;
+    const int n = ds->n[b], obs = ds->obs_dim[b];
+    if (n < 1 || obs < 1) return TMC_ERR_INVALID_ARG;
+    if (obs > kMaxD) return TMC_ERR_UNSUPPORTED;
     const int* par = ds->parent + poff;
     if (par[0] != -1) return TMC_ERR_INVALID_ARG;
     for (int i = 1; i < n; ++i)
       if (par[i] < 0 || par[i] >= i) return TMC_ERR_INVALID_ARG;
-    if (p->shared && b > 0) {
-      if (n != ds->n[0] || d != ds->d[0] || obs != ds->obs_dim[0]) return TMC_ERR_INVALID_ARG;
-      for (int i = 0; i < n; ++i)
-        if (par[i] != ds->parent[i]) return TMC_ERR_INVALID_ARG;
+    // per-latent sizes: K_node / d_node when given, else the instance's K[b] / d[b]
+    std::vector<int> Kv(n), dv(n);
+    for (int i = 0; i < n; ++i) {
+      Kv[i] = ds->K_node ? ds->K_node[poff + i] : ds->K[b];
+      dv[i] = ds->d_node ? ds->d_node[poff + i] : ds->d[b];
+      if (Kv[i] < 1 || dv[i] < 1) return TMC_ERR_INVALID_ARG;
+      if (Kv[i] > kMaxK || dv[i] > kMaxD) return TMC_ERR_UNSUPPORTED;
+      if (Kv[i] != Kv[0] || dv[i] != dv[0]) p->ragged = true;
     }
     const int node0 = (int)p->nodes.size();
-    // children lists and levels
+    // children lists, levels, and the leaves' common dimension (one C per instance)
     std::vector<std::vector<int>> ch(n);
     std::vector<int> level(n, 0);
     for (int i = 1; i < n; ++i) {
       ch[par[i]].push_back(i);
       level[i] = level[par[i]] + 1;
     }
-    // instance-level offsets
+    int dl = -1, Kmax = 0;
+    for (int i = 0; i < n; ++i) {
+      Kmax = std::max(Kmax, Kv[i]);
+      if (ch[i].empty()) {
+        if (dl >= 0 && dl != dv[i]) return TMC_ERR_INVALID_ARG;
+        dl = dv[i];
+      }
+    }
+    if (p->shared && b > 0) {
+      if (n != ds->n[0] || obs != ds->obs_dim[0]) return TMC_ERR_INVALID_ARG;
+      for (int i = 0; i < n; ++i)
+        if (par[i] != ds->parent[i] || dv[i] != p->nodes[i].d) return TMC_ERR_INVALID_ARG;
+    }
+    // instance-level offsets.  Per-sample workspace blocks hold Kmax rows per latent, so a
+    // latent's block also holds the K_parent values indexed by its parent's samples (the
+    // message it sends, the parent-sample conditional means).
     const long long iW = p->shared ? 0 : off_W, ib = p->shared ? 0 : off_bias,
                     iC = p->shared ? 0 : off_C;
     int leaves = 0;
+    long long e = 0, q = 0, w = 0, kd = 0;
     for (int i = 0; i < n; ++i) {
       NodeInfo nd{};
       nd.b = b;
       nd.i = i;
       nd.parent = i ? node0 + par[i] : -1;
-      nd.K = K;
-      nd.d = d;
+      nd.K = Kv[i];
+      nd.d = dv[i];
+      nd.Kp = i ? Kv[par[i]] : 0;
+      nd.dp = i ? dv[par[i]] : dv[0];
       nd.obs = obs;
       nd.leaf_slot = ch[i].empty() ? leaves++ : -1;
       nd.child_begin = (int)p->children.size();
@@ -197,52 +222,67 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
       if (i == 0) p->root_fanout = std::max(p->root_fanout, nd.child_end - nd.child_begin);
       nd.level = level[i];
       nd.root = node0;
-      nd.off_nk = off_nk + (long long)i * K;
-      nd.off_nkd = off_nkd + (long long)i * K * d;
-      nd.off_q = off_q + (long long)i * d;
-      nd.off_W = iW + (long long)i * d * d;
-      nd.off_bias = ib + (long long)i * d;
+      nd.off_nk = off_nk + (long long)i * Kmax;
+      nd.off_nkd = off_nkd + kd;
+      nd.off_e = off_e + e;
+      nd.off_q = off_q + q;
+      nd.off_W = iW + w;
+      nd.off_bias = ib + q;
       nd.off_C = iC;
       nd.off_x = off_x + (long long)(nd.leaf_slot >= 0 ? nd.leaf_slot : 0) * obs;
-      nd.off_pW = off_pW + (long long)i * d * d;
+      nd.off_pW = off_pW + w;
       p->nodes.push_back(nd);
       p->maxlevel = std::max(p->maxlevel, level[i]);
+      e += (long long)Kv[i] * dv[i];
+      kd += (long long)Kmax * dv[i];
+      q += dv[i];
+      w += (long long)dv[i] * nd.dp;
+      p->maxK = std::max(p->maxK, Kv[i]);
+      p->maxd = std::max(p->maxd, dv[i]);
     }
     InstInfo in{};
     in.node0 = node0;
     in.n = n;
-    in.K = K;
-    in.d = d;
+    in.K = Kv[0];
+    in.d = dl;
     in.obs = obs;
     in.off_C = iC;
     in.off_pC = off_pC;
     p->insts.push_back(in);
-    p->maxK = std::max(p->maxK, K);
-    p->maxd = std::max(p->maxd, d);
     p->maxobs = std::max(p->maxobs, obs);
+    if (b == 0) {  // sizes of one instance's parameters (the shared reduction)
+      p->shared_nW = w;
+      p->shared_nb = q;
+      p->shared_nC = (long long)obs * dl;
+      p->shared_rootW = (long long)dv[0] * dv[0];
+    }
     poff += n;
-    off_nk += (long long)n * K;
-    off_nkd += (long long)n * K * d;
-    off_q += (long long)n * d;
+    off_nk += (long long)n * Kmax;
+    off_nkd += kd;
+    off_e += e;
+    off_q += q;
     off_x += (long long)leaves * obs;
-    off_pW += (long long)n * d * d;
-    off_pC += (long long)obs * d;
+    off_pW += w;
+    off_pC += (long long)obs * dl;
     if (!p->shared) {
-      off_W += (long long)n * d * d;
-      off_bias += (long long)n * d;
-      off_C += (long long)obs * d;
+      off_W += w;
+      off_bias += q;
+      off_C += (long long)obs * dl;
     }
   }
   p->tot_nk = off_nk;
   p->tot_nkd = off_nkd;
   p->tot_q = off_q;
-  p->shared_n = ds->n[0];
-  p->shared_d = ds->d[0];
-  p->shared_obs = ds->obs_dim[0];
+  // the materialised-factor baseline is built for one K and d per instance
+  if (p->ragged && p->precision == TMC_PREC_FP32_UNFUSED) return TMC_ERR_UNSUPPORTED;
 
-  // tile lists
+  // tile lists (a tile is a node and 64 of its rows: its own samples, or, for the tiles of an
+  // edge p -> i in the projection, forward and rows-adjoint lists, the parent's samples)
   auto add_tiles = [&](int g) {
     for (int r = 0; r < p->nodes[g].K; r += kTile) p->tiles.push_back(Tile{g, r});
+  };
+  auto add_parent_tiles = [&](int g) {
+    for (int r = 0; r < p->nodes[g].Kp; r += kTile) p->tiles.push_back(Tile{g, r});
   };
   const int G = (int)p->nodes.size();
   p->t_sample_b = (int)p->tiles.size();
@@ -255,7 +295,7 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
   p->t_proj_b = (int)p->tiles.size();
   for (int g = 0; g < G; ++g)
     if (p->nodes[g].parent >= 0) {
-      add_tiles(g);
+      add_parent_tiles(g);
       p->nonroot.push_back(g);
     }
   p->t_proj_e = (int)p->tiles.size();
@@ -264,16 +304,22 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
     for (int g = 0; g < G; ++g)
       if (p->nodes[g].parent >= 0) {
         p->fac_off[g] = p->fac_total;
-        p->fac_total += (long long)p->nodes[g].K * p->nodes[g].K;
+        p->fac_total += (long long)p->nodes[g].Kp * p->nodes[g].K;
       }
   }
   p->t_level_b.assign(p->maxlevel + 1, 0);
   p->t_level_e.assign(p->maxlevel + 1, 0);
+  p->t_clevel_b.assign(p->maxlevel + 1, 0);
+  p->t_clevel_e.assign(p->maxlevel + 1, 0);
   for (int L = 1; L <= p->maxlevel; ++L) {
     p->t_level_b[L] = (int)p->tiles.size();
     for (int g = 0; g < G; ++g)
-      if (p->nodes[g].level == L) add_tiles(g);
+      if (p->nodes[g].level == L) add_parent_tiles(g);
     p->t_level_e[L] = (int)p->tiles.size();
+    p->t_clevel_b[L] = (int)p->tiles.size();
+    for (int g = 0; g < G; ++g)
+      if (p->nodes[g].level == L) add_tiles(g);
+    p->t_clevel_e[L] = (int)p->tiles.size();
   }
   return TMC_OK;
 }
@@ -303,9 +349,9 @@ tmc_status alloc_device(tmc_plan p) {
   if (cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) return TMC_ERR_CUDA;
 
   const long long nk = p->tot_nk, nkd = p->tot_nkd, G = (long long)p->nodes.size();
-  const long long nW = p->shared ? (long long)p->B * p->shared_n * p->shared_d * p->shared_d : 0;
-  const long long nb = p->shared ? (long long)p->B * p->shared_n * p->shared_d : 0;
-  const long long nC = p->shared ? (long long)p->B * p->shared_obs * p->shared_d : 0;
+  const long long nW = p->shared ? (long long)p->B * p->shared_nW : 0;
+  const long long nb = p->shared ? (long long)p->B * p->shared_nb : 0;
+  const long long nC = p->shared ? (long long)p->B * p->shared_nC : 0;
   // layout: 256-byte aligned sub-buffers
   struct Sub { void** dst; size_t bytes; };
   float *zt, *mut, *zn, *mun, *u, *beta, *lam, *q, *nodemax, *dmu, *gz, *pW, *pbias, *pC, *fac;
@@ -421,8 +467,8 @@ tmc_status tmc_plan_create(const tmc_problem_desc* desc, tmc_plan* out) {
   if (!p) return TMC_ERR_NOMEM;
   p->fault = fault_from_env();
   tmc_status st = build_plan(desc, p);
-  if (st == TMC_OK && (p->precision == TMC_PREC_FP16_TC))
-    st = tc::supported(p->nodes, p->precision);
+  if (st == TMC_OK && p->precision == TMC_PREC_FP16_TC)
+    st = p->ragged ? TMC_ERR_UNSUPPORTED : tc::supported(p->nodes, p->precision);
   if (st == TMC_OK) st = alloc_device(p);
   if (st != TMC_OK) {
     free_plan(p);
@@ -508,8 +554,8 @@ tmc_status tmc_backward(tmc_plan p, const tmc_inputs* in, const double* grad_out
       TRY(timed(p, TMC_KC_SAMPLE_GRAD, s, [&] { tc::launch_edge_rows(p->tcw, D, s); }));
   } else {
     for (int L = 1; L <= p->maxlevel; ++L) {
-      const int b = p->t_level_b[L], e = p->t_level_e[L];
-      TRY(timed(p, TMC_KC_EDGE_BWD, s, [&] { launch_edge_bwd_cols_f32(D, T + b, e - b, p->maxK, s); }));
+      const int b = p->t_level_b[L], e = p->t_level_e[L], cb = p->t_clevel_b[L], ce = p->t_clevel_e[L];
+      TRY(timed(p, TMC_KC_EDGE_BWD, s, [&] { launch_edge_bwd_cols_f32(D, T + cb, ce - cb, p->maxK, s); }));
       TRY(timed(p, TMC_KC_EDGE_BWD, s, [&] { launch_edge_bwd_rows_f32(D, T + b, e - b, p->maxK, s); }));
     }
   }
@@ -524,7 +570,9 @@ tmc_status tmc_backward(tmc_plan p, const tmc_inputs* in, const double* grad_out
     if (g->dC) TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_param_dC(D, p->maxd, p->maxobs, s); }));
   }
   if (p->shared && (g->dW || g->dbias || g->dC))
-    TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_shared_reduce(D, p->shared_n, p->shared_d, p->shared_obs, s); }));
+    TRY(timed(p, TMC_KC_PARAM, s, [&] {
+      launch_shared_reduce(D, p->shared_nW, p->shared_nb, p->shared_nC, p->shared_rootW, s);
+    }));
   return TMC_OK;
 }
 

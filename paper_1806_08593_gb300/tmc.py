@@ -41,7 +41,7 @@ class ProblemDesc(ctypes.Structure):
                 ("parent", ctypes.c_void_p), ("K", ctypes.c_void_p), ("d", ctypes.c_void_p),
                 ("obs_dim", ctypes.c_void_p), ("shared_params", ctypes.c_int32),
                 ("prior_var", ctypes.c_double), ("obs_var", ctypes.c_double),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("K_node", ctypes.c_void_p), ("d_node", ctypes.c_void_p)]
 
 
 class Inputs(ctypes.Structure):
@@ -119,13 +119,15 @@ class Plan:
     """Owns a tmc_plan (topology, schedule, device workspace) for one batch shape."""
 
     def __init__(self, n, parent, K, d, obs, shared: bool, prior_var: float, obs_var: float,
-                 precision: str = "fp32"):
+                 precision: str = "fp32", K_node=None, d_node=None):
         lib = load_library()
         self._keep = [np.ascontiguousarray(a, dtype=np.int32) for a in (n, parent, K, d, obs)]
         n_, par_, K_, d_, o_ = self._keep
+        per = [None if a is None else np.ascontiguousarray(a, dtype=np.int32) for a in (K_node, d_node)]
+        self._keep += per
         desc = ProblemDesc(len(n_), n_.ctypes.data, par_.ctypes.data, K_.ctypes.data, d_.ctypes.data,
                            o_.ctypes.data, int(bool(shared)), float(prior_var), float(obs_var),
-                           PRECISIONS[precision])
+                           PRECISIONS[precision], *[None if a is None else a.ctypes.data for a in per])
         h = ctypes.c_void_p()
         _check(lib.tmc_plan_create(ctypes.byref(desc), ctypes.byref(h)), "tmc_plan_create")
         self._h = h
@@ -137,7 +139,8 @@ class Plan:
 
     @classmethod
     def from_problem(cls, p, precision: str = "fp32") -> "Plan":
-        return cls(p.n, p.parent, p.K, p.d, p.obs, p.shared, p.prior_var, p.obs_var, precision)
+        return cls(p.n, p.parent, p.K, p.d, p.obs, p.shared, p.prior_var, p.obs_var, precision,
+                   K_node=p.Kn, d_node=p.dn)
 
     @staticmethod
     def to_device(p, device="cuda") -> dict:
@@ -235,7 +238,7 @@ def log_marginal_noalloc(p, t: dict, out=None, stream=None):
     lib = load_library()
     keep = [np.ascontiguousarray(a, dtype=np.int32) for a in (p.n, p.parent, p.K, p.d, p.obs)]
     desc = ProblemDesc(len(keep[0]), *[a.ctypes.data for a in keep], int(bool(p.shared)),
-                       float(p.prior_var), float(p.obs_var), PRECISIONS["fp32"])
+                       float(p.prior_var), float(p.obs_var), PRECISIONS["fp32"], None, None)
     if out is None:
         out = torch.empty(len(keep[0]), dtype=torch.float64, device=t["eps"].device)
     inp = Inputs(*[_ptr(t[k]) for k in INPUT_NAMES])

@@ -64,6 +64,23 @@ def test_mixed_roots_fp32():
     compare(p, gpu_run(p, "fp32"), oracle_run(p), TOL_LOGP_F32, TOL_GRAD)
 
 
+@pytest.mark.parametrize("which", ["layered", "trees", "shared_K"])
+def test_ragged_fp32(which):
+    """A different K_i and d_i per latent (Eq. (is)); W_i of shape d_i x d_parent."""
+    if which == "layered":  # the paper's five-layer widths, K = 20, synthetic observations
+        p = wl.layered_chain([4, 8, 16, 32, 64], 20, obs=96, B=6, seed=711)
+    elif which == "trees":
+        p = wl.ragged_trees(8, seed=712, n_choices=(1, 3, 6, 9), Ks=(1, 17, 64, 100, 130),
+                            ds=(1, 8, 24, 65), max_depth=4)
+    else:  # shared model, the same d_i everywhere, K_i differing between instances too
+        p = wl.make_problem([wl.chain_parents(4)] * 3, [[70, 20, 130, 64], [5, 90, 64, 64], [128] * 4],
+                            [[6, 33, 70, 12]] * 3, [24] * 3, shared=True, seed=713)
+    assert p.ragged
+    got = gpu_run(p, "fp32", grad_out=np.linspace(0.5, 1.5, p.B))
+    ref = oracle_run(p, grad_out=np.linspace(0.5, 1.5, p.B))
+    compare(p, got, ref, TOL_LOGP_F32, TOL_GRAD)
+
+
 def test_star_fig2_fp32():
     parent = np.array([-1] + [0] * 9, dtype=np.int32)
     p = wl.make_problem([parent] * 3, [70] * 3, [5] * 3, [7] * 3, shared=True, seed=99)
