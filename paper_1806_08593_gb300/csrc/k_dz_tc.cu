@@ -159,8 +159,8 @@ __global__ void __launch_bounds__(kDzThreads) k_dz_tc(
   const float gb = D.grad_out ? (float)D.grad_out[nd.b] : 1.f;
   const float w = valid ? D.q[nd.off_nk + k] * gb * D.inv_var : 0.f;
   const uint32_t lane_acc = acc + ((uint32_t)(32 * warp) << 16);
-  const long long row = nd.off_nkd + (long long)k * d;
-  const bool vec4 = ((nd.off_nkd | (long long)d) & 3) == 0;
+  const long long row = nd.off_e + (long long)k * d;  // eps / dz / deps: the caller's layout
+  const bool vec4 = ((nd.off_e | (long long)d) & 3) == 0;
 #pragma unroll 1
   for (int g = 0; g < DP / 32 && g * 32 < d; ++g) {  // warp-uniform
     uint32_t v[32];
@@ -210,8 +210,8 @@ tmc_status prepare_dz(TcWork& w, const std::vector<NodeInfo>& nodes) {
   w.dz_tiles.clear();
   for (int c = 0; c < 2; ++c) {
     w.dz_b[c] = (int)w.dz_tiles.size();
-    for (int g = 0; g < (int)nodes.size(); ++g)
-      if (((nodes[g].d > 64) ? 1 : 0) == c)
+    for (int g = 0; g < (int)nodes.size(); ++g)  // the instance's class: its terms' K-dims vary
+      if ((w.inst_dp[nodes[g].b] > 64 ? 1 : 0) == c)
         for (int r = 0; r < nodes[g].K; r += kRows) w.dz_tiles.push_back(Tile{g, r});
     w.dz_e[c] = (int)w.dz_tiles.size();
   }

@@ -221,14 +221,14 @@ constexpr int kSampleConsumers = 7;             // consumer warps
 
 struct __align__(16) SampleStage {  // 16-byte aligned: the vectors are read as float4
   float std_[kTcMaxD], off[kTcMaxD], c[kTcMaxD];
-  long long off_nk, off_nkd;
+  long long off_nk, off_nkd, off_e;
   int d, row0, rows, root, bulk;
 };
 constexpr size_t kSampleSmem = kSampleNS * (kSampleStage + sizeof(SampleStage)) + 64;
 static_assert(sizeof(SampleStage) % 16 == 0 && kSampleStage % 64 == 0, "sampler stage alignment");
 
 __device__ __forceinline__ bool sample_bulk_ok(const Dev& D, const NodeInfo& nd) {
-  return (nd.d & 3) == 0 && (nd.off_nkd & 3) == 0 && ((uintptr_t)D.eps & 15) == 0;
+  return (nd.d & 3) == 0 && (nd.off_e & 3) == 0 && ((uintptr_t)D.eps & 15) == 0;
 }
 
 // Rows of one stage; element (r, col) of the tile is src[r * d + col].
@@ -352,6 +352,7 @@ __global__ void __launch_bounds__(256) k_sample_tc(Dev D, TcDev T, const Tile* _
       if (lane == 0) {
         st[s].off_nk = nd.off_nk;
         st[s].off_nkd = nd.off_nkd;
+        st[s].off_e = nd.off_e;
         st[s].d = nd.d;
         st[s].row0 = t.row0;
         st[s].rows = rows;
@@ -363,7 +364,7 @@ __global__ void __launch_bounds__(256) k_sample_tc(Dev D, TcDev T, const Tile* _
         if (bulk) {
           const uint32_t bytes = (uint32_t)rows * nd.d * 4;
           mbar_arrive_expect_tx(&full[s], bytes);
-          bulk_load(buf + (size_t)s * (kSampleStage / 4), D.eps + nd.off_nkd + (long long)t.row0 * nd.d, bytes,
+          bulk_load(buf + (size_t)s * (kSampleStage / 4), D.eps + nd.off_e + (long long)t.row0 * nd.d, bytes,
                     &full[s]);
         } else {
           mbar_arrive(&full[s]);  // release of the stage record; the rows are read from global
@@ -383,7 +384,7 @@ __global__ void __launch_bounds__(256) k_sample_tc(Dev D, TcDev T, const Tile* _
       const int s = n % kSampleNS;
       if (!mbar_wait(&full[s], (n / kSampleNS) & 1)) { ok = false; break; }
       const SampleStage& stg = st[s];
-      const float* src = stg.bulk ? buf + (size_t)s * (kSampleStage / 4) : D.eps + stg.off_nkd + (long long)stg.row0 * stg.d;
+      const float* src = stg.bulk ? buf + (size_t)s * (kSampleStage / 4) : D.eps + stg.off_e + (long long)stg.row0 * stg.d;
       const int d = stg.d;
       if (d > 64) bad |= sample_stage<3, 4>(D, T, stg, src);
       else if (d > 32) bad |= sample_stage<3, 2>(D, T, stg, src);
@@ -406,9 +407,9 @@ __global__ void k_pack_w(Dev D, TcDev T, const int* __restrict__ nonroot) {
   const int g = nonroot[blockIdx.x];
   const NodeInfo nd = D.nodes[g];
   if (D.shared && nd.b != 0) return;  // shared parameters: pack once (instance 0's nodes)
-  const int d = nd.d, dp = d > 64 ? 128 : 64;
+  const int d = nd.d, dq = nd.dp;  // W_i is d x dq (dq: the parent's dimension)
   const int r0 = blockIdx.y * 32, c0 = blockIdx.z * 32;
-  if (r0 >= d || c0 >= d) return;  // tiles beyond d stay zero from plan creation
+  if (r0 >= d || c0 >= dq) return;  // tiles beyond d x dq stay zero from plan creation
   const int slot = slot_of(D, nd, g);
   const long long o = (long long)slot * kLdp * kLdp;
   const float* Wi = D.W + nd.off_W;
@@ -417,7 +418,7 @@ __global__ void k_pack_w(Dev D, TcDev T, const int* __restrict__ nonroot) {
 #pragma unroll
   for (int x = 0; x < 4; ++x) {  // every load before the first store
     const int r = r0 + ty + 8 * x, c = c0 + tx;
-    v[x] = (r < d && c < d) ? __ldg(Wi + (long long)r * d + c) : 0.f;
+    v[x] = (r < d && c < dq) ? __ldg(Wi + (long long)r * dq + c) : 0.f;
   }
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
@@ -446,28 +447,28 @@ __global__ void __launch_bounds__(128) k_pack_c(Dev D, TcDev T, const int* __res
   const int g = nonroot[blockIdx.x];
   const NodeInfo nd = D.nodes[g];
   const NodeInfo pn = D.nodes[nd.parent];
-  const int d = nd.d, dp = d > 64 ? 128 : 64;
-  for (int j = threadIdx.x; j < kTcMaxD; j += blockDim.x) mp[j] = j < d ? D.q_mean[pn.off_q + j] : 0.f;
+  const int d = nd.d, dq = nd.dp, dp = kTcMaxD;  // W_i is d x dq; c_i padded to 128 with zeros
+  for (int j = threadIdx.x; j < kTcMaxD; j += blockDim.x) mp[j] = j < dq ? D.q_mean[pn.off_q + j] : 0.f;
   __syncthreads();
-  const bool vec = (d & 3) == 0 && (nd.off_W & 3) == 0;
+  const bool vec = (dq & 3) == 0 && (nd.off_W & 3) == 0;
   for (int r = threadIdx.x; r < dp; r += blockDim.x) {
     float s = 0.f;
     if (r < d) {
-      const float* wr = D.W + nd.off_W + (long long)r * d;
+      const float* wr = D.W + nd.off_W + (long long)r * dq;
       float s0 = 0.f, s1 = 0.f;
       if (vec) {
-        for (int c = 0; c < d; c += 8) {
+        for (int c = 0; c < dq; c += 8) {
           const float4 a = *reinterpret_cast<const float4*>(wr + c);
           s0 = fmaf(a.x, mp[c], s0); s0 = fmaf(a.y, mp[c + 1], s0);
           s0 = fmaf(a.z, mp[c + 2], s0); s0 = fmaf(a.w, mp[c + 3], s0);
-          if (c + 4 < d) {
+          if (c + 4 < dq) {
             const float4 b = *reinterpret_cast<const float4*>(wr + c + 4);
             s1 = fmaf(b.x, mp[c + 4], s1); s1 = fmaf(b.y, mp[c + 5], s1);
             s1 = fmaf(b.z, mp[c + 6], s1); s1 = fmaf(b.w, mp[c + 7], s1);
           }
         }
       } else {
-        for (int c = 0; c < d; ++c) s0 = fmaf(wr[c], mp[c], s0);
+        for (int c = 0; c < dq; ++c) s0 = fmaf(wr[c], mp[c], s0);
       }
       s = (s0 + s1) + D.bias[nd.off_bias + r] - D.q_mean[nd.off_q + r];
     }
@@ -859,7 +860,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       if (lane == 0)
         for (int c = nd.child_begin; c < nd.child_end; ++c) {
           const int cg = D.children[c];
-          dep_ok = wait_count(done + cg, tiles_of(D.nodes[cg].K), D.wait_limit) && dep_ok;
+          dep_ok = wait_count(done + cg, tiles_of(D.nodes[cg].Kp), D.wait_limit) && dep_ok;
         }
       dep_ok = __shfl_sync(0xffffffffu, dep_ok, 0);
       __syncwarp();  // lane 0's acquire of the counters orders the other lanes' reads below
@@ -987,7 +988,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     for (int item = blockIdx.x; item < ntiles; item += gridDim.x, ++it) {
       const Tile t = tiles[item];
       const NodeInfo nd = D.nodes[t.node];
-      const int K = nd.K, nch = tiles_of(K);
+      const int K = nd.Kp, nch = tiles_of(nd.K);  // rows: parent samples; chunks: child samples
       const int k = t.row0 + r;
       const int ib = it % ncb;
       const float* cb = cbuf + (size_t)ib * cbk;
@@ -1167,10 +1168,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   const Tile t = s_tile[sl];
   const NodeInfo nd = s_nd[sl];
   const NodeInfo pn = s_pn[sl];
-  const int K = nd.K, nch = (K + kRows - 1) / kRows, d = nd.d;
   // the node whose samples fill the chunks, and the node whose 128 rows the item owns
   const NodeInfo& chn = ROWS ? nd : pn;
   const long long own_off = ROWS ? pn.off_nk : nd.off_nk;
+  const int Kch = chn.K, Krow = ROWS ? nd.Kp : nd.K;  // chunk samples, row samples
+  const int nch = (Kch + kRows - 1) / kRows;
   // Epilogue operands in the ring.  With 3 or more chunks this CTA's own Z~ tile is loaded
   // into the stage of chunk nch - 3 as soon as its V MMAs are done (no later chunk uses that
   // stage), under the last two chunks, and the V tile goes to the last chunk's stage; with
@@ -1375,14 +1377,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     const int r = 32 * qd + lane;
     const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
     const int kq = t.row0 + r;  // sample owned by this thread's row (ROWS: a parent sample)
-    const bool valid = kq < K;
+    const bool valid = kq < Krow;
     if constexpr (ROWS) {
       // column (child sample) terms: (beta_i - |z~_i|^2 / (2 var)) log2 e, as in the forward
       float bv[kJt], zv[kJt];
 #pragma unroll
       for (int i = 0; i < kJt; ++i) {
         const int j = mt + i * kMath;
-        const bool in = j < K;
+        const bool in = j < Kch;
         bv[i] = in ? D.beta[nd.off_nk + j] : 0.f;
         zv[i] = in ? D.zn[nd.off_nk + j] : 0.f;
       }
@@ -1390,7 +1392,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       for (int i = 0; i < kJt; ++i) {
         const int j = mt + i * kMath;
         if (j >= nch * kRows) break;
-        ak[j] = (j < K) ? (bv[i] - 0.5f * zv[i] * iv) * kLog2e : -INFINITY;
+        ak[j] = (j < Kch) ? (bv[i] - 0.5f * zv[i] * iv) * kLog2e : -INFINITY;
       }
     } else {
       // column (parent sample) terms: (log q_p - lam_i - |mu~|^2 / (2 var)) log2 e; all loads first
@@ -1398,7 +1400,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 #pragma unroll
       for (int i = 0; i < kJt; ++i) {
         const int j = mt + i * kMath;
-        const bool in = j < K;
+        const bool in = j < Kch;
         qv[i] = in ? __ldcg(D.q + pn.off_nk + j) : 0.f;  // may come from this launch
         lv[i] = in ? D.lam[nd.off_nk + j] : 0.f;
         mv[i] = in ? D.mun[nd.off_nk + j] : 0.f;
@@ -1407,7 +1409,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       for (int i = 0; i < kJt; ++i) {
         const int j = mt + i * kMath;
         if (j >= nch * kRows) break;
-        ak[j] = (j < K) ? (logf(qv[i]) - lv[i] - 0.5f * mv[i] * iv) * kLog2e : -INFINITY;
+        ak[j] = (j < Kch) ? (logf(qv[i]) - lv[i] - 0.5f * mv[i] * iv) * kLog2e : -INFINITY;
       }
     }
     // row term: adjoint (beta_i - |z~|^2 / (2 var) + z~ . c_i / var) log2 e; ROWS the row
@@ -1999,12 +2001,12 @@ __global__ void __launch_bounds__(kMoThreads, 1)
   }
 }
 
-// Zeroes the d x d block of every node in a [node][128][128] array (the part the readers use;
-// the adjoint launch adds its tile partials of G into it).
+// Zeroes the dp x d block of every node in a [node][128][128] array (the part the readers use:
+// G_i = sum pi z~_p z~_i^T is d_parent x d_i; the adjoint launch adds its tile partials into it).
 __global__ void __launch_bounds__(256) k_zero_dd(Dev D, float* __restrict__ base) {
-  const int d = D.nodes[blockIdx.x].d;
+  const int d = D.nodes[blockIdx.x].d, dq = D.nodes[blockIdx.x].dp;
   float* blk = base + (long long)blockIdx.x * kLdp * kLdp;
-  for (int i = threadIdx.x; i < d * d; i += blockDim.x) blk[(i / d) * kLdp + i % d] = 0.f;
+  for (int i = threadIdx.x; i < dq * d; i += blockDim.x) blk[(i / d) * kLdp + i % d] = 0.f;
 }
 
 // =======================================================================================
@@ -2023,33 +2025,35 @@ __global__ void __launch_bounds__(128) k_asm_edge_vec(Dev D, TcDev T, const int*
   __shared__ float zp[kTcMaxD], dbs[kTcMaxD];
   const int g = nonroot[blockIdx.x];
   const NodeInfo nd = D.nodes[g];
-  const int d = nd.d;
+  const int d = nd.d, dq = nd.dp;  // W_c is d x dq
   const float iv = D.inv_var;
   const float go = D.grad_out ? (float)D.grad_out[nd.b] : 1.f;
   const float* W = D.W + nd.off_W;
   const float* zbc = T.zbar + (long long)g * kLdp;
   const float* cc = T.cvec + (long long)g * kLdp;
   const int j = threadIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (j < d) zp[j] = __ldg(T.zbar + (long long)nd.parent * kLdp + j);
+  if (j < dq) zp[j] = __ldg(T.zbar + (long long)nd.parent * kLdp + j);
   __syncthreads();
   // (W_c zbar_p)[r]: one warp per row, lanes along the row (coalesced)
   for (int r = w; r < d; r += 4) {
     float s = 0.f;
-    for (int c = lane; c < d; c += 32) s = fmaf(__ldg(W + (long long)r * d + c), zp[c], s);
+    for (int c = lane; c < dq; c += 32) s = fmaf(__ldg(W + (long long)r * dq + c), zp[c], s);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) dbs[r] = (__ldg(zbc + r) - s - __ldg(cc + r)) * iv;
   }
   __syncthreads();
-  if (j >= d) return;
-  const float db = dbs[j];
-  T.sgC[(long long)g * kLdp + j] = -db;
-  if (D.shared) { if (D.pbias) D.pbias[nd.off_q + j] = go * db; }
-  else if (D.dbias) D.dbias[nd.off_bias + j] = go * db;
-  // (W^T db')[j] = sum_a W[a][j] db'[a] (coalesced over j).  The child-side sum of g z~ is
-  // diag(W_c G_c) / var (k_asm_edge_mat, which holds both tiles, into the zeroed tgC) plus
-  // (c_c zbar_c - diag M2_c) / var (added by k_asm_node)
+  if (j < d) {
+    const float db = dbs[j];
+    T.sgC[(long long)g * kLdp + j] = -db;
+    if (D.shared) { if (D.pbias) D.pbias[nd.off_q + j] = go * db; }
+    else if (D.dbias) D.dbias[nd.off_bias + j] = go * db;
+  }
+  // (W^T db')[j] = sum_a W[a][j] db'[a] (coalesced over j, j < dq).  The child-side sum of
+  // g z~ is diag(W_c G_c) / var (k_asm_edge_mat, which holds both tiles, into the zeroed tgC)
+  // plus (c_c zbar_c - diag M2_c) / var (added by k_asm_node)
+  if (j >= dq) return;
   float sg = 0.f;
-  for (int a = 0; a < d; ++a) sg = fmaf(__ldg(W + (long long)a * d + j), dbs[a], sg);
+  for (int a = 0; a < d; ++a) sg = fmaf(__ldg(W + (long long)a * dq + j), dbs[a], sg);
   T.sgP[(long long)g * kLdp + j] = sg;
 }
 
@@ -2063,9 +2067,9 @@ __global__ void __launch_bounds__(kThreads) k_asm_edge_mat(Dev D, TcDev T, const
   const int g = nonroot[blockIdx.x];
   const NodeInfo nd = D.nodes[g];
   const NodeInfo pn = D.nodes[nd.parent];
-  const int d = nd.d;
+  const int d = nd.d, dq = nd.dp;  // D_c and W_c are d x dq, G_c is dq x d
   const int a0 = (blockIdx.y >> 1) * kTile, b0 = (blockIdx.y & 1) * kTile;
-  if (a0 >= d || b0 >= d) return;
+  if (a0 >= d || b0 >= dq) return;
   const float iv = D.inv_var;
   const float go = D.grad_out ? (float)D.grad_out[nd.b] : 1.f;
   const float* W = D.W + nd.off_W;
@@ -2082,8 +2086,8 @@ __global__ void __launch_bounds__(kThreads) k_asm_edge_mat(Dev D, TcDev T, const
 #pragma unroll
     for (int x = 0; x < NV; ++x) {
       const int e = threadIdx.x + x * kThreads, r = e >> 6, c = e & 63;
-      wv[x] = (a0 + r < d && b0 + c < d) ? __ldg(W + (long long)(a0 + r) * d + b0 + c) : 0.f;
-      gv[x] = (b0 + r < d && a0 + c < d) ? __ldg(Gc + (long long)(b0 + r) * kLdp + a0 + c) : 0.f;
+      wv[x] = (a0 + r < d && b0 + c < dq) ? __ldg(W + (long long)(a0 + r) * dq + b0 + c) : 0.f;
+      gv[x] = (b0 + r < dq && a0 + c < d) ? __ldg(Gc + (long long)(b0 + r) * kLdp + a0 + c) : 0.f;
     }
 #pragma unroll
     for (int x = 0; x < NV; ++x) {
@@ -2095,8 +2099,8 @@ __global__ void __launch_bounds__(kThreads) k_asm_edge_mat(Dev D, TcDev T, const
   float acc[4][4];
   zero_acc(acc);
   // acc[a][b] = sum_j W[a][j] M2_p[j][b]   (tile_gemm synchronises before its first read)
-  tile_gemm<true, false>(acc, W + (long long)a0 * d, d, min(kTile, d - a0), M2p + b0, kLdp,
-                         min(kTile, d - b0), d, sm);
+  tile_gemm<true, false>(acc, W + (long long)a0 * dq, dq, min(kTile, d - a0), M2p + b0, kLdp,
+                         min(kTile, dq - b0), dq, sm);
   float tcol[4] = {0.f, 0.f, 0.f, 0.f};
   float wrow[4] = {0.f, 0.f, 0.f, 0.f};
   // every vector operand of the epilogue in registers before the first store
@@ -2106,8 +2110,8 @@ __global__ void __launch_bounds__(kThreads) k_asm_edge_mat(Dev D, TcDev T, const
     const int a = a0 + ty * 4 + i, bb = b0 + tx * 4 + i;
     dbv[i] = a < d ? -__ldg(T.sgC + (long long)g * kLdp + a) : 0.f;  // db'[a], from k_asm_edge_vec
     cav[i] = a < d ? __ldg(cc + a) : 0.f;
-    zpv[i] = bb < d ? __ldg(zbp + bb) : 0.f;
-    mpv[i] = bb < d ? __ldg(D.q_mean + pn.off_q + bb) : 0.f;
+    zpv[i] = bb < dq ? __ldg(zbp + bb) : 0.f;
+    mpv[i] = bb < dq ? __ldg(D.q_mean + pn.off_q + bb) : 0.f;
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -2116,14 +2120,14 @@ __global__ void __launch_bounds__(kThreads) k_asm_edge_mat(Dev D, TcDev T, const
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
       const int bl = tx * 4 + jj, bb = b0 + bl;
-      if (a >= d || bb >= d) continue;
+      if (a >= d || bb >= dq) continue;
       const float wab = sW[al][bl], gt = sG[bl][al];
       const float Dab = (gt - acc[i][jj] - ca * zpv[jj]) * iv;
       tcol[jj] = fmaf(wab, Dab, tcol[jj]);
       wrow[i] = fmaf(wab, gt, wrow[i]);
       const float v = go * (Dab + db * mpv[jj]);
-      if (D.shared) { if (D.pW) D.pW[nd.off_pW + (long long)a * d + bb] = v; }
-      else if (D.dW) D.dW[nd.off_W + (long long)a * d + bb] = v;
+      if (D.shared) { if (D.pW) D.pW[nd.off_pW + (long long)a * dq + bb] = v; }
+      else if (D.dW) D.dW[nd.off_W + (long long)a * dq + bb] = v;
     }
   }
 #pragma unroll
@@ -2137,7 +2141,7 @@ __global__ void __launch_bounds__(kThreads) k_asm_edge_mat(Dev D, TcDev T, const
 #pragma unroll
   for (int jj = 0; jj < 4; ++jj) colpart[ty][tx * 4 + jj] = tcol[jj];
   __syncthreads();
-  if (threadIdx.x < kTile && b0 + threadIdx.x < d) {
+  if (threadIdx.x < kTile && b0 + threadIdx.x < dq) {
     float s = 0.f;
     for (int i = 0; i < 16; ++i) s += colpart[i][threadIdx.x];
     atomicAdd(T.tgP + (long long)g * kLdp + b0 + threadIdx.x, s);
@@ -2533,28 +2537,33 @@ void build_items(TcWork& w, const std::vector<NodeInfo>& nodes, int schedule) {
   w.schedule = schedule;
   std::vector<double> work(w.num_inst, 0.0);
   for (const NodeInfo& nd : nodes)
-    if (nd.parent >= 0) work[nd.b] += (double)nd.K * nd.K * nd.d;
-  for (int dir = 0; dir < 2; ++dir)
+    if (nd.parent >= 0) work[nd.b] += (double)nd.Kp * nd.K * nd.d;
+  // rows of an edge's tiles: the parent's samples (forward, row pass) or the child's (adjoint)
+  auto rows_of = [&](int dir, int g) { return dir == 1 ? nodes[g].K : nodes[g].Kp; };
+  for (int dir = 0; dir < 3; ++dir)
     for (int c = 0; c < 2; ++c) {
       w.it_b[dir][c] = (int)w.tiles.size();
       for (int step = 0; step < w.maxlevel; ++step) {
         const int L = dir == 0 ? w.maxlevel - step : 1 + step;
         std::vector<int> lv;
         for (int g = 0; g < (int)nodes.size(); ++g)
-          if (nodes[g].level == L && ((nodes[g].d > 64) ? 1 : 0) == c) lv.push_back(g);
+          if (nodes[g].level == L && (w.inst_dp[nodes[g].b] > 64 ? 1 : 0) == c) lv.push_back(g);
         if (schedule == 2)
           std::stable_sort(lv.begin(), lv.end(), [&](int x, int y) { return work[nodes[x].b] > work[nodes[y].b]; });
         if (schedule == 1) {
           for (int r = 0;; r += kRows) {
             bool any = false;
             for (int g : lv)
-              if (r < nodes[g].K && !(dir == 0 && g == w.stall_node)) { w.tiles.push_back(Tile{g, r}); any = true; }
+              if (r < rows_of(dir, g) && !(dir == 0 && g == w.stall_node)) {
+                w.tiles.push_back(Tile{g, r});
+                any = true;
+              }
             if (!any) break;
           }
         } else {
           for (int g : lv)
             if (!(dir == 0 && g == w.stall_node))  // (the stall fault drops one node's tiles)
-              for (int r = 0; r < nodes[g].K; r += kRows) w.tiles.push_back(Tile{g, r});
+              for (int r = 0; r < rows_of(dir, g); r += kRows) w.tiles.push_back(Tile{g, r});
         }
       }
       w.it_e[dir][c] = (int)w.tiles.size();
@@ -2724,6 +2733,9 @@ tmc_status prepare(TcWork& w, const std::vector<NodeInfo>& nodes, const std::vec
   int maxlevel = 0;
   for (const NodeInfo& nd : nodes) maxlevel = std::max(maxlevel, nd.level);
   w.maxlevel = maxlevel;
+  w.inst_dp.assign(w.num_inst, 64);
+  for (const NodeInfo& nd : nodes)
+    if (nd.d > 64) w.inst_dp[nd.b] = 128;
   build_items(w, nodes, 0);
   cudaDeviceGetAttribute(&w.num_sms, cudaDevAttrMultiProcessorCount, 0);
   {
@@ -2868,10 +2880,9 @@ void launch_edge_bwd(TcWork& w, const Dev& D, cudaStream_t s) {
 }
 
 void launch_edge_rows(TcWork& w, const Dev& D, cudaStream_t s) {
-  // the adjoint's tile list serves: tile r of edge p -> i names parent rows r .. r + 127
-  // (the same K on both sides); no item depends on another
+  // tile r of edge p -> i names parent rows r .. r + 127; no item depends on another
   for (int c = 0; c < 2; ++c) {
-    const int b = w.it_b[1][c], n = w.it_e[1][c] - b;
+    const int b = w.it_b[2][c], n = w.it_e[2][c] - b;
     if (!n) continue;
     const int grid = n < w.num_sms ? n : w.num_sms;
     if (c == 0)

@@ -468,7 +468,7 @@ tmc_status tmc_plan_create(const tmc_problem_desc* desc, tmc_plan* out) {
   p->fault = fault_from_env();
   tmc_status st = build_plan(desc, p);
   if (st == TMC_OK && p->precision == TMC_PREC_FP16_TC)
-    st = p->ragged ? TMC_ERR_UNSUPPORTED : tc::supported(p->nodes, p->precision);
+    st = tc::supported(p->nodes, p->precision);
   if (st == TMC_OK) st = alloc_device(p);
   if (st != TMC_OK) {
     free_plan(p);

@@ -80,9 +80,13 @@ struct TcWork {
   CUtensorMap mZH, mZL, mWH, mWL, mWTH, mWTL;
   CUtensorMap mZH64, mZL64;       // the sample tiles in 64-row boxes (node moments)
   // edge tiles in dependency order: [direction][class] ranges into d_tiles; direction 0 =
-  // forward (deepest level first), 1 = adjoint (level 1 first); class 0: d <= 64, 1: d <= 128
+  // forward (deepest level first, rows = the parent's samples), 1 = adjoint (level 1 first,
+  // rows = the child's samples), 2 = the row-direction pass of the sample gradients (rows = the
+  // parent's samples, no dependencies); class 0: every latent of the instance has d <= 64,
+  // class 1: d <= 128 (one class per instance, so no dependency crosses launches)
   std::vector<Tile> tiles;
-  int it_b[2][2] = {{0, 0}, {0, 0}}, it_e[2][2] = {{0, 0}, {0, 0}};
+  int it_b[3][2] = {{0, 0}, {0, 0}, {0, 0}}, it_e[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  std::vector<int> inst_dp;       // per instance: widest padded latent dimension (64 or 128)
   int num_sms = 148;
   Tile* d_tiles = nullptr;
   std::vector<int> nonroot;

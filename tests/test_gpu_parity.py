@@ -64,7 +64,7 @@ def test_mixed_roots_fp32():
     compare(p, gpu_run(p, "fp32"), oracle_run(p), TOL_LOGP_F32, TOL_GRAD)
 
 
-@pytest.mark.parametrize("which", ["layered", "trees", "shared_K"])
+@pytest.mark.parametrize("which", ["layered", "trees", "shared_K", "wide"])
 def test_ragged_fp32(which):
     """A different K_i and d_i per latent (Eq. (is)); W_i of shape d_i x d_parent."""
     if which == "layered":  # the paper's five-layer widths, K = 20, synthetic observations
@@ -72,9 +72,14 @@ def test_ragged_fp32(which):
     elif which == "trees":
         p = wl.ragged_trees(8, seed=712, n_choices=(1, 3, 6, 9), Ks=(1, 17, 64, 100, 130),
                             ds=(1, 8, 24, 65), max_depth=4)
-    else:  # shared model, the same d_i everywhere, K_i differing between instances too
+    elif which == "shared_K":  # shared model, the same d_i everywhere, K_i differing between instances too
         p = wl.make_problem([wl.chain_parents(4)] * 3, [[70, 20, 130, 64], [5, 90, 64, 64], [128] * 4],
                             [[6, 33, 70, 12]] * 3, [24] * 3, shared=True, seed=713)
+    else:  # wide latents of both sizes, several 64-row tiles per edge
+        p = wl.make_problem([np.array([-1, 0, 1, 1, 0], dtype=np.int32)] * 2,
+                            [[300, 129, 260, 90, 200], [64, 256, 128, 300, 40]],
+                            [[128, 40, 100, 100, 100], [30, 128, 100, 100, 100]], [64, 70],
+                            shared=False, seed=714)
     assert p.ragged
     got = gpu_run(p, "fp32", grad_out=np.linspace(0.5, 1.5, p.B))
     ref = oracle_run(p, grad_out=np.linspace(0.5, 1.5, p.B))

@@ -70,6 +70,26 @@ def test_large_star_tc():
     _check(wl.star(2000, 128, 1, B=2, seed=1234))
 
 
+@pytest.mark.parametrize("which", ["layered", "trees", "shared_K", "wide"])
+def test_ragged_tc(which):
+    """A different K_i and d_i per latent (Eq. (is)); W_i of shape d_i x d_parent."""
+    if which == "layered":  # the paper's five-layer widths, K = 20, synthetic observations
+        p = wl.layered_chain([4, 8, 16, 32, 64], 20, obs=96, B=6, seed=711)
+    elif which == "trees":
+        p = wl.ragged_trees(8, seed=712, n_choices=(1, 3, 6, 9), Ks=(1, 17, 64, 100, 130),
+                            ds=(1, 8, 24, 65), max_depth=4)
+    elif which == "shared_K":  # shared model, K_i differing between instances too
+        p = wl.make_problem([wl.chain_parents(4)] * 3, [[70, 20, 130, 64], [5, 90, 64, 64], [128] * 4],
+                            [[6, 33, 70, 12]] * 3, [24] * 3, shared=True, seed=713)
+    else:  # both dimension classes in one instance, several chunks per edge
+        p = wl.make_problem([np.array([-1, 0, 1, 1, 0], dtype=np.int32)] * 2,
+                            [[300, 129, 260, 90, 200], [64, 256, 128, 300, 40]],
+                            [[128, 40, 100, 100, 100], [30, 128, 100, 100, 100]], [64, 70],
+                            shared=False, seed=714)
+    assert p.ragged
+    _check(p, grad_out=np.linspace(0.5, 1.5, p.B))
+
+
 def test_mixed_roots_tc():
     _check(mixed_roots_problem())
 
