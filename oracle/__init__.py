@@ -51,9 +51,9 @@ def _load():
             lib = ctypes.CDLL(build())
             P = ctypes.c_void_p
             common = [ctypes.c_int, P, P, P, P, P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                      P, P, P, P, P, P, P]
+                      P, P, P, P, P, P, P, P]
             lib.tmc_oracle_log_marginal.argtypes = common + [P]
-            lib.tmc_oracle_grad.argtypes = common + [P, P, P, P, P, P, P, P]
+            lib.tmc_oracle_grad.argtypes = common + [P, P, P, P, P, P, P, P, P]
             lib.tmc_oracle_brute_force.argtypes = common + [ctypes.c_longlong, P]
             for f in (lib.tmc_oracle_log_marginal, lib.tmc_oracle_grad, lib.tmc_oracle_brute_force):
                 f.restype = ctypes.c_int
@@ -73,10 +73,12 @@ def _common(p, overrides=None):
     arrs = dict(n=i32(p.n), parent=i32(p.parent), K=i32(p.K_nodes()), d=i32(p.d_nodes()), obs=i32(p.obs),
                 eps=f64("eps"), q_mean=f64("q_mean"), q_logstd=f64("q_logstd"), W=f64("W"),
                 bias=f64("bias"), C=f64("C"), x=f64("x"))
+    qa = o.get("q_A", p.q_A)  # coupled (non-factorised) proposal, or None
+    arrs["q_A"] = None if qa is None else np.ascontiguousarray(qa, dtype=np.float64)
     args = [p.B, _ptr(arrs["n"]), _ptr(arrs["parent"]), _ptr(arrs["K"]), _ptr(arrs["d"]),
             _ptr(arrs["obs"]), int(p.shared), float(p.prior_var), float(p.obs_var),
-            _ptr(arrs["eps"]), _ptr(arrs["q_mean"]), _ptr(arrs["q_logstd"]), _ptr(arrs["W"]),
-            _ptr(arrs["bias"]), _ptr(arrs["C"]), _ptr(arrs["x"])]
+            _ptr(arrs["eps"]), _ptr(arrs["q_mean"]), _ptr(arrs["q_logstd"]), _ptr(arrs["q_A"]),
+            _ptr(arrs["W"]), _ptr(arrs["bias"]), _ptr(arrs["C"]), _ptr(arrs["x"])]
     return args, arrs
 
 
@@ -101,10 +103,13 @@ def grad(p, grad_out=None, want_dz=True, **overrides) -> dict:
     g = None if grad_out is None else np.ascontiguousarray(grad_out, dtype=np.float64)
     out = dict(log_phat=np.zeros(p.B), dz=np.zeros(p.eps.size) if want_dz else None,
                dq_mean=np.zeros(p.q_mean.size), dq_logstd=np.zeros(p.q_logstd.size),
+               dq_A=None if keep["q_A"] is None else np.zeros(keep["q_A"].size),
                dW=np.zeros(p.W.size), dbias=np.zeros(p.bias.size), dC=np.zeros(p.C.size))
     _check(lib.tmc_oracle_grad(*args, _ptr(g), _ptr(out["log_phat"]), _ptr(out["dz"]),
-                               _ptr(out["dq_mean"]), _ptr(out["dq_logstd"]), _ptr(out["dW"]),
-                               _ptr(out["dbias"]), _ptr(out["dC"])), "grad")
+                               _ptr(out["dq_mean"]), _ptr(out["dq_logstd"]), _ptr(out["dq_A"]),
+                               _ptr(out["dW"]), _ptr(out["dbias"]), _ptr(out["dC"])), "grad")
+    if out["dq_A"] is None:
+        del out["dq_A"]
     return out
 
 
@@ -133,4 +138,6 @@ def subset(p, idx):
         kw.update(W=p.W.copy(), bias=p.bias.copy(), C=p.C.copy())
     else:
         kw.update(W=cat("W", "W"), bias=cat("bias", "bias"), C=cat("C", "C"))
+    if p.q_A is not None:  # per-instance couplings, laid out like per-instance W blocks
+        kw.update(q_A=np.concatenate([p.q_A[s["A"][0]:s["A"][1]] for s in sl]))
     return Problem(shared=p.shared, prior_var=p.prior_var, obs_var=p.obs_var, name=p.name, **kw)

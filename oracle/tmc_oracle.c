@@ -26,7 +26,12 @@
  *
  * Model: z_0 ~ N(bias_0, prior_var I); z_i | z_p ~ N(W_i z_p + bias_i, prior_var I) for i >= 1
  * with p = parent[i] < i (W_i is d_i x d_p); every leaf l carries x_l ~ N(C z_l, obs_var I).
- * Proposal: Q_i(z) = N(z; m_i, diag(exp(2 logs_i))), samples z_i^k = m_i + exp(logs_i) eps_i^k.
+ * Proposal: Q_i(z) = N(z; m_i, diag(exp(2 logs_i))), samples z_i^k = m_i + exp(logs_i) eps_i^k,
+ * or, with coupling matrices A_i (the non-factorised proposals of Section 2.3 "Non-factorised
+ * proposals" and the appendix), Q_i(z_i^k | all samples of the parent) =
+ * N(z_i^k; m_i + A_i (z_p^k - m_p), diag(exp(2 logs_i))): sample k of latent i is drawn given
+ * the parent's sample with the same index k, so the proposal factor is still indexed by k_i
+ * alone and the elimination is unchanged; only the samples and -log Q_i move.
  *
  * Factors (Appendix):  f_i^{(k_i, k_p)} = P(z_i^{k_i} | z_p^{k_p}) / Q_i(z_i^{k_i})   (i >= 1)
  *                      f_0^{k_0}        = P(z_0^{k_0}) / Q_0(z_0^{k_0})
@@ -59,13 +64,14 @@ typedef struct {
   const int *parent, *K, *d;
   long long *oz, *oq, *ow, *ok, *oe, *oed;
   const double *eps, *m, *logs, *W, *bias, *C, *x;
+  const double* A; /* proposal coupling matrices (layout of W), or NULL: factorised proposal */
   double prior_var, obs_var;
   int* leaf_slot; /* leaf_slot[i] = index of leaf i among the instance's leaves, or -1 */
   long long nz, nq, nw, nk, ne, ned;
 } inst_t;
 
 typedef struct {
-  long long eps, q, x, W, C, parent;
+  long long eps, q, x, W, C, parent, A;
 } offs_t;
 
 static int count_leaves(int n, const int* parent, int* leaf_slot) {
@@ -80,7 +86,7 @@ static int count_leaves(int n, const int* parent, int* leaf_slot) {
 }
 
 static int validate(int B, const int* n, const int* parent, const int* K, const int* d,
-                    const int* obs) {
+                    const int* obs, int coupled) {
   long long off = 0;
   int b, i, dl;
   for (b = 0; b < B; ++b) {
@@ -90,6 +96,10 @@ static int validate(int B, const int* n, const int* parent, const int* K, const 
       if (K[off + i] < 1 || d[off + i] < 1) return TMC_ORACLE_BAD_ARG;
     for (i = 1; i < n[b]; ++i)
       if (parent[off + i] < 0 || parent[off + i] >= i) return TMC_ORACLE_BAD_ARG;
+    /* a coupled proposal draws sample k of latent i given the parent's sample k */
+    if (coupled)
+      for (i = 1; i < n[b]; ++i)
+        if (K[off + i] > K[off + parent[off + i]]) return TMC_ORACLE_BAD_ARG;
     /* the leaves of an instance share one dimension (one observation matrix C) */
     dl = -1;
     for (i = 0; i < n[b]; ++i) {
@@ -110,11 +120,25 @@ static int validate(int B, const int* n, const int* parent, const int* K, const 
 #define DI(I, i) ((I)->d[i])
 #define DP(I, i) ((i) ? (I)->d[(I)->parent[i]] : (I)->d[0])
 
-/* z_i^k = m_i + exp(logs_i) * eps_i^k (reparameterised sample). */
-static void sample(const inst_t* I, int i, int k, double* z) {
+/* Proposal mean of z_i^k: m_i, plus A_i (z_p^k - m_p) with a coupled proposal (zp = the
+   parent's sample with the same index k; NULL at the root). */
+static void q_mean_of(const inst_t* I, int i, const double* zp, double* mq) {
+  int r, c, d = DI(I, i), dp = DP(I, i);
+  for (r = 0; r < d; ++r) {
+    double s = I->m[I->oq[i] + r];
+    if (I->A && i > 0 && zp)
+      for (c = 0; c < dp; ++c)
+        s += I->A[I->ow[i] + (long long)r * dp + c] * (zp[c] - I->m[I->oq[I->parent[i]] + c]);
+    mq[r] = s;
+  }
+}
+
+/* z_i^k = (proposal mean) + exp(logs_i) * eps_i^k (reparameterised sample). */
+static void sample(const inst_t* I, int i, int k, const double* zp, double* z) {
   int j, d = DI(I, i);
   const double* e = I->eps + I->oz[i] + (long long)k * d;
-  for (j = 0; j < d; ++j) z[j] = I->m[I->oq[i] + j] + exp(I->logs[I->oq[i] + j]) * e[j];
+  q_mean_of(I, i, zp, z);
+  for (j = 0; j < d; ++j) z[j] += exp(I->logs[I->oq[i] + j]) * e[j];
 }
 
 /* log N(y; mean, var I) in dimension dim. */
@@ -128,13 +152,15 @@ static double log_normal_iso(const double* y, const double* mean, int dim, doubl
   return -0.5 * s / var - 0.5 * dim * (LOG_2PI + log(var));
 }
 
-/* log Q_i(z) for the diagonal Gaussian proposal, evaluated as a density of z. */
-static double log_q(const inst_t* I, int i, const double* z) {
-  double s = 0.0;
+/* log Q_i(z | zp) for the diagonal Gaussian proposal, evaluated as a density of z (zp: the
+   parent's sample the proposal of this sample was conditioned on). */
+static double log_q(const inst_t* I, int i, const double* z, const double* zp) {
+  double s = 0.0, mq[1024];
   int j;
+  q_mean_of(I, i, zp, mq);
   for (j = 0; j < DI(I, i); ++j) {
     double ls = I->logs[I->oq[i] + j];
-    double r = (z[j] - I->m[I->oq[i] + j]) * exp(-ls);
+    double r = (z[j] - mq[j]) * exp(-ls);
     s += -0.5 * r * r - ls - 0.5 * LOG_2PI;
   }
   return s;
@@ -214,8 +240,8 @@ static double log_pair(const ws_t* w, const inst_t* I, int i, int k, int kp) {
 /* Forward recursion; returns log P_TMC of the instance. */
 static double instance_forward(const inst_t* I, ws_t* w) {
   int n = I->n, i, k, kp;
-  for (i = 0; i < n; ++i)
-    for (k = 0; k < KI(I, i); ++k) sample(I, i, k, Z(w, I, i, k));
+  for (i = 0; i < n; ++i)  /* parents first: a coupled proposal reads the parent's sample k */
+    for (k = 0; k < KI(I, i); ++k) sample(I, i, k, i ? Z(w, I, I->parent[i], k) : NULL, Z(w, I, i, k));
   for (i = 1; i < n; ++i) {
     int p = I->parent[i];
     for (kp = 0; kp < KI(I, p); ++kp) cond_mean(I, i, Z(w, I, p, kp), MU(w, I, i, kp));
@@ -223,7 +249,7 @@ static double instance_forward(const inst_t* I, ws_t* w) {
   for (i = 0; i < n; ++i)
     for (k = 0; k < KI(I, i); ++k) {
       const double* z = Z(w, I, i, k);
-      double v = -log_q(I, i, z);
+      double v = -log_q(I, i, z, i ? Z(w, I, I->parent[i], k) : NULL);
       if (i == 0) v += log_normal_iso(z, I->bias + I->oq[0], DI(I, 0), I->prior_var);
       if (I->leaf_slot[i] >= 0) v += log_obs(I, I->leaf_slot[i], z, w->pred);
       w->node[I->ok[i] + k] = v;
@@ -251,8 +277,8 @@ static double instance_forward(const inst_t* I, ws_t* w) {
 static int make_instance(inst_t* I, int b, const offs_t* o, int shared, const int* n, const int* parent,
                          const int* K, const int* d, const int* obs, double prior_var,
                          double obs_var, const double* eps, const double* q_mean,
-                         const double* q_logstd, const double* W, const double* bias,
-                         const double* C, const double* x, int* leaf_slot) {
+                         const double* q_logstd, const double* q_A, const double* W,
+                         const double* bias, const double* C, const double* x, int* leaf_slot) {
   int i, nn = n[b];
   long long z = 0, q = 0, wo = 0, kk = 0, e = 0, ed = 0;
   I->n = nn;
@@ -277,6 +303,7 @@ static int make_instance(inst_t* I, int b, const offs_t* o, int shared, const in
   I->m = q_mean + o->q;
   I->logs = q_logstd + o->q;
   I->W = W + o->W;
+  I->A = q_A ? q_A + o->A : NULL;
   I->bias = shared ? bias : bias + o->q; /* bias shares q_mean's offsets unless shared */
   I->C = C + o->C;
   I->x = x + o->x;
@@ -296,6 +323,7 @@ static void advance(offs_t* o, const inst_t* I, int shared, int nleaves) {
   o->q += I->nq;
   o->x += (long long)nleaves * I->obs;
   o->parent += I->n;
+  o->A += I->nw; /* the proposal is per instance even when the model is shared */
   if (!shared) {
     o->W += I->nw;
     o->C += (long long)I->obs * I->dl;
@@ -305,10 +333,10 @@ static void advance(offs_t* o, const inst_t* I, int shared, int nleaves) {
 int tmc_oracle_log_marginal(int B, const int* n, const int* parent, const int* K, const int* d,
                             const int* obs, int shared, double prior_var, double obs_var,
                             const double* eps, const double* q_mean, const double* q_logstd,
-                            const double* W, const double* bias, const double* C,
-                            const double* x, double* log_phat) {
+                            const double* q_A, const double* W, const double* bias,
+                            const double* C, const double* x, double* log_phat) {
   offs_t o;
-  int b, rc = validate(B, n, parent, K, d, obs);
+  int b, rc = validate(B, n, parent, K, d, obs, q_A != NULL);
   if (rc) return rc;
   memset(&o, 0, sizeof(o));
   for (b = 0; b < B; ++b) {
@@ -317,7 +345,7 @@ int tmc_oracle_log_marginal(int B, const int* n, const int* parent, const int* K
     int* slot = (int*)malloc(sizeof(int) * n[b]);
     int nl = count_leaves(n[b], parent + o.parent, slot);
     if (make_instance(&I, b, &o, shared, n, parent, K, d, obs, prior_var, obs_var, eps, q_mean,
-                      q_logstd, W, bias, C, x, slot)) { free(slot); return TMC_ORACLE_NOMEM; }
+                      q_logstd, q_A, W, bias, C, x, slot)) { free(slot); return TMC_ORACLE_NOMEM; }
     if (ws_alloc(&w, &I)) { inst_free(&I); free(slot); return TMC_ORACLE_NOMEM; }
     log_phat[b] = instance_forward(&I, &w);
     ws_free(&w);
@@ -335,14 +363,23 @@ int tmc_oracle_log_marginal(int B, const int* n, const int* parent, const int* K
  *                                              - log K_i - logmsg_i[kp])
  *   weight of a sample        w_i[k]   = sum_kp pi_i[kp][k]
  * dL/d(log f_i^{(k,kp)}) = pi_i[kp][k]; dL/d(node_i[k]) = w_i[k].
- * Samples: dz = sum over factors touching z of weight * d(log factor)/dz, with -log Q taken
- * as a density of z at fixed (m, logs).  Reparameterisation: z = m + exp(logs) eps, and
- * -log Q(m + exp(logs) eps) = sum_j (eps_j^2/2 + logs_j + log(2 pi)/2), so with
- * g = dz - w * (z - m)/exp(2 logs)  (dz without the proposal's own score):
- *   dm = sum_k g,   dlogs = sum_k w + sum_k g * (z - m).
+ * G_i^k = sum over the factors of log P(x, z) touching z_i^k of weight * d(log factor)/dz
+ * (every other sample held fixed).  Reparameterisation: z_i^k = mq_i^k + s_i eps_i^k with
+ * mq_i^k = m_i (+ A_i (z_p^k - m_p) for a coupled proposal) and s_i = exp(logs_i); in terms
+ * of eps, -log Q_i = sum_j (eps_j^2/2 + logs_j + log(2 pi)/2).  With eps held fixed, moving
+ * z_i^k moves every descendant's sample k through the couplings, so the total derivative is
+ *   T_i^k = G_i^k + sum_{children c} A_c^T T_c^k     (T = G for a factorised proposal),
+ * and
+ *   d/d eps_i^k = s_i T_i^k + w_i[k] eps_i^k,   reported as dz = that / s_i
+ *                 (= G + w (z - m)/s^2 for a factorised proposal: the gradient w.r.t. z with
+ *                 Q evaluated as a density of z),
+ *   dm_i    = sum_k G_i^k          (m_i moves z_i, and the children's samples not at all),
+ *   dlogs_i = sum_k w_i[k] + sum_k T_i^k s_i eps_i^k,
+ *   dA_i    = sum_k T_i^k (z_p^k - m_p)^T.
  * ------------------------------------------------------------------------------------- */
 static void instance_backward(const inst_t* I, ws_t* w, double L, double go, double* dz,
-                              double* dm, double* dlogs, double* dW, double* dbias, double* dC) {
+                              double* dm, double* dlogs, double* dA, double* dW, double* dbias,
+                              double* dC) {
   int n = I->n, i, k, kp, j, c;
   const int dl = I->dl;
   double var = I->prior_var;
@@ -400,10 +437,6 @@ static void instance_backward(const inst_t* I, ws_t* w, double L, double go, dou
       const double* z = Z(w, I, i, k);
       double wk = wt[I->ok[i] + k];
       double* g = dzl + I->oz[i] + (long long)k * d;
-      for (j = 0; j < d; ++j) {
-        double s2 = exp(2.0 * I->logs[I->oq[i] + j]);
-        g[j] += wk * (z[j] - I->m[I->oq[i] + j]) / s2; /* from -log Q_i(z) */
-      }
       if (i == 0)
         for (j = 0; j < d; ++j) {
           double r = (z[j] - I->bias[I->oq[0] + j]) / var;
@@ -426,25 +459,51 @@ static void instance_backward(const inst_t* I, ws_t* w, double L, double go, dou
       }
     }
   }
-  /* outputs */
-  for (i = 0; i < n; ++i) {
-    int d = DI(I, i);
-    double wsum = 0.0;
-    for (k = 0; k < KI(I, i); ++k) wsum += wt[I->ok[i] + k];
-    for (j = 0; j < d; ++j) {
-      double s2 = exp(2.0 * I->logs[I->oq[i] + j]), am = 0.0, al = 0.0;
-      for (k = 0; k < KI(I, i); ++k) {
-        const double* z = Z(w, I, i, k);
-        double g = dzl[I->oz[i] + (long long)k * d + j];
-        double zc = z[j] - I->m[I->oq[i] + j];
-        double gp = g - wt[I->ok[i] + k] * zc / s2;
-        am += gp;
-        al += gp * zc;
-        if (dz) dz[I->oz[i] + (long long)k * d + j] += go * g;
+  /* T = G, then the couplings, children before parents (a child's index is the larger) */
+  {
+    double* T = (double*)malloc(sizeof(double) * (size_t)I->nz);
+    memcpy(T, dzl, sizeof(double) * (size_t)I->nz);
+    if (I->A)
+      for (i = n - 1; i >= 1; --i) {
+        int p = I->parent[i], d = DI(I, i), dp = DI(I, p);
+        for (k = 0; k < KI(I, i); ++k)
+          for (c = 0; c < dp; ++c) {
+            double s = 0.0;
+            for (j = 0; j < d; ++j)
+              s += I->A[I->ow[i] + (long long)j * dp + c] * T[I->oz[i] + (long long)k * d + j];
+            T[I->oz[p] + (long long)k * dp + c] += s;
+          }
       }
-      dm[I->oq[i] + j] += go * am;
-      dlogs[I->oq[i] + j] += go * (wsum + al);
+    /* outputs */
+    for (i = 0; i < n; ++i) {
+      int d = DI(I, i);
+      double wsum = 0.0;
+      for (k = 0; k < KI(I, i); ++k) wsum += wt[I->ok[i] + k];
+      for (j = 0; j < d; ++j) {
+        double s = exp(I->logs[I->oq[i] + j]), am = 0.0, al = 0.0;
+        for (k = 0; k < KI(I, i); ++k) {
+          const long long e = I->oz[i] + (long long)k * d + j;
+          const double ep = I->eps[e];
+          am += dzl[e];
+          al += T[e] * s * ep;
+          if (dz) dz[e] += go * (T[e] + wt[I->ok[i] + k] * ep / s);
+        }
+        dm[I->oq[i] + j] += go * am;
+        dlogs[I->oq[i] + j] += go * (wsum + al);
+      }
+      if (I->A && dA && i > 0) {
+        int p = I->parent[i], dp = DI(I, p);
+        for (j = 0; j < d; ++j)
+          for (c = 0; c < dp; ++c) {
+            double s = 0.0;
+            for (k = 0; k < KI(I, i); ++k)
+              s += T[I->oz[i] + (long long)k * d + j] *
+                   (Z(w, I, p, k)[c] - I->m[I->oq[p] + c]);
+            dA[I->ow[i] + (long long)j * dp + c] += go * s;
+          }
+      }
     }
+    free(T);
   }
   free(wt); free(dzl); free(pred);
 }
@@ -452,11 +511,12 @@ static void instance_backward(const inst_t* I, ws_t* w, double L, double go, dou
 int tmc_oracle_grad(int B, const int* n, const int* parent, const int* K, const int* d,
                     const int* obs, int shared, double prior_var, double obs_var,
                     const double* eps, const double* q_mean, const double* q_logstd,
-                    const double* W, const double* bias, const double* C, const double* x,
-                    const double* grad_out, double* log_phat, double* dz, double* dq_mean,
-                    double* dq_logstd, double* dW, double* dbias, double* dC) {
+                    const double* q_A, const double* W, const double* bias, const double* C,
+                    const double* x, const double* grad_out, double* log_phat, double* dz,
+                    double* dq_mean, double* dq_logstd, double* dq_A, double* dW, double* dbias,
+                    double* dC) {
   offs_t o;
-  int b, rc = validate(B, n, parent, K, d, obs);
+  int b, rc = validate(B, n, parent, K, d, obs, q_A != NULL);
   if (rc) return rc;
   memset(&o, 0, sizeof(o));
   for (b = 0; b < B; ++b) {
@@ -466,14 +526,14 @@ int tmc_oracle_grad(int B, const int* n, const int* parent, const int* K, const 
     int* slot = (int*)malloc(sizeof(int) * n[b]);
     int nl = count_leaves(n[b], parent + o.parent, slot);
     if (make_instance(&I, b, &o, shared, n, parent, K, d, obs, prior_var, obs_var, eps, q_mean,
-                      q_logstd, W, bias, C, x, slot)) { free(slot); return TMC_ORACLE_NOMEM; }
+                      q_logstd, q_A, W, bias, C, x, slot)) { free(slot); return TMC_ORACLE_NOMEM; }
     if (ws_alloc(&w, &I)) { inst_free(&I); free(slot); return TMC_ORACLE_NOMEM; }
     L = instance_forward(&I, &w);
     if (log_phat) log_phat[b] = L;
     /* the bias gradient lives where bias does: dbias + 0 (shared) or dbias + o.q */
     instance_backward(&I, &w, L, grad_out ? grad_out[b] : 1.0, dz ? dz + o.eps : NULL,
-                      dq_mean + o.q, dq_logstd + o.q, dW + o.W, shared ? dbias : dbias + o.q,
-                      dC + o.C);
+                      dq_mean + o.q, dq_logstd + o.q, dq_A ? dq_A + o.A : NULL, dW + o.W,
+                      shared ? dbias : dbias + o.q, dC + o.C);
     ws_free(&w);
     advance(&o, &I, shared, nl);
     inst_free(&I);
@@ -489,10 +549,11 @@ int tmc_oracle_grad(int B, const int* n, const int* parent, const int* K, const 
 int tmc_oracle_brute_force(int B, const int* n, const int* parent, const int* K, const int* d,
                            const int* obs, int shared, double prior_var, double obs_var,
                            const double* eps, const double* q_mean, const double* q_logstd,
-                           const double* W, const double* bias, const double* C,
-                           const double* x, long long max_combos, double* log_phat) {
+                           const double* q_A, const double* W, const double* bias,
+                           const double* C, const double* x, long long max_combos,
+                           double* log_phat) {
   offs_t o;
-  int b, rc = validate(B, n, parent, K, d, obs);
+  int b, rc = validate(B, n, parent, K, d, obs, q_A != NULL);
   if (rc) return rc;
   memset(&o, 0, sizeof(o));
   for (b = 0; b < B; ++b) {
@@ -503,7 +564,7 @@ int tmc_oracle_brute_force(int B, const int* n, const int* parent, const int* K,
     int i;
     double lognorm = 0.0;
     if (make_instance(&I, b, &o, shared, n, parent, K, d, obs, prior_var, obs_var, eps, q_mean,
-                      q_logstd, W, bias, C, x, slot)) { free(slot); return TMC_ORACLE_NOMEM; }
+                      q_logstd, q_A, W, bias, C, x, slot)) { free(slot); return TMC_ORACLE_NOMEM; }
     for (i = 0; i < I.n; ++i) {
       combos *= KI(&I, i);
       lognorm += log((double)KI(&I, i));
@@ -511,31 +572,40 @@ int tmc_oracle_brute_force(int B, const int* n, const int* parent, const int* K,
     }
     {
       double* lw = (double*)malloc(sizeof(double) * combos);
-      double* zs = (double*)malloc(sizeof(double) * (size_t)I.nq);
+      double* all = (double*)malloc(sizeof(double) * (size_t)I.nz); /* every sample, [i][k][:] */
       double* mu = (double*)malloc(sizeof(double) * (size_t)I.nq);
       double* pred = (double*)malloc(sizeof(double) * I.obs);
       int* kk = (int*)malloc(sizeof(int) * I.n);
+      int k;
+      /* the samples, parents first (a coupled proposal reads the parent's sample k) */
+      for (i = 0; i < I.n; ++i)
+        for (k = 0; k < KI(&I, i); ++k)
+          sample(&I, i, k, i ? all + I.oz[I.parent[i]] + (long long)k * DI(&I, I.parent[i]) : NULL,
+                 all + I.oz[i] + (long long)k * DI(&I, i));
+#define ZB(i, k) (all + I.oz[i] + (long long)(k) * DI(&I, i))
       for (t = 0; t < combos; ++t) {
         long long r = t;
         double v = 0.0;
         for (i = 0; i < I.n; ++i) { kk[i] = (int)(r % KI(&I, i)); r /= KI(&I, i); }
-        for (i = 0; i < I.n; ++i) sample(&I, i, kk[i], zs + I.oq[i]);
-        /* log P(x, z): root prior, conditionals, observations */
+        /* log P(x, z) of the combination: root prior, conditionals, observations; then the
+           proposal densities, sample k_i of latent i given its parent's sample k_i */
         for (i = 0; i < I.n; ++i) {
           int j;
+          const double* zi = ZB(i, kk[i]);
           if (i == 0) {
             for (j = 0; j < DI(&I, 0); ++j) mu[j] = I.bias[I.oq[0] + j];
           } else {
-            cond_mean(&I, i, zs + I.oq[I.parent[i]], mu);
+            cond_mean(&I, i, ZB(I.parent[i], kk[I.parent[i]]), mu);
           }
-          v += log_normal_iso(zs + I.oq[i], mu, DI(&I, i), I.prior_var);
-          if (slot[i] >= 0) v += log_obs(&I, slot[i], zs + I.oq[i], pred);
-          v -= log_q(&I, i, zs + I.oq[i]);
+          v += log_normal_iso(zi, mu, DI(&I, i), I.prior_var);
+          if (slot[i] >= 0) v += log_obs(&I, slot[i], zi, pred);
+          v -= log_q(&I, i, zi, i ? ZB(I.parent[i], kk[i]) : NULL);
         }
         lw[t] = v;
       }
+#undef ZB
       log_phat[b] = logsumexp(lw, (int)combos) - lognorm;
-      free(lw); free(zs); free(mu); free(pred); free(kk);
+      free(lw); free(all); free(mu); free(pred); free(kk);
     }
     advance(&o, &I, shared, nl);
     inst_free(&I);

@@ -20,9 +20,15 @@
  * same W/bias/C (and must have the same n, parent, d_i, obs); their gradients are summed over
  * instances.
  *
+ *   q_A   [sum d_i*d_p] per instance, or NULL   proposal couplings (layout of W, root block
+ *                                     unused): Q_i(z_i^k | parent samples) =
+ *                                     N(m_i + A_i (z_p^k - m_p), diag(exp(2 logs_i))); needs
+ *                                     K_i <= K_parent.  NULL: the factorised Q_i = N(m_i, .)
+ *
  * Gradient outputs have the layout of the matching input and are ACCUMULATED (+=), each
  * instance's contribution multiplied by grad_out[b] (grad_out may be NULL: all ones).
- * dz may be NULL.  Return value: TMC_ORACLE_* status.
+ * dz (= the gradient w.r.t. eps divided by exp(logs)) and dq_A may be NULL.  Return value:
+ * TMC_ORACLE_* status.
  */
 #ifndef TMC_ORACLE_H
 #define TMC_ORACLE_H
@@ -37,23 +43,25 @@ enum { TMC_ORACLE_OK = 0, TMC_ORACLE_BAD_ARG = 1, TMC_ORACLE_NOMEM = 2, TMC_ORAC
 int tmc_oracle_log_marginal(int B, const int* n, const int* parent, const int* K, const int* d,
                             const int* obs, int shared, double prior_var, double obs_var,
                             const double* eps, const double* q_mean, const double* q_logstd,
-                            const double* W, const double* bias, const double* C,
-                            const double* x, double* log_phat);
+                            const double* q_A, const double* W, const double* bias,
+                            const double* C, const double* x, double* log_phat);
 
 /* Analytic gradient of sum_b grad_out[b] * log P_TMC_b (reparameterisation gradients). */
 int tmc_oracle_grad(int B, const int* n, const int* parent, const int* K, const int* d,
                     const int* obs, int shared, double prior_var, double obs_var,
                     const double* eps, const double* q_mean, const double* q_logstd,
-                    const double* W, const double* bias, const double* C, const double* x,
-                    const double* grad_out, double* log_phat, double* dz, double* dq_mean,
-                    double* dq_logstd, double* dW, double* dbias, double* dC);
+                    const double* q_A, const double* W, const double* bias, const double* C,
+                    const double* x, const double* grad_out, double* log_phat, double* dz,
+                    double* dq_mean, double* dq_logstd, double* dq_A, double* dW, double* dbias,
+                    double* dC);
 
 /* Eq. (is) enumerated over all prod K_i combinations; TMC_ORACLE_TOO_BIG above max_combos. */
 int tmc_oracle_brute_force(int B, const int* n, const int* parent, const int* K, const int* d,
                            const int* obs, int shared, double prior_var, double obs_var,
                            const double* eps, const double* q_mean, const double* q_logstd,
-                           const double* W, const double* bias, const double* C,
-                           const double* x, long long max_combos, double* log_phat);
+                           const double* q_A, const double* W, const double* bias,
+                           const double* C, const double* x, long long max_combos,
+                           double* log_phat);
 
 #ifdef __cplusplus
 }

@@ -72,6 +72,10 @@ class Problem:
     meta: dict = field(default_factory=dict)
     Kn: np.ndarray | None = None   # [sum n] int32 per-latent K, or None
     dn: np.ndarray | None = None   # [sum n] int32 per-latent d, or None
+    # coupled (non-factorised) proposal: A_i per latent, laid out like per-instance W blocks
+    # (even when the model is shared); Q_i(z_i^k | parent samples) = N(m_i + A_i (z_p^k - m_p),
+    # diag(exp(2 logs_i))).  None: the factorised proposal.
+    q_A: np.ndarray | None = None
 
     @property
     def B(self) -> int:
@@ -129,7 +133,7 @@ class Problem:
     def slices(self, b: int) -> dict:
         """Slices of every flat array belonging to instance b."""
         nl = [len(self.leaves_of(i)) for i in range(self.B)]
-        eps = q = w = x = c = 0
+        eps = q = w = x = c = a = 0
         out = {}
         for i in range(b + 1):
             Kn, dn, dp = self.node_sizes(i)
@@ -137,13 +141,13 @@ class Problem:
             se, sq, sw = int(np.sum(Kn * dn)), int(np.sum(dn)), int(np.sum(dn * dp))
             sx, sc = nl[i] * int(self.obs[i]), int(self.obs[i]) * dl
             if i == b:
-                out = dict(eps=(eps, eps + se), q=(q, q + sq), x=(x, x + sx),
+                out = dict(eps=(eps, eps + se), q=(q, q + sq), x=(x, x + sx), A=(a, a + sw),
                            parent=(int(np.sum(self.n[:b])), int(np.sum(self.n[:b + 1]))))
                 if self.shared:
                     out.update(W=(0, self.W.size), bias=(0, self.bias.size), C=(0, self.C.size))
                 else:
                     out.update(W=(w, w + sw), bias=(q, q + sq), C=(c, c + sc))
-            eps += se; q += sq; w += sw; x += sx; c += sc
+            eps += se; q += sq; w += sw; x += sx; c += sc; a += sw
         return out
 
 
@@ -440,6 +444,45 @@ def ragged_trees(B, seed, n_choices=(1, 2, 3, 5, 7), Ks=(1, 2, 3, 4), ds=(1, 2, 
         dns.append([dl if i in leaves else int(rng.choice(ds)) for i in range(len(par))])
     obss = [int(rng.integers(1, 5)) for _ in range(B)]
     return make_problem(parents, Kns, dns, obss, shared=False, seed=seed, **kw)
+
+
+def couple_proposal(p: Problem, mode: str = "prior", alpha: float = 0.5) -> Problem:
+    """The same instances with a coupled (non-factorised) proposal: sample k of latent i is
+    drawn given its parent's sample k (Section 2.3, "Non-factorised proposals").
+      mode "prior":  Q_i(z_i | z_p) = P(z_i | z_p) for every non-root latent (A_i = W_i,
+                     m_i = W_i m_p + b_i, std = prior std), as in the paper's comparison of
+                     factorised and non-factorised proposals; the root keeps its proposal.
+      mode "scaled": A_i = alpha W_i with the factorised proposal's m_i and std.
+    Requires one K per instance (sample k of a latent needs a parent sample k)."""
+    import copy
+    q = copy.deepcopy(p)
+    A_l, m_l, ls_l = [], [], []
+    for b in range(p.B):
+        Kn, dn, dp = p.node_sizes(b)
+        assert np.all(Kn == Kn[0]), "a coupled proposal here needs one K per instance"
+        s = p.slices(b)
+        par = p.parents_of(b)
+        Wf = p.W[s["W"][0]:s["W"][1]].astype(np.float64)
+        bf = p.bias[s["bias"][0]:s["bias"][1]].astype(np.float64)
+        m = p.q_mean[s["q"][0]:s["q"][1]].astype(np.float64).copy()
+        ls = p.q_logstd[s["q"][0]:s["q"][1]].astype(np.float64).copy()
+        oq = np.concatenate([[0], np.cumsum(dn)]).astype(int)
+        ow = np.concatenate([[0], np.cumsum(dn * dp)]).astype(int)
+        A = np.zeros(int(ow[-1]))
+        for i in range(1, len(par)):
+            Wi = Wf[ow[i]:ow[i + 1]].reshape(dn[i], dp[i])
+            if mode == "prior":
+                A[ow[i]:ow[i + 1]] = Wi.ravel()
+                m[oq[i]:oq[i + 1]] = Wi @ m[oq[par[i]]:oq[par[i] + 1]] + bf[oq[i]:oq[i + 1]]
+                ls[oq[i]:oq[i + 1]] = 0.5 * np.log(p.prior_var)
+            else:
+                A[ow[i]:ow[i + 1]] = alpha * Wi.ravel()
+        A_l.append(A); m_l.append(m); ls_l.append(ls)
+    q.q_A = np.concatenate(A_l).astype(np.float32)
+    q.q_mean = np.concatenate(m_l).astype(np.float32)
+    q.q_logstd = np.concatenate(ls_l).astype(np.float32)
+    q.name = (p.name or "problem") + "_coupled_" + mode
+    return q
 
 
 def redraw_eps(p: Problem, seed: int) -> np.ndarray:
