@@ -84,6 +84,11 @@ typedef struct {
   int32_t precision;      /* tmc_precision                                                  */
   const int32_t* K_node;  /* [sum n_b] per-latent K_i, or NULL                               */
   const int32_t* d_node;  /* [sum n_b] per-latent d_i, or NULL                               */
+  int32_t coupled_proposal; /* 0: factorised Q_i = N(m_i, diag(exp(2 logs_i))) (Section 2.1);
+                               1: sample k of latent i is drawn given its parent's sample k,
+                               Q_i = N(m_i + A_i (z_p^k - m_p), diag(exp(2 logs_i))) -- a
+                               non-factorised proposal of Section 2.3 (needs K_i <= K_parent,
+                               tmc_inputs.q_A, and not the materialised-factor baseline)      */
 } tmc_problem_desc;
 
 /* Device inputs: contiguous float32, instance b directly after instance b-1 and latent i
@@ -98,6 +103,8 @@ typedef struct {
  *   x         [sum leaves_b*obs_b]  one observation per leaf, leaves in node order */
 typedef struct {
   const float *eps, *q_mean, *q_logstd, *W, *bias, *C, *x;
+  const float* q_A;  /* coupled proposals: A_i, [sum d_i*d_p] per instance (layout of unshared W,
+                        root blocks ignored); NULL otherwise                                 */
 } tmc_inputs;
 
 /* Device gradient outputs (same layouts as the inputs).  Every non-NULL buffer is
@@ -109,10 +116,14 @@ typedef struct {
  *              parameters held fixed)
  *   dq_mean, dq_logstd   reparameterisation gradients w.r.t. m_i and logs_i
  *   dW, dbias, dC        model gradients (summed over instances when shared)
- *   deps       gradient w.r.t. the noise eps (= exp(logs) * dz), same layout as eps; last, so
- *              the fields before it keep the order dz, dq_mean, dq_logstd, dW, dbias, dC */
+ *   deps       gradient w.r.t. the noise eps (= exp(logs) * dz), same layout as eps; after the
+ *              others, so the fields before it keep the order dz, dq_mean, dq_logstd, dW,
+ *              dbias, dC
+ * With a coupled proposal the samples move with their parents' (eps held fixed), and dz is
+ * defined as (d / d eps) / exp(logs) -- which is the factorised definition above when A = 0. */
 typedef struct {
   float *dz, *dq_mean, *dq_logstd, *dW, *dbias, *dC, *deps;
+  float* dq_A;  /* coupled proposals: gradient w.r.t. A_i (layout of q_A; root blocks zero)  */
 } tmc_grads;
 
 /* Builds a plan: validates the description (tree shape, sizes), derives the

@@ -56,9 +56,11 @@ __global__ void __launch_bounds__(256) k_pack_cc(Dev D, TcDev T) {
 // shared-memory stage (TMA) and issues their MMAs into a DP-column accumulator; every thread
 // then owns one sample row (TMEM lane) for the epilogue.  Several CTAs share an SM (64 KB of
 // shared memory, DP TMEM columns each), so one CTA's loads overlap another's MMAs and stores.
+// gmode (coupled proposals): the path gradient G = dz without the proposal's own term and
+// without grad_out, from the FP32 samples, into D.gsrc (layout of the FP32 sample vectors).
 template <int DP>
 __global__ void __launch_bounds__(kDzThreads) k_dz_tc(
-    Dev D, TcDev T, const Tile* __restrict__ tiles, const __grid_constant__ CUtensorMap mVH,
+    Dev D, TcDev T, const Tile* __restrict__ tiles, int gmode, const __grid_constant__ CUtensorMap mVH,
     const __grid_constant__ CUtensorMap mVL, const __grid_constant__ CUtensorMap mEH,
     const __grid_constant__ CUtensorMap mEL, const __grid_constant__ CUtensorMap mZH,
     const __grid_constant__ CUtensorMap mZL, const __grid_constant__ CUtensorMap mWH,
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(kDzThreads) k_dz_tc(
     if (j < d) {
       const float ls = D.q_logstd[nd.off_q + j];
       sd[j] = expf(ls);
-      diag[j] = (float)D.prior_var * expf(-2.f * ls) - 1.f;
+      diag[j] = gmode ? -1.f : (float)D.prior_var * expf(-2.f * ls) - 1.f;
       float v = nd.parent >= 0 ? T.cvec[(long long)t.node * kLdp + j]
                                : D.bias[nd.off_bias + j] - D.q_mean[nd.off_q + j];
       if (nd.leaf_slot >= 0) {
@@ -156,11 +158,26 @@ __global__ void __launch_bounds__(kDzThreads) k_dz_tc(
   // epilogue: thread r owns sample t.row0 + r (TMEM lane r)
   const int k = t.row0 + (int)threadIdx.x;
   const bool valid = s_ok && k < nd.K;
-  const float gb = D.grad_out ? (float)D.grad_out[nd.b] : 1.f;
+  const float gb = (D.grad_out && !gmode) ? (float)D.grad_out[nd.b] : 1.f;
   const float w = valid ? D.q[nd.off_nk + k] * gb * D.inv_var : 0.f;
   const uint32_t lane_acc = acc + ((uint32_t)(32 * warp) << 16);
   const long long row = nd.off_e + (long long)k * d;  // eps / dz / deps: the caller's layout
   const bool vec4 = ((nd.off_e | (long long)d) & 3) == 0;
+  if (gmode) {  // G from the FP32 samples (z~ is no longer s eps with couplings)
+    const long long zrow = nd.off_nkd + (long long)k * d;
+#pragma unroll 1
+    for (int g = 0; g < DP / 32 && g * 32 < d; ++g) {  // warp-uniform
+      uint32_t v[32];
+      tmem_ld32(lane_acc + g * 32, v);
+      tmem_wait_ld();
+      if (!valid) continue;
+#pragma unroll
+      for (int x = 0; x < 32; ++x) {
+        const int c = g * 32 + x;
+        if (c < d) D.gsrc[zrow + c] = w * (__uint_as_float(v[x]) + vec[c] + D.zt[zrow + c] * diag[c]);
+      }
+    }
+  } else
 #pragma unroll 1
   for (int g = 0; g < DP / 32 && g * 32 < d; ++g) {  // warp-uniform
     uint32_t v[32];
@@ -237,16 +254,49 @@ void release_dz(TcWork& w) {
 
 void launch_dz(TcWork& w, const Dev& D, cudaStream_t s) {
   k_pack_cc<<<w.num_c, 256, 0, s>>>(D, w.t);
+  const int gmode = D.coupled ? 1 : 0;
   for (int c = 0; c < 2; ++c) {
     const int b = w.dz_b[c], n = w.dz_e[c] - b;
     if (!n) continue;
     if (c == 0)
-      k_dz_tc<64><<<n, kDzThreads, kDzSmem, s>>>(D, w.t, w.d_dz_tiles + b, w.mVH, w.mVL, w.mEH, w.mEL, w.mZH, w.mZL,
-                                                 w.mWH, w.mWL, w.mWTH, w.mWTL, w.mCCH, w.mCCL);
+      k_dz_tc<64><<<n, kDzThreads, kDzSmem, s>>>(D, w.t, w.d_dz_tiles + b, gmode, w.mVH, w.mVL, w.mEH, w.mEL, w.mZH,
+                                                 w.mZL, w.mWH, w.mWL, w.mWTH, w.mWTL, w.mCCH, w.mCCL);
     else
-      k_dz_tc<128><<<n, kDzThreads, kDzSmem, s>>>(D, w.t, w.d_dz_tiles + b, w.mVH, w.mVL, w.mEH, w.mEL, w.mZH, w.mZL,
-                                                  w.mWH, w.mWL, w.mWTH, w.mWTL, w.mCCH, w.mCCL);
+      k_dz_tc<128><<<n, kDzThreads, kDzSmem, s>>>(D, w.t, w.d_dz_tiles + b, gmode, w.mVH, w.mVL, w.mEH, w.mEL,
+                                                  w.mZH, w.mZL, w.mWH, w.mWL, w.mWTH, w.mWTL, w.mCCH, w.mCCL);
   }
+}
+
+// Coupled proposals: rows of the FP32 samples -> split fp16 operand rows, and z~ . c_i.
+// One warp per sample row (lanes over the latent dimension); grid: 128-row tiles of every node.
+__global__ void __launch_bounds__(256) k_pack_z(Dev D, TcDev T, const Tile* __restrict__ tiles) {
+  const Tile t = tiles[blockIdx.x];
+  const NodeInfo nd = D.nodes[t.node];
+  const int d = nd.d, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool root = nd.parent < 0;
+  for (int r = w; r < kRows; r += 8) {
+    const int k = t.row0 + r;
+    if (k >= nd.K) break;
+    const float* z = D.zt + nd.off_nkd + (long long)k * d;
+    __half* zh = T.ZH + (nd.off_nk + k) * kLdp;
+    __half* zl = T.ZL + (nd.off_nk + k) * kLdp;
+    float zc = 0.f;
+    for (int j = lane; j < d; j += 32) {
+      const float v = z[j];
+      float hi, lo;
+      split_half(v, hi, lo);
+      zh[j] = __float2half_rn(hi);
+      zl[j] = __float2half_rn(lo);
+      if (!root) zc = fmaf(v, T.cvec[(long long)t.node * kLdp + j], zc);
+    }
+    for (int o = 16; o > 0; o >>= 1) zc += __shfl_xor_sync(0xffffffffu, zc, o);
+    if (lane == 0) T.zc[nd.off_nk + k] = zc;
+  }
+}
+
+void launch_pack_z(TcWork& w, const Dev& D, cudaStream_t s) {
+  const int n = (int)w.dz_tiles.size();
+  if (n) k_pack_z<<<n, 256, 0, s>>>(D, w.t, w.d_dz_tiles);
 }
 
 }  // namespace tc

@@ -1523,7 +1523,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     __threadfence();  // weights visible device-wide before the completion count moves
     // sample gradients requested: V / q (the conditional mean of the parent's samples given
     // this child sample) to the V rows, split, for the sample-gradient assembly
-    const bool want_v = D.dz != nullptr || D.deps != nullptr;
+    const bool want_v = D.dz != nullptr || D.deps != nullptr || D.coupled;
     const float rq = qtot > 0.f ? 1.f / qtot : 0.f;
     // epilogue: V row -> fp16 A tile of G
     if (ok) ok = mbar_wait(&bar_v, 0);

@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(kThreads) k_node_grad(Dev D, const Tile* __res
           g += D.gz[idx];
         }
         D.gz[idx] = g;
-        if (D.dz || D.deps) {
+        if ((D.dz || D.deps) && !D.coupled) {  // coupled proposals: k_couple_out
           const long long eidx = nd.off_e + (long long)k * d + c;
           const float ls = D.q_logstd[nd.off_q + c];
           const float dzv = go * (g + qk[a] * zt * expf(-2.f * ls));

@@ -35,6 +35,7 @@ struct NodeInfo {
   long long off_C;     // start of the instance's C ([obs][d])
   long long off_x;     // start of this leaf's observation ([obs]) in x (leaves only)
   long long off_pW;    // start of this node's block in the per-(instance, node) dW partials
+  long long off_A;     // start of A_i ([d][dp]) in q_A / dq_A (per instance, like unshared W)
 };
 
 struct InstInfo {
@@ -85,6 +86,12 @@ struct Dev {
   float* pC;      // per-instance dC partials (shared params only)
   int* err;       // device error word
   long long wait_limit;   // clock cycles a cross-CTA dependency wait polls before giving up
+  // coupled proposals (sample k of a latent drawn given its parent's sample k)
+  int coupled;
+  const float* q_A;       // input: A_i blocks
+  float* dq_A;            // output
+  float* tq;              // [nkd] total derivative T of every sample (eps held fixed)
+  float* gsrc;            // [nkd] path gradient G of every sample (FP32 path: gz)
   float* fac;             // unfused baseline: every edge's K x K log-factors (relative)
   const long long* fac_off;  // per node: start of its edge's block in fac
   // roots with more than kRootChunk children: their messages are summed in chunks of children
@@ -125,5 +132,10 @@ void launch_param_dC(const Dev& D, int maxd, int maxobs, cudaStream_t s);
 void launch_shared_reduce(const Dev& D, long long nW, long long nb, long long nC, long long rootW,
                           cudaStream_t s);
 void launch_root_bias(const Dev& D, cudaStream_t s);
+// coupled proposals (k_couple.cu)
+void launch_couple_fwd(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s);
+void launch_couple_T(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s);
+void launch_couple_out(const Dev& D, const Tile* tiles, int ntiles, const int* nonroot, int n_nonroot,
+                       int maxd, cudaStream_t s);
 
 }  // namespace tmc

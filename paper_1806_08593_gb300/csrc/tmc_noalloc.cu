@@ -74,6 +74,7 @@ tmc_status build_tables(const tmc_problem_desc* ds, Layout& L) {
   if (!(ds->prior_var > 0.0) || !(ds->obs_var > 0.0)) return TMC_ERR_INVALID_ARG;
   if (ds->precision != TMC_PREC_FP32) return TMC_ERR_UNSUPPORTED;
   if (ds->K_node || ds->d_node) return TMC_ERR_UNSUPPORTED;  // one K and d per instance here
+  if (ds->coupled_proposal) return TMC_ERR_UNSUPPORTED;      // factorised proposals here
   if (B > kNaMaxInst) return TMC_ERR_UNSUPPORTED;
   L = Layout();
   L.B = B;

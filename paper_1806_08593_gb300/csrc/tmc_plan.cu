@@ -35,6 +35,7 @@ struct tmc_plan_s {
   int B = 0, shared = 0, precision = 0;
   double prior_var = 1.0, obs_var = 1.0;
   int maxK = 0, maxd = 0, maxobs = 0, maxlevel = 0;
+  int coupled = 0;      // coupled (non-factorised) proposal
   bool ragged = false;  // some instance has a different K or d from latent to latent
   long long shared_nW = 0, shared_nb = 0, shared_nC = 0, shared_rootW = 0;  // one instance's parameter sizes
   int root_fanout = 0;  // most children of any instance's root
@@ -154,6 +155,7 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
     return TMC_ERR_INVALID_ARG;
   p->B = B;
   p->shared = ds->shared_params ? 1 : 0;
+  p->coupled = ds->coupled_proposal ? 1 : 0;
   p->precision = ds->precision;
   p->prior_var = ds->prior_var;
   p->obs_var = ds->obs_var;
@@ -193,6 +195,9 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
         dl = dv[i];
       }
     }
+    if (p->coupled)  // sample k of a latent is drawn given its parent's sample k
+      for (int i = 1; i < n; ++i)
+        if (Kv[i] > Kv[par[i]]) return TMC_ERR_INVALID_ARG;
     if (p->shared && b > 0) {
       if (n != ds->n[0] || obs != ds->obs_dim[0]) return TMC_ERR_INVALID_ARG;
       for (int i = 0; i < n; ++i)
@@ -231,6 +236,7 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
       nd.off_C = iC;
       nd.off_x = off_x + (long long)(nd.leaf_slot >= 0 ? nd.leaf_slot : 0) * obs;
       nd.off_pW = off_pW + w;
+      nd.off_A = off_pW + w;  // the couplings are per instance, laid out like unshared W
       p->nodes.push_back(nd);
       p->maxlevel = std::max(p->maxlevel, level[i]);
       e += (long long)Kv[i] * dv[i];
@@ -273,8 +279,9 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
   p->tot_nk = off_nk;
   p->tot_nkd = off_nkd;
   p->tot_q = off_q;
-  // the materialised-factor baseline is built for one K and d per instance
-  if (p->ragged && p->precision == TMC_PREC_FP32_UNFUSED) return TMC_ERR_UNSUPPORTED;
+  // the materialised-factor baseline is built for one K and d per instance and a factorised
+  // proposal
+  if ((p->ragged || p->coupled) && p->precision == TMC_PREC_FP32_UNFUSED) return TMC_ERR_UNSUPPORTED;
 
   // tile lists (a tile is a node and 64 of its rows: its own samples, or, for the tiles of an
   // edge p -> i in the projection, forward and rows-adjoint lists, the parent's samples)
@@ -311,6 +318,10 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
   p->t_level_e.assign(p->maxlevel + 1, 0);
   p->t_clevel_b.assign(p->maxlevel + 1, 0);
   p->t_clevel_e.assign(p->maxlevel + 1, 0);
+  p->t_clevel_b[0] = (int)p->tiles.size();  // the roots' own rows (coupled proposals' T)
+  for (int g = 0; g < G; ++g)
+    if (p->nodes[g].level == 0) add_tiles(g);
+  p->t_clevel_e[0] = (int)p->tiles.size();
   for (int L = 1; L <= p->maxlevel; ++L) {
     p->t_level_b[L] = (int)p->tiles.size();
     for (int g = 0; g < G; ++g)
@@ -357,10 +368,16 @@ tmc_status alloc_device(tmc_plan p) {
   float *zt, *mut, *zn, *mun, *u, *beta, *lam, *q, *nodemax, *dmu, *gz, *pW, *pbias, *pC, *fac;
   double *nodeconst, *root_part;
   const bool tc_plan = p->precision == TMC_PREC_FP16_TC;
-  const long long nkd32 = tc_plan ? 0 : nkd;  // FP32-path sample vectors (unused on the tc path)
+  // FP32-path sample vectors (unused on the tc path, except T and G of coupled proposals, kept
+  // in mut and gz)
+  const long long nkd32 = tc_plan ? 0 : nkd, nkdc = (tc_plan && p->coupled) ? nkd : nkd32;
+  const long long nkdt = p->coupled ? nkd : 0;  // T of coupled proposals (its own buffer: mu~
+                                                // must survive for a second backward call)
+  float* tqb = nullptr;
   std::vector<Sub> subs = {
       {(void**)&zt, sizeof(float) * nkd},      {(void**)&mut, sizeof(float) * nkd32},
-      {(void**)&dmu, sizeof(float) * nkd32},   {(void**)&gz, sizeof(float) * nkd32},
+      {(void**)&dmu, sizeof(float) * nkd32},   {(void**)&gz, sizeof(float) * nkdc},
+      {(void**)&tqb, sizeof(float) * nkdt},
       {(void**)&zn, sizeof(float) * nk},       {(void**)&mun, sizeof(float) * nk},
       {(void**)&u, sizeof(float) * nk},        {(void**)&beta, sizeof(float) * nk},
       {(void**)&lam, sizeof(float) * nk},      {(void**)&q, sizeof(float) * nk},
@@ -400,6 +417,9 @@ tmc_status alloc_device(tmc_plan p) {
   D.pW = nW ? pW : nullptr; D.pbias = nb ? pbias : nullptr; D.pC = nC ? pC : nullptr;
   D.err = p->d_err;
   D.wait_limit = p->wait_limit;
+  D.coupled = p->coupled;
+  D.tq = p->coupled ? tqb : nullptr;
+  D.gsrc = p->coupled ? gz : nullptr;  // G: written by the FP32 node gradients or k_dz_tc
   D.fac = p->fac_total ? fac : nullptr;
   D.fac_off = p->d_fac_off;
   D.root_chunks = p->d_root_chunks;
@@ -493,23 +513,40 @@ tmc_status tmc_plan_workspace_bytes(tmc_plan p, size_t* bytes) {
 
 tmc_status tmc_log_marginal(tmc_plan p, const tmc_inputs* in, double* log_phat, void* stream) {
   if (!p || !inputs_ok(in) || !log_phat) return TMC_ERR_INVALID_ARG;
+  if (p->coupled && !in->q_A) return TMC_ERR_INVALID_ARG;
   if (p->fault == kFaultLaunch) return TMC_ERR_CUDA;  // as if the first launch failed
   cudaStream_t s = (cudaStream_t)stream;
   Dev D = p->dev;
   D.eps = in->eps; D.q_mean = in->q_mean; D.q_logstd = in->q_logstd;
   D.W = in->W; D.bias = in->bias; D.C = in->C; D.x = in->x;
+  D.q_A = p->coupled ? in->q_A : nullptr;
   D.log_phat = log_phat;
   const Tile* T = p->d_tiles;
   const bool tc_path = p->precision == TMC_PREC_FP16_TC;
+  // coupled proposals: z~_i += A_i z~_p, level by level from the root (FP32 samples)
+  auto couple_samples = [&]() -> tmc_status {
+    for (int L = 1; L <= p->maxlevel; ++L) {
+      const int b = p->t_clevel_b[L], e = p->t_clevel_e[L];
+      TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_couple_fwd(D, T + b, e - b, s); }));
+    }
+    return TMC_OK;
+  };
   TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_node_const(D, s); }));
   if (tc_path) {
     // split W_i and c_i first: the sampling kernel forms z~ . c_i, the conditional means are
     // formed inside the edge kernels
     TRY(timed(p, TMC_KC_PROJECT, s, [&] { tc::launch_pack(p->tcw, D, s); }));
-    TRY(timed(p, TMC_KC_SAMPLE, s, [&] { tc::launch_sample(p->tcw, D, s); }));
+    if (p->coupled) {  // FP32 samples through the couplings, then split into the tc operands
+      TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_sample(D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
+      TRY(couple_samples());
+      TRY(timed(p, TMC_KC_SAMPLE, s, [&] { tc::launch_pack_z(p->tcw, D, s); }));
+    } else {
+      TRY(timed(p, TMC_KC_SAMPLE, s, [&] { tc::launch_sample(p->tcw, D, s); }));
+    }
     TRY(timed(p, TMC_KC_SAMPLE, s, [&] { tc::launch_obs(p->tcw, D, s); }));
   } else {
     TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_sample(D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
+    if (p->coupled) TRY(couple_samples());
     TRY(timed(p, TMC_KC_SAMPLE, s, [&] { launch_obs_fwd(D, T + p->t_leaf_b, p->t_leaf_e - p->t_leaf_b, s); }));
     TRY(timed(p, TMC_KC_PROJECT, s, [&] { launch_project(D, T + p->t_proj_b, p->t_proj_e - p->t_proj_b, s); }));
   }
@@ -546,8 +583,12 @@ tmc_status tmc_backward(tmc_plan p, const tmc_inputs* in, const double* grad_out
   D.grad_out = grad_out;
   D.dz = g->dz; D.deps = g->deps; D.dq_mean = g->dq_mean; D.dq_logstd = g->dq_logstd;
   D.dW = g->dW; D.dbias = g->dbias; D.dC = g->dC;
+  D.q_A = p->coupled ? in->q_A : nullptr;
+  D.dq_A = p->coupled ? g->dq_A : nullptr;
   const Tile* T = p->d_tiles;
-  const bool sample_grads = g->dz || g->deps;
+  // per-sample path gradients are needed for dz / deps, and, with coupled proposals, for the
+  // proposal gradients too (they run through the couplings sample by sample)
+  const bool sample_grads = g->dz || g->deps || p->coupled;
   if (tc_path) {
     if (p->maxlevel >= 1) TRY(timed(p, TMC_KC_EDGE_BWD, s, [&] { tc::launch_edge_bwd(p->tcw, D, s); }));
     if (sample_grads && p->maxlevel >= 1)
@@ -559,12 +600,25 @@ tmc_status tmc_backward(tmc_plan p, const tmc_inputs* in, const double* grad_out
       TRY(timed(p, TMC_KC_EDGE_BWD, s, [&] { launch_edge_bwd_rows_f32(D, T + b, e - b, p->maxK, s); }));
     }
   }
+  // coupled proposals: T = G + sum_c A_c^T T_c from the leaves up, then dz, deps, dlogs, dA
+  auto couple_grads = [&]() -> tmc_status {
+    for (int L = p->maxlevel; L >= 0; --L) {
+      const int b = p->t_clevel_b[L], e = p->t_clevel_e[L];
+      TRY(timed(p, TMC_KC_SAMPLE_GRAD, s, [&] { launch_couple_T(D, T + b, e - b, s); }));
+    }
+    return timed(p, TMC_KC_SAMPLE_GRAD, s, [&] {
+      launch_couple_out(D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, p->d_nonroot,
+                        (int)p->nonroot.size(), p->maxd, s);
+    });
+  };
   if (tc_path) {
     TRY(timed(p, TMC_KC_PARAM, s, [&] { tc::launch_unpack_grads(p->tcw, D, s); }));
     if (sample_grads) TRY(timed(p, TMC_KC_SAMPLE_GRAD, s, [&] { tc::launch_dz(p->tcw, D, s); }));
+    if (p->coupled) TRY(couple_grads());  // (k_dz_tc wrote the path gradients G)
   } else {
     TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_node_grad(D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
     TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_node_reduce(D, s); }));
+    if (p->coupled) TRY(couple_grads());
     if (g->dW || g->dbias)
       TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_param_dW(D, p->d_nonroot, (int)p->nonroot.size(), p->maxd, s); }));
     if (g->dC) TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_param_dC(D, p->maxd, p->maxobs, s); }));

@@ -139,6 +139,9 @@ void launch_unpack_grads(TcWork& w, const Dev& D, cudaStream_t s);
 // set, and launch_unpack_grads, which forms C^T C): the row-direction edge pass, then the
 // assembly (k_dz_tc.cu).
 void launch_edge_rows(TcWork& w, const Dev& D, cudaStream_t s);
+// Coupled proposals: split the FP32 samples (after the couplings) into the packed operands,
+// with z~ . c_i (the other per-sample terms come from the FP32 sampler).
+void launch_pack_z(TcWork& w, const Dev& D, cudaStream_t s);
 void launch_dz(TcWork& w, const Dev& D, cudaStream_t s);
 tmc_status prepare_dz(TcWork& w, const std::vector<NodeInfo>& nodes);
 void release_dz(TcWork& w);

@@ -41,15 +41,17 @@ class ProblemDesc(ctypes.Structure):
                 ("parent", ctypes.c_void_p), ("K", ctypes.c_void_p), ("d", ctypes.c_void_p),
                 ("obs_dim", ctypes.c_void_p), ("shared_params", ctypes.c_int32),
                 ("prior_var", ctypes.c_double), ("obs_var", ctypes.c_double),
-                ("precision", ctypes.c_int32), ("K_node", ctypes.c_void_p), ("d_node", ctypes.c_void_p)]
+                ("precision", ctypes.c_int32), ("K_node", ctypes.c_void_p), ("d_node", ctypes.c_void_p),
+                ("coupled_proposal", ctypes.c_int32)]
 
 
 class Inputs(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_void_p) for k in ("eps", "q_mean", "q_logstd", "W", "bias", "C", "x")]
+    _fields_ = [(k, ctypes.c_void_p) for k in ("eps", "q_mean", "q_logstd", "W", "bias", "C", "x", "q_A")]
 
 
 class Grads(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_void_p) for k in ("dz", "dq_mean", "dq_logstd", "dW", "dbias", "dC", "deps")]
+    _fields_ = [(k, ctypes.c_void_p) for k in ("dz", "dq_mean", "dq_logstd", "dW", "dbias", "dC", "deps",
+                                               "dq_A")]
 
 
 INPUT_NAMES = [f[0] for f in Inputs._fields_]
@@ -119,7 +121,7 @@ class Plan:
     """Owns a tmc_plan (topology, schedule, device workspace) for one batch shape."""
 
     def __init__(self, n, parent, K, d, obs, shared: bool, prior_var: float, obs_var: float,
-                 precision: str = "fp32", K_node=None, d_node=None):
+                 precision: str = "fp32", K_node=None, d_node=None, coupled: bool = False):
         lib = load_library()
         self._keep = [np.ascontiguousarray(a, dtype=np.int32) for a in (n, parent, K, d, obs)]
         n_, par_, K_, d_, o_ = self._keep
@@ -127,7 +129,9 @@ class Plan:
         self._keep += per
         desc = ProblemDesc(len(n_), n_.ctypes.data, par_.ctypes.data, K_.ctypes.data, d_.ctypes.data,
                            o_.ctypes.data, int(bool(shared)), float(prior_var), float(obs_var),
-                           PRECISIONS[precision], *[None if a is None else a.ctypes.data for a in per])
+                           PRECISIONS[precision], *[None if a is None else a.ctypes.data for a in per],
+                           int(bool(coupled)))
+        self.coupled = bool(coupled)
         h = ctypes.c_void_p()
         _check(lib.tmc_plan_create(ctypes.byref(desc), ctypes.byref(h)), "tmc_plan_create")
         self._h = h
@@ -140,13 +144,13 @@ class Plan:
     @classmethod
     def from_problem(cls, p, precision: str = "fp32") -> "Plan":
         return cls(p.n, p.parent, p.K, p.d, p.obs, p.shared, p.prior_var, p.obs_var, precision,
-                   K_node=p.Kn, d_node=p.dn)
+                   K_node=p.Kn, d_node=p.dn, coupled=p.q_A is not None)
 
     @staticmethod
     def to_device(p, device="cuda") -> dict:
         import torch
         return {k: torch.from_numpy(np.ascontiguousarray(getattr(p, k), dtype=np.float32)).to(device)
-                for k in INPUT_NAMES}
+                for k in INPUT_NAMES if getattr(p, k, None) is not None}
 
     def close(self):
         if getattr(self, "_h", None):
@@ -161,7 +165,7 @@ class Plan:
 
     # ---- raw C-ABI calls ---------------------------------------------------------------
     def _inputs(self, t: dict) -> Inputs:
-        return Inputs(*[_ptr(t[k]) for k in INPUT_NAMES])
+        return Inputs(*[_ptr(t.get(k)) for k in INPUT_NAMES])
 
     def forward(self, t: dict, out=None, stream=None):
         """log P_TMC per instance (float64 CUDA tensor [B])."""
@@ -179,7 +183,7 @@ class Plan:
         """Gradients of sum_b grad_out[b] log P_TMC_b; ``want`` selects the outputs."""
         import torch
         src = {"dz": "eps", "deps": "eps", "dq_mean": "q_mean", "dq_logstd": "q_logstd",
-               "dW": "W", "dbias": "bias", "dC": "C"}
+               "dW": "W", "dbias": "bias", "dC": "C", "dq_A": "q_A"}
         if out is None:
             out = {k: torch.empty_like(t[src[k]]) for k in want}
         g = Grads(*[_ptr(out.get(k)) for k in GRAD_NAMES])
@@ -241,7 +245,7 @@ def log_marginal_noalloc(p, t: dict, out=None, stream=None):
                        float(p.prior_var), float(p.obs_var), PRECISIONS["fp32"], None, None)
     if out is None:
         out = torch.empty(len(keep[0]), dtype=torch.float64, device=t["eps"].device)
-    inp = Inputs(*[_ptr(t[k]) for k in INPUT_NAMES])
+    inp = Inputs(*[_ptr(t.get(k)) for k in INPUT_NAMES])
     _check(lib.tmc_log_marginal_noalloc(ctypes.byref(desc), ctypes.byref(inp), _ptr(out), _stream(stream)),
            "tmc_log_marginal_noalloc")
     return out
@@ -254,9 +258,11 @@ def _autograd():
         """log P_TMC per instance; backward runs the library's fused adjoint."""
 
         @staticmethod
-        def forward(ctx, plan, eps, q_mean, q_logstd, W, bias, C, x):
+        def forward(ctx, plan, eps, q_mean, q_logstd, W, bias, C, x, q_A=None):
             t = dict(eps=eps.contiguous(), q_mean=q_mean.contiguous(), q_logstd=q_logstd.contiguous(),
                      W=W.contiguous(), bias=bias.contiguous(), C=C.contiguous(), x=x.contiguous())
+            if q_A is not None:
+                t["q_A"] = q_A.contiguous()
             out = plan.forward(t)
             ctx.plan = plan
             ctx.t = t
@@ -266,17 +272,17 @@ def _autograd():
         @staticmethod
         def backward(ctx, grad_out):
             plan, t = ctx.plan, ctx.t
-            names = ["deps", "dq_mean", "dq_logstd", "dW", "dbias", "dC"]
-            flags = ctx.needs_input_grad[1:7]
-            want = [n for n, f in zip(names, flags) if f]
+            names = ["deps", "dq_mean", "dq_logstd", "dW", "dbias", "dC", None, "dq_A"]
+            flags = ctx.needs_input_grad[1:9]
+            want = [n for n, f in zip(names, flags) if f and n]
             if not want:
-                return (None,) * 8
+                return (None,) * 9
             # the adjoint reads the state saved by the matching forward; redo it if another
             # forward ran on this plan in between
             if plan.forward_calls != ctx.call:
                 plan.forward(t)
             g = plan.backward(t, grad_out=grad_out.contiguous(), want=want)
-            return (None,) + tuple(g.get(n) for n in names) + (None,)
+            return (None,) + tuple(g.get(n) if n else None for n in names)
 
     return TMCLogMarginal
 
@@ -284,9 +290,10 @@ def _autograd():
 _TMC = None
 
 
-def tmc_log_marginal(plan: Plan, eps, q_mean, q_logstd, W, bias, C, x):
-    """Differentiable log P_TMC[b] (float64, [B]) through the CUDA library."""
+def tmc_log_marginal(plan: Plan, eps, q_mean, q_logstd, W, bias, C, x, q_A=None):
+    """Differentiable log P_TMC[b] (float64, [B]) through the CUDA library (q_A: the coupling
+    matrices of a coupled-proposal plan)."""
     global _TMC
     if _TMC is None:
         _TMC = _autograd()
-    return _TMC.apply(plan, eps, q_mean, q_logstd, W, bias, C, x)
+    return _TMC.apply(plan, eps, q_mean, q_logstd, W, bias, C, x, q_A)

@@ -16,7 +16,8 @@ def gpu_run(p, precision="fp32", grads=True, grad_out=None, want=None):
     out = {"log_phat": None}
     if grads:
         go = None if grad_out is None else torch.as_tensor(grad_out, dtype=torch.float64, device="cuda")
-        want = want or ("dz", "deps", "dq_mean", "dq_logstd", "dW", "dbias", "dC")
+        want = want or ("dz", "deps", "dq_mean", "dq_logstd", "dW", "dbias", "dC") + \
+            (("dq_A",) if p.q_A is not None else ())
         g = plan.backward(t, grad_out=go, want=want)
         out.update({k: v.cpu().numpy().astype(np.float64) for k, v in g.items()})
     torch.cuda.synchronize()
