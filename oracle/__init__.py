@@ -27,6 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle_tmc.so")
 _SRC = os.path.join(_HERE, "tmc_oracle.c")
+_SRC_LOOPY = os.path.join(_HERE, "tmc_oracle_loopy.c")
 _lock = threading.Lock()
 _lib = None
 
@@ -35,10 +36,11 @@ def build(force: bool = False) -> str:
     """Compile the oracle with the host C compiler (OpenMP over parent-sample rows)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "tmc_oracle.h"))):
+            os.path.getmtime(_SRC), os.path.getmtime(_SRC_LOOPY),
+            os.path.getmtime(os.path.join(_HERE, "tmc_oracle.h"))):
         tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
-               "-Wall", "-o", tmp, _SRC, "-lm"]
+               "-Wall", "-o", tmp, _SRC, _SRC_LOOPY, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -55,7 +57,12 @@ def _load():
             lib.tmc_oracle_log_marginal.argtypes = common + [P]
             lib.tmc_oracle_grad.argtypes = common + [P, P, P, P, P, P, P, P, P]
             lib.tmc_oracle_brute_force.argtypes = common + [ctypes.c_longlong, P]
-            for f in (lib.tmc_oracle_log_marginal, lib.tmc_oracle_grad, lib.tmc_oracle_brute_force):
+            dia = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                   ctypes.c_double, ctypes.c_double, P, P, P, P, P, P, P]
+            lib.tmc_oracle_diamond_log_marginal.argtypes = dia + [P]
+            lib.tmc_oracle_diamond_brute_force.argtypes = dia + [ctypes.c_longlong, P]
+            for f in (lib.tmc_oracle_log_marginal, lib.tmc_oracle_grad, lib.tmc_oracle_brute_force,
+                      lib.tmc_oracle_diamond_log_marginal, lib.tmc_oracle_diamond_brute_force):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -119,6 +126,33 @@ def brute_force(p, max_combos: int = 2_000_000, **overrides) -> np.ndarray:
     out = np.zeros(p.B, dtype=np.float64)
     _check(lib.tmc_oracle_brute_force(*args, ctypes.c_longlong(max_combos), _ptr(out)),
            "brute_force")
+    return out
+
+
+def _diamond_args(p, overrides):
+    o = dict(overrides or {})
+    f64 = lambda k: np.ascontiguousarray(o.get(k, getattr(p, k)), dtype=np.float64)
+    keep = {k: f64(k) for k in ("eps", "q_mean", "q_logstd", "W", "bias", "C", "x")}
+    args = [p.B, int(p.K), int(p.d), int(p.obs), int(p.shared), float(p.prior_var), float(p.obs_var)] + \
+        [_ptr(keep[k]) for k in ("eps", "q_mean", "q_logstd", "W", "bias", "C", "x")]
+    return args, keep
+
+
+def diamond_log_marginal(p, **overrides) -> np.ndarray:
+    """log P_TMC of the loopy graph of Fig. 1 (a workload.Diamond) by its two matrix messages."""
+    lib = _load()
+    args, keep = _diamond_args(p, overrides)
+    out = np.zeros(p.B)
+    _check(lib.tmc_oracle_diamond_log_marginal(*args, _ptr(out)), "diamond_log_marginal")
+    return out
+
+
+def diamond_brute_force(p, max_combos: int = 2_000_000, **overrides) -> np.ndarray:
+    lib = _load()
+    args, keep = _diamond_args(p, overrides)
+    out = np.zeros(p.B)
+    _check(lib.tmc_oracle_diamond_brute_force(*args, ctypes.c_longlong(max_combos), _ptr(out)),
+           "diamond_brute_force")
     return out
 
 

@@ -63,6 +63,20 @@ int tmc_oracle_brute_force(int B, const int* n, const int* parent, const int* K,
                            const double* C, const double* x, long long max_combos,
                            double* log_phat);
 
+/* The loopy graph of Fig. 1 (z1 -> z2, z1 -> z3, {z2, z3} -> z4 -> x), K samples of every
+ * latent, all of dimension d; see tmc_oracle_loopy.c for the model and layouts.  log P_TMC by
+ * summing out k4 and k1 (two matrix messages over (k2, k3)), or by enumerating all K^4
+ * combinations (TMC_ORACLE_TOO_BIG above max_combos). */
+int tmc_oracle_diamond_log_marginal(int B, int K, int d, int obs, int shared, double prior_var,
+                                    double obs_var, const double* eps, const double* q_mean,
+                                    const double* q_logstd, const double* W, const double* bias,
+                                    const double* C, const double* x, double* log_phat);
+int tmc_oracle_diamond_brute_force(int B, int K, int d, int obs, int shared, double prior_var,
+                                   double obs_var, const double* eps, const double* q_mean,
+                                   const double* q_logstd, const double* W, const double* bias,
+                                   const double* C, const double* x, long long max_combos,
+                                   double* log_phat);
+
 #ifdef __cplusplus
 }
 #endif

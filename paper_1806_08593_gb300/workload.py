@@ -489,3 +489,113 @@ def redraw_eps(p: Problem, seed: int) -> np.ndarray:
     """Fresh proposal noise for the same model/x/proposal (used for unbiasedness checks)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.standard_normal(p.eps.shape, dtype=np.float32)
+
+
+# ---------------------------------------------------------------------------------------
+# The loopy graph of Fig. 1: z1 -> z2, z1 -> z3, {z2, z3} -> z4 -> x.
+# ---------------------------------------------------------------------------------------
+@dataclass
+class Diamond:
+    """B instances of the Fig. 1 model, K samples of each of its four latents (dimension d).
+    Layouts: eps [B][4][K][d], q_mean / q_logstd [B][4][d], W [5][d][d] (W_1: z2|z1,
+    W_2: z3|z1, W_3 and W_4: z4|z2 and z4|z3; W_0 unused), bias [4][d], C [obs][d], x [B][obs];
+    W, bias, C once when shared, else per instance."""
+
+    B: int
+    K: int
+    d: int
+    obs: int
+    shared: bool
+    prior_var: float
+    obs_var: float
+    eps: np.ndarray
+    q_mean: np.ndarray
+    q_logstd: np.ndarray
+    W: np.ndarray
+    bias: np.ndarray
+    C: np.ndarray
+    x: np.ndarray
+    name: str = ""
+
+    def entries(self) -> int:
+        """Factor entries formed per call: the two matrix messages (K^3 each) and the K^2
+        final sum, per instance."""
+        return int(self.B * (2 * self.K ** 3 + self.K ** 2))
+
+    def instance(self, b):
+        d, obs = self.d, self.obs
+        W = self.W.reshape(-1, 5, d, d)[0 if self.shared else b].astype(np.float64)
+        bias = self.bias.reshape(-1, 4, d)[0 if self.shared else b].astype(np.float64)
+        C = self.C.reshape(-1, obs, d)[0 if self.shared else b].astype(np.float64)
+        return W, bias, C, self.x.reshape(self.B, obs)[b].astype(np.float64)
+
+
+def _diamond_model(rng, d, obs, orth_C=False):
+    W = np.zeros((5, d, d))
+    W[1] = rng.standard_normal((d, d)) / np.sqrt(d)
+    W[2] = rng.standard_normal((d, d)) / np.sqrt(d)
+    W[3] = rng.standard_normal((d, d)) / np.sqrt(2 * d)  # two parents: input variance 2d
+    W[4] = rng.standard_normal((d, d)) / np.sqrt(2 * d)
+    bias = np.zeros((4, d))
+    bias[1:] = rng.standard_normal((3, d))
+    C = rng.standard_normal((obs, d)) / np.sqrt(d)
+    if orth_C:
+        q, _ = np.linalg.qr(C)
+        C = q * rng.uniform(0.5, 1.5, size=d)
+    return W, bias, C
+
+
+def diamond_joint(W, bias, prior_var):
+    """Mean and covariance of (z1, z2, z3, z4) under the Fig. 1 model: z = A z + bias + noise."""
+    d = W.shape[1]
+    A = np.zeros((4 * d, 4 * d))
+    blk = lambda i: slice(i * d, (i + 1) * d)
+    A[blk(1), blk(0)] = W[1]
+    A[blk(2), blk(0)] = W[2]
+    A[blk(3), blk(1)] = W[3]
+    A[blk(3), blk(2)] = W[4]
+    Minv = np.linalg.inv(np.eye(4 * d) - A)
+    return Minv @ bias.ravel(), prior_var * Minv @ Minv.T, A
+
+
+def make_diamond(K, d, obs, B, seed, shared=True, prior_var=1.0, obs_var=0.1, exact_proposal=False,
+                 zero_W=False, orth_C=False, mean_noise=0.5, std_scale=1.2) -> Diamond:
+    """Seeded instances of the Fig. 1 model; the proposal is placed from the exact posterior
+    marginals (+ N(0, mean_noise^2) mean offset, std_scale x the std), as for the trees."""
+    base = np.random.PCG64(seed)
+    mrng = np.random.Generator(base)
+    models = []
+    for b in range(1 if shared else B):
+        W, bias, C = _diamond_model(mrng if shared else np.random.Generator(base.jumped(1000 + b)), d, obs, orth_C)
+        if zero_W:
+            W[:] = 0.0
+        models.append((W, bias, C))
+    eps_l, m_l, ls_l, x_l = [], [], [], []
+    for b in range(B):
+        rng = np.random.Generator(base.jumped(b + 1))
+        W, bias, C = models[0 if shared else b]
+        mu0, S0, A = diamond_joint(W, bias, prior_var)
+        z = rng.multivariate_normal(mu0, S0)
+        x = C @ z[3 * d:] + np.sqrt(obs_var) * rng.standard_normal(obs)
+        # exact posterior of (z1..z4) given x (information form)
+        P0 = (np.eye(4 * d) - A).T @ (np.eye(4 * d) - A) / prior_var
+        Lam = P0.copy()
+        Lam[3 * d:, 3 * d:] += C.T @ C / obs_var
+        h = P0 @ mu0
+        h[3 * d:] += C.T @ x / obs_var
+        cf = sla.cho_factor(Lam, lower=True)
+        pm = sla.cho_solve(cf, h)
+        ps = np.sqrt(np.diag(sla.cho_solve(cf, np.eye(4 * d))))
+        if exact_proposal:
+            m, s = pm, ps
+        else:
+            m = pm + mean_noise * rng.standard_normal(4 * d)
+            s = std_scale * ps
+        eps_l.append(rng.standard_normal((4, K, d), dtype=np.float32).ravel())
+        m_l.append(m); ls_l.append(np.log(s)); x_l.append(x)
+    f32 = lambda lst: np.ascontiguousarray(np.concatenate([np.ravel(a) for a in lst]).astype(np.float32))
+    return Diamond(B=B, K=K, d=d, obs=obs, shared=bool(shared), prior_var=float(prior_var),
+                   obs_var=float(obs_var), eps=f32(eps_l), q_mean=f32(m_l), q_logstd=f32(ls_l),
+                   W=f32([m[0] for m in models]), bias=f32([m[1] for m in models]),
+                   C=f32([m[2] for m in models]), x=f32(x_l),
+                   name="diamond_K%d_d%d_B%d" % (K, d, B))
