@@ -107,7 +107,14 @@ static void dia_prepare(dia_t* I) {
 static double dia_eliminate(const dia_t* I) {
   const int K = I->K, d = I->d;
   double* M = (double*)malloc(sizeof(double) * (size_t)K * K);
-  int k2;
+  /* the conditional means of z2 and z3 given z1^k1 depend on k1 alone: computed once */
+  double* mu2 = (double*)malloc(sizeof(double) * (size_t)K * d);
+  double* mu3 = (double*)malloc(sizeof(double) * (size_t)K * d);
+  int k2, k;
+  for (k = 0; k < K; ++k) {
+    affine(I, 1, DZ(I, 0, k), 0, NULL, 1, mu2 + (long long)k * d);
+    affine(I, 2, DZ(I, 0, k), 0, NULL, 2, mu3 + (long long)k * d);
+  }
 #pragma omp parallel for schedule(static)
   for (k2 = 0; k2 < K; ++k2) {
     double* t = (double*)malloc(sizeof(double) * K);
@@ -120,10 +127,8 @@ static double dia_eliminate(const dia_t* I) {
       m4 = lse(t, K) - log((double)K);
       for (k1 = 0; k1 < K; ++k1) {
         double v = I->u[k1];
-        affine(I, 1, DZ(I, 0, k1), 0, NULL, 1, mu);
-        v += lnorm(DZ(I, 1, k2), mu, d, I->pv);
-        affine(I, 2, DZ(I, 0, k1), 0, NULL, 2, mu);
-        v += lnorm(DZ(I, 2, k3), mu, d, I->pv);
+        v += lnorm(DZ(I, 1, k2), mu2 + (long long)k1 * d, d, I->pv);
+        v += lnorm(DZ(I, 2, k3), mu3 + (long long)k1 * d, d, I->pv);
         t[k1] = v;
       }
       m1 = lse(t, K) - log((double)K);
@@ -135,6 +140,8 @@ static double dia_eliminate(const dia_t* I) {
   {
     double r = lse(M, (long long)K * K) - 2.0 * log((double)K);
     free(M);
+    free(mu2);
+    free(mu3);
     return r;
   }
 }
