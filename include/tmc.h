@@ -241,6 +241,53 @@ tmc_status tmc_profile_enable(tmc_plan plan, int enable);
 tmc_status tmc_profile_read(tmc_plan plan, int kernel_class, double* total_ms,
                             long long* launches);
 
+/* ---- the loopy graph of Fig. 1: matrix messages (Section 2.2) ---------------------------
+ * Four latents of dimension d, K samples each, where z4 has two parents that share the parent
+ * z1 (a loop in the undirected graph):
+ *   z1 ~ N(bias_0, prior_var I),  z2 | z1 ~ N(W_1 z1 + bias_1, prior_var I),
+ *   z3 | z1 ~ N(W_2 z1 + bias_2, prior_var I),  z4 | z2, z3 ~ N(W_3 z2 + W_4 z3 + bias_3, prior_var I),
+ *   x | z4 ~ N(C z4, obs_var I);   Q_i = N(m_i, diag(exp(2 logs_i))) (factorised).
+ * Summing out k4 and then k1 (Fig. 1 C, D) leaves two factors over (k2, k3), each a log-domain
+ * matrix product of K x K factor matrices (the Appendix's "Numerically stable matrix (tensor)
+ * products"); log P_TMC is the log-mean-exp of their sum with the (k2, k3) factor.
+ * Inputs (tmc_inputs, DEVICE float32; q_A unused):
+ *   eps [B][4][K][d], q_mean / q_logstd [B][4][d], W [5][d][d] per instance (W_0 unused),
+ *   bias [4][d] per instance, C [obs][d] per instance (one instance's when shared), x [B][obs].
+ * Arithmetic: factor matrices from split fp16 operands on tcgen05 tensor cores (as
+ * TMC_PREC_FP16_TC), the matrix products exp(X - x) exp(Y - y)^T of the messages from bf16
+ * exponentials on tcgen05 (split pairs or single, see message_precision; FP32 range), entries
+ * whose sum underflows recomputed exactly; FP64 final reduction.
+ * Limits: d <= 128, obs_dim <= 1024, K <= 16384 (TMC_ERR_UNSUPPORTED beyond). */
+typedef struct tmc_loopy_plan_s* tmc_loopy_plan;
+typedef struct {
+  int32_t num_instances; /* B >= 1                                                         */
+  int32_t K;             /* samples per latent                                             */
+  int32_t d;             /* latent dimension                                               */
+  int32_t obs_dim;       /* observation dimension                                          */
+  int32_t shared_params; /* 1: one W, bias, C for all instances                            */
+  double prior_var, obs_var;
+  int32_t message_precision; /* operands exp(X - x), exp(Y - y) of the two message products:
+                                0 split bf16 pairs (hi*hi + lo*hi + hi*lo, ~16 bits, 3 MMAs);
+                                1 single bf16 (1 MMA; each product within 2^-8 relative, so
+                                each message entry within 3.9e-3 nats, log P_TMC within
+                                7.8e-3)                                                      */
+} tmc_loopy_desc;
+
+/* Allocates the plan and its device workspace (about B (10 K^2 + 24 K d) * 4 bytes).
+ * Errors: TMC_ERR_INVALID_ARG, TMC_ERR_UNSUPPORTED, TMC_ERR_NOMEM, TMC_ERR_CUDA. */
+tmc_status tmc_loopy_plan_create(const tmc_loopy_desc* desc, tmc_loopy_plan* out);
+/* Enqueues log P_TMC[b] (DEVICE double[B]) on `stream`; returns without synchronising. */
+tmc_status tmc_loopy_log_marginal(tmc_loopy_plan plan, const tmc_inputs* in, double* log_phat,
+                                  void* stream);
+/* Synchronises; returns (HOST, each may be NULL) the summed device time of the factor stage
+ * and of the message stage since the last call, the forward calls timed, and the number of
+ * message entries recomputed exactly; then turns stage timing on (enable = 1) or off and
+ * resets the counters.  TMC_ERR_TIMEOUT if a bounded device wait gave up since the last call. */
+tmc_status tmc_loopy_profile(tmc_loopy_plan plan, int enable, double* factor_ms,
+                             double* message_ms, long long* calls, int* exact_entries);
+/* Releases the plan (synchronises the device first).  NULL is a no-op. */
+tmc_status tmc_loopy_plan_destroy(tmc_loopy_plan plan);
+
 #ifdef __cplusplus
 }
 #endif

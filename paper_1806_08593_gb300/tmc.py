@@ -27,7 +27,8 @@ EXPORTS = ["tmc_plan_create", "tmc_log_marginal", "tmc_backward", "tmc_plan_sync
            "tmc_plan_workspace_bytes", "tmc_plan_destroy", "tmc_status_string",
            "tmc_profile_enable", "tmc_profile_read", "tmc_log_marginal_noalloc",
            "tmc_plan_instance_times", "tmc_plan_set_schedule", "tmc_plan_get_schedule",
-           "tmc_plan_set_wait_limit"]
+           "tmc_plan_set_wait_limit", "tmc_loopy_plan_create", "tmc_loopy_log_marginal",
+           "tmc_loopy_profile", "tmc_loopy_plan_destroy"]
 
 
 class TMCError(RuntimeError):
@@ -43,6 +44,13 @@ class ProblemDesc(ctypes.Structure):
                 ("prior_var", ctypes.c_double), ("obs_var", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("K_node", ctypes.c_void_p), ("d_node", ctypes.c_void_p),
                 ("coupled_proposal", ctypes.c_int32)]
+
+
+class LoopyDesc(ctypes.Structure):
+    _fields_ = [("num_instances", ctypes.c_int32), ("K", ctypes.c_int32), ("d", ctypes.c_int32),
+                ("obs_dim", ctypes.c_int32), ("shared_params", ctypes.c_int32),
+                ("prior_var", ctypes.c_double), ("obs_var", ctypes.c_double),
+                ("message_precision", ctypes.c_int32)]
 
 
 class Inputs(ctypes.Structure):
@@ -89,6 +97,14 @@ def load_library(path: str = LIB_PATH):
     lib.tmc_plan_get_schedule.restype = ctypes.c_int
     lib.tmc_plan_set_wait_limit.argtypes = [P, ctypes.c_longlong]
     lib.tmc_plan_set_wait_limit.restype = ctypes.c_int
+    lib.tmc_loopy_plan_create.argtypes = [ctypes.POINTER(LoopyDesc), ctypes.POINTER(P)]
+    lib.tmc_loopy_log_marginal.argtypes = [P, ctypes.POINTER(Inputs), P, V]
+    lib.tmc_loopy_profile.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(ctypes.c_int)]
+    lib.tmc_loopy_plan_destroy.argtypes = [P]
+    for f in ("tmc_loopy_plan_create", "tmc_loopy_log_marginal", "tmc_loopy_profile", "tmc_loopy_plan_destroy"):
+        getattr(lib, f).restype = ctypes.c_int
     for f in ("tmc_plan_create", "tmc_log_marginal", "tmc_backward", "tmc_plan_sync_status",
               "tmc_plan_workspace_bytes", "tmc_plan_destroy", "tmc_profile_enable", "tmc_profile_read",
               "tmc_log_marginal_noalloc"):
@@ -231,6 +247,59 @@ class Plan:
                    "tmc_profile_read")
             res[name] = (ms.value, n.value)
         return res
+
+
+class LoopyPlan:
+    """Owns a tmc_loopy_plan: log P_TMC of the loopy graph of Fig. 1 (two matrix messages)."""
+
+    MESSAGE_PRECISIONS = {"bf16x2": 0, "bf16": 1}
+
+    def __init__(self, B: int, K: int, d: int, obs: int, shared: bool, prior_var: float, obs_var: float,
+                 message_precision: str = "bf16x2"):
+        lib = load_library()
+        desc = LoopyDesc(int(B), int(K), int(d), int(obs), int(bool(shared)), float(prior_var), float(obs_var),
+                         self.MESSAGE_PRECISIONS[message_precision])
+        h = ctypes.c_void_p()
+        _check(lib.tmc_loopy_plan_create(ctypes.byref(desc), ctypes.byref(h)), "tmc_loopy_plan_create")
+        self._h, self._lib, self.B = h, lib, int(B)
+
+    @classmethod
+    def from_problem(cls, p, message_precision: str = "bf16x2") -> "LoopyPlan":
+        return cls(p.B, p.K, p.d, p.obs, p.shared, p.prior_var, p.obs_var, message_precision)
+
+    @staticmethod
+    def to_device(p, device="cuda") -> dict:
+        import torch
+        return {k: torch.from_numpy(np.ascontiguousarray(getattr(p, k), dtype=np.float32)).to(device)
+                for k in ("eps", "q_mean", "q_logstd", "W", "bias", "C", "x")}
+
+    def forward(self, t: dict, out=None, stream=None):
+        """log P_TMC per instance (float64 CUDA tensor [B])."""
+        import torch
+        if out is None:
+            out = torch.empty(self.B, dtype=torch.float64, device=t["eps"].device)
+        inp = Inputs(*[_ptr(t.get(k)) for k in INPUT_NAMES])
+        _check(self._lib.tmc_loopy_log_marginal(self._h, ctypes.byref(inp), _ptr(out), _stream(stream)),
+               "tmc_loopy_log_marginal")
+        return out
+
+    def profile(self, enable: bool = True) -> dict:
+        """Stage times since the last call (ms), forward calls timed, exactly recomputed entries."""
+        f, m, n, e = ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong(), ctypes.c_int()
+        _check(self._lib.tmc_loopy_profile(self._h, int(enable), ctypes.byref(f), ctypes.byref(m),
+                                           ctypes.byref(n), ctypes.byref(e)), "tmc_loopy_profile")
+        return dict(factor_ms=f.value, message_ms=m.value, calls=n.value, exact_entries=e.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.tmc_loopy_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def log_marginal_noalloc(p, t: dict, out=None, stream=None):
