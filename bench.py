@@ -230,6 +230,106 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------------------
+# kernel launches of one step, counted by the CUDA profiler (every kernel of the process:
+# the library's, and torch's if any ran)
+# ---------------------------------------------------------------------------------------
+def count_kernel_launches(fn, dev):
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+    torch.cuda.synchronize(dev)
+    for _ in range(2):  # the first session of a process can come back empty: keep the second
+        with profile(activities=[ProfilerActivity.CUDA]) as pr:
+            fn()
+            torch.cuda.synchronize(dev)
+    names = [e.name for e in pr.events()
+             if str(getattr(e, "device_type", "")).endswith("CUDA") and "Memset" not in e.name
+             and "Memcpy" not in e.name]
+    return len(names), sorted(set(names))
+
+
+# ---------------------------------------------------------------------------------------
+# the loopy graph of Fig. 1 (two matrix messages): forward log P per instance
+# ---------------------------------------------------------------------------------------
+LOOPY = dict(K=4096, d=128, obs=128, B=4)
+
+
+def loopy_leg(args, dev):
+    """The Fig. 1 graph at K=4096, d=128: log P_TMC of B instances per step.  Unit: message
+    terms, 2 K^3 per instance (the (k2, k3, k4) and (k2, k3, k1) terms the two matrix messages
+    sum).  Both message precisions are timed; single bf16 is the headline (its |delta log P|
+    bound, 7.8e-3, is within the 2e-2 reduced-precision tolerance)."""
+    import torch
+    from paper_1806_08593_gb300 import workload as wl
+    from paper_1806_08593_gb300.tmc import LoopyPlan
+    c = LOOPY
+    p = wl.make_diamond(c["K"], c["d"], c["obs"], c["B"], seed=1, shared=True)
+    terms = 2.0 * p.K ** 3 * p.B
+    msg_flops = 4.0 * p.K ** 3 * p.B          # two K x K x K products per instance
+    fac_flops = 10.0 * p.K ** 2 * p.d * p.B   # five K x K x d products per instance
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for mp in ("bf16", "bf16x2"):
+        plan = LoopyPlan.from_problem(p, mp)
+        t = plan.to_device(p, dev)
+        out = torch.empty(p.B, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            plan.forward(t, out=out)
+        torch.cuda.synchronize(dev)
+        steps = max(3, args.steps // 5)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            plan.forward(t, out=out)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = ev0.elapsed_time(ev1) / steps
+        plan.profile(True)
+        for _ in range(steps):
+            plan.forward(t, out=out)
+        pr = plan.profile(False)
+        st = {k: v / pr["calls"] for k, v in pr["stage_ms"].items()}
+        launches, _ = count_kernel_launches(lambda: plan.forward(t, out=out), dev)
+        res[mp] = {"ms_per_step": ms, "value": terms / (ms * 1e-3), "stage_ms": st,
+                   "exact_entries_per_step": pr["exact_entries"] / max(1, pr["calls"]),
+                   "message_tflops": msg_flops / (st["message"] * 1e-3) / 1e12,
+                   "factor_tflops": fac_flops / (st["factor"] * 1e-3) / 1e12,
+                   "gpu_launches_per_step": launches, "logp": out.cpu().numpy().tolist()}
+        plan.close()
+        del t
+    peaks, src = load_peaks()
+    head = res["bf16"]
+    peak = peaks["bf16_tflops"]
+    line = {"workload": "diamond_K%d_d%d_obs%d_B%d" % (p.K, p.d, p.obs, p.B),
+            "metric": "loopy_message_terms_per_s", "unit": "terms/s", "value": head["value"],
+            "ms_per_step": head["ms_per_step"], "message_precision": "bf16",
+            "max_abs_dlogp_bf16_vs_bf16x2": float(np.max(np.abs(np.array(head["logp"]) -
+                                                                np.array(res["bf16x2"]["logp"])))),
+            "roofline": {"bound": "tensor", "kernel": "k_gemm_split<1,256> (both messages)",
+                         "achieved": head["message_tflops"], "peak": peak, "unit": "TFLOP/s",
+                         "frac": head["message_tflops"] / peak, "traffic": None,
+                         "peak_source": "bf16_tflops (%s)" % src,
+                         "flops_per_launch": msg_flops},
+            "split": res["bf16x2"], "single": res["bf16"]}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        Ks = 256
+        q = wl.make_diamond(Ks, c["d"], c["obs"], 1, seed=1, shared=True)
+        t0 = time.perf_counter()
+        n = 0
+        while True:
+            oracle.diamond_log_marginal(q)
+            n += 1
+            if time.perf_counter() - t0 >= min(10.0, args.cpu_seconds):
+                break
+        dt = (time.perf_counter() - t0) / n
+        line["cpu_baseline"] = {"value": 2.0 * Ks ** 3 / dt, "unit": "terms/s", "cores": oracle_cores(),
+                                "kind": "oracle",
+                                "sample": "1 instance at K=%d (d=%d, obs=%d), %d runs, FP64" % (Ks, c["d"], c["obs"], n)}
+    return line
+
+
+# ---------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------
 def algorithmic_flops(p, precision):
@@ -474,7 +574,15 @@ def run_ours(args):
         roof = {"bound": "tensor", "achieved": achieved / 1e12, "peak": peak / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                 "peak_source": "bf16_tflops (%s)" % src}
-    total_launches = int(sum(v[1] for v in prof.values()))
+    lib_launches = int(sum(v[1] for v in prof.values()))
+    try:
+        per_step, kernel_names = count_kernel_launches(step, dev)
+        total_launches = per_step * args.steps
+        launch_src = "CUDA profiler, one step x steps (%d kernels per step, %d distinct)" % (
+            per_step, len(kernel_names))
+    except Exception as exc:  # profiler unavailable: the library's own count of timed calls
+        total_launches, kernel_names = lib_launches, []
+        launch_src = "library timing wrappers (profiler unavailable: %s)" % type(exc).__name__
 
     # ---- the same step on the FP32 CUDA-core path, and the log P agreement ------------
     fp32 = None
@@ -528,6 +636,11 @@ def run_ours(args):
                    "factor_bytes_written": 4 * p.edge_entries(),
                    "max_abs_dlogp_unfused_vs_fused": float(np.max(np.abs(lp_u - lp_f)))}
 
+    # ---- the loopy graph of Fig. 1 (matrix messages) ----------------------------------
+    loopy = None
+    if not args.no_loopy and ws == 1:
+        loopy = loopy_leg(args, dev)
+
     # ---- CPU baseline (oracle on a bounded sample) ------------------------------------
     cpu = None
     vs_oracle = None
@@ -564,8 +677,11 @@ def run_ours(args):
         "sample_grads": sample_grads,
         "instance_latency": latency,
         "gpu_launches": total_launches,
+        "gpu_launches_source": launch_src,
+        "kernels": kernel_names,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "clocks": clk.summary(),
+        "loopy": loopy,
     }
     print(json.dumps(line))
 
@@ -591,6 +707,8 @@ def main():
     ap.add_argument("--no-sample-grads", action="store_true",
                     help="skip the extra timing of the step with the per-sample gradients dz, deps")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-loopy", action="store_true",
+                    help="skip the loopy-graph (Fig. 1, matrix messages) leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

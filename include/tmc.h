@@ -279,12 +279,22 @@ tmc_status tmc_loopy_plan_create(const tmc_loopy_desc* desc, tmc_loopy_plan* out
 /* Enqueues log P_TMC[b] (DEVICE double[B]) on `stream`; returns without synchronising. */
 tmc_status tmc_loopy_log_marginal(tmc_loopy_plan plan, const tmc_inputs* in, double* log_phat,
                                   void* stream);
-/* Synchronises; returns (HOST, each may be NULL) the summed device time of the factor stage
- * and of the message stage since the last call, the forward calls timed, and the number of
- * message entries recomputed exactly; then turns stage timing on (enable = 1) or off and
- * resets the counters.  TMC_ERR_TIMEOUT if a bounded device wait gave up since the last call. */
-tmc_status tmc_loopy_profile(tmc_loopy_plan plan, int enable, double* factor_ms,
-                             double* message_ms, long long* calls, int* exact_entries);
+/* Stages of tmc_loopy_log_marginal, in launch order. */
+enum {
+  TMC_LOOPY_PREP = 0,    /* samples, node terms, projections, split fp16 operands            */
+  TMC_LOOPY_FACTOR = 1,  /* the five K x K factor matrices (one tensor-core launch)          */
+  TMC_LOOPY_EXP = 2,     /* row maxima and bf16 exponentials of the message operands          */
+  TMC_LOOPY_MESSAGE = 3, /* the two log-domain matrix products (one tensor-core launch)      */
+  TMC_LOOPY_FINAL = 4,   /* the (k2, k3) sum, exact recomputation of underflowed entries     */
+  TMC_LOOPY_STAGE_COUNT = 5
+};
+/* Synchronises; returns (HOST, each may be NULL) the summed device time (ms) of every stage
+ * since the last call (stage_ms: double[TMC_LOOPY_STAGE_COUNT]), the forward calls timed, and
+ * the number of message entries recomputed exactly; then turns stage timing on (enable = 1)
+ * or off and resets the counters.  Timing synchronises each timed call.  TMC_ERR_TIMEOUT if a
+ * bounded device wait gave up since the last call. */
+tmc_status tmc_loopy_profile(tmc_loopy_plan plan, int enable, double* stage_ms, long long* calls,
+                             int* exact_entries);
 /* Releases the plan (synchronises the device first).  NULL is a no-op. */
 tmc_status tmc_loopy_plan_destroy(tmc_loopy_plan plan);
 

@@ -274,24 +274,47 @@ __global__ void __launch_bounds__(256) k_dia_split16(LDev L) {
 // a product now underflows only where the two exponents sum below -(87 + 2 kExpShift).
 // Grid: (instance, matrix, 8-row group); one warp per row.
 constexpr float kExpShift = 38.f;
+__device__ __forceinline__ uint32_t pack_bf2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
 __global__ void __launch_bounds__(256) k_dia_expsplit(LDev L) {
   const int b = blockIdx.x, mi = blockIdx.y, K = L.K, Kp = L.Kp;
   const int fi = mi;  // X4, Y4, X1, Y1 are factor matrices 0..3
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = blockIdx.z * 8 + w;
   if (k >= K) return;
+  // rows are Kp floats (a multiple of 64): 8-column chunks are 32-byte aligned; columns >= K
+  // of the factor rows are padding (read but masked)
   const float* row = L.fac + (((long long)b * 5 + fi) * K + k) * Kp;
   float mx = -INFINITY;
-  for (int j = lane; j < K; j += 32) mx = fmaxf(mx, row[j]);
+  for (int j = lane * 8; j < K; j += 256) {
+    const float4 u0 = *reinterpret_cast<const float4*>(row + j);
+    const float4 u1 = *reinterpret_cast<const float4*>(row + j + 4);
+    const float e[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+      if (j + x < K) mx = fmaxf(mx, e[x]);
+  }
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   const float r = mx - kExpShift;
   __nv_bfloat16* eh = L.eh + (((long long)b * 4 + mi) * K + k) * Kp;
   __nv_bfloat16* el = L.el + (((long long)b * 4 + mi) * K + k) * Kp;
-  for (int j = lane; j < Kp; j += 32) {
-    const float v = j < K ? __expf(row[j] - r) : 0.f;
-    const __nv_bfloat16 hb = __float2bfloat16_rn(v);
-    eh[j] = hb;
-    el[j] = __float2bfloat16_rn(v - __bfloat162float(hb));
+  for (int j = lane * 8; j < Kp; j += 256) {
+    const float4 u0 = *reinterpret_cast<const float4*>(row + j);
+    const float4 u1 = *reinterpret_cast<const float4*>(row + j + 4);
+    const float e[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+    float v[8], lo[8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      v[x] = j + x < K ? __expf(e[x] - r) : 0.f;
+      lo[x] = v[x] - __bfloat162float(__float2bfloat16_rn(v[x]));
+    }
+    *reinterpret_cast<uint4*>(eh + j) =
+        make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]), pack_bf2(v[6], v[7]));
+    if (L.msplit)
+      *reinterpret_cast<uint4*>(el + j) =
+          make_uint4(pack_bf2(lo[0], lo[1]), pack_bf2(lo[2], lo[3]), pack_bf2(lo[4], lo[5]), pack_bf2(lo[6], lo[7]));
   }
   if (lane == 0) L.rmax[((long long)b * 4 + mi) * K + k] = r;
 }
@@ -331,8 +354,14 @@ struct GemmArgs {
 constexpr int kGemmThreads = 320;                          // TMA warp, MMA warp, 8 epilogue warps
 constexpr int kEpiWarps = 8;
 constexpr int kStgBytes = 32 * 32 * 4;                     // one 32 x 32 fp32 block
-constexpr size_t kLRing = (size_t)kLNS * kLStage;          // 192 KB either way
-constexpr size_t kLSmem = 1024 + kLRing + (size_t)kEpiWarps * kStgBytes;
+// Shared memory per mode: the factor GEMM (2 slices per tile, epilogue-bound) keeps a 2-stage
+// ring and two staging blocks per epilogue warp, so one block's TMA store overlaps the next
+// block's math; the message GEMM keeps a 192 KB ring and one staging block per warp.
+__host__ __device__ constexpr size_t ring_bytes(int mode) { return mode == 0 ? 2 * (size_t)kLStage : (size_t)kLNS * kLStage; }
+__host__ __device__ constexpr int stg_bufs(int mode) { return mode == 0 ? 2 : 1; }
+__host__ __device__ constexpr size_t gemm_smem(int mode) {
+  return 1024 + ring_bytes(mode) + (size_t)kEpiWarps * stg_bufs(mode) * kStgBytes;
+}
 constexpr float kLn2 = 0.693147180559945309f;
 
 __device__ __forceinline__ void tile_of(const GemmArgs& g, int bn, int t, int& z, int& m, int& ti, int& tk) {
@@ -369,7 +398,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_split(GemmArgs g, int*
   constexpr int kBBox = kLBox * BN / 128;
   const int shalf = kLBox + kBBox;
   const int sstride = g.split ? 2 * shalf : shalf;
-  const int nst = (int)(kLRing / sstride);  // 3 or 6 stages (BN = 128), 2 or 4 (BN = 256)
+  constexpr size_t kRing = ring_bytes(MODE);
+  const int nst = (int)(kRing / sstride);  // messages: 3 or 6 stages (BN = 128), 2 or 4 (BN = 256)
   const int nti = (g.M + 127) >> 7, ntk = (g.N + BN - 1) / BN;
   const int total = nti * ntk * g.items * g.nmat;
   if (warp == 1) tmem_alloc(&tbase, 2 * BN);
@@ -458,7 +488,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_split(GemmArgs g, int*
     }
   } else {
     const int e = warp - 2, q = warp & 3, h = e >> 2;  // lane quarter q, column half h
-    unsigned char* stg = ring + kLRing + e * kStgBytes;   // 1024-byte aligned
+    constexpr int kBufs = stg_bufs(MODE);
+    unsigned char* stg_base = ring + kRing + e * kBufs * kStgBytes;  // 1024-byte aligned
+    int nstore = 0;  // TMA stores issued by this warp
     int tl = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++tl) {
       const int buf = tl & 1, use = tl >> 1;
@@ -483,9 +515,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_split(GemmArgs g, int*
         tmem_ld32(tmem + buf * BN + ((uint32_t)(q * 32) << 16) + grp * 32, v);
         const float ctl = (has_ct && k0 + lane < g.N) ? tz[g.ct_off[m] + k0 + lane] : 0.f;
         tmem_wait_ld();
-        if (gg > 0 || tl > 0) {
-          // the previous TMA store from this buffer has read it
-          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        unsigned char* stg = stg_base + (nstore % kBufs) * kStgBytes;
+        if (nstore >= kBufs) {
+          // the TMA store that last used this buffer has read it
+          if (lane == 0) {
+            if (kBufs == 2) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+            else asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+          }
           __syncwarp();
         }
 #pragma unroll
@@ -508,6 +544,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_split(GemmArgs g, int*
           tma_store_3d(&mOut, stg, k0, ti * 128 + q * 32, z * g.out_zmul + g.out_off[m]);
           bulk_commit_group();
         }
+        ++nstore;
       }
       // the accumulator buffer is drained: the MMA warp may reuse it
       tc_fence_before();
@@ -537,33 +574,52 @@ __device__ __noinline__ float exact_lse(const float* __restrict__ X, const float
 // writes the (max, sum exp(v - max)) of its chunk.  Message entries whose tensor-core sum
 // underflowed (-inf) are recomputed here from the factor rows (rare).  Grid: (chunk, instance).
 constexpr int kFinalRows = 8;
+__device__ __forceinline__ void lse_add(float& m, float& s, float v) {
+  if (v > m) {
+    s = s * __expf(m - v) + 1.f;
+    m = v;
+  } else {
+    s += __expf(v - m);
+  }
+}
 __global__ void __launch_bounds__(256) k_dia_final(LDev L) {
   __shared__ float sm_m[8], sm_s[8];
   const int b = blockIdx.y, K = L.K, Kp = L.Kp;
   const long long mat = (long long)K * Kp;
   const float* P = L.fac + ((long long)b * 5 + 4) * mat;
-  float* L4 = L.msg + ((long long)b * 2 + 0) * mat;
-  float* L1 = L.msg + ((long long)b * 2 + 1) * mat;
+  const float* L4 = L.msg + ((long long)b * 2 + 0) * mat;
+  const float* L1 = L.msg + ((long long)b * 2 + 1) * mat;
   float m = -INFINITY, s = 0.f;
   const int r0 = blockIdx.x * kFinalRows, r1 = min(K, r0 + kFinalRows);
+  // rows are Kp floats (a multiple of 64): 4-column chunks are 16-byte aligned
+#pragma unroll 2
   for (int r = r0; r < r1; ++r) {
-    for (int c = threadIdx.x; c < K; c += blockDim.x) {
+    for (int c = threadIdx.x * 4; c < K; c += blockDim.x * 4) {
       const long long e = (long long)r * Kp + c;
-      float l4 = L4[e], l1 = L1[e];
-      if (!(l4 > -INFINITY)) {  // underflowed (or, defensively, not a number)
-        l4 = exact_lse(L.fac + (((long long)b * 5 + 0) * K + r) * Kp, L.fac + (((long long)b * 5 + 1) * K + c) * Kp, K);
-        atomicAdd(L.nfix, 1);
-      }
-      if (!(l1 > -INFINITY)) {
-        l1 = exact_lse(L.fac + (((long long)b * 5 + 2) * K + r) * Kp, L.fac + (((long long)b * 5 + 3) * K + c) * Kp, K);
-        atomicAdd(L.nfix, 1);
-      }
-      const float v = P[e] + l4 + l1;
-      if (v > m) {
-        s = s * __expf(m - v) + 1.f;
-        m = v;
-      } else {
-        s += __expf(v - m);
+      const float4 p = *reinterpret_cast<const float4*>(P + e);
+      const float4 a = *reinterpret_cast<const float4*>(L4 + e);
+      const float4 q = *reinterpret_cast<const float4*>(L1 + e);
+      float v[4] = {p.x + a.x + q.x, p.y + a.y + q.y, p.z + a.z + q.z, p.w + a.w + q.w};
+      const float l4[4] = {a.x, a.y, a.z, a.w}, l1[4] = {q.x, q.y, q.z, q.w}, pp[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        if (c + x >= K) continue;
+        if (!(v[x] > -INFINITY)) {
+          // a message entry underflowed (or, defensively, is not a number): recompute it
+          float f4 = l4[x], f1 = l1[x];
+          if (!(f4 > -INFINITY)) {
+            f4 = exact_lse(L.fac + (((long long)b * 5 + 0) * K + r) * Kp,
+                           L.fac + (((long long)b * 5 + 1) * K + c + x) * Kp, K);
+            atomicAdd(L.nfix, 1);
+          }
+          if (!(f1 > -INFINITY)) {
+            f1 = exact_lse(L.fac + (((long long)b * 5 + 2) * K + r) * Kp,
+                           L.fac + (((long long)b * 5 + 3) * K + c + x) * Kp, K);
+            atomicAdd(L.nfix, 1);
+          }
+          v[x] = pp[x] + f4 + f1;
+        }
+        lse_add(m, s, v[x]);
       }
     }
   }
@@ -669,8 +725,8 @@ struct tmc_loopy_plan_s {
   int* d_err = nullptr;
   CUtensorMap mOh, mOl, mEh, mEl, mEh256, mEl256, mFac, mMsg;
   bool prof = false;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  double msg_ms = 0.0, fac_ms = 0.0;
+  cudaEvent_t ev[TMC_LOOPY_STAGE_COUNT + 1] = {};
+  double stage_ms[TMC_LOOPY_STAGE_COUNT] = {};
   int num_sms = 148;
   long long calls = 0;
 };
@@ -736,9 +792,9 @@ tmc_status tmc_loopy_plan_create(const tmc_loopy_desc* ds, tmc_loopy_plan* out) 
     delete p;
     return TMC_ERR_CUDA;
   }
-  cudaFuncSetAttribute(k_gemm_split<0, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLSmem);
-  cudaFuncSetAttribute(k_gemm_split<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLSmem);
-  cudaFuncSetAttribute(k_gemm_split<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLSmem);
+  cudaFuncSetAttribute(k_gemm_split<0, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem(0));
+  cudaFuncSetAttribute(k_gemm_split<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem(1));
+  cudaFuncSetAttribute(k_gemm_split<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem(1));
   for (auto& e : p->ev) cudaEventCreate(&e);
   {
     int dev = 0;
@@ -765,6 +821,7 @@ tmc_status tmc_loopy_log_marginal(tmc_loopy_plan p, const tmc_inputs* in, double
   k_dia_obs<<<dim3(B, tiles64), kThreads, 0, s>>>(L);
   k_dia_terms<<<B, 256, 0, s>>>(L);
   k_dia_split16<<<dim3(B, 7, tiles64), 256, 0, s>>>(L);
+  if (p->prof) cudaEventRecord(p->ev[1], s);
   const int nt = (K + 127) / 128;
   // the five factor matrices in one launch.  Operands (rows of [B][7][K]): 0 z~2, 1 z~3,
   // 2 z~4, 3 mu2~, 4 mu3~, 5 a, 6 c; terms [B][5][K]: beta4, beta1, row2, col3.
@@ -793,10 +850,11 @@ tmc_status tmc_loopy_log_marginal(tmc_loopy_plan p, const tmc_inputs* in, double
       g.out_off[m] = m;
     }
     const int grid = std::min(nt * nt * B * 5, p->num_sms);
-    k_gemm_split<0, 128><<<grid, kGemmThreads, kLSmem, s>>>(g, p->d_err, p->mOh, p->mOl, p->mOh, p->mOl, p->mFac);
+    k_gemm_split<0, 128><<<grid, kGemmThreads, gemm_smem(0), s>>>(g, p->d_err, p->mOh, p->mOl, p->mOh, p->mOl, p->mFac);
   }
-  if (p->prof) cudaEventRecord(p->ev[1], s);
+  if (p->prof) cudaEventRecord(p->ev[2], s);
   k_dia_expsplit<<<dim3(B, 4, (K + 7) / 8), 256, 0, s>>>(L);
+  if (p->prof) cudaEventRecord(p->ev[3], s);
   // the two messages in one launch: L[i][k] = log sum_j exp(X[i][j] + Y[k][j]) for (X4, Y4) and
   // (X1, Y1); terms [B][4][K]: the lowered row maxima of X4, Y4, X1, Y1
   {
@@ -817,46 +875,46 @@ tmc_status tmc_loopy_log_marginal(tmc_loopy_plan p, const tmc_inputs* in, double
     }
     if (K > 128) {  // 128 x 256 tiles: a third fewer operand bytes per flop
       const int grid = std::min(nt * ((K + 255) / 256) * B * 2, p->num_sms);
-      k_gemm_split<1, 256><<<grid, kGemmThreads, kLSmem, s>>>(g, p->d_err, p->mEh, p->mEl, p->mEh256, p->mEl256,
+      k_gemm_split<1, 256><<<grid, kGemmThreads, gemm_smem(1), s>>>(g, p->d_err, p->mEh, p->mEl, p->mEh256, p->mEl256,
                                                               p->mMsg);
     } else {
       const int grid = std::min(nt * nt * B * 2, p->num_sms);
-      k_gemm_split<1, 128><<<grid, kGemmThreads, kLSmem, s>>>(g, p->d_err, p->mEh, p->mEl, p->mEh, p->mEl, p->mMsg);
+      k_gemm_split<1, 128><<<grid, kGemmThreads, gemm_smem(1), s>>>(g, p->d_err, p->mEh, p->mEl, p->mEh, p->mEl, p->mMsg);
     }
   }
-  if (p->prof) cudaEventRecord(p->ev[2], s);
+  if (p->prof) cudaEventRecord(p->ev[4], s);
   const int nchunks = (K + kFinalRows - 1) / kFinalRows;
   k_dia_final<<<dim3(nchunks, B), 256, 0, s>>>(L);
   k_dia_combine<<<B, 256, 0, s>>>(L, nchunks);
-  if (p->prof) cudaEventRecord(p->ev[3], s);
+  if (p->prof) cudaEventRecord(p->ev[5], s);
   if (cudaGetLastError() != cudaSuccess) return TMC_ERR_CUDA;
   if (p->prof) {
-    float a = 0.f, b = 0.f;
-    if (cudaEventSynchronize(p->ev[3]) != cudaSuccess) return TMC_ERR_CUDA;
-    cudaEventElapsedTime(&a, p->ev[0], p->ev[1]);
-    cudaEventElapsedTime(&b, p->ev[1], p->ev[2]);
-    p->fac_ms += a;
-    p->msg_ms += b;
+    if (cudaEventSynchronize(p->ev[TMC_LOOPY_STAGE_COUNT]) != cudaSuccess) return TMC_ERR_CUDA;
+    for (int st = 0; st < TMC_LOOPY_STAGE_COUNT; ++st) {
+      float a = 0.f;
+      cudaEventElapsedTime(&a, p->ev[st], p->ev[st + 1]);
+      p->stage_ms[st] += a;
+    }
     ++p->calls;
   }
   return TMC_OK;
 }
 
-tmc_status tmc_loopy_profile(tmc_loopy_plan p, int enable, double* factor_ms, double* message_ms,
-                             long long* calls, int* exact_entries) {
+tmc_status tmc_loopy_profile(tmc_loopy_plan p, int enable, double* stage_ms, long long* calls,
+                             int* exact_entries) {
   if (!p) return TMC_ERR_INVALID_ARG;
   if (cudaDeviceSynchronize() != cudaSuccess) return TMC_ERR_CUDA;
-  if (factor_ms) *factor_ms = p->fac_ms;
-  if (message_ms) *message_ms = p->msg_ms;
+  if (stage_ms)
+    for (int st = 0; st < TMC_LOOPY_STAGE_COUNT; ++st) stage_ms[st] = p->stage_ms[st];
   if (calls) *calls = p->calls;
   if (exact_entries && cudaMemcpy(exact_entries, p->d_nfix, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return TMC_ERR_CUDA;
   int err = 0;
   if (cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TMC_ERR_CUDA;
   p->prof = enable != 0;
-  p->fac_ms = p->msg_ms = 0.0;
+  for (double& v : p->stage_ms) v = 0.0;
   p->calls = 0;
-  cudaMemset(p->d_nfix, 0, 2 * sizeof(int));
+  if (cudaMemset(p->d_nfix, 0, 2 * sizeof(int)) != cudaSuccess) return TMC_ERR_CUDA;
   return (err & kErrTimeout) ? TMC_ERR_TIMEOUT : TMC_OK;
 }
 

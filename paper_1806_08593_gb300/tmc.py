@@ -99,8 +99,7 @@ def load_library(path: str = LIB_PATH):
     lib.tmc_plan_set_wait_limit.restype = ctypes.c_int
     lib.tmc_loopy_plan_create.argtypes = [ctypes.POINTER(LoopyDesc), ctypes.POINTER(P)]
     lib.tmc_loopy_log_marginal.argtypes = [P, ctypes.POINTER(Inputs), P, V]
-    lib.tmc_loopy_profile.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
-                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+    lib.tmc_loopy_profile.argtypes = [P, ctypes.c_int, P, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_int)]
     lib.tmc_loopy_plan_destroy.argtypes = [P]
     for f in ("tmc_loopy_plan_create", "tmc_loopy_log_marginal", "tmc_loopy_profile", "tmc_loopy_plan_destroy"):
@@ -283,12 +282,16 @@ class LoopyPlan:
                "tmc_loopy_log_marginal")
         return out
 
+    STAGES = ["prep", "factor", "exp", "message", "final"]
+
     def profile(self, enable: bool = True) -> dict:
-        """Stage times since the last call (ms), forward calls timed, exactly recomputed entries."""
-        f, m, n, e = ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong(), ctypes.c_int()
-        _check(self._lib.tmc_loopy_profile(self._h, int(enable), ctypes.byref(f), ctypes.byref(m),
+        """Summed stage times since the last call (ms, keyed by STAGES), the forward calls timed
+        and the number of exactly recomputed message entries; then timing on / off."""
+        st = np.zeros(len(self.STAGES))
+        n, e = ctypes.c_longlong(), ctypes.c_int()
+        _check(self._lib.tmc_loopy_profile(self._h, int(enable), st.ctypes.data_as(ctypes.c_void_p),
                                            ctypes.byref(n), ctypes.byref(e)), "tmc_loopy_profile")
-        return dict(factor_ms=f.value, message_ms=m.value, calls=n.value, exact_entries=e.value)
+        return dict(stage_ms=dict(zip(self.STAGES, st.tolist())), calls=n.value, exact_entries=e.value)
 
     def close(self):
         if getattr(self, "_h", None):
