@@ -251,6 +251,19 @@ def count_kernel_launches(fn, dev):
 # the loopy graph of Fig. 1 (two matrix messages): forward log P per instance
 # ---------------------------------------------------------------------------------------
 LOOPY = dict(K=4096, d=128, obs=128, B=4)
+# DRAM bytes (read + write) of one message launch per instance, single bf16 operands, from an
+# ncu capture of k_gemm_split<1,256> at K=4096, d=128, B=1 (scaled by instances)
+LOOPY_MSG_TRAFFIC_PER_INSTANCE = {(4096, 128): 280.3e6}
+
+
+def loopy_config(spec):
+    """'diamond:K=..,d=..,obs=..,B=..' (missing keys from LOOPY), or None for LOOPY."""
+    c = dict(LOOPY)
+    if spec:
+        if not spec.startswith("diamond:"):
+            raise SystemExit("unknown loopy workload %s" % spec)
+        c.update({k: int(v) for k, v in (x.split("=") for x in spec[8:].split(","))})
+    return c
 
 
 def loopy_leg(args, dev):
@@ -261,7 +274,7 @@ def loopy_leg(args, dev):
     import torch
     from paper_1806_08593_gb300 import workload as wl
     from paper_1806_08593_gb300.tmc import LoopyPlan
-    c = LOOPY
+    c = loopy_config(args.loopy_workload)
     p = wl.make_diamond(c["K"], c["d"], c["obs"], c["B"], seed=1, shared=True)
     terms = 2.0 * p.K ** 3 * p.B
     msg_flops = 4.0 * p.K ** 3 * p.B          # two K x K x K products per instance
@@ -306,7 +319,9 @@ def loopy_leg(args, dev):
                                                                 np.array(res["bf16x2"]["logp"])))),
             "roofline": {"bound": "tensor", "kernel": "k_gemm_split<1,256> (both messages)",
                          "achieved": head["message_tflops"], "peak": peak, "unit": "TFLOP/s",
-                         "frac": head["message_tflops"] / peak, "traffic": None,
+                         "frac": head["message_tflops"] / peak,
+                         "traffic": LOOPY_MSG_TRAFFIC_PER_INSTANCE.get((p.K, p.d)) and
+                         LOOPY_MSG_TRAFFIC_PER_INSTANCE[(p.K, p.d)] * p.B,
                          "peak_source": "bf16_tflops (%s)" % src,
                          "flops_per_launch": msg_flops},
             "split": res["bf16x2"], "single": res["bf16"]}
@@ -709,9 +724,20 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-loopy", action="store_true",
                     help="skip the loopy-graph (Fig. 1, matrix messages) leg")
+    ap.add_argument("--loopy-only", action="store_true",
+                    help="run only the loopy-graph leg and print its JSON object")
+    ap.add_argument("--loopy-workload", default=None,
+                    help="diamond:K=..,d=..,obs=..,B=.. (default K=4096,d=128,obs=128,B=4)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.loopy_only:
+        import torch
+        from paper_1806_08593_gb300.build import build
+        build()
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        print(json.dumps(loopy_leg(args, dev)))
     else:
         run_ours(args)
 
