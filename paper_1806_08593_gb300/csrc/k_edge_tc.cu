@@ -653,14 +653,18 @@ __global__ void __launch_bounds__(128) k_obs_tc(Dev D, TcDev T, const Tile* __re
 // Forward edge kernel, pipelined across the CTA's items.
 // Roles: warp 0 lane 0 issues TMA; warp 1 lane 0 issues MMAs; warp 2 owns the TMEM
 // allocation; warp 3 prepares the next item's message vector (dependency
-// wait, beta_i, its maximum, c_i); warps 4..11 run the exponentials in two groups: group h =
+// wait, beta_i, its maximum); warps 4..11 run the exponentials in two groups: group h =
 // (w-4)/4 takes the chunks in S buffer h (warp w serves TMEM lanes 32*(w%4)..) and half h of
 // the latent dimension in the prologue split.
+// The A operand is double-buffered in TMEM: item j's mu~ accumulates (FP32) into region
+// j & 1 and is split there in place (each 32-column group becomes 16 columns of hi pairs and
+// 16 of lo pairs), so item j + 1's split never waits for item j's last S MMA, and it reads
+// c_i from global memory, so it never waits for item j + 1's message vector either.
 // The barriers are initialised once; every role walks the same item sequence and derives the
 // phase of each barrier from running counters:
 //   ring uses   : per item [Z~_p tile, W_i, chunk 0 .. chunk nch-1], stage = use % NS
 //   S buffers   : running chunk count, buffer = chunk & 1
-//   per item    : mu_full (mu~ in TMEM), a_full (A operand written), phase = item count & 1
+//   per item    : mu_full (mu~ in TMEM region j & 1), a_full (A operand written), phase = j & 1
 //   beta buffers: NCB (1 or 2) SMEM copies of cb / c_i, written by warp 3, freed by the math warps
 // so the TMA and MMA warps run into item j + 1 (its operands, mu~ = Z~_p W^T into TMEM) while
 // the math warps still finish item j, and warp 3 has item j + 1's message vector ready.
@@ -677,6 +681,8 @@ struct FwdCfg {
 // Chunk of an item before which the next item's prologue operands and mu~ MMAs are placed
 // in the ring / MMA order: two chunks before the end, so they overlap this item's tail.
 __host__ __device__ constexpr int pro_slot(int nch) { return nch >= 2 ? nch - 2 : 0; }
+// TMEM column (within an A region) of the hi pairs of K-step kk after the in-place split
+__device__ __forceinline__ uint32_t a_col(int kk) { return (uint32_t)(32 * (kk >> 1) + 8 * (kk & 1)); }
 
 // Bounded wait that also gives up as soon as another role of the CTA has given up.
 __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort) {
@@ -705,8 +711,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   __shared__ uint64_t full[NS], empty[NS], sfull[2], sfree[2], mu_full, a_full, cb_full[2], cb_empty[2],
       bar_done;
   __shared__ uint32_t tbase;
-  __shared__ int s_abort, s_early;
-  __shared__ __align__(16) float cvb[2][kTcMaxD];
+  __shared__ int s_abort;
+  __shared__ __align__(16) float cvn[2][kTcMaxD];  // c_i of item j in cvn[j & 1], for its split
   __shared__ float nrm_h[2][2][kRows], m_h[2][kRows], s_h[2][kRows];
   volatile int* abort = &s_abort;
 
@@ -734,8 +740,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tb = tbase;
-  // TMEM: S double buffer [0,256), mu~ accumulator [256,384), A operand hi [384,448) lo [448,512)
-  const uint32_t tS[2] = {tb, tb + 128}, tMU = tb + 256, tAH = tb + 384, tAL = tb + 448;
+  // TMEM: S double buffer [0,256); A regions [256,384) and [384,512): item j's mu~ (FP32), then
+  // its A operand (split in place) in region j & 1
+  const uint32_t tS[2] = {tb, tb + 128}, tR[2] = {tb + 256, tb + 384};
 
   if (warp == 0) {
     if (lane == 0) {
@@ -798,8 +805,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       long long gu = 0, gc = 0;
       int it = 0;
       bool ok = true;
-      // mu~ = Z~_p W_i^T (split products) from the next two ring uses into MU
-      auto mu_mmas = [&]() -> bool {
+      // mu~ = Z~_p W_i^T (split products) of item `itm` from the next two ring uses into
+      // region itm & 1 (its previous A, read by MMAs issued before these)
+      auto mu_mmas = [&](int itm) -> bool {
+        const uint32_t tMU = tR[itm & 1];
         const int sz = (int)(gu % NS), sw = (int)((gu + 1) % NS);
         if (!mbar_wait_ab(&full[sz], (uint32_t)((gu / NS) & 1), abort) ||
             !mbar_wait_ab(&full[sw], (uint32_t)(((gu + 1) / NS) & 1), abort))
@@ -816,7 +825,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         gu += 2;
         return true;
       };
-      if (blockIdx.x < ntiles) ok = mu_mmas();
+      if (blockIdx.x < ntiles) ok = mu_mmas(0);
       for (int item = blockIdx.x; ok && item < ntiles; item += gridDim.x, ++it) {
         const NodeInfo nd = D.nodes[tiles[item].node];
         const int nch = tiles_of(nd.K);
@@ -826,16 +835,18 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         if (!mbar_wait_ab(&a_full, (uint32_t)(it & 1), abort)) { ok = false; break; }
         for (int c = 0; c < nch; ++c, ++gu, ++gc) {
           // the next item's mu~ between this item's chunks, where the tensor pipe has room
-          if (c == pro_slot(nch) && has_next && !mu_mmas()) { ok = false; break; }
+          if (c == pro_slot(nch) && has_next && !mu_mmas(it + 1)) { ok = false; break; }
           const int s = (int)(gu % NS), b = (int)(gc & 1);
           if (!mbar_wait_ab(&full[s], (uint32_t)((gu / NS) & 1), abort)) { ok = false; break; }
           if (gc >= 2 && !mbar_wait_ab(&sfree[b], (uint32_t)(((gc >> 1) + 1) & 1), abort)) { ok = false; break; }
           tc_fence_after();
           const uint64_t dbh = kdesc(ring + s * 2 * TB, 0), dbl = kdesc(ring + s * 2 * TB + TB, 0);
-          // S = (A_hi + A_lo)(B_hi + B_lo)^T without lo*lo; A from tensor memory (2 fp16 / column)
-          for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kstep(dbh, kk), id_s, kk > 0);
-          for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAL + kk * 8, kstep(dbh, kk), id_s, 1);
-          for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tAH + kk * 8, kstep(dbl, kk), id_s, 1);
+          // S = (A_hi + A_lo)(B_hi + B_lo)^T without lo*lo; A from tensor memory (2 fp16 / column):
+          // K-step kk's 16 elements are hi pairs at columns 32 (kk / 2) + 8 (kk % 2), lo 16 further
+          const uint32_t tA = tR[it & 1];
+          for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tA + a_col(kk), kstep(dbh, kk), id_s, kk > 0);
+          for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tA + a_col(kk) + 16, kstep(dbh, kk), id_s, 1);
+          for (int kk = 0; kk < KS; ++kk) mma_ts(tS[b], tA + a_col(kk), kstep(dbl, kk), id_s, 1);
           mma_commit(&sfull[b]);
           mma_commit(&empty[s]);
         }
@@ -920,9 +931,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         }
       }
       if (store && lane == 0) D.nodemax[t.node] = mx;
-      for (int j = lane; j < kTcMaxD; j += 32) cvb[ib][j] = __ldg(T.cvec + (long long)t.node * kLdp + j);
       __syncwarp();
-      if (lane == 0) mbar_arrive(&cb_full[ib]);  // release: cb / c_i visible to the math warps
+      if (lane == 0) mbar_arrive(&cb_full[ib]);  // release: cb visible to the math warps
     }
     if (!ok) set_timeout(D);
   } else if (warp >= 4) {
@@ -935,18 +945,18 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     // A failed wait leaves `ok` false for this thread: it skips its remaining work of the
     // item but still reaches every named barrier; after the item's last barrier all math
     // threads read the shared abort flag and stop together.
-    // Per item: the chunk loop, then (as soon as the last S has been read, so every MMA of
-    // the item is complete) the next item's mu~ is split into A and a_full released, and only
-    // then this item's messages are combined and published.
+    // Per item: the chunk loop (the group without the item's last chunk splits the next
+    // item's mu~ after its own last chunk), then this item's messages are combined and
+    // published.
     bool ok = true;
-    // mu~ of item `it` (+ c_i) -> A operand; its squared norm into nrm_h[it & 1].  Each group
-    // splits its half of the columns, or (all) one group splits every column and arrives on
-    // a_full for the other group's threads too.
+    // mu~ of item `it_s` (+ c_i) -> A operand, in place in region it_s & 1; its squared norm
+    // into nrm_h[it_s & 1].  Each group splits its half of the columns, or (all) one group
+    // splits every column and arrives on a_full for the other group's threads too.
     auto split = [&](int it_s, bool all) {
-      const int ibs = it_s % ncb;
-      ok = ok && mbar_wait_ab(&cb_full[ibs], (uint32_t)((it_s / ncb) & 1), abort) &&
-           mbar_wait_ab(&mu_full, (uint32_t)(it_s & 1), abort);
+      ok = ok && mbar_wait_ab(&mu_full, (uint32_t)(it_s & 1), abort);
       tc_fence_after();
+      const uint32_t tMU = tR[it_s & 1];
+      const float* cvg = cvn[it_s & 1];
       // the two column halves keep separate norm partials, so the norm is the same sum
       // whichever way the split ran (the results do not depend on the work order)
       float nrm_lo = 0.f, nrm_hi = 0.f;  // columns [0, DP/2) and [DP/2, DP)
@@ -960,15 +970,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           float f[32], nrm = g >= GH ? nrm_hi : nrm_lo;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            f[j] = __uint_as_float(v[j]) + cvb[ibs][g * 32 + j];
+            f[j] = __uint_as_float(v[j]) + cvg[g * 32 + j];
             nrm = fmaf(f[j], f[j], nrm);
           }
           if (g >= GH) nrm_hi = nrm;
           else nrm_lo = nrm;
           uint32_t hi[16], lo[16];
           split_pack32(f, hi, lo);
-          tmem_st16(tAH + lane_off + g * 16, hi);
-          tmem_st16(tAL + lane_off + g * 16, lo);
+          // in place: this thread has read its row's 32 columns of the group
+          tmem_st16(tMU + lane_off + g * 32, hi);
+          tmem_st16(tMU + lane_off + g * 32 + 16, lo);
         }
         tmem_wait_st();
       }
@@ -984,7 +995,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     };
     long long gc = 0;
     int it = 0;
-    if (blockIdx.x < ntiles) split(0, false);
+    if (blockIdx.x < ntiles) {
+      if (mt < kTcMaxD) cvn[0][mt] = __ldg(T.cvec + (long long)tiles[blockIdx.x].node * kLdp + mt);
+      sync_math();
+      split(0, false);
+    }
     for (int item = blockIdx.x; item < ntiles; item += gridDim.x, ++it) {
       const Tile t = tiles[item];
       const NodeInfo nd = D.nodes[t.node];
@@ -992,10 +1007,22 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       const int k = t.row0 + r;
       const int ib = it % ncb;
       const float* cb = cbuf + (size_t)ib * cbk;
+      // this item's message vector (warp 3, after the item's dependencies) before any chunk
+      ok = ok && mbar_wait_ab(&cb_full[ib], (uint32_t)((it / ncb) & 1), abort);
       sync_math();  // both half norms of this item are complete
       const float nrm_all = nrm_h[it & 1][0][r] + nrm_h[it & 1][1][r];
       if (ok && h == 0 && k < K) D.mun[nd.off_nk + k] = nrm_all;
       float m = -INFINITY, ssum = 0.f;
+      // The group that does not hold the item's last chunk splits the next item's mu~ (every
+      // column) into the other A region as soon as it is done with its own chunks, while the
+      // other group still works on the last chunk; its threads fetch that item's c_i now, so
+      // the loads complete under the chunks.
+      const bool has_next = item + (int)gridDim.x < ntiles;
+      const int blast = (int)((gc + nch - 1) & 1);
+      if (h != blast && has_next) {
+        const int ml = mt - h * (kMath / 2);
+        if (ml < kTcMaxD) cvn[(it + 1) & 1][ml] = __ldg(T.cvec + (long long)tiles[item + gridDim.x].node * kLdp + ml);
+      }
       // the two warp groups take alternate chunks (group h: the chunks in S buffer h), each
       // thread a whole 128-column row of its chunks, so one group's TMEM loads and
       // exponentials overlap the other's
@@ -1043,28 +1070,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           }
         }
       }
-      // The group that does not hold the last chunk splits the next item's mu~ (every column)
-      // as soon as the last S MMAs, which read A, are complete -- while the other group still
-      // works on the last chunk.  It may do so before this item's messages are published only
-      // when the next item's message vector is already prepared (warp 3 has passed its
-      // dependency wait); otherwise the next item may depend on this one, and the split waits
-      // until after the release below.  The decision is published in s_early.
-      const bool has_next = item + (int)gridDim.x < ntiles;
-      const long long glast = gc + nch - 1;
-      const int blast = (int)(glast & 1);
-      if (h != blast) {
-        if (has_next) ok = ok && mbar_wait_ab(&sfull[blast], (uint32_t)((glast >> 1) & 1), abort);
-        if (mt == h * (kMath / 2))
-          s_early = has_next && ok && mbar_try_wait(&cb_full[(it + 1) % ncb], (uint32_t)(((it + 1) / ncb) & 1));
-        asm volatile("bar.sync 3, 128;" ::: "memory");  // this group only, whatever ok says
-        if (s_early) split(it + 1, true);
+      if (h != blast && has_next) {
+        asm volatile("bar.sync 3, 128;" ::: "memory");  // this group's c_i loads are in cvn
+        split(it + 1, true);
       }
       gc += nch;
-      mbar_arrive(&cb_empty[ib]);  // cb of this item is no longer read (c_i was read by its split)
+      mbar_arrive(&cb_empty[ib]);  // cb of this item is no longer read
       m_h[h][r] = m;
       s_h[h][r] = ssum;
-      sync_math();  // m_h / s_h complete, s_early published
-      const bool early = s_early != 0;
+      sync_math();  // m_h / s_h complete
       if (ok && h == 0 && k < K) {
         const float m0 = m_h[0][r], m1 = m_h[1][r];
         const float M = fmaxf(m0, m1);
@@ -1085,7 +1099,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         if (mt == 0) set_timeout(D);
         break;
       }
-      if (has_next && !early) split(it + 1, false);
     }
   }
   tc_fence_before();
