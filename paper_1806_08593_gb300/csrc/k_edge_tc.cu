@@ -173,8 +173,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 // Per-instance completion stamps of a persistent edge launch (direction dir).
-__device__ __forceinline__ void stamp_item_start(TcDev& T, int dir, int item) {
-  if (item == (int)blockIdx.x) atomicMin(T.t_start + dir, global_ns());
+__device__ __forceinline__ void stamp_item_start(TcDev& T, int dir, bool first) {
+  if (first) atomicMin(T.t_start + dir, global_ns());
 }
 // An instance's end time is the latest end time of its tiles (a fire-and-forget max).
 __device__ __forceinline__ void stamp_item_end(const Dev& D, TcDev& T, int dir, int b) {
@@ -681,6 +681,15 @@ struct FwdCfg {
 // Chunk of an item before which the next item's prologue operands and mu~ MMAs are placed
 // in the ring / MMA order: two chunks before the end, so they overlap this item's tail.
 __host__ __device__ constexpr int pro_slot(int nch) { return nch >= 2 ? nch - 2 : 0; }
+// Items of a persistent edge launch are claimed from a counter in list order, which is
+// dependency order: every item an item depends on was claimed earlier by a running CTA, so the
+// launch progresses however many of its CTAs are resident.  -1 once the list is exhausted.
+__device__ __forceinline__ int claim_item(int* counter, int ntiles) {
+  const int v = atomicAdd(counter, 1);
+  return v < ntiles ? v : -1;
+}
+constexpr int kSeq = 4;                     // forward item-sequence ring
+constexpr int kSeqReaders = 2 + kMath / 32; // MMA issuer, warp 3, one arrival per math warp
 // TMEM column (within an A region) of the hi pairs of K-step kk after the in-place split
 __device__ __forceinline__ uint32_t a_col(int kk) { return (uint32_t)(32 * (kk >> 1) + 8 * (kk & 1)); }
 
@@ -699,7 +708,8 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, vol
 
 template <int DP>
 __global__ void __launch_bounds__(kThreadsTc, 1)
-    k_edge_fwd_tc(Dev D, TcDev T, const Tile* __restrict__ tiles, int ntiles, int* __restrict__ done, int ncb, int cbk,
+    k_edge_fwd_tc(Dev D, TcDev T, const Tile* __restrict__ tiles, int ntiles, int* __restrict__ done,
+                  int* __restrict__ claim, int ncb, int cbk,
                   const __grid_constant__ CUtensorMap mZH, const __grid_constant__ CUtensorMap mZL,
                   const __grid_constant__ CUtensorMap mWH, const __grid_constant__ CUtensorMap mWL) {
   using C = FwdCfg<DP>;
@@ -713,6 +723,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   __shared__ uint32_t tbase;
   __shared__ int s_abort;
   __shared__ __align__(16) float cvn[2][kTcMaxD];  // c_i of item j in cvn[j & 1], for its split
+  // The CTA's item sequence: the producer claims items from the launch's counter in list
+  // (dependency) order, one ahead of the item it loads, into a ring of kSeq slots; the MMA
+  // issuer, warp 3 and the math warps read it (an entry < 0 ends the sequence).
+  __shared__ int s_seq[kSeq];
+  __shared__ uint64_t q_full[kSeq], q_empty[kSeq];
   __shared__ float nrm_h[2][2][kRows], m_h[2][kRows], s_h[2][kRows];
   volatile int* abort = &s_abort;
 
@@ -733,6 +748,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     mbar_init(&mu_full, 1);
     mbar_init(&a_full, kMath);
     mbar_init(&bar_done, 1);
+    for (int i = 0; i < kSeq; ++i) {
+      mbar_init(&q_full[i], 1);
+      mbar_init(&q_empty[i], kSeqReaders);
+    }
     fence_barrier_init();
     s_abort = 0;
   }
@@ -743,6 +762,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   // TMEM: S double buffer [0,256); A regions [256,384) and [384,512): item j's mu~ (FP32), then
   // its A operand (split in place) in region j & 1
   const uint32_t tS[2] = {tb, tb + 128}, tR[2] = {tb + 256, tb + 384};
+  // entry j of the item sequence (every reader waits; one arrival per reading unit on release)
+  auto seq_get = [&](int j, int& v) -> bool {
+    if (!mbar_wait_ab(&q_full[j % kSeq], (uint32_t)((j / kSeq) & 1), abort)) return false;
+    v = s_seq[j % kSeq];
+    return true;
+  };
 
   if (warp == 0) {
     if (lane == 0) {
@@ -774,13 +799,23 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         return load_use(&mZH, &mZL, (int)(D.nodes[nd.parent].off_nk + t.row0)) &&
                load_use(&mWH, &mWL, slot_of(D, nd, t.node) * kLdp);
       };
-      if (blockIdx.x < ntiles) ok = load_pro(blockIdx.x);
-      for (int item = blockIdx.x; ok && item < ntiles; item += gridDim.x) {
+      // publish entry j of the sequence: a claimed item, or -1 once the list is exhausted
+      auto publish = [&](int j) -> int {
+        if (j >= kSeq && !mbar_wait_ab(&q_empty[j % kSeq], (uint32_t)(((j / kSeq) - 1) & 1), abort)) return -2;
+        const int v = claim_item(claim, ntiles);
+        s_seq[j % kSeq] = v;
+        mbar_arrive(&q_full[j % kSeq]);  // (release)
+        return v;
+      };
+      int cur = publish(0), nxt = cur >= 0 ? publish(1) : -1;
+      if (cur == -2 || nxt == -2) ok = false;
+      if (ok && cur >= 0) ok = load_pro(cur);
+      for (int j = 0; ok && cur >= 0; ++j) {
+        const int item = cur;
         const Tile t = tiles[item];
         const NodeInfo nd = D.nodes[t.node];
         const int nch = tiles_of(nd.K);
-        const int nxt = item + (int)gridDim.x;
-        if (item == (int)blockIdx.x) stamp_item_start(T, 0, item);
+        stamp_item_start(T, 0, j == 0);
         // the 8 row tiles of an edge walk the child's chunks in the same order; each pulls
         // "its" chunk (index = its row tile) into L2 up front
         for (int b = 0; b < NB; ++b) {
@@ -788,8 +823,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           tma_prefetch_l2_2d(&mZL, b * 64, (int)(nd.off_nk + t.row0));
         }
         for (int c = 0; ok && c < nch; ++c) {
-          if (c == pro_slot(nch) && nxt < ntiles) ok = load_pro(nxt);
+          if (c == pro_slot(nch) && nxt >= 0) ok = load_pro(nxt);
           ok = ok && load_use(&mZH, &mZL, (int)(nd.off_nk + c * kRows));
+        }
+        // the next item becomes current; claim the one after it
+        cur = nxt;
+        if (ok && cur >= 0) {
+          nxt = publish(j + 2);
+          if (nxt == -2) ok = false;
         }
       }
       if (!ok) set_timeout(D);
@@ -825,11 +866,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         gu += 2;
         return true;
       };
-      if (blockIdx.x < ntiles) ok = mu_mmas(0);
-      for (int item = blockIdx.x; ok && item < ntiles; item += gridDim.x, ++it) {
+      int cur = -1, nxt = -1;
+      ok = seq_get(0, cur);
+      if (ok && cur >= 0) ok = mu_mmas(0);
+      for (; ok && cur >= 0; ++it) {
+        const int item = cur;
+        if (!seq_get(it + 1, nxt)) { ok = false; break; }
+        mbar_arrive(&q_empty[it % kSeq]);
         const NodeInfo nd = D.nodes[tiles[item].node];
         const int nch = tiles_of(nd.K);
-        const bool has_next = item + (int)gridDim.x < ntiles;
+        const bool has_next = nxt >= 0;
         // A of this item written by the math warps (they have also read MU, so the next
         // item's mu~ may go there)
         if (!mbar_wait_ab(&a_full, (uint32_t)(it & 1), abort)) { ok = false; break; }
@@ -850,6 +896,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           mma_commit(&sfull[b]);
           mma_commit(&empty[s]);
         }
+        cur = nxt;
       }
       if (!ok) set_timeout(D);
       mma_commit(&bar_done);
@@ -860,7 +907,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     // cb[k'] = (beta_i[k'] - max beta_i - |z~_i^{k'}|^2 / (2 var)) log2(e), -inf past K; c_i.
     int it = 0;
     bool ok = true;
-    for (int item = blockIdx.x; ok && item < ntiles; item += gridDim.x, ++it) {
+    for (;; ++it) {
+      int item = -1;
+      if (lane == 0) ok = seq_get(it, item);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      item = __shfl_sync(0xffffffffu, item, 0);
+      if (lane == 0) mbar_arrive(&q_empty[it % kSeq]);
+      if (!ok || item < 0) break;
       const Tile t = tiles[item];
       const NodeInfo nd = D.nodes[t.node];
       const int K = nd.K, nch = tiles_of(K);
@@ -995,12 +1048,20 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     };
     long long gc = 0;
     int it = 0;
-    if (blockIdx.x < ntiles) {
-      if (mt < kTcMaxD) cvn[0][mt] = __ldg(T.cvec + (long long)tiles[blockIdx.x].node * kLdp + mt);
+    int cur = -1, nxt = -1;
+    ok = seq_get(0, cur);
+    if (__any_sync(0xffffffffu, !ok)) cur = -1;  // (a failed read ends every thread's loop below)
+    cur = sync_math_or(cur < 0) ? -1 : cur;
+    if (cur >= 0) {
+      if (mt < kTcMaxD) cvn[0][mt] = __ldg(T.cvec + (long long)tiles[cur].node * kLdp + mt);
       sync_math();
       split(0, false);
     }
-    for (int item = blockIdx.x; item < ntiles; item += gridDim.x, ++it) {
+    for (; cur >= 0; ++it) {
+      const int item = cur;
+      ok = ok && seq_get(it + 1, nxt);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&q_empty[it % kSeq]);
       const Tile t = tiles[item];
       const NodeInfo nd = D.nodes[t.node];
       const int K = nd.Kp, nch = tiles_of(nd.K);  // rows: parent samples; chunks: child samples
@@ -1017,11 +1078,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       // column) into the other A region as soon as it is done with its own chunks, while the
       // other group still works on the last chunk; its threads fetch that item's c_i now, so
       // the loads complete under the chunks.
-      const bool has_next = item + (int)gridDim.x < ntiles;
+      const bool has_next = ok && nxt >= 0;
       const int blast = (int)((gc + nch - 1) & 1);
       if (h != blast && has_next) {
         const int ml = mt - h * (kMath / 2);
-        if (ml < kTcMaxD) cvn[(it + 1) & 1][ml] = __ldg(T.cvec + (long long)tiles[item + gridDim.x].node * kLdp + ml);
+        if (ml < kTcMaxD) cvn[(it + 1) & 1][ml] = __ldg(T.cvec + (long long)tiles[nxt].node * kLdp + ml);
       }
       // the two warp groups take alternate chunks (group h: the chunks in S buffer h), each
       // thread a whole 128-column row of its chunks, so one group's TMEM loads and
@@ -1099,6 +1160,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         if (mt == 0) set_timeout(D);
         break;
       }
+      cur = nxt;  // the same value in every math thread (every read succeeded)
     }
   }
   tc_fence_before();
@@ -1127,6 +1189,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 template <int DP, bool ROWS>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     k_edge_bwd_tc(Dev D, TcDev T, const Tile* __restrict__ tiles, int ntiles, int* __restrict__ done,
+                  int* __restrict__ claim,
                   const __grid_constant__ CUtensorMap mZH, const __grid_constant__ CUtensorMap mZL,
                   const __grid_constant__ CUtensorMap mWTH, const __grid_constant__ CUtensorMap mWTL,
                   const __grid_constant__ CUtensorMap mG) {
@@ -1152,15 +1215,22 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   __shared__ Tile s_tile[2];
   __shared__ NodeInfo s_nd[2], s_pn[2];
   __shared__ int s_dep[2];
+  // the items of this CTA, claimed from the launch's counter in list (dependency) order: thread
+  // 0 claims item iter + 1 at the start of item iter (slot iter & 1 holds item iter)
+  __shared__ int s_claim[2];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float iv = D.inv_var;
   if (warp == 2) tmem_alloc(&tbase, 512);
-  if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) {
-    s_tile[0] = tiles[blockIdx.x];
-    s_nd[0] = D.nodes[s_tile[0].node];
-    s_pn[0] = D.nodes[s_nd[0].parent];
-    s_dep[0] = 0;
+  if (threadIdx.x == 0) {
+    const int first = claim_item(claim, ntiles);
+    s_claim[0] = first;
+    if (first >= 0) {
+      s_tile[0] = tiles[first];
+      s_nd[0] = D.nodes[s_tile[0].node];
+      s_pn[0] = D.nodes[s_nd[0].parent];
+      s_dep[0] = 0;
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -1176,8 +1246,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   const uint32_t tG = tb;
 
   // persistent loop over the edge tiles of every level, root side first
-  for (int item = blockIdx.x, iter = 0; item < ntiles; item += gridDim.x, ++iter) {
+  for (int iter = 0;; ++iter) {
   const int sl = iter & 1;
+  const int item = s_claim[sl];  // written before the last CTA-wide barrier
+  if (item < 0) break;
   const Tile t = s_tile[sl];
   const NodeInfo nd = s_nd[sl];
   const NodeInfo pn = s_pn[sl];
@@ -1195,11 +1267,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   unsigned char* eZL = eZH + TB;                                            // Z~_i lo
   unsigned char* eSV = early_ez ? ring + ((nch + 1) % NS) * 2 * TB : ring + 2 * TB;  // V tile
   if (threadIdx.x == 0) {
+    s_claim[sl ^ 1] = claim_item(claim, ntiles);  // the next item (its records: warp 3)
     // the parent's sample weights must be final (the root's come from an earlier launch)
     if (!ROWS) {
       if (pn.parent >= 0 && !s_dep[sl] && !wait_count(done + nd.parent, tiles_of(pn.K), D.wait_limit))
         set_timeout(D);
-      stamp_item_start(T, 1, item);
+      stamp_item_start(T, 1, iter == 0);
     }
     mbar_init(&bar_pro, 1);
     mbar_init(&bar_mu, 1);
@@ -1240,8 +1313,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       tma_load_2d(ring + 2 * TB + b * kBox, &mWTH, &bar_pro, b * 64, slot * kLdp);
       tma_load_2d(ring + 3 * TB + b * kBox, &mWTL, &bar_pro, b * 64, slot * kLdp);
     }
-    if (item + (int)gridDim.x < ntiles) {  // next item's own tile into L2 while this one runs
-      const Tile tn = tiles[item + gridDim.x];
+    if (s_claim[sl ^ 1] >= 0) {  // next item's own tile into L2 while this one runs
+      const Tile tn = tiles[s_claim[sl ^ 1]];
       const NodeInfo& nn = D.nodes[tn.node];
       const int row_n = (int)((ROWS ? D.nodes[nn.parent].off_nk : nn.off_nk) + tn.row0);
       for (int b = 0; b < NB; ++b) {
@@ -1373,8 +1446,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     // (three dependent loads) and one look at its dependency, while this item runs; if the
     // dependency is not met yet (it may be this very item), thread 0 waits for it at the
     // next item's start.
-    const int nx = item + (int)gridDim.x;
-    if (nx < ntiles) {
+    const int nx = s_claim[sl ^ 1];
+    if (nx >= 0) {
       const Tile tn = tiles[nx];
       const NodeInfo ndn = D.nodes[tn.node];
       const NodeInfo pnn = D.nodes[ndn.parent];
@@ -2616,6 +2689,7 @@ void workspace_layout(TcWork& w, const std::vector<NodeInfo>& nodes, long long n
   subs.push_back({(void**)&w.t.ZL, pk});
   subs.push_back({(void**)&w.t.zc, (size_t)nk * sizeof(float)});
   subs.push_back({(void**)&w.t.done, (size_t)w.num_nodes * sizeof(int)});
+  subs.push_back({(void**)&w.t.claim, 8 * sizeof(int)});  // item counters: fwd, adjoint, rows x 2 classes
   subs.push_back({(void**)&w.t.inst_t, (size_t)2 * w.num_inst * sizeof(unsigned long long)});
   subs.push_back({(void**)&w.t.t_start, 2 * sizeof(unsigned long long)});
   subs.push_back({(void**)&w.t.WH, pw});
@@ -2855,6 +2929,7 @@ void launch_obs(TcWork& w, const Dev& D, cudaStream_t s) {
 
 void launch_edge_fwd(TcWork& w, const Dev& D, cudaStream_t s) {
   cudaMemsetAsync(w.t.done, 0, (size_t)w.num_nodes * sizeof(int), s);
+  cudaMemsetAsync(w.t.claim, 0, 2 * sizeof(int), s);
   cudaMemsetAsync(w.t.inst_t, 0, sizeof(unsigned long long) * w.num_inst, s);
   cudaMemsetAsync(w.t.t_start, 0xFF, sizeof(unsigned long long), s);
   for (int c = 0; c < 2; ++c) {
@@ -2864,11 +2939,13 @@ void launch_edge_fwd(TcWork& w, const Dev& D, cudaStream_t s) {
     int ncb = 1, cbk = 0;
     if (c == 0) {
       const size_t sm = fwd_smem<64>(w.maxK, &ncb, &cbk);
-      k_edge_fwd_tc<64><<<grid, kThreadsTc, sm, s>>>(D, w.t, w.d_tiles + b, n, w.t.done, ncb, cbk, w.mZH, w.mZL,
+      k_edge_fwd_tc<64><<<grid, kThreadsTc, sm, s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.t.claim + c, ncb, cbk,
+                                                      w.mZH, w.mZL,
                                                       w.mWH, w.mWL);
     } else {
       const size_t sm = fwd_smem<128>(w.maxK, &ncb, &cbk);
-      k_edge_fwd_tc<128><<<grid, kThreadsTc, sm, s>>>(D, w.t, w.d_tiles + b, n, w.t.done, ncb, cbk, w.mZH, w.mZL,
+      k_edge_fwd_tc<128><<<grid, kThreadsTc, sm, s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.t.claim + c, ncb, cbk,
+                                                       w.mZH, w.mZL,
                                                        w.mWH, w.mWL);
     }
   }
@@ -2877,6 +2954,7 @@ void launch_edge_fwd(TcWork& w, const Dev& D, cudaStream_t s) {
 void launch_edge_bwd(TcWork& w, const Dev& D, cudaStream_t s) {
   k_zero_dd<<<w.num_nodes, 256, 0, s>>>(D, w.t.G);
   cudaMemsetAsync(w.t.done, 0, (size_t)w.num_nodes * sizeof(int), s);
+  cudaMemsetAsync(w.t.claim + 2, 0, 2 * sizeof(int), s);
   cudaMemsetAsync(w.t.inst_t + w.num_inst, 0, sizeof(unsigned long long) * w.num_inst, s);
   cudaMemsetAsync(w.t.t_start + 1, 0xFF, sizeof(unsigned long long), s);
   for (int c = 0; c < 2; ++c) {
@@ -2884,26 +2962,30 @@ void launch_edge_bwd(TcWork& w, const Dev& D, cudaStream_t s) {
     if (!n) continue;
     const int grid = n < w.num_sms ? n : w.num_sms;
     if (c == 0)
-      k_edge_bwd_tc<64, false><<<grid, kThreadsTc, bwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH, w.mZL,
+      k_edge_bwd_tc<64, false><<<grid, kThreadsTc, bwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done,
+                                                                     w.t.claim + 2 + c, w.mZH, w.mZL,
                                                                      w.mWTH, w.mWTL, w.mG);
     else
-      k_edge_bwd_tc<128, false><<<grid, kThreadsTc, bwd_smem<128>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH,
+      k_edge_bwd_tc<128, false><<<grid, kThreadsTc, bwd_smem<128>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done,
+                                                                       w.t.claim + 2 + c, w.mZH,
                                                                        w.mZL, w.mWTH, w.mWTL, w.mG);
   }
 }
 
 void launch_edge_rows(TcWork& w, const Dev& D, cudaStream_t s) {
+  cudaMemsetAsync(w.t.claim + 4, 0, 2 * sizeof(int), s);
   // tile r of edge p -> i names parent rows r .. r + 127; no item depends on another
   for (int c = 0; c < 2; ++c) {
     const int b = w.it_b[2][c], n = w.it_e[2][c] - b;
     if (!n) continue;
     const int grid = n < w.num_sms ? n : w.num_sms;
     if (c == 0)
-      k_edge_bwd_tc<64, true><<<grid, kThreadsTc, bwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.mZH,
+      k_edge_bwd_tc<64, true><<<grid, kThreadsTc, bwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done,
+                                                                           w.t.claim + 4 + c, w.mZH,
                                                                            w.mZL, w.mWH, w.mWL, w.mG);
     else
       k_edge_bwd_tc<128, true><<<grid, kThreadsTc, bwd_smem<128>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done,
-                                                                             w.mZH, w.mZL, w.mWH, w.mWL, w.mG);
+                                                                             w.t.claim + 4 + c, w.mZH, w.mZL, w.mWH, w.mWL, w.mG);
   }
 }
 

@@ -67,6 +67,7 @@ struct TcDev {
   __half *EH, *EL;             // [rows][128] split R - mu~ per edge, rows = the parent's samples
   __half *CCH, *CCL;           // [num_c*128][128] split -(prior_var / obs_var) C^T C
   int* done;                   // [nodes] tiles finished per node in the running edge launch
+  int* claim;                  // [8] next unclaimed item of each persistent edge launch
   unsigned long long* inst_t;  // [2][B] %globaltimer when an instance's last tile finished (fwd, adjoint)
   unsigned long long* t_start; // [2]    %globaltimer at the first tile of each launch
   int shared;
