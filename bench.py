@@ -285,6 +285,10 @@ def loopy_leg(args, dev):
         plan = LoopyPlan.from_problem(p, mp)
         t = plan.to_device(p, dev)
         out = torch.empty(p.B, dtype=torch.float64, device=dev)
+        tuned = None
+        if args.autotune:
+            from paper_1806_08593_gb300.autotune import autotune_loopy
+            tuned = autotune_loopy(plan, p, t, cache_path=None)
         for _ in range(3):
             plan.forward(t, out=out)
         torch.cuda.synchronize(dev)
@@ -306,7 +310,8 @@ def loopy_leg(args, dev):
                    "exact_entries_per_step": pr["exact_entries"] / max(1, pr["calls"]),
                    "message_tflops": msg_flops / (st["message"] * 1e-3) / 1e12,
                    "factor_tflops": fac_flops / (st["factor"] * 1e-3) / 1e12,
-                   "gpu_launches_per_step": launches, "logp": out.cpu().numpy().tolist()}
+                   "gpu_launches_per_step": launches, "logp": out.cpu().numpy().tolist(),
+                   "autotune": tuned}
         plan.close()
         del t
     peaks, src = load_peaks()
@@ -713,8 +718,10 @@ def main():
     ap.add_argument("--precision", default=os.environ.get("TMC_BENCH_PRECISION", "fp16"),
                     choices=["fp32", "fp16"])
     ap.add_argument("--no-fp32-compare", action="store_true")
-    ap.add_argument("--autotune", action="store_true",
-                    help="time every persistent work order on the workload first and keep the fastest")
+    ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
+                    help="time every combination of the persistent-launch knobs (work order, prologue "
+                         "lead, grid) on the workload first and keep the fastest (default; the loopy leg "
+                         "tunes the N tile of its message products)")
     ap.add_argument("--graph", action=argparse.BooleanOptionalAction, default=True,
                     help="capture one step in a CUDA graph and time graph replays (default; "
                          "--no-graph times plain launches)")

@@ -215,6 +215,21 @@ const char* tmc_status_string(tmc_status s);
 tmc_status tmc_plan_set_schedule(tmc_plan plan, int schedule);
 tmc_status tmc_plan_get_schedule(tmc_plan plan, int* schedule);
 
+/* Tuning knobs of a tensor-core plan (the autotuner in the Python binding sweeps them); none
+ * changes the arithmetic of a tile, so every setting gives the same log P_TMC bit for bit:
+ *   TMC_TUNE_SCHEDULE      the work order above (0, 1, 2)
+ *   TMC_TUNE_PROLOGUE_LEAD chunks before the end of a forward item at which the next item's
+ *                          prologue operands and mu~ product enter the ring / MMA order (1..3;
+ *                          default 2): earlier overlaps more, later keeps more ring stages for
+ *                          the item's own chunks
+ *   TMC_TUNE_GRID          CTAs of each persistent edge launch: 0 (default) one per SM, else
+ *                          that many (capped at the SM count and the item count)
+ * set: no allocation; TMC_ERR_UNSUPPORTED on FP32 plans, TMC_ERR_INVALID_ARG for an unknown
+ * knob or value. */
+enum { TMC_TUNE_SCHEDULE = 0, TMC_TUNE_PROLOGUE_LEAD = 1, TMC_TUNE_GRID = 2 };
+tmc_status tmc_plan_set_tuning(tmc_plan plan, int knob, int value);
+tmc_status tmc_plan_get_tuning(tmc_plan plan, int knob, int* value);
+
 /* Per-instance completion times of the last tmc_log_marginal / tmc_backward on a tensor-core
  * plan: the time (microseconds) from the first edge tile of the persistent edge launch to
  * the moment the instance's last edge tile finished, in each direction.  HOST double[B]
@@ -295,6 +310,10 @@ enum {
  * bounded device wait gave up since the last call. */
 tmc_status tmc_loopy_profile(tmc_loopy_plan plan, int enable, double* stage_ms, long long* calls,
                              int* exact_entries);
+/* N tile of the message products: 128 or 256 columns per CTA tile (0: 256 when K > 128, the
+ * default).  No allocation; the results are the same up to the order of the FP32 sums within
+ * a tile.  TMC_ERR_INVALID_ARG for another value. */
+tmc_status tmc_loopy_plan_set_tile(tmc_loopy_plan plan, int n_tile);
 /* Releases the plan (synchronises the device first).  NULL is a no-op. */
 tmc_status tmc_loopy_plan_destroy(tmc_loopy_plan plan);
 

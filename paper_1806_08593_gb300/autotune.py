@@ -1,21 +1,31 @@
-"""Autotuner of the persistent edge launches (tensor-core plans).
+"""Autotuner of the tensor-core launches.
 
-The tcgen05 tile is fixed by the M = 128 instruction shape; what varies with the batch is
-the order in which the persistent CTAs take the edge tiles (tmc_plan_set_schedule).  The
-tuner times one forward + backward step of the plan under every order on the caller's
-inputs (CUDA events, after warm-up) and keeps the fastest.  Results are cached in a JSON
-file keyed by GPU name, driver version and a digest of the problem's shape (instances,
-trees, K, d, obs, precision), so a later process with the same shapes skips the timing.
+Tree / chain plans (tmc_plan_set_tuning): the tcgen05 tile is fixed by the M = 128
+instruction shape and the S-chunk width by tensor memory, so the knobs are those of the
+persistent edge launches:
+  schedule       the order in which the CTAs take the edge tiles of a level (0, 1, 2)
+  prologue_lead  chunks before the end of a forward item at which the next item's prologue
+                 enters the ring and the MMA order (1, 2, 3)
+  grid           CTAs per persistent launch (one per SM, or three quarters of that)
+Loopy plans (tmc_loopy_plan_set_tile): the N tile of the message products (128 or 256).
+The tuner times the plan's own step on the caller's inputs under every combination (CUDA
+events, after warm-up), keeps the fastest, and caches the choice in a JSON file keyed by GPU
+name, driver version and a digest of the problem's shape, so a later process with the same
+shapes skips the timing.  No knob changes the arithmetic of a tile: every choice gives the same
+log P_TMC bit for bit (tree plans) or up to the order of FP32 sums within a tile (loopy).
 """
 from __future__ import annotations
 
 import hashlib
+import itertools
 import json
 import os
 
 import numpy as np
 
 SCHEDULES = (0, 1, 2)
+PROLOGUE_LEADS = (1, 2, 3)
+KEY_VERSION = "v2"  # the knob set; entries written by another knob set are not reused
 DEFAULT_CACHE = os.environ.get("TMC_AUTOTUNE_CACHE",
                                os.path.join(os.path.expanduser("~"), ".cache", "tmc_gb300_autotune.json"))
 GRADS = ("dq_mean", "dq_logstd", "dW", "dbias", "dC")
@@ -25,7 +35,10 @@ def problem_key(p, precision: str) -> str:
     h = hashlib.sha1()
     for a in (p.n, p.parent, p.K, p.d, p.obs):
         h.update(np.ascontiguousarray(a, dtype=np.int32).tobytes())
-    h.update(("%d|%s" % (int(p.shared), precision)).encode())
+    for a in (p.Kn, p.dn):
+        if a is not None:
+            h.update(np.ascontiguousarray(a, dtype=np.int32).tobytes())
+    h.update(("%d|%s|%d" % (int(p.shared), precision, int(p.q_A is not None))).encode())
     return h.hexdigest()[:16]
 
 
@@ -42,50 +55,97 @@ def device_key() -> str:
     return "%s|%s" % (name, drv)
 
 
-def _time_step(plan, t, out, g, reps=5, warm=2):
+def _events_ms(fn, reps=5, warm=2):
     import torch
     for _ in range(warm):
-        plan.forward(t, out=out)
-        plan.backward(t, out=g, want=GRADS)
+        fn()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
-        plan.forward(t, out=out)
-        plan.backward(t, out=g, want=GRADS)
+        fn()
     e1.record()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
 
 
-def autotune(plan, p, t, cache_path: str | None = DEFAULT_CACHE, force: bool = False) -> dict:
-    """Chooses the persistent work order for ``plan`` (problem ``p``, device inputs ``t``)."""
-    import torch
-    key = device_key() + "|" + problem_key(p, plan.precision)
-    cache = {}
+def _load(cache_path):
     if cache_path and os.path.exists(cache_path):
         try:
-            cache = json.load(open(cache_path))
+            return json.load(open(cache_path))
         except (OSError, ValueError):
-            cache = {}
+            pass
+    return {}
+
+
+def _store(cache_path, cache):
+    if not cache_path:
+        return
+    os.makedirs(os.path.dirname(cache_path) or ".", exist_ok=True)
+    tmp = cache_path + ".%d.tmp" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1)
+    os.replace(tmp, cache_path)
+
+
+def grid_choices() -> tuple:
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return (0, (3 * sms) // 4)
+
+
+def apply(plan, choice: dict):
+    for k in ("schedule", "prologue_lead", "grid"):
+        plan.set_tuning(k, choice[k])
+
+
+def autotune(plan, p, t, cache_path: str | None = DEFAULT_CACHE, force: bool = False) -> dict:
+    """Chooses the persistent-launch knobs of ``plan`` (problem ``p``, device inputs ``t``)
+    by timing one forward + parameter-gradient step per combination."""
+    import torch
+    key = "%s|%s|%s" % (KEY_VERSION, device_key(), problem_key(p, plan.precision))
+    cache = _load(cache_path)
     if not force and key in cache:
-        plan.set_schedule(cache[key]["schedule"])
+        apply(plan, cache[key])
         return dict(cache[key], cached=True)
     out = torch.empty(p.B, dtype=torch.float64, device=t["eps"].device)
     src = {"dq_mean": "q_mean", "dq_logstd": "q_logstd", "dW": "W", "dbias": "bias", "dC": "C"}
     g = {k: torch.empty_like(t[src[k]]) for k in GRADS}
+
+    def step():
+        plan.forward(t, out=out)
+        plan.backward(t, out=g, want=GRADS)
+
     times = {}
-    for s in SCHEDULES:
-        plan.set_schedule(s)
-        times[s] = _time_step(plan, t, out, g)
+    for s, lead, grid in itertools.product(SCHEDULES, PROLOGUE_LEADS, grid_choices()):
+        apply(plan, {"schedule": s, "prologue_lead": lead, "grid": grid})
+        times["%d/%d/%d" % (s, lead, grid)] = _events_ms(step)
     best = min(times, key=times.get)
-    plan.set_schedule(best)
-    res = {"schedule": int(best), "ms": {str(k): v for k, v in times.items()}}
-    if cache_path:
-        cache[key] = res
-        os.makedirs(os.path.dirname(cache_path) or ".", exist_ok=True)
-        tmp = cache_path + ".%d.tmp" % os.getpid()
-        with open(tmp, "w") as f:
-            json.dump(cache, f, indent=1)
-        os.replace(tmp, cache_path)
+    s, lead, grid = (int(v) for v in best.split("/"))
+    res = {"schedule": s, "prologue_lead": lead, "grid": grid, "ms": times,
+           "spread": max(times.values()) / min(times.values()) - 1.0}
+    apply(plan, res)
+    cache[key] = res
+    _store(cache_path, cache)
+    return dict(res, cached=False)
+
+
+def autotune_loopy(plan, p, t, cache_path: str | None = DEFAULT_CACHE, force: bool = False) -> dict:
+    """Chooses the N tile of a loopy plan's message products by timing its forward."""
+    import torch
+    key = "%s|%s|loopy|%d|%d|%d|%d|%d" % (KEY_VERSION, device_key(), p.B, p.K, p.d, p.obs, int(p.shared))
+    cache = _load(cache_path)
+    if not force and key in cache:
+        plan.set_tile(cache[key]["n_tile"])
+        return dict(cache[key], cached=True)
+    out = torch.empty(p.B, dtype=torch.float64, device=t["eps"].device)
+    times = {}
+    for n_tile in ((128, 256) if p.K > 128 else (128,)):
+        plan.set_tile(n_tile)
+        times[str(n_tile)] = _events_ms(lambda: plan.forward(t, out=out))
+    best = int(min(times, key=times.get))
+    plan.set_tile(best)
+    res = {"n_tile": best, "ms": times, "spread": max(times.values()) / min(times.values()) - 1.0}
+    cache[key] = res
+    _store(cache_path, cache)
     return dict(res, cached=False)

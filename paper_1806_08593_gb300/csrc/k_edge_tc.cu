@@ -680,7 +680,7 @@ struct FwdCfg {
 
 // Chunk of an item before which the next item's prologue operands and mu~ MMAs are placed
 // in the ring / MMA order: two chunks before the end, so they overlap this item's tail.
-__host__ __device__ constexpr int pro_slot(int nch) { return nch >= 2 ? nch - 2 : 0; }
+__host__ __device__ constexpr int pro_slot(int nch, int lead) { return nch >= lead ? nch - lead : 0; }
 // Items of a persistent edge launch are claimed from a counter in list order, which is
 // dependency order: every item an item depends on was claimed earlier by a running CTA, so the
 // launch progresses however many of its CTAs are resident.  -1 once the list is exhausted.
@@ -709,7 +709,7 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, vol
 template <int DP>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     k_edge_fwd_tc(Dev D, TcDev T, const Tile* __restrict__ tiles, int ntiles, int* __restrict__ done,
-                  int* __restrict__ claim, int ncb, int cbk,
+                  int* __restrict__ claim, int lead, int ncb, int cbk,
                   const __grid_constant__ CUtensorMap mZH, const __grid_constant__ CUtensorMap mZL,
                   const __grid_constant__ CUtensorMap mWH, const __grid_constant__ CUtensorMap mWL) {
   using C = FwdCfg<DP>;
@@ -823,7 +823,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           tma_prefetch_l2_2d(&mZL, b * 64, (int)(nd.off_nk + t.row0));
         }
         for (int c = 0; ok && c < nch; ++c) {
-          if (c == pro_slot(nch) && nxt >= 0) ok = load_pro(nxt);
+          if (c == pro_slot(nch, lead) && nxt >= 0) ok = load_pro(nxt);
           ok = ok && load_use(&mZH, &mZL, (int)(nd.off_nk + c * kRows));
         }
         // the next item becomes current; claim the one after it
@@ -881,7 +881,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         if (!mbar_wait_ab(&a_full, (uint32_t)(it & 1), abort)) { ok = false; break; }
         for (int c = 0; c < nch; ++c, ++gu, ++gc) {
           // the next item's mu~ between this item's chunks, where the tensor pipe has room
-          if (c == pro_slot(nch) && has_next && !mu_mmas(it + 1)) { ok = false; break; }
+          if (c == pro_slot(nch, lead) && has_next && !mu_mmas(it + 1)) { ok = false; break; }
           const int s = (int)(gu % NS), b = (int)(gc & 1);
           if (!mbar_wait_ab(&full[s], (uint32_t)((gu / NS) & 1), abort)) { ok = false; break; }
           if (gc >= 2 && !mbar_wait_ab(&sfree[b], (uint32_t)(((gc >> 1) + 1) & 1), abort)) { ok = false; break; }
@@ -2927,6 +2927,11 @@ void launch_obs(TcWork& w, const Dev& D, cudaStream_t s) {
   }
 }
 
+// CTAs of a persistent edge launch of n items: one per SM, or the tuned count
+static int edge_grid(const TcWork& w, int n) {
+  int g = w.grid_ctas > 0 && w.grid_ctas < w.num_sms ? w.grid_ctas : w.num_sms;
+  return n < g ? n : g;
+}
 void launch_edge_fwd(TcWork& w, const Dev& D, cudaStream_t s) {
   cudaMemsetAsync(w.t.done, 0, (size_t)w.num_nodes * sizeof(int), s);
   cudaMemsetAsync(w.t.claim, 0, 2 * sizeof(int), s);
@@ -2935,17 +2940,17 @@ void launch_edge_fwd(TcWork& w, const Dev& D, cudaStream_t s) {
   for (int c = 0; c < 2; ++c) {
     const int b = w.it_b[0][c], n = w.it_e[0][c] - b;
     if (!n) continue;
-    const int grid = n < w.num_sms ? n : w.num_sms;
+    const int grid = edge_grid(w, n);
     int ncb = 1, cbk = 0;
     if (c == 0) {
       const size_t sm = fwd_smem<64>(w.maxK, &ncb, &cbk);
-      k_edge_fwd_tc<64><<<grid, kThreadsTc, sm, s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.t.claim + c, ncb, cbk,
-                                                      w.mZH, w.mZL,
+      k_edge_fwd_tc<64><<<grid, kThreadsTc, sm, s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.t.claim + c, w.pro_lead,
+                                                      ncb, cbk, w.mZH, w.mZL,
                                                       w.mWH, w.mWL);
     } else {
       const size_t sm = fwd_smem<128>(w.maxK, &ncb, &cbk);
-      k_edge_fwd_tc<128><<<grid, kThreadsTc, sm, s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.t.claim + c, ncb, cbk,
-                                                       w.mZH, w.mZL,
+      k_edge_fwd_tc<128><<<grid, kThreadsTc, sm, s>>>(D, w.t, w.d_tiles + b, n, w.t.done, w.t.claim + c, w.pro_lead,
+                                                       ncb, cbk, w.mZH, w.mZL,
                                                        w.mWH, w.mWL);
     }
   }
@@ -2960,7 +2965,7 @@ void launch_edge_bwd(TcWork& w, const Dev& D, cudaStream_t s) {
   for (int c = 0; c < 2; ++c) {
     const int b = w.it_b[1][c], n = w.it_e[1][c] - b;
     if (!n) continue;
-    const int grid = n < w.num_sms ? n : w.num_sms;
+    const int grid = edge_grid(w, n);
     if (c == 0)
       k_edge_bwd_tc<64, false><<<grid, kThreadsTc, bwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done,
                                                                      w.t.claim + 2 + c, w.mZH, w.mZL,
@@ -2978,7 +2983,7 @@ void launch_edge_rows(TcWork& w, const Dev& D, cudaStream_t s) {
   for (int c = 0; c < 2; ++c) {
     const int b = w.it_b[2][c], n = w.it_e[2][c] - b;
     if (!n) continue;
-    const int grid = n < w.num_sms ? n : w.num_sms;
+    const int grid = edge_grid(w, n);
     if (c == 0)
       k_edge_bwd_tc<64, true><<<grid, kThreadsTc, bwd_smem<64>(w.maxK), s>>>(D, w.t, w.d_tiles + b, n, w.t.done,
                                                                            w.t.claim + 4 + c, w.mZH,

@@ -728,6 +728,7 @@ struct tmc_loopy_plan_s {
   cudaEvent_t ev[TMC_LOOPY_STAGE_COUNT + 1] = {};
   double stage_ms[TMC_LOOPY_STAGE_COUNT] = {};
   int num_sms = 148;
+  int n_tile = 0;  // message GEMM N tile: 0 automatic, 128 or 256
   long long calls = 0;
 };
 
@@ -873,7 +874,8 @@ tmc_status tmc_loopy_log_marginal(tmc_loopy_plan p, const tmc_inputs* in, double
       g.alpha[m] = 1.f;
       g.out_off[m] = m;
     }
-    if (K > 128) {  // 128 x 256 tiles: a third fewer operand bytes per flop
+    const bool wide = p->n_tile == 256 || (p->n_tile == 0 && K > 128);
+    if (wide) {  // 128 x 256 tiles: a third fewer operand bytes per flop
       const int grid = std::min(nt * ((K + 255) / 256) * B * 2, p->num_sms);
       k_gemm_split<1, 256><<<grid, kGemmThreads, gemm_smem(1), s>>>(g, p->d_err, p->mEh, p->mEl, p->mEh256, p->mEl256,
                                                               p->mMsg);
@@ -916,6 +918,12 @@ tmc_status tmc_loopy_profile(tmc_loopy_plan p, int enable, double* stage_ms, lon
   p->calls = 0;
   if (cudaMemset(p->d_nfix, 0, 2 * sizeof(int)) != cudaSuccess) return TMC_ERR_CUDA;
   return (err & kErrTimeout) ? TMC_ERR_TIMEOUT : TMC_OK;
+}
+
+tmc_status tmc_loopy_plan_set_tile(tmc_loopy_plan p, int n_tile) {
+  if (!p || (n_tile != 0 && n_tile != 128 && n_tile != 256)) return TMC_ERR_INVALID_ARG;
+  p->n_tile = n_tile;
+  return TMC_OK;
 }
 
 tmc_status tmc_loopy_plan_destroy(tmc_loopy_plan p) {

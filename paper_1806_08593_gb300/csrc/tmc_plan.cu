@@ -661,6 +661,33 @@ tmc_status tmc_plan_get_schedule(tmc_plan p, int* schedule) {
   return TMC_OK;
 }
 
+tmc_status tmc_plan_set_tuning(tmc_plan p, int knob, int value) {
+  if (!p) return TMC_ERR_INVALID_ARG;
+  if (!(p->precision == TMC_PREC_FP16_TC)) return TMC_ERR_UNSUPPORTED;
+  switch (knob) {
+    case TMC_TUNE_SCHEDULE: return tc::set_schedule(p->tcw, p->nodes, value);
+    case TMC_TUNE_PROLOGUE_LEAD:
+      if (value < 1 || value > 3) return TMC_ERR_INVALID_ARG;
+      p->tcw.pro_lead = value;
+      return TMC_OK;
+    case TMC_TUNE_GRID:
+      if (value < 0) return TMC_ERR_INVALID_ARG;
+      p->tcw.grid_ctas = value;
+      return TMC_OK;
+    default: return TMC_ERR_INVALID_ARG;
+  }
+}
+
+tmc_status tmc_plan_get_tuning(tmc_plan p, int knob, int* value) {
+  if (!p || !value) return TMC_ERR_INVALID_ARG;
+  switch (knob) {
+    case TMC_TUNE_SCHEDULE: *value = p->tcw.schedule; return TMC_OK;
+    case TMC_TUNE_PROLOGUE_LEAD: *value = p->tcw.pro_lead; return TMC_OK;
+    case TMC_TUNE_GRID: *value = p->tcw.grid_ctas; return TMC_OK;
+    default: return TMC_ERR_INVALID_ARG;
+  }
+}
+
 tmc_status tmc_plan_instance_times(tmc_plan p, double* fwd_us, double* bwd_us) {
   if (!p || (!fwd_us && !bwd_us)) return TMC_ERR_INVALID_ARG;
   if (!(p->precision == TMC_PREC_FP16_TC)) return TMC_ERR_UNSUPPORTED;

@@ -94,6 +94,8 @@ struct TcWork {
   int* d_nonroot = nullptr;
   int maxK = 0;
   int schedule = 0;               // work order of the persistent launches (see build_items)
+  int pro_lead = 2;               // forward: chunks before an item's end for the next prologue
+  int grid_ctas = 0;              // CTAs per persistent edge launch (0: one per SM)
   int stall_node = -1;            // fault injection: node whose forward tiles are left out
   int maxdp = 128;                // widest padded latent dimension (64 or 128)
   int n_pack_w = 0;               // leading non-root nodes whose W is packed

@@ -28,7 +28,9 @@ EXPORTS = ["tmc_plan_create", "tmc_log_marginal", "tmc_backward", "tmc_plan_sync
            "tmc_profile_enable", "tmc_profile_read", "tmc_log_marginal_noalloc",
            "tmc_plan_instance_times", "tmc_plan_set_schedule", "tmc_plan_get_schedule",
            "tmc_plan_set_wait_limit", "tmc_loopy_plan_create", "tmc_loopy_log_marginal",
-           "tmc_loopy_profile", "tmc_loopy_plan_destroy"]
+           "tmc_loopy_profile", "tmc_loopy_plan_destroy", "tmc_plan_set_tuning", "tmc_plan_get_tuning",
+           "tmc_loopy_plan_set_tile"]
+TUNING = {"schedule": 0, "prologue_lead": 1, "grid": 2}
 
 
 class TMCError(RuntimeError):
@@ -97,6 +99,11 @@ def load_library(path: str = LIB_PATH):
     lib.tmc_plan_get_schedule.restype = ctypes.c_int
     lib.tmc_plan_set_wait_limit.argtypes = [P, ctypes.c_longlong]
     lib.tmc_plan_set_wait_limit.restype = ctypes.c_int
+    lib.tmc_plan_set_tuning.argtypes = [P, ctypes.c_int, ctypes.c_int]
+    lib.tmc_plan_get_tuning.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    lib.tmc_loopy_plan_set_tile.argtypes = [P, ctypes.c_int]
+    for f in ("tmc_plan_set_tuning", "tmc_plan_get_tuning", "tmc_loopy_plan_set_tile"):
+        getattr(lib, f).restype = ctypes.c_int
     lib.tmc_loopy_plan_create.argtypes = [ctypes.POINTER(LoopyDesc), ctypes.POINTER(P)]
     lib.tmc_loopy_log_marginal.argtypes = [P, ctypes.POINTER(Inputs), P, V]
     lib.tmc_loopy_profile.argtypes = [P, ctypes.c_int, P, ctypes.POINTER(ctypes.c_longlong),
@@ -222,6 +229,15 @@ class Plan:
     def set_wait_limit(self, cycles: int):
         _check(self._lib.tmc_plan_set_wait_limit(self._h, int(cycles)), "tmc_plan_set_wait_limit")
 
+    def set_tuning(self, knob: str, value: int):
+        """One tuning knob of a tensor-core plan (TUNING: schedule, prologue_lead, grid)."""
+        _check(self._lib.tmc_plan_set_tuning(self._h, TUNING[knob], int(value)), "tmc_plan_set_tuning")
+
+    def get_tuning(self, knob: str) -> int:
+        v = ctypes.c_int()
+        _check(self._lib.tmc_plan_get_tuning(self._h, TUNING[knob], ctypes.byref(v)), "tmc_plan_get_tuning")
+        return int(v.value)
+
     def get_schedule(self) -> int:
         v = ctypes.c_int()
         _check(self._lib.tmc_plan_get_schedule(self._h, ctypes.byref(v)), "tmc_plan_get_schedule")
@@ -283,6 +299,10 @@ class LoopyPlan:
         return out
 
     STAGES = ["prep", "factor", "exp", "message", "final"]
+
+    def set_tile(self, n_tile: int):
+        """N tile of the message products: 128, 256, or 0 (automatic)."""
+        _check(self._lib.tmc_loopy_plan_set_tile(self._h, int(n_tile)), "tmc_loopy_plan_set_tile")
 
     def profile(self, enable: bool = True) -> dict:
         """Summed stage times since the last call (ms, keyed by STAGES), the forward calls timed
