@@ -419,7 +419,7 @@ def time_plan_steps(p, precision, dev, steps, warmup):
 # (dram__bytes_read.sum + dram__bytes_write.sum) of chain n=3, K=1024, d=128, obs=256, B=64:
 # 1024 tiles per launch, forward 113.2 MB, adjoint 126.2 MB.  Scaled by the tiles of a launch;
 # only quoted for that K and d, and only while the kernels are the captured ones.
-TRAFFIC_PER_TILE = {("edge_fwd", 1024, 128): 115.0e6 / 1024, ("edge_bwd", 1024, 128): 126.5e6 / 1024}
+TRAFFIC_PER_TILE = {("edge_fwd", 1024, 128): 123.1e6 / 1024, ("edge_bwd", 1024, 128): 134.2e6 / 1024}
 
 
 def edge_tiles(p):
