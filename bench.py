@@ -32,7 +32,16 @@ sys.path.insert(0, ROOT)
 DEFAULT_WORKLOAD = "chain_n16_K1024_d128_B64"
 # A training step needs the gradients of every parameter of the model and the proposal.
 GRADS = ("dq_mean", "dq_logstd", "dW", "dbias", "dC")
-RESULT_GRADS = GRADS  # read back in the e2e leg
+GRAD_SRC = {"dq_mean": "q_mean", "dq_logstd": "q_logstd", "dW": "W", "dbias": "bias", "dC": "C",
+            "dq_A": "q_A"}
+
+
+def step_grads(p):
+    """The gradients of a training step: every model and proposal parameter (with a coupled
+    proposal its couplings A_i as well)."""
+    return GRADS + (("dq_A",) if p.q_A is not None else ())
+
+
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
 SM_MAX_MHZ = 2070.0
@@ -58,6 +67,16 @@ def make_workload(name):
         kv = dict(x.split("=") for x in name[5:].split(","))
         c = {k: int(v) for k, v in kv.items()}
         p = wl.star(c["N"], c["K"], c.get("d", 1), c.get("obs"), c.get("B", 1))
+        p.name = name
+        return p
+    if name.startswith("layered:"):  # the paper's five-layer widths 4/8/16/32/64 (per-latent d_i)
+        kv = dict(x.split("=") for x in name[8:].split(",") if x)
+        c = {k: int(v) for k, v in kv.items()}
+        p = wl.layered_chain([4, 8, 16, 32, 64], c.get("K", 20), c.get("obs", 96), c.get("B", 16384), seed=1)
+        p.name = name
+        return p
+    if name.startswith("coupled:"):  # the prior as a coupled (non-factorised) proposal
+        p = wl.couple_proposal(make_workload(name[8:]), "prior")
         p.name = name
         return p
     if name.startswith("chain:"):
@@ -179,20 +198,24 @@ def time_oracle_sample(p, target_s=15.0, max_inst=None):
     oracle.build()
     entries_per_inst = p.entries() / p.B
     n_inst, elapsed, done = 1, 0.0, 0
-    t_all = 0.0
+    t_all = wall = 0.0
     logp = []
     while True:
         idx = list(range(done, min(p.B, done + n_inst)))
         if not idx:
             break
+        t_sub = time.perf_counter()
         sub = oracle.subset(p, idx)
         t0 = time.perf_counter()
         g = oracle.grad(sub)
         dt = time.perf_counter() - t0
         logp.extend(g["log_phat"].tolist())
         t_all += dt
+        wall += time.perf_counter() - t_sub
         done += len(idx)
-        if t_all >= target_s or done >= p.B or (max_inst and done >= max_inst):
+        # the budget bounds the wall time as well: cutting a sample out of a large batch
+        # can cost more than the oracle itself on small instances
+        if t_all >= target_s or wall >= 2 * target_s or done >= p.B or (max_inst and done >= max_inst):
             break
         n_inst = max(1, int(len(idx) * min(4.0, (target_s - t_all) / max(dt, 1e-3))))
     return entries_per_inst * done / t_all, done, t_all, np.array(logp)
@@ -353,12 +376,21 @@ def loopy_leg(args, dev):
 # our arm
 # ---------------------------------------------------------------------------------------
 def algorithmic_flops(p, precision):
-    """Algorithmic FLOPs of the edge kernels per step (pairwise contractions, per edge with
-    K_p = K_i = K): forward 2*K^2*d (S = mu~ z~^T); adjoint 4*K^2*d (S recomputed, V = P z~_p).
-    The split-fp16 tensor-core path executes each S product as 3 MMAs; those extra MMAs are
-    not counted."""
-    e = (p.n.astype(np.int64) - 1) * p.K.astype(np.int64) ** 2 * p.d.astype(np.int64)
-    return {"edge_fwd": 2.0 * float(e.sum()), "edge_bwd": 4.0 * float(e.sum())}
+    """Algorithmic FLOPs of the edge kernels per step, per edge p -> i: forward 2*K_p*K_i*d_i
+    (S = mu~ z~^T); adjoint 2*K_p*K_i*(d_i + d_p) (S recomputed, V = P z~_p), i.e. 4*K^2*d for
+    uniform sizes.  The split-fp16 tensor-core path executes each S product as 3 MMAs; those
+    extra MMAs are not counted."""
+    Kn, dn = p.K_nodes().astype(np.int64), p.d_nodes().astype(np.int64)
+    fwd = bwd = 0.0
+    off = 0
+    for b in range(p.B):
+        par = p.parents_of(b)
+        for i in range(1, len(par)):
+            kk = float(Kn[off + par[i]] * Kn[off + i])
+            fwd += 2.0 * kk * dn[off + i]
+            bwd += 2.0 * kk * (dn[off + i] + dn[off + par[i]])
+        off += len(par)
+    return {"edge_fwd": fwd, "edge_bwd": bwd}
 
 
 def time_forward(p, precision, dev, steps, warmup):
@@ -393,17 +425,17 @@ def time_plan_steps(p, precision, dev, steps, warmup):
     plan = Plan.from_problem(p, precision)
     t = plan.to_device(p, dev)
     out = torch.empty(p.B, dtype=torch.float64, device=dev)
-    g = {k: torch.empty_like(t[{"dq_mean": "q_mean", "dq_logstd": "q_logstd", "dW": "W",
-                                 "dbias": "bias", "dC": "C"}[k]]) for k in GRADS}
+    want = step_grads(p)
+    g = {k: torch.empty_like(t[GRAD_SRC[k]]) for k in want}
     for _ in range(warmup):
         plan.forward(t, out=out)
-        plan.backward(t, out=g, want=GRADS)
+        plan.backward(t, out=g, want=want)
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(steps):
         plan.forward(t, out=out)
-        plan.backward(t, out=g, want=GRADS)
+        plan.backward(t, out=g, want=want)
     e1.record()
     torch.cuda.synchronize(dev)
     plan.sync_status()
@@ -453,13 +485,13 @@ def run_ours(args):
     plan = Plan.from_problem(p, args.precision)
     t = plan.to_device(p, dev)
     out_lp = torch.empty(p.B, dtype=torch.float64, device=dev)
-    grads = {k: torch.empty_like(t[{"dq_mean": "q_mean", "dq_logstd": "q_logstd",
-                                    "dW": "W", "dbias": "bias", "dC": "C"}[k]]) for k in GRADS}
+    GR = step_grads(p)
+    grads = {k: torch.empty_like(t[GRAD_SRC[k]]) for k in GR}
     stream = torch.cuda.current_stream(dev)
 
     def step():
         plan.forward(t, out=out_lp)
-        plan.backward(t, out=grads, want=GRADS)
+        plan.backward(t, out=grads, want=GR)
 
     tuned = None
     if args.autotune and args.precision == "fp16":
@@ -530,7 +562,7 @@ def run_ours(args):
     # so step i + 1's upload overlaps step i's kernels (as a serving loop would run them).
     host_in = {k: v.cpu().pin_memory() for k, v in t.items()}
     dev_in = [{k: torch.empty_like(v) for k, v in t.items()} for _ in range(2)]
-    host_out = {k: torch.empty(grads[k].shape, dtype=grads[k].dtype).pin_memory() for k in RESULT_GRADS}
+    host_out = {k: torch.empty(grads[k].shape, dtype=grads[k].dtype).pin_memory() for k in GR}
     host_lp = torch.empty(p.B, dtype=torch.float64).pin_memory()
     h2d = sum(v.numel() * v.element_size() for v in host_in.values())
     d2h = host_lp.numel() * 8 + sum(v.numel() * v.element_size() for v in host_out.values())
@@ -554,10 +586,10 @@ def run_ours(args):
                 upload(i + 1)
             stream.wait_event(uploaded[i % 2])
             plan.forward(dev_in[i % 2], out=out_lp)
-            plan.backward(dev_in[i % 2], out=grads, want=GRADS)
+            plan.backward(dev_in[i % 2], out=grads, want=GR)
             consumed[i % 2].record(stream)
             host_lp.copy_(out_lp, non_blocking=True)
-            for k in RESULT_GRADS:
+            for k in GR:
                 host_out[k].copy_(grads[k], non_blocking=True)
 
     e2e_run(2)
@@ -618,7 +650,7 @@ def run_ours(args):
     # ---- the same step with the per-sample gradients dz / deps as well -----------------
     sample_grads = None
     if args.precision == "fp16" and not args.no_sample_grads:
-        want = GRADS + ("dz", "deps")
+        want = GR + ("dz", "deps")
         gz = dict(grads)
         gz["dz"] = torch.empty_like(t["eps"])
         gz["deps"] = torch.empty_like(t["eps"])
@@ -686,7 +718,7 @@ def run_ours(args):
                    "cuda_graph": bool(args.graph),
                    "schedule": plan.get_schedule() if args.precision == "fp16" else None,
                    "autotune": tuned,
-                   "entries_per_step": entries, "grads": list(GRADS),
+                   "entries_per_step": entries, "grads": list(GR),
                    "l2": "inputs larger than L2 (eps %.0f MB per step)" % (p.eps.nbytes / 1e6),
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roof,

@@ -160,7 +160,8 @@ def subset(p, idx):
     """The sub-batch of instances ``idx`` of problem p (same flat layout)."""
     from paper_1806_08593_gb300.workload import Problem
     idx = list(idx)
-    sl = [p.slices(b) for b in idx]
+    every = p.slices_all(max(idx) + 1) if idx else []
+    sl = [every[b] for b in idx]
     cat = lambda key, name: np.concatenate([getattr(p, name)[s[key][0]:s[key][1]] for s in sl])
     kw = dict(n=p.n[idx].copy(), K=p.K[idx].copy(), d=p.d[idx].copy(), obs=p.obs[idx].copy(),
               parent=cat("parent", "parent"), eps=cat("eps", "eps"), q_mean=cat("q", "q_mean"),

@@ -132,23 +132,29 @@ class Problem:
 
     def slices(self, b: int) -> dict:
         """Slices of every flat array belonging to instance b."""
-        nl = [len(self.leaves_of(i)) for i in range(self.B)]
+        return self.slices_all(b + 1)[b]
+
+    def slices_all(self, upto: int | None = None) -> list[dict]:
+        """slices(b) of the instances b < upto (all by default), in one pass."""
+        upto = self.B if upto is None else upto
         eps = q = w = x = c = a = 0
-        out = {}
-        for i in range(b + 1):
+        outs = []
+        for i in range(upto):
             Kn, dn, dp = self.node_sizes(i)
-            dl = int(dn[self.leaves_of(i)[0]])
+            leaves = self.leaves_of(i)
+            dl = int(dn[leaves[0]])
             se, sq, sw = int(np.sum(Kn * dn)), int(np.sum(dn)), int(np.sum(dn * dp))
-            sx, sc = nl[i] * int(self.obs[i]), int(self.obs[i]) * dl
-            if i == b:
-                out = dict(eps=(eps, eps + se), q=(q, q + sq), x=(x, x + sx), A=(a, a + sw),
-                           parent=(int(np.sum(self.n[:b])), int(np.sum(self.n[:b + 1]))))
-                if self.shared:
-                    out.update(W=(0, self.W.size), bias=(0, self.bias.size), C=(0, self.C.size))
-                else:
-                    out.update(W=(w, w + sw), bias=(q, q + sq), C=(c, c + sc))
+            sx, sc = len(leaves) * int(self.obs[i]), int(self.obs[i]) * dl
+            n0 = int(np.sum(self.n[:i]))
+            out = dict(eps=(eps, eps + se), q=(q, q + sq), x=(x, x + sx), A=(a, a + sw),
+                       parent=(n0, n0 + int(self.n[i])))
+            if self.shared:
+                out.update(W=(0, self.W.size), bias=(0, self.bias.size), C=(0, self.C.size))
+            else:
+                out.update(W=(w, w + sw), bias=(q, q + sq), C=(c, c + sc))
+            outs.append(out)
             eps += se; q += sq; w += sw; x += sx; c += sc; a += sw
-        return out
+        return outs
 
 
 # ---------------------------------------------------------------------------------------
@@ -457,10 +463,11 @@ def couple_proposal(p: Problem, mode: str = "prior", alpha: float = 0.5) -> Prob
     import copy
     q = copy.deepcopy(p)
     A_l, m_l, ls_l = [], [], []
+    every = p.slices_all()
     for b in range(p.B):
         Kn, dn, dp = p.node_sizes(b)
         assert np.all(Kn == Kn[0]), "a coupled proposal here needs one K per instance"
-        s = p.slices(b)
+        s = every[b]
         par = p.parents_of(b)
         Wf = p.W[s["W"][0]:s["W"][1]].astype(np.float64)
         bf = p.bias[s["bias"][0]:s["bias"][1]].astype(np.float64)
