@@ -207,7 +207,7 @@ static_assert(4 * kRows * 64 * 2 >= 2 * kRows * 64 * 2 + 2 * kBox && 4 * kRows *
 // Persistent, warp-specialised sampler.  A tile is a node and up to sample_rows(d) of its
 // rows (32 KB of eps whatever d is).  Warp 0 is the producer: for each tile of the CTA it
 // reads the tile's node record, forms the per-dimension vectors (exp(logs), m - bias at the
-// root, c_i), and bulk-copies the tile's eps rows into a ring stage; warps 1..7 consume the
+// root, c_i), and bulk-copies the tile's eps rows into a ring stage; warps 1..8 consume the
 // stages: split z~ = exp(logs) eps into fp16 hi / lo rows and form the row sums.  Tiles whose
 // eps rows are not 16-byte aligned (d not a multiple of 4) are read from global memory by the
 // consumers instead.
@@ -217,7 +217,7 @@ static_assert(4 * kRows * 64 * 2 >= 2 * kRows * 64 * 2 + 2 * kBox && 4 * kRows *
 __host__ __device__ constexpr int sample_rows(int d) { return d > 64 ? 64 : d > 32 ? 128 : d > 16 ? 256 : 512; }
 constexpr int kSampleStage = 64 * kTcMaxD * 4;  // bytes of one eps stage (= rows x d x 4 at most)
 constexpr int kSampleNS = 3;                    // ring stages
-constexpr int kSampleConsumers = 7;             // consumer warps
+constexpr int kSampleConsumers = 8;             // consumer warps (64 rows at d = 128: two full passes)
 
 struct __align__(16) SampleStage {  // 16-byte aligned: the vectors are read as float4
   float std_[kTcMaxD], off[kTcMaxD], c[kTcMaxD];
@@ -307,7 +307,8 @@ __device__ __forceinline__ bool sample_stage(const Dev& D, const TcDev& T, const
   return bad;
 }
 
-__global__ void __launch_bounds__(256) k_sample_tc(Dev D, TcDev T, const Tile* __restrict__ tiles, int ntiles) {
+constexpr int kSampleThreads = 32 * (1 + kSampleConsumers);
+__global__ void __launch_bounds__(kSampleThreads, 2) k_sample_tc(Dev D, TcDev T, const Tile* __restrict__ tiles, int ntiles) {
   extern __shared__ __align__(128) unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 63) & ~(uintptr_t)63);
   float* buf = reinterpret_cast<float*>(sm);                                        // [NS][stage]
@@ -324,22 +325,31 @@ __global__ void __launch_bounds__(256) k_sample_tc(Dev D, TcDev T, const Tile* _
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
     // ------------------------------------------------------------------ producer
+    // tiles blockIdx.x, + gridDim.x, ...; the next tile's record, node and proposal vectors
+    // are loaded right after the current tile's copy is issued, so their latency overlaps the
+    // wait for the next free stage
     int n = 0;
     bool ok = true;
-    for (int item = blockIdx.x; item < ntiles; item += gridDim.x, ++n) {
-      const int s = n % kSampleNS, fill = n / kSampleNS;
-      if (fill >= 1 && !mbar_wait(&empty[s], (fill - 1) & 1)) { ok = false; break; }
-      const Tile t = tiles[item];
-      const NodeInfo nd = D.nodes[t.node];
-      const bool root = nd.parent < 0;
-      float lsv[4], ofv[4], ccv[4];  // every load before the first store
+    Tile t{};
+    NodeInfo nd{};
+    float lsv[4], ofv[4], ccv[4];
+    auto fetch = [&](int item) {
+      t = tiles[item];
+      nd = D.nodes[t.node];
+      const bool rt = nd.parent < 0;
 #pragma unroll
       for (int x = 0; x < 4; ++x) {
         const int j = lane + 32 * x;
         lsv[x] = j < nd.d ? __ldg(D.q_logstd + nd.off_q + j) : 0.f;
-        ofv[x] = (root && j < nd.d) ? __ldg(D.q_mean + nd.off_q + j) - __ldg(D.bias + nd.off_bias + j) : 0.f;
-        ccv[x] = (root || j >= nd.d) ? 0.f : __ldg(T.cvec + (long long)t.node * kLdp + j);
+        ofv[x] = (rt && j < nd.d) ? __ldg(D.q_mean + nd.off_q + j) - __ldg(D.bias + nd.off_bias + j) : 0.f;
+        ccv[x] = (rt || j >= nd.d) ? 0.f : __ldg(T.cvec + (long long)t.node * kLdp + j);
       }
+    };
+    if (blockIdx.x < ntiles) fetch(blockIdx.x);
+    for (int item = blockIdx.x; item < ntiles; item += gridDim.x, ++n) {
+      const int s = n % kSampleNS, fill = n / kSampleNS;
+      if (fill >= 1 && !mbar_wait(&empty[s], (fill - 1) & 1)) { ok = false; break; }
+      const bool root = nd.parent < 0;
 #pragma unroll
       for (int x = 0; x < 4; ++x) {
         const int j = lane + 32 * x;
@@ -370,6 +380,8 @@ __global__ void __launch_bounds__(256) k_sample_tc(Dev D, TcDev T, const Tile* _
           mbar_arrive(&full[s]);  // release of the stage record; the rows are read from global
         }
       }
+      __syncwarp();  // every lane has read this tile's record before it is replaced
+      if (item + (int)gridDim.x < ntiles) fetch(item + gridDim.x);
     }
     if (!ok && lane == 0) set_timeout(D);
     // the last fills still in flight land before the CTA exits
@@ -2089,10 +2101,12 @@ __global__ void __launch_bounds__(kMoThreads, 1)
 
 // Zeroes the dp x d block of every node in a [node][128][128] array (the part the readers use:
 // G_i = sum pi z~_p z~_i^T is d_parent x d_i; the adjoint launch adds its tile partials into it).
+// Rows are zeroed in whole float4s (up to three entries past d, inside the 128-float row).
 __global__ void __launch_bounds__(256) k_zero_dd(Dev D, float* __restrict__ base) {
-  const int d = D.nodes[blockIdx.x].d, dq = D.nodes[blockIdx.x].dp;
-  float* blk = base + (long long)blockIdx.x * kLdp * kLdp;
-  for (int i = threadIdx.x; i < dq * d; i += blockDim.x) blk[(i / d) * kLdp + i % d] = 0.f;
+  const int d4 = (D.nodes[blockIdx.x].d + 3) >> 2, dq = D.nodes[blockIdx.x].dp;
+  float4* blk = reinterpret_cast<float4*>(base + (long long)blockIdx.x * kLdp * kLdp);
+  for (int i = threadIdx.x; i < dq * d4; i += blockDim.x)
+    blk[(i / d4) * (kLdp / 4) + i % d4] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // =======================================================================================
@@ -2234,10 +2248,187 @@ __global__ void __launch_bounds__(kThreads) k_asm_edge_mat(Dev D, TcDev T, const
   }
 }
 
+// ---- shared parameters: every instance uses the same W_c ---------------------------------
+// The W_c M2_p term of dW_c is linear in M2_p, so it is applied once to the instance sum:
+//   dW_c = sum_b go_b [(G_c,b^T - c_c,b zbar_p,b^T) / var + db'_c,b m_p,b^T]
+//          - W_c (sum_b go_b M2_p,b) / var
+// and the parent-side sum of each instance needs only O(d^2) work given W_c^T W_c (symmetric,
+// as is M2_p):
+//   diag(W_c^T D_c,b)[j] = (sum_a W[a][j] (G^T[a][j] - c_a zbar_p[j]) - sum_l (W^T W)[l][j] M2_p[l][j]) / var
+// so no d x d x d product is formed per instance.  Positions are the local indices 1 .. n-1
+// of the instances' common graph (local index = global id in instance 0).
+constexpr int kAsmInst = 8;  // instances per group of k_asm_shared (group sums in a fixed order)
+
+// W_c^T W_c per position.  Grid: (position, 64 x 64 tile (2 x 2)).
+__global__ void __launch_bounds__(kThreads) k_wtw(Dev D, TcDev T) {
+  __shared__ TileSmemDeep sm;
+  const int i = blockIdx.x + 1;
+  const NodeInfo nd = D.nodes[i];
+  const int d = nd.d, dq = nd.dp;  // W_c is d x dq
+  const int l0 = (blockIdx.y >> 1) * kTile, j0 = (blockIdx.y & 1) * kTile;
+  if (l0 >= dq || j0 >= dq) return;
+  const float* W = D.W + nd.off_W;
+  float acc[4][4];
+  zero_acc(acc);
+  // acc[l][j] = sum_a W[a][l] W[a][j]
+  tile_gemm_deep<false, false>(acc, W + l0, dq, min(kTile, dq - l0), W + j0, dq, min(kTile, dq - j0), d, sm);
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  float* out = T.WtW + (long long)i * kLdp * kLdp;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int l = l0 + ty * 4 + a, j = j0 + tx * 4 + b;
+      if (l < dq && j < dq) out[(long long)l * kLdp + j] = acc[a][b];
+    }
+}
+
+// Grid: (position, 64 x 64 tile (2 x 2), instance group of kAsmInst).  Per instance of the
+// group: the child- and parent-side sums of the edge (tgC, tgP) and, summed over the group's
+// instances in order, the dW terms without W_c M2_p (into Ppart) and go M2_p / var (into
+// Spart).  Thread (ty, tx) holds rows a0 + 4 ty .. +3 (child index a of W_c and G_c^T, and
+// parent index l of M2_p) and columns b0 + 4 tx .. +3 (parent index j).  The instances'
+// offsets are read once into shared memory, only the edge's own rows and columns are loaded,
+// and the column sums of every instance are formed after one barrier at the end.
+__global__ void __launch_bounds__(kThreads, 2) k_asm_shared(Dev D, TcDev T, long long nW, long long nS) {
+  __shared__ float colpart[kAsmInst][16][kTile + 1];
+  __shared__ int s_n0[kAsmInst];
+  __shared__ long long s_offq[kAsmInst];
+  __shared__ float s_go[kAsmInst];
+  const int i = blockIdx.x + 1;
+  const NodeInfo nd = D.nodes[i];
+  const int d = nd.d, dq = nd.dp, pi = nd.parent;  // local index of the parent = its id in instance 0
+  const int a0 = (blockIdx.y >> 1) * kTile, b0 = (blockIdx.y & 1) * kTile;
+  if (b0 >= dq || a0 >= max(d, dq)) return;
+  const int bb = blockIdx.z * kAsmInst, nb = min(D.num_inst - bb, kAsmInst);
+  if (threadIdx.x < nb) {
+    const int b = bb + threadIdx.x, n0 = D.insts[b].node0;
+    s_n0[threadIdx.x] = n0;
+    s_offq[threadIdx.x] = D.nodes[n0 + pi].off_q;
+    s_go[threadIdx.x] = D.grad_out ? (float)D.grad_out[b] : 1.f;
+  }
+  const float iv = D.inv_var;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  const int ar = a0 + ty * 4, jc = b0 + tx * 4;  // first row / column of the thread
+  const float* W = D.W + nd.off_W;
+  const float* WtW = T.WtW + (long long)i * kLdp * kLdp;
+  float wv[4][4], ww[4][4], pw[4][4], s2[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int a = ar + r, j = jc + c;
+      wv[r][c] = (a < d && j < dq) ? __ldg(W + (long long)a * dq + j) : 0.f;
+      ww[r][c] = (a < dq && j < dq) ? __ldg(WtW + (long long)a * kLdp + j) : 0.f;
+      pw[r][c] = 0.f;
+      s2[r][c] = 0.f;
+    }
+  // loads stay inside the nodes' 128 x 128 blocks; entries outside the edge's sizes are
+  // not used (the workspace there is not initialised)
+  const bool g_rows = ar < d, m_cols = jc < dq;
+  __syncthreads();
+  for (int u = 0; u < nb; ++u) {
+    const int gc = s_n0[u] + i, gp = s_n0[u] + pi;
+    const float go = s_go[u];
+    const float* Gc = T.G + (long long)gc * kLdp * kLdp;
+    const float* M2p = T.M2 + (long long)gp * kLdp * kLdp;
+    // G^T[a][j] = G[j][a]: four consecutive a per column j; M2_p[l][j]: four consecutive j per row l
+    float4 gq[4], mq[4];
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      gq[c] = (g_rows && jc + c < dq) ? __ldg(reinterpret_cast<const float4*>(Gc + (long long)(jc + c) * kLdp + ar)) : z4;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      mq[r] = (m_cols && ar + r < dq) ? __ldg(reinterpret_cast<const float4*>(M2p + (long long)(ar + r) * kLdp + jc)) : z4;
+    const float4 ca4 = g_rows ? __ldg(reinterpret_cast<const float4*>(T.cvec + (long long)gc * kLdp + ar)) : z4;
+    const float4 db4 = g_rows ? __ldg(reinterpret_cast<const float4*>(T.sgC + (long long)gc * kLdp + ar)) : z4;
+    const float4 zp4 = m_cols ? __ldg(reinterpret_cast<const float4*>(T.zbar + (long long)gp * kLdp + jc)) : z4;
+    float mpv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) mpv[k] = jc + k < dq ? __ldg(D.q_mean + s_offq[u] + jc + k) : 0.f;
+    const float cav[4] = {ca4.x, ca4.y, ca4.z, ca4.w};
+    const float dbv[4] = {-db4.x, -db4.y, -db4.z, -db4.w};  // db'[a] = -sgC, from k_asm_edge_vec
+    const float zpv[4] = {zp4.x, zp4.y, zp4.z, zp4.w};
+    const float giv = go * iv;
+    float wrow[4] = {0.f, 0.f, 0.f, 0.f}, tcol[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int a = ar + r, j = jc + c;
+        const float gt = (a < d && j < dq) ? (&gq[c].x)[r] : 0.f;
+        const float m2 = (a < dq && j < dq) ? (&mq[r].x)[c] : 0.f;
+        const float ca = a < d ? cav[r] : 0.f, db = a < d ? dbv[r] : 0.f;
+        const float zp = j < dq ? zpv[c] : 0.f;
+        const float dp = (gt - ca * zp) * iv;
+        pw[r][c] = fmaf(go, fmaf(db, mpv[c], dp), pw[r][c]);
+        s2[r][c] = fmaf(giv, m2, s2[r][c]);
+        wrow[r] = fmaf(wv[r][c], gt, wrow[r]);
+        tcol[c] = fmaf(wv[r][c], dp, fmaf(-ww[r][c] * iv, m2, tcol[c]));
+      }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {  // the 16 threads of one ty sit in one half-warp
+      float v = wrow[r];
+      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      // two column tiles per row into a zeroed entry: the two additions commute exactly
+      if (tx == 0 && ar + r < d) atomicAdd(T.tgC + (long long)gc * kLdp + ar + r, v * iv);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) colpart[u][ty][tx * 4 + c] = tcol[c];
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < nb * kTile; x += kThreads) {
+    const int u = x / kTile, col = x % kTile;
+    if (b0 + col >= dq) continue;
+    float v = 0.f;
+    for (int r = 0; r < 16; ++r) v += colpart[u][r][col];
+    atomicAdd(T.tgP + (long long)(s_n0[u] + i) * kLdp + b0 + col, v);  // two row tiles, as above
+  }
+  float* pp = T.Ppart + (long long)blockIdx.z * nW + nd.off_W;
+  float* sp = T.Spart + (long long)blockIdx.z * nS + nd.off_S;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int a = ar + r, j = jc + c;
+      if (j >= dq) continue;
+      if (a < d) pp[(long long)a * dq + j] = pw[r][c];
+      if (a < dq) sp[(long long)a * dq + j] = s2[r][c];
+    }
+}
+
+// dW_c = P_c - W_c S2_c.  Grid: (position, 64 x 64 tile (2 x 2)).
+__global__ void __launch_bounds__(kThreads) k_shared_dw(Dev D, TcDev T) {
+  __shared__ TileSmemDeep sm;
+  const int i = blockIdx.x + 1;
+  const NodeInfo nd = D.nodes[i];
+  const int d = nd.d, dq = nd.dp;
+  const int a0 = (blockIdx.y >> 1) * kTile, b0 = (blockIdx.y & 1) * kTile;
+  if (a0 >= d || b0 >= dq) return;
+  const float* W = D.W + nd.off_W;
+  const float* S2 = T.S2 + nd.off_S;
+  float acc[4][4];
+  zero_acc(acc);
+  // acc[a][j] = sum_l W[a][l] S2[l][j]
+  tile_gemm_deep<true, false>(acc, W + (long long)a0 * dq, dq, min(kTile, d - a0), S2 + b0, dq,
+                         min(kTile, dq - b0), dq, sm);
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int a = a0 + ty * 4 + r, j = b0 + tx * 4 + c;
+      if (a >= d || j >= dq) continue;
+      const long long e = nd.off_W + (long long)a * dq + j;
+      D.dW[e] = T.P[e] - acc[r][c];
+    }
+}
+
 // C^T C per distinct observation matrix (one for shared parameters, else one per instance).
 // Grid: (matrix, 64x64 tile (2 x 2), 64-row slab of C); slabs add into the zeroed C^T C.
 __global__ void __launch_bounds__(kThreads) k_ctc(Dev D, TcDev T) {
-  __shared__ TileSmem sm;
+  __shared__ TileSmemDeep sm;
   const InstInfo in = D.insts[blockIdx.x];
   const int d = in.d, obs = in.obs;
   const int a0 = (blockIdx.y >> 1) * kTile, b0 = (blockIdx.y & 1) * kTile, o0 = blockIdx.z * kTile;
@@ -2245,7 +2436,7 @@ __global__ void __launch_bounds__(kThreads) k_ctc(Dev D, TcDev T) {
   const float* C = D.C + in.off_C + (long long)o0 * d;
   float acc[4][4];
   zero_acc(acc);
-  tile_gemm<false, false>(acc, C + a0, d, min(kTile, d - a0), C + b0, d, min(kTile, d - b0),
+  tile_gemm_deep<false, false>(acc, C + a0, d, min(kTile, d - a0), C + b0, d, min(kTile, d - b0),
                           min(kTile, obs - o0), sm);
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
   float* out = T.CtC + (long long)blockIdx.x * kLdp * kLdp;
@@ -2414,7 +2605,11 @@ __global__ void __launch_bounds__(kThreads) k_leaf_S(Dev D, TcDev T) {
   const int a0 = (blockIdx.y >> 1) * kTile, b0 = (blockIdx.y & 1) * kTile;
   if (a0 >= d || b0 >= d) return;
   const int rt = min(kTile, d - a0), ct = min(kTile, d - b0), np = rt * ct;
-  float* S = T.S + (long long)blockIdx.x * kLdp * kLdp;
+  // shared C: go_b S_b / obs_var, packed d x d (its instance sum multiplies C once); else S_b
+  const bool sh = D.shared != 0;
+  const long long ld = sh ? d : kLdp;
+  const float sc = sh ? (D.grad_out ? (float)D.grad_out[blockIdx.x] : 1.f) * D.inv_obs_var : 1.f;
+  float* S = T.S + (long long)blockIdx.x * (sh ? (long long)d * d : (long long)kLdp * kLdp);
   if (np < kThreads) {
     const int G = kThreads / np, e = threadIdx.x % np, grp = threadIdx.x / np;
     const int a = a0 + e / ct, cc = b0 + e % ct;
@@ -2428,7 +2623,7 @@ __global__ void __launch_bounds__(kThreads) k_leaf_S(Dev D, TcDev T) {
     if (threadIdx.x < np) {
       float v = 0.f;
       for (int g = 0; g < G; ++g) v += part[g * np + threadIdx.x];
-      S[(long long)a * kLdp + cc] = v;
+      S[(long long)a * ld + cc] = sh ? v * sc : v;
     }
     return;
   }
@@ -2452,7 +2647,7 @@ __global__ void __launch_bounds__(kThreads) k_leaf_S(Dev D, TcDev T) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
     const int a = a0 + r0 + 4 * i;
-    if (a < d && b0 + c < d) S[(long long)a * kLdp + b0 + c] = acc[i];
+    if (a < d && b0 + c < d) S[(long long)a * ld + b0 + c] = sh ? acc[i] * sc : acc[i];
   }
 }
 
@@ -2460,7 +2655,7 @@ __global__ void __launch_bounds__(kThreads) k_leaf_S(Dev D, TcDev T) {
 // X = sum_leaves x~ (zbar + m)^T is split over the leaves like k_leaf_S when the tile has
 // fewer entries than threads.
 __global__ void __launch_bounds__(kThreads) k_asm_dC(Dev D, TcDev T) {
-  __shared__ TileSmem sm;
+  __shared__ TileSmemDeep sm;
   __shared__ float part[kThreads];
   const InstInfo in = D.insts[blockIdx.x];
   const int d = in.d, obs = in.obs;
@@ -2472,9 +2667,10 @@ __global__ void __launch_bounds__(kThreads) k_asm_dC(Dev D, TcDev T) {
   const float* C = D.C + in.off_C;
   float acc[4][4];
   zero_acc(acc);
-  // acc = C[o0.., :] S[:, c0..]
-  tile_gemm<true, false>(acc, C + (long long)o0 * d, d, rows, T.S + (long long)blockIdx.x * kLdp * kLdp + c0,
-                         kLdp, cols, d, sm);
+  // acc = C[o0.., :] S[:, c0..]; a shared C multiplies the instance sum of S once (k_shared_dC)
+  if (!D.shared)
+    tile_gemm_deep<true, false>(acc, C + (long long)o0 * d, d, rows, T.S + (long long)blockIdx.x * kLdp * kLdp + c0,
+                           kLdp, cols, d, sm);
   float X[4][4];
   zero_acc(X);
   const int np = rows * cols;
@@ -2534,6 +2730,28 @@ __global__ void __launch_bounds__(kThreads) k_asm_dC(Dev D, TcDev T) {
       const float v = go * (X[i][j] - acc[i][j]) * D.inv_obs_var;
       if (D.shared) { if (D.pC) D.pC[in.off_pC + (long long)o * d + c] = v; }
       else if (D.dC) D.dC[in.off_C + (long long)o * d + c] = v;
+    }
+}
+
+// Shared C: dC = sum_b go_b X_b / obs_var (already in dC) - C Ssum, Ssum = sum_b go_b S_b / obs_var.
+// Grid: (64-row tile of observation dims, 64-col tile of latent dims).
+__global__ void __launch_bounds__(kThreads) k_shared_dC(Dev D, TcDev T) {
+  __shared__ TileSmemDeep sm;
+  const InstInfo in = D.insts[0];
+  const int d = in.d, obs = in.obs;
+  const int o0 = blockIdx.x * kTile, c0 = blockIdx.y * kTile;
+  if (o0 >= obs || c0 >= d) return;
+  const int rows = min(kTile, obs - o0), cols = min(kTile, d - c0);
+  float acc[4][4];
+  zero_acc(acc);
+  tile_gemm_deep<true, false>(acc, D.C + (long long)o0 * d, d, rows, T.Ssum + c0, d, cols, d, sm);
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int o = o0 + ty * 4 + i, c = c0 + tx * 4 + j;
+      if (o < obs && c < d) D.dC[(long long)o * d + c] -= acc[i][j];
     }
 }
 
@@ -2705,6 +2923,20 @@ void workspace_layout(TcWork& w, const std::vector<NodeInfo>& nodes, long long n
   subs.push_back({(void**)&w.t.sgP, nv});
   subs.push_back({(void**)&w.t.tgP, nv});
   subs.push_back({(void**)&w.t.CtC, (size_t)(w.t.shared ? 1 : w.num_inst) * kLdp * kLdp * sizeof(float)});
+  if (w.t.shared) {  // shared parameters: W^T W per position, the instance-group partials and sums
+    w.asm_groups = (w.num_inst + kAsmInst - 1) / kAsmInst;
+    w.shared_rootW = (long long)nodes[0].d * nodes[0].d;
+    const size_t nw = (size_t)w.shared_nW * sizeof(float), ns = (size_t)w.shared_nS * sizeof(float);
+    subs.push_back({(void**)&w.t.WtW, (size_t)slots * kLdp * kLdp * sizeof(float)});
+    subs.push_back({(void**)&w.t.P, nw});
+    subs.push_back({(void**)&w.t.S2, ns});
+    subs.push_back({(void**)&w.t.Ppart, nw * w.asm_groups});
+    subs.push_back({(void**)&w.t.Spart, ns * w.asm_groups});
+    for (const NodeInfo& nd : nodes)  // the leaves' common dimension and the observation size
+      if (nd.b == 0 && nd.leaf_slot >= 0) w.leaf_d = nd.d;
+    w.obs0 = nodes[0].obs;
+    subs.push_back({(void**)&w.t.Ssum, (size_t)w.leaf_d * w.leaf_d * sizeof(float)});
+  }
   w.num_c = w.t.shared ? 1 : w.num_inst;
   long long cr = 0;
   for (const NodeInfo& nd : nodes)
@@ -2717,7 +2949,9 @@ void workspace_layout(TcWork& w, const std::vector<NodeInfo>& nodes, long long n
   for (const NodeInfo& nd : nodes)
     if (nd.leaf_slot >= 0) nx = std::max(nx, nd.off_x + nd.obs);
   subs.push_back({(void**)&w.t.xs, (size_t)std::max(nx, 1ll) * sizeof(float)});
-  subs.push_back({(void**)&w.t.S, (size_t)w.num_inst * kLdp * kLdp * sizeof(float)});
+  // per instance: the leaves' M2 + zbar m^T sum ([128][128]; shared C: packed d x d)
+  subs.push_back({(void**)&w.t.S, (size_t)w.num_inst * (w.t.shared ? (size_t)w.leaf_d * w.leaf_d
+                                                                    : (size_t)kLdp * kLdp) * sizeof(float)});
   subs.push_back({(void**)&w.t.VH, pk});
   subs.push_back({(void**)&w.t.VL, pk});
   subs.push_back({(void**)&w.t.EH, pk});
@@ -2900,7 +3134,7 @@ void release(TcWork& w) {
 
 void launch_sample(TcWork& w, const Dev& D, cudaStream_t s) {
   const int n = (int)w.sample_tiles.size();
-  if (n) k_sample_tc<<<std::min(n, 2 * w.num_sms), 256, kSampleSmem, s>>>(D, w.t, w.d_sample_tiles, n);
+  if (n) k_sample_tc<<<std::min(n, 2 * w.num_sms), kSampleThreads, kSampleSmem, s>>>(D, w.t, w.d_sample_tiles, n);
 }
 
 void launch_pack(TcWork& w, const Dev& D, cudaStream_t s) {
@@ -3017,12 +3251,31 @@ void launch_unpack_grads(TcWork& w, const Dev& D, cudaStream_t s) {
   cudaMemsetAsync(w.t.tgC, 0, (size_t)w.num_nodes * kLdp * sizeof(float), s);
   if (nr) {
     k_asm_edge_vec<<<nr, 128, 0, s>>>(D, w.t, w.d_nonroot);
-    k_asm_edge_mat<<<dim3(nr, w.maxdp > 64 ? 4 : 1), kThreads, 0, s>>>(D, w.t, w.d_nonroot);
+    const int ty = w.maxdp > 64 ? 4 : 1;
+    if (D.shared) {  // one W_c per position: no d x d x d product per instance
+      const int np = w.num_slots - 1;
+      k_wtw<<<dim3(np, ty), kThreads, 0, s>>>(D, w.t);
+      k_asm_shared<<<dim3(np, ty, w.asm_groups), kThreads, 0, s>>>(D, w.t, w.shared_nW, w.shared_nS);
+      if (D.dW) {
+        const long long nw = w.shared_nW - w.shared_rootW;
+        rows_sum(w.t.Ppart + w.shared_rootW, w.asm_groups, nw, w.shared_nW, w.t.P + w.shared_rootW, D.rsum, s);
+        rows_sum(w.t.Spart, w.asm_groups, w.shared_nS, w.shared_nS, w.t.S2, D.rsum, s);
+        k_shared_dw<<<dim3(np, ty), kThreads, 0, s>>>(D, w.t);
+      }
+    } else {
+      k_asm_edge_mat<<<dim3(nr, ty), kThreads, 0, s>>>(D, w.t, w.d_nonroot);
+    }
   }
   if (w.maxdp > 64) k_asm_node<4><<<D.num_nodes, 4 * kTcMaxD, 0, s>>>(D, w.t);
   else k_asm_node<1><<<D.num_nodes, kTcMaxD, 0, s>>>(D, w.t);
   k_leaf_S<<<dim3(D.num_inst, w.maxdp > 64 ? 4 : 1), kThreads, 0, s>>>(D, w.t);
   k_asm_dC<<<dim3(D.num_inst, (w.maxobs + kTile - 1) / kTile, w.maxdp / kTile), kThreads, 0, s>>>(D, w.t);
+  if (D.shared && D.dC) {  // one product of C with the instance sum of S
+    const long long nC = (long long)w.obs0 * w.leaf_d, nS = (long long)w.leaf_d * w.leaf_d;
+    rows_sum(D.pC, w.num_inst, nC, nC, D.dC, D.rsum, s);
+    rows_sum(w.t.S, w.num_inst, nS, nS, w.t.Ssum, D.rsum, s);
+    k_shared_dC<<<dim3((w.obs0 + kTile - 1) / kTile, (w.leaf_d + kTile - 1) / kTile), kThreads, 0, s>>>(D, w.t);
+  }
 }
 
 }  // namespace tc

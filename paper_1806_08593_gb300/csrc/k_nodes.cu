@@ -611,27 +611,22 @@ __global__ void __launch_bounds__(kThreads) k_param_dC(Dev D) {
   }
 }
 
-// Shared parameters: dW, dbias, dC = sum over instances of the partials (fixed order).
-// nW, nb, nC: one instance's sizes; the root's block of W (the first rootW entries) is zero.
-__global__ void k_shared_reduce(Dev D, long long nW, long long nb, long long nC, long long rootW) {
-  const long long total = nW + nb + nC;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    float s = 0.f;
-    if (e < nW) {
-      if (e >= rootW)
-        for (int b = 0; b < D.num_inst; ++b) s += D.pW[(long long)b * nW + e];
-      if (D.dW) D.dW[e] = s;
-    } else if (e < nW + nb) {
-      const long long f = e - nW;
-      for (int b = 0; b < D.num_inst; ++b) s += D.pbias[(long long)b * nb + f];
-      if (D.dbias) D.dbias[f] = s;
-    } else {
-      const long long f = e - nW - nb;
-      for (int b = 0; b < D.num_inst; ++b) s += D.pC[(long long)b * nC + f];
-      if (D.dC) D.dC[f] = s;
-    }
+// One level of rows_sum: out[g * E + e] = sum of rows g * kRowChunk .. +kRowChunk - 1 (in order).
+// Eight rows' loads are issued before they are added.
+__global__ void __launch_bounds__(256) k_rows_sum(const float* __restrict__ in, long long R, long long E,
+                                                  long long stride, float* __restrict__ out) {
+  const long long e = blockIdx.x * 256ll + threadIdx.x;
+  if (e >= E) return;
+  const long long r0 = (long long)blockIdx.y * kRowChunk, r1 = min(R, r0 + kRowChunk);
+  float s = 0.f;
+  for (long long r = r0; r < r1; r += 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = r + u < r1 ? __ldg(in + (r + u) * stride + e) : 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += v[u];
   }
+  out[(long long)blockIdx.y * E + e] = s;
 }
 
 // ---- launchers ----------------------------------------------------------------------------
@@ -668,11 +663,38 @@ void launch_param_dC(const Dev& D, int maxd, int maxobs, cudaStream_t s) {
   k_param_dC<<<dim3(D.num_inst, (maxobs + kTile - 1) / kTile, (maxd + kTile - 1) / kTile), kThreads,
                kMaxD * sizeof(float), s>>>(D);
 }
+void rows_sum(const float* in, long long R, long long E, long long stride, float* out, float* scratch,
+              cudaStream_t s) {
+  if (E <= 0) return;
+  const unsigned ex = (unsigned)((E + 255) / 256);
+  const long long half = (R + kRowChunk - 1) / kRowChunk * E;
+  const float* src = in;
+  long long rows = R, ld = stride;
+  int ping = 0;
+  while (rows > kRowChunk) {  // one level: chunks of kRowChunk rows -> one row each
+    const long long g = (rows + kRowChunk - 1) / kRowChunk;
+    float* dst = scratch + ping * half;
+    k_rows_sum<<<dim3(ex, (unsigned)g), 256, 0, s>>>(src, rows, E, ld, dst);
+    src = dst;
+    rows = g;
+    ld = E;
+    ping ^= 1;
+  }
+  k_rows_sum<<<dim3(ex, 1), 256, 0, s>>>(src, rows, E, ld, out);
+}
+
+// Shared parameters: dW, dbias, dC = sum over instances of the per-instance partials (rows_sum,
+// fixed order); the root's block of W (the first rootW entries) is zero.  tc_done: dW past the
+// root block and dC were written by the tensor-core path's own kernels.
 void launch_shared_reduce(const Dev& D, long long nW, long long nb, long long nC, long long rootW,
-                          cudaStream_t s) {
-  const long long total = nW + nb + nC;
-  const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
-  k_shared_reduce<<<blocks, 256, 0, s>>>(D, nW, nb, nC, rootW);
+                          bool tc_done, cudaStream_t s) {
+  const long long B = D.num_inst;
+  if (D.dW) {
+    if (rootW) cudaMemsetAsync(D.dW, 0, sizeof(float) * rootW, s);
+    if (!tc_done && nW > rootW) rows_sum(D.pW + rootW, B, nW - rootW, nW, D.dW + rootW, D.rsum, s);
+  }
+  if (D.dbias && nb) rows_sum(D.pbias, B, nb, nb, D.dbias, D.rsum, s);
+  if (D.dC && nC && !tc_done) rows_sum(D.pC, B, nC, nC, D.dC, D.rsum, s);
 }
 void launch_root_bias(const Dev&, cudaStream_t) {}
 

@@ -98,6 +98,63 @@ __device__ __forceinline__ void tile_gemm(float acc[4][4], const float* __restri
   }
 }
 
+// The same product in 64-deep slices (short contractions, L <= a few hundred): each slice is
+// one round of loads (16 values per operand and thread), the next slice's loads are issued
+// before the current one is multiplied, so a 128-deep product waits on global memory twice
+// instead of eight times.
+constexpr int kDeep = 64;
+constexpr int kDeepVals = kDeep * kTile / kThreads;
+struct TileSmemDeep {
+  float a[kDeep * kLd];
+  float b[kDeep * kLd];
+};
+template <bool TRANS>
+__device__ __forceinline__ void fetch_deep(float (&r)[kDeepVals], const float* __restrict__ src, long long ld,
+                                           int mlim, int l0, int llim) {
+#pragma unroll
+  for (int x = 0; x < kDeepVals; ++x) {
+    const int e = threadIdx.x + x * kThreads;
+    int l, m;
+    if (TRANS) { m = e >> 6; l = e & 63; }
+    else       { l = e >> 6; m = e & 63; }
+    const int gl = l0 + l;
+    r[x] = (m < mlim && gl < llim) ? (TRANS ? src[(long long)m * ld + gl] : src[(long long)gl * ld + m]) : 0.f;
+  }
+}
+template <bool TRANS>
+__device__ __forceinline__ void store_deep(float* s, const float (&r)[kDeepVals]) {
+#pragma unroll
+  for (int x = 0; x < kDeepVals; ++x) {
+    const int e = threadIdx.x + x * kThreads;
+    int l, m;
+    if (TRANS) { m = e >> 6; l = e & 63; }
+    else       { l = e >> 6; m = e & 63; }
+    s[l * kLd + m] = r[x];
+  }
+}
+template <bool A_TRANS, bool B_TRANS>
+__device__ __forceinline__ void tile_gemm_deep(float acc[4][4], const float* __restrict__ A,
+                                               long long lda, int ma, const float* __restrict__ B,
+                                               long long ldb, int nb, int L, TileSmemDeep& sm) {
+  float ra[kDeepVals], rb[kDeepVals];
+  if (L > 0) {
+    fetch_deep<A_TRANS>(ra, A, lda, ma, 0, L);
+    fetch_deep<B_TRANS>(rb, B, ldb, nb, 0, L);
+  }
+  for (int l0 = 0; l0 < L; l0 += kDeep) {
+    store_deep<A_TRANS>(sm.a, ra);
+    store_deep<B_TRANS>(sm.b, rb);
+    __syncthreads();
+    if (l0 + kDeep < L) {
+      fetch_deep<A_TRANS>(ra, A, lda, ma, l0 + kDeep, L);
+      fetch_deep<B_TRANS>(rb, B, ldb, nb, l0 + kDeep, L);
+    }
+#pragma unroll
+    for (int q = 0; q < kDeep / kSlice; ++q) slice_fma(acc, sm.a + q * kSlice * kLd, sm.b + q * kSlice * kLd);
+    __syncthreads();
+  }
+}
+
 __device__ __forceinline__ void zero_acc(float acc[4][4]) {
 #pragma unroll
   for (int i = 0; i < 4; ++i)

@@ -36,6 +36,8 @@ struct NodeInfo {
   long long off_x;     // start of this leaf's observation ([obs]) in x (leaves only)
   long long off_pW;    // start of this node's block in the per-(instance, node) dW partials
   long long off_A;     // start of A_i ([d][dp]) in q_A / dq_A (per instance, like unshared W)
+  long long off_S;     // start of this latent's dp x dp block in one instance's packed [dp x dp]
+                       // blocks of the non-root latents (the root's block is empty)
 };
 
 struct InstInfo {
@@ -84,6 +86,7 @@ struct Dev {
   float* pW;      // per-(instance, node) dW partials  (shared params only)
   float* pbias;   // per-(instance, node) dbias partials (shared params only)
   float* pC;      // per-instance dC partials (shared params only)
+  float* rsum;    // scratch of the row sums (rows_sum), shared parameters only
   int* err;       // device error word
   long long wait_limit;   // clock cycles a cross-CTA dependency wait polls before giving up
   // coupled proposals (sample k of a latent drawn given its parent's sample k)
@@ -128,9 +131,20 @@ void launch_node_grad(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t 
 void launch_node_reduce(const Dev& D, cudaStream_t s);
 void launch_param_dW(const Dev& D, const int* nonroot, int n_nonroot, int maxd, cudaStream_t s);
 void launch_param_dC(const Dev& D, int maxd, int maxobs, cudaStream_t s);
-// nW, nb, nC: one instance's W, bias, C sizes; rootW: its unused root block of W
+// out[e] = sum over rows r < R of in[r * stride + e], e < E: rows in order within chunks of
+// kRowChunk, chunk sums in order (a tree with a fixed shape: the result does not depend on the
+// launch).  scratch: rows_sum_scratch(R, E) floats.
+constexpr int kRowChunk = 64;
+inline long long rows_sum_scratch(long long R, long long E) {
+  return R > kRowChunk ? 2 * ((R + kRowChunk - 1) / kRowChunk) * E : 0;
+}
+void rows_sum(const float* in, long long R, long long E, long long stride, float* out, float* scratch,
+              cudaStream_t s);
+// nW, nb, nC: one instance's W, bias, C sizes; rootW: its unused root block of W; tc_done: dW
+// past the root block and dC are already written (the tensor-core path), the root block of dW
+// is zeroed and dbias reduced
 void launch_shared_reduce(const Dev& D, long long nW, long long nb, long long nC, long long rootW,
-                          cudaStream_t s);
+                          bool tc_done, cudaStream_t s);
 void launch_root_bias(const Dev& D, cudaStream_t s);
 // coupled proposals (k_couple.cu)
 void launch_couple_fwd(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s);

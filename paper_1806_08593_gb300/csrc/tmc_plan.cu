@@ -38,6 +38,8 @@ struct tmc_plan_s {
   int coupled = 0;      // coupled (non-factorised) proposal
   bool ragged = false;  // some instance has a different K or d from latent to latent
   long long shared_nW = 0, shared_nb = 0, shared_nC = 0, shared_rootW = 0;  // one instance's parameter sizes
+  long long shared_nS = 0;  // one instance's packed dp x dp blocks of the non-root latents
+  long long shared_nL2 = 0; // the leaves' dimension squared (the instance sum of the leaf moments)
   int root_fanout = 0;  // most children of any instance's root
   long long tot_nk = 0, tot_nkd = 0, tot_q = 0, tot_W = 0;
 
@@ -209,7 +211,7 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
     const long long iW = p->shared ? 0 : off_W, ib = p->shared ? 0 : off_bias,
                     iC = p->shared ? 0 : off_C;
     int leaves = 0;
-    long long e = 0, q = 0, w = 0, kd = 0;
+    long long e = 0, q = 0, w = 0, kd = 0, sq = 0;
     for (int i = 0; i < n; ++i) {
       NodeInfo nd{};
       nd.b = b;
@@ -237,6 +239,8 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
       nd.off_x = off_x + (long long)(nd.leaf_slot >= 0 ? nd.leaf_slot : 0) * obs;
       nd.off_pW = off_pW + w;
       nd.off_A = off_pW + w;  // the couplings are per instance, laid out like unshared W
+      nd.off_S = sq;
+      if (i) sq += (long long)nd.dp * nd.dp;
       p->nodes.push_back(nd);
       p->maxlevel = std::max(p->maxlevel, level[i]);
       e += (long long)Kv[i] * dv[i];
@@ -261,6 +265,8 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
       p->shared_nb = q;
       p->shared_nC = (long long)obs * dl;
       p->shared_rootW = (long long)dv[0] * dv[0];
+      p->shared_nS = sq;
+      p->shared_nL2 = (long long)dl * dl;
     }
     poff += n;
     off_nk += (long long)n * Kmax;
@@ -360,12 +366,19 @@ tmc_status alloc_device(tmc_plan p) {
   if (cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) return TMC_ERR_CUDA;
 
   const long long nk = p->tot_nk, nkd = p->tot_nkd, G = (long long)p->nodes.size();
-  const long long nW = p->shared ? (long long)p->B * p->shared_nW : 0;
+  // per-instance dW partials: the FP32 path with shared parameters (the tensor-core path sums
+  // its dW terms per instance group itself)
+  const long long nW = (p->shared && p->precision != TMC_PREC_FP16_TC) ? (long long)p->B * p->shared_nW : 0;
   const long long nb = p->shared ? (long long)p->B * p->shared_nb : 0;
   const long long nC = p->shared ? (long long)p->B * p->shared_nC : 0;
   // layout: 256-byte aligned sub-buffers
   struct Sub { void** dst; size_t bytes; };
-  float *zt, *mut, *zn, *mun, *u, *beta, *lam, *q, *nodemax, *dmu, *gz, *pW, *pbias, *pC, *fac;
+  float *zt, *mut, *zn, *mun, *u, *beta, *lam, *q, *nodemax, *dmu, *gz, *pW, *pbias, *pC, *fac, *rsum;
+  // row-sum scratch: B instances (or fewer instance groups) of one instance's largest block
+  const long long nrs =
+      p->shared ? rows_sum_scratch(p->B, std::max(std::max(std::max(p->shared_nW, p->shared_nS), p->shared_nL2),
+                                                  std::max(p->shared_nb, p->shared_nC)))
+                : 0;
   double *nodeconst, *root_part;
   const bool tc_plan = p->precision == TMC_PREC_FP16_TC;
   // FP32-path sample vectors (unused on the tc path, except T and G of coupled proposals, kept
@@ -383,13 +396,15 @@ tmc_status alloc_device(tmc_plan p) {
       {(void**)&lam, sizeof(float) * nk},      {(void**)&q, sizeof(float) * nk},
       {(void**)&nodemax, sizeof(float) * G},   {(void**)&nodeconst, sizeof(double) * G},
       {(void**)&pW, sizeof(float) * nW},       {(void**)&pbias, sizeof(float) * nb},
-      {(void**)&pC, sizeof(float) * nC},
+      {(void**)&pC, sizeof(float) * nC},       {(void**)&rsum, sizeof(float) * nrs},
       {(void**)&fac, sizeof(float) * p->fac_total},
       {(void**)&root_part, sizeof(double) * p->root_chunks.size() * p->maxK},
   };
   std::vector<tc::TcSub> tsubs;
   p->tcw.t.shared = p->shared;
   p->tcw.precision = p->precision;
+  p->tcw.shared_nW = p->shared_nW;
+  p->tcw.shared_nS = p->shared_nS;
   if (tc_plan) tc::workspace_layout(p->tcw, p->nodes, nk, nkd, tsubs);
   size_t total = 0;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -415,6 +430,7 @@ tmc_status alloc_device(tmc_plan p) {
   D.zt = zt; D.mut = mut; D.zn = zn; D.mun = mun; D.u = u; D.beta = beta; D.lam = lam; D.q = q;
   D.nodemax = nodemax; D.nodeconst = nodeconst; D.dmu = dmu; D.gz = gz;
   D.pW = nW ? pW : nullptr; D.pbias = nb ? pbias : nullptr; D.pC = nC ? pC : nullptr;
+  D.rsum = nrs ? rsum : nullptr;
   D.err = p->d_err;
   D.wait_limit = p->wait_limit;
   D.coupled = p->coupled;
@@ -625,7 +641,7 @@ tmc_status tmc_backward(tmc_plan p, const tmc_inputs* in, const double* grad_out
   }
   if (p->shared && (g->dW || g->dbias || g->dC))
     TRY(timed(p, TMC_KC_PARAM, s, [&] {
-      launch_shared_reduce(D, p->shared_nW, p->shared_nb, p->shared_nC, p->shared_rootW, s);
+      launch_shared_reduce(D, p->shared_nW, p->shared_nb, p->shared_nC, p->shared_rootW, tc_path, s);
     }));
   return TMC_OK;
 }

@@ -56,6 +56,12 @@ struct TcDev {
   float* sgP;
   float* tgP;
   float* CtC;                  // [1 or B][128*128]  C^T C per observation matrix
+  // shared parameters (one W_c per position = local node index): W_c^T W_c ([slot][128*128]);
+  // per instance group the partial sums of dW without the W_c M2_p term (Ppart, [group][W
+  // layout of one instance]) and of go M2_p / var (Spart, [group][packed dp x dp blocks,
+  // NodeInfo::off_S]); P and S2 = their sums over the groups
+  float *WtW, *P, *S2, *Ppart, *Spart;
+  float* Ssum;                 // shared C: sum_b go_b S_b / obs_var ([d][d], d = the leaves' dimension)
   __half *CH, *CL;             // [c_rows][128] split observation matrices, row = c_row[b] + o
   int* c_row;                  // [1 or B] first row of each observation matrix in CH / CL
   float* xs;                   // centred observations x - C m of the leaves (layout of x)
@@ -99,6 +105,10 @@ struct TcWork {
   int stall_node = -1;            // fault injection: node whose forward tiles are left out
   int maxdp = 128;                // widest padded latent dimension (64 or 128)
   int n_pack_w = 0;               // leading non-root nodes whose W is packed
+  // shared parameters: one instance's W size, its root block, its packed dp x dp blocks, and
+  // the instance groups of the gradient assembly
+  long long shared_nW = 0, shared_rootW = 0, shared_nS = 0;
+  int asm_groups = 0, leaf_d = 0, obs0 = 0;
   // observation term: split C rows and the 128-sample leaf tiles per d class
   long long c_rows = 0;
   int num_c = 0;                  // distinct observation matrices (1 when shared)
