@@ -373,6 +373,38 @@ def loopy_leg(args, dev):
 
 
 # ---------------------------------------------------------------------------------------
+# the other workloads of the hot path, one short timing each
+# ---------------------------------------------------------------------------------------
+WIDENING = (
+    ("trees", "512 uneven trees, per-instance models (config 5)"),
+    ("layered:B=16384,K=20", "five-layer chain, widths 4/8/16/32/64, K=20 (per-latent d_i)"),
+    ("coupled:chain_n16_K1024_d128_B64", "the bench chain with the prior as a coupled proposal"),
+    ("star:N=10000,K=128,d=1", "one root with 10^4 children (Section 3.1 toy at scale)"),
+)
+
+
+def widening_leg(args, dev):
+    """Each workload once: device time per training step (log P and every parameter gradient,
+    plain launches, default work order, CUDA events over 10 steps after 3 warm-up steps) and
+    |delta log P| to the oracle on its first and last instance."""
+    import oracle
+    oracle.build()
+    res = {}
+    for name, what in WIDENING:
+        p = make_workload(name)
+        ms, lp = time_plan_steps(p, args.precision, dev, steps=10, warmup=3)
+        idx = sorted({0, p.B - 1})
+        ref = oracle.log_marginal(oracle.subset(p, idx))
+        res[name] = {"what": what, "ms_per_step": ms, "value": p.entries() / (ms * 1e-3),
+                     "unit": "entries/s", "B": int(p.B), "entries_per_step": int(p.entries()),
+                     "grads": list(step_grads(p)),
+                     "max_abs_dlogp_vs_oracle": float(np.max(np.abs(lp[idx] - ref))),
+                     "instances_checked": idx}
+        del p
+    return res
+
+
+# ---------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------
 def algorithmic_flops(p, precision):
@@ -694,6 +726,9 @@ def run_ours(args):
     loopy = None
     if not args.no_loopy and ws == 1:
         loopy = loopy_leg(args, dev)
+    widening = None
+    if not args.no_widening and args.workload == DEFAULT_WORKLOAD and ws == 1 and args.precision == "fp16":
+        widening = widening_leg(args, dev)
 
     # ---- CPU baseline (oracle on a bounded sample) ------------------------------------
     cpu = None
@@ -736,6 +771,7 @@ def run_ours(args):
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "clocks": clk.summary(),
         "loopy": loopy,
+        "widening": widening,
     }
     print(json.dumps(line))
 
@@ -765,6 +801,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-loopy", action="store_true",
                     help="skip the loopy-graph (Fig. 1, matrix messages) leg")
+    ap.add_argument("--no-widening", action="store_true",
+                    help="skip the short timings of the other workloads (trees, layered, coupled, star)")
     ap.add_argument("--loopy-only", action="store_true",
                     help="run only the loopy-graph leg and print its JSON object")
     ap.add_argument("--loopy-workload", default=None,

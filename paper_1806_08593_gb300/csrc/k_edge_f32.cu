@@ -24,8 +24,16 @@ constexpr float kInvalid = -1.0e30f;
 // ---------------------------------------------------------------------------------------
 // Forward message of one edge, 64 parent samples per CTA.
 // ---------------------------------------------------------------------------------------
+// Latents with d <= kResD keep the CTA's 64 x d block of mu~ in shared memory for the whole
+// sweep over the child's samples (only the z~ tiles stream, in 64-deep slices); wider latents
+// stream both operands in 16-deep slices.
+constexpr int kResD = 128;
+__host__ __device__ constexpr int res_smem_floats(int maxK) {
+  return ((maxK + 3) & ~3) + (kResD + 2 * kDeep) * kLd;
+}
+
 __global__ void __launch_bounds__(kThreads) k_edge_fwd_f32(Dev D, const Tile* __restrict__ tiles) {
-  extern __shared__ float cb[];  // [K]: beta - |z~|^2 / (2 var)
+  extern __shared__ __align__(16) float cb[];  // [K]: beta - |z~|^2 / (2 var); then sa, sb
   __shared__ TileSmem sm;
   __shared__ float red[32];
   const Tile t = tiles[blockIdx.x];
@@ -59,13 +67,18 @@ __global__ void __launch_bounds__(kThreads) k_edge_fwd_f32(Dev D, const Tile* __
   const int rows = min(kTile, Kp - t.row0);
   const float* M = D.mut + nd.off_nkd + (long long)t.row0 * d;
   const float* Z = D.zt + nd.off_nkd;
+  const bool res = d <= kResD;
+  float* sa = cb + ((K + 3) & ~3);  // [kResD][kLd], then sb [kDeep][kLd]
+  float* sb = sa + kResD * kLd;
+  if (res) load_resident<true>(sa, M, d, rows, d);
   float rm[4], rs[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) { rm[a] = -INFINITY; rs[a] = 0.f; }
   for (int c0 = 0; c0 < K; c0 += kTile) {
     float acc[4][4];
     zero_acc(acc);
-    tile_gemm<true, true>(acc, M, d, rows, Z + (long long)c0 * d, d, min(kTile, K - c0), d, sm);
+    if (res) tile_gemm_resA<true>(acc, sa, Z + (long long)c0 * d, d, min(kTile, K - c0), d, sb);
+    else tile_gemm<true, true>(acc, M, d, rows, Z + (long long)c0 * d, d, min(kTile, K - c0), d, sm);
     float cv[4];
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
@@ -108,8 +121,8 @@ __device__ __forceinline__ float adj_row_bias(const Dev& D, const NodeInfo& nd, 
 // The d columns are covered 128 at a time (two 64-wide accumulators); wider d repeats
 // the sweep over k' per 128-column chunk.
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_edge_bwd_rows_f32(Dev D, const Tile* __restrict__ tiles) {
-  extern __shared__ float cb[];  // [K]: beta - |z~|^2 / (2 var)
+__global__ void __launch_bounds__(kThreads, 2) k_edge_bwd_rows_f32(Dev D, const Tile* __restrict__ tiles) {
+  extern __shared__ __align__(16) float cb[];  // [K]: beta - |z~|^2 / (2 var); then sa, sb, sb2
   __shared__ TileSmem sm;
   __shared__ float ps[kTile * kLd];  // pi tile stored [k'][k]
   const Tile t = tiles[blockIdx.x];
@@ -130,6 +143,11 @@ __global__ void __launch_bounds__(kThreads) k_edge_bwd_rows_f32(Dev D, const Til
   __syncthreads();
   const float* M = D.mut + nd.off_nkd + (long long)t.row0 * d;
   const float* Z = D.zt + nd.off_nkd;
+  const bool res = d <= kResD;
+  float* sa = cb + ((K + 3) & ~3);  // [kResD][kLd]: mu~ of the CTA's rows, resident
+  float* sb = sa + kResD * kLd;     // [kDeep][kLd] x 2: streamed z~ slices
+  float* sb2 = sb + kDeep * kLd;
+  if (res) load_resident<true>(sa, M, d, rows, d);
   for (int j0 = 0; j0 < d; j0 += 2 * kTile) {
     float o0[4][4], o1[4][4], rsum[4] = {0.f, 0.f, 0.f, 0.f};
     zero_acc(o0);
@@ -138,7 +156,8 @@ __global__ void __launch_bounds__(kThreads) k_edge_bwd_rows_f32(Dev D, const Til
       const int cols = min(kTile, K - c0);
       float acc[4][4];
       zero_acc(acc);
-      tile_gemm<true, true>(acc, M, d, rows, Z + (long long)c0 * d, d, cols, d, sm);
+      if (res) tile_gemm_resA<true>(acc, sa, Z + (long long)c0 * d, d, cols, d, sb);
+      else tile_gemm<true, true>(acc, M, d, rows, Z + (long long)c0 * d, d, cols, d, sm);
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const int c = c0 + tx * 4 + b;
@@ -150,16 +169,34 @@ __global__ void __launch_bounds__(kThreads) k_edge_bwd_rows_f32(Dev D, const Til
           ps[(tx * 4 + b) * kLd + ty * 4 + a] = p;
         }
       }
-      __syncthreads();
       // o[k][j] += sum_k' pi[k][k'] z~[k'][j]
-      for (int l0 = 0; l0 < cols; l0 += kSlice) {
-        const float* Zc = Z + (long long)c0 * d + j0;
-        load_slice<false>(sm.a, Zc, d, min(kTile, d - j0), l0, cols);
-        if (j0 + kTile < d) load_slice<false>(sm.b, Zc + kTile, d, min(kTile, d - j0 - kTile), l0, cols);
+      const float* Zc = Z + (long long)c0 * d + j0;
+      if (res) {  // the tile's 64 rows of z~ in one round of loads
+        float rv[kDeepVals];
+        fetch_deep<false>(rv, Zc, d, min(kTile, d - j0), 0, cols);
+        __syncthreads();  // the pi tile is written; the readers of sb are done
+        store_deep<false>(sb, rv);
+        if (j0 + kTile < d) {
+          fetch_deep<false>(rv, Zc + kTile, d, min(kTile, d - j0 - kTile), 0, cols);
+          store_deep<false>(sb2, rv);
+        }
         __syncthreads();
-        slice_fma(o0, ps + l0 * kLd, sm.a);
-        if (j0 + kTile < d) slice_fma(o1, ps + l0 * kLd, sm.b);
+        const int nq = (cols + kSlice - 1) / kSlice;
+        for (int q = 0; q < nq; ++q) {
+          slice_fma(o0, ps + q * kSlice * kLd, sb + q * kSlice * kLd);
+          if (j0 + kTile < d) slice_fma(o1, ps + q * kSlice * kLd, sb2 + q * kSlice * kLd);
+        }
+        __syncthreads();  // ps and sb are rewritten by the next tile
+      } else {
         __syncthreads();
+        for (int l0 = 0; l0 < cols; l0 += kSlice) {
+          load_slice<false>(sm.a, Zc, d, min(kTile, d - j0), l0, cols);
+          if (j0 + kTile < d) load_slice<false>(sm.b, Zc + kTile, d, min(kTile, d - j0 - kTile), l0, cols);
+          __syncthreads();
+          slice_fma(o0, ps + l0 * kLd, sm.a);
+          if (j0 + kTile < d) slice_fma(o1, ps + l0 * kLd, sm.b);
+          __syncthreads();
+        }
       }
     }
 #pragma unroll
@@ -183,8 +220,8 @@ __global__ void __launch_bounds__(kThreads) k_edge_bwd_rows_f32(Dev D, const Til
 // Adjoint, columns pass: CTA owns 64 child samples k'; writes q_i[k'] and the edge part of
 // gz_i[k'] (all d columns).
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_edge_bwd_cols_f32(Dev D, const Tile* __restrict__ tiles) {
-  extern __shared__ float rb[];  // [K]: row bias per parent sample k
+__global__ void __launch_bounds__(kThreads, 2) k_edge_bwd_cols_f32(Dev D, const Tile* __restrict__ tiles) {
+  extern __shared__ __align__(16) float rb[];  // [Kp]: row bias per parent sample k; then sa, sb, sb2
   __shared__ TileSmem sm;
   __shared__ float ps[kTile * kLd];  // pi^T tile stored [k][k']
   const Tile t = tiles[blockIdx.x];
@@ -204,6 +241,11 @@ __global__ void __launch_bounds__(kThreads) k_edge_bwd_cols_f32(Dev D, const Til
   __syncthreads();
   const float* Zo = D.zt + nd.off_nkd + (long long)t.row0 * d;
   const float* M = D.mut + nd.off_nkd;
+  const bool res = d <= kResD;
+  float* sa = rb + ((Kp + 3) & ~3);  // [kResD][kLd]: z~ of the CTA's child samples, resident
+  float* sb = sa + kResD * kLd;      // [kDeep][kLd] x 2: streamed mu~ slices
+  float* sb2 = sb + kDeep * kLd;
+  if (res) load_resident<true>(sa, Zo, d, cols, d);
   for (int j0 = 0; j0 < d; j0 += 2 * kTile) {
     float o0[4][4], o1[4][4], qsum[4] = {0.f, 0.f, 0.f, 0.f};
     zero_acc(o0);
@@ -212,7 +254,8 @@ __global__ void __launch_bounds__(kThreads) k_edge_bwd_cols_f32(Dev D, const Til
       const int rws = min(kTile, Kp - r0);
       float acc[4][4];  // acc[a][b]: child k' = row0 + ty*4 + a, parent k = r0 + tx*4 + b
       zero_acc(acc);
-      tile_gemm<true, true>(acc, Zo, d, cols, M + (long long)r0 * d, d, rws, d, sm);
+      if (res) tile_gemm_resA<true>(acc, sa, M + (long long)r0 * d, d, rws, d, sb);
+      else tile_gemm<true, true>(acc, Zo, d, cols, M + (long long)r0 * d, d, rws, d, sm);
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const int k = r0 + tx * 4 + b;
@@ -224,15 +267,33 @@ __global__ void __launch_bounds__(kThreads) k_edge_bwd_cols_f32(Dev D, const Til
           ps[(tx * 4 + b) * kLd + ty * 4 + a] = p;
         }
       }
-      __syncthreads();
-      for (int l0 = 0; l0 < rws; l0 += kSlice) {
-        const float* Mr = M + (long long)r0 * d + j0;
-        load_slice<false>(sm.a, Mr, d, min(kTile, d - j0), l0, rws);
-        if (j0 + kTile < d) load_slice<false>(sm.b, Mr + kTile, d, min(kTile, d - j0 - kTile), l0, rws);
+      const float* Mr = M + (long long)r0 * d + j0;
+      if (res) {  // the tile's 64 rows of mu~ in one round of loads
+        float rv[kDeepVals];
+        fetch_deep<false>(rv, Mr, d, min(kTile, d - j0), 0, rws);
+        __syncthreads();  // the pi tile is written; the readers of sb are done
+        store_deep<false>(sb, rv);
+        if (j0 + kTile < d) {
+          fetch_deep<false>(rv, Mr + kTile, d, min(kTile, d - j0 - kTile), 0, rws);
+          store_deep<false>(sb2, rv);
+        }
         __syncthreads();
-        slice_fma(o0, ps + l0 * kLd, sm.a);
-        if (j0 + kTile < d) slice_fma(o1, ps + l0 * kLd, sm.b);
+        const int nq = (rws + kSlice - 1) / kSlice;
+        for (int q = 0; q < nq; ++q) {
+          slice_fma(o0, ps + q * kSlice * kLd, sb + q * kSlice * kLd);
+          if (j0 + kTile < d) slice_fma(o1, ps + q * kSlice * kLd, sb2 + q * kSlice * kLd);
+        }
+        __syncthreads();  // ps and sb are rewritten by the next tile
+      } else {
         __syncthreads();
+        for (int l0 = 0; l0 < rws; l0 += kSlice) {
+          load_slice<false>(sm.a, Mr, d, min(kTile, d - j0), l0, rws);
+          if (j0 + kTile < d) load_slice<false>(sm.b, Mr + kTile, d, min(kTile, d - j0 - kTile), l0, rws);
+          __syncthreads();
+          slice_fma(o0, ps + l0 * kLd, sm.a);
+          if (j0 + kTile < d) slice_fma(o1, ps + l0 * kLd, sm.b);
+          __syncthreads();
+        }
       }
     }
 #pragma unroll
@@ -260,19 +321,25 @@ static void allow_dynamic_smem(Kern k) {
 }
 
 void launch_edge_fwd_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK, cudaStream_t s) {
-  static bool once = (allow_dynamic_smem(k_edge_fwd_f32), true);
+  static bool once = (cudaFuncSetAttribute(k_edge_fwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           res_smem_floats(kMaxK) * (int)sizeof(float)),
+                      true);
   (void)once;
-  if (ntiles) k_edge_fwd_f32<<<ntiles, kThreads, maxK * sizeof(float), s>>>(D, tiles);
+  if (ntiles) k_edge_fwd_f32<<<ntiles, kThreads, res_smem_floats(maxK) * sizeof(float), s>>>(D, tiles);
 }
 void launch_edge_bwd_rows_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK, cudaStream_t s) {
-  static bool once = (allow_dynamic_smem(k_edge_bwd_rows_f32), true);
+  static bool once = (cudaFuncSetAttribute(k_edge_bwd_rows_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           res_smem_floats(kMaxK) * (int)sizeof(float)),
+                      true);
   (void)once;
-  if (ntiles) k_edge_bwd_rows_f32<<<ntiles, kThreads, maxK * sizeof(float), s>>>(D, tiles);
+  if (ntiles) k_edge_bwd_rows_f32<<<ntiles, kThreads, res_smem_floats(maxK) * sizeof(float), s>>>(D, tiles);
 }
 void launch_edge_bwd_cols_f32(const Dev& D, const Tile* tiles, int ntiles, int maxK, cudaStream_t s) {
-  static bool once = (allow_dynamic_smem(k_edge_bwd_cols_f32), true);
+  static bool once = (cudaFuncSetAttribute(k_edge_bwd_cols_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           res_smem_floats(kMaxK) * (int)sizeof(float)),
+                      true);
   (void)once;
-  if (ntiles) k_edge_bwd_cols_f32<<<ntiles, kThreads, maxK * sizeof(float), s>>>(D, tiles);
+  if (ntiles) k_edge_bwd_cols_f32<<<ntiles, kThreads, res_smem_floats(maxK) * sizeof(float), s>>>(D, tiles);
 }
 
 }  // namespace tmc

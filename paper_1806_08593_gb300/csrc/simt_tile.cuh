@@ -155,6 +155,35 @@ __device__ __forceinline__ void tile_gemm_deep(float acc[4][4], const float* __r
   }
 }
 
+// acc += opA * opB with opA resident in shared memory, sa[l * kLd + m] for every l < L rounded
+// up to kDeep (rows past L zero), and opB streamed through sb ([kDeep * kLd]) in 64-deep
+// slices (register prefetch of the next slice).  The first barrier also orders the caller's
+// stores of sa.
+template <bool B_TRANS>
+__device__ __forceinline__ void tile_gemm_resA(float acc[4][4], const float* sa, const float* __restrict__ B,
+                                               long long ldb, int nb, int L, float* sb) {
+  float rb[kDeepVals];
+  fetch_deep<B_TRANS>(rb, B, ldb, nb, 0, L);
+  for (int l0 = 0; l0 < L; l0 += kDeep) {
+    __syncthreads();  // the previous readers of sb are done
+    store_deep<B_TRANS>(sb, rb);
+    __syncthreads();
+    if (l0 + kDeep < L) fetch_deep<B_TRANS>(rb, B, ldb, nb, l0 + kDeep, L);
+    const int nq = (min(kDeep, L - l0) + kSlice - 1) / kSlice;
+    for (int q = 0; q < nq; ++q) slice_fma(acc, sa + (l0 + q * kSlice) * kLd, sb + q * kSlice * kLd);
+  }
+}
+// Stores opA (A_TRANS layout as in tile_gemm) of an ma x L tile into sa[l * kLd + m], in
+// 64-deep slices (zeros past L up to the next multiple of kDeep).
+template <bool A_TRANS>
+__device__ __forceinline__ void load_resident(float* sa, const float* __restrict__ A, long long lda, int ma, int L) {
+  for (int l0 = 0; l0 < L; l0 += kDeep) {
+    float r[kDeepVals];
+    fetch_deep<A_TRANS>(r, A, lda, ma, l0, L);
+    store_deep<A_TRANS>(sa + l0 * kLd, r);
+  }
+}
+
 __device__ __forceinline__ void zero_acc(float acc[4][4]) {
 #pragma unroll
   for (int i = 0; i < 4; ++i)
