@@ -2135,23 +2135,12 @@ __global__ void __launch_bounds__(128) k_asm_edge_vec(Dev D, TcDev T, const int*
   const int j = threadIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (j < dq) zp[j] = __ldg(T.zbar + (long long)nd.parent * kLdp + j);
   __syncthreads();
-  // (W_c zbar_p)[r]: one warp per row, lanes along the row (coalesced); four rows at a time so
-  // their loads are in flight together
-  for (int r0 = w * 4; r0 < d; r0 += 16) {
-    float sr[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int c = lane; c < dq; c += 32) {
-      const float zc = zp[c];
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (r0 + q < d) sr[q] = fmaf(__ldg(W + (long long)(r0 + q) * dq + c), zc, sr[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      for (int o = 16; o > 0; o >>= 1) sr[q] += __shfl_xor_sync(0xffffffffu, sr[q], o);
-    if (lane < 4 && r0 + lane < d) {
-      const float v = lane == 0 ? sr[0] : lane == 1 ? sr[1] : lane == 2 ? sr[2] : sr[3];
-      dbs[r0 + lane] = (__ldg(zbc + r0 + lane) - v - __ldg(cc + r0 + lane)) * iv;
-    }
+  // (W_c zbar_p)[r]: one warp per row, lanes along the row (coalesced)
+  for (int r = w; r < d; r += 4) {
+    float s = 0.f;
+    for (int c = lane; c < dq; c += 32) s = fmaf(__ldg(W + (long long)r * dq + c), zp[c], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) dbs[r] = (__ldg(zbc + r) - s - __ldg(cc + r)) * iv;
   }
   __syncthreads();
   if (j < d) {
@@ -2164,13 +2153,9 @@ __global__ void __launch_bounds__(128) k_asm_edge_vec(Dev D, TcDev T, const int*
   // g z~ is diag(W_c G_c) / var (k_asm_edge_mat, which holds both tiles, into the zeroed tgC)
   // plus (c_c zbar_c - diag M2_c) / var (added by k_asm_node)
   if (j >= dq) return;
-  float sg[4] = {0.f, 0.f, 0.f, 0.f};
-  int a = 0;
-  for (; a + 4 <= d; a += 4)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) sg[q] = fmaf(__ldg(W + (long long)(a + q) * dq + j), dbs[a + q], sg[q]);
-  for (; a < d; ++a) sg[0] = fmaf(__ldg(W + (long long)a * dq + j), dbs[a], sg[0]);
-  T.sgP[(long long)g * kLdp + j] = (sg[0] + sg[1]) + (sg[2] + sg[3]);
+  float sg = 0.f;
+  for (int a = 0; a < d; ++a) sg = fmaf(__ldg(W + (long long)a * dq + j), dbs[a], sg);
+  T.sgP[(long long)g * kLdp + j] = sg;
 }
 
 // Grid: (edge, 64x64 tile of D_c (2 x 2)).  The W_c and G_c^T tiles are staged through

@@ -612,19 +612,19 @@ __global__ void __launch_bounds__(kThreads) k_param_dC(Dev D) {
 }
 
 // One level of rows_sum: out[g * E + e] = sum of rows g * kRowChunk .. +kRowChunk - 1 (in order).
-// Eight rows' loads are issued before they are added.
+// 32 rows' loads are issued before they are added.
 __global__ void __launch_bounds__(256) k_rows_sum(const float* __restrict__ in, long long R, long long E,
                                                   long long stride, float* __restrict__ out) {
   const long long e = blockIdx.x * 256ll + threadIdx.x;
   if (e >= E) return;
   const long long r0 = (long long)blockIdx.y * kRowChunk, r1 = min(R, r0 + kRowChunk);
   float s = 0.f;
-  for (long long r = r0; r < r1; r += 8) {
-    float v[8];
+  for (long long r = r0; r < r1; r += 32) {
+    float v[32];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = r + u < r1 ? __ldg(in + (r + u) * stride + e) : 0.f;
+    for (int u = 0; u < 32; ++u) v[u] = r + u < r1 ? __ldg(in + (r + u) * stride + e) : 0.f;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) s += v[u];
+    for (int u = 0; u < 32; ++u) s += v[u];
   }
   out[(long long)blockIdx.y * E + e] = s;
 }

@@ -47,6 +47,15 @@ def test_chains_fp32(n, K, d, obs, B):
     compare(p, got, ref, TOL_LOGP_F32, TOL_GRAD)
 
 
+def test_shared_many_instances_fp32():
+    """One model shared by 150 instances: the shared gradients are per-instance partials summed
+    by a tree of 64-row chunks (two levels here), weighted by a different grad_out each."""
+    B = 150
+    p = wl.make_chain(4, 16, 24, 30, B, seed=716)
+    go = np.linspace(0.25, 1.75, B)
+    compare(p, gpu_run(p, "fp32", grad_out=go), oracle_run(p, grad_out=go), TOL_LOGP_F32, TOL_GRAD)
+
+
 def test_uneven_trees_fp32():
     p = wl.tree_batch(B=12, seed=4242)
     got = gpu_run(p, "fp32")

@@ -56,6 +56,18 @@ def test_chains_tc(n, K, d, obs, B):
     _check(wl.make_chain(n, K, d, obs, B, seed=2000 + n * 7 + K + d), grad_out=np.linspace(0.5, 1.5, B))
 
 
+@pytest.mark.parametrize("B,layered", [(150, False), (70, True)])
+def test_shared_many_instances_tc(B, layered):
+    """One model shared by many instances: the gradients of the shared W, bias and C are sums
+    over instances (groups of 8 instances, then a tree of 64-row chunks; 150 instances take
+    two levels), weighted by a different grad_out per instance."""
+    if layered:
+        p = wl.layered_chain([4, 8, 16, 32, 64], 20, obs=40, B=B, seed=717)
+    else:
+        p = wl.make_chain(4, 16, 24, 30, B, seed=716)
+    _check(p, grad_out=np.linspace(0.25, 1.75, B))
+
+
 def test_uneven_trees_tc():
     _check(wl.tree_batch(B=10, seed=777))
 
