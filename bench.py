@@ -193,6 +193,25 @@ def oracle_cores():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
+def gpu_local_cpus(dev):
+    """The CPUs the system lists as local to the GPU (sysfs), intersected with the ones this
+    process may use; None when either is unknown or they coincide."""
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        bus = "%04x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        txt = open("/sys/bus/pci/devices/%s/local_cpulist" % bus).read().strip()
+        cpus = set()
+        for part in txt.split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        allowed = os.sched_getaffinity(0)
+        use = cpus & allowed
+        return use if use and use != allowed else None
+    except Exception:
+        return None
+
+
 def time_oracle_sample(p, target_s=15.0, max_inst=None):
     import oracle
     oracle.build()
@@ -592,22 +611,34 @@ def run_ours(args):
     # Every step copies its inputs from pinned host memory and reads its results back inside
     # the timed region.  The uploads run on a copy stream into one of two device input sets,
     # so step i + 1's upload overlaps step i's kernels (as a serving loop would run them).
+    # pinned host buffers are placed while the process runs on the GPU's own CPUs (when the
+    # system reports them), so the uploads do not cross a socket link
+    numa = gpu_local_cpus(dev)
+    prev_aff = os.sched_getaffinity(0) if numa else None
+    if numa:
+        os.sched_setaffinity(0, numa)
     host_in = {k: v.cpu().pin_memory() for k, v in t.items()}
     dev_in = [{k: torch.empty_like(v) for k, v in t.items()} for _ in range(2)]
     host_out = {k: torch.empty(grads[k].shape, dtype=grads[k].dtype).pin_memory() for k in GR}
     host_lp = torch.empty(p.B, dtype=torch.float64).pin_memory()
+    if numa:
+        os.sched_setaffinity(0, prev_aff)
     h2d = sum(v.numel() * v.element_size() for v in host_in.values())
     d2h = host_lp.numel() * 8 + sum(v.numel() * v.element_size() for v in host_out.values())
     copy_stream = torch.cuda.Stream(device=dev)
-    uploaded = [torch.cuda.Event() for _ in range(2)]
+    uploaded = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     consumed = [torch.cuda.Event() for _ in range(2)]
+    copy_ms = []  # duration of each upload of the timed run (diagnostic: host link bandwidth)
 
     def upload(i):
         with torch.cuda.stream(copy_stream):
             copy_stream.wait_event(consumed[i % 2])  # the step that last read this set is done
+            c0 = torch.cuda.Event(enable_timing=True)
+            c0.record(copy_stream)
             for k, v in dev_in[i % 2].items():
                 v.copy_(host_in[k], non_blocking=True)
             uploaded[i % 2].record(copy_stream)
+            copy_ms.append((c0, uploaded[i % 2]))
 
     def e2e_run(nsteps):
         for i in range(2):
@@ -634,6 +665,9 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     barrier()
     e2e_ms = max_over_ranks(ev0.elapsed_time(ev1), dev) / e2e_steps
+    # an upload's events are re-recorded two uploads later: time each before it is reused
+    up_ms = [a.elapsed_time(b) for a, b in copy_ms[-2:]]
+    h2d_gbs = h2d / (float(np.mean(up_ms)) * 1e-3) / 1e9 if up_ms else None
     plan.sync_status()
 
     if rank != 0:
@@ -760,6 +794,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "vs_oracle": vs_oracle,
         "e2e": {"value": entries * ws / (e2e_ms * 1e-3), "unit": "entries/s",
+                "h2d_gbs": h2d_gbs, "host_cpus": (sorted(numa)[0], sorted(numa)[-1]) if numa else None,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "fp32_path": fp32,
         "unfused_baseline": unfused,

@@ -215,6 +215,8 @@ static_assert(4 * kRows * 64 * 2 >= 2 * kRows * 64 * 2 + 2 * kBox && 4 * kRows *
 // float4 groups at columns 4 sub + 4 L q (q < Q), so a row sum needs LG shuffle steps per
 // 32 / L rows.
 __host__ __device__ constexpr int sample_rows(int d) { return d > 64 ? 64 : d > 32 ? 128 : d > 16 ? 256 : 512; }
+// Above this many nodes the per-node set-up kernels take several nodes per CTA.
+constexpr int kManyNodes = 8192;
 constexpr int kSampleStage = 64 * kTcMaxD * 4;  // bytes of one eps stage (= rows x d x 4 at most)
 constexpr int kSampleNS = 3;                    // ring stages
 constexpr int kSampleConsumers = 8;             // consumer warps (64 rows at d = 128: two full passes)
@@ -454,22 +456,30 @@ __global__ void k_pack_w(Dev D, TcDev T, const int* __restrict__ nonroot) {
 
 // c_i = W_i m_p + bias_i - m_i per non-root node (zero in the padding up to d_pad).  One
 // thread per row of W_i, each streaming its own row (independent loads).
-__global__ void __launch_bounds__(128) k_pack_c(Dev D, TcDev T, const int* __restrict__ nonroot) {
-  __shared__ __align__(16) float mp[kTcMaxD];
-  const int g = nonroot[blockIdx.x];
-  const NodeInfo nd = D.nodes[g];
+// NPB nodes per CTA (128 / NPB threads each): several nodes per CTA when there are many small
+// latents (one CTA per latent spends its time on launch and latency).
+template <int NPB>
+__global__ void __launch_bounds__(128) k_pack_c(Dev D, TcDev T, const int* __restrict__ nonroot, int n) {
+  constexpr int TPN = 128 / NPB;
+  __shared__ __align__(16) float mp_all[NPB][kTcMaxD];
+  const int slot = threadIdx.x / TPN, tid = threadIdx.x % TPN;
+  const int idx = blockIdx.x * NPB + slot;
+  const bool live = idx < n;
+  const int g = live ? nonroot[idx] : 0;
+  const NodeInfo nd = D.nodes[live ? g : nonroot[0]];
   const NodeInfo pn = D.nodes[nd.parent];
   const int d = nd.d, dq = nd.dp, dp = kTcMaxD;  // W_i is d x dq; c_i padded to 128 with zeros
-  for (int j = threadIdx.x; j < kTcMaxD; j += blockDim.x) mp[j] = j < dq ? D.q_mean[pn.off_q + j] : 0.f;
+  float* mp = mp_all[slot];
+  for (int j = tid; j < kTcMaxD; j += TPN) mp[j] = j < dq ? D.q_mean[pn.off_q + j] : 0.f;
   __syncthreads();
+  if (!live) return;
   const bool vec = (dq & 3) == 0 && (nd.off_W & 3) == 0;
-  for (int r = threadIdx.x; r < dp; r += blockDim.x) {
+  for (int r = tid; r < dp; r += TPN) {
     float s = 0.f;
     if (r < d) {
       const float* wr = D.W + nd.off_W + (long long)r * dq;
       float s0 = 0.f, s1 = 0.f;
       if (vec) {
-#pragma unroll 4
         for (int c = 0; c < dq; c += 8) {
           const float4 a = *reinterpret_cast<const float4*>(wr + c);
           s0 = fmaf(a.x, mp[c], s0); s0 = fmaf(a.y, mp[c + 1], s0);
@@ -492,14 +502,21 @@ __global__ void __launch_bounds__(128) k_pack_c(Dev D, TcDev T, const int* __res
 // Centred observations of the leaves, x~_l = x_l - C m_l, kept for the observation kernel
 // and the gradient assembly.  Grid: one CTA per leaf; thread per observation row, each thread
 // streaming its own row of C (independent loads, no per-row reduction chain).
-__global__ void __launch_bounds__(128) k_obs_center(Dev D, TcDev T, const int* __restrict__ leaves) {
-  __shared__ __align__(16) float m[kTcMaxD];
-  const NodeInfo nd = D.nodes[leaves[blockIdx.x]];
+template <int NPB>
+__global__ void __launch_bounds__(128) k_obs_center(Dev D, TcDev T, const int* __restrict__ leaves, int n) {
+  constexpr int TPN = 128 / NPB;
+  __shared__ __align__(16) float m_all[NPB][kTcMaxD];
+  const int slot = threadIdx.x / TPN, tid = threadIdx.x % TPN;
+  const int idx = blockIdx.x * NPB + slot;
+  const bool live = idx < n;
+  const NodeInfo nd = D.nodes[leaves[live ? idx : 0]];
   const int d = nd.d;
-  for (int j = threadIdx.x; j < kTcMaxD; j += blockDim.x) m[j] = j < d ? D.q_mean[nd.off_q + j] : 0.f;
+  float* m = m_all[slot];
+  for (int j = tid; j < kTcMaxD; j += TPN) m[j] = j < d ? D.q_mean[nd.off_q + j] : 0.f;
   __syncthreads();
+  if (!live) return;
   const bool vec = (d & 3) == 0 && (nd.off_C & 3) == 0;
-  for (int o = threadIdx.x; o < nd.obs; o += blockDim.x) {
+  for (int o = tid; o < nd.obs; o += TPN) {
     const float* c = D.C + nd.off_C + (long long)o * d;
     float s0 = 0.f, s1 = 0.f;
     if (vec) {
@@ -2102,11 +2119,16 @@ __global__ void __launch_bounds__(kMoThreads, 1)
 
 // Zeroes the dp x d block of every node in a [node][128][128] array (the part the readers use:
 // G_i = sum pi z~_p z~_i^T is d_parent x d_i; the adjoint launch adds its tile partials into it).
-// Rows are zeroed in whole float4s (up to three entries past d, inside the 128-float row).
+// Rows are zeroed in whole float4s (up to three entries past d, inside the 128-float row);
+// NPB nodes per CTA.
+template <int NPB>
 __global__ void __launch_bounds__(256) k_zero_dd(Dev D, float* __restrict__ base) {
-  const int d4 = (D.nodes[blockIdx.x].d + 3) >> 2, dq = D.nodes[blockIdx.x].dp;
-  float4* blk = reinterpret_cast<float4*>(base + (long long)blockIdx.x * kLdp * kLdp);
-  for (int i = threadIdx.x; i < dq * d4; i += blockDim.x)
+  constexpr int TPN = 256 / NPB;
+  const int g = blockIdx.x * NPB + threadIdx.x / TPN, tid = threadIdx.x % TPN;
+  if (g >= D.num_nodes) return;
+  const int d4 = (D.nodes[g].d + 3) >> 2, dq = D.nodes[g].dp;
+  float4* blk = reinterpret_cast<float4*>(base + (long long)g * kLdp * kLdp);
+  for (int i = tid; i < dq * d4; i += TPN)
     blk[(i / d4) * (kLdp / 4) + i % d4] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
@@ -3142,12 +3164,15 @@ void launch_pack(TcWork& w, const Dev& D, cudaStream_t s) {
   const int n = (int)w.nonroot.size();
   if (!n) return;
   if (w.n_pack_w) k_pack_w<<<dim3(w.n_pack_w, w.maxdp / 32, w.maxdp / 32), 256, 0, s>>>(D, w.t, w.d_nonroot);
-  k_pack_c<<<n, 128, 0, s>>>(D, w.t, w.d_nonroot);
+  if (n > kManyNodes) k_pack_c<4><<<(n + 3) / 4, 128, 0, s>>>(D, w.t, w.d_nonroot, n);
+  else k_pack_c<1><<<n, 128, 0, s>>>(D, w.t, w.d_nonroot, n);
 }
 
 void launch_obs(TcWork& w, const Dev& D, cudaStream_t s) {
   if (w.obs_tiles.empty()) return;
-  k_obs_center<<<(int)w.leaves.size(), 128, 0, s>>>(D, w.t, w.d_leaves);
+  const int nl = (int)w.leaves.size();
+  if (nl > kManyNodes) k_obs_center<4><<<(nl + 3) / 4, 128, 0, s>>>(D, w.t, w.d_leaves, nl);
+  else k_obs_center<1><<<nl, 128, 0, s>>>(D, w.t, w.d_leaves, nl);
   k_pack_cobs<<<dim3(w.num_c, (w.maxobs + 7) / 8), 256, 0, s>>>(D, w.t);
   for (int c = 0; c < 2; ++c) {
     const int b = w.ob_b[c], n = w.ob_e[c] - b;
@@ -3192,7 +3217,8 @@ void launch_edge_fwd(TcWork& w, const Dev& D, cudaStream_t s) {
 }
 
 void launch_edge_bwd(TcWork& w, const Dev& D, cudaStream_t s) {
-  k_zero_dd<<<w.num_nodes, 256, 0, s>>>(D, w.t.G);
+  if (w.num_nodes > kManyNodes) k_zero_dd<4><<<(w.num_nodes + 3) / 4, 256, 0, s>>>(D, w.t.G);
+  else k_zero_dd<1><<<w.num_nodes, 256, 0, s>>>(D, w.t.G);
   cudaMemsetAsync(w.t.done, 0, (size_t)w.num_nodes * sizeof(int), s);
   cudaMemsetAsync(w.t.claim + 2, 0, 2 * sizeof(int), s);
   cudaMemsetAsync(w.t.inst_t + w.num_inst, 0, sizeof(unsigned long long) * w.num_inst, s);

@@ -63,17 +63,20 @@ __device__ __forceinline__ float block_sum_f(float v, float* red) {
 // FP64 node constants: sum_j logs_ij + (d/2) log 2pi  (from -log Q_i)
 //   + root: -(d/2) log(2 pi prior_var)   + leaf: -(obs/2) log(2 pi obs_var)
 // ---------------------------------------------------------------------------------------
-__global__ void k_node_const(Dev D) {
-  __shared__ double red[32];
-  const NodeInfo nd = D.nodes[blockIdx.x];
+// One warp per node (8 nodes per CTA): lanes sum logs_i over the dimension in FP64.
+constexpr int kConstNodesPerCta = 8;
+__global__ void __launch_bounds__(32 * kConstNodesPerCta) k_node_const(Dev D) {
+  const int g = blockIdx.x * kConstNodesPerCta + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (g >= D.num_nodes) return;
+  const NodeInfo nd = D.nodes[g];
   double s = 0.0;
-  for (int j = threadIdx.x; j < nd.d; j += blockDim.x) s += (double)D.q_logstd[nd.off_q + j];
-  s = block_sum_d(s, red);
-  if (threadIdx.x == 0) {
+  for (int j = lane; j < nd.d; j += 32) s += (double)D.q_logstd[nd.off_q + j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
     double c = s + 0.5 * nd.d * kLog2Pi;
     if (nd.parent < 0) c += -0.5 * nd.d * (kLog2Pi + log(D.prior_var));
     if (nd.leaf_slot >= 0) c += -0.5 * nd.obs * (kLog2Pi + log(D.obs_var));
-    D.nodeconst[blockIdx.x] = c;
+    D.nodeconst[g] = c;
   }
 }
 
@@ -631,7 +634,7 @@ __global__ void __launch_bounds__(256) k_rows_sum(const float* __restrict__ in, 
 
 // ---- launchers ----------------------------------------------------------------------------
 void launch_node_const(const Dev& D, cudaStream_t s) {
-  k_node_const<<<D.num_nodes, 128, 0, s>>>(D);
+  k_node_const<<<(D.num_nodes + kConstNodesPerCta - 1) / kConstNodesPerCta, 32 * kConstNodesPerCta, 0, s>>>(D);
 }
 void launch_sample(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s) {
   k_sample<<<ntiles, kThreads, 2 * kMaxD * sizeof(float), s>>>(D, tiles);

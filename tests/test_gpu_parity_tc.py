@@ -68,6 +68,12 @@ def test_shared_many_instances_tc(B, layered):
     _check(p, grad_out=np.linspace(0.25, 1.75, B))
 
 
+def test_many_nodes_tc():
+    """More than 8192 latents, non-root latents and leaves: the per-node set-up kernels take
+    four nodes per CTA (9000 observed children of one root)."""
+    _check(wl.star(9000, 16, 2, B=1, seed=1236))
+
+
 def test_uneven_trees_tc():
     _check(wl.tree_batch(B=10, seed=777))
 
