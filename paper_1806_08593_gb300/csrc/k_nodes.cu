@@ -331,6 +331,40 @@ __global__ void k_root(Dev D) {
 // deps = exp(logs) * dz.
 // Grid: (node, 64-sample tile); loops over 64-wide latent-dimension tiles.
 // ---------------------------------------------------------------------------------------
+// Sum over one chunk of a wide latent's children of dmu_c W_c for 64 sample rows and 64 columns.
+// Grid: (item = node and first row, chunk of kParamChunk children, 64-column tile).  Chunks past
+// the latent's children write zeros (every chunk row of part is summed).
+__global__ void __launch_bounds__(kThreads) k_child_sum(Dev D, const Tile* __restrict__ items, float* __restrict__ part,
+                                                         long long cs_total) {
+  __shared__ TileSmem sm;
+  const Tile t = items[blockIdx.x];
+  const NodeInfo nd = D.nodes[t.node];
+  const int d = nd.d, K = nd.K;
+  const int c0 = blockIdx.z * kTile;
+  if (c0 >= d) return;
+  const int rows = min(kTile, K - t.row0), ncol = min(kTile, d - c0);
+  const int cb = nd.child_begin + blockIdx.y * kParamChunk, ce = min(nd.child_end, cb + kParamChunk);
+  float acc[4][4];
+  zero_acc(acc);
+  for (int ci = cb; ci < ce; ++ci) {
+    const NodeInfo ch = D.nodes[D.children[ci]];
+    tile_gemm<true, false>(acc, D.dmu + ch.off_nkd + (long long)t.row0 * ch.d, ch.d, rows,
+                           D.W + ch.off_W + c0, d, ncol, ch.d, sm);
+  }
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  float* out = part + (long long)blockIdx.y * cs_total + nd.off_cs;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int k = t.row0 + ty * 4 + a;
+    if (k >= K) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = c0 + tx * 4 + b;
+      if (c < d) out[(long long)k * d + c] = acc[a][b];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) k_node_grad(Dev D, const Tile* __restrict__ tiles) {
   extern __shared__ float xs[];  // centred observation (leaves)
   __shared__ TileSmem sm;
@@ -355,11 +389,22 @@ __global__ void __launch_bounds__(kThreads) k_node_grad(Dev D, const Tile* __res
     const int ncol = min(kTile, d - c0);
     float acc[4][4];
     zero_acc(acc);
-    // children: out[k][c] += sum_r dmu_c[k][r] W_c[r][c]   (W_c is d_c x d)
-    for (int ci = nd.child_begin; ci < nd.child_end; ++ci) {
-      const NodeInfo ch = D.nodes[D.children[ci]];
-      tile_gemm<true, false>(acc, D.dmu + ch.off_nkd + (long long)t.row0 * ch.d, ch.d, rows,
-                             D.W + ch.off_W + c0, d, ncol, ch.d, sm);
+    // children: out[k][c] += sum_r dmu_c[k][r] W_c[r][c]   (W_c is d_c x d); a latent with
+    // many children reads the sum formed beforehand by k_child_sum
+    if (nd.off_cs >= 0) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int k = t.row0 + ty * 4 + a, c = c0 + tx * 4 + b;
+          acc[a][b] = (k < K && c < d) ? D.csum[nd.off_cs + (long long)k * d + c] : 0.f;
+        }
+    } else {
+      for (int ci = nd.child_begin; ci < nd.child_end; ++ci) {
+        const NodeInfo ch = D.nodes[D.children[ci]];
+        tile_gemm<true, false>(acc, D.dmu + ch.off_nkd + (long long)t.row0 * ch.d, ch.d, rows,
+                               D.W + ch.off_W + c0, d, ncol, ch.d, sm);
+      }
     }
     if (leaf) {
       // out[k][c] += q[k] / obs_var * sum_o r[k][o] C[o][c],  r = x~ - C z~
@@ -527,17 +572,21 @@ __global__ void __launch_bounds__(kThreads) k_param_dW(Dev D, const int* __restr
 
 // ---------------------------------------------------------------------------------------
 // dC = grad_out * sum_{leaves l} sum_k q_l[k] (x_l - C z_l^k) z_l^k^T / obs_var.
-// Grid: (instance, 64-row tile of C (observation), 64-col tile of C (latent)).
+// Grid: (instance, 64 x 64 tile of C (observation tile * ctiles + latent tile), chunk of
+// kParamChunk nodes).  With one chunk the CTA writes dC (or the shared-parameter partial);
+// with several it writes its chunk's partial, part[chunk][same layout], summed afterwards.
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_param_dC(Dev D) {
+__global__ void __launch_bounds__(kThreads) k_param_dC(Dev D, int ctiles, float* __restrict__ part, long long part_ld) {
   extern __shared__ float xs[];
   __shared__ TileSmem sm;
   __shared__ float rsm[kTile * kLd];  // q-weighted residuals, [k][o]
   __shared__ float rsum[kTile];
   const InstInfo in = D.insts[blockIdx.x];
   const int d = in.d, obs = in.obs;  // d of the leaves
-  const int o0 = blockIdx.y * kTile, c0 = blockIdx.z * kTile;
+  const int o0 = (blockIdx.y / ctiles) * kTile, c0 = (blockIdx.y % ctiles) * kTile;
   if (o0 >= obs || c0 >= d) return;
+  const int g_begin = in.node0 + min(in.n, (int)blockIdx.z * kParamChunk);
+  const int g_end = in.node0 + min(in.n, ((int)blockIdx.z + 1) * kParamChunk);
   const int nob = min(kTile, obs - o0), ncol = min(kTile, d - c0);
   const float go = D.grad_out ? (float)D.grad_out[blockIdx.x] : 1.f;
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
@@ -545,7 +594,7 @@ __global__ void __launch_bounds__(kThreads) k_param_dC(Dev D) {
   zero_acc(acc);
   float macc[4][4];                          // sum_k r[k][o] * m[c]: folded at the end per leaf
   zero_acc(macc);
-  for (int g = in.node0; g < in.node0 + in.n; ++g) {
+  for (int g = g_begin; g < g_end; ++g) {
     const NodeInfo nd = D.nodes[g];
     if (nd.leaf_slot < 0) continue;
     __syncthreads();
@@ -608,8 +657,10 @@ __global__ void __launch_bounds__(kThreads) k_param_dC(Dev D) {
       const int c = c0 + tx * 4 + b;
       if (c >= d) continue;
       const float v = go * (acc[a][b] + macc[a][b]);
-      if (D.shared) D.pC[in.off_pC + (long long)o * d + c] = v;
-      else D.dC[in.off_C + (long long)o * d + c] = v;
+      const long long e = (D.shared ? in.off_pC : in.off_C) + (long long)o * d + c;
+      if (part) part[(long long)blockIdx.z * part_ld + e] = v;
+      else if (D.shared) D.pC[e] = v;
+      else D.dC[e] = v;
     }
   }
 }
@@ -656,15 +707,25 @@ void launch_root(const Dev& D, int maxK, int root_fanout, cudaStream_t s) {
 void launch_node_grad(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s) {
   k_node_grad<<<ntiles, kThreads, kMaxD * sizeof(float), s>>>(D, tiles);
 }
+void launch_child_sum(const Dev& D, const Tile* items, int nitems, int maxd, int chunks, long long cs_total,
+                      float* part, cudaStream_t s) {
+  if (!nitems) return;
+  k_child_sum<<<dim3(nitems, chunks, (maxd + kTile - 1) / kTile), kThreads, 0, s>>>(D, items, part, cs_total);
+  rows_sum(part, chunks, cs_total, cs_total, D.csum, D.rsum, s);
+}
 void launch_node_reduce(const Dev& D, cudaStream_t s) { k_node_reduce<<<D.num_nodes, 256, 0, s>>>(D); }
 void launch_param_dW(const Dev& D, const int* nonroot, int n_nonroot, int maxd, cudaStream_t s) {
   if (!n_nonroot) return;
   const int t = (maxd + kTile - 1) / kTile;
   k_param_dW<<<dim3(n_nonroot, t, t), kThreads, 0, s>>>(D, nonroot);
 }
-void launch_param_dC(const Dev& D, int maxd, int maxobs, cudaStream_t s) {
-  k_param_dC<<<dim3(D.num_inst, (maxobs + kTile - 1) / kTile, (maxd + kTile - 1) / kTile), kThreads,
-               kMaxD * sizeof(float), s>>>(D);
+void launch_param_dC(const Dev& D, int maxd, int maxobs, int maxn, long long c_total, float* part,
+                     cudaStream_t s) {
+  const int ctiles = (maxd + kTile - 1) / kTile, chunks = (maxn + kParamChunk - 1) / kParamChunk;
+  float* out = D.shared ? D.pC : D.dC;
+  k_param_dC<<<dim3(D.num_inst, ((maxobs + kTile - 1) / kTile) * ctiles, chunks), kThreads,
+               kMaxD * sizeof(float), s>>>(D, ctiles, chunks > 1 ? part : nullptr, c_total);
+  if (chunks > 1 && out) rows_sum(part, chunks, c_total, c_total, out, D.rsum, s);
 }
 void rows_sum(const float* in, long long R, long long E, long long stride, float* out, float* scratch,
               cudaStream_t s) {

@@ -38,6 +38,8 @@ struct NodeInfo {
   long long off_A;     // start of A_i ([d][dp]) in q_A / dq_A (per instance, like unshared W)
   long long off_S;     // start of this latent's dp x dp block in one instance's packed [dp x dp]
                        // blocks of the non-root latents (the root's block is empty)
+  long long off_cs;    // FP32 path, latents with more than kParamChunk children: start of the
+                       // [K][d] sum over children of dmu_c W_c (k_child_sum); -1 otherwise
 };
 
 struct InstInfo {
@@ -86,7 +88,8 @@ struct Dev {
   float* pW;      // per-(instance, node) dW partials  (shared params only)
   float* pbias;   // per-(instance, node) dbias partials (shared params only)
   float* pC;      // per-instance dC partials (shared params only)
-  float* rsum;    // scratch of the row sums (rows_sum), shared parameters only
+  float* rsum;    // scratch of the row sums (rows_sum)
+  float* csum;    // FP32 path: children sums of the latents with many children (NodeInfo::off_cs)
   int* err;       // device error word
   long long wait_limit;   // clock cycles a cross-CTA dependency wait polls before giving up
   // coupled proposals (sample k of a latent drawn given its parent's sample k)
@@ -130,7 +133,17 @@ void launch_edge_bwd_cols_f32(const Dev& D, const Tile* tiles, int ntiles, int m
 void launch_node_grad(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s);
 void launch_node_reduce(const Dev& D, cudaStream_t s);
 void launch_param_dW(const Dev& D, const int* nonroot, int n_nonroot, int maxd, cudaStream_t s);
-void launch_param_dC(const Dev& D, int maxd, int maxobs, cudaStream_t s);
+// Instances with more than kParamChunk latents split the dC sum over their leaves into chunks:
+// part holds chunks x c_total floats (c_total: the size of dC, or of the per-instance dC
+// partials with shared parameters) and D.rsum the row-sum scratch of chunks x c_total.
+constexpr int kParamChunk = 64;
+// Latents with more than kParamChunk children (FP32 path): the sum over children of
+// dmu_c W_c is formed in chunks of kParamChunk children, part[chunk][cs_total], then summed
+// in order into D.csum.  items: (node, first sample row) of every 64-row tile of those latents.
+void launch_child_sum(const Dev& D, const Tile* items, int nitems, int maxd, int chunks, long long cs_total,
+                      float* part, cudaStream_t s);
+void launch_param_dC(const Dev& D, int maxd, int maxobs, int maxn, long long c_total, float* part,
+                     cudaStream_t s);
 // out[e] = sum over rows r < R of in[r * stride + e], e < E: rows in order within chunks of
 // kRowChunk, chunk sums in order (a tree with a fixed shape: the result does not depend on the
 // launch).  scratch: rows_sum_scratch(R, E) floats.

@@ -104,6 +104,7 @@ tmc_status build_tables(const tmc_problem_desc* ds, Layout& L) {
     for (int i = 0; i < n; ++i) {
       NodeInfo& nd = h_nodes[node0 + i];
       nd = NodeInfo{};
+      nd.off_cs = -1;
       nd.b = b;
       nd.i = i;
       nd.parent = i ? node0 + par[i] : -1;

@@ -34,7 +34,8 @@ struct tmc_plan_s {
   // description
   int B = 0, shared = 0, precision = 0;
   double prior_var = 1.0, obs_var = 1.0;
-  int maxK = 0, maxd = 0, maxobs = 0, maxlevel = 0;
+  int maxK = 0, maxd = 0, maxobs = 0, maxlevel = 0, maxn = 0;
+  long long c_total = 0;  // size of dC (per-instance dC partials with shared parameters)
   int coupled = 0;      // coupled (non-factorised) proposal
   bool ragged = false;  // some instance has a different K or d from latent to latent
   long long shared_nW = 0, shared_nb = 0, shared_nC = 0, shared_rootW = 0;  // one instance's parameter sizes
@@ -66,8 +67,16 @@ struct tmc_plan_s {
   int* d_children = nullptr;
   int* d_nonroot = nullptr;
   Tile* d_tiles = nullptr;
+  // FP32 path, latents with more than kParamChunk children: their 64-row tiles, the chunk count
+  // of the largest, and the size of all their [K][d] children sums
+  std::vector<Tile> cs_items;
+  Tile* d_cs_items = nullptr;
+  int cs_chunks = 0;
+  long long cs_total = 0;
+  float* cs_part = nullptr;
   int* d_err = nullptr;
   void* ws = nullptr;
+  float* dc_part = nullptr;  // FP32 path: per-chunk dC partials of instances with many latents
   size_t ws_bytes = 0;
   Dev dev{};
   tc::TcWork tcw{};
@@ -260,6 +269,7 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
     in.off_pC = off_pC;
     p->insts.push_back(in);
     p->maxobs = std::max(p->maxobs, obs);
+    p->maxn = std::max(p->maxn, n);
     if (b == 0) {  // sizes of one instance's parameters (the shared reduction)
       p->shared_nW = w;
       p->shared_nb = q;
@@ -285,6 +295,7 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
   p->tot_nk = off_nk;
   p->tot_nkd = off_nkd;
   p->tot_q = off_q;
+  p->c_total = p->shared ? off_pC : off_C;
   // the materialised-factor baseline is built for one K and d per instance and a factorised
   // proposal
   if ((p->ragged || p->coupled) && p->precision == TMC_PREC_FP32_UNFUSED) return TMC_ERR_UNSUPPORTED;
@@ -356,6 +367,20 @@ tmc_status alloc_device(tmc_plan p) {
     TRY(upload(&p->d_root_chunks, p->root_chunks));
     TRY(upload(&p->d_root_chunk_off, p->root_chunk_off));
   }
+  p->cs_items.clear();
+  p->cs_chunks = 0;
+  p->cs_total = 0;
+  for (int g = 0; g < (int)p->nodes.size(); ++g) {
+    NodeInfo& nd = p->nodes[g];
+    nd.off_cs = -1;
+    const int nch = nd.child_end - nd.child_begin;
+    if (p->precision == TMC_PREC_FP16_TC || nch <= kParamChunk) continue;
+    nd.off_cs = p->cs_total;
+    p->cs_total += (long long)nd.K * nd.d;
+    p->cs_chunks = std::max(p->cs_chunks, (nch + kParamChunk - 1) / kParamChunk);
+    for (int r = 0; r < nd.K; r += kTile) p->cs_items.push_back(Tile{g, r});
+  }
+  if (!p->cs_items.empty()) TRY(upload(&p->d_cs_items, p->cs_items));
   TRY(upload(&p->d_nodes, p->nodes));
   TRY(upload(&p->d_insts, p->insts));
   TRY(upload(&p->d_children, p->children));
@@ -375,12 +400,20 @@ tmc_status alloc_device(tmc_plan p) {
   struct Sub { void** dst; size_t bytes; };
   float *zt, *mut, *zn, *mun, *u, *beta, *lam, *q, *nodemax, *dmu, *gz, *pW, *pbias, *pC, *fac, *rsum;
   // row-sum scratch: B instances (or fewer instance groups) of one instance's largest block
-  const long long nrs =
+  const bool tc_plan = p->precision == TMC_PREC_FP16_TC;
+  // FP32 path: the dC sum of an instance with more than kParamChunk latents is split into
+  // chunks (partials, then rows_sum)
+  const long long dc_chunks = tc_plan ? 1 : (p->maxn + kParamChunk - 1) / kParamChunk;
+  const long long ndcp = dc_chunks > 1 ? dc_chunks * p->c_total : 0;
+  const long long ncsp = p->cs_total ? (long long)p->cs_chunks * p->cs_total : 0;
+  const long long nrs = std::max(std::max(
       p->shared ? rows_sum_scratch(p->B, std::max(std::max(std::max(p->shared_nW, p->shared_nS), p->shared_nL2),
                                                   std::max(p->shared_nb, p->shared_nC)))
-                : 0;
+                : 0ll,
+      ndcp ? rows_sum_scratch(dc_chunks, p->c_total) : 0ll),
+      ncsp ? rows_sum_scratch(p->cs_chunks, p->cs_total) : 0ll);
+  float* csum = nullptr;
   double *nodeconst, *root_part;
-  const bool tc_plan = p->precision == TMC_PREC_FP16_TC;
   // FP32-path sample vectors (unused on the tc path, except T and G of coupled proposals, kept
   // in mut and gz)
   const long long nkd32 = tc_plan ? 0 : nkd, nkdc = (tc_plan && p->coupled) ? nkd : nkd32;
@@ -397,6 +430,9 @@ tmc_status alloc_device(tmc_plan p) {
       {(void**)&nodemax, sizeof(float) * G},   {(void**)&nodeconst, sizeof(double) * G},
       {(void**)&pW, sizeof(float) * nW},       {(void**)&pbias, sizeof(float) * nb},
       {(void**)&pC, sizeof(float) * nC},       {(void**)&rsum, sizeof(float) * nrs},
+      {(void**)&p->dc_part, sizeof(float) * ndcp},
+      {(void**)&p->cs_part, sizeof(float) * ncsp},
+      {(void**)&csum, sizeof(float) * p->cs_total},
       {(void**)&fac, sizeof(float) * p->fac_total},
       {(void**)&root_part, sizeof(double) * p->root_chunks.size() * p->maxK},
   };
@@ -431,6 +467,7 @@ tmc_status alloc_device(tmc_plan p) {
   D.nodemax = nodemax; D.nodeconst = nodeconst; D.dmu = dmu; D.gz = gz;
   D.pW = nW ? pW : nullptr; D.pbias = nb ? pbias : nullptr; D.pC = nC ? pC : nullptr;
   D.rsum = nrs ? rsum : nullptr;
+  D.csum = p->cs_total ? csum : nullptr;
   D.err = p->d_err;
   D.wait_limit = p->wait_limit;
   D.coupled = p->coupled;
@@ -461,6 +498,7 @@ void free_plan(tmc_plan p) {
   cudaFree(p->d_children);
   cudaFree(p->d_nonroot);
   cudaFree(p->d_tiles);
+  cudaFree(p->d_cs_items);
   cudaFree(p->d_fac_off);
   cudaFree(p->d_root_chunks);
   cudaFree(p->d_root_chunk_off);
@@ -632,12 +670,20 @@ tmc_status tmc_backward(tmc_plan p, const tmc_inputs* in, const double* grad_out
     if (sample_grads) TRY(timed(p, TMC_KC_SAMPLE_GRAD, s, [&] { tc::launch_dz(p->tcw, D, s); }));
     if (p->coupled) TRY(couple_grads());  // (k_dz_tc wrote the path gradients G)
   } else {
+    if (!p->cs_items.empty())
+      TRY(timed(p, TMC_KC_PARAM, s, [&] {
+        launch_child_sum(D, p->d_cs_items, (int)p->cs_items.size(), p->maxd, p->cs_chunks, p->cs_total,
+                         p->cs_part, s);
+      }));
     TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_node_grad(D, T + p->t_sample_b, p->t_sample_e - p->t_sample_b, s); }));
     TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_node_reduce(D, s); }));
     if (p->coupled) TRY(couple_grads());
     if (g->dW || g->dbias)
       TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_param_dW(D, p->d_nonroot, (int)p->nonroot.size(), p->maxd, s); }));
-    if (g->dC) TRY(timed(p, TMC_KC_PARAM, s, [&] { launch_param_dC(D, p->maxd, p->maxobs, s); }));
+    if (g->dC)
+      TRY(timed(p, TMC_KC_PARAM, s, [&] {
+        launch_param_dC(D, p->maxd, p->maxobs, p->maxn, p->c_total, p->dc_part, s);
+      }));
   }
   if (p->shared && (g->dW || g->dbias || g->dC))
     TRY(timed(p, TMC_KC_PARAM, s, [&] {
