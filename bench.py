@@ -420,6 +420,17 @@ def widening_leg(args, dev):
                      "max_abs_dlogp_vs_oracle": float(np.max(np.abs(lp[idx] - ref))),
                      "instances_checked": idx}
         del p
+    # config 2's materialised-factor baseline: the FP32 forward with and without the factors
+    # written to memory and read back
+    p = make_workload("chain_n8_K128_d32_B256")
+    ms_f, lp_f = time_forward(p, "fp32", dev, steps=10, warmup=3)
+    ms_u, lp_u = time_forward(p, "fp32_unfused", dev, steps=10, warmup=3)
+    ms_t, _ = time_forward(p, "fp16", dev, steps=10, warmup=3)
+    res["unfused:chain_n8_K128_d32_B256"] = {
+        "what": "forward only: fused FP32 kernels against the materialised-factor baseline",
+        "fused_fp32_fwd_ms": ms_f, "unfused_fp32_fwd_ms": ms_u, "fused_speedup": ms_u / ms_f,
+        "fp16_fwd_ms": ms_t, "factor_bytes_written": 4 * p.edge_entries(),
+        "max_abs_dlogp_unfused_vs_fused": float(np.max(np.abs(lp_u - lp_f)))}
     return res
 
 
