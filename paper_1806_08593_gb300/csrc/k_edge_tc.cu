@@ -2678,7 +2678,7 @@ __global__ void __launch_bounds__(kThreads) k_leaf_S(Dev D, TcDev T) {
 // X = sum_leaves x~ (zbar + m)^T is split over the leaves like k_leaf_S when the tile has
 // fewer entries than threads.
 __global__ void __launch_bounds__(kThreads) k_asm_dC(Dev D, TcDev T) {
-  __shared__ TileSmemDeep sm;
+  __shared__ TileSmem sm;
   __shared__ float part[kThreads];
   const InstInfo in = D.insts[blockIdx.x];
   const int d = in.d, obs = in.obs;
@@ -2692,7 +2692,7 @@ __global__ void __launch_bounds__(kThreads) k_asm_dC(Dev D, TcDev T) {
   zero_acc(acc);
   // acc = C[o0.., :] S[:, c0..]; a shared C multiplies the instance sum of S once (k_shared_dC)
   if (!D.shared)
-    tile_gemm_deep<true, false>(acc, C + (long long)o0 * d, d, rows, T.S + (long long)blockIdx.x * kLdp * kLdp + c0,
+    tile_gemm<true, false>(acc, C + (long long)o0 * d, d, rows, T.S + (long long)blockIdx.x * kLdp * kLdp + c0,
                            kLdp, cols, d, sm);
   float X[4][4];
   zero_acc(X);

@@ -61,7 +61,9 @@ __device__ __forceinline__ float block_sum_f(float v, float* red) {
 
 // ---------------------------------------------------------------------------------------
 // FP64 node constants: sum_j logs_ij + (d/2) log 2pi  (from -log Q_i)
-//   + root: -(d/2) log(2 pi prior_var)   + leaf: -(obs/2) log(2 pi obs_var)
+//   - (d/2) log(2 pi prior_var)  (the prior or transition normaliser)
+//   - log K_i for i >= 1  (Eq. (is)'s 1 / K_i; the root's is added by k_root)
+//   + leaf: -(obs/2) log(2 pi obs_var)
 // ---------------------------------------------------------------------------------------
 // One warp per node (8 nodes per CTA): lanes sum logs_i over the dimension in FP64.
 constexpr int kConstNodesPerCta = 8;
@@ -72,10 +74,10 @@ __global__ void __launch_bounds__(32 * kConstNodesPerCta) k_node_const(Dev D) {
   double s = 0.0;
   for (int j = lane; j < nd.d; j += 32) s += (double)D.q_logstd[nd.off_q + j];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) {
-    double c = s + 0.5 * nd.d * kLog2Pi;
-    if (nd.parent < 0) c += -0.5 * nd.d * (kLog2Pi + log(D.prior_var));
-    if (nd.leaf_slot >= 0) c += -0.5 * nd.obs * (kLog2Pi + log(D.obs_var));
+  if (lane == 0) {  // proposal and prior normalisers, the observation's, and 1 / K_i (Eq. (is))
+    double c = s + 0.5 * nd.d * kLog2Pi - 0.5 * nd.d * (kLog2Pi + D.log_prior_var);
+    if (nd.parent >= 0) c -= nd.log_K;
+    if (nd.leaf_slot >= 0) c += -0.5 * nd.obs * (kLog2Pi + D.log_obs_var);
     D.nodeconst[g] = c;
   }
 }
@@ -237,8 +239,7 @@ constexpr int kRootThreads = 1024;
 // Root: closes the sum of Eq. (is) in FP64.
 //   beta'_0 = u_0 + sum_children lam_c (FP64: a root may have thousands of children),
 //   M_0 = max beta'_0,  beta_0 = beta'_0 - M_0,
-//   log P = sum_nodes (nodeconst + M) + sum_{i>=1} (-(d/2) log(2 pi prior_var) - log K)
-//           + log sum_k exp(beta_0[k]) - log K_0,
+//   log P = sum_nodes (nodeconst + M) + log sum_k exp(beta_0[k]) - log K_0,
 // and the root's sample weights q_0[k] = exp(beta_0[k] - logsumexp(beta_0)).
 // ---------------------------------------------------------------------------------------
 // A chunk of a wide root's children: their messages summed per sample, in child order.
@@ -306,16 +307,12 @@ __global__ void k_root(Dev D) {
   const float lse = logf(s);
   for (int k = threadIdx.x; k < K; k += blockDim.x) D.q[nd.off_nk + k] = expf((float)(sbd[k] - mxd) - lse);
   double acc = 0.0;
-  for (int g = in.node0 + threadIdx.x; g < in.node0 + in.n; g += blockDim.x) {
-    const NodeInfo ng = D.nodes[g];
-    double m = (g == in.node0) ? mxd : (double)D.nodemax[g];
-    acc += D.nodeconst[g] + m;
-    if (ng.parent >= 0) acc += -0.5 * ng.d * (kLog2Pi + log(D.prior_var)) - log((double)ng.K);
-  }
+  for (int g = in.node0 + threadIdx.x; g < in.node0 + in.n; g += blockDim.x)
+    acc += D.nodeconst[g] + ((g == in.node0) ? mxd : (double)D.nodemax[g]);
   acc = block_sum_d(acc, redd);
   if (threadIdx.x == 0) {
     D.nodemax[in.node0] = mx;
-    const double lp = acc + (double)lse - log((double)K);
+    const double lp = acc + (double)lse - nd.log_K;
     D.log_phat[blockIdx.x] = lp;
     if (!isfinite(lp)) flag_error(D.err, kErrNumeric);
   }
@@ -701,7 +698,11 @@ void launch_root(const Dev& D, int maxK, int root_fanout, cudaStream_t s) {
                                            (kMaxK + kRootThreads) * (int)sizeof(double)), true);
   (void)once;
   if (D.root_part) k_root_children<<<D.root_nchunk, 256, 0, s>>>(D);
-  const int threads = (root_fanout > 32 && !D.root_part) ? kRootThreads : 256;
+  // wide roots summed in the kernel take kRootThreads; otherwise 256, or one or a few warps
+  // when every root has few samples (many small instances)
+  const int threads = (root_fanout > 32 && !D.root_part) ? kRootThreads
+                      : maxK <= 128                      ? std::max(32, (maxK + 31) / 32 * 32)
+                                                         : 256;
   k_root<<<D.num_inst, threads, (maxK + threads) * sizeof(double), s>>>(D);
 }
 void launch_node_grad(const Dev& D, const Tile* tiles, int ntiles, cudaStream_t s) {

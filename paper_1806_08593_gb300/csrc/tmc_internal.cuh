@@ -38,6 +38,7 @@ struct NodeInfo {
   long long off_A;     // start of A_i ([d][dp]) in q_A / dq_A (per instance, like unshared W)
   long long off_S;     // start of this latent's dp x dp block in one instance's packed [dp x dp]
                        // blocks of the non-root latents (the root's block is empty)
+  double log_K;        // log K_i (host-computed)
   long long off_cs;    // FP32 path, latents with more than kParamChunk children: start of the
                        // [K][d] sum over children of dmu_c W_c (k_child_sum); -1 otherwise
 };
@@ -67,6 +68,7 @@ struct Dev {
   int num_nodes, num_inst;
   float inv_var, inv_obs_var;   // 1/prior_var, 1/obs_var
   double prior_var, obs_var;
+  double log_prior_var, log_obs_var;  // their logarithms (host-computed: FP64 log is slow here)
   int shared;
 
   // inputs (caller's device memory)

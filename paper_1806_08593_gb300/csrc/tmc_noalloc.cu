@@ -10,6 +10,7 @@
 // holds kNoAllocScratchBytes until the process exits.  Every call shares it: a call rewrites
 // all of it that it reads, and two calls whose work overlaps on the GPU (different streams,
 // or different host threads) race on it -- serialise them.
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -109,6 +110,7 @@ tmc_status build_tables(const tmc_problem_desc* ds, Layout& L) {
       nd.i = i;
       nd.parent = i ? node0 + par[i] : -1;
       nd.K = K;
+      nd.log_K = std::log((double)K);
       nd.d = d;
       nd.Kp = i ? K : 0;
       nd.dp = d;
@@ -235,6 +237,8 @@ extern "C" tmc_status tmc_log_marginal_noalloc(const tmc_problem_desc* desc, con
   D.inv_obs_var = (float)(1.0 / desc->obs_var);
   D.prior_var = desc->prior_var;
   D.obs_var = desc->obs_var;
+  D.log_prior_var = std::log(desc->prior_var);
+  D.log_obs_var = std::log(desc->obs_var);
   D.shared = desc->shared_params ? 1 : 0;
   D.eps = in->eps; D.q_mean = in->q_mean; D.q_logstd = in->q_logstd;
   D.W = in->W; D.bias = in->bias; D.C = in->C; D.x = in->x;

@@ -227,6 +227,7 @@ tmc_status build_plan(const tmc_problem_desc* ds, tmc_plan p) {
       nd.i = i;
       nd.parent = i ? node0 + par[i] : -1;
       nd.K = Kv[i];
+      nd.log_K = std::log((double)Kv[i]);
       nd.d = dv[i];
       nd.Kp = i ? Kv[par[i]] : 0;
       nd.dp = i ? dv[par[i]] : dv[0];
@@ -462,6 +463,8 @@ tmc_status alloc_device(tmc_plan p) {
   D.inv_obs_var = (float)(1.0 / p->obs_var);
   D.prior_var = p->prior_var;
   D.obs_var = p->obs_var;
+  D.log_prior_var = std::log(p->prior_var);
+  D.log_obs_var = std::log(p->obs_var);
   D.shared = p->shared;
   D.zt = zt; D.mut = mut; D.zn = zn; D.mun = mun; D.u = u; D.beta = beta; D.lam = lam; D.q = q;
   D.nodemax = nodemax; D.nodeconst = nodeconst; D.dmu = dmu; D.gz = gz;
