@@ -3283,12 +3283,6 @@ void launch_unpack_grads(TcWork& w, const Dev& D, cudaStream_t s) {
       const int np = w.num_slots - 1;
       k_wtw<<<dim3(np, ty), kThreads, 0, s>>>(D, w.t);
       k_asm_shared<<<dim3(np, ty, w.asm_groups), kThreads, 0, s>>>(D, w.t, w.shared_nW, w.shared_nS);
-      if (D.dW) {
-        const long long nw = w.shared_nW - w.shared_rootW;
-        rows_sum(w.t.Ppart + w.shared_rootW, w.asm_groups, nw, w.shared_nW, w.t.P + w.shared_rootW, D.rsum, s);
-        rows_sum(w.t.Spart, w.asm_groups, w.shared_nS, w.shared_nS, w.t.S2, D.rsum, s);
-        k_shared_dw<<<dim3(np, ty), kThreads, 0, s>>>(D, w.t);
-      }
     } else {
       k_asm_edge_mat<<<dim3(nr, ty), kThreads, 0, s>>>(D, w.t, w.d_nonroot);
     }
@@ -3297,12 +3291,26 @@ void launch_unpack_grads(TcWork& w, const Dev& D, cudaStream_t s) {
   else k_asm_node<1><<<D.num_nodes, kTcMaxD, 0, s>>>(D, w.t);
   k_leaf_S<<<dim3(D.num_inst, w.maxdp > 64 ? 4 : 1), kThreads, 0, s>>>(D, w.t);
   k_asm_dC<<<dim3(D.num_inst, (w.maxobs + kTile - 1) / kTile, w.maxdp / kTile), kThreads, 0, s>>>(D, w.t);
-  if (D.shared && D.dC) {  // one product of C with the instance sum of S
-    const long long nC = (long long)w.obs0 * w.leaf_d, nS = (long long)w.leaf_d * w.leaf_d;
-    rows_sum(D.pC, w.num_inst, nC, nC, D.dC, D.rsum, s);
-    rows_sum(w.t.S, w.num_inst, nS, nS, w.t.Ssum, D.rsum, s);
-    k_shared_dC<<<dim3((w.obs0 + kTile - 1) / kTile, (w.leaf_d + kTile - 1) / kTile), kThreads, 0, s>>>(D, w.t);
+  if (!D.shared) return;
+  // shared parameters: every sum over instances (groups) in one launch, then the two products
+  // with the shared W_c and C
+  RowSeg segs[kMaxRowSegs];
+  int n = 0;
+  const long long nw = w.shared_nW - w.shared_rootW;
+  const long long nC = (long long)w.obs0 * w.leaf_d, nS = (long long)w.leaf_d * w.leaf_d;
+  if (D.dW && nr) {
+    segs[n++] = RowSeg{w.t.Ppart + w.shared_rootW, w.t.P + w.shared_rootW, w.asm_groups, nw, w.shared_nW};
+    segs[n++] = RowSeg{w.t.Spart, w.t.S2, w.asm_groups, w.shared_nS, w.shared_nS};
   }
+  if (D.dC) {
+    segs[n++] = RowSeg{D.pC, D.dC, w.num_inst, nC, nC};
+    segs[n++] = RowSeg{w.t.S, w.t.Ssum, w.num_inst, nS, nS};
+  }
+  if (D.dbias && D.pbias) segs[n++] = RowSeg{D.pbias, D.dbias, w.num_inst, w.shared_nb, w.shared_nb};
+  rows_sum_batch(segs, n, D.rsum, s);
+  if (D.dW && nr) k_shared_dw<<<dim3(w.num_slots - 1, w.maxdp > 64 ? 4 : 1), kThreads, 0, s>>>(D, w.t);
+  if (D.dC)  // one product of C with the instance sum of S
+    k_shared_dC<<<dim3((w.obs0 + kTile - 1) / kTile, (w.leaf_d + kTile - 1) / kTile), kThreads, 0, s>>>(D, w.t);
 }
 
 }  // namespace tc

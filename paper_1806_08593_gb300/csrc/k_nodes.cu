@@ -728,6 +728,49 @@ void launch_param_dC(const Dev& D, int maxd, int maxobs, int maxn, long long c_t
                kMaxD * sizeof(float), s>>>(D, ctiles, chunks > 1 ? part : nullptr, c_total);
   if (chunks > 1 && out) rows_sum(part, chunks, c_total, c_total, out, D.rsum, s);
 }
+struct RowSegs {
+  RowSeg s[kMaxRowSegs];
+  int blk0[kMaxRowSegs + 1];  // first block of each segment
+  int n;
+};
+// Single-level sums of several segments (R <= kRowChunk each): block b belongs to the last
+// segment whose first block is <= b; the sum is the one k_rows_sum forms (rows in order, 32
+// loads in flight).
+__global__ void __launch_bounds__(256) k_rows_sum_multi(RowSegs S) {
+  int si = 0;
+  while (si + 1 < S.n && (int)blockIdx.x >= S.blk0[si + 1]) ++si;
+  const RowSeg g = S.s[si];
+  const long long e = (long long)(blockIdx.x - S.blk0[si]) * 256 + threadIdx.x;
+  if (e >= g.E) return;
+  float s = 0.f;
+  for (long long r = 0; r < g.R; r += 32) {
+    float v[32];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) v[u] = r + u < g.R ? __ldg(g.in + (r + u) * g.stride + e) : 0.f;
+#pragma unroll
+    for (int u = 0; u < 32; ++u) s += v[u];
+  }
+  g.out[e] = s;
+}
+
+void rows_sum_batch(const RowSeg* segs, int n, float* scratch, cudaStream_t s) {
+  RowSegs S{};
+  int blocks = 0;
+  for (int i = 0; i < n; ++i) {
+    if (segs[i].E <= 0) continue;
+    if (segs[i].R > kRowChunk) {
+      rows_sum(segs[i].in, segs[i].R, segs[i].E, segs[i].stride, segs[i].out, scratch, s);
+      continue;
+    }
+    S.s[S.n] = segs[i];
+    S.blk0[S.n] = blocks;
+    blocks += (int)((segs[i].E + 255) / 256);
+    ++S.n;
+  }
+  S.blk0[S.n] = blocks;
+  if (S.n) k_rows_sum_multi<<<blocks, 256, 0, s>>>(S);
+}
+
 void rows_sum(const float* in, long long R, long long E, long long stride, float* out, float* scratch,
               cudaStream_t s) {
   if (E <= 0) return;
@@ -754,12 +797,14 @@ void rows_sum(const float* in, long long R, long long E, long long stride, float
 void launch_shared_reduce(const Dev& D, long long nW, long long nb, long long nC, long long rootW,
                           bool tc_done, cudaStream_t s) {
   const long long B = D.num_inst;
-  if (D.dW) {
-    if (rootW) cudaMemsetAsync(D.dW, 0, sizeof(float) * rootW, s);
-    if (!tc_done && nW > rootW) rows_sum(D.pW + rootW, B, nW - rootW, nW, D.dW + rootW, D.rsum, s);
-  }
-  if (D.dbias && nb) rows_sum(D.pbias, B, nb, nb, D.dbias, D.rsum, s);
-  if (D.dC && nC && !tc_done) rows_sum(D.pC, B, nC, nC, D.dC, D.rsum, s);
+  if (D.dW && rootW) cudaMemsetAsync(D.dW, 0, sizeof(float) * rootW, s);
+  if (tc_done) return;
+  RowSeg segs[3];
+  int n = 0;
+  if (D.dW && nW > rootW) segs[n++] = RowSeg{D.pW + rootW, D.dW + rootW, B, nW - rootW, nW};
+  if (D.dbias && nb) segs[n++] = RowSeg{D.pbias, D.dbias, B, nb, nb};
+  if (D.dC && nC) segs[n++] = RowSeg{D.pC, D.dC, B, nC, nC};
+  rows_sum_batch(segs, n, D.rsum, s);
 }
 void launch_root_bias(const Dev&, cudaStream_t) {}
 

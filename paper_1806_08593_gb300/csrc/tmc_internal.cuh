@@ -155,9 +155,18 @@ inline long long rows_sum_scratch(long long R, long long E) {
 }
 void rows_sum(const float* in, long long R, long long E, long long stride, float* out, float* scratch,
               cudaStream_t s);
+// Several row sums at once: each segment with R <= kRowChunk rows is summed exactly as rows_sum
+// sums it (one launch for all of them); longer ones go through rows_sum.
+struct RowSeg {
+  const float* in;
+  float* out;
+  long long R, E, stride;
+};
+constexpr int kMaxRowSegs = 6;
+void rows_sum_batch(const RowSeg* segs, int n, float* scratch, cudaStream_t s);
 // nW, nb, nC: one instance's W, bias, C sizes; rootW: its unused root block of W; tc_done: dW
-// past the root block and dC are already written (the tensor-core path), the root block of dW
-// is zeroed and dbias reduced
+// past the root block, dbias and dC are already written (the tensor-core path), only the root
+// block of dW is zeroed
 void launch_shared_reduce(const Dev& D, long long nW, long long nb, long long nC, long long rootW,
                           bool tc_done, cudaStream_t s);
 void launch_root_bias(const Dev& D, cudaStream_t s);

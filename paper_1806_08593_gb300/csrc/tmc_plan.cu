@@ -442,6 +442,7 @@ tmc_status alloc_device(tmc_plan p) {
   p->tcw.precision = p->precision;
   p->tcw.shared_nW = p->shared_nW;
   p->tcw.shared_nS = p->shared_nS;
+  p->tcw.shared_nb = p->shared_nb;
   if (tc_plan) tc::workspace_layout(p->tcw, p->nodes, nk, nkd, tsubs);
   size_t total = 0;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };

@@ -107,7 +107,7 @@ struct TcWork {
   int n_pack_w = 0;               // leading non-root nodes whose W is packed
   // shared parameters: one instance's W size, its root block, its packed dp x dp blocks, and
   // the instance groups of the gradient assembly
-  long long shared_nW = 0, shared_rootW = 0, shared_nS = 0;
+  long long shared_nW = 0, shared_rootW = 0, shared_nS = 0, shared_nb = 0;
   int asm_groups = 0, leaf_d = 0, obs0 = 0;
   // observation term: split C rows and the 128-sample leaf tiles per d class
   long long c_rows = 0;
