@@ -1850,11 +1850,16 @@ __global__ void __launch_bounds__(kMoThreads, 1)
         if (pj >= nb) return;
         const long long prow = __shfl_sync(0xffffffffu, rec.row, pj);
         const int pnr = __shfl_sync(0xffffffffu, rec.nrows, pj);
-        if (lane == 0)
+        if (lane == 0) {
           for (int b = 0; b < NB; ++b) {
             tma_prefetch_l2_2d(&mZH, b * 64, (int)(prow + pu * kMoUnit));
             tma_prefetch_l2_2d(&mZL, b * 64, (int)(prow + pu * kMoUnit));
           }
+          // the unit's sample weights (two 128-byte lines), read by the weight loads below
+          const float* qp = D.q + prow + pu * kMoUnit;
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(qp) : "memory");
+          if (pu * kMoUnit + 32 < pnr) asm volatile("prefetch.global.L2 [%0];" ::"l"(qp + 32) : "memory");
+        }
         if (++pu * kMoUnit >= pnr) {
           pu = 0;
           ++pj;
