@@ -1749,7 +1749,7 @@ constexpr int kMoSlabs = 8;
 constexpr int kMoMath = 256;                 // math warps 0-7
 constexpr int kMoProd = kMoMath / 32;        // producer warp; the MMA warp follows, then 4 epilogue warps
 constexpr int kMoThreads = kMoMath + 6 * 32;
-constexpr int kMoPrefetch = 6;               // units prefetched into L2 ahead of the ring loads
+constexpr int kMoPrefetch = 4;               // units prefetched into L2 ahead of the ring loads
 constexpr int kMoUnit = 64;                  // samples per unit
 constexpr int kMoAtom = kMoUnit * 128;       // one 64-row, 128-byte-swizzled atom
 constexpr int kMoXLd = 68;                   // row stride (floats) of the epilogue scratch
