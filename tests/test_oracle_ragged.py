@@ -125,3 +125,24 @@ def test_ragged_grad_vs_central_differences(fn_name, shared):
             b = base.copy(); b[i] -= H
             fd = (np.dot(go, fn(p, **{name: a})) - np.dot(go, fn(p, **{name: b}))) / (2 * H)
             assert abs(fd - ga[i]) <= 2e-5 * max(1.0, abs(ga[i])), (name, int(i), fd, ga[i])
+
+
+def test_instance_slices_partition_the_flat_arrays():
+    """Problem.slices_all (one pass) gives every instance the same slices as slices(b), and the
+    per-instance slices of the per-instance arrays tile them without gaps or overlap; subset()
+    of every instance reproduces the batch's oracle result."""
+    import oracle
+    p = wl.ragged_trees(9, seed=641)
+    every = p.slices_all()
+    assert len(every) == p.B
+    for key, arr in (("eps", p.eps), ("q", p.q_mean), ("x", p.x), ("W", p.W), ("C", p.C)):
+        end = 0
+        for b in range(p.B):
+            assert every[b] == p.slices(b)
+            lo, hi = every[b][key]
+            assert lo == end and hi >= lo
+            end = hi
+        assert end == arr.size, key
+    whole = oracle.log_marginal(p)
+    parts = oracle.log_marginal(oracle.subset(p, list(range(p.B))))
+    np.testing.assert_array_equal(whole, parts)
